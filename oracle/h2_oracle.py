@@ -1,0 +1,514 @@
+"""Plain, slow FP64 CPU oracle for the H²-matrix × dense-block product and block CG.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline / reference leg may import this module.  The
+library in ``paper_2509_17257_gb300`` never imports, links or calls it, and
+this module imports nothing from the library: the two share no code.
+
+What it follows (arXiv 2509.17257, "On efficient block Krylov solvers for
+H²-matrices"):
+
+* Sec. 2, Def. "Cluster tree"          -> :func:`build_cluster_tree`
+* Sec. 2, Def. "Block tree"            -> :func:`build_block_tree`
+* Sec. 2, Eq. (admiss)                 -> :func:`admissible`
+* Sec. 2, Eq. (h2_admissible) and Def. "Cluster basis" (nested bases with
+  transfer matrices E), built here by tensor Chebyshev interpolation, one of
+  the constructions Sec. 2 names   -> :class:`H2Matrix`
+* Sec. 3, Alg. "H2_mvm" (forward transformation, multiplication phase
+  "fast_addeval", backward transformation) with the coefficient blocks of
+  Sec. 4 (x̂_s, ŷ_t in K^{k×m})  -> :func:`h2mm`
+* Sec. 5.1, Alg. "block CG" (per-column α_i, β_i, γ_i) -> :func:`block_cg`
+
+Readings where the paper is silent (split rule, diam/dist of point boxes,
+interpolation nodes, kernel, shift, stopping rule) are the ones stated in the
+docstrings below; the same readings are listed in the design doc.
+
+Parity status: every function here is pinned by ``tests/test_oracle_*.py``
+against closed forms, brute force or library routines (see each test).  The
+interpolation *accuracy* against the exact kernel has no number in the paper
+to compare with; it is pinned only by its decay in q.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "Cluster",
+    "Block",
+    "build_cluster_tree",
+    "clusters_preorder",
+    "diam",
+    "dist",
+    "admissible",
+    "build_block_tree",
+    "leaf_blocks",
+    "exp_kernel",
+    "cluster_nodes",
+    "tensor_nodes",
+    "lagrange_1d",
+    "tensor_lagrange",
+    "H2Matrix",
+    "h2mm",
+    "dense_expand",
+    "kernel_matrix",
+    "block_cg",
+    "CGResult",
+]
+
+
+# ---------------------------------------------------------------------------
+# Cluster tree (Sec. 2, Def. "Cluster tree")
+# ---------------------------------------------------------------------------
+class Cluster:
+    """A node t of the cluster tree T_I.
+
+    ``idx``  : original point indices of the label t̂, in pre-order (the
+               concatenation of the sons' labels), so t̂ is the contiguous range
+               [offset, offset + size) of the permutation ``root.idx``.
+    ``lo/hi``: the tight axis-aligned bounding box of the points of t̂.
+    """
+
+    __slots__ = ("idx", "lo", "hi", "sons", "level", "offset", "parent", "id")
+
+    def __init__(self, idx, lo, hi, level, offset, parent):
+        self.idx = idx
+        self.lo = lo
+        self.hi = hi
+        self.sons = []
+        self.level = level
+        self.offset = offset
+        self.parent = parent
+        self.id = -1
+
+    @property
+    def size(self) -> int:
+        return int(self.idx.shape[0])
+
+    @property
+    def is_leaf(self) -> bool:
+        return not self.sons
+
+
+def build_cluster_tree(points: np.ndarray, leaf_size: int) -> Cluster:
+    """Recursive geometric bisection (Sec. 2: split into non-overlapping parts
+    until each cluster is small).
+
+    Split rule (the paper gives none; this is the reading used on both sides):
+    a cluster with more than ``leaf_size`` points is split; its box is the
+    tight AABB of its points; the longest side (ties -> lowest axis) is cut at
+    its midpoint ``(lo + hi) * 0.5``; points with coordinate <= midpoint form
+    son 0, the rest son 1, both in their current order.  If one side would be
+    empty (coincident points), the index range is halved instead: the first
+    ``size // 2`` points form son 0.
+    """
+    points = np.asarray(points, dtype=np.float64)
+    n = points.shape[0]
+    if n < 1:
+        raise ValueError("empty point set")
+
+    def rec(idx, level, offset, parent):
+        pts = points[idx]
+        lo = pts.min(axis=0)
+        hi = pts.max(axis=0)
+        c = Cluster(idx, lo, hi, level, offset, parent)
+        if idx.shape[0] > leaf_size:
+            w = hi - lo
+            d = int(np.argmax(w))  # first maximal side
+            mid = (lo[d] + hi[d]) * 0.5
+            mask = pts[:, d] <= mid
+            i0 = idx[mask]
+            i1 = idx[~mask]
+            if i0.shape[0] == 0 or i1.shape[0] == 0:
+                h = idx.shape[0] // 2
+                i0, i1 = idx[:h], idx[h:]
+            s0 = rec(i0, level + 1, offset, c)
+            s1 = rec(i1, level + 1, offset + i0.shape[0], c)
+            c.sons = [s0, s1]
+            c.idx = np.concatenate([s0.idx, s1.idx])
+        return c
+
+    root = rec(np.arange(n, dtype=np.int64), 0, 0, None)
+    for i, c in enumerate(clusters_preorder(root)):
+        c.id = i
+    return root
+
+
+def clusters_preorder(root: Cluster):
+    """All clusters in pre-order (parent before sons, son 0 before son 1)."""
+    out = []
+    stack = [root]
+    while stack:
+        c = stack.pop()
+        out.append(c)
+        stack.extend(reversed(c.sons))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Admissibility (Sec. 2, Eq. (admiss))
+# ---------------------------------------------------------------------------
+def diam(c: Cluster) -> float:
+    """Euclidean length of the box diagonal, sqrt((w0² + w1²) + w2²)."""
+    w0 = float(c.hi[0] - c.lo[0])
+    w1 = float(c.hi[1] - c.lo[1])
+    w2 = float(c.hi[2] - c.lo[2])
+    return math.sqrt((w0 * w0 + w1 * w1) + w2 * w2)
+
+
+def dist(t: Cluster, s: Cluster) -> float:
+    """Euclidean distance between the two boxes (0 when they touch or overlap)."""
+    g = []
+    for d in range(3):
+        a = float(s.lo[d] - t.hi[d])
+        b = float(t.lo[d] - s.hi[d])
+        g.append(max(a, b, 0.0))
+    return math.sqrt((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2])
+
+
+def admissible(t: Cluster, s: Cluster, eta: float) -> bool:
+    """Eq. (admiss): max{diam t, diam s} <= eta·dist(t, s), with dist > 0 required."""
+    dd = dist(t, s)
+    if not dd > 0.0:
+        return False
+    return max(diam(t), diam(s)) <= eta * dd
+
+
+# ---------------------------------------------------------------------------
+# Block tree (Sec. 2, Def. "Block tree")
+# ---------------------------------------------------------------------------
+@dataclass(eq=False)
+class Block:
+    t: Cluster
+    s: Cluster
+    kind: str  # "adm" (L+), "near" (L-), or "inner"
+    sons: list = field(default_factory=list)
+
+
+def build_block_tree(root_t: Cluster, root_s: Cluster, eta: float) -> Block:
+    """Block tree from (root, root) with the sons rule of Def. "Block tree".
+
+    Stopping (the paper gives only the sons rule): a block is a leaf iff it is
+    admissible (L+) or both clusters are leaves (then it is in L-).
+    """
+
+    def rec(t, s):
+        if admissible(t, s, eta):
+            return Block(t, s, "adm")
+        if t.is_leaf and s.is_leaf:
+            return Block(t, s, "near")
+        b = Block(t, s, "inner")
+        if t.is_leaf:
+            b.sons = [rec(t, s2) for s2 in s.sons]
+        elif s.is_leaf:
+            b.sons = [rec(t2, s) for t2 in t.sons]
+        else:
+            b.sons = [rec(t2, s2) for t2 in t.sons for s2 in s.sons]
+        return b
+
+    return rec(root_t, root_s)
+
+
+def leaf_blocks(b: Block):
+    """The leaves L_{I×J} of a block tree, split into (admissible, inadmissible)."""
+    adm, near = [], []
+    stack = [b]
+    while stack:
+        x = stack.pop()
+        if x.kind == "adm":
+            adm.append(x)
+        elif x.kind == "near":
+            near.append(x)
+        else:
+            stack.extend(reversed(x.sons))
+    return adm, near
+
+
+# ---------------------------------------------------------------------------
+# Kernel function g and tensor Chebyshev interpolation (Sec. 2)
+# ---------------------------------------------------------------------------
+def exp_kernel(length: float = 0.5):
+    """g(x, y) = exp(-||x - y||_2 / length), broadcasting over leading axes."""
+
+    def g(x, y):
+        d = x - y
+        r = np.sqrt((d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2])
+        return np.exp(-r / length)
+
+    return g
+
+
+def cluster_nodes(c: Cluster, q: int) -> np.ndarray:
+    """Chebyshev points of the first kind mapped to the cluster's box, shape (3, q).
+
+    node_{d,i} = center_d + half_d · cos((2i+1)π / (2q)).  A degenerate side
+    (half-width below 1e-8 × the largest half-width) is widened to that floor so
+    the nodes stay distinct; a box with no extent at all gets half-widths 1e-8.
+    """
+    center = (c.lo + c.hi) * 0.5
+    half = (c.hi - c.lo) * 0.5
+    hmax = float(half.max())
+    floor = 1e-8 * hmax if hmax > 0.0 else 1e-8
+    half = np.maximum(half, floor)
+    ref = np.cos((2.0 * np.arange(q) + 1.0) * math.pi / (2.0 * q))
+    return center[:, None] + half[:, None] * ref[None, :]
+
+
+def tensor_nodes(nodes: np.ndarray) -> np.ndarray:
+    """The k = q³ tensor nodes, shape (k, 3), with index ν = ν_x + q·ν_y + q²·ν_z."""
+    q = nodes.shape[1]
+    out = np.empty((q ** 3, 3))
+    for nz in range(q):
+        for ny in range(q):
+            for nx in range(q):
+                nu = nx + q * ny + q * q * nz
+                out[nu] = (nodes[0, nx], nodes[1, ny], nodes[2, nz])
+    return out
+
+
+def lagrange_1d(nodes_1d: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """L_i(x) = prod_{j != i} (x - ξ_j) / (ξ_i - ξ_j); returns shape (len(x), q)."""
+    x = np.asarray(x, dtype=np.float64)
+    q = nodes_1d.shape[0]
+    out = np.ones((x.shape[0], q))
+    for i in range(q):
+        for j in range(q):
+            if j != i:
+                out[:, i] *= (x - nodes_1d[j]) / (nodes_1d[i] - nodes_1d[j])
+    return out
+
+
+def tensor_lagrange(nodes: np.ndarray, pts: np.ndarray) -> np.ndarray:
+    """Tensor Lagrange polynomials L_ν(x) = L_{ν_x}(x_0) L_{ν_y}(x_1) L_{ν_z}(x_2), shape (len(pts), k)."""
+    q = nodes.shape[1]
+    lx = lagrange_1d(nodes[0], pts[:, 0])
+    ly = lagrange_1d(nodes[1], pts[:, 1])
+    lz = lagrange_1d(nodes[2], pts[:, 2])
+    out = np.empty((pts.shape[0], q ** 3))
+    for nz in range(q):
+        for ny in range(q):
+            for nx in range(q):
+                out[:, nx + q * ny + q * q * nz] = lx[:, nx] * ly[:, ny] * lz[:, nz]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# The H² matrix (Sec. 2, Def. "H²-matrix"; W = V since I = J and g is real)
+# ---------------------------------------------------------------------------
+class H2Matrix:
+    """Interpolation-based H² matrix A = Â + σI for a point cloud.
+
+    * leaf matrices   V_t[i, ν] = L_{t,ν}(x_i), t leaf (Def. "Cluster basis")
+    * transfer        E_{t'}[μ, ν] = L_{t,ν}(ξ_{t',μ}), t = father of t', so
+                      that V_t|_{t̂'×k} = V_{t'} E_{t'}
+    * coupling        S_b[ν, μ] = g(ξ_{t,ν}, ξ_{s,μ}), b = (t, s) ∈ L+ (Eq. (h2_admissible))
+    * nearfield       G_b[i, j] = g(x_i, x_j), b ∈ L-  (stored explicitly, Sec. 2)
+    * shift           σ on the diagonal only, applied separately.
+
+    Over R the paper's W_s* and E* become transposes, and W = V.
+    """
+
+    def __init__(self, points, q=3, leaf_size=64, eta=2.0, kernel=None, sigma=0.0, length=0.5):
+        self.points = np.ascontiguousarray(points, dtype=np.float64)
+        self.n = self.points.shape[0]
+        self.q = q
+        self.k = q ** 3
+        self.eta = eta
+        self.sigma = float(sigma)
+        self.g = kernel if kernel is not None else exp_kernel(length)
+        self.root = build_cluster_tree(self.points, leaf_size)
+        self.clusters = clusters_preorder(self.root)
+        self.perm = self.root.idx
+        self.btree = build_block_tree(self.root, self.root, eta)
+        self.adm, self.near = leaf_blocks(self.btree)
+        self.nodes = {c.id: cluster_nodes(c, q) for c in self.clusters}
+        self.tnodes = {c.id: tensor_nodes(self.nodes[c.id]) for c in self.clusters}
+        self.V = {}
+        self.E = {}
+        for c in self.clusters:
+            if c.is_leaf:
+                self.V[c.id] = tensor_lagrange(self.nodes[c.id], self.points[c.idx])
+            if c.parent is not None:
+                self.E[c.id] = tensor_lagrange(self.nodes[c.parent.id], self.tnodes[c.id])
+        for b in self.adm:
+            b.S = self.g(self.tnodes[b.t.id][:, None, :], self.tnodes[b.s.id][None, :, :])
+        for b in self.near:
+            b.G = self.g(self.points[b.t.idx][:, None, :], self.points[b.s.idx][None, :, :])
+
+    # -- sizes -----------------------------------------------------------
+    def counts(self):
+        leaves = [c for c in self.clusters if c.is_leaf]
+        return dict(
+            n=self.n,
+            n_clusters=len(self.clusters),
+            n_leaves=len(leaves),
+            n_adm=len(self.adm),
+            n_near=len(self.near),
+            nnz_near=int(sum(b.t.size * b.s.size for b in self.near)),
+            depth=max(c.level for c in self.clusters),
+        )
+
+
+# ---------------------------------------------------------------------------
+# H² × dense block (Sec. 3 Alg. "H2_mvm" with the k×m blocks of Sec. 4)
+# ---------------------------------------------------------------------------
+def _forward(H: H2Matrix, s: Cluster, X: np.ndarray, xhat: dict):
+    """Forward transformation: x̂_s = V_sᵀ x|_ŝ at leaves, x̂_s = Σ E_{s'}ᵀ x̂_{s'} above."""
+    if s.is_leaf:
+        xhat[s.id] = H.V[s.id].T @ X[s.idx]
+    else:
+        acc = np.zeros((H.k, X.shape[1]))
+        for s2 in s.sons:
+            _forward(H, s2, X, xhat)
+            acc = acc + H.E[s2.id].T @ xhat[s2.id]
+        xhat[s.id] = acc
+
+
+def _fast_addeval(H, alpha, b: Block, xhat, yhat, X, Y, transposed):
+    """Multiplication phase: ŷ_t += α S_b x̂_s on L+, y|_t̂ += α G_b x|_ŝ on L-."""
+    if b.kind == "adm":
+        if transposed:  # block (s, t) of Aᵀ is V_s S_bᵀ V_tᵀ
+            yhat[b.s.id] += alpha * (b.S.T @ xhat[b.t.id])
+        else:
+            yhat[b.t.id] += alpha * (b.S @ xhat[b.s.id])
+    elif b.kind == "near":
+        if transposed:
+            Y[b.s.idx] += alpha * (b.G.T @ X[b.t.idx])
+        else:
+            Y[b.t.idx] += alpha * (b.G @ X[b.s.idx])
+    else:
+        for b2 in b.sons:
+            _fast_addeval(H, alpha, b2, xhat, yhat, X, Y, transposed)
+
+
+def _backward(H: H2Matrix, t: Cluster, Y: np.ndarray, yhat: dict):
+    """Backward transformation: ŷ_{t'} += E_{t'} ŷ_t downwards, y|_t̂ += V_t ŷ_t at leaves."""
+    if t.is_leaf:
+        Y[t.idx] += H.V[t.id] @ yhat[t.id]
+    else:
+        for t2 in t.sons:
+            yhat[t2.id] = yhat[t2.id] + H.E[t2.id] @ yhat[t.id]
+            _backward(H, t2, Y, yhat)
+
+
+def h2mm(H: H2Matrix, alpha: float, X: np.ndarray, Y: np.ndarray | None = None,
+         transposed: bool = False) -> np.ndarray:
+    """Return Y + α·A·X (or Y + α·Aᵀ·X) for A = Â + σI; X, Y are n×m in the
+    caller's point order.  Follows Alg. "H2_mvm": forward, fast_addeval,
+    backward, then the diagonal shift."""
+    X = np.asarray(X, dtype=np.float64)
+    squeeze = X.ndim == 1
+    if squeeze:
+        X = X[:, None]
+    m = X.shape[1]
+    Yo = np.zeros((H.n, m)) if Y is None else np.array(Y, dtype=np.float64).reshape(H.n, m)
+    xhat = {}
+    yhat = {c.id: np.zeros((H.k, m)) for c in H.clusters}
+    _forward(H, H.root, X, xhat)
+    _fast_addeval(H, alpha, H.btree, xhat, yhat, X, Yo, transposed)
+    _backward(H, H.root, Yo, yhat)
+    Yo += (alpha * H.sigma) * X
+    return Yo[:, 0] if squeeze else Yo
+
+
+def _expanded_basis(H: H2Matrix, c: Cluster) -> np.ndarray:
+    """V_t for any cluster via the nesting V_t|_{t̂'} = V_{t'} E_{t'} (Def. "Cluster basis")."""
+    if c.is_leaf:
+        return H.V[c.id]
+    return np.vstack([_expanded_basis(H, c2) @ H.E[c2.id] for c2 in c.sons])
+
+
+def dense_expand(H: H2Matrix) -> np.ndarray:
+    """The dense n×n matrix Â + σI represented by H (caller's point order)."""
+    A = np.zeros((H.n, H.n))
+    cache = {}
+
+    def vb(c):
+        if c.id not in cache:
+            cache[c.id] = _expanded_basis(H, c)
+        return cache[c.id]
+
+    for b in H.adm:
+        A[np.ix_(b.t.idx, b.s.idx)] = vb(b.t) @ b.S @ vb(b.s).T
+    for b in H.near:
+        A[np.ix_(b.t.idx, b.s.idx)] = b.G
+    A[np.diag_indices(H.n)] += H.sigma
+    return A
+
+
+def kernel_matrix(points: np.ndarray, g, sigma: float = 0.0) -> np.ndarray:
+    """Brute-force K_ij = g(x_i, x_j) + σ δ_ij (the matrix the H² matrix approximates)."""
+    K = g(points[:, None, :], points[None, :, :])
+    K[np.diag_indices(points.shape[0])] += sigma
+    return K
+
+
+# ---------------------------------------------------------------------------
+# Block CG (Sec. 5.1, Alg. "block CG"; Alg. "CG" for its scalar form)
+# ---------------------------------------------------------------------------
+@dataclass
+class CGResult:
+    X: np.ndarray
+    iterations: int
+    col_iterations: np.ndarray
+    rel_residual: np.ndarray  # recurrence residual ||r_i|| / ||b_i|| at exit
+    status: str  # "converged", "breakdown", "noconverge"
+
+
+def block_cg(apply_A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8,
+             max_iter: int = 10000) -> CGResult:
+    """Alg. "block CG": each column keeps its own Krylov space; one block
+    product a = A p per iteration; per column
+    β_i = <p_i, a_i>, α_i = <p_i, r_i>/β_i, x_i += α_i p_i, r_i -= α_i a_i,
+    γ_i = <a_i, r_i>/β_i, p_i = r_i - γ_i p_i.
+
+    Stopping (readings): column i has converged once ||r_i||/||b_i|| <= tol
+    (||b_i|| = 0 is read as 1); converged columns are frozen; the loop runs
+    until every column has converged.  β_i <= 0 or a non-finite value on an
+    unconverged column is a breakdown.
+    """
+    B = np.asarray(B, dtype=np.float64)
+    n, m = B.shape
+    # columns are stored contiguously so each column's arithmetic is the same
+    # whether it is solved alone or inside a block
+    X = np.zeros((n, m), order="F") if X0 is None else np.array(X0, dtype=np.float64, order="F")
+    R = np.asfortranarray(B - apply_A(X))
+    P = R.copy(order="F")
+    bn = np.linalg.norm(B, axis=0)
+    bn[bn == 0.0] = 1.0
+    done = np.linalg.norm(R, axis=0) / bn <= tol
+    col_it = np.zeros(m, dtype=np.int64)
+    it = 0
+    status = "converged"
+    while not done.all():
+        if it >= max_iter:
+            status = "noconverge"
+            break
+        Aq = np.asfortranarray(apply_A(P))
+        it += 1
+        for i in range(m):
+            if done[i]:
+                continue
+            p, a, r = P[:, i], Aq[:, i], R[:, i]
+            beta = float(p @ a)
+            if not (beta > 0.0) or not math.isfinite(beta):
+                status = "breakdown"
+                break
+            alpha = float(p @ r) / beta
+            X[:, i] += alpha * p
+            r = r - alpha * a
+            R[:, i] = r
+            gamma = float(a @ r) / beta
+            P[:, i] = r - gamma * p
+            col_it[i] = it
+            if not math.isfinite(alpha) or not math.isfinite(gamma):
+                status = "breakdown"
+                break
+            if np.linalg.norm(r) / bn[i] <= tol:
+                done[i] = True
+        if status == "breakdown":
+            break
+    rel = np.linalg.norm(R, axis=0) / bn
+    return CGResult(X=X, iterations=it, col_iterations=col_it, rel_residual=rel, status=status)
