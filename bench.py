@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the H² × dense-block product (H2MM) and the block-CG solve.
+
+Workload: n = 65536 points uniform on the unit sphere (seed 0), kernel
+exp(-|x-y|/0.5) + 1e-2·I, leaf size 64, eta = 2, tensor Chebyshev order q = 4
+(k = 64), m = 32 N(0,1) right-hand sides per GPU.
+
+A timed step is one product Y += A·X (all phases: forward transformation,
+transfer passes, coupling, nearfield, backward transformation) through the C
+ABI on device-resident blocks, in the compute precision of the mixed solve
+(FP32).  value = algorithmic H2MM GFLOP/s summed over ranks (weak scaling: each
+rank owns its own 32 columns; columns never communicate).  The line also
+carries the FP64 product rate, the block-CG time to a 1e-8 relative residual
+for the mixed-precision and the FP64 solve, the roofline of the dominant
+kernel (coupling), the end-to-end rate through the C ABI on pinned host
+buffers, and the FP64 CPU oracle timed on this host as a baseline.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from workloads import CONFIGS, gaussian_rhs, sphere_points  # noqa: E402
+
+WORKLOAD = "precision_n65536"
+METRIC = "H2MM GFLOP/s (n=65536, q=4, m=32 per GPU; block-CG time to 1e-8 mixed vs FP64 reported alongside)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+SM_COUNT = 152
+FP32_FMA_PER_CLK_SM = 128
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_products(cfg, steps: int, warmup: int):
+    """Time the FP64 CPU oracle's product on the workload (build untimed)."""
+    from oracle import h2_oracle as O
+
+    pts = sphere_points(cfg["n"], cfg["point_seed"])
+    t0 = time.perf_counter()
+    H = O.H2Matrix(pts, q=cfg["q"], leaf_size=cfg["leaf"], eta=cfg["eta"], sigma=cfg["sigma"],
+                   length=cfg["length"])
+    build_s = time.perf_counter() - t0
+    X = gaussian_rhs(cfg["n"], cfg["m"], cfg["rhs_seed"])
+    for _ in range(warmup):
+        O.h2mm(H, 1.0, X)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        O.h2mm(H, 1.0, X)
+        times.append(time.perf_counter() - t0)
+    c = H.counts()
+    k = cfg["q"] ** 3
+    flops = cfg["m"] * (4.0 * c["n"] * k + 4.0 * (c["n_clusters"] - 1) * k * k + 2.0 * c["n_adm"] * k * k
+                        + 2.0 * c["nnz_near"] + 2.0 * c["n"])
+    return flops, times, build_s
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    cfg = CONFIGS[WORKLOAD]
+    flops, times, build_s = oracle_products(cfg, args.steps, args.warmup)
+    t = sum(times) / len(times)
+    v = flops / t / 1e9
+    cores = _cpu_cores()
+    sample = (f"{args.steps} FP64 oracle products at n={cfg['n']}, q={cfg['q']}, m={cfg['m']} after "
+              f"{args.warmup} warm-up; oracle build {build_s:.1f} s untimed")
+    line = {
+        "metric": METRIC, "value": round(v, 3), "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "n": cfg["n"], "q": cfg["q"], "m": cfg["m"], "leaf": cfg["leaf"],
+                   "eta": cfg["eta"], "kernel": "exp(-r/0.5)+1e-2*I", "parallelism": "cpu"},
+        "cpu_baseline": {"value": round(v, 3), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(v, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2509_17257_gb300 as P
+
+    ws, rank, local = _dist()
+    if ws != args.gpus:
+        args.gpus = ws
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = CONFIGS[WORKLOAD]
+    n, m = cfg["n"], cfg["m"]
+    peaks, peak_kind = _peaks()
+
+    pts = sphere_points(n, cfg["point_seed"])
+    t0 = time.perf_counter()
+    G = P.H2Matrix(pts, q=cfg["q"], leaf_size=cfg["leaf"], eta=cfg["eta"], length=cfg["length"],
+                   sigma=cfg["sigma"], precisions=("f32",))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    info = G.info
+    k = info["k"]
+    X = torch.from_numpy(gaussian_rhs(n, m, cfg["rhs_seed"] + 1000 * rank)).to(dev)
+    Y = torch.zeros_like(X)
+    flops_step = G.flops(m)
+    stream = torch.cuda.current_stream()
+
+    def timed(dtype, steps, warmup, timing=False):
+        for _ in range(warmup):
+            G.matmul(X, Y, dtype=dtype)
+        if timing:
+            P.h2_timing_query(G.handle, reset=True)
+            P.h2_timing_enable(G.handle, True)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            G.matmul(X, Y, dtype=dtype)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ms = e0.elapsed_time(e1) / steps
+        phases = None
+        if timing:
+            P.h2_timing_enable(G.handle, False)
+            phases, calls = P.h2_timing_query(G.handle, reset=True)
+            phases = {kk: v / max(calls, 1) for kk, v in phases.items()}
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, phases
+
+    dtype = args.dtype
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, phases = timed(dtype, args.steps, args.warmup, timing=True)
+    clk = clocks.stop()
+    value = flops_step * ws / (ms * 1e-3) / 1e9
+
+    # FP64 product rate (fewer steps: it is ~50x slower)
+    k64 = max(3, min(args.steps, 10))
+    ms64, phases64 = timed("f64", k64, 3, timing=True)
+    value64 = flops_step * ws / (ms64 * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: the coupling phase (one launch per product)
+    elt = 8 if dtype == "f64" else 4
+    n_adm, nc = info["n_adm"], info["n_clusters"]
+    coup_bytes = elt * (n_adm * k * k + 2 * nc * k * m)
+    coup_flops = 2.0 * n_adm * k * k * m
+    coup_ms = phases["coupling"]
+    clock_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    hbm_peak = peaks["hbm_gbs"]
+    if dtype == "f64":
+        alu_peak_tf = FP64_NOMINAL_TFLOPS
+        alu_note = "FP64 nominal 1.25 TFLOP/s (recipe table)"
+    else:
+        alu_peak_tf = SM_COUNT * FP32_FMA_PER_CLK_SM * 2 * clock_mhz * 1e6 / 1e12
+        alu_note = f"FP32 FFMA: 152 SM x 128 FMA/clk x 2 x {clock_mhz:.0f} MHz (median SM clock under load)"
+    t_hbm = coup_bytes / (hbm_peak * 1e9)
+    t_alu = coup_flops / (alu_peak_tf * 1e12)
+    if t_alu >= t_hbm:
+        achieved = coup_flops / (coup_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak_tf, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / alu_peak_tf, 4), "traffic": None,
+                "kernel": "k_coupling", "peak_source": alu_note}
+    else:
+        achieved = coup_bytes / (coup_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": None, "kernel": "k_coupling",
+                "peak_source": f"{peak_kind} hbm_gbs"}
+    roof["algorithmic_bytes_per_launch"] = int(coup_bytes)
+    roof["algorithmic_flops_per_launch"] = coup_flops
+    roof["ms_per_launch"] = round(coup_ms, 4)
+
+    # end to end through the C ABI on pinned host buffers
+    Xh = X.cpu().pin_memory()
+    Yh = torch.zeros(n, m, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        G.matmul(Xh, Yh, dtype=dtype)
+    ke = max(3, min(args.steps, 10))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        G.matmul(Xh, Yh, dtype=dtype)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ke
+    e2e = {"value": round(flops_step * ws / e2e_s / 1e9, 3), "unit": "GFLOP/s",
+           "h2d_bytes_per_step": 2 * n * m * 8, "d2h_bytes_per_step": n * m * 8,
+           "ms_per_step": round(e2e_s * 1e3, 3)}
+
+    # block CG to a 1e-8 relative residual: mixed (FP32 inner, FP64 refinement) vs FP64
+    solve = None
+    if not args.no_solve:
+        solve = {}
+        B = torch.from_numpy(gaussian_rhs(n, m, cfg["rhs_seed"] + 1000 * rank + 7)).to(dev)
+        for name, inner in (("mixed_f32", "f32"), ("fp64", "f64")):
+            Xs = torch.zeros_like(B)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = G.block_cg(B, Xs, tol=1e-8, max_iter=args.solve_max_iter, inner_dtype=inner, inner_tol=1e-4,
+                           check_every=4)
+            torch.cuda.synchronize()
+            solve[name] = {"seconds": round(time.perf_counter() - t0, 3), "status": r.status_name,
+                           "iterations": int(r.iterations), "outer_steps": int(r.outer_steps),
+                           "h2mm_calls": int(r.h2mm_calls),
+                           "max_true_rel_residual": float(np.max(r.rel_residual))}
+        if solve["fp64"]["seconds"] > 0:
+            solve["speedup_mixed_vs_fp64"] = round(solve["fp64"]["seconds"] / solve["mixed_f32"]["seconds"], 3)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        c_flops, c_times, c_build = oracle_products(CONFIGS[WORKLOAD], steps=3, warmup=0)
+        ct = sum(c_times) / len(c_times)
+        cpu = {"value": round(c_flops / ct / 1e9, 3), "unit": "GFLOP/s", "cores": _cpu_cores(), "kind": "oracle",
+               "sample": f"3 FP64 oracle products at n={n}, q={cfg['q']}, m={m}; oracle build {c_build:.1f} s "
+                         f"untimed"}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "q": cfg["q"], "k": k, "m_per_gpu": m, "leaf": cfg["leaf"],
+                   "eta": cfg["eta"], "kernel": "exp(-r/0.5)+1e-2*I", "parallelism": f"column shards x{ws}",
+                   "l2": f"inputs larger than L2 (matrix data {info['bytes_f32'] / 1e9:.2f} GB FP32, "
+                         f"{info['bytes_f64'] / 1e9:.2f} GB FP64)",
+                   "n_clusters": nc, "n_adm": n_adm, "n_near": info["n_near"], "nnz_near": info["nnz_near"],
+                   "depth": info["depth"], "build_s": round(build_s, 2)},
+        "gflop_per_step": round(flops_step / 1e9, 4),
+        "h2mm_f64": {"value": round(value64, 3), "unit": "GFLOP/s", "ms_per_step": round(ms64, 4)},
+        "phases_ms": {kk: round(v, 4) for kk, v in phases.items()},
+        "phases_ms_f64": {kk: round(v, 4) for kk, v in phases64.items()},
+        "roofline": roof,
+        "e2e": e2e,
+        "solve": solve,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "gpu_launches": int(info["launches"]) * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    G.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--dtype", choices=["f32", "f64", "bf16"], default="f32")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve-max-iter", type=int, default=8000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

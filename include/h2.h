@@ -1,0 +1,210 @@
+/*
+ * h2.h — C ABI of the GB300 H²-matrix block-Krylov library (libh2.so).
+ *
+ * The library computes, for an H² matrix A built from a point cloud, the
+ * product of A with a dense block of m columns and solves A X = B for m
+ * right-hand sides by block CG (arXiv 2509.17257: the problem statement
+ * A x^(i) = b^(i), i = 1..m, of Sec. 1, Eq. (matrix_system); the product
+ * y <- y + alpha G x of Sec. 3 Alg. "H2_mvm" and its block form of Sec. 4;
+ * the block CG of Sec. 5.1 Alg. "block CG").
+ *
+ * Conventions for every entry point:
+ *  - Return 0 (H2_OK) on success, a negative H2_E_* code otherwise.  No call
+ *    aborts or traps; h2_last_error_string() describes the last failure of
+ *    the calling thread.
+ *  - Dense blocks are row-major n×m arrays of double with a leading
+ *    dimension (ld >= m, in elements); row i belongs to point i in the
+ *    caller's original order.  A pointer may be device memory or host
+ *    memory (pageable or pinned); host blocks are staged through device
+ *    memory on the call's stream and the call returns after the result is
+ *    back on the host.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls on
+ *    device pointers are asynchronous with respect to the host unless stated.
+ *  - The library owns every h2_matrix / h2_tree it returns; free them with
+ *    h2_free / h2_tree_free.  The caller owns X, Y, B and the result arrays.
+ *  - A matrix handle may be used by one thread/stream at a time (its
+ *    internal workspace is shared by the calls on it).
+ */
+#ifndef H2_H_
+#define H2_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define H2_OK 0
+#define H2_E_BADARG (-1)      /* invalid argument (null pointer, bad size, NaN point, ...) */
+#define H2_E_CUDA (-2)        /* a CUDA runtime call failed */
+#define H2_E_NOCONVERGE (-3)  /* block CG hit max_iter / max_outer before every column converged */
+#define H2_E_BREAKDOWN (-4)   /* block CG breakdown: <p, A p> <= 0 or a non-finite scalar */
+#define H2_E_TIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define H2_E_OOM (-6)         /* device or host allocation failed */
+#define H2_E_UNSUPPORTED (-7) /* precision copy not built, or parameter outside the supported range */
+
+/* ---- compute precision of the H² product ------------------------------- */
+typedef enum h2_dtype {
+    H2_F64 = 0,  /* all arithmetic in FP64 */
+    H2_F32 = 1,  /* FP32 matrices and coefficients, FP32 accumulation */
+    H2_BF16 = 2  /* BF16 matrices on the tensor cores, FP32 accumulation */
+} h2_dtype;
+
+/* ---- construction ------------------------------------------------------ */
+/* Parameters of the interpolation-based H² matrix
+ *   A = Â + sigma·I,  Â ≈ [g(x_i, x_j)],  g(x, y) = exp(-|x - y|_2 / length).
+ * Cluster tree: bisection of the tight bounding box at the midpoint of its
+ * longest side while a cluster has more than leaf_size points (Sec. 2, Def.
+ * "Cluster tree").  Block tree: sons rule of Sec. 2 Def. "Block tree", a
+ * block is a leaf iff admissible (Eq. (admiss): max diam <= eta·dist, dist >
+ * 0) or leaf × leaf.  Cluster bases: tensor Chebyshev interpolation of order
+ * q per axis, rank k = q³, nested through transfer matrices (Def. "Cluster
+ * basis"); coupling matrices S_b = [g(ξ_t,ν, ξ_s,μ)] (Eq. (h2_admissible));
+ * inadmissible leaves stored densely. */
+typedef struct h2_build_params {
+    int32_t q;           /* interpolation order per axis, 1 <= q <= 5 (k = q³)   */
+    int32_t leaf_size;   /* maximum points per leaf cluster, 1 <= leaf_size <= 64 */
+    double eta;          /* admissibility parameter, > 0                          */
+    double length;       /* kernel length scale, > 0                              */
+    double sigma;        /* diagonal shift                                        */
+    uint32_t precisions; /* bit mask of extra copies to build: (1u<<H2_F32) | (1u<<H2_BF16);
+                            the FP64 copy is always built                         */
+    void* stream;        /* cudaStream_t used for the device part of the build    */
+} h2_build_params;
+
+typedef struct h2_matrix h2_matrix;
+
+/* Sizes of a built matrix. */
+typedef struct h2_info_t {
+    int64_t n;            /* points                                   */
+    int64_t k;            /* rank q³                                   */
+    int64_t n_clusters;   /* |T_I|                                     */
+    int64_t n_leaves;     /* |L_I|                                     */
+    int64_t n_adm;        /* |L+|  (admissible leaf blocks)            */
+    int64_t n_near;       /* |L-|  (inadmissible leaf blocks)          */
+    int64_t nnz_near;     /* sum over L- of |t̂|·|ŝ|                    */
+    int32_t depth;        /* deepest cluster level (root = 0)          */
+    int32_t q;
+    int64_t bytes_f64;    /* device bytes of the FP64 matrix data      */
+    int64_t bytes_f32;    /* device bytes of the FP32 copy (0 if none) */
+    int64_t bytes_bf16;   /* device bytes of the BF16 copy (0 if none) */
+    double flops_per_col; /* algorithmic flops of one product per column of X */
+    int32_t launches;     /* kernel launches of one product                      */
+} h2_info_t;
+
+/* Build A from n points (pts: n×3 row-major doubles, host or device).  On
+ * success *out owns all device memory of the matrix.  The call synchronises
+ * params->stream before returning.  Errors: H2_E_BADARG (n < 1, bad params,
+ * non-finite coordinate), H2_E_OOM, H2_E_CUDA. */
+int h2_build(const h2_build_params* params, const double* pts, int64_t n, h2_matrix** out);
+
+/* Release a matrix (NULL is allowed). */
+int h2_free(h2_matrix* A);
+
+/* Report sizes. */
+int h2_info(const h2_matrix* A, h2_info_t* info);
+
+/* Y <- Y + alpha·A·X  (Sec. 3 Alg. "H2_mvm": forward transformation, the
+ * multiplication phase over the row-cluster lists of Alg. "prepare_addeval"
+ * / "list_addeval", backward transformation; Sec. 4 for m columns).
+ * X: n×m (ldx >= m), Y: n×m (ldy >= m), doubles, host or device; X and Y must
+ * not overlap.  dtype selects the compute precision; H2_F32 / H2_BF16 need
+ * that copy in params->precisions at build time (else H2_E_UNSUPPORTED).
+ * m = 0 is a no-op.  Not re-entrant on the same A. */
+int h2_matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
+              int64_t m, int32_t dtype, void* stream);
+
+/* Y <- Y + alpha·Aᵀ·X: the same traversal with the roles of row and column
+ * clusters swapped (S_bᵀ on admissible blocks, G_bᵀ on inadmissible ones). */
+int h2_matmul_transposed(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y,
+                         int64_t ldy, int64_t m, int32_t dtype, void* stream);
+
+/* ---- per-phase device timing ---------------------------------------------
+ * Phases of one product: 0 gather of X into cluster order, 1 leaf forward
+ * transformation, 2 upward transfer pass, 3 coupling (admissible part of the
+ * multiplication phase), 4 downward transfer pass, 5 leaf backward
+ * transformation + nearfield + shift (scatter into Y).  When enabled, every
+ * product records CUDA events on its stream between the phases; the times are
+ * resolved when queried.  Slots 6..7 are reserved (0). */
+#define H2_NPHASE 8
+/* enable != 0 turns recording on, 0 turns it off; pending records are kept. */
+int h2_timing_enable(h2_matrix* A, int32_t enable);
+/* ms[H2_NPHASE] receives the accumulated milliseconds per phase and *calls the
+ * number of recorded products since the last reset; reset != 0 clears them.
+ * Synchronises with the recorded events. */
+int h2_timing_query(h2_matrix* A, double* ms, int64_t* calls, int32_t reset);
+
+/* ---- block CG (Sec. 5.1, Alg. "block CG") ------------------------------- */
+typedef enum h2_cg_variant {
+    H2_CG_COLUMNWISE = 0 /* the paper's block CG: per-column α_i, β_i, γ_i */
+} h2_cg_variant;
+
+typedef struct h2_cg_params {
+    double tol;          /* per-column relative residual target |r_i|/|b_i| (|b_i| = 0 read as 1) */
+    int32_t max_iter;    /* cap on CG iterations (inner iterations summed for refinement)        */
+    int32_t variant;     /* h2_cg_variant                                                          */
+    int32_t inner_dtype; /* H2_F64: plain FP64 solve.  H2_F32 / H2_BF16: iterative refinement,
+                            FP64 residual B - A X outside, block CG with the low-precision product
+                            and FP64 vector arithmetic inside                                      */
+    double inner_tol;    /* relative reduction asked of each inner solve (refinement only)          */
+    int32_t max_outer;   /* cap on refinement steps                                                  */
+    int32_t check_every; /* convergence test every this many iterations (>= 1)                      */
+    void* stream;        /* cudaStream_t                                                            */
+} h2_cg_params;
+
+typedef struct h2_cg_result {
+    int32_t status;         /* H2_OK, H2_E_NOCONVERGE or H2_E_BREAKDOWN (also the return value)    */
+    int32_t iterations;     /* CG iterations performed (max over columns; summed over refinement)   */
+    int32_t outer_steps;    /* refinement steps (0 for a plain FP64 solve)                          */
+    int32_t h2mm_calls;     /* H² products performed                                                */
+    int32_t* col_iterations;/* optional, caller-owned [m]: iteration at which column i converged    */
+    double* rel_residual;   /* optional, caller-owned [m]: |b_i - A x_i|/|b_i| recomputed in FP64     */
+    double seconds;         /* wall time of the solve                                                */
+} h2_cg_result;
+
+/* Solve A X = B for m columns.  B: n×m (ldb >= m), X: n×m (ldx >= m), host
+ * or device doubles; X holds the initial guess on entry and the solution on
+ * exit.  Blocks until the solve ends.  Returns H2_OK when every column
+ * reached tol, H2_E_NOCONVERGE / H2_E_BREAKDOWN otherwise (X then holds the
+ * last iterate and `res` is filled). */
+int h2_block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
+                const h2_cg_params* params, h2_cg_result* res);
+
+/* ---- host-only topology (Sec. 2 trees; Alg. "prepare_addeval" lists) ---- */
+typedef struct h2_tree h2_tree;
+
+typedef struct h2_tree_view {
+    int64_t n, n_clusters, n_adm, n_near;
+    int32_t depth;
+    const int64_t* perm;       /* [n]   point index at each position of the cluster order       */
+    const int64_t* cl_offset;  /* [n_clusters] first position of t̂ (clusters in pre-order)       */
+    const int64_t* cl_size;    /* [n_clusters]                                                   */
+    const int32_t* cl_level;   /* [n_clusters] root = 0                                          */
+    const int32_t* cl_parent;  /* [n_clusters] -1 for the root                                   */
+    const int32_t* cl_son0;    /* [n_clusters] -1 for a leaf                                     */
+    const int32_t* cl_son1;    /* [n_clusters] -1 for a leaf                                     */
+    const double* cl_box;      /* [n_clusters×6] lo x,y,z then hi x,y,z                          */
+    const int64_t* adm_rowptr; /* [n_clusters+1] admissible blocks of row cluster t: [rowptr[t], rowptr[t+1]) */
+    const int32_t* adm_col;    /* [n_adm] column cluster s of each admissible block              */
+    const int64_t* near_rowptr;/* [n_clusters+1] inadmissible blocks of row cluster t            */
+    const int32_t* near_col;   /* [n_near] column cluster of each inadmissible block             */
+} h2_tree_view;
+
+/* Build only the host topology (no GPU needed).  pts: host n×3 doubles.
+ * Only q, leaf_size and eta of params are read. */
+int h2_tree_build(const h2_build_params* params, const double* pts, int64_t n, h2_tree** out);
+/* Pointers stay valid until h2_tree_free. */
+int h2_tree_view_get(const h2_tree* T, h2_tree_view* view);
+int h2_tree_free(h2_tree* T);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char* h2_last_error_string(void);
+
+/* Library version string. */
+const char* h2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* H2_H_ */

@@ -1,0 +1,241 @@
+// The extern "C" entry points declared in include/h2.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "h2_internal.cuh"
+
+namespace h2 {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int device_alloc(h2_matrix* A, void** ptr, size_t bytes) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? H2_E_OOM : H2_E_CUDA;
+    }
+    A->allocations.push_back(p);
+    *ptr = p;
+    return 0;
+}
+
+}  // namespace h2
+
+struct h2_tree {
+    h2::Tree T;
+};
+
+namespace {
+
+int check_params(const h2_build_params* p) {
+    if (!p) { h2::set_error("null params"); return H2_E_BADARG; }
+    if (p->q < 1 || p->q > 5) { h2::set_error("q must be in [1, 5]"); return H2_E_UNSUPPORTED; }
+    if (p->leaf_size < 1 || p->leaf_size > 64) { h2::set_error("leaf_size must be in [1, 64]"); return H2_E_UNSUPPORTED; }
+    if (!(p->eta > 0.0) || !std::isfinite(p->eta)) { h2::set_error("eta must be finite and > 0"); return H2_E_BADARG; }
+    if (!(p->length > 0.0) || !std::isfinite(p->length)) { h2::set_error("length must be finite and > 0"); return H2_E_BADARG; }
+    if (!std::isfinite(p->sigma)) { h2::set_error("sigma must be finite"); return H2_E_BADARG; }
+    return 0;
+}
+
+void free_matrix(h2_matrix* A) {
+    if (!A) return;
+    for (auto& ev : A->timing.pending)
+        for (auto e : ev) cudaEventDestroy(e);
+    for (auto e : A->timing.free_events) cudaEventDestroy(e);
+    for (void* p : A->allocations) cudaFree(p);
+    if (A->ws.base) cudaFree(A->ws.base);
+    if (A->ws.stage_x) cudaFree(A->ws.stage_x);
+    if (A->ws.stage_y) cudaFree(A->ws.stage_y);
+    delete A;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* h2_last_error_string(void) { return h2::g_last_error.c_str(); }
+
+const char* h2_version(void) { return "h2bcg 0.1 (sm_103a)"; }
+
+int h2_tree_build(const h2_build_params* params, const double* pts, int64_t n, h2_tree** out) {
+    if (!out) { h2::set_error("null out"); return H2_E_BADARG; }
+    *out = nullptr;
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (!pts || n < 1) { h2::set_error("need n >= 1 host points"); return H2_E_BADARG; }
+    h2_tree* T = new (std::nothrow) h2_tree();
+    if (!T) { h2::set_error("host allocation failed"); return H2_E_OOM; }
+    std::string err = h2::build_tree(pts, n, params->leaf_size, params->eta, T->T);
+    if (!err.empty()) {
+        delete T;
+        h2::set_error(err);
+        return H2_E_BADARG;
+    }
+    *out = T;
+    return 0;
+}
+
+int h2_tree_view_get(const h2_tree* T, h2_tree_view* v) {
+    if (!T || !v) { h2::set_error("null argument"); return H2_E_BADARG; }
+    v->n = T->T.n;
+    v->n_clusters = T->T.n_clusters();
+    v->n_adm = T->T.n_adm();
+    v->n_near = T->T.n_near();
+    v->depth = T->T.depth;
+    v->perm = T->T.perm.data();
+    v->cl_offset = T->T.off.data();
+    v->cl_size = T->T.size.data();
+    v->cl_level = T->T.level.data();
+    v->cl_parent = T->T.parent.data();
+    v->cl_son0 = T->T.son0.data();
+    v->cl_son1 = T->T.son1.data();
+    v->cl_box = T->T.box.data();
+    v->adm_rowptr = T->T.adm_rowptr.data();
+    v->adm_col = T->T.adm_col.data();
+    v->near_rowptr = T->T.near_rowptr.data();
+    v->near_col = T->T.near_col.data();
+    return 0;
+}
+
+int h2_tree_free(h2_tree* T) {
+    delete T;
+    return 0;
+}
+
+int h2_build(const h2_build_params* params, const double* pts, int64_t n, h2_matrix** out) {
+    if (!out) { h2::set_error("null out"); return H2_E_BADARG; }
+    *out = nullptr;
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (!pts || n < 1) { h2::set_error("need n >= 1 points"); return H2_E_BADARG; }
+    cudaStream_t st = (cudaStream_t)params->stream;
+    std::vector<double> host;
+    const double* hp = pts;
+    if (h2::is_device_pointer(pts)) {
+        host.resize((size_t)n * 3);
+        cudaError_t e = cudaMemcpy(host.data(), pts, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { h2::set_error(cudaGetErrorString(e)); return H2_E_CUDA; }
+        hp = host.data();
+    }
+    h2_matrix* A = new (std::nothrow) h2_matrix();
+    if (!A) { h2::set_error("host allocation failed"); return H2_E_OOM; }
+    std::string err = h2::build_tree(hp, n, params->leaf_size, params->eta, A->T);
+    if (!err.empty()) {
+        delete A;
+        h2::set_error(err);
+        return H2_E_BADARG;
+    }
+    A->q = params->q;
+    A->k = params->q * params->q * params->q;
+    A->length = params->length;
+    A->sigma = params->sigma;
+    A->n = n;
+    A->nc = A->T.n_clusters();
+    A->n_adm = A->T.n_adm();
+    A->n_near = A->T.n_near();
+    A->depth = A->T.depth;
+    int64_t nl = 0;
+    for (int64_t c = 0; c < A->nc; ++c) nl += A->T.is_leaf((int32_t)c);
+    A->n_leaves = nl;
+    rc = h2::build_device(A, hp, params->precisions, st);
+    if (rc) {
+        free_matrix(A);
+        return rc;
+    }
+    *out = A;
+    return 0;
+}
+
+int h2_free(h2_matrix* A) {
+    free_matrix(A);
+    return 0;
+}
+
+int h2_info(const h2_matrix* A, h2_info_t* info) {
+    if (!A || !info) { h2::set_error("null argument"); return H2_E_BADARG; }
+    info->n = A->n;
+    info->k = A->k;
+    info->n_clusters = A->nc;
+    info->n_leaves = A->n_leaves;
+    info->n_adm = A->n_adm;
+    info->n_near = A->n_near;
+    info->nnz_near = A->nnz_near;
+    info->depth = A->depth;
+    info->q = A->q;
+    info->bytes_f64 = A->f64.bytes;
+    info->bytes_f32 = A->f32.built ? A->f32.bytes : 0;
+    info->bytes_bf16 = 0;
+    const double k = (double)A->k;
+    // leaf forward + leaf backward, up + down transfers, coupling, nearfield, shift
+    info->flops_per_col = 2.0 * 2.0 * (double)A->n * k + 2.0 * 2.0 * (double)(A->nc - 1) * k * k +
+                          2.0 * (double)A->n_adm * k * k + 2.0 * (double)A->nnz_near + 2.0 * (double)A->n;
+    info->launches = A->launches_per_product;
+    return 0;
+}
+
+int h2_timing_enable(h2_matrix* A, int32_t enable) {
+    if (!A) { h2::set_error("null argument"); return H2_E_BADARG; }
+    A->timing.on = enable != 0;
+    return 0;
+}
+
+int h2_timing_query(h2_matrix* A, double* ms, int64_t* calls, int32_t reset) {
+    if (!A) { h2::set_error("null argument"); return H2_E_BADARG; }
+    auto& Tm = A->timing;
+    for (auto& ev : Tm.pending) {
+        if (!ev.empty()) {
+            cudaError_t e = cudaEventSynchronize(ev.back());
+            if (e != cudaSuccess) { h2::set_error(cudaGetErrorString(e)); return H2_E_CUDA; }
+        }
+        for (size_t i = 0; i + 1 < ev.size() && i < H2_NPHASE; ++i) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) Tm.ms[i] += t;
+        }
+        for (auto e : ev) Tm.free_events.push_back(e);
+        Tm.calls += 1;
+    }
+    Tm.pending.clear();
+    if (ms) for (int i = 0; i < H2_NPHASE; ++i) ms[i] = Tm.ms[i];
+    if (calls) *calls = Tm.calls;
+    if (reset) {
+        for (int i = 0; i < H2_NPHASE; ++i) Tm.ms[i] = 0.0;
+        Tm.calls = 0;
+    }
+    return 0;
+}
+
+int h2_matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
+              int32_t dtype, void* stream) {
+    return h2::matmul(A, alpha, X, ldx, Y, ldy, m, dtype, (cudaStream_t)stream, false);
+}
+
+int h2_matmul_transposed(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                         int64_t m, int32_t dtype, void* stream) {
+    return h2::matmul(A, alpha, X, ldx, Y, ldy, m, dtype, (cudaStream_t)stream, true);
+}
+
+int h2_block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
+                const h2_cg_params* params, h2_cg_result* res) {
+    return h2::block_cg(A, B, ldb, X, ldx, m, params, res);
+}
+
+}  // extern "C"

@@ -1,0 +1,338 @@
+// Device construction of the H² matrix entries (Sec. 2): leaf matrices V_t,
+// transfer matrices E_t', coupling matrices S_b and nearfield blocks G_b from
+// tensor Chebyshev interpolation of g(x, y) = exp(-|x - y| / length), plus the
+// typed low-precision copies.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "h2_internal.cuh"
+
+namespace h2 {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Chebyshev points of the first kind on each side of the cluster box:
+// node_{d,i} = center_d + half_d·cos((2i+1)π/(2q)); a side narrower than
+// 1e-8 × the widest half-width is widened to that floor (1e-8 absolute for a
+// box without extent).
+__global__ void k_nodes(const double* __restrict__ box, int nc, int q, double* __restrict__ nodes) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const double* b = box + 6 * (size_t)c;
+    double half[3], center[3];
+    double hmax = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        center[d] = (b[d] + b[3 + d]) * 0.5;
+        half[d] = (b[3 + d] - b[d]) * 0.5;
+        hmax = fmax(hmax, half[d]);
+    }
+    const double floor_h = hmax > 0.0 ? 1e-8 * hmax : 1e-8;
+    for (int d = 0; d < 3; ++d) {
+        const double h = fmax(half[d], floor_h);
+        for (int i = 0; i < q; ++i)
+            nodes[((size_t)c * 3 + d) * q + i] = center[d] + h * cos((2.0 * i + 1.0) * kPi / (2.0 * q));
+    }
+}
+
+// Lagrange polynomial L_i of the q nodes nd at x.
+__device__ __forceinline__ double lagrange(const double* nd, int q, int i, double x) {
+    double v = 1.0;
+    for (int j = 0; j < q; ++j)
+        if (j != i) v *= (x - nd[j]) / (nd[i] - nd[j]);
+    return v;
+}
+
+// L_ν(x) = L_{ν_x}(x_0) L_{ν_y}(x_1) L_{ν_z}(x_2), ν = ν_x + q ν_y + q² ν_z.
+__device__ __forceinline__ double tensor_lagrange(const double* nodes3, int q, int nu, const double* x) {
+    const int nx = nu % q, ny = (nu / q) % q, nz = nu / (q * q);
+    return lagrange(nodes3, q, nx, x[0]) * lagrange(nodes3 + q, q, ny, x[1]) *
+           lagrange(nodes3 + 2 * q, q, nz, x[2]);
+}
+
+__device__ __forceinline__ void tensor_node(const double* nodes3, int q, int mu, double* out) {
+    out[0] = nodes3[mu % q];
+    out[1] = nodes3[q + (mu / q) % q];
+    out[2] = nodes3[2 * q + mu / (q * q)];
+}
+
+__device__ __forceinline__ double kernel_g(const double* x, const double* y, double inv_len) {
+    const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+    return exp(-sqrt((d0 * d0 + d1 * d1) + d2 * d2) * inv_len);
+}
+
+// V_t[i, ν] = L_{t,ν}(x_i) for the points i of leaf t (one CTA per leaf).
+__global__ void k_leaf_basis(const int32_t* __restrict__ leaves, const int32_t* __restrict__ cl_off,
+                             const int32_t* __restrict__ cl_size, const double* __restrict__ pts,
+                             const double* __restrict__ nodes, int q, double* __restrict__ V) {
+    const int t = leaves[blockIdx.x];
+    const int off = cl_off[t], sz = cl_size[t];
+    const int k = q * q * q;
+    const double* nd = nodes + (size_t)t * 3 * q;
+    for (int e = threadIdx.x; e < sz * k; e += blockDim.x) {
+        const int i = e / k, nu = e % k;
+        V[(size_t)(off + i) * k + nu] = tensor_lagrange(nd, q, nu, pts + 3 * (size_t)(off + i));
+    }
+}
+
+// E_{t'}[μ, ν] = L_{t,ν}(ξ_{t',μ}), t = parent of t' (one CTA per cluster).
+__global__ void k_transfer(const int32_t* __restrict__ parent, const double* __restrict__ nodes, int q,
+                           double* __restrict__ E) {
+    const int c = blockIdx.x;
+    const int p = parent[c];
+    if (p < 0) return;
+    const int k = q * q * q;
+    const double* ndc = nodes + (size_t)c * 3 * q;
+    const double* ndp = nodes + (size_t)p * 3 * q;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        const int mu = e / k, nu = e % k;
+        double xi[3];
+        tensor_node(ndc, q, mu, xi);
+        E[(size_t)c * k * k + e] = tensor_lagrange(ndp, q, nu, xi);
+    }
+}
+
+// S_b[ν, μ] = g(ξ_{t,ν}, ξ_{s,μ}) for admissible blocks in list order.
+__global__ void k_coupling_entries(const int32_t* __restrict__ adm_row, const int32_t* __restrict__ adm_col,
+                                   int64_t n_adm, const double* __restrict__ nodes, int q, double inv_len,
+                                   double* __restrict__ S) {
+    const int k = q * q * q;
+    for (int64_t j = blockIdx.x; j < n_adm; j += gridDim.x) {
+        const double* nt = nodes + (size_t)adm_row[j] * 3 * q;
+        const double* ns = nodes + (size_t)adm_col[j] * 3 * q;
+        for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+            const int nu = e / k, mu = e % k;
+            double a[3], b[3];
+            tensor_node(nt, q, nu, a);
+            tensor_node(ns, q, mu, b);
+            S[(size_t)j * k * k + e] = kernel_g(a, b, inv_len);
+        }
+    }
+}
+
+// G_b[i, j] = g(x_i, x_j) for inadmissible blocks.
+__global__ void k_near_entries(const int32_t* __restrict__ near_row, const int32_t* __restrict__ near_col,
+                               const int64_t* __restrict__ near_off, int64_t n_near,
+                               const int32_t* __restrict__ cl_off, const int32_t* __restrict__ cl_size,
+                               const double* __restrict__ pts, double inv_len, double* __restrict__ G) {
+    for (int64_t j = blockIdx.x; j < n_near; j += gridDim.x) {
+        const int t = near_row[j], s = near_col[j];
+        const int ot = cl_off[t], nt = cl_size[t], os = cl_off[s], ns = cl_size[s];
+        double* g = G + near_off[j];
+        for (int e = threadIdx.x; e < nt * ns; e += blockDim.x) {
+            const int r = e / ns, c = e % ns;
+            g[e] = kernel_g(pts + 3 * (size_t)(ot + r), pts + 3 * (size_t)(os + c), inv_len);
+        }
+    }
+}
+
+__global__ void k_cast_f32(const double* __restrict__ in, float* __restrict__ out, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+template <typename T>
+int upload(h2_matrix* A, T** dst, const std::vector<T>& src, cudaStream_t st) {
+    void* p = nullptr;
+    const size_t bytes = src.size() * sizeof(T);
+    int rc = device_alloc(A, &p, bytes > 0 ? bytes : sizeof(T));
+    if (rc) return rc;
+    if (bytes) H2_CUDA_TRY(cudaMemcpyAsync(p, src.data(), bytes, cudaMemcpyHostToDevice, st));
+    *dst = (T*)p;
+    return 0;
+}
+
+int cast_copy(h2_matrix* A, const double* src, void** dst, int64_t count, cudaStream_t st) {
+    int rc = device_alloc(A, dst, (size_t)(count > 0 ? count : 1) * sizeof(float));
+    if (rc) return rc;
+    if (count > 0) {
+        k_cast_f32<<<1216, 256, 0, st>>>(src, (float*)*dst, count);
+        H2_LAUNCH_CHECK();
+    }
+    return 0;
+}
+
+}  // namespace
+
+int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cudaStream_t st) {
+    const Tree& T = A->T;
+    const int64_t n = A->n, nc = A->nc;
+    const int q = A->q, k = A->k;
+
+    // ---- host-side schedule ----
+    std::vector<int32_t> perm32(n), off32(nc), size32(nc), parent32(nc), son0(nc), son1(nc);
+    for (int64_t i = 0; i < n; ++i) perm32[i] = (int32_t)T.perm[i];
+    for (int64_t c = 0; c < nc; ++c) {
+        off32[c] = (int32_t)T.off[c];
+        size32[c] = (int32_t)T.size[c];
+        parent32[c] = T.parent[c];
+        son0[c] = T.son0[c];
+        son1[c] = T.son1[c];
+    }
+    const int L = A->depth;
+    A->up_ptr.assign(L + 2, 0);
+    A->down_ptr.assign(L + 2, 0);
+    std::vector<int32_t> up_list, down_list;
+    for (int l = 0; l <= L; ++l) {
+        A->up_ptr[l] = (int64_t)up_list.size();
+        A->down_ptr[l] = (int64_t)down_list.size();
+        for (int64_t c = 0; c < nc; ++c) {
+            if (T.level[c] != l) continue;
+            if (!T.is_leaf((int32_t)c)) up_list.push_back((int32_t)c);
+            if (T.parent[c] >= 0) down_list.push_back((int32_t)c);
+        }
+    }
+    A->up_ptr[L + 1] = (int64_t)up_list.size();
+    A->down_ptr[L + 1] = (int64_t)down_list.size();
+    A->launches_per_product = 4;  // gather, leaf forward, coupling, leaf backward
+    for (int l = 0; l <= L; ++l) {
+        A->launches_per_product += A->up_ptr[l + 1] > A->up_ptr[l];
+        A->launches_per_product += A->down_ptr[l + 1] > A->down_ptr[l];
+    }
+    A->leaves.clear();
+    std::vector<int32_t> leaf_pos(nc, -1);
+    for (int64_t c = 0; c < nc; ++c)
+        if (T.is_leaf((int32_t)c)) {
+            leaf_pos[c] = (int32_t)A->leaves.size();
+            A->leaves.push_back((int32_t)c);
+        }
+
+    // admissible lists by row cluster, and the transposed lists by column cluster
+    std::vector<int32_t> adm_rowptr(nc + 1), adm_col(A->n_adm), adm_row(A->n_adm);
+    for (int64_t c = 0; c <= nc; ++c) adm_rowptr[c] = (int32_t)T.adm_rowptr[c];
+    for (int64_t t = 0; t < nc; ++t)
+        for (int64_t j = T.adm_rowptr[t]; j < T.adm_rowptr[t + 1]; ++j) {
+            adm_col[j] = T.adm_col[j];
+            adm_row[j] = (int32_t)t;
+        }
+    std::vector<int32_t> admT_rowptr(nc + 1, 0), admT_row(A->n_adm), admT_blk(A->n_adm);
+    for (int64_t j = 0; j < A->n_adm; ++j) admT_rowptr[adm_col[j] + 1]++;
+    for (int64_t c = 0; c < nc; ++c) admT_rowptr[c + 1] += admT_rowptr[c];
+    {
+        std::vector<int32_t> pos(admT_rowptr.begin(), admT_rowptr.end() - 1);
+        for (int64_t j = 0; j < A->n_adm; ++j) {
+            const int32_t p = pos[adm_col[j]]++;
+            admT_row[p] = adm_row[j];
+            admT_blk[p] = (int32_t)j;
+        }
+    }
+    // nearfield lists by row leaf position, offsets of the dense blocks
+    const int64_t NL = (int64_t)A->leaves.size();
+    std::vector<int32_t> near_ptr(NL + 1, 0), near_col(A->n_near), near_row(A->n_near);
+    std::vector<int64_t> near_off(A->n_near);
+    int64_t acc = 0;
+    {
+        int64_t j = 0;
+        for (int64_t lp = 0; lp < NL; ++lp) {
+            const int32_t t = A->leaves[lp];
+            near_ptr[lp] = (int32_t)j;
+            for (int64_t e = T.near_rowptr[t]; e < T.near_rowptr[t + 1]; ++e, ++j) {
+                near_col[j] = T.near_col[e];
+                near_row[j] = t;
+                near_off[j] = acc;
+                acc += T.size[t] * T.size[T.near_col[e]];
+            }
+        }
+        near_ptr[NL] = (int32_t)j;
+    }
+    A->nnz_near = acc;
+    std::vector<int32_t> nearT_ptr(NL + 1, 0), nearT_row(A->n_near), nearT_blk(A->n_near);
+    for (int64_t j = 0; j < A->n_near; ++j) nearT_ptr[leaf_pos[near_col[j]] + 1]++;
+    for (int64_t lp = 0; lp < NL; ++lp) nearT_ptr[lp + 1] += nearT_ptr[lp];
+    {
+        std::vector<int32_t> pos(nearT_ptr.begin(), nearT_ptr.end() - 1);
+        for (int64_t j = 0; j < A->n_near; ++j) {
+            const int32_t p = pos[leaf_pos[near_col[j]]]++;
+            nearT_row[p] = near_row[j];
+            nearT_blk[p] = (int32_t)j;
+        }
+    }
+    std::vector<double> pts_p((size_t)n * 3);
+    for (int64_t i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d) pts_p[3 * i + d] = pts_host[3 * T.perm[i] + d];
+
+    int rc = 0;
+#define UP(dst, src) if ((rc = upload(A, &(dst), (src), st))) return rc
+    UP(A->d_perm, perm32);
+    UP(A->d_cl_off, off32);
+    UP(A->d_cl_size, size32);
+    UP(A->d_parent, parent32);
+    UP(A->d_son0, son0);
+    UP(A->d_son1, son1);
+    UP(A->d_leaves, A->leaves);
+    UP(A->d_up_list, up_list);
+    UP(A->d_down_list, down_list);
+    UP(A->d_adm_rowptr, adm_rowptr);
+    UP(A->d_adm_col, adm_col);
+    UP(A->d_adm_row, adm_row);
+    UP(A->d_admT_rowptr, admT_rowptr);
+    UP(A->d_admT_row, admT_row);
+    UP(A->d_admT_blk, admT_blk);
+    UP(A->d_near_ptr, near_ptr);
+    UP(A->d_near_col, near_col);
+    UP(A->d_near_row, near_row);
+    UP(A->d_near_off, near_off);
+    UP(A->d_nearT_ptr, nearT_ptr);
+    UP(A->d_nearT_row, nearT_row);
+    UP(A->d_nearT_blk, nearT_blk);
+    UP(A->d_pts, pts_p);
+    double* d_box = nullptr;
+    UP(d_box, T.box);
+#undef UP
+
+    // ---- entries in FP64 ----
+    void* p = nullptr;
+    if ((rc = device_alloc(A, &p, (size_t)nc * 3 * q * sizeof(double)))) return rc;
+    A->d_nodes = (double*)p;
+    k_nodes<<<(unsigned)((nc + 127) / 128), 128, 0, st>>>(d_box, (int)nc, q, A->d_nodes);
+    H2_LAUNCH_CHECK();
+
+    const size_t bV = (size_t)n * k * sizeof(double);
+    const size_t bE = (size_t)nc * k * k * sizeof(double);
+    const size_t bS = (size_t)A->n_adm * k * k * sizeof(double);
+    const size_t bN = (size_t)A->nnz_near * sizeof(double);
+    if ((rc = device_alloc(A, &A->f64.V, bV))) return rc;
+    if ((rc = device_alloc(A, &A->f64.E, bE))) return rc;
+    if ((rc = device_alloc(A, &A->f64.S, bS > 0 ? bS : 8))) return rc;
+    if ((rc = device_alloc(A, &A->f64.Near, bN > 0 ? bN : 8))) return rc;
+    A->f64.bytes = (int64_t)(bV + bE + bS + bN);
+    H2_CUDA_TRY(cudaMemsetAsync(A->f64.E, 0, bE, st));
+
+    const double inv_len = 1.0 / A->length;
+    k_leaf_basis<<<(unsigned)NL, 256, 0, st>>>(A->d_leaves, A->d_cl_off, A->d_cl_size, A->d_pts, A->d_nodes,
+                                               q, (double*)A->f64.V);
+    H2_LAUNCH_CHECK();
+    k_transfer<<<(unsigned)nc, 256, 0, st>>>(A->d_parent, A->d_nodes, q, (double*)A->f64.E);
+    H2_LAUNCH_CHECK();
+    if (A->n_adm > 0) {
+        const unsigned g = (unsigned)std::min<int64_t>(A->n_adm, 152 * 64);
+        k_coupling_entries<<<g, 256, 0, st>>>(A->d_adm_row, A->d_adm_col, A->n_adm, A->d_nodes, q, inv_len,
+                                              (double*)A->f64.S);
+        H2_LAUNCH_CHECK();
+    }
+    if (A->n_near > 0) {
+        const unsigned g = (unsigned)std::min<int64_t>(A->n_near, 152 * 64);
+        k_near_entries<<<g, 256, 0, st>>>(A->d_near_row, A->d_near_col, A->d_near_off, A->n_near, A->d_cl_off,
+                                          A->d_cl_size, A->d_pts, inv_len, (double*)A->f64.Near);
+        H2_LAUNCH_CHECK();
+    }
+    A->f64.built = true;
+
+    if (precisions & (1u << H2_F32)) {
+        if ((rc = cast_copy(A, (const double*)A->f64.V, &A->f32.V, (int64_t)n * k, st))) return rc;
+        if ((rc = cast_copy(A, (const double*)A->f64.E, &A->f32.E, nc * k * k, st))) return rc;
+        if ((rc = cast_copy(A, (const double*)A->f64.S, &A->f32.S, A->n_adm * k * k, st))) return rc;
+        if ((rc = cast_copy(A, (const double*)A->f64.Near, &A->f32.Near, A->nnz_near, st))) return rc;
+        A->f32.bytes = A->f64.bytes / 2;
+        A->f32.built = true;
+    }
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
+    return 0;
+}
+
+}  // namespace h2

@@ -1,0 +1,130 @@
+// Internal state of an h2_matrix and helpers shared by the CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/h2.h"
+#include "h2_tree.hpp"
+
+namespace h2 {
+
+void set_error(const std::string& msg);
+
+#define H2_CUDA_TRY(expr)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            ::h2::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));            \
+            return e_ == cudaErrorMemoryAllocation ? H2_E_OOM : H2_E_CUDA;                 \
+        }                                                                                  \
+    } while (0)
+
+#define H2_LAUNCH_CHECK()                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = cudaGetLastError();                                               \
+        if (e_ != cudaSuccess) {                                                           \
+            ::h2::set_error(std::string("kernel launch: ") + cudaGetErrorString(e_));       \
+            return H2_E_CUDA;                                                              \
+        }                                                                                  \
+    } while (0)
+
+// One typed copy of the matrix data (V leaf rows, transfer E, coupling S,
+// nearfield G), row-major:
+//   V    [n][k]         rows in cluster order (position i = point perm[i])
+//   E    [n_c][k][k]    E[c][μ][ν], c != root (root slot unused)
+//   S    [n_adm][k][k]  S[j][ν][μ] in row-cluster list order
+//   Near concatenated  G_j[|t̂|][|ŝ|] blocks at near_off[j]
+struct MatData {
+    void* V = nullptr;
+    void* E = nullptr;
+    void* S = nullptr;
+    void* Near = nullptr;
+    int64_t bytes = 0;
+    bool built = false;
+};
+
+// Per-phase event timing of the product (h2_timing_enable / h2_timing_query).
+struct Timing {
+    bool on = false;
+    std::vector<cudaEvent_t> free_events;
+    std::vector<std::vector<cudaEvent_t>> pending;  // 7 events per recorded product
+    double ms[H2_NPHASE] = {0};
+    int64_t calls = 0;
+};
+
+struct Workspace {
+    void* base = nullptr;
+    size_t bytes = 0;
+    double* stage_x = nullptr;  // host-pointer staging (n×m doubles each)
+    double* stage_y = nullptr;
+    size_t stage_bytes = 0;
+};
+
+}  // namespace h2
+
+struct h2_matrix {
+    h2::Tree T;
+    int q = 0, k = 0;
+    double length = 0, sigma = 0;
+    int64_t n = 0, nc = 0, n_leaves = 0, n_adm = 0, n_near = 0, nnz_near = 0;
+    int32_t depth = 0;
+
+    // host copies of the level schedule
+    std::vector<int64_t> up_ptr;    // [depth+2] inner clusters of level l: up_list[up_ptr[l]..up_ptr[l+1])
+    std::vector<int64_t> down_ptr;  // [depth+2] non-root clusters of level l
+    std::vector<int32_t> leaves;    // leaf cluster ids in pre-order
+
+    // device topology (int32 ids/positions; int64 element offsets)
+    int32_t* d_perm = nullptr;       // [n]
+    int32_t* d_cl_off = nullptr;     // [nc]
+    int32_t* d_cl_size = nullptr;    // [nc]
+    int32_t* d_parent = nullptr;     // [nc]
+    int32_t* d_leaves = nullptr;     // [n_leaves]
+    int32_t* d_up_list = nullptr;    // inner clusters by level
+    int32_t* d_son0 = nullptr;       // [nc]
+    int32_t* d_son1 = nullptr;       // [nc]
+    int32_t* d_down_list = nullptr;  // non-root clusters by level
+    int32_t* d_adm_rowptr = nullptr; // [nc+1] by row cluster
+    int32_t* d_adm_col = nullptr;    // [n_adm]
+    int32_t* d_adm_row = nullptr;    // [n_adm]
+    int32_t* d_admT_rowptr = nullptr;// [nc+1] by column cluster (transposed product)
+    int32_t* d_admT_row = nullptr;   // [n_adm] row cluster t of each entry
+    int32_t* d_admT_blk = nullptr;   // [n_adm] index j of S_j
+    int32_t* d_near_ptr = nullptr;   // [n_leaves+1] by row leaf position
+    int32_t* d_near_col = nullptr;   // [n_near] column cluster id
+    int32_t* d_near_row = nullptr;   // [n_near] row cluster id
+    int64_t* d_near_off = nullptr;   // [n_near] element offset of G_j
+    int32_t* d_nearT_ptr = nullptr;  // [n_leaves+1] by column leaf position
+    int32_t* d_nearT_row = nullptr;  // [n_near] row cluster t
+    int32_t* d_nearT_blk = nullptr;  // [n_near] block index j
+    double* d_pts = nullptr;         // [n][3] points in cluster order
+    double* d_nodes = nullptr;       // [nc][3][q] Chebyshev nodes per cluster
+
+    h2::MatData f64, f32;
+    h2::Workspace ws;
+    h2::Timing timing;
+    int32_t launches_per_product = 0;
+    std::vector<void*> allocations;
+};
+
+namespace h2 {
+
+// Entry points implemented in h2_build.cu / h2_mm.cu / h2_cg.cu.
+int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cudaStream_t st);
+int matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
+           int64_t m, int32_t dtype, cudaStream_t st, bool transposed);
+// Device-pointer product used by the solvers: Y = overwrite ? alpha·A·X : Y + alpha·A·X.
+int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y,
+                  int64_t ldy, int64_t m, int32_t dtype, cudaStream_t st, bool transposed,
+                  bool overwrite);
+int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
+             const h2_cg_params* p, h2_cg_result* res);
+
+bool is_device_pointer(const void* p);
+int device_alloc(h2_matrix* A, void** ptr, size_t bytes);
+
+}  // namespace h2

@@ -1,0 +1,428 @@
+// H² matrix × dense block, SIMT kernels for FP64 and FP32 (Sec. 3 Alg.
+// "H2_mvm" with the k×m coefficient blocks of Sec. 4).
+//
+// The product Y += α·A·X runs as a stream-ordered chain:
+//   gather      Xp = X[perm]                       (cluster order, compute type)
+//   leaf_fwd    x̂_t = V_tᵀ Xp|_t̂                  (forward transformation, leaves)
+//   up(l)       x̂_t = Σ_{t'∈sons(t)} E_{t'}ᵀ x̂_{t'}  levels deepest-1 .. 0
+//   coupling    ŷ_t = Σ_{b=(t,s)∈L+} S_b x̂_s      (multiplication phase, admissible part;
+//                                                  one owner per row cluster, Alg. "list_addeval")
+//   down(l)     ŷ_{t'} += E_{t'} ŷ_t                levels 1 .. deepest
+//   leaf_bwd    Y|_t̂ += α (V_t ŷ_t + Σ_{b=(t,s)∈L-} G_b Xp|_ŝ + σ Xp|_t̂)   scattered through perm
+// Every output tile has exactly one owning CTA, so no atomics are needed: the
+// race the paper resolves by sequential sums (Sec. 3, after Alg.
+// "forward/backward") is resolved here by ownership.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "h2_internal.cuh"
+
+namespace h2 {
+
+namespace {
+
+constexpr int kThreads = 256;  // 16 × 16 thread grid per CTA
+constexpr int kKC = 32;        // K chunk staged in shared memory
+
+// Per-thread register tile: rows ty + 16·r (r < RM), columns tx + 16·c (c < CN).
+template <typename T, int RM, int CN>
+struct Acc {
+    T v[RM][CN];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int r = 0; r < RM; ++r)
+#pragma unroll
+            for (int c = 0; c < CN; ++c) v[r][c] = T(0);
+    }
+};
+
+template <typename T, int RM, int CN>
+struct Smem {
+    T a[kKC][16 * RM + 1];
+    T b[kKC][16 * CN];
+};
+
+// acc += op(A)[row0 : row0+16RM, 0:K] · B[0:K, col0 : col0+16CN]
+// op(A) = A (A is M×K row-major, leading dimension lda) or, with TA, Aᵀ
+// (A stored K×M row-major).  Rows >= M, k >= K and columns >= ncol read as 0.
+template <typename T, int RM, int CN, bool TA>
+__device__ __forceinline__ void mac(Acc<T, RM, CN>& acc, Smem<T, RM, CN>& sm, const T* __restrict__ A,
+                                    int64_t lda, int M, int K, int row0, const T* __restrict__ B,
+                                    int64_t ldb, int ncol, int col0) {
+    constexpr int MT = 16 * RM, NT = 16 * CN;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int k0 = 0; k0 < K; k0 += kKC) {
+        const int kc = min(kKC, K - k0);
+        __syncthreads();
+        if (TA) {
+            for (int e = tid; e < MT * kKC; e += kThreads) {
+                const int r = e % MT, kk = e / MT;
+                const int gr = row0 + r;
+                sm.a[kk][r] = (gr < M && kk < kc) ? A[(int64_t)(k0 + kk) * lda + gr] : T(0);
+            }
+        } else {
+            for (int e = tid; e < MT * kKC; e += kThreads) {
+                const int kk = e % kKC, r = e / kKC;
+                const int gr = row0 + r;
+                sm.a[kk][r] = (gr < M && kk < kc) ? A[(int64_t)gr * lda + k0 + kk] : T(0);
+            }
+        }
+        for (int e = tid; e < NT * kKC; e += kThreads) {
+            const int c = e % NT, kk = e / NT;
+            const int gc = col0 + c;
+            sm.b[kk][c] = (gc < ncol && kk < kc) ? B[(int64_t)(k0 + kk) * ldb + gc] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kc; ++kk) {
+            T a[RM], b[CN];
+#pragma unroll
+            for (int r = 0; r < RM; ++r) a[r] = sm.a[kk][ty + 16 * r];
+#pragma unroll
+            for (int c = 0; c < CN; ++c) b[c] = sm.b[kk][tx + 16 * c];
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int c = 0; c < CN; ++c) acc.v[r][c] = fma(a[r], b[c], acc.v[r][c]);
+        }
+    }
+}
+
+template <typename T, int RM, int CN, bool ACCUM>
+__device__ __forceinline__ void store_tile(const Acc<T, RM, CN>& acc, T* __restrict__ C, int64_t ldc, int M,
+                                           int ncol, int row0, int col0) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+        const int gr = row0 + ty + 16 * r;
+        if (gr >= M) continue;
+#pragma unroll
+        for (int c = 0; c < CN; ++c) {
+            const int gc = col0 + tx + 16 * c;
+            if (gc >= ncol) continue;
+            T* p = C + (int64_t)gr * ldc + gc;
+            if (ACCUM) *p += acc.v[r][c]; else *p = acc.v[r][c];
+        }
+    }
+}
+
+// ---- gather: Xp[i, :] = X[perm[i], :] in the compute type ----
+template <typename T>
+__global__ void k_gather(const double* __restrict__ X, int64_t ldx, const int32_t* __restrict__ perm, int64_t n,
+                         int m, T* __restrict__ Xp) {
+    const int64_t total = n * m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / m;
+        const int c = (int)(e % m);
+        Xp[e] = (T)X[(int64_t)perm[i] * ldx + c];
+    }
+}
+
+// ---- forward transformation at the leaves: x̂_t = V_tᵀ Xp|_t̂ ----
+template <typename T, int RM, int CN>
+__global__ void __launch_bounds__(kThreads) k_leaf_fwd(const int32_t* __restrict__ leaves,
+                                                       const int32_t* __restrict__ cl_off,
+                                                       const int32_t* __restrict__ cl_size,
+                                                       const T* __restrict__ V, const T* __restrict__ Xp,
+                                                       T* __restrict__ xhat, int k, int m) {
+    __shared__ Smem<T, RM, CN> sm;
+    const int t = leaves[blockIdx.x];
+    const int col0 = blockIdx.y * 16 * CN, row0 = blockIdx.z * 16 * RM;
+    Acc<T, RM, CN> acc;
+    acc.zero();
+    const int off = cl_off[t];
+    mac<T, RM, CN, true>(acc, sm, V + (int64_t)off * k, k, k, cl_size[t], row0, Xp + (int64_t)off * m, m, m,
+                         col0);
+    store_tile<T, RM, CN, false>(acc, xhat + (int64_t)t * k * m, m, k, m, row0, col0);
+}
+
+// ---- upward pass on one level: x̂_t = Σ_{t'} E_{t'}ᵀ x̂_{t'} ----
+template <typename T, int RM, int CN>
+__global__ void __launch_bounds__(kThreads) k_up(const int32_t* __restrict__ list, const int32_t* __restrict__ son0,
+                                                 const int32_t* __restrict__ son1, const T* __restrict__ E,
+                                                 T* __restrict__ xhat, int k, int m) {
+    __shared__ Smem<T, RM, CN> sm;
+    const int t = list[blockIdx.x];
+    const int col0 = blockIdx.y * 16 * CN, row0 = blockIdx.z * 16 * RM;
+    Acc<T, RM, CN> acc;
+    acc.zero();
+    const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
+    const int s0 = son0[t], s1 = son1[t];
+    mac<T, RM, CN, true>(acc, sm, E + s0 * kk, k, k, k, row0, xhat + s0 * km, m, m, col0);
+    mac<T, RM, CN, true>(acc, sm, E + s1 * kk, k, k, k, row0, xhat + s1 * km, m, m, col0);
+    store_tile<T, RM, CN, false>(acc, xhat + (int64_t)t * km, m, k, m, row0, col0);
+}
+
+// ---- multiplication phase, admissible part: ŷ_t = Σ_{b∈C_t} S_b x̂_s ----
+// TRANS: the list is by column cluster and S_bᵀ is applied (product with Aᵀ).
+template <typename T, int RM, int CN, bool TRANS>
+__global__ void __launch_bounds__(kThreads) k_coupling(const int32_t* __restrict__ rowptr,
+                                                       const int32_t* __restrict__ other,
+                                                       const int32_t* __restrict__ blk, const T* __restrict__ S,
+                                                       const T* __restrict__ xhat, T* __restrict__ yhat, int k,
+                                                       int m) {
+    __shared__ Smem<T, RM, CN> sm;
+    const int t = blockIdx.x;
+    const int col0 = blockIdx.y * 16 * CN, row0 = blockIdx.z * 16 * RM;
+    Acc<T, RM, CN> acc;
+    acc.zero();
+    const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
+    for (int e = rowptr[t]; e < rowptr[t + 1]; ++e) {
+        const int s = other[e];
+        const int64_t j = TRANS ? blk[e] : e;
+        mac<T, RM, CN, TRANS>(acc, sm, S + j * kk, k, k, k, row0, xhat + s * km, m, m, col0);
+    }
+    store_tile<T, RM, CN, false>(acc, yhat + (int64_t)t * km, m, k, m, row0, col0);
+}
+
+// ---- downward pass on one level: ŷ_{t'} += E_{t'} ŷ_{parent(t')} ----
+template <typename T, int RM, int CN>
+__global__ void __launch_bounds__(kThreads) k_down(const int32_t* __restrict__ list,
+                                                   const int32_t* __restrict__ parent, const T* __restrict__ E,
+                                                   T* __restrict__ yhat, int k, int m) {
+    __shared__ Smem<T, RM, CN> sm;
+    const int c = list[blockIdx.x];
+    const int col0 = blockIdx.y * 16 * CN, row0 = blockIdx.z * 16 * RM;
+    Acc<T, RM, CN> acc;
+    acc.zero();
+    const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
+    mac<T, RM, CN, false>(acc, sm, E + c * kk, k, k, k, row0, yhat + (int64_t)parent[c] * km, m, m, col0);
+    store_tile<T, RM, CN, true>(acc, yhat + (int64_t)c * km, m, k, m, row0, col0);
+}
+
+// ---- backward transformation at the leaves + inadmissible part + shift ----
+// Y[perm[off_t + i], :] += α (V_t ŷ_t + Σ_b G_b Xp|_ŝ + σ Xp|_t̂)[i, :]
+template <typename T, int RM, int CN, bool TRANS>
+__global__ void __launch_bounds__(kThreads) k_leaf_bwd_near(
+    const int32_t* __restrict__ leaves, const int32_t* __restrict__ cl_off, const int32_t* __restrict__ cl_size,
+    const int32_t* __restrict__ perm, const T* __restrict__ V, const T* __restrict__ yhat,
+    const int32_t* __restrict__ nptr, const int32_t* __restrict__ nother, const int32_t* __restrict__ nblk,
+    const int64_t* __restrict__ near_off, const T* __restrict__ G, const T* __restrict__ Xp, double* __restrict__ Y,
+    int64_t ldy, double alpha, double sigma, int k, int m, int overwrite) {
+    __shared__ Smem<T, RM, CN> sm;
+    const int lp = blockIdx.x;
+    const int t = leaves[lp];
+    const int col0 = blockIdx.y * 16 * CN, row0 = blockIdx.z * 16 * RM;
+    const int off = cl_off[t], nt = cl_size[t];
+    Acc<T, RM, CN> acc;
+    acc.zero();
+    mac<T, RM, CN, false>(acc, sm, V + (int64_t)off * k, k, nt, k, row0, yhat + (int64_t)t * k * m, m, m, col0);
+    for (int e = nptr[lp]; e < nptr[lp + 1]; ++e) {
+        const int s = nother[e];
+        const int64_t j = TRANS ? nblk[e] : e;
+        const int os = cl_off[s], ns = cl_size[s];
+        // G_j is |row leaf| × |column leaf| row-major; for Aᵀ the row leaf is s.
+        mac<T, RM, CN, TRANS>(acc, sm, G + near_off[j], TRANS ? nt : ns, nt, ns, row0, Xp + (int64_t)os * m, m, m,
+                              col0);
+    }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+        const int i = row0 + ty + 16 * r;
+        if (i >= nt) continue;
+        double* yrow = Y + (int64_t)perm[off + i] * ldy;
+        const T* xrow = Xp + (int64_t)(off + i) * m;
+#pragma unroll
+        for (int c = 0; c < CN; ++c) {
+            const int gc = col0 + tx + 16 * c;
+            if (gc >= m) continue;
+            const double z = (double)acc.v[r][c] + sigma * (double)xrow[gc];
+            if (overwrite) yrow[gc] = alpha * z; else yrow[gc] += alpha * z;
+        }
+    }
+}
+
+// Records an event between phases when timing is enabled (h2_timing_enable).
+struct PhaseMarks {
+    h2_matrix* A;
+    cudaStream_t st;
+    std::vector<cudaEvent_t> ev;
+    bool failed = false;
+    PhaseMarks(h2_matrix* a, cudaStream_t s) : A(a), st(s) {}
+    void mark() {
+        if (!A->timing.on || failed) return;
+        cudaEvent_t e;
+        if (!A->timing.free_events.empty()) {
+            e = A->timing.free_events.back();
+            A->timing.free_events.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            failed = true;
+            return;
+        }
+        if (cudaEventRecord(e, st) != cudaSuccess) failed = true;
+        ev.push_back(e);
+    }
+    int commit() {
+        if (!A->timing.on) return 0;
+        if (failed) {
+            for (auto e : ev) A->timing.free_events.push_back(e);
+            set_error("timing event record failed");
+            return H2_E_CUDA;
+        }
+        A->timing.pending.push_back(ev);
+        ev.clear();
+        return 0;
+    }
+};
+
+template <typename T, int RM, int CN>
+int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
+              int m, cudaStream_t st, bool transposed, bool overwrite, T* Xp, T* xhat, T* yhat) {
+    constexpr int MT = 16 * RM, NT = 16 * CN;
+    const int k = A->k;
+    const unsigned gy = (unsigned)((m + NT - 1) / NT);
+    const unsigned gzk = (unsigned)((k + MT - 1) / MT);
+    const unsigned gzl = (unsigned)((A->T.leaf_size + MT - 1) / MT);
+    const T* V = (const T*)D.V;
+    const T* E = (const T*)D.E;
+    const T* S = (const T*)D.S;
+    const T* G = (const T*)D.Near;
+    PhaseMarks marks(A, st);
+    marks.mark();
+    {
+        const int64_t total = A->n * m;
+        const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+        k_gather<T><<<g, 256, 0, st>>>(X, ldx, A->d_perm, A->n, m, Xp);
+        H2_LAUNCH_CHECK();
+    }
+    marks.mark();
+    const unsigned NL = (unsigned)A->leaves.size();
+    k_leaf_fwd<T, RM, CN><<<dim3(NL, gy, gzk), kThreads, 0, st>>>(A->d_leaves, A->d_cl_off, A->d_cl_size, V, Xp,
+                                                                  xhat, k, m);
+    H2_LAUNCH_CHECK();
+    marks.mark();
+    for (int l = A->depth - 1; l >= 0; --l) {
+        const int64_t b = A->up_ptr[l], e = A->up_ptr[l + 1];
+        if (e == b) continue;
+        k_up<T, RM, CN><<<dim3((unsigned)(e - b), gy, gzk), kThreads, 0, st>>>(A->d_up_list + b, A->d_son0,
+                                                                              A->d_son1, E, xhat, k, m);
+        H2_LAUNCH_CHECK();
+    }
+    marks.mark();
+    if (transposed)
+        k_coupling<T, RM, CN, true><<<dim3((unsigned)A->nc, gy, gzk), kThreads, 0, st>>>(
+            A->d_admT_rowptr, A->d_admT_row, A->d_admT_blk, S, xhat, yhat, k, m);
+    else
+        k_coupling<T, RM, CN, false><<<dim3((unsigned)A->nc, gy, gzk), kThreads, 0, st>>>(
+            A->d_adm_rowptr, A->d_adm_col, nullptr, S, xhat, yhat, k, m);
+    H2_LAUNCH_CHECK();
+    marks.mark();
+    for (int l = 1; l <= A->depth; ++l) {
+        const int64_t b = A->down_ptr[l], e = A->down_ptr[l + 1];
+        if (e == b) continue;
+        k_down<T, RM, CN><<<dim3((unsigned)(e - b), gy, gzk), kThreads, 0, st>>>(A->d_down_list + b, A->d_parent,
+                                                                                E, yhat, k, m);
+        H2_LAUNCH_CHECK();
+    }
+    marks.mark();
+    if (transposed)
+        k_leaf_bwd_near<T, RM, CN, true><<<dim3(NL, gy, gzl), kThreads, 0, st>>>(
+            A->d_leaves, A->d_cl_off, A->d_cl_size, A->d_perm, V, yhat, A->d_nearT_ptr, A->d_nearT_row,
+            A->d_nearT_blk, A->d_near_off, G, Xp, Y, ldy, alpha, A->sigma, k, m, overwrite ? 1 : 0);
+    else
+        k_leaf_bwd_near<T, RM, CN, false><<<dim3(NL, gy, gzl), kThreads, 0, st>>>(
+            A->d_leaves, A->d_cl_off, A->d_cl_size, A->d_perm, V, yhat, A->d_near_ptr, A->d_near_col, nullptr,
+            A->d_near_off, G, Xp, Y, ldy, alpha, A->sigma, k, m, overwrite ? 1 : 0);
+    H2_LAUNCH_CHECK();
+    marks.mark();
+    return marks.commit();
+}
+
+template <typename T>
+int dispatch_cn(h2_matrix* A, const MatData& D, double alpha, const double* X, int64_t ldx, double* Y,
+                int64_t ldy, int m, cudaStream_t st, bool transposed, bool overwrite, T* Xp, T* xhat, T* yhat) {
+    if (m <= 16) return run_chain<T, 4, 1>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat);
+    if (m <= 32) return run_chain<T, 4, 2>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat);
+    return run_chain<T, 4, 4>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat);
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int ensure_workspace(h2_matrix* A, size_t bytes, cudaStream_t st) {
+    if (A->ws.bytes >= bytes) return 0;
+    if (A->ws.base) {
+        H2_CUDA_TRY(cudaStreamSynchronize(st));
+        H2_CUDA_TRY(cudaFree(A->ws.base));
+        A->ws.base = nullptr;
+        A->ws.bytes = 0;
+    }
+    H2_CUDA_TRY(cudaMalloc(&A->ws.base, bytes));
+    A->ws.bytes = bytes;
+    return 0;
+}
+
+}  // namespace
+
+int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
+                  int32_t dtype, cudaStream_t st, bool transposed, bool overwrite) {
+    if (m == 0) return 0;
+    const size_t elt = dtype == H2_F64 ? sizeof(double) : sizeof(float);
+    const size_t bXp = align_up((size_t)A->n * m * elt);
+    const size_t bC = align_up((size_t)A->nc * A->k * m * elt);
+    int rc = ensure_workspace(A, bXp + 2 * bC, st);
+    if (rc) return rc;
+    char* base = (char*)A->ws.base;
+    if (dtype == H2_F64) {
+        if (!A->f64.built) { set_error("FP64 data not built"); return H2_E_UNSUPPORTED; }
+        return dispatch_cn<double>(A, A->f64, alpha, X, ldx, Y, ldy, (int)m, st, transposed, overwrite,
+                                   (double*)base, (double*)(base + bXp), (double*)(base + bXp + bC));
+    }
+    if (dtype == H2_F32) {
+        if (!A->f32.built) { set_error("FP32 copy not built (add 1<<H2_F32 to params->precisions)"); return H2_E_UNSUPPORTED; }
+        return dispatch_cn<float>(A, A->f32, alpha, X, ldx, Y, ldy, (int)m, st, transposed, overwrite,
+                                  (float*)base, (float*)(base + bXp), (float*)(base + bXp + bC));
+    }
+    set_error("unsupported dtype for the product");
+    return H2_E_UNSUPPORTED;
+}
+
+int matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
+           int32_t dtype, cudaStream_t st, bool transposed) {
+    if (!A || (!X && m > 0) || (!Y && m > 0)) { set_error("null argument"); return H2_E_BADARG; }
+    if (m < 0 || ldx < m || ldy < m || m > (int64_t)1 << 20) { set_error("bad m / leading dimension"); return H2_E_BADARG; }
+    if (dtype != H2_F64 && dtype != H2_F32 && dtype != H2_BF16) { set_error("bad dtype"); return H2_E_BADARG; }
+    if (m == 0) return 0;
+    const bool dx = is_device_pointer(X), dy = is_device_pointer(Y);
+    if (dx && dy) return matmul_device(A, alpha, X, ldx, Y, ldy, m, dtype, st, transposed, false);
+    // host blocks: stage through device buffers (packed, ld = m)
+    const size_t bytes = (size_t)A->n * m * sizeof(double);
+    if (A->ws.stage_bytes < bytes) {
+        H2_CUDA_TRY(cudaStreamSynchronize(st));
+        if (A->ws.stage_x) cudaFree(A->ws.stage_x);
+        if (A->ws.stage_y) cudaFree(A->ws.stage_y);
+        A->ws.stage_x = A->ws.stage_y = nullptr;
+        A->ws.stage_bytes = 0;
+        H2_CUDA_TRY(cudaMalloc(&A->ws.stage_x, bytes));
+        H2_CUDA_TRY(cudaMalloc(&A->ws.stage_y, bytes));
+        A->ws.stage_bytes = bytes;
+    }
+    const double* Xd = X;
+    int64_t ldxd = ldx;
+    if (!dx) {
+        H2_CUDA_TRY(cudaMemcpy2DAsync(A->ws.stage_x, m * sizeof(double), X, ldx * sizeof(double),
+                                      m * sizeof(double), A->n, cudaMemcpyHostToDevice, st));
+        Xd = A->ws.stage_x;
+        ldxd = m;
+    }
+    double* Yd = Y;
+    int64_t ldyd = ldy;
+    if (!dy) {
+        H2_CUDA_TRY(cudaMemcpy2DAsync(A->ws.stage_y, m * sizeof(double), Y, ldy * sizeof(double),
+                                      m * sizeof(double), A->n, cudaMemcpyHostToDevice, st));
+        Yd = A->ws.stage_y;
+        ldyd = m;
+    }
+    int rc = matmul_device(A, alpha, Xd, ldxd, Yd, ldyd, m, dtype, st, transposed, false);
+    if (rc) return rc;
+    if (!dy) {
+        H2_CUDA_TRY(cudaMemcpy2DAsync(Y, ldy * sizeof(double), A->ws.stage_y, m * sizeof(double),
+                                      m * sizeof(double), A->n, cudaMemcpyDeviceToHost, st));
+        H2_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return 0;
+}
+
+}  // namespace h2

@@ -1,0 +1,323 @@
+"""Python binding of libh2.so (ctypes).
+
+Argument marshalling only: every step of the product and of the solve runs in
+the CUDA library.  Functions keep the C names (``h2_build``, ``h2_matmul``,
+``h2_matmul_transposed``, ``h2_block_cg``, ...).  Dense blocks are torch
+tensors (device or host) or numpy arrays (host), float64, n×m with unit column
+stride; PyTorch only supplies the memory and the stream.  If the compiled
+library is missing the import of any entry point raises: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libh2.so")
+
+H2_OK = 0
+H2_E_BADARG = -1
+H2_E_CUDA = -2
+H2_E_NOCONVERGE = -3
+H2_E_BREAKDOWN = -4
+H2_E_TIMEOUT = -5
+H2_E_OOM = -6
+H2_E_UNSUPPORTED = -7
+
+H2_F64, H2_F32, H2_BF16 = 0, 1, 2
+DTYPES = {"f64": H2_F64, "f32": H2_F32, "bf16": H2_BF16}
+H2_CG_COLUMNWISE = 0
+
+_STATUS = {0: "ok", -1: "badarg", -2: "cuda", -3: "noconverge", -4: "breakdown", -5: "timeout", -6: "oom",
+           -7: "unsupported"}
+
+
+class H2Error(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {_STATUS.get(code, code)} ({code}): {msg}")
+        self.code = code
+
+
+class BuildParams(C.Structure):
+    _fields_ = [("q", C.c_int32), ("leaf_size", C.c_int32), ("eta", C.c_double), ("length", C.c_double),
+                ("sigma", C.c_double), ("precisions", C.c_uint32), ("stream", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("k", C.c_int64), ("n_clusters", C.c_int64), ("n_leaves", C.c_int64),
+                ("n_adm", C.c_int64), ("n_near", C.c_int64), ("nnz_near", C.c_int64), ("depth", C.c_int32),
+                ("q", C.c_int32), ("bytes_f64", C.c_int64), ("bytes_f32", C.c_int64), ("bytes_bf16", C.c_int64),
+                ("flops_per_col", C.c_double), ("launches", C.c_int32)]
+
+
+class CGParams(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("variant", C.c_int32),
+                ("inner_dtype", C.c_int32), ("inner_tol", C.c_double), ("max_outer", C.c_int32),
+                ("check_every", C.c_int32), ("stream", C.c_void_p)]
+
+
+class CGResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("outer_steps", C.c_int32),
+                ("h2mm_calls", C.c_int32), ("col_iterations", C.POINTER(C.c_int32)),
+                ("rel_residual", C.POINTER(C.c_double)), ("seconds", C.c_double)]
+
+
+class TreeView(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_clusters", C.c_int64), ("n_adm", C.c_int64), ("n_near", C.c_int64),
+                ("depth", C.c_int32),
+                ("perm", C.POINTER(C.c_int64)), ("cl_offset", C.POINTER(C.c_int64)),
+                ("cl_size", C.POINTER(C.c_int64)), ("cl_level", C.POINTER(C.c_int32)),
+                ("cl_parent", C.POINTER(C.c_int32)), ("cl_son0", C.POINTER(C.c_int32)),
+                ("cl_son1", C.POINTER(C.c_int32)), ("cl_box", C.POINTER(C.c_double)),
+                ("adm_rowptr", C.POINTER(C.c_int64)), ("adm_col", C.POINTER(C.c_int32)),
+                ("near_rowptr", C.POINTER(C.c_int64)), ("near_col", C.POINTER(C.c_int32))]
+
+
+#: every symbol include/h2.h declares
+EXPORTS = ["h2_build", "h2_free", "h2_info", "h2_matmul", "h2_matmul_transposed", "h2_block_cg",
+           "h2_timing_enable", "h2_timing_query",
+           "h2_tree_build", "h2_tree_view_get", "h2_tree_free", "h2_last_error_string", "h2_version"]
+H2_NPHASE = 8
+PHASES = ["gather", "leaf_fwd", "up", "coupling", "down", "leaf_bwd_near"]
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libh2.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library missing: {LIB_PATH} (run __graft_entry__.build())")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    L.h2_build.argtypes = [C.POINTER(BuildParams), vp, i64, C.POINTER(vp)]
+    L.h2_free.argtypes = [vp]
+    L.h2_info.argtypes = [vp, C.POINTER(Info)]
+    for f in (L.h2_matmul, L.h2_matmul_transposed):
+        f.argtypes = [vp, dbl, vp, i64, vp, i64, i64, i32, vp]
+    L.h2_block_cg.argtypes = [vp, vp, i64, vp, i64, i64, C.POINTER(CGParams), C.POINTER(CGResult)]
+    L.h2_timing_enable.argtypes = [vp, i32]
+    L.h2_timing_query.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
+    L.h2_tree_build.argtypes = [C.POINTER(BuildParams), vp, i64, C.POINTER(vp)]
+    L.h2_tree_view_get.argtypes = [vp, C.POINTER(TreeView)]
+    L.h2_tree_free.argtypes = [vp]
+    L.h2_last_error_string.restype = C.c_char_p
+    L.h2_version.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("h2_last_error_string", "h2_version"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str, ok=(0,)):
+    if rc not in ok:
+        raise H2Error(rc, where, lib().h2_last_error_string().decode())
+    return rc
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr_ld(a, name: str, want_rows: int | None = None, writable=False):
+    """(pointer, leading dimension, m, keepalive) of a float64 n×m block."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64:
+            raise TypeError(f"{name} must be float64")
+        if a.dim() == 1:
+            a = a.view(-1, 1)
+        if a.dim() != 2 or (a.shape[1] > 1 and a.stride(1) != 1):
+            raise ValueError(f"{name} must be 2-D with unit column stride")
+        ld = a.stride(0) if a.shape[0] > 1 else a.shape[1]
+        if want_rows is not None and a.shape[0] != want_rows:
+            raise ValueError(f"{name} must have {want_rows} rows")
+        return a.data_ptr(), int(ld), int(a.shape[1]), a
+    arr = np.asarray(a)
+    if arr.dtype != np.float64:
+        raise TypeError(f"{name} must be float64")
+    if arr.ndim == 1:
+        arr = arr.reshape(-1, 1)
+    if writable and not arr.flags.writeable:
+        raise ValueError(f"{name} must be writable")
+    if arr.strides[1] != 8 and arr.shape[1] > 1:
+        raise ValueError(f"{name} must have unit column stride")
+    if want_rows is not None and arr.shape[0] != want_rows:
+        raise ValueError(f"{name} must have {want_rows} rows")
+    ld = arr.strides[0] // 8 if arr.shape[0] > 1 else arr.shape[1]
+    return arr.ctypes.data, int(ld), int(arr.shape[1]), arr
+
+
+# ---------------------------------------------------------------------------
+# C-named entry points
+# ---------------------------------------------------------------------------
+def h2_build(points, q=3, leaf_size=64, eta=2.0, length=0.5, sigma=1e-2, precisions=("f32",), stream=None):
+    """Build the H² matrix of a point cloud; returns an opaque handle (int)."""
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64))
+    if pts.ndim != 2 or pts.shape[1] != 3:
+        raise ValueError("points must be n×3")
+    mask = 0
+    for p in precisions:
+        mask |= 1 << DTYPES[p]
+    bp = BuildParams(q, leaf_size, eta, length, sigma, mask, _stream_ptr(stream))
+    h = C.c_void_p()
+    _check(lib().h2_build(C.byref(bp), pts.ctypes.data, pts.shape[0], C.byref(h)), "h2_build")
+    return h.value
+
+
+def h2_free(handle) -> None:
+    lib().h2_free(handle)
+
+
+def h2_info(handle) -> dict:
+    info = Info()
+    _check(lib().h2_info(handle, C.byref(info)), "h2_info")
+    return {f: getattr(info, f) for f, _ in Info._fields_}
+
+
+def _mm(fn, where, handle, alpha, X, Y, dtype, stream):
+    info_n = h2_info(handle)["n"]
+    xp, ldx, m, kx = _ptr_ld(X, "X", info_n)
+    yp, ldy, my, ky = _ptr_ld(Y, "Y", info_n, writable=True)
+    if my != m:
+        raise ValueError("X and Y must have the same number of columns")
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    _check(fn(handle, float(alpha), xp, ldx, yp, ldy, m, dt, _stream_ptr(stream)), where)
+    return Y
+
+
+def h2_matmul(handle, alpha, X, Y, dtype="f64", stream=None):
+    """Y += alpha·A·X (Y is updated in place and returned)."""
+    return _mm(lib().h2_matmul, "h2_matmul", handle, alpha, X, Y, dtype, stream)
+
+
+def h2_matmul_transposed(handle, alpha, X, Y, dtype="f64", stream=None):
+    """Y += alpha·Aᵀ·X."""
+    return _mm(lib().h2_matmul_transposed, "h2_matmul_transposed", handle, alpha, X, Y, dtype, stream)
+
+
+def h2_timing_enable(handle, enable: bool = True) -> None:
+    _check(lib().h2_timing_enable(handle, 1 if enable else 0), "h2_timing_enable")
+
+
+def h2_timing_query(handle, reset: bool = False):
+    """(dict phase -> accumulated ms, number of recorded products)."""
+    ms = (C.c_double * H2_NPHASE)()
+    calls = C.c_int64()
+    _check(lib().h2_timing_query(handle, ms, C.byref(calls), 1 if reset else 0), "h2_timing_query")
+    return {p: ms[i] for i, p in enumerate(PHASES)}, calls.value
+
+
+@dataclass
+class SolveResult:
+    status: int
+    iterations: int
+    outer_steps: int
+    h2mm_calls: int
+    col_iterations: np.ndarray
+    rel_residual: np.ndarray
+    seconds: float
+
+    @property
+    def status_name(self) -> str:
+        return _STATUS.get(self.status, str(self.status))
+
+
+def h2_block_cg(handle, B, X, tol=1e-8, max_iter=20000, inner_dtype="f64", inner_tol=1e-4, max_outer=30,
+                check_every=1, variant=H2_CG_COLUMNWISE, stream=None) -> SolveResult:
+    """Solve A X = B (X: initial guess in, solution out).  Returns the result;
+    non-convergence and breakdown are reported in ``status``, not raised."""
+    n = h2_info(handle)["n"]
+    bp, ldb, m, kb = _ptr_ld(B, "B", n)
+    xp, ldx, mx, kx = _ptr_ld(X, "X", n, writable=True)
+    if mx != m:
+        raise ValueError("B and X must have the same number of columns")
+    it = np.zeros(max(m, 1), dtype=np.int32)
+    rel = np.zeros(max(m, 1), dtype=np.float64)
+    dt = DTYPES[inner_dtype] if isinstance(inner_dtype, str) else int(inner_dtype)
+    prm = CGParams(tol, max_iter, variant, dt, inner_tol, max_outer, check_every, _stream_ptr(stream))
+    res = CGResult(0, 0, 0, 0, it.ctypes.data_as(C.POINTER(C.c_int32)), rel.ctypes.data_as(C.POINTER(C.c_double)),
+                   0.0)
+    rc = lib().h2_block_cg(handle, bp, ldb, xp, ldx, m, C.byref(prm), C.byref(res))
+    _check(rc, "h2_block_cg", ok=(H2_OK, H2_E_NOCONVERGE, H2_E_BREAKDOWN))
+    return SolveResult(res.status, res.iterations, res.outer_steps, res.h2mm_calls, it[:m].copy(), rel[:m].copy(),
+                       res.seconds)
+
+
+def h2_tree_build(points, leaf_size=64, eta=2.0, q=3) -> dict:
+    """Host-only topology (no GPU): numpy copies of the trees and block lists."""
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64))
+    bp = BuildParams(q, leaf_size, eta, 0.5, 0.0, 0, None)
+    h = C.c_void_p()
+    _check(lib().h2_tree_build(C.byref(bp), pts.ctypes.data, pts.shape[0], C.byref(h)), "h2_tree_build")
+    try:
+        v = TreeView()
+        _check(lib().h2_tree_view_get(h, C.byref(v)), "h2_tree_view_get")
+        nc = v.n_clusters
+
+        def arr(ptr, count):
+            return np.ctypeslib.as_array(ptr, shape=(count,)).copy() if count > 0 else np.zeros(0)
+
+        return dict(
+            n=v.n, n_clusters=nc, n_adm=v.n_adm, n_near=v.n_near, depth=v.depth,
+            perm=arr(v.perm, v.n), offset=arr(v.cl_offset, nc), size=arr(v.cl_size, nc),
+            level=arr(v.cl_level, nc), parent=arr(v.cl_parent, nc), son0=arr(v.cl_son0, nc),
+            son1=arr(v.cl_son1, nc), box=arr(v.cl_box, 6 * nc).reshape(nc, 6),
+            adm_rowptr=arr(v.adm_rowptr, nc + 1), adm_col=arr(v.adm_col, v.n_adm),
+            near_rowptr=arr(v.near_rowptr, nc + 1), near_col=arr(v.near_col, v.n_near),
+        )
+    finally:
+        lib().h2_tree_free(h)
+
+
+class H2Matrix:
+    """Owning wrapper around an h2_matrix handle."""
+
+    def __init__(self, points, q=3, leaf_size=64, eta=2.0, length=0.5, sigma=1e-2, precisions=("f32",),
+                 stream=None):
+        self.handle = h2_build(points, q, leaf_size, eta, length, sigma, precisions, stream)
+        self.info = h2_info(self.handle)
+        self.n = self.info["n"]
+
+    def matmul(self, X, Y, alpha=1.0, dtype="f64", stream=None):
+        return h2_matmul(self.handle, alpha, X, Y, dtype, stream)
+
+    def matmul_transposed(self, X, Y, alpha=1.0, dtype="f64", stream=None):
+        return h2_matmul_transposed(self.handle, alpha, X, Y, dtype, stream)
+
+    def block_cg(self, B, X, **kw) -> SolveResult:
+        return h2_block_cg(self.handle, B, X, **kw)
+
+    def flops(self, m: int) -> float:
+        return self.info["flops_per_col"] * m
+
+    def close(self):
+        if self.handle:
+            h2_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,160 @@
+"""GPU parity of the H² product through the C ABI against the FP64 oracle.
+
+Tolerances (relative Frobenius error of Y_out = Y + α A X): FP64 1e-12,
+FP32 1e-5.  Sizes span several tiles and ragged tails (m not a multiple of
+the 16/32/64-column tiles, leaves of uneven size, trees whose leaves sit on
+several levels)."""
+import numpy as np
+import pytest
+
+from _helpers import rel_fro, require_cuda
+from oracle import h2_oracle as O
+from workloads import ellipsoid_points, gaussian_rhs, sphere_points
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2509_17257_gb300.build as bld
+    bld.build()
+    import paper_2509_17257_gb300 as P
+    return P
+
+
+def _pair(P, pts, q, leaf=64, eta=2.0, sigma=1e-2, length=0.5):
+    H = O.H2Matrix(pts, q=q, leaf_size=leaf, eta=eta, sigma=sigma, length=length)
+    G = P.H2Matrix(pts, q=q, leaf_size=leaf, eta=eta, sigma=sigma, length=length, precisions=("f32",))
+    return H, G
+
+
+def _gpu_apply(G, X, Y0, alpha, dtype, transposed=False):
+    torch = require_cuda()
+    Xd = torch.from_numpy(X).cuda()
+    Yd = torch.from_numpy(Y0).cuda()
+    if transposed:
+        G.matmul_transposed(Xd, Yd, alpha=alpha, dtype=dtype)
+    else:
+        G.matmul(Xd, Yd, alpha=alpha, dtype=dtype)
+    torch.cuda.synchronize()
+    return Yd.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def sphere4096(P):
+    return _pair(P, sphere_points(4096, 0), q=3)
+
+
+def test_counts_match_oracle(sphere4096):
+    H, G = sphere4096
+    c = H.counts()
+    for key in ("n_clusters", "n_leaves", "n_adm", "n_near", "nnz_near", "depth"):
+        assert G.info[key] == c[key], key
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("m", [1, 3, 8, 17, 40, 65])
+def test_matmul_matches_oracle(sphere4096, dtype, m):
+    H, G = sphere4096
+    X = gaussian_rhs(4096, m, 10 + m)
+    Y0 = gaussian_rhs(4096, m, 20 + m)
+    alpha = -0.625
+    want = O.h2mm(H, alpha, X, Y0)
+    got = _gpu_apply(G, X, Y0, alpha, dtype)
+    assert rel_fro(got, want) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_transposed_matches_oracle(sphere4096, dtype):
+    H, G = sphere4096
+    X = gaussian_rhs(4096, 5, 3)
+    Y0 = gaussian_rhs(4096, 5, 4)
+    want = O.h2mm(H, 1.5, X, Y0, transposed=True)
+    got = _gpu_apply(G, X, Y0, 1.5, dtype, transposed=True)
+    assert rel_fro(got, want) <= TOL[dtype]
+
+
+def test_host_buffers_and_leading_dimension(P, sphere4096):
+    torch = require_cuda()
+    H, G = sphere4096
+    X = gaussian_rhs(4096, 12, 5)
+    Y0 = gaussian_rhs(4096, 12, 6)
+    want = O.h2mm(H, 2.0, X[:, 2:9], Y0[:, 1:8])
+    # host numpy views with ld = 12 > m = 7
+    Yh = Y0.copy()
+    G.matmul(X[:, 2:9], Yh[:, 1:8], alpha=2.0)
+    assert rel_fro(Yh[:, 1:8], want) <= 1e-12
+    assert np.array_equal(Yh[:, 0], Y0[:, 0]) and np.array_equal(Yh[:, 8:], Y0[:, 8:])
+    # device views with ld = 12
+    Xd = torch.from_numpy(X).cuda()
+    Yd = torch.from_numpy(Y0).cuda()
+    G.matmul(Xd[:, 2:9], Yd[:, 1:8], alpha=2.0)
+    out = Yd.cpu().numpy()
+    assert rel_fro(out[:, 1:8], want) <= 1e-12
+    assert np.array_equal(out[:, 0], Y0[:, 0]) and np.array_equal(out[:, 8:], Y0[:, 8:])
+    # m = 0 is a no-op
+    G.matmul(np.zeros((4096, 0)), np.zeros((4096, 0)))
+
+
+@pytest.mark.parametrize("case", ["n1", "n64", "n65", "coincident", "planar", "q1", "q2", "q4", "q5",
+                                  "ellipsoid_leaf17"])
+def test_edge_cases(P, case):
+    q, leaf, eta = 3, 64, 2.0
+    if case == "n1":
+        pts = sphere_points(1, 1)
+    elif case == "n64":
+        pts = sphere_points(64, 1)
+    elif case == "n65":
+        pts = sphere_points(65, 1)
+    elif case == "coincident":
+        pts = np.vstack([np.full((150, 3), 0.3), sphere_points(200, 2)])
+    elif case == "planar":
+        pts = sphere_points(3000, 3)
+        pts[:, 2] = 0.0
+    elif case.startswith("q"):
+        q = int(case[1])
+        pts = sphere_points(2500, 4)
+    else:
+        pts = ellipsoid_points(3000, (0.6, 1.9, 1.2), 5)
+        leaf, eta = 17, 1.0
+    H, G = _pair(P, pts, q=q, leaf=leaf, eta=eta)
+    n = pts.shape[0]
+    X = gaussian_rhs(n, 6, 7)
+    Y0 = gaussian_rhs(n, 6, 8)
+    for dtype in ("f64", "f32"):
+        want = O.h2mm(H, 0.75, X, Y0)
+        got = _gpu_apply(G, X, Y0, 0.75, dtype)
+        assert rel_fro(got, want) <= TOL[dtype], (case, dtype)
+        want_t = O.h2mm(H, 0.75, X, Y0, transposed=True)
+        got_t = _gpu_apply(G, X, Y0, 0.75, dtype, transposed=True)
+        assert rel_fro(got_t, want_t) <= TOL[dtype], (case, dtype, "T")
+
+
+def test_precision_workload_full_size(P):
+    """n = 65536 sphere, q = 4, m = 32: the full product against the oracle."""
+    pts = sphere_points(65536, 0)
+    H, G = _pair(P, pts, q=4)
+    X = gaussian_rhs(65536, 32, 1)
+    Y0 = np.zeros((65536, 32))
+    want = O.h2mm(H, 1.0, X, Y0)
+    for dtype in ("f64", "f32"):
+        got = _gpu_apply(G, X, Y0, 1.0, dtype)
+        assert rel_fro(got, want) <= TOL[dtype], dtype
+
+
+def test_errors(P, sphere4096):
+    _, G = sphere4096
+    X = np.zeros((4096, 2))
+    with pytest.raises(P.H2Error) as e:
+        G.matmul(X, X.copy(), dtype="bf16")
+    assert e.value.code == P.H2_E_UNSUPPORTED
+    with pytest.raises(P.H2Error) as e:
+        G.matmul(X, X.copy(), dtype=7)
+    assert e.value.code == P.H2_E_BADARG
+    with pytest.raises(ValueError):
+        G.matmul(np.zeros((4095, 2)), np.zeros((4095, 2)))
+    with pytest.raises(P.H2Error) as e:
+        P.h2_build(np.zeros((0, 3)))
+    assert e.value.code == P.H2_E_BADARG
