@@ -297,7 +297,7 @@ def run_ours(args):
             Xs = torch.zeros_like(B)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            r = G.block_cg(B, Xs, tol=1e-8, max_iter=args.solve_max_iter, inner_dtype=inner, inner_tol=1e-4,
+            r = G.block_cg(B, Xs, tol=1e-8, max_iter=args.solve_max_iter, dtype=inner, inner_tol=1e-4,
                            check_every=4)
             torch.cuda.synchronize()
             solve[name] = {"seconds": round(time.perf_counter() - t0, 3), "status": r.status_name,

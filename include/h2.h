@@ -144,9 +144,11 @@ typedef struct h2_cg_params {
     double tol;          /* per-column relative residual target |r_i|/|b_i| (|b_i| = 0 read as 1) */
     int32_t max_iter;    /* cap on CG iterations (inner iterations summed for refinement)        */
     int32_t variant;     /* h2_cg_variant                                                          */
-    int32_t inner_dtype; /* H2_F64: plain FP64 solve.  H2_F32 / H2_BF16: iterative refinement,
-                            FP64 residual B - A X outside, block CG with the low-precision product
-                            and FP64 vector arithmetic inside                                      */
+    int32_t dtype;       /* precision of the product inside block CG (vectors are always FP64)    */
+    int32_t refine;      /* dtype != H2_F64 only: 1 = iterative refinement (FP64 residual B - A X
+                            outside, block CG with the dtype product inside, X += D); 0 = plain
+                            block CG with the dtype product (converges to the dtype operator's
+                            solution only)                                                         */
     double inner_tol;    /* relative reduction asked of each inner solve (refinement only)          */
     int32_t max_outer;   /* cap on refinement steps                                                  */
     int32_t check_every; /* convergence test every this many iterations (>= 1)                      */

@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "h2_internal.cuh"
@@ -112,8 +114,8 @@ __global__ void __launch_bounds__(256) k_cg_dots(const double* __restrict__ P, c
     if (threadIdx.y == 0 && col < m) {
         double pa = 0.0, pr = 0.0;
         for (unsigned b = 0; b < gridDim.x; ++b) {
-            pa += d.partial[((size_t)b * m + col) * 2 + 0];
-            pr += d.partial[((size_t)b * m + col) * 2 + 1];
+            pa += __ldcg(&d.partial[((size_t)b * m + col) * 2 + 0]);
+            pr += __ldcg(&d.partial[((size_t)b * m + col) * 2 + 1]);
         }
         double alpha = 0.0;
         if (d.active[col]) {
@@ -155,8 +157,8 @@ __global__ void __launch_bounds__(256) k_cg_update(double* __restrict__ X, int64
     if (threadIdx.y == 0 && col < m && d.active[col]) {
         double ar = 0.0, rr = 0.0;
         for (unsigned b = 0; b < gridDim.x; ++b) {
-            ar += d.partial[((size_t)b * m + col) * 2 + 0];
-            rr += d.partial[((size_t)b * m + col) * 2 + 1];
+            ar += __ldcg(&d.partial[((size_t)b * m + col) * 2 + 0]);
+            rr += __ldcg(&d.partial[((size_t)b * m + col) * 2 + 1]);
         }
         const double gamma = ar / d.beta[col];
         d.gamma[col] = gamma;
@@ -234,24 +236,32 @@ struct Solver {
     int init() {
         const size_t nm = (size_t)n * m;
         const int groups = (m + kColsPerCta - 1) / kColsPerCta;
-        size_t bytes = 3 * nm * sizeof(double) + 5 * m * sizeof(double) + 2 * m * sizeof(int) + 4 * sizeof(int) +
-                       (size_t)kRowBlocks * m * 2 * sizeof(double) + groups * sizeof(unsigned) + 1024;
-        H2_CUDA_TRY(cudaMallocAsync(&mem, bytes, st));
+        // carve one allocation into 256-byte aligned pieces; offsets first, then the total
+        size_t off = 0;
+        auto piece = [&](size_t b) { const size_t o = off; off += (b + 255) & ~(size_t)255; return o; };
+        const size_t oR = piece(nm * sizeof(double)), oP = piece(nm * sizeof(double)),
+                     oAP = piece(nm * sizeof(double));
+        const size_t oBn = piece(m * sizeof(double)), oAl = piece(m * sizeof(double)),
+                     oBe = piece(m * sizeof(double)), oGa = piece(m * sizeof(double)),
+                     oRn = piece(m * sizeof(double));
+        const size_t oAct = piece(m * sizeof(int)), oCi = piece(m * sizeof(int)), oSum = piece(4 * sizeof(int));
+        const size_t oPart = piece((size_t)kRowBlocks * m * 2 * sizeof(double));
+        const size_t oTk = piece(groups * sizeof(unsigned));
+        H2_CUDA_TRY(cudaMallocAsync(&mem, off, st));
         char* p = (char*)mem;
-        auto take = [&](size_t b) { char* r = p; p += (b + 255) & ~(size_t)255; return r; };
-        R = (double*)take(nm * sizeof(double));
-        P = (double*)take(nm * sizeof(double));
-        AP = (double*)take(nm * sizeof(double));
-        d.bnorm = (double*)take(m * sizeof(double));
-        d.alpha = (double*)take(m * sizeof(double));
-        d.beta = (double*)take(m * sizeof(double));
-        d.gamma = (double*)take(m * sizeof(double));
-        d.rnorm = (double*)take(m * sizeof(double));
-        d.active = (int*)take(m * sizeof(int));
-        d.conv_iter = (int*)take(m * sizeof(int));
-        d.summary = (int*)take(4 * sizeof(int));
-        d.partial = (double*)take((size_t)kRowBlocks * m * 2 * sizeof(double));
-        d.ticket = (unsigned*)take(groups * sizeof(unsigned));
+        R = (double*)(p + oR);
+        P = (double*)(p + oP);
+        AP = (double*)(p + oAP);
+        d.bnorm = (double*)(p + oBn);
+        d.alpha = (double*)(p + oAl);
+        d.beta = (double*)(p + oBe);
+        d.gamma = (double*)(p + oGa);
+        d.rnorm = (double*)(p + oRn);
+        d.active = (int*)(p + oAct);
+        d.conv_iter = (int*)(p + oCi);
+        d.summary = (int*)(p + oSum);
+        d.partial = (double*)(p + oPart);
+        d.ticket = (unsigned*)(p + oTk);
         H2_CUDA_TRY(cudaMemsetAsync(d.ticket, 0, groups * sizeof(unsigned), st));
         H2_CUDA_TRY(cudaHostAlloc(&h_summary, 4 * sizeof(int), cudaHostAllocDefault));
         return 0;
@@ -263,12 +273,12 @@ struct Solver {
 
     unsigned copy_grid() const { return (unsigned)std::min<int64_t>(((int64_t)n * m + 255) / 256, 152 * 16); }
 
-    // R = B - A X (FP64 product)
-    int residual(const double* B, int64_t ldb, const double* X, int64_t ldx) {
+    // R = B - A X (product in dtype, FP64 by default)
+    int residual(const double* B, int64_t ldb, const double* X, int64_t ldx, int32_t dtype = H2_F64) {
         k_copy2d<<<copy_grid(), 256, 0, st>>>(B, ldb, R, m, n, m);
         H2_LAUNCH_CHECK();
         ++h2mm_calls;
-        return matmul_device(A, -1.0, X, ldx, R, m, m, H2_F64, st, false, false);
+        return matmul_device(A, -1.0, X, ldx, R, m, m, dtype, st, false, false);
     }
 
     // Column-wise block CG on A_dtype X = B with R already holding B - A X.
@@ -286,6 +296,9 @@ struct Solver {
         H2_CUDA_TRY(cudaStreamSynchronize(st));
         int it = 0;
         int status = 0;
+        // H2_CG_TRACE=k prints the largest relative recurrence residual every k checks
+        const char* tr = getenv("H2_CG_TRACE");
+        const int trace = tr ? atoi(tr) : 0;
         if (h_summary[0] > 0) {
             for (it = 1; it <= max_iter; ++it) {
                 ++h2mm_calls;
@@ -300,6 +313,19 @@ struct Solver {
                 if (it % check_every == 0 || it == max_iter) {
                     H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
                     H2_CUDA_TRY(cudaStreamSynchronize(st));
+                    if (trace && (it % trace == 0 || it <= 3)) {
+                        std::vector<double> rn(m), bn(m);
+                        double a0 = 0, b0 = 0, g0 = 0;
+                        cudaMemcpy(rn.data(), d.rnorm, m * sizeof(double), cudaMemcpyDeviceToHost);
+                        cudaMemcpy(bn.data(), d.bnorm, m * sizeof(double), cudaMemcpyDeviceToHost);
+                        cudaMemcpy(&a0, d.alpha, sizeof(double), cudaMemcpyDeviceToHost);
+                        cudaMemcpy(&b0, d.beta, sizeof(double), cudaMemcpyDeviceToHost);
+                        cudaMemcpy(&g0, d.gamma, sizeof(double), cudaMemcpyDeviceToHost);
+                        double mx = 0.0;
+                        for (int i = 0; i < m; ++i) mx = std::max(mx, rn[i] / bn[i]);
+                        fprintf(stderr, "[h2 cg] dtype %d iter %d active %d max |r|/|b| %.3e  col0 alpha %.3e beta %.3e gamma %.3e |r| %.3e |b| %.3e\n", dtype, it,
+                                h_summary[0], mx, a0, b0, g0, rn[0], bn[0]);
+                    }
                     if (h_summary[1]) { status = H2_E_BREAKDOWN; break; }
                     if (h_summary[0] == 0) break;
                 }
@@ -325,8 +351,9 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
     if (m < 0 || (m > 0 && (!B || !X)) || ldb < m || ldx < m) { set_error("bad m / leading dimension"); return H2_E_BADARG; }
     if (!(p->tol >= 0.0) || p->max_iter < 0 || p->check_every < 1) { set_error("bad solver parameters"); return H2_E_BADARG; }
     if (p->variant != H2_CG_COLUMNWISE) { set_error("unsupported CG variant"); return H2_E_UNSUPPORTED; }
-    const int32_t inner = p->inner_dtype;
-    if (inner != H2_F64 && inner != H2_F32 && inner != H2_BF16) { set_error("bad inner dtype"); return H2_E_BADARG; }
+    const int32_t inner = p->dtype;
+    if (inner != H2_F64 && inner != H2_F32 && inner != H2_BF16) { set_error("bad dtype"); return H2_E_BADARG; }
+    const bool refine = inner != H2_F64 && p->refine != 0;
     res->status = 0;
     res->iterations = res->outer_steps = res->h2mm_calls = 0;
     res->seconds = 0.0;
@@ -361,10 +388,10 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
         int rc = S.init();
         if (rc) return rc;
         int total_iters = 0;
-        if (inner == H2_F64) {
-            if ((rc = S.residual(Bd, ldbd, Xd, ldxd))) return rc;
+        if (!refine) {
+            if ((rc = S.residual(Bd, ldbd, Xd, ldxd, inner))) return rc;
             int it = 0;
-            status = S.cg(H2_F64, Bd, ldbd, Xd, ldxd, p->tol, p->max_iter, p->check_every, &it);
+            status = S.cg(inner, Bd, ldbd, Xd, ldxd, p->tol, p->max_iter, p->check_every, &it);
             if (status < 0 && status != H2_E_BREAKDOWN && status != H2_E_NOCONVERGE) return status;
             total_iters = it;
         } else {
@@ -423,7 +450,7 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
                                           cudaMemcpyDeviceToHost, st));
         H2_CUDA_TRY(cudaStreamSynchronize(st));
         if (res->rel_residual) for (int64_t i = 0; i < m; ++i) res->rel_residual[i] = rel[i];
-        if (res->col_iterations) for (int64_t i = 0; i < m; ++i) res->col_iterations[i] = inner == H2_F64 ? ci[i] : total_iters;
+        if (res->col_iterations) for (int64_t i = 0; i < m; ++i) res->col_iterations[i] = refine ? total_iters : ci[i];
         res->h2mm_calls = S.h2mm_calls;
         if (status == 0 && inner == H2_F64) {
             // the recurrence residual reached tol; report the true one as it is

@@ -56,8 +56,8 @@ class Info(C.Structure):
 
 class CGParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("variant", C.c_int32),
-                ("inner_dtype", C.c_int32), ("inner_tol", C.c_double), ("max_outer", C.c_int32),
-                ("check_every", C.c_int32), ("stream", C.c_void_p)]
+                ("dtype", C.c_int32), ("refine", C.c_int32), ("inner_tol", C.c_double),
+                ("max_outer", C.c_int32), ("check_every", C.c_int32), ("stream", C.c_void_p)]
 
 
 class CGResult(C.Structure):
@@ -243,10 +243,12 @@ class SolveResult:
         return _STATUS.get(self.status, str(self.status))
 
 
-def h2_block_cg(handle, B, X, tol=1e-8, max_iter=20000, inner_dtype="f64", inner_tol=1e-4, max_outer=30,
-                check_every=1, variant=H2_CG_COLUMNWISE, stream=None) -> SolveResult:
-    """Solve A X = B (X: initial guess in, solution out).  Returns the result;
-    non-convergence and breakdown are reported in ``status``, not raised."""
+def h2_block_cg(handle, B, X, tol=1e-8, max_iter=20000, dtype="f64", refine=True, inner_tol=1e-4,
+                max_outer=30, check_every=1, variant=H2_CG_COLUMNWISE, stream=None) -> SolveResult:
+    """Solve A X = B (X: initial guess in, solution out).  ``dtype`` is the
+    precision of the product; with a low precision and ``refine`` the solve is
+    an FP64 iterative refinement around low-precision block CG.  Returns the
+    result; non-convergence and breakdown are reported in ``status``, not raised."""
     n = h2_info(handle)["n"]
     bp, ldb, m, kb = _ptr_ld(B, "B", n)
     xp, ldx, mx, kx = _ptr_ld(X, "X", n, writable=True)
@@ -254,8 +256,9 @@ def h2_block_cg(handle, B, X, tol=1e-8, max_iter=20000, inner_dtype="f64", inner
         raise ValueError("B and X must have the same number of columns")
     it = np.zeros(max(m, 1), dtype=np.int32)
     rel = np.zeros(max(m, 1), dtype=np.float64)
-    dt = DTYPES[inner_dtype] if isinstance(inner_dtype, str) else int(inner_dtype)
-    prm = CGParams(tol, max_iter, variant, dt, inner_tol, max_outer, check_every, _stream_ptr(stream))
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    prm = CGParams(tol, max_iter, variant, dt, 1 if refine else 0, inner_tol, max_outer, check_every,
+                   _stream_ptr(stream))
     res = CGResult(0, 0, 0, 0, it.ctypes.data_as(C.POINTER(C.c_int32)), rel.ctypes.data_as(C.POINTER(C.c_double)),
                    0.0)
     rc = lib().h2_block_cg(handle, bp, ldb, xp, ldx, m, C.byref(prm), C.byref(res))
