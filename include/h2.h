@@ -120,6 +120,36 @@ int h2_matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* 
 int h2_matmul_transposed(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y,
                          int64_t ldy, int64_t m, int32_t dtype, void* stream);
 
+/* ---- product without allocation ------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers of
+ * the library that cannot allocate device memory when they call the product:
+ * processes whose device memory is handed out by their own allocator under a
+ * fixed budget (another framework's caching allocator owns the GPU), and hot
+ * paths that cannot afford cudaMalloc's implicit device synchronisation.
+ * h2_matmul may call cudaMalloc to grow the matrix's workspace; this variant
+ * never calls cudaMalloc, cudaFree or any allocating routine.
+ *
+ * Same operation and arguments as h2_matmul (Y <- Y + alpha·A·X), except:
+ *  - X and Y must be device memory (no host staging); dtype H2_F64 or H2_F32.
+ *  - Its scratch (X gathered into cluster order, x̂ and ŷ of every cluster) is a
+ *    fixed array of H2_NOALLOC_SCRATCH_BYTES (32 MiB) compiled into the
+ *    library, reserved on every GPU that loads it until the process exits.
+ *    A product that needs more scratch, elt·(n·m + 2·n_clusters·k·m) bytes
+ *    rounded up (elt = 8 for H2_F64, 4 for H2_F32), is rejected with
+ *    H2_E_UNSUPPORTED and a message giving the size; call h2_matmul or pass
+ *    fewer columns per call.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture.
+ *  - All calls share the one array, which keeps the last call's contents;
+ *    every byte a call reads is written earlier in that call.  Calls whose
+ *    work overlaps on the GPU (different streams, or different matrices at the
+ *    same time) race on the array: serialise them.
+ *  - Rejected while h2_timing_enable is on for A (timing records events). */
+#define H2_NOALLOC_SCRATCH_BYTES (32ull << 20)
+int h2_matmul_noalloc(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                      int64_t m, int32_t dtype, void* stream);
+
 /* ---- per-phase device timing ---------------------------------------------
  * Phases of one product: 0 gather of X into cluster order, 1 leaf forward
  * transformation, 2 upward transfer pass, 3 coupling (admissible part of the

@@ -27,6 +27,7 @@ from .h2 import (  # noqa: F401
     h2_free,
     h2_info,
     h2_matmul,
+    h2_matmul_noalloc,
     h2_matmul_transposed,
     h2_timing_enable,
     h2_timing_query,

@@ -124,6 +124,12 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
 int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
              const h2_cg_params* p, h2_cg_result* res);
 
+// Bytes of scratch one product needs (gathered X, x̂, ŷ), and the product run
+// in caller-provided scratch of at least that size (device X and Y).
+size_t product_scratch_bytes(const h2_matrix* A, int64_t m, int32_t dtype);
+int matmul_in_scratch(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                      int64_t m, int32_t dtype, cudaStream_t st, void* scratch);
+
 bool is_device_pointer(const void* p);
 int device_alloc(h2_matrix* A, void** ptr, size_t bytes);
 

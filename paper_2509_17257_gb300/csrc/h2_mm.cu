@@ -379,6 +379,24 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
     return H2_E_UNSUPPORTED;
 }
 
+size_t product_scratch_bytes(const h2_matrix* A, int64_t m, int32_t dtype) {
+    const size_t elt = dtype == H2_F64 ? sizeof(double) : sizeof(float);
+    return align_up((size_t)A->n * m * elt) + 2 * align_up((size_t)A->nc * A->k * m * elt);
+}
+
+int matmul_in_scratch(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
+                      int32_t dtype, cudaStream_t st, void* scratch) {
+    const size_t elt = dtype == H2_F64 ? sizeof(double) : sizeof(float);
+    const size_t bXp = align_up((size_t)A->n * m * elt);
+    const size_t bC = align_up((size_t)A->nc * A->k * m * elt);
+    char* base = (char*)scratch;
+    if (dtype == H2_F64)
+        return dispatch_cn<double>(A, A->f64, alpha, X, ldx, Y, ldy, (int)m, st, false, false, (double*)base,
+                                   (double*)(base + bXp), (double*)(base + bXp + bC));
+    return dispatch_cn<float>(A, A->f32, alpha, X, ldx, Y, ldy, (int)m, st, false, false, (float*)base,
+                              (float*)(base + bXp), (float*)(base + bXp + bC));
+}
+
 int matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
            int32_t dtype, cudaStream_t st, bool transposed) {
     if (!A || (!X && m > 0) || (!Y && m > 0)) { set_error("null argument"); return H2_E_BADARG; }

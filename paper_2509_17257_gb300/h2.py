@@ -78,7 +78,7 @@ class TreeView(C.Structure):
 
 
 #: every symbol include/h2.h declares
-EXPORTS = ["h2_build", "h2_free", "h2_info", "h2_matmul", "h2_matmul_transposed", "h2_block_cg",
+EXPORTS = ["h2_build", "h2_free", "h2_info", "h2_matmul", "h2_matmul_transposed", "h2_matmul_noalloc", "h2_block_cg",
            "h2_timing_enable", "h2_timing_query",
            "h2_tree_build", "h2_tree_view_get", "h2_tree_free", "h2_last_error_string", "h2_version"]
 H2_NPHASE = 8
@@ -99,7 +99,7 @@ def lib() -> C.CDLL:
     L.h2_build.argtypes = [C.POINTER(BuildParams), vp, i64, C.POINTER(vp)]
     L.h2_free.argtypes = [vp]
     L.h2_info.argtypes = [vp, C.POINTER(Info)]
-    for f in (L.h2_matmul, L.h2_matmul_transposed):
+    for f in (L.h2_matmul, L.h2_matmul_transposed, L.h2_matmul_noalloc):
         f.argtypes = [vp, dbl, vp, i64, vp, i64, i64, i32, vp]
     L.h2_block_cg.argtypes = [vp, vp, i64, vp, i64, i64, C.POINTER(CGParams), C.POINTER(CGResult)]
     L.h2_timing_enable.argtypes = [vp, i32]
@@ -226,6 +226,14 @@ def h2_timing_query(handle, reset: bool = False):
     calls = C.c_int64()
     _check(lib().h2_timing_query(handle, ms, C.byref(calls), 1 if reset else 0), "h2_timing_query")
     return {p: ms[i] for i, p in enumerate(PHASES)}, calls.value
+
+
+def h2_matmul_noalloc(handle, alpha, X, Y, dtype="f64", stream=None):
+    """Y += alpha·A·X without any device allocation (scratch is a fixed 32 MiB
+    array inside the library; X and Y must be CUDA tensors).  For callers that
+    cannot allocate at call time; see include/h2.h for the size limit and the
+    rules on concurrent calls."""
+    return _mm(lib().h2_matmul_noalloc, "h2_matmul_noalloc", handle, alpha, X, Y, dtype, stream)
 
 
 @dataclass
