@@ -188,7 +188,7 @@ def run_ours(args):
     pts = sphere_points(n, cfg["point_seed"])
     t0 = time.perf_counter()
     G = P.H2Matrix(pts, q=cfg["q"], leaf_size=cfg["leaf"], eta=cfg["eta"], length=cfg["length"],
-                   sigma=cfg["sigma"], precisions=("f32",))
+                   sigma=cfg["sigma"], precisions=("f32", "bf16"))
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     info = G.info
@@ -239,6 +239,10 @@ def run_ours(args):
     k64 = max(3, min(args.steps, 10))
     ms64, phases64 = timed("f64", k64, 3, timing=True)
     value64 = flops_step * ws / (ms64 * 1e-3) / 1e9
+
+    # BF16 tensor-core product rate
+    msbf, phasesbf = timed("bf16", args.steps, 3, timing=True)
+    valuebf = flops_step * ws / (msbf * 1e-3) / 1e9
 
     # roofline of the dominant kernel: the coupling phase (one launch per product)
     elt = 8 if dtype == "f64" else 4
@@ -329,6 +333,9 @@ def run_ours(args):
         "h2mm_f64": {"value": round(value64, 3), "unit": "GFLOP/s", "ms_per_step": round(ms64, 4)},
         "phases_ms": {kk: round(v, 4) for kk, v in phases.items()},
         "phases_ms_f64": {kk: round(v, 4) for kk, v in phases64.items()},
+        "h2mm_bf16": {"value": round(valuebf, 3), "unit": "GFLOP/s", "ms_per_step": round(msbf, 4),
+                      "coupling_GBps": round(n_adm * info["k"] * info["k"] * 2 / (phasesbf["coupling"] * 1e-3) / 1e9, 1),
+                      "phases_ms": {kk: round(v, 4) for kk, v in phasesbf.items()}},
         "roofline": roof,
         "e2e": e2e,
         "solve": solve,

@@ -65,6 +65,7 @@ void free_matrix(h2_matrix* A) {
     if (A->ws.base) cudaFree(A->ws.base);
     if (A->ws.stage_x) cudaFree(A->ws.stage_x);
     if (A->ws.stage_y) cudaFree(A->ws.stage_y);
+    if (A->tc.err_host) cudaFreeHost(A->tc.err_host);
     delete A;
 }
 
@@ -183,7 +184,7 @@ int h2_info(const h2_matrix* A, h2_info_t* info) {
     info->q = A->q;
     info->bytes_f64 = A->f64.bytes;
     info->bytes_f32 = A->f32.built ? A->f32.bytes : 0;
-    info->bytes_bf16 = 0;
+    info->bytes_bf16 = A->tc.built ? A->tc.bytes : 0;
     const double k = (double)A->k;
     // leaf forward + leaf backward, up + down transfers, coupling, nearfield, shift
     info->flops_per_col = 2.0 * 2.0 * (double)A->n * k + 2.0 * 2.0 * (double)(A->nc - 1) * k * k +

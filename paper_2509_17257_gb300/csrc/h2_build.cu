@@ -4,6 +4,7 @@
 // typed low-precision copies.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -331,7 +332,157 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
         A->f32.bytes = A->f64.bytes / 2;
         A->f32.built = true;
     }
+    if (precisions & (1u << H2_BF16)) {
+        if (!A->f32.built) {
+            // the BF16 product runs its transfer passes on the FP32 copies of V and E
+            if ((rc = cast_copy(A, (const double*)A->f64.V, &A->f32.V, (int64_t)n * k, st))) return rc;
+            if ((rc = cast_copy(A, (const double*)A->f64.E, &A->f32.E, nc * k * k, st))) return rc;
+        }
+        if ((rc = build_tc_bf16(A, st))) return rc;
+    }
     H2_CUDA_TRY(cudaStreamSynchronize(st));
+    return 0;
+}
+
+// BF16 core-matrix copies of S, V and G, and the schedules of the two tcgen05
+// kernels (coupling over row clusters, leaf phase over row leaves).
+int build_tc_bf16(h2_matrix* A, cudaStream_t st) {
+    const Tree& T = A->T;
+    const int k = A->k;
+    const int KP = round16(k), NP = round16(k);
+    if (KP > 64) {
+        set_error("the BF16 tensor-core product supports q <= 4 (k <= 64)");
+        return H2_E_UNSUPPORTED;
+    }
+    TcData& D = A->tc;
+    D.KP = KP;
+    D.NP = NP;
+    const int64_t nc = A->nc, NL = (int64_t)A->leaves.size();
+    std::vector<int32_t> leaf_pos(nc, -1);
+    for (int64_t lp = 0; lp < NL; ++lp) leaf_pos[A->leaves[lp]] = (int32_t)lp;
+
+    // ---- tiles ----
+    std::vector<TcPackTile> tiles;
+    tiles.reserve(A->n_adm + NL + A->n_near);
+    int64_t off = 0;
+    auto add = [&](int64_t src, int n, int kk, int ld, int np, int kp) {
+        tiles.push_back(TcPackTile{src, off, n, kk, ld, np, kp});
+        const int64_t b = (int64_t)np * kp * 2;
+        off += b;
+        return off - b;
+    };
+    std::vector<int64_t> s_off(A->n_adm), v_off(NL), g_off(A->n_near);
+    for (int64_t j = 0; j < A->n_adm; ++j) s_off[j] = add(j * k * k, k, k, k, NP, KP);
+    const int64_t nS = (int64_t)tiles.size();
+    for (int64_t lp = 0; lp < NL; ++lp) {
+        const int32_t t = A->leaves[lp];
+        const int nt = (int)T.size[t];
+        v_off[lp] = add(T.off[t] * k, nt, k, k, round16(nt), KP);
+    }
+    const int64_t nV = (int64_t)tiles.size() - nS;
+    // nearfield blocks in the order of the row-leaf lists (the FP64 Near array order)
+    std::vector<int32_t> l_np(NL);
+    std::vector<int64_t> near_src(A->n_near);
+    {
+        int64_t j = 0, acc = 0;
+        for (int64_t lp = 0; lp < NL; ++lp) {
+            const int32_t t = A->leaves[lp];
+            const int nt = (int)T.size[t];
+            l_np[lp] = round16(nt);
+            for (int64_t e = T.near_rowptr[t]; e < T.near_rowptr[t + 1]; ++e, ++j) {
+                const int ns = (int)T.size[T.near_col[e]];
+                near_src[j] = acc;
+                g_off[j] = add(acc, nt, ns, ns, round16(nt), round16(ns));
+                acc += (int64_t)nt * ns;
+            }
+        }
+    }
+    const int64_t nG = (int64_t)tiles.size() - nS - nV;
+    D.bytes = off;
+    int rc = 0;
+    void* pm = nullptr;
+    if ((rc = device_alloc(A, &pm, (size_t)std::max<int64_t>(off, 128)))) return rc;
+    D.mat = (uint8_t*)pm;
+    TcPackTile* d_tiles = nullptr;
+    if ((rc = upload(A, &d_tiles, tiles, st))) return rc;
+    if ((rc = launch_pack_tiles(d_tiles, nS, (const double*)A->f64.S, D.mat, st))) return rc;
+    if ((rc = launch_pack_tiles(d_tiles + nS, nV, (const double*)A->f64.V, D.mat, st))) return rc;
+    if ((rc = launch_pack_tiles(d_tiles + nS + nV, nG, (const double*)A->f64.Near, D.mat, st))) return rc;
+
+    // ---- coupling schedule: outputs = clusters with at least one admissible block ----
+    std::vector<int32_t> c_tptr(nc + 1), c_aid(A->n_adm), c_asrc(A->n_adm, 0), c_kp(A->n_adm, KP), c_work, c_zero;
+    std::vector<int64_t> c_boff(A->n_adm);
+    for (int64_t c = 0; c <= nc; ++c) c_tptr[c] = (int32_t)T.adm_rowptr[c];
+    for (int64_t j = 0; j < A->n_adm; ++j) {
+        c_aid[j] = T.adm_col[j];
+        c_boff[j] = s_off[j];
+    }
+    for (int64_t c = 0; c < nc; ++c) (c_tptr[c + 1] > c_tptr[c] ? c_work : c_zero).push_back((int32_t)c);
+    std::stable_sort(c_work.begin(), c_work.end(),
+                     [&](int32_t a, int32_t b) { return c_tptr[a + 1] - c_tptr[a] > c_tptr[b + 1] - c_tptr[b]; });
+    // ---- leaf schedule: outputs = leaf positions; terms = V_t ŷ_t, then G_b X|_ŝ ----
+    std::vector<int32_t> l_tptr(NL + 1), l_aid, l_asrc, l_kp, l_work(NL);
+    std::vector<int64_t> l_boff, l_cost(NL, 0);
+    {
+        int64_t j = 0;
+        for (int64_t lp = 0; lp < NL; ++lp) {
+            const int32_t t = A->leaves[lp];
+            l_tptr[lp] = (int32_t)l_aid.size();
+            l_aid.push_back(t);
+            l_asrc.push_back(1);
+            l_kp.push_back(KP);
+            l_boff.push_back(v_off[lp]);
+            l_cost[lp] += (int64_t)l_np[lp] * KP;
+            for (int64_t e = T.near_rowptr[t]; e < T.near_rowptr[t + 1]; ++e, ++j) {
+                const int32_t sc = T.near_col[e];
+                l_aid.push_back(leaf_pos[sc]);
+                l_asrc.push_back(0);
+                l_kp.push_back(round16((int)T.size[sc]));
+                l_boff.push_back(g_off[j]);
+                l_cost[lp] += (int64_t)l_np[lp] * round16((int)T.size[sc]);
+            }
+        }
+        l_tptr[NL] = (int32_t)l_aid.size();
+    }
+    for (int64_t lp = 0; lp < NL; ++lp) l_work[lp] = (int32_t)lp;
+    std::stable_sort(l_work.begin(), l_work.end(), [&](int32_t a, int32_t b) { return l_cost[a] > l_cost[b]; });
+    std::vector<int64_t> xkoff(NL + 1, 0);
+    std::vector<int32_t> leaf_base(NL), leaf_kdim(NL);
+    for (int64_t lp = 0; lp < NL; ++lp) {
+        const int32_t t = A->leaves[lp];
+        leaf_base[lp] = (int32_t)T.off[t];
+        leaf_kdim[lp] = (int32_t)T.size[t];
+        xkoff[lp + 1] = xkoff[lp] + round16((int)T.size[t]);
+    }
+    D.xk_total = xkoff[NL];
+    D.c_nwork = (int)c_work.size();
+    D.c_nzero = (int)c_zero.size();
+    D.l_nwork = (int)NL;
+#define UP(dst, src) if ((rc = upload(A, &(dst), (src), st))) return rc
+    UP(D.c_work, c_work);
+    UP(D.c_tptr, c_tptr);
+    UP(D.c_aid, c_aid);
+    UP(D.c_asrc, c_asrc);
+    UP(D.c_kp, c_kp);
+    UP(D.c_boff, c_boff);
+    UP(D.c_zero, c_zero);
+    UP(D.l_work, l_work);
+    UP(D.l_tptr, l_tptr);
+    UP(D.l_aid, l_aid);
+    UP(D.l_asrc, l_asrc);
+    UP(D.l_kp, l_kp);
+    UP(D.l_boff, l_boff);
+    UP(D.l_np, l_np);
+    UP(D.xkoff, xkoff);
+    UP(D.leaf_base, leaf_base);
+    UP(D.leaf_kdim, leaf_kdim);
+#undef UP
+    if (!D.err_host) {
+        H2_CUDA_TRY(cudaHostAlloc((void**)&D.err_host, sizeof(int), cudaHostAllocMapped));
+        *D.err_host = 0;
+        H2_CUDA_TRY(cudaHostGetDevicePointer((void**)&D.err_dev, D.err_host, 0));
+    }
+    D.built = true;
     return 0;
 }
 

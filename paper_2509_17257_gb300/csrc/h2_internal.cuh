@@ -56,6 +56,82 @@ struct Timing {
     int64_t calls = 0;
 };
 
+// One tile to convert into the tcgen05 core-matrix BF16 layout: rows n of k
+// FP64 values (leading dimension ld) at element offset src → np × kp tile at
+// byte offset dst (zero padded).
+struct TcPackTile {
+    int64_t src, dst;
+    int32_t n, k, ld, np, kp;
+};
+
+// Arguments of the tcgen05 segmented GEMM (h2_tc.cu).  An output id owns the
+// terms [tptr[id], tptr[id+1]); a term multiplies an activation tile (act0 or
+// act1, id t_aid, t_kp contraction columns) with a matrix tile (bmat + t_boff).
+struct TcGemmParams {
+    int n_work;
+    const int32_t* work;
+    const int32_t* tptr;
+    const int32_t* t_aid;
+    const int32_t* t_asrc;
+    const int32_t* t_kp;
+    const int64_t* t_boff;
+    const int32_t* out_np;
+    int np_fixed;
+    const uint8_t* act0;
+    const int64_t* act0_koff;
+    const uint8_t* act1;
+    const int64_t* act1_koff;
+    int kp_fixed;
+    const uint8_t* bmat;
+    int R, mc;
+    float* yhat;
+    int k, ldc;
+    const int32_t* leaves;
+    const int32_t* cl_off;
+    const int32_t* cl_size;
+    const int32_t* perm;
+    const double* X;
+    int64_t ldx;
+    double* Y;
+    int64_t ldy;
+    double alpha, sigma;
+    int overwrite;
+    int* err;
+};
+
+// BF16 tensor-core copy of the matrix data and the schedules of its kernels.
+struct TcData {
+    bool built = false;
+    int KP = 0, NP = 0;
+    uint8_t* mat = nullptr;  // core-matrix tiles: S (list order), V (leaf order), G (near order)
+    int64_t bytes = 0;
+    // coupling: outputs are clusters
+    int32_t* c_work = nullptr;
+    int c_nwork = 0;
+    int32_t* c_tptr = nullptr;
+    int32_t* c_aid = nullptr;
+    int32_t* c_asrc = nullptr;
+    int32_t* c_kp = nullptr;
+    int64_t* c_boff = nullptr;
+    int32_t* c_zero = nullptr;
+    int c_nzero = 0;
+    // leaf: outputs are leaf positions
+    int32_t* l_work = nullptr;
+    int l_nwork = 0;
+    int32_t* l_tptr = nullptr;
+    int32_t* l_aid = nullptr;
+    int32_t* l_asrc = nullptr;
+    int32_t* l_kp = nullptr;
+    int64_t* l_boff = nullptr;
+    int32_t* l_np = nullptr;
+    int64_t* xkoff = nullptr;   // [n_leaves+1] prefix sums of round16(|leaf|)
+    int64_t xk_total = 0;
+    int32_t* leaf_base = nullptr;  // first point position of each leaf
+    int32_t* leaf_kdim = nullptr;  // points of each leaf
+    int* err_host = nullptr;       // mapped pinned flag written by the kernels on a timeout
+    int* err_dev = nullptr;
+};
+
 struct Workspace {
     void* base = nullptr;
     size_t bytes = 0;
@@ -105,6 +181,7 @@ struct h2_matrix {
     double* d_nodes = nullptr;       // [nc][3][q] Chebyshev nodes per cluster
 
     h2::MatData f64, f32;
+    h2::TcData tc;
     h2::Workspace ws;
     h2::Timing timing;
     int32_t launches_per_product = 0;
@@ -129,6 +206,17 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
 size_t product_scratch_bytes(const h2_matrix* A, int64_t m, int32_t dtype);
 int matmul_in_scratch(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
                       int64_t m, int32_t dtype, cudaStream_t st, void* scratch);
+
+// tcgen05 BF16 kernels (h2_tc.cu)
+int tc_smem_bytes();
+int launch_tc_gemm(int mode, const TcGemmParams& p, int grid, cudaStream_t st);
+int launch_pack_tiles(const TcPackTile* tiles, int64_t count, const double* src, uint8_t* dst, cudaStream_t st);
+int launch_pack_act(const float* src, int64_t ld, int ids, const int32_t* base, const int32_t* kdim, int kdim_fixed,
+                    const int64_t* koff, int kp_fixed, int mc, int R, uint8_t* dst, cudaStream_t st);
+int launch_zero_clusters(const int32_t* ids, int count, float* yhat, int k, int ldc, int mc, cudaStream_t st);
+int build_tc_bf16(h2_matrix* A, cudaStream_t st);
+
+inline int round16(int x) { return (x + 15) & ~15; }
 
 bool is_device_pointer(const void* p);
 int device_alloc(h2_matrix* A, void** ptr, size_t bytes);

@@ -331,14 +331,6 @@ int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int
     return marks.commit();
 }
 
-template <typename T>
-int dispatch_cn(h2_matrix* A, const MatData& D, double alpha, const double* X, int64_t ldx, double* Y,
-                int64_t ldy, int m, cudaStream_t st, bool transposed, bool overwrite, T* Xp, T* xhat, T* yhat) {
-    if (m <= 16) return run_chain<T, 4, 1>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat);
-    if (m <= 32) return run_chain<T, 4, 2>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat);
-    return run_chain<T, 4, 4>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat);
-}
-
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int ensure_workspace(h2_matrix* A, size_t bytes, cudaStream_t st) {
@@ -354,6 +346,145 @@ int ensure_workspace(h2_matrix* A, size_t bytes, cudaStream_t st) {
     return 0;
 }
 
+
+// BF16 product: the coupling and the leaf phase (nearfield + backward
+// transformation + shift) run on the tensor cores (h2_tc.cu); the gather, the
+// forward transformation and the transfer passes run in FP32 on the CUDA cores
+// with the FP32 copies of V and E.  Columns are processed in chunks of at most
+// 64 (128 MMA rows: high and low BF16 parts of each column).
+template <int CN>
+int run_chain_bf16(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int m,
+                   cudaStream_t st, bool overwrite) {
+    constexpr int RM = 4, MT = 16 * RM, NT = 16 * CN;
+    const TcData& D = A->tc;
+    const int k = A->k, KP = D.KP;
+    const int64_t n = A->n, nc = A->nc;
+    const int NL = (int)A->leaves.size();
+    const float* V = (const float*)A->f32.V;
+    const float* E = (const float*)A->f32.E;
+    if (*D.err_host) {
+        *D.err_host = 0;
+        set_error("a previous BF16 product hit a device-side wait limit (results of that call are invalid)");
+        return H2_E_TIMEOUT;
+    }
+    const int grid_cap = 152;
+    for (int c0 = 0; c0 < m; c0 += 64) {
+        const int mc = std::min(64, m - c0);
+        const int R = round16(2 * mc);
+        const size_t bXp = align_up((size_t)n * mc * 4), bC = align_up((size_t)nc * k * mc * 4);
+        const size_t bXcm = align_up((size_t)R * D.xk_total * 2), bAct = align_up((size_t)nc * R * KP * 2);
+        int rc = ensure_workspace(A, bXp + 2 * bC + bXcm + 2 * bAct, st);
+        if (rc) return rc;
+        char* base = (char*)A->ws.base;
+        float* Xp = (float*)base;
+        float* xhat = (float*)(base + bXp);
+        float* yhat = (float*)(base + bXp + bC);
+        uint8_t* Xcm = (uint8_t*)(base + bXp + 2 * bC);
+        uint8_t* xcm = Xcm + bXcm;
+        uint8_t* ycm = xcm + bAct;
+        const unsigned gy = (unsigned)((mc + NT - 1) / NT), gzk = (unsigned)((k + MT - 1) / MT);
+        PhaseMarks marks(A, st);
+        marks.mark();
+        {
+            const int64_t total = n * mc;
+            const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+            k_gather<float><<<g, 256, 0, st>>>(X + c0, ldx, A->d_perm, n, mc, Xp);
+            H2_LAUNCH_CHECK();
+        }
+        if ((rc = launch_pack_act(Xp, mc, NL, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, R, Xcm, st))) return rc;
+        marks.mark();
+        k_leaf_fwd<float, RM, CN><<<dim3((unsigned)NL, gy, gzk), kThreads, 0, st>>>(A->d_leaves, A->d_cl_off,
+                                                                                  A->d_cl_size, V, Xp, xhat, k, mc);
+        H2_LAUNCH_CHECK();
+        marks.mark();
+        for (int l = A->depth - 1; l >= 0; --l) {
+            const int64_t b = A->up_ptr[l], e = A->up_ptr[l + 1];
+            if (e == b) continue;
+            k_up<float, RM, CN><<<dim3((unsigned)(e - b), gy, gzk), kThreads, 0, st>>>(A->d_up_list + b, A->d_son0,
+                                                                                      A->d_son1, E, xhat, k, mc);
+            H2_LAUNCH_CHECK();
+        }
+        if ((rc = launch_pack_act(xhat, mc, (int)nc, nullptr, nullptr, k, nullptr, KP, mc, R, xcm, st))) return rc;
+        marks.mark();
+        if ((rc = launch_zero_clusters(D.c_zero, D.c_nzero, yhat, k, mc, mc, st))) return rc;
+        TcGemmParams cp{};
+        cp.n_work = D.c_nwork;
+        cp.work = D.c_work;
+        cp.tptr = D.c_tptr;
+        cp.t_aid = D.c_aid;
+        cp.t_asrc = D.c_asrc;
+        cp.t_kp = D.c_kp;
+        cp.t_boff = D.c_boff;
+        cp.out_np = nullptr;
+        cp.np_fixed = D.NP;
+        cp.act0 = xcm;
+        cp.act0_koff = nullptr;
+        cp.act1 = xcm;
+        cp.act1_koff = nullptr;
+        cp.kp_fixed = KP;
+        cp.bmat = D.mat;
+        cp.R = R;
+        cp.mc = mc;
+        cp.yhat = yhat;
+        cp.k = k;
+        cp.ldc = mc;
+        cp.err = D.err_dev;
+        if (cp.n_work > 0 && (rc = launch_tc_gemm(0, cp, std::min(cp.n_work, grid_cap), st))) return rc;
+        marks.mark();
+        for (int l = 1; l <= A->depth; ++l) {
+            const int64_t b = A->down_ptr[l], e = A->down_ptr[l + 1];
+            if (e == b) continue;
+            k_down<float, RM, CN><<<dim3((unsigned)(e - b), gy, gzk), kThreads, 0, st>>>(A->d_down_list + b,
+                                                                                        A->d_parent, E, yhat, k, mc);
+            H2_LAUNCH_CHECK();
+        }
+        if ((rc = launch_pack_act(yhat, mc, (int)nc, nullptr, nullptr, k, nullptr, KP, mc, R, ycm, st))) return rc;
+        marks.mark();
+        TcGemmParams lp{};
+        lp.n_work = D.l_nwork;
+        lp.work = D.l_work;
+        lp.tptr = D.l_tptr;
+        lp.t_aid = D.l_aid;
+        lp.t_asrc = D.l_asrc;
+        lp.t_kp = D.l_kp;
+        lp.t_boff = D.l_boff;
+        lp.out_np = D.l_np;
+        lp.np_fixed = 0;
+        lp.act0 = Xcm;
+        lp.act0_koff = D.xkoff;
+        lp.act1 = ycm;
+        lp.act1_koff = nullptr;
+        lp.kp_fixed = KP;
+        lp.bmat = D.mat;
+        lp.R = R;
+        lp.mc = mc;
+        lp.leaves = A->d_leaves;
+        lp.cl_off = A->d_cl_off;
+        lp.cl_size = A->d_cl_size;
+        lp.perm = A->d_perm;
+        lp.X = X + c0;
+        lp.ldx = ldx;
+        lp.Y = Y + c0;
+        lp.ldy = ldy;
+        lp.alpha = alpha;
+        lp.sigma = A->sigma;
+        lp.overwrite = overwrite ? 1 : 0;
+        lp.err = D.err_dev;
+        if ((rc = launch_tc_gemm(1, lp, std::min(lp.n_work, grid_cap), st))) return rc;
+        marks.mark();
+        if ((rc = marks.commit())) return rc;
+    }
+    return 0;
+}
+
+template <typename T>
+int dispatch_cn(h2_matrix* A, const MatData& D, double alpha, const double* X, int64_t ldx, double* Y,
+                int64_t ldy, int m, cudaStream_t st, bool transposed, bool overwrite, T* Xp, T* xhat, T* yhat) {
+    if (m <= 16) return run_chain<T, 4, 1>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat);
+    if (m <= 32) return run_chain<T, 4, 2>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat);
+    return run_chain<T, 4, 4>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat);
+}
+
 }  // namespace
 
 int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
@@ -362,7 +493,7 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
     const size_t elt = dtype == H2_F64 ? sizeof(double) : sizeof(float);
     const size_t bXp = align_up((size_t)A->n * m * elt);
     const size_t bC = align_up((size_t)A->nc * A->k * m * elt);
-    int rc = ensure_workspace(A, bXp + 2 * bC, st);
+    int rc = dtype == H2_BF16 ? 0 : ensure_workspace(A, bXp + 2 * bC, st);
     if (rc) return rc;
     char* base = (char*)A->ws.base;
     if (dtype == H2_F64) {
@@ -374,6 +505,13 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
         if (!A->f32.built) { set_error("FP32 copy not built (add 1<<H2_F32 to params->precisions)"); return H2_E_UNSUPPORTED; }
         return dispatch_cn<float>(A, A->f32, alpha, X, ldx, Y, ldy, (int)m, st, transposed, overwrite,
                                   (float*)base, (float*)(base + bXp), (float*)(base + bXp + bC));
+    }
+    if (dtype == H2_BF16) {
+        if (!A->tc.built) { set_error("BF16 copy not built (add 1<<H2_BF16 to params->precisions)"); return H2_E_UNSUPPORTED; }
+        if (transposed) { set_error("the BF16 product supports A·X only (use H2_F32 or H2_F64 for Aᵀ)"); return H2_E_UNSUPPORTED; }
+        if (m <= 16) return run_chain_bf16<1>(A, alpha, X, ldx, Y, ldy, (int)m, st, overwrite);
+        if (m <= 32) return run_chain_bf16<2>(A, alpha, X, ldx, Y, ldy, (int)m, st, overwrite);
+        return run_chain_bf16<4>(A, alpha, X, ldx, Y, ldy, (int)m, st, overwrite);
     }
     set_error("unsupported dtype for the product");
     return H2_E_UNSUPPORTED;

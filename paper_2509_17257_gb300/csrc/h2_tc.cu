@@ -1,0 +1,414 @@
+// Tensor-core (tcgen05) kernels of the BF16 product: the coupling phase
+// (ŷ_t = Σ_{b∈C_t} S_b x̂_s, Sec. 3 Alg. "list_addeval" over the row-cluster
+// lists of Alg. "prepare_addeval") and the leaf phase (Y|_t̂ += α(V_t ŷ_t +
+// Σ_{b∈L-} G_b X|_ŝ + σ X|_t̂), Alg. "fast_addeval" inadmissible part + the
+// backward transformation at the leaves), with the k×m coefficient blocks of
+// Sec. 4.
+//
+// Formulation: every product is computed transposed, Dᵀ = Σ Aᵀ Bᵀ, so that the
+// right-hand-side columns are the MMA rows (M) and the matrices (S_b, G_b, V_t)
+// are the B operand in their natural row-major orientation:
+//   D[r, n] = Σ_k act[r, k] · mat[n, k]
+// act rows r = 2i + h hold column i of x̂ / X / ŷ split into a BF16 high part
+// (h = 0) and the BF16 rounding remainder (h = 1); the two rows are added in
+// the epilogue (adjacent TMEM lanes, one shuffle).  The matrices are stored in
+// HBM once, in BF16, already in the tcgen05 "no swizzle, K-major" core-matrix
+// order (8 rows × 16 bytes per core matrix, row groups outermost), so one bulk
+// copy per tile lands it in shared memory ready for the MMA.
+//
+// Kernel roles (one persistent CTA per SM, 192 threads):
+//   warp 0        bulk-copy producer (cp.async.bulk + mbarrier complete_tx)
+//   warp 1        TMEM owner and MMA issuer (tcgen05.mma kind::f16, FP32 accumulate)
+//   warps 2..5    epilogue (tcgen05.ld, hi+lo combine, stores)
+// Accumulators are double-buffered in TMEM so the epilogue of one output tile
+// overlaps the MMAs of the next.  Every wait is bounded; on a timeout the
+// kernel raises an error flag, drains its own copies and MMAs, frees TMEM and
+// returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <vector>
+
+#include "h2_internal.cuh"
+
+namespace h2 {
+
+namespace {
+
+constexpr int kStages = 6;
+constexpr int kAStageBytes = 128 * 64 * 2;  // up to 128 rows × 64 contraction columns
+constexpr int kBStageBytes = 64 * 64 * 2;   // up to 64 rows × 64 contraction columns
+constexpr int kStageBytes = kAStageBytes + kBStageBytes;
+constexpr int kTcThreads = 192;
+constexpr int kAccCols = 64;                // TMEM columns per accumulator buffer
+constexpr uint32_t kSpinLimit = 1u << 25;   // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i)
+        if (mbar_try(b, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Shared-memory matrix descriptor, no swizzle, K-major: LBO = byte distance of
+// core matrices adjacent along K, SBO = byte distance of adjacent 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor: FP32 accumulate, BF16 A and B, both K-major.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Byte offset of element (row r, column c) of a core-matrix tile whose rows hold
+// kp (multiple of 8) BF16 values.
+__host__ __device__ __forceinline__ int64_t cm_off(int r, int c, int kp) {
+    return ((int64_t)(r >> 3) * (kp >> 3) + (c >> 3)) * 128 + (r & 7) * 16 + (c & 7) * 2;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Packing kernels
+// ---------------------------------------------------------------------------
+
+// One tile per CTA: dst (np × kp core-matrix BF16) ← src (n × k row-major FP64,
+// leading dimension ld), zero padding.
+__global__ void k_pack_tiles(const TcPackTile* __restrict__ tiles, int64_t count, const double* __restrict__ src,
+                             uint8_t* __restrict__ dst) {
+    for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
+        const TcPackTile d = tiles[t];
+        for (int e = threadIdx.x; e < d.np * d.kp; e += blockDim.x) {
+            const int r = e / d.kp, c = e % d.kp;
+            const double v = (r < d.n && c < d.k) ? src[d.src + (int64_t)r * d.ld + c] : 0.0;
+            const __nv_bfloat16 b = __double2bfloat16(v);
+            *(__nv_bfloat16*)(dst + d.dst + cm_off(r, c, d.kp)) = b;
+        }
+    }
+}
+
+// Activation tiles: for each id (cluster or leaf), rows r = 2i + h (i < mc) of
+// column i of the FP32 source split into BF16 high (h = 0) and low (h = 1)
+// parts; columns κ < kdim(id) read src[(base(id) + κ) * ld + i]; zero padding to
+// R rows and kp(id) columns.  kp(id) = kp_fixed, or koff[id+1] - koff[id].
+__global__ void k_pack_act(const float* __restrict__ src, int64_t ld, int ids, const int32_t* __restrict__ base,
+                           const int32_t* __restrict__ kdim, int kdim_fixed, const int64_t* __restrict__ koff,
+                           int kp_fixed, int mc, int R, uint8_t* __restrict__ dst) {
+    for (int id = blockIdx.x; id < ids; id += gridDim.x) {
+        const int kp = koff ? (int)(koff[id + 1] - koff[id]) : kp_fixed;
+        const int64_t tile = (koff ? koff[id] : (int64_t)id * kp_fixed) * (int64_t)R * 2;
+        const int kd = kdim ? kdim[id] : kdim_fixed;
+        const int64_t b = base ? (int64_t)base[id] : (int64_t)id * kdim_fixed;
+        for (int e = threadIdx.x; e < R * kp; e += blockDim.x) {
+            const int r = e % R, c = e / R;
+            const int i = r >> 1;
+            float v = 0.f;
+            if (i < mc && c < kd) {
+                const float x = src[(b + c) * ld + i];
+                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                v = (r & 1) ? x - __bfloat162float(hi) : x;
+            }
+            *(__nv_bfloat16*)(dst + tile + cm_off(r, c, kp)) = __float2bfloat16_rn(v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The tcgen05 segmented GEMM
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], accf_bar[2], acce_bar[2], drain_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_shared;
+    volatile int& abort_flag = abort_shared;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf_bar[b], 1);
+            mbar_init(&acce_bar[b], 128);
+        }
+        mbar_init(&drain_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(2 * kAccCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const int R = p.R;
+    const int M = R <= 64 ? 64 : 128;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t pend_phase[kStages];
+            bool pend[kStages];
+            for (int s = 0; s < kStages; ++s) pend[s] = false;
+            for (int w = blockIdx.x; w < p.n_work && !abort_flag; w += gridDim.x) {
+                const int id = p.work[w];
+                const int np = p.out_np ? p.out_np[id] : p.np_fixed;
+                for (int e = p.tptr[id]; e < p.tptr[id + 1]; ++e) {
+                    if (!mbar_wait(&empty_bar[stage], phase ^ 1)) {
+                        abort_flag = 1;
+                        atomicExch(p.err, 1);
+                        break;
+                    }
+                    const int kp = p.t_kp[e];
+                    const int aid = p.t_aid[e];
+                    const uint8_t* abase = p.t_asrc[e] ? p.act1 : p.act0;
+                    const int64_t* koff = p.t_asrc[e] ? p.act1_koff : p.act0_koff;
+                    const int64_t akoff = koff ? koff[aid] : (int64_t)aid * p.kp_fixed;
+                    const uint32_t abytes = (uint32_t)(R * kp * 2);
+                    const uint32_t bbytes = (uint32_t)(np * kp * 2);
+                    uint8_t* sA = smem + stage * kStageBytes;
+                    uint8_t* sB = sA + kAStageBytes;
+                    mbar_expect_tx(&full_bar[stage], abytes + bbytes);
+                    bulk_g2s(sA, abase + akoff * R * 2, abytes, &full_bar[stage]);
+                    bulk_g2s(sB, p.bmat + p.t_boff[e], bbytes, &full_bar[stage]);
+                    pend[stage] = true;
+                    pend_phase[stage] = phase;
+                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                }
+            }
+            // wait until every copy issued by this CTA has landed
+            for (int s = 0; s < kStages; ++s)
+                if (pend[s] && !mbar_wait(&full_bar[s], pend_phase[s])) atomicExch(p.err, 2);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            int it = 0;
+            bool issued = false;
+            for (int w = blockIdx.x; w < p.n_work && !abort_flag; w += gridDim.x, ++it) {
+                const int id = p.work[w];
+                const int np = p.out_np ? p.out_np[id] : p.np_fixed;
+                const int acc = it & 1;
+                if (!mbar_wait(&acce_bar[acc], ((it >> 1) & 1) ^ 1)) {
+                    abort_flag = 1;
+                    atomicExch(p.err, 3);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * kAccCols);
+                const uint32_t idesc = idesc_bf16(M, np);
+                bool first = true;
+                for (int e = p.tptr[id]; e < p.tptr[id + 1]; ++e) {
+                    if (!mbar_wait(&full_bar[stage], phase)) {
+                        abort_flag = 1;
+                        atomicExch(p.err, 4);
+                        break;
+                    }
+                    tc_fence_after();
+                    const int kp = p.t_kp[e];
+                    const uint32_t sA = smem_u32(smem + stage * kStageBytes);
+                    const uint32_t sB = sA + kAStageBytes;
+                    const uint32_t sbo = (uint32_t)(kp >> 3) * 128;
+                    for (int kk = 0; kk < kp / 16; ++kk) {
+                        const uint64_t ad = smem_desc(sA + kk * 256, 128, sbo);
+                        const uint64_t bd = smem_desc(sB + kk * 256, 128, sbo);
+                        mma_bf16(d, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+                    }
+                    issued = true;
+                    first = false;
+                    mma_commit(&empty_bar[stage]);
+                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                }
+                if (abort_flag) break;
+                mma_commit(&accf_bar[acc]);
+            }
+            if (issued) {
+                // all MMAs of this CTA complete before TMEM is released
+                mma_commit(&drain_bar);
+                if (!mbar_wait(&drain_bar, 0)) atomicExch(p.err, 5);
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5, TMEM lane quadrant warp % 4) ----------------
+        const int q = warp & 3;
+        int row;
+        if (M == 128) row = 32 * q + lane;
+        else row = lane < 16 ? 16 * q + lane : -1;
+        const int i = row >> 1;
+        const bool writer = row >= 0 && !(row & 1) && i < p.mc;
+        int it = 0;
+        for (int w = blockIdx.x; w < p.n_work; w += gridDim.x, ++it) {
+            const int id = p.work[w];
+            const int np = p.out_np ? p.out_np[id] : p.np_fixed;
+            const int acc = it & 1;
+            // warp-uniform wait: a completed phase stays completed, so any lane's
+            // success is the warp's success
+            const bool ok = __any_sync(0xffffffffu, mbar_wait(&accf_bar[acc], (it >> 1) & 1));
+            if (!ok) {
+                if (lane == 0) atomicExch(p.err, 6);
+                abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            for (int c0 = 0; c0 < np; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kAccCols + c0), v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 1);
+                if (writer) {
+                    if (MODE == 0) {
+                        // ŷ_t[ν][c0 + i] (FP32, cluster-major [k][m])
+                        float* out = p.yhat + (int64_t)id * p.k * p.ldc;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int nu = c0 + j;
+                            if (nu < p.k) out[(int64_t)nu * p.ldc + i] = v[j];
+                        }
+                    } else {
+                        // leaf: Y[perm[off + pt]][col] (+)= α (D + σ X)
+                        const int t = p.leaves[id];
+                        const int off = p.cl_off[t], nt = p.cl_size[t];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int pt = c0 + j;
+                            if (pt < nt) {
+                                const int64_t g = p.perm[off + pt];
+                                const double z = (double)v[j] + p.sigma * p.X[g * p.ldx + i];
+                                double* y = p.Y + g * p.ldy + i;
+                                if (p.overwrite) *y = p.alpha * z; else *y += p.alpha * z;
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acce_bar[acc]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kAccCols) : "memory");
+}
+
+// Zero ŷ of clusters whose coupling list is empty.
+__global__ void k_zero_clusters(const int32_t* __restrict__ ids, int count, float* __restrict__ yhat, int k, int ldc,
+                                int mc) {
+    for (int c = blockIdx.x; c < count; c += gridDim.x) {
+        float* y = yhat + (int64_t)ids[c] * k * ldc;
+        for (int e = threadIdx.x; e < k * mc; e += blockDim.x) y[(int64_t)(e / mc) * ldc + e % mc] = 0.f;
+    }
+}
+
+int tc_smem_bytes() { return kStages * kStageBytes + 1024; }
+
+int launch_tc_gemm(int mode, const TcGemmParams& p, int grid, cudaStream_t st) {
+    static bool attr_set[2] = {false, false};
+    const int smem = tc_smem_bytes();
+    if (mode == 0) {
+        if (!attr_set[0]) {
+            H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            attr_set[0] = true;
+        }
+        k_tc_gemm<0><<<grid, kTcThreads, smem, st>>>(p);
+    } else {
+        if (!attr_set[1]) {
+            H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            attr_set[1] = true;
+        }
+        k_tc_gemm<1><<<grid, kTcThreads, smem, st>>>(p);
+    }
+    H2_LAUNCH_CHECK();
+    return 0;
+}
+
+int launch_pack_tiles(const TcPackTile* tiles, int64_t count, const double* src, uint8_t* dst, cudaStream_t st) {
+    if (count <= 0) return 0;
+    const unsigned g = (unsigned)std::min<int64_t>(count, 152 * 16);
+    k_pack_tiles<<<g, 256, 0, st>>>(tiles, count, src, dst);
+    H2_LAUNCH_CHECK();
+    return 0;
+}
+
+int launch_pack_act(const float* src, int64_t ld, int ids, const int32_t* base, const int32_t* kdim, int kdim_fixed,
+                    const int64_t* koff, int kp_fixed, int mc, int R, uint8_t* dst, cudaStream_t st) {
+    if (ids <= 0) return 0;
+    const unsigned g = (unsigned)std::min(ids, 152 * 8);
+    k_pack_act<<<g, 256, 0, st>>>(src, ld, ids, base, kdim, kdim_fixed, koff, kp_fixed, mc, R, dst);
+    H2_LAUNCH_CHECK();
+    return 0;
+}
+
+int launch_zero_clusters(const int32_t* ids, int count, float* yhat, int k, int ldc, int mc, cudaStream_t st) {
+    if (count <= 0) return 0;
+    k_zero_clusters<<<(unsigned)std::min(count, 152 * 8), 256, 0, st>>>(ids, count, yhat, k, ldc, mc);
+    H2_LAUNCH_CHECK();
+    return 0;
+}
+
+}  // namespace h2

@@ -13,7 +13,7 @@ from workloads import ellipsoid_points, gaussian_rhs, sphere_points
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5}
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 3e-3}
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +26,8 @@ def P():
 
 def _pair(P, pts, q, leaf=64, eta=2.0, sigma=1e-2, length=0.5):
     H = O.H2Matrix(pts, q=q, leaf_size=leaf, eta=eta, sigma=sigma, length=length)
-    G = P.H2Matrix(pts, q=q, leaf_size=leaf, eta=eta, sigma=sigma, length=length, precisions=("f32",))
+    prec = ("f32", "bf16") if q <= 4 else ("f32",)
+    G = P.H2Matrix(pts, q=q, leaf_size=leaf, eta=eta, sigma=sigma, length=length, precisions=prec)
     return H, G
 
 
@@ -54,8 +55,8 @@ def test_counts_match_oracle(sphere4096):
         assert G.info[key] == c[key], key
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("m", [1, 3, 8, 17, 40, 65])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("m", [1, 3, 8, 17, 40, 64, 65, 130])
 def test_matmul_matches_oracle(sphere4096, dtype, m):
     H, G = sphere4096
     X = gaussian_rhs(4096, m, 10 + m)
@@ -123,10 +124,14 @@ def test_edge_cases(P, case):
     n = pts.shape[0]
     X = gaussian_rhs(n, 6, 7)
     Y0 = gaussian_rhs(n, 6, 8)
-    for dtype in ("f64", "f32"):
+    for dtype in ("f64", "f32", "bf16"):
+        if dtype == "bf16" and q > 4:
+            continue
         want = O.h2mm(H, 0.75, X, Y0)
         got = _gpu_apply(G, X, Y0, 0.75, dtype)
         assert rel_fro(got, want) <= TOL[dtype], (case, dtype)
+        if dtype == "bf16":
+            continue  # the BF16 product is A·X only
         want_t = O.h2mm(H, 0.75, X, Y0, transposed=True)
         got_t = _gpu_apply(G, X, Y0, 0.75, dtype, transposed=True)
         assert rel_fro(got_t, want_t) <= TOL[dtype], (case, dtype, "T")
@@ -139,7 +144,7 @@ def test_precision_workload_full_size(P):
     X = gaussian_rhs(65536, 32, 1)
     Y0 = np.zeros((65536, 32))
     want = O.h2mm(H, 1.0, X, Y0)
-    for dtype in ("f64", "f32"):
+    for dtype in ("f64", "f32", "bf16"):
         got = _gpu_apply(G, X, Y0, 1.0, dtype)
         assert rel_fro(got, want) <= TOL[dtype], dtype
 
@@ -147,8 +152,15 @@ def test_precision_workload_full_size(P):
 def test_errors(P, sphere4096):
     _, G = sphere4096
     X = np.zeros((4096, 2))
+    G32 = P.H2Matrix(sphere_points(1000, 3), q=3, precisions=("f32",))
     with pytest.raises(P.H2Error) as e:
-        G.matmul(X, X.copy(), dtype="bf16")
+        G32.matmul(np.zeros((1000, 2)), np.zeros((1000, 2)), dtype="bf16")
+    assert e.value.code == P.H2_E_UNSUPPORTED
+    with pytest.raises(P.H2Error) as e:
+        G.matmul_transposed(X, X.copy(), dtype="bf16")
+    assert e.value.code == P.H2_E_UNSUPPORTED
+    with pytest.raises(P.H2Error) as e:
+        P.h2_build(sphere_points(1000, 3), q=5, precisions=("bf16",))
     assert e.value.code == P.H2_E_UNSUPPORTED
     with pytest.raises(P.H2Error) as e:
         G.matmul(X, X.copy(), dtype=7)
