@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <new>
 #include <string>
 #include <vector>
@@ -157,6 +158,8 @@ int h2_build(const h2_build_params* params, const double* pts, int64_t n, h2_mat
     int64_t nl = 0;
     for (int64_t c = 0; c < A->nc; ++c) nl += A->T.is_leaf((int32_t)c);
     A->n_leaves = nl;
+    const char* fs = getenv("H2_FORCE_SIMT");
+    A->force_simt = fs && fs[0] == '1';
     rc = h2::build_device(A, hp, params->precisions, st);
     if (rc) {
         free_matrix(A);
@@ -184,12 +187,14 @@ int h2_info(const h2_matrix* A, h2_info_t* info) {
     info->q = A->q;
     info->bytes_f64 = A->f64.bytes;
     info->bytes_f32 = A->f32.built ? A->f32.bytes : 0;
-    info->bytes_bf16 = A->tc.built ? A->tc.bytes : 0;
+    info->bytes_bf16 = A->tc.has_bf16 ? A->tc.bytes : 0;
     const double k = (double)A->k;
     // leaf forward + leaf backward, up + down transfers, coupling, nearfield, shift
     info->flops_per_col = 2.0 * 2.0 * (double)A->n * k + 2.0 * 2.0 * (double)(A->nc - 1) * k * k +
                           2.0 * (double)A->n_adm * k * k + 2.0 * (double)A->nnz_near + 2.0 * (double)A->n;
     info->launches = A->launches_per_product;
+    // tensor-core chain: + packing of X, x̂ and ŷ, + zeroing of clusters without couplings
+    info->launches_tc = A->tc.built ? A->launches_per_product + 3 + (A->tc.c_nzero > 0 ? 1 : 0) : 0;
     return 0;
 }
 

@@ -332,28 +332,31 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
         A->f32.bytes = A->f64.bytes / 2;
         A->f32.built = true;
     }
-    if (precisions & (1u << H2_BF16)) {
+    const bool want_bf16 = (precisions & (1u << H2_BF16)) != 0;
+    const bool want_tf32 = (precisions & (1u << H2_F32)) != 0 && k <= 64;
+    if (want_bf16 && k > 64) {
+        set_error("the BF16 tensor-core product supports q <= 4 (k <= 64)");
+        return H2_E_UNSUPPORTED;
+    }
+    if (want_bf16 || want_tf32) {
         if (!A->f32.built) {
-            // the BF16 product runs its transfer passes on the FP32 copies of V and E
+            // the tensor-core products run their transfer passes on the FP32 copies of V and E
             if ((rc = cast_copy(A, (const double*)A->f64.V, &A->f32.V, (int64_t)n * k, st))) return rc;
             if ((rc = cast_copy(A, (const double*)A->f64.E, &A->f32.E, nc * k * k, st))) return rc;
         }
-        if ((rc = build_tc_bf16(A, st))) return rc;
+        if ((rc = build_tc(A, want_bf16, want_tf32, st))) return rc;
     }
     H2_CUDA_TRY(cudaStreamSynchronize(st));
     return 0;
 }
 
-// BF16 core-matrix copies of S, V and G, and the schedules of the two tcgen05
-// kernels (coupling over row clusters, leaf phase over row leaves).
-int build_tc_bf16(h2_matrix* A, cudaStream_t st) {
+// Core-matrix copies of S, V and G for the tensor cores (BF16 and/or FP32 for
+// the split-TF32 product), and the schedules of the two tcgen05 kernels
+// (coupling over row clusters, leaf phase over row leaves).
+int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     const Tree& T = A->T;
     const int k = A->k;
     const int KP = round16(k), NP = round16(k);
-    if (KP > 64) {
-        set_error("the BF16 tensor-core product supports q <= 4 (k <= 64)");
-        return H2_E_UNSUPPORTED;
-    }
     TcData& D = A->tc;
     D.KP = KP;
     D.NP = NP;
@@ -398,16 +401,22 @@ int build_tc_bf16(h2_matrix* A, cudaStream_t st) {
         }
     }
     const int64_t nG = (int64_t)tiles.size() - nS - nV;
-    D.bytes = off;
+    D.bytes = off;  // BF16 bytes; the FP32 copy is twice that
     int rc = 0;
-    void* pm = nullptr;
-    if ((rc = device_alloc(A, &pm, (size_t)std::max<int64_t>(off, 128)))) return rc;
-    D.mat = (uint8_t*)pm;
     TcPackTile* d_tiles = nullptr;
     if ((rc = upload(A, &d_tiles, tiles, st))) return rc;
-    if ((rc = launch_pack_tiles(d_tiles, nS, (const double*)A->f64.S, D.mat, st))) return rc;
-    if ((rc = launch_pack_tiles(d_tiles + nS, nV, (const double*)A->f64.V, D.mat, st))) return rc;
-    if ((rc = launch_pack_tiles(d_tiles + nS + nV, nG, (const double*)A->f64.Near, D.mat, st))) return rc;
+    for (int es = 2; es <= 4; es += 2) {
+        if ((es == 2 && !bf16) || (es == 4 && !tf32)) continue;
+        void* pm = nullptr;
+        if ((rc = device_alloc(A, &pm, (size_t)std::max<int64_t>(off * (es / 2), 128)))) return rc;
+        uint8_t* dst = (uint8_t*)pm;
+        if ((rc = launch_pack_tiles(d_tiles, nS, (const double*)A->f64.S, dst, es, st))) return rc;
+        if ((rc = launch_pack_tiles(d_tiles + nS, nV, (const double*)A->f64.V, dst, es, st))) return rc;
+        if ((rc = launch_pack_tiles(d_tiles + nS + nV, nG, (const double*)A->f64.Near, dst, es, st))) return rc;
+        if (es == 2) D.mat = dst; else D.mat32 = dst;
+    }
+    D.has_bf16 = bf16;
+    D.has_tf32 = tf32;
 
     // ---- coupling schedule: outputs = clusters with at least one admissible block ----
     std::vector<int32_t> c_tptr(nc + 1), c_aid(A->n_adm), c_asrc(A->n_adm, 0), c_kp(A->n_adm, KP), c_work, c_zero;

@@ -97,14 +97,17 @@ struct TcGemmParams {
     double alpha, sigma;
     int overwrite;
     int* err;
+    int a_stage_bytes, nstages;  // filled by launch_tc_gemm
 };
 
 // BF16 tensor-core copy of the matrix data and the schedules of its kernels.
 struct TcData {
     bool built = false;
     int KP = 0, NP = 0;
-    uint8_t* mat = nullptr;  // core-matrix tiles: S (list order), V (leaf order), G (near order)
+    uint8_t* mat = nullptr;    // BF16 core-matrix tiles: S (list order), V (leaf order), G (near order)
+    uint8_t* mat32 = nullptr;  // the same tiles in FP32 (offsets ×2), for the 3xTF32 product
     int64_t bytes = 0;
+    bool has_bf16 = false, has_tf32 = false;
     // coupling: outputs are clusters
     int32_t* c_work = nullptr;
     int c_nwork = 0;
@@ -185,6 +188,7 @@ struct h2_matrix {
     h2::Workspace ws;
     h2::Timing timing;
     int32_t launches_per_product = 0;
+    bool force_simt = false;  // H2_FORCE_SIMT=1 at build: FP32 product on the CUDA cores only
     std::vector<void*> allocations;
 };
 
@@ -209,12 +213,13 @@ int matmul_in_scratch(h2_matrix* A, double alpha, const double* X, int64_t ldx, 
 
 // tcgen05 BF16 kernels (h2_tc.cu)
 int tc_smem_bytes();
-int launch_tc_gemm(int mode, const TcGemmParams& p, int grid, cudaStream_t st);
-int launch_pack_tiles(const TcPackTile* tiles, int64_t count, const double* src, uint8_t* dst, cudaStream_t st);
+int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st);
+int launch_pack_tiles(const TcPackTile* tiles, int64_t count, const double* src, uint8_t* dst, int es,
+                      cudaStream_t st);
 int launch_pack_act(const float* src, int64_t ld, int ids, const int32_t* base, const int32_t* kdim, int kdim_fixed,
-                    const int64_t* koff, int kp_fixed, int mc, int R, uint8_t* dst, cudaStream_t st);
+                    const int64_t* koff, int kp_fixed, int mc, int R, uint8_t* dst, int es, cudaStream_t st);
 int launch_zero_clusters(const int32_t* ids, int count, float* yhat, int k, int ldc, int mc, cudaStream_t st);
-int build_tc_bf16(h2_matrix* A, cudaStream_t st);
+int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st);
 
 inline int round16(int x) { return (x + 15) & ~15; }
 

@@ -347,14 +347,16 @@ int ensure_workspace(h2_matrix* A, size_t bytes, cudaStream_t st) {
 }
 
 
-// BF16 product: the coupling and the leaf phase (nearfield + backward
-// transformation + shift) run on the tensor cores (h2_tc.cu); the gather, the
-// forward transformation and the transfer passes run in FP32 on the CUDA cores
-// with the FP32 copies of V and E.  Columns are processed in chunks of at most
-// 64 (128 MMA rows: high and low BF16 parts of each column).
+// Tensor-core product (KIND 0: BF16; KIND 1: FP32 on split TF32): the
+// coupling and the leaf phase (nearfield + backward transformation + shift)
+// run on the tensor cores (h2_tc.cu); the gather, the forward transformation
+// and the transfer passes run in FP32 on the CUDA cores with the FP32 copies of
+// V and E.  Columns are processed in chunks of at most 64 (128 MMA rows: the
+// high and low parts of each column).
 template <int CN>
-int run_chain_bf16(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int m,
-                   cudaStream_t st, bool overwrite) {
+int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int m,
+                 cudaStream_t st, bool overwrite) {
+    const int es = kind == 0 ? 2 : 4;
     constexpr int RM = 4, MT = 16 * RM, NT = 16 * CN;
     const TcData& D = A->tc;
     const int k = A->k, KP = D.KP;
@@ -364,7 +366,7 @@ int run_chain_bf16(h2_matrix* A, double alpha, const double* X, int64_t ldx, dou
     const float* E = (const float*)A->f32.E;
     if (*D.err_host) {
         *D.err_host = 0;
-        set_error("a previous BF16 product hit a device-side wait limit (results of that call are invalid)");
+        set_error("a previous tensor-core product hit a device-side wait limit (results of that call are invalid)");
         return H2_E_TIMEOUT;
     }
     const int grid_cap = 152;
@@ -372,7 +374,7 @@ int run_chain_bf16(h2_matrix* A, double alpha, const double* X, int64_t ldx, dou
         const int mc = std::min(64, m - c0);
         const int R = round16(2 * mc);
         const size_t bXp = align_up((size_t)n * mc * 4), bC = align_up((size_t)nc * k * mc * 4);
-        const size_t bXcm = align_up((size_t)R * D.xk_total * 2), bAct = align_up((size_t)nc * R * KP * 2);
+        const size_t bXcm = align_up((size_t)R * D.xk_total * es), bAct = align_up((size_t)nc * R * KP * es);
         int rc = ensure_workspace(A, bXp + 2 * bC + bXcm + 2 * bAct, st);
         if (rc) return rc;
         char* base = (char*)A->ws.base;
@@ -391,7 +393,7 @@ int run_chain_bf16(h2_matrix* A, double alpha, const double* X, int64_t ldx, dou
             k_gather<float><<<g, 256, 0, st>>>(X + c0, ldx, A->d_perm, n, mc, Xp);
             H2_LAUNCH_CHECK();
         }
-        if ((rc = launch_pack_act(Xp, mc, NL, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, R, Xcm, st))) return rc;
+        if ((rc = launch_pack_act(Xp, mc, NL, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, R, Xcm, es, st))) return rc;
         marks.mark();
         k_leaf_fwd<float, RM, CN><<<dim3((unsigned)NL, gy, gzk), kThreads, 0, st>>>(A->d_leaves, A->d_cl_off,
                                                                                   A->d_cl_size, V, Xp, xhat, k, mc);
@@ -404,7 +406,7 @@ int run_chain_bf16(h2_matrix* A, double alpha, const double* X, int64_t ldx, dou
                                                                                       A->d_son1, E, xhat, k, mc);
             H2_LAUNCH_CHECK();
         }
-        if ((rc = launch_pack_act(xhat, mc, (int)nc, nullptr, nullptr, k, nullptr, KP, mc, R, xcm, st))) return rc;
+        if ((rc = launch_pack_act(xhat, mc, (int)nc, nullptr, nullptr, k, nullptr, KP, mc, R, xcm, es, st))) return rc;
         marks.mark();
         if ((rc = launch_zero_clusters(D.c_zero, D.c_nzero, yhat, k, mc, mc, st))) return rc;
         TcGemmParams cp{};
@@ -422,14 +424,14 @@ int run_chain_bf16(h2_matrix* A, double alpha, const double* X, int64_t ldx, dou
         cp.act1 = xcm;
         cp.act1_koff = nullptr;
         cp.kp_fixed = KP;
-        cp.bmat = D.mat;
+        cp.bmat = kind == 0 ? D.mat : D.mat32;
         cp.R = R;
         cp.mc = mc;
         cp.yhat = yhat;
         cp.k = k;
         cp.ldc = mc;
         cp.err = D.err_dev;
-        if (cp.n_work > 0 && (rc = launch_tc_gemm(0, cp, std::min(cp.n_work, grid_cap), st))) return rc;
+        if (cp.n_work > 0 && (rc = launch_tc_gemm(0, kind, cp, std::min(cp.n_work, grid_cap), st))) return rc;
         marks.mark();
         for (int l = 1; l <= A->depth; ++l) {
             const int64_t b = A->down_ptr[l], e = A->down_ptr[l + 1];
@@ -438,7 +440,7 @@ int run_chain_bf16(h2_matrix* A, double alpha, const double* X, int64_t ldx, dou
                                                                                         A->d_parent, E, yhat, k, mc);
             H2_LAUNCH_CHECK();
         }
-        if ((rc = launch_pack_act(yhat, mc, (int)nc, nullptr, nullptr, k, nullptr, KP, mc, R, ycm, st))) return rc;
+        if ((rc = launch_pack_act(yhat, mc, (int)nc, nullptr, nullptr, k, nullptr, KP, mc, R, ycm, es, st))) return rc;
         marks.mark();
         TcGemmParams lp{};
         lp.n_work = D.l_nwork;
@@ -455,7 +457,7 @@ int run_chain_bf16(h2_matrix* A, double alpha, const double* X, int64_t ldx, dou
         lp.act1 = ycm;
         lp.act1_koff = nullptr;
         lp.kp_fixed = KP;
-        lp.bmat = D.mat;
+        lp.bmat = kind == 0 ? D.mat : D.mat32;
         lp.R = R;
         lp.mc = mc;
         lp.leaves = A->d_leaves;
@@ -470,11 +472,18 @@ int run_chain_bf16(h2_matrix* A, double alpha, const double* X, int64_t ldx, dou
         lp.sigma = A->sigma;
         lp.overwrite = overwrite ? 1 : 0;
         lp.err = D.err_dev;
-        if ((rc = launch_tc_gemm(1, lp, std::min(lp.n_work, grid_cap), st))) return rc;
+        if ((rc = launch_tc_gemm(1, kind, lp, std::min(lp.n_work, grid_cap), st))) return rc;
         marks.mark();
         if ((rc = marks.commit())) return rc;
     }
     return 0;
+}
+
+int dispatch_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                int64_t m, cudaStream_t st, bool overwrite) {
+    if (m <= 16) return run_chain_tc<1>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite);
+    if (m <= 32) return run_chain_tc<2>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite);
+    return run_chain_tc<4>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite);
 }
 
 template <typename T>
@@ -503,15 +512,15 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
     }
     if (dtype == H2_F32) {
         if (!A->f32.built) { set_error("FP32 copy not built (add 1<<H2_F32 to params->precisions)"); return H2_E_UNSUPPORTED; }
+        if (!transposed && A->tc.has_tf32 && !A->force_simt)
+            return dispatch_tc(A, 1, alpha, X, ldx, Y, ldy, m, st, overwrite);
         return dispatch_cn<float>(A, A->f32, alpha, X, ldx, Y, ldy, (int)m, st, transposed, overwrite,
                                   (float*)base, (float*)(base + bXp), (float*)(base + bXp + bC));
     }
     if (dtype == H2_BF16) {
-        if (!A->tc.built) { set_error("BF16 copy not built (add 1<<H2_BF16 to params->precisions)"); return H2_E_UNSUPPORTED; }
+        if (!A->tc.has_bf16) { set_error("BF16 copy not built (add 1<<H2_BF16 to params->precisions)"); return H2_E_UNSUPPORTED; }
         if (transposed) { set_error("the BF16 product supports A·X only (use H2_F32 or H2_F64 for Aᵀ)"); return H2_E_UNSUPPORTED; }
-        if (m <= 16) return run_chain_bf16<1>(A, alpha, X, ldx, Y, ldy, (int)m, st, overwrite);
-        if (m <= 32) return run_chain_bf16<2>(A, alpha, X, ldx, Y, ldy, (int)m, st, overwrite);
-        return run_chain_bf16<4>(A, alpha, X, ldx, Y, ldy, (int)m, st, overwrite);
+        return dispatch_tc(A, 0, alpha, X, ldx, Y, ldy, m, st, overwrite);
     }
     set_error("unsupported dtype for the product");
     return H2_E_UNSUPPORTED;

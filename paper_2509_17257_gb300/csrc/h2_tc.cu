@@ -37,11 +37,9 @@ namespace h2 {
 
 namespace {
 
-constexpr int kStages = 6;
-constexpr int kAStageBytes = 128 * 64 * 2;  // up to 128 rows × 64 contraction columns
-constexpr int kBStageBytes = 64 * 64 * 2;   // up to 64 rows × 64 contraction columns
-constexpr int kStageBytes = kAStageBytes + kBStageBytes;
-constexpr int kTcThreads = 192;
+constexpr int kMaxStages = 16;
+constexpr int kSmemBudget = 225 * 1024;  // dynamic shared memory per CTA (one CTA per SM)
+constexpr int kTcThreads = 256;
 constexpr int kAccCols = 64;                // TMEM columns per accumulator buffer
 constexpr uint32_t kSpinLimit = 1u << 25;   // bounded mbarrier waits
 
@@ -83,15 +81,27 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
-// Instruction descriptor: FP32 accumulate, BF16 A and B, both K-major.
-__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor: FP32 accumulate, A and B K-major, BF16 (KIND 0:
+// format 1 of kind::f16) or TF32 (KIND 1: format 2 of kind::tf32).
+template <int KIND>
+__device__ __forceinline__ uint32_t idesc_for(int M, int N) {
+    const uint32_t fmt = KIND == 0 ? 1u : 2u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
+template <int KIND>
+__device__ __forceinline__ void mma_issue(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (KIND == 0)
+        asm volatile(
+            "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
+                d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(
+                d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -113,9 +123,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 // Byte offset of element (row r, column c) of a core-matrix tile whose rows hold
-// kp (multiple of 8) BF16 values.
-__host__ __device__ __forceinline__ int64_t cm_off(int r, int c, int kp) {
-    return ((int64_t)(r >> 3) * (kp >> 3) + (c >> 3)) * 128 + (r & 7) * 16 + (c & 7) * 2;
+// kp values of es bytes (kp·es a multiple of 16): 8-row groups outermost, then
+// 16-byte column chunks, then the 8 rows of 16 bytes of one core matrix.
+__host__ __device__ __forceinline__ int64_t cm_off(int r, int c, int kp, int es) {
+    const int per = 16 / es;
+    return ((int64_t)(r >> 3) * (kp / per) + (c / per)) * 128 + (r & 7) * 16 + (c % per) * es;
 }
 
 }  // namespace
@@ -124,43 +136,50 @@ __host__ __device__ __forceinline__ int64_t cm_off(int r, int c, int kp) {
 // Packing kernels
 // ---------------------------------------------------------------------------
 
-// One tile per CTA: dst (np × kp core-matrix BF16) ← src (n × k row-major FP64,
-// leading dimension ld), zero padding.
+// One tile per CTA: dst (np × kp core-matrix tile, BF16 if es = 2 else FP32)
+// ← src (n × k row-major FP64, leading dimension ld), zero padding.  Tile
+// offsets are given for BF16 and scaled by es/2.
 __global__ void k_pack_tiles(const TcPackTile* __restrict__ tiles, int64_t count, const double* __restrict__ src,
-                             uint8_t* __restrict__ dst) {
+                             uint8_t* __restrict__ dst, int es) {
     for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
         const TcPackTile d = tiles[t];
+        uint8_t* base = dst + d.dst * (es / 2);
         for (int e = threadIdx.x; e < d.np * d.kp; e += blockDim.x) {
             const int r = e / d.kp, c = e % d.kp;
             const double v = (r < d.n && c < d.k) ? src[d.src + (int64_t)r * d.ld + c] : 0.0;
-            const __nv_bfloat16 b = __double2bfloat16(v);
-            *(__nv_bfloat16*)(dst + d.dst + cm_off(r, c, d.kp)) = b;
+            if (es == 2) *(__nv_bfloat16*)(base + cm_off(r, c, d.kp, 2)) = __double2bfloat16(v);
+            else *(float*)(base + cm_off(r, c, d.kp, 4)) = (float)v;
         }
     }
 }
 
-// Activation tiles: for each id (cluster or leaf), rows r = 2i + h (i < mc) of
-// column i of the FP32 source split into BF16 high (h = 0) and low (h = 1)
-// parts; columns κ < kdim(id) read src[(base(id) + κ) * ld + i]; zero padding to
-// R rows and kp(id) columns.  kp(id) = kp_fixed, or koff[id+1] - koff[id].
+// Activation tiles: for each id (cluster or leaf), rows r = 2i + h (i < mc)
+// hold column i of the FP32 source split into a high part (h = 0) and the
+// remainder (h = 1): BF16 (es = 2): bf16(x) and bf16(x - bf16(x)); TF32 (es = 4):
+// x itself (the MMA reads tf32(x)) and x - tf32(x).  Columns κ < kdim(id) read
+// src[(base(id) + κ) * ld + i]; zero padding to R rows and kp(id) columns;
+// kp(id) = kp_fixed, or koff[id+1] - koff[id].
 __global__ void k_pack_act(const float* __restrict__ src, int64_t ld, int ids, const int32_t* __restrict__ base,
                            const int32_t* __restrict__ kdim, int kdim_fixed, const int64_t* __restrict__ koff,
-                           int kp_fixed, int mc, int R, uint8_t* __restrict__ dst) {
+                           int kp_fixed, int mc, int R, uint8_t* __restrict__ dst, int es) {
     for (int id = blockIdx.x; id < ids; id += gridDim.x) {
         const int kp = koff ? (int)(koff[id + 1] - koff[id]) : kp_fixed;
-        const int64_t tile = (koff ? koff[id] : (int64_t)id * kp_fixed) * (int64_t)R * 2;
+        const int64_t tile = (koff ? koff[id] : (int64_t)id * kp_fixed) * (int64_t)R * es;
         const int kd = kdim ? kdim[id] : kdim_fixed;
         const int64_t b = base ? (int64_t)base[id] : (int64_t)id * kdim_fixed;
         for (int e = threadIdx.x; e < R * kp; e += blockDim.x) {
             const int r = e % R, c = e / R;
             const int i = r >> 1;
-            float v = 0.f;
-            if (i < mc && c < kd) {
-                const float x = src[(b + c) * ld + i];
+            float x = 0.f;
+            if (i < mc && c < kd) x = src[(b + c) * ld + i];
+            if (es == 2) {
                 const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                v = (r & 1) ? x - __bfloat162float(hi) : x;
+                const float v = (r & 1) ? x - __bfloat162float(hi) : x;
+                *(__nv_bfloat16*)(dst + tile + cm_off(r, c, kp, 2)) = __float2bfloat16_rn(v);
+            } else {
+                const float v = (r & 1) ? x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u) : x;
+                *(float*)(dst + tile + cm_off(r, c, kp, 4)) = v;
             }
-            *(__nv_bfloat16*)(dst + tile + cm_off(r, c, kp)) = __float2bfloat16_rn(v);
         }
     }
 }
@@ -168,19 +187,36 @@ __global__ void k_pack_act(const float* __restrict__ src, int64_t ld, int ids, c
 // ---------------------------------------------------------------------------
 // The tcgen05 segmented GEMM
 // ---------------------------------------------------------------------------
-template <int MODE>
+// KIND 0: BF16 operands, one MMA (kind::f16) per 16-wide K step.
+// KIND 1: FP32 data on the TF32 units with split operands ("3xTF32"): the
+//   activation rows carry x and x - tf32(x); the matrix tile is read once as
+//   tf32(S) (the MMA drops the low 13 mantissa bits) and once as the remainder
+//   S - tf32(S), which the splitter warps write next to it in shared memory, so
+//   D = x·tf32(S) + x·(S - tf32(S)) with both parts of x reaches FP32 accuracy.
+// Stage layout: [A: R rows | B: 64 rows | B_lo: 64 rows (KIND 1)], element size
+// es = 2 (KIND 0) or 4 (KIND 1), 64 contraction columns at most.
+template <int MODE, int KIND>
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p) {
+    constexpr int ES = KIND == 0 ? 2 : 4;
+    constexpr int KSTEP = KIND == 0 ? 16 : 8;  // K of one MMA instruction
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], accf_bar[2], acce_bar[2], drain_bar;
+    __shared__ __align__(8) uint64_t full_bar[kMaxStages], split_bar[kMaxStages], empty_bar[kMaxStages];
+    __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_shared;
     volatile int& abort_flag = abort_shared;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int R = p.R;
+    const int M = R <= 64 ? 64 : 128;
+    const int nst = p.nstages;
+    const int a_bytes = p.a_stage_bytes, b_bytes = 64 * 64 * ES;
+    const int stage_bytes = a_bytes + b_bytes * (KIND == 1 ? 2 : 1);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < nst; ++s) {
             mbar_init(&full_bar[s], 1);
+            mbar_init(&split_bar[s], 2);
             mbar_init(&empty_bar[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -201,17 +237,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const int R = p.R;
-    const int M = R <= 64 ? 64 : 128;
 
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- producer ----------------
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t pend_phase[kStages];
-            bool pend[kStages];
-            for (int s = 0; s < kStages; ++s) pend[s] = false;
+            uint32_t pend_phase[kMaxStages];
+            bool pend[kMaxStages];
+            for (int s = 0; s < kMaxStages; ++s) pend[s] = false;
             for (int w = blockIdx.x; w < p.n_work && !abort_flag; w += gridDim.x) {
                 const int id = p.work[w];
                 const int np = p.out_np ? p.out_np[id] : p.np_fixed;
@@ -226,20 +260,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                     const uint8_t* abase = p.t_asrc[e] ? p.act1 : p.act0;
                     const int64_t* koff = p.t_asrc[e] ? p.act1_koff : p.act0_koff;
                     const int64_t akoff = koff ? koff[aid] : (int64_t)aid * p.kp_fixed;
-                    const uint32_t abytes = (uint32_t)(R * kp * 2);
-                    const uint32_t bbytes = (uint32_t)(np * kp * 2);
-                    uint8_t* sA = smem + stage * kStageBytes;
-                    uint8_t* sB = sA + kAStageBytes;
-                    mbar_expect_tx(&full_bar[stage], abytes + bbytes);
-                    bulk_g2s(sA, abase + akoff * R * 2, abytes, &full_bar[stage]);
-                    bulk_g2s(sB, p.bmat + p.t_boff[e], bbytes, &full_bar[stage]);
+                    const uint32_t ab = (uint32_t)(R * kp * ES);
+                    const uint32_t bb = (uint32_t)(np * kp * ES);
+                    uint8_t* sA = smem + stage * stage_bytes;
+                    uint8_t* sB = sA + a_bytes;
+                    mbar_expect_tx(&full_bar[stage], ab + bb);
+                    bulk_g2s(sA, abase + akoff * R * ES, ab, &full_bar[stage]);
+                    bulk_g2s(sB, p.bmat + p.t_boff[e] * (ES / 2), bb, &full_bar[stage]);
                     pend[stage] = true;
                     pend_phase[stage] = phase;
-                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                    if (++stage == nst) { stage = 0; phase ^= 1; }
                 }
             }
-            // wait until every copy issued by this CTA has landed
-            for (int s = 0; s < kStages; ++s)
+            for (int s = 0; s < nst; ++s)
                 if (pend[s] && !mbar_wait(&full_bar[s], pend_phase[s])) atomicExch(p.err, 2);
         }
     } else if (warp == 1) {
@@ -260,39 +293,42 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(acc * kAccCols);
-                const uint32_t idesc = idesc_bf16(M, np);
+                const uint32_t idesc = idesc_for<KIND>(M, np);
                 bool first = true;
                 for (int e = p.tptr[id]; e < p.tptr[id + 1]; ++e) {
-                    if (!mbar_wait(&full_bar[stage], phase)) {
+                    if (!mbar_wait(KIND == 1 ? &split_bar[stage] : &full_bar[stage], phase)) {
                         abort_flag = 1;
                         atomicExch(p.err, 4);
                         break;
                     }
                     tc_fence_after();
                     const int kp = p.t_kp[e];
-                    const uint32_t sA = smem_u32(smem + stage * kStageBytes);
-                    const uint32_t sB = sA + kAStageBytes;
-                    const uint32_t sbo = (uint32_t)(kp >> 3) * 128;
-                    for (int kk = 0; kk < kp / 16; ++kk) {
+                    const uint32_t sA = smem_u32(smem + stage * stage_bytes);
+                    const uint32_t sB = sA + a_bytes;
+                    const uint32_t sbo = (uint32_t)(kp * ES / 16) * 128;
+                    for (int kk = 0; kk < kp / KSTEP; ++kk) {
                         const uint64_t ad = smem_desc(sA + kk * 256, 128, sbo);
                         const uint64_t bd = smem_desc(sB + kk * 256, 128, sbo);
-                        mma_bf16(d, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+                        mma_issue<KIND>(d, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+                        if (KIND == 1) {
+                            const uint64_t bl = smem_desc(sB + b_bytes + kk * 256, 128, sbo);
+                            mma_issue<KIND>(d, ad, bl, idesc, 1u);
+                        }
                     }
                     issued = true;
                     first = false;
                     mma_commit(&empty_bar[stage]);
-                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                    if (++stage == nst) { stage = 0; phase ^= 1; }
                 }
                 if (abort_flag) break;
                 mma_commit(&accf_bar[acc]);
             }
             if (issued) {
-                // all MMAs of this CTA complete before TMEM is released
                 mma_commit(&drain_bar);
                 if (!mbar_wait(&drain_bar, 0)) atomicExch(p.err, 5);
             }
         }
-    } else {
+    } else if (warp < 6) {
         // ---------------- epilogue (warps 2..5, TMEM lane quadrant warp % 4) ----------------
         const int q = warp & 3;
         int row;
@@ -321,7 +357,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                 for (int j = 0; j < 16; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 1);
                 if (writer) {
                     if (MODE == 0) {
-                        // ŷ_t[ν][c0 + i] (FP32, cluster-major [k][m])
                         float* out = p.yhat + (int64_t)id * p.k * p.ldc;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
@@ -329,7 +364,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                             if (nu < p.k) out[(int64_t)nu * p.ldc + i] = v[j];
                         }
                     } else {
-                        // leaf: Y[perm[off + pt]][col] (+)= α (D + σ X)
                         const int t = p.leaves[id];
                         const int off = p.cl_off[t], nt = p.cl_size[t];
 #pragma unroll
@@ -348,6 +382,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             tc_fence_before();
             mbar_arrive(&acce_bar[acc]);
         }
+    } else if (KIND == 1) {
+        // ---------------- splitter (warps 6, 7): B_lo = B - tf32(B) ----------------
+        const int sw = warp - 6;  // 0 or 1
+        int stage = 0;
+        uint32_t phase = 0;
+        for (int w = blockIdx.x; w < p.n_work; w += gridDim.x) {
+            const int id = p.work[w];
+            const int np = p.out_np ? p.out_np[id] : p.np_fixed;
+            bool ok = true;
+            for (int e = p.tptr[id]; e < p.tptr[id + 1]; ++e) {
+                ok = __any_sync(0xffffffffu, mbar_wait(&full_bar[stage], phase));
+                if (!ok) break;
+                const int n4 = np * p.t_kp[e] / 4;  // float4 count of the B tile
+                const float4* src = (const float4*)(smem + stage * stage_bytes + a_bytes);
+                float4* dst = (float4*)(smem + stage * stage_bytes + a_bytes + b_bytes);
+                for (int x = sw * 32 + lane; x < n4; x += 64) {
+                    float4 v = src[x], l;
+                    l.x = v.x - __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+                    l.y = v.y - __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+                    l.z = v.z - __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+                    l.w = v.w - __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+                    dst[x] = l;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&split_bar[stage]);
+                if (++stage == nst) { stage = 0; phase ^= 1; }
+            }
+            if (!ok) {
+                if (lane == 0) atomicExch(p.err, 7);
+                abort_flag = 1;
+                break;
+            }
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -365,41 +433,54 @@ __global__ void k_zero_clusters(const int32_t* __restrict__ ids, int count, floa
     }
 }
 
-int tc_smem_bytes() { return kStages * kStageBytes + 1024; }
+// Stage geometry for R activation rows and element size es: A holds R rows,
+// B (and B_lo for TF32) 64 rows, all with up to 64 contraction columns.
+void tc_stage_geometry(int R, int es, int* a_bytes, int* stage_bytes, int* nstages) {
+    const int rows = R <= 64 ? 64 : 128;  // the MMA reads M = 64 or 128 rows
+    *a_bytes = rows * 64 * es;
+    *stage_bytes = *a_bytes + 64 * 64 * es * (es == 4 ? 2 : 1);
+    *nstages = std::min(kMaxStages, (kSmemBudget - 1024) / *stage_bytes);
+}
 
-int launch_tc_gemm(int mode, const TcGemmParams& p, int grid, cudaStream_t st) {
-    static bool attr_set[2] = {false, false};
-    const int smem = tc_smem_bytes();
-    if (mode == 0) {
-        if (!attr_set[0]) {
-            H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            attr_set[0] = true;
-        }
-        k_tc_gemm<0><<<grid, kTcThreads, smem, st>>>(p);
-    } else {
-        if (!attr_set[1]) {
-            H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            attr_set[1] = true;
-        }
-        k_tc_gemm<1><<<grid, kTcThreads, smem, st>>>(p);
+template <int MODE, int KIND>
+int launch_one(const TcGemmParams& p, int grid, int smem, cudaStream_t st) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+        attr_set = true;
     }
+    k_tc_gemm<MODE, KIND><<<grid, kTcThreads, smem, st>>>(p);
     H2_LAUNCH_CHECK();
     return 0;
 }
 
-int launch_pack_tiles(const TcPackTile* tiles, int64_t count, const double* src, uint8_t* dst, cudaStream_t st) {
+int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st) {
+    int a_bytes, stage_bytes, nstages;
+    tc_stage_geometry(p.R, kind == 0 ? 2 : 4, &a_bytes, &stage_bytes, &nstages);
+    if (nstages < 2) { set_error("tensor-core stage does not fit in shared memory"); return H2_E_UNSUPPORTED; }
+    p.a_stage_bytes = a_bytes;
+    p.nstages = nstages;
+    const int smem = nstages * stage_bytes + 1024;
+    if (mode == 0 && kind == 0) return launch_one<0, 0>(p, grid, smem, st);
+    if (mode == 1 && kind == 0) return launch_one<1, 0>(p, grid, smem, st);
+    if (mode == 0 && kind == 1) return launch_one<0, 1>(p, grid, smem, st);
+    return launch_one<1, 1>(p, grid, smem, st);
+}
+
+int launch_pack_tiles(const TcPackTile* tiles, int64_t count, const double* src, uint8_t* dst, int es,
+                      cudaStream_t st) {
     if (count <= 0) return 0;
     const unsigned g = (unsigned)std::min<int64_t>(count, 152 * 16);
-    k_pack_tiles<<<g, 256, 0, st>>>(tiles, count, src, dst);
+    k_pack_tiles<<<g, 256, 0, st>>>(tiles, count, src, dst, es);
     H2_LAUNCH_CHECK();
     return 0;
 }
 
 int launch_pack_act(const float* src, int64_t ld, int ids, const int32_t* base, const int32_t* kdim, int kdim_fixed,
-                    const int64_t* koff, int kp_fixed, int mc, int R, uint8_t* dst, cudaStream_t st) {
+                    const int64_t* koff, int kp_fixed, int mc, int R, uint8_t* dst, int es, cudaStream_t st) {
     if (ids <= 0) return 0;
     const unsigned g = (unsigned)std::min(ids, 152 * 8);
-    k_pack_act<<<g, 256, 0, st>>>(src, ld, ids, base, kdim, kdim_fixed, koff, kp_fixed, mc, R, dst);
+    k_pack_act<<<g, 256, 0, st>>>(src, ld, ids, base, kdim, kdim_fixed, koff, kp_fixed, mc, R, dst, es);
     H2_LAUNCH_CHECK();
     return 0;
 }

@@ -137,6 +137,18 @@ def test_edge_cases(P, case):
         assert rel_fro(got_t, want_t) <= TOL[dtype], (case, dtype, "T")
 
 
+def test_fp32_cuda_core_path_matches_oracle(P, monkeypatch):
+    """The FP32 product on the CUDA cores (the tensor-core path is disabled with
+    H2_FORCE_SIMT=1 at build time) against the oracle."""
+    monkeypatch.setenv("H2_FORCE_SIMT", "1")
+    pts = sphere_points(3000, 9)
+    H, G = _pair(P, pts, q=3)
+    X = gaussian_rhs(3000, 20, 1)
+    Y0 = gaussian_rhs(3000, 20, 2)
+    want = O.h2mm(H, -1.25, X, Y0)
+    assert rel_fro(_gpu_apply(G, X, Y0, -1.25, "f32"), want) <= TOL["f32"]
+
+
 def test_precision_workload_full_size(P):
     """n = 65536 sphere, q = 4, m = 32: the full product against the oracle."""
     pts = sphere_points(65536, 0)
