@@ -135,16 +135,19 @@ int h2_matmul_transposed(h2_matrix* A, double alpha, const double* X, int64_t ld
  *  - Its scratch (X gathered into cluster order, x̂ and ŷ of every cluster) is a
  *    fixed array of H2_NOALLOC_SCRATCH_BYTES (32 MiB) compiled into the
  *    library, reserved on every GPU that loads it until the process exits.
- *    A product that needs more scratch, elt·(n·m + 2·n_clusters·k·m) bytes
- *    rounded up (elt = 8 for H2_F64, 4 for H2_F32), is rejected with
+ *    A product that needs more scratch, about elt·(n·m + 2·n_clusters·k·m)
+ *    bytes (elt = 8 for H2_F64, 4 for H2_F32) plus 8·n_clusters bytes per
+ *    64 columns of counters, is rejected with
  *    H2_E_UNSUPPORTED and a message giving the size; call h2_matmul or pass
  *    fewer columns per call.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) and caches it; make that first call before any
  *    stream capture.
- *  - All calls share the one array, which keeps the last call's contents;
- *    every byte a call reads is written earlier in that call.  Calls whose
- *    work overlaps on the GPU (different streams, or different matrices at the
+ *  - All calls share the one array, which keeps the last call's contents.
+ *    Each call first clears the small region of counters and flags its
+ *    transfer passes start from (a stream-ordered memset, not an allocation)
+ *    and writes every other byte before reading it.  Calls whose work
+ *    overlaps on the GPU (different streams, or different matrices at the
  *    same time) race on the array: serialise them.
  *  - Rejected while h2_timing_enable is on for A (timing records events). */
 #define H2_NOALLOC_SCRATCH_BYTES (32ull << 20)

@@ -66,7 +66,8 @@ void free_matrix(h2_matrix* A) {
     if (A->ws.base) cudaFree(A->ws.base);
     if (A->ws.stage_x) cudaFree(A->ws.stage_x);
     if (A->ws.stage_y) cudaFree(A->ws.stage_y);
-    if (A->tc.err_host) cudaFreeHost(A->tc.err_host);
+    if (A->err_host) cudaFreeHost(A->err_host);
+    if (A->sync_cnt) cudaFree(A->sync_cnt);
     delete A;
 }
 

@@ -332,6 +332,11 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
         A->f32.bytes = A->f64.bytes / 2;
         A->f32.built = true;
     }
+    if (!A->err_host) {
+        H2_CUDA_TRY(cudaHostAlloc((void**)&A->err_host, sizeof(int), cudaHostAllocMapped));
+        *A->err_host = 0;
+        H2_CUDA_TRY(cudaHostGetDevicePointer((void**)&A->err_dev, A->err_host, 0));
+    }
     const bool want_bf16 = (precisions & (1u << H2_BF16)) != 0;
     const bool want_tf32 = (precisions & (1u << H2_F32)) != 0 && k <= 64;
     if (want_bf16 && k > 64) {
@@ -486,11 +491,6 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     UP(D.leaf_base, leaf_base);
     UP(D.leaf_kdim, leaf_kdim);
 #undef UP
-    if (!D.err_host) {
-        H2_CUDA_TRY(cudaHostAlloc((void**)&D.err_host, sizeof(int), cudaHostAllocMapped));
-        *D.err_host = 0;
-        H2_CUDA_TRY(cudaHostGetDevicePointer((void**)&D.err_dev, D.err_host, 0));
-    }
     D.built = true;
     return 0;
 }

@@ -131,8 +131,17 @@ struct TcData {
     int64_t xk_total = 0;
     int32_t* leaf_base = nullptr;  // first point position of each leaf
     int32_t* leaf_kdim = nullptr;  // points of each leaf
-    int* err_host = nullptr;       // mapped pinned flag written by the kernels on a timeout
-    int* err_dev = nullptr;
+};
+
+// Inter-CTA bookkeeping of the one-launch transfer passes: arrival counters of
+// the upward pass (self-resetting), ready flags of the downward pass (equal to
+// the product's epoch once set) and its claim tickets (reset per product).
+struct SyncBufs {
+    unsigned* cnt = nullptr;
+    int* flag = nullptr;
+    unsigned* claim = nullptr;
+    int epoch = 0;
+    int* err = nullptr;
 };
 
 struct Workspace {
@@ -188,6 +197,13 @@ struct h2_matrix {
     h2::Workspace ws;
     h2::Timing timing;
     int32_t launches_per_product = 0;
+    int* err_host = nullptr;  // mapped pinned flag: a bounded device-side wait gave up
+    int* err_dev = nullptr;
+    unsigned* sync_cnt = nullptr;  // [nc × sync_tiles]
+    int* sync_flag = nullptr;      // [nc × sync_tiles]
+    unsigned* sync_claim = nullptr;// [sync_tiles]
+    int64_t sync_tiles = 0;
+    int epoch = 0;
     bool force_simt = false;  // H2_FORCE_SIMT=1 at build: FP32 product on the CUDA cores only
     std::vector<void*> allocations;
 };
@@ -205,8 +221,9 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
 int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
              const h2_cg_params* p, h2_cg_result* res);
 
-// Bytes of scratch one product needs (gathered X, x̂, ŷ), and the product run
-// in caller-provided scratch of at least that size (device X and Y).
+// Bytes of scratch one product needs (gathered X, x̂, ŷ, transfer-pass
+// bookkeeping), and the product run in caller-provided scratch of at least
+// that size (device X and Y).
 size_t product_scratch_bytes(const h2_matrix* A, int64_t m, int32_t dtype);
 int matmul_in_scratch(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
                       int64_t m, int32_t dtype, cudaStream_t st, void* scratch);

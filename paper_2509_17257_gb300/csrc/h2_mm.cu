@@ -47,9 +47,11 @@ struct Smem {
 // acc += op(A)[row0 : row0+16RM, 0:K] · B[0:K, col0 : col0+16CN]
 // op(A) = A (A is M×K row-major, leading dimension lda) or, with TA, Aᵀ
 // (A stored K×M row-major).  Rows >= M, k >= K and columns >= ncol read as 0.
-template <typename T, int RM, int CN, bool TA>
+// CGB: read B through L2 only (ld.global.cg), for data another CTA of the same
+// launch wrote.
+template <typename T, int RM, int CN, bool TA, bool CGB = false>
 __device__ __forceinline__ void mac(Acc<T, RM, CN>& acc, Smem<T, RM, CN>& sm, const T* __restrict__ A,
-                                    int64_t lda, int M, int K, int row0, const T* __restrict__ B,
+                                    int64_t lda, int M, int K, int row0, const T* B,
                                     int64_t ldb, int ncol, int col0) {
     constexpr int MT = 16 * RM, NT = 16 * CN;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -72,7 +74,8 @@ __device__ __forceinline__ void mac(Acc<T, RM, CN>& acc, Smem<T, RM, CN>& sm, co
         for (int e = tid; e < NT * kKC; e += kThreads) {
             const int c = e % NT, kk = e / NT;
             const int gc = col0 + c;
-            sm.b[kk][c] = (gc < ncol && kk < kc) ? B[(int64_t)(k0 + kk) * ldb + gc] : T(0);
+            if (CGB) sm.b[kk][c] = (gc < ncol && kk < kc) ? __ldcg(B + (int64_t)(k0 + kk) * ldb + gc) : T(0);
+            else sm.b[kk][c] = (gc < ncol && kk < kc) ? B[(int64_t)(k0 + kk) * ldb + gc] : T(0);
         }
         __syncthreads();
 #pragma unroll 4
@@ -154,6 +157,111 @@ __global__ void __launch_bounds__(kThreads) k_up(const int32_t* __restrict__ lis
     mac<T, RM, CN, true>(acc, sm, E + s0 * kk, k, k, k, row0, xhat + s0 * km, m, m, col0);
     mac<T, RM, CN, true>(acc, sm, E + s1 * kk, k, k, k, row0, xhat + s1 * km, m, m, col0);
     store_tile<T, RM, CN, false>(acc, xhat + (int64_t)t * km, m, k, m, row0, col0);
+}
+
+// ---- forward transformation in one launch (leaves and all levels) ----
+// One CTA per (leaf, column tile) computes x̂_leaf = V_tᵀ X|_t̂, then climbs:
+// the second son to finish (arrival counter of the parent) computes the
+// parent x̂_t = Σ_{t'} E_{t'}ᵀ x̂_{t'} and continues; the first one stops.  No
+// CTA ever waits.  Counters are reset by their second arrival.
+template <typename T, int RM, int CN>
+__global__ void __launch_bounds__(kThreads) k_up_fused(const int32_t* __restrict__ leaves,
+                                                       const int32_t* __restrict__ cl_off,
+                                                       const int32_t* __restrict__ cl_size,
+                                                       const int32_t* __restrict__ parent,
+                                                       const int32_t* __restrict__ son0,
+                                                       const int32_t* __restrict__ son1, const T* __restrict__ V,
+                                                       const T* __restrict__ E, const T* __restrict__ Xp, T* xhat,
+                                                       unsigned* __restrict__ cnt, int k, int m) {
+    __shared__ Smem<T, RM, CN> sm;
+    __shared__ int s_go;
+    const int tile = blockIdx.y, gy = gridDim.y;
+    const int col0 = tile * 16 * CN;
+    const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
+    int c = leaves[blockIdx.x];
+    Acc<T, RM, CN> acc;
+    acc.zero();
+    const int off = cl_off[c];
+    mac<T, RM, CN, true>(acc, sm, V + (int64_t)off * k, k, k, cl_size[c], 0, Xp + (int64_t)off * m, m, m, col0);
+    store_tile<T, RM, CN, false>(acc, xhat + (int64_t)c * km, m, k, m, 0, col0);
+    while (true) {
+        const int par = parent[c];
+        if (par < 0) break;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned old = atomicAdd(&cnt[(int64_t)par * gy + tile], 1u);
+            s_go = old == 1u;
+            if (old == 1u) cnt[(int64_t)par * gy + tile] = 0u;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        __threadfence();
+        c = par;
+        const int s0 = son0[c], s1 = son1[c];
+        acc.zero();
+        mac<T, RM, CN, true, true>(acc, sm, E + s0 * kk, k, k, k, 0, xhat + s0 * km, m, m, col0);
+        mac<T, RM, CN, true, true>(acc, sm, E + s1 * kk, k, k, k, 0, xhat + s1 * km, m, m, col0);
+        store_tile<T, RM, CN, false>(acc, xhat + (int64_t)c * km, m, k, m, 0, col0);
+    }
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---- backward transfer pass in one launch ----
+// Items are the non-root clusters in top-down level order.  A CTA claims the
+// next item (atomic ticket), waits until its parent's ŷ is final (the parent
+// has a smaller ticket, so a running CTA holds it; the wait is bounded and
+// reports a timeout through err), adds E_{t'} ŷ_parent and publishes its own
+// flag (= epoch of this product).
+template <typename T, int RM, int CN>
+__global__ void __launch_bounds__(kThreads) k_down_fused(const int32_t* __restrict__ order, int n_items,
+                                                         const int32_t* __restrict__ parent, const T* __restrict__ E,
+                                                         T* yhat, unsigned* __restrict__ claim, int* flag, int epoch,
+                                                         int* __restrict__ err, int k, int m) {
+    __shared__ Smem<T, RM, CN> sm;
+    __shared__ int s_item, s_ok;
+    const int tile = blockIdx.y, gy = gridDim.y;
+    const int col0 = tile * 16 * CN;
+    const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(&claim[tile], 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items) break;
+        const int c = order[item];
+        const int par = parent[c];
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            if (parent[par] >= 0) {  // the root's ŷ is final after the coupling phase
+                const int* f = flag + (int64_t)par * gy + tile;
+                uint32_t spins = 0;
+                while (ld_acquire(f) != epoch) {
+                    if (++spins > (1u << 24)) { ok = 0; break; }
+                    __nanosleep(32);
+                }
+            }
+            s_ok = ok;
+            if (!ok) atomicExch(err, 8);
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        Acc<T, RM, CN> acc;
+        acc.zero();
+        mac<T, RM, CN, false, true>(acc, sm, E + (int64_t)c * kk, k, k, k, 0, yhat + (int64_t)par * km, m, m, col0);
+        store_tile<T, RM, CN, true>(acc, yhat + (int64_t)c * km, m, k, m, 0, col0);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) st_release(flag + (int64_t)c * gy + tile, epoch);
+    }
 }
 
 // ---- multiplication phase, admissible part: ŷ_t = Σ_{b∈C_t} S_b x̂_s ----
@@ -268,28 +376,22 @@ struct PhaseMarks {
     }
 };
 
+// Forward transformation: leaves + upward pass (one launch when k <= 64, per
+// level otherwise).  Records the leaf-forward and upward phase marks.
 template <typename T, int RM, int CN>
-int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
-              int m, cudaStream_t st, bool transposed, bool overwrite, T* Xp, T* xhat, T* yhat) {
-    constexpr int MT = 16 * RM, NT = 16 * CN;
+int forward_pass(h2_matrix* A, const T* V, const T* E, const T* Xp, T* xhat, int m, unsigned gy, unsigned gzk,
+                 cudaStream_t st, const SyncBufs& sb, PhaseMarks& marks) {
     const int k = A->k;
-    const unsigned gy = (unsigned)((m + NT - 1) / NT);
-    const unsigned gzk = (unsigned)((k + MT - 1) / MT);
-    const unsigned gzl = (unsigned)((A->T.leaf_size + MT - 1) / MT);
-    const T* V = (const T*)D.V;
-    const T* E = (const T*)D.E;
-    const T* S = (const T*)D.S;
-    const T* G = (const T*)D.Near;
-    PhaseMarks marks(A, st);
-    marks.mark();
-    {
-        const int64_t total = A->n * m;
-        const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
-        k_gather<T><<<g, 256, 0, st>>>(X, ldx, A->d_perm, A->n, m, Xp);
-        H2_LAUNCH_CHECK();
-    }
-    marks.mark();
     const unsigned NL = (unsigned)A->leaves.size();
+    if (gzk == 1) {
+        k_up_fused<T, RM, CN><<<dim3(NL, gy), kThreads, 0, st>>>(A->d_leaves, A->d_cl_off, A->d_cl_size,
+                                                                A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat,
+                                                                sb.cnt, k, m);
+        H2_LAUNCH_CHECK();
+        marks.mark();
+        marks.mark();
+        return 0;
+    }
     k_leaf_fwd<T, RM, CN><<<dim3(NL, gy, gzk), kThreads, 0, st>>>(A->d_leaves, A->d_cl_off, A->d_cl_size, V, Xp,
                                                                   xhat, k, m);
     H2_LAUNCH_CHECK();
@@ -302,6 +404,58 @@ int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int
         H2_LAUNCH_CHECK();
     }
     marks.mark();
+    return 0;
+}
+
+// Backward transfer pass ŷ_{t'} += E_{t'} ŷ_t (one launch when k <= 64).
+template <typename T, int RM, int CN>
+int backward_pass(h2_matrix* A, const T* E, T* yhat, int m, unsigned gy, unsigned gzk, cudaStream_t st,
+                  const SyncBufs& sb) {
+    const int k = A->k;
+    const int n_items = (int)A->down_ptr[A->depth + 1];
+    if (n_items == 0) return 0;
+    if (gzk == 1) {
+        H2_CUDA_TRY(cudaMemsetAsync(sb.claim, 0, gy * sizeof(unsigned), st));
+        const unsigned g = (unsigned)std::min(n_items, 152 * 6);
+        k_down_fused<T, RM, CN><<<dim3(g, gy), kThreads, 0, st>>>(A->d_down_list, n_items, A->d_parent, E, yhat,
+                                                                 sb.claim, sb.flag, sb.epoch, sb.err, k, m);
+        H2_LAUNCH_CHECK();
+        return 0;
+    }
+    for (int l = 1; l <= A->depth; ++l) {
+        const int64_t b = A->down_ptr[l], e = A->down_ptr[l + 1];
+        if (e == b) continue;
+        k_down<T, RM, CN><<<dim3((unsigned)(e - b), gy, gzk), kThreads, 0, st>>>(A->d_down_list + b, A->d_parent, E,
+                                                                                yhat, k, m);
+        H2_LAUNCH_CHECK();
+    }
+    return 0;
+}
+
+template <typename T, int RM, int CN>
+int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
+              int m, cudaStream_t st, bool transposed, bool overwrite, T* Xp, T* xhat, T* yhat, const SyncBufs& sb) {
+    constexpr int MT = 16 * RM, NT = 16 * CN;
+    const int k = A->k;
+    const unsigned gy = (unsigned)((m + NT - 1) / NT);
+    const unsigned gzk = (unsigned)((k + MT - 1) / MT);
+    const unsigned gzl = (unsigned)((A->T.leaf_size + MT - 1) / MT);
+    const T* V = (const T*)D.V;
+    const T* E = (const T*)D.E;
+    const T* S = (const T*)D.S;
+    const T* G = (const T*)D.Near;
+    PhaseMarks marks(A, st);
+    int rc = 0;
+    marks.mark();
+    {
+        const int64_t total = A->n * m;
+        const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+        k_gather<T><<<g, 256, 0, st>>>(X, ldx, A->d_perm, A->n, m, Xp);
+        H2_LAUNCH_CHECK();
+    }
+    marks.mark();
+    const unsigned NL = (unsigned)A->leaves.size();
+    if ((rc = forward_pass<T, RM, CN>(A, V, E, Xp, xhat, m, gy, gzk, st, sb, marks))) return rc;
     if (transposed)
         k_coupling<T, RM, CN, true><<<dim3((unsigned)A->nc, gy, gzk), kThreads, 0, st>>>(
             A->d_admT_rowptr, A->d_admT_row, A->d_admT_blk, S, xhat, yhat, k, m);
@@ -310,13 +464,7 @@ int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int
             A->d_adm_rowptr, A->d_adm_col, nullptr, S, xhat, yhat, k, m);
     H2_LAUNCH_CHECK();
     marks.mark();
-    for (int l = 1; l <= A->depth; ++l) {
-        const int64_t b = A->down_ptr[l], e = A->down_ptr[l + 1];
-        if (e == b) continue;
-        k_down<T, RM, CN><<<dim3((unsigned)(e - b), gy, gzk), kThreads, 0, st>>>(A->d_down_list + b, A->d_parent,
-                                                                                E, yhat, k, m);
-        H2_LAUNCH_CHECK();
-    }
+    if ((rc = backward_pass<T, RM, CN>(A, E, yhat, m, gy, gzk, st, sb))) return rc;
     marks.mark();
     if (transposed)
         k_leaf_bwd_near<T, RM, CN, true><<<dim3(NL, gy, gzl), kThreads, 0, st>>>(
@@ -355,7 +503,7 @@ int ensure_workspace(h2_matrix* A, size_t bytes, cudaStream_t st) {
 // high and low parts of each column).
 template <int CN>
 int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int m,
-                 cudaStream_t st, bool overwrite) {
+                 cudaStream_t st, bool overwrite, const SyncBufs& sb) {
     const int es = kind == 0 ? 2 : 4;
     constexpr int RM = 4, MT = 16 * RM, NT = 16 * CN;
     const TcData& D = A->tc;
@@ -364,14 +512,12 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
     const int NL = (int)A->leaves.size();
     const float* V = (const float*)A->f32.V;
     const float* E = (const float*)A->f32.E;
-    if (*D.err_host) {
-        *D.err_host = 0;
-        set_error("a previous tensor-core product hit a device-side wait limit (results of that call are invalid)");
-        return H2_E_TIMEOUT;
-    }
+
     const int grid_cap = 152;
+    SyncBufs sbc = sb;
     for (int c0 = 0; c0 < m; c0 += 64) {
         const int mc = std::min(64, m - c0);
+        if (c0 > 0) sbc.epoch = ++A->epoch;  // every chunk's downward pass needs fresh ready flags
         const int R = round16(2 * mc);
         const size_t bXp = align_up((size_t)n * mc * 4), bC = align_up((size_t)nc * k * mc * 4);
         const size_t bXcm = align_up((size_t)R * D.xk_total * es), bAct = align_up((size_t)nc * R * KP * es);
@@ -395,19 +541,8 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         }
         if ((rc = launch_pack_act(Xp, mc, NL, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, R, Xcm, es, st))) return rc;
         marks.mark();
-        k_leaf_fwd<float, RM, CN><<<dim3((unsigned)NL, gy, gzk), kThreads, 0, st>>>(A->d_leaves, A->d_cl_off,
-                                                                                  A->d_cl_size, V, Xp, xhat, k, mc);
-        H2_LAUNCH_CHECK();
-        marks.mark();
-        for (int l = A->depth - 1; l >= 0; --l) {
-            const int64_t b = A->up_ptr[l], e = A->up_ptr[l + 1];
-            if (e == b) continue;
-            k_up<float, RM, CN><<<dim3((unsigned)(e - b), gy, gzk), kThreads, 0, st>>>(A->d_up_list + b, A->d_son0,
-                                                                                      A->d_son1, E, xhat, k, mc);
-            H2_LAUNCH_CHECK();
-        }
+        if ((rc = forward_pass<float, RM, CN>(A, V, E, Xp, xhat, mc, gy, gzk, st, sbc, marks))) return rc;
         if ((rc = launch_pack_act(xhat, mc, (int)nc, nullptr, nullptr, k, nullptr, KP, mc, R, xcm, es, st))) return rc;
-        marks.mark();
         if ((rc = launch_zero_clusters(D.c_zero, D.c_nzero, yhat, k, mc, mc, st))) return rc;
         TcGemmParams cp{};
         cp.n_work = D.c_nwork;
@@ -430,16 +565,10 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         cp.yhat = yhat;
         cp.k = k;
         cp.ldc = mc;
-        cp.err = D.err_dev;
+        cp.err = A->err_dev;
         if (cp.n_work > 0 && (rc = launch_tc_gemm(0, kind, cp, std::min(cp.n_work, grid_cap), st))) return rc;
         marks.mark();
-        for (int l = 1; l <= A->depth; ++l) {
-            const int64_t b = A->down_ptr[l], e = A->down_ptr[l + 1];
-            if (e == b) continue;
-            k_down<float, RM, CN><<<dim3((unsigned)(e - b), gy, gzk), kThreads, 0, st>>>(A->d_down_list + b,
-                                                                                        A->d_parent, E, yhat, k, mc);
-            H2_LAUNCH_CHECK();
-        }
+        if ((rc = backward_pass<float, RM, CN>(A, E, yhat, mc, gy, gzk, st, sbc))) return rc;
         if ((rc = launch_pack_act(yhat, mc, (int)nc, nullptr, nullptr, k, nullptr, KP, mc, R, ycm, es, st))) return rc;
         marks.mark();
         TcGemmParams lp{};
@@ -471,7 +600,7 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         lp.alpha = alpha;
         lp.sigma = A->sigma;
         lp.overwrite = overwrite ? 1 : 0;
-        lp.err = D.err_dev;
+        lp.err = A->err_dev;
         if ((rc = launch_tc_gemm(1, kind, lp, std::min(lp.n_work, grid_cap), st))) return rc;
         marks.mark();
         if ((rc = marks.commit())) return rc;
@@ -480,18 +609,55 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
 }
 
 int dispatch_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
-                int64_t m, cudaStream_t st, bool overwrite) {
-    if (m <= 16) return run_chain_tc<1>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite);
-    if (m <= 32) return run_chain_tc<2>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite);
-    return run_chain_tc<4>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite);
+                int64_t m, cudaStream_t st, bool overwrite, const SyncBufs& sb) {
+    if (m <= 16) return run_chain_tc<1>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb);
+    if (m <= 32) return run_chain_tc<2>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb);
+    return run_chain_tc<4>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb);
 }
 
 template <typename T>
 int dispatch_cn(h2_matrix* A, const MatData& D, double alpha, const double* X, int64_t ldx, double* Y,
-                int64_t ldy, int m, cudaStream_t st, bool transposed, bool overwrite, T* Xp, T* xhat, T* yhat) {
-    if (m <= 16) return run_chain<T, 4, 1>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat);
-    if (m <= 32) return run_chain<T, 4, 2>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat);
-    return run_chain<T, 4, 4>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat);
+                int64_t ldy, int m, cudaStream_t st, bool transposed, bool overwrite, T* Xp, T* xhat, T* yhat,
+                const SyncBufs& sb) {
+    if (m <= 16) return run_chain<T, 4, 1>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat, sb);
+    if (m <= 32) return run_chain<T, 4, 2>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat, sb);
+    return run_chain<T, 4, 4>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat, sb);
+}
+
+// Column tiles of the SIMT chain (and of the tensor-core chain, whose chunks of
+// at most 64 columns are one tile): the bookkeeping is sized per tile.
+int64_t sync_tiles_for(int64_t m) { return m <= 32 ? 1 : (m + 63) / 64; }
+
+int ensure_sync(h2_matrix* A, int64_t tiles, cudaStream_t st, SyncBufs* sb) {
+    if (A->sync_tiles < tiles) {
+        H2_CUDA_TRY(cudaStreamSynchronize(st));
+        if (A->sync_cnt) cudaFree(A->sync_cnt);
+        A->sync_cnt = nullptr;
+        A->sync_tiles = 0;
+        const size_t per = (size_t)A->nc * tiles;
+        const size_t bytes = per * (sizeof(unsigned) + sizeof(int)) + tiles * sizeof(unsigned);
+        H2_CUDA_TRY(cudaMalloc(&A->sync_cnt, bytes));
+        H2_CUDA_TRY(cudaMemsetAsync(A->sync_cnt, 0, bytes, st));
+        A->sync_flag = (int*)(A->sync_cnt + per);
+        A->sync_claim = (unsigned*)(A->sync_flag + per);
+        A->sync_tiles = tiles;
+        A->epoch = 0;
+    }
+    sb->cnt = A->sync_cnt;
+    sb->flag = A->sync_flag;
+    sb->claim = A->sync_claim;
+    sb->epoch = ++A->epoch;
+    sb->err = A->err_dev;
+    return 0;
+}
+
+int check_device_error(h2_matrix* A) {
+    if (A->err_host && *A->err_host) {
+        *A->err_host = 0;
+        set_error("a previous product hit a bounded device-side wait (its result is invalid)");
+        return H2_E_TIMEOUT;
+    }
+    return 0;
 }
 
 }  // namespace
@@ -502,25 +668,29 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
     const size_t elt = dtype == H2_F64 ? sizeof(double) : sizeof(float);
     const size_t bXp = align_up((size_t)A->n * m * elt);
     const size_t bC = align_up((size_t)A->nc * A->k * m * elt);
-    int rc = dtype == H2_BF16 ? 0 : ensure_workspace(A, bXp + 2 * bC, st);
+    int rc = check_device_error(A);
     if (rc) return rc;
+    rc = dtype == H2_BF16 ? 0 : ensure_workspace(A, bXp + 2 * bC, st);
+    if (rc) return rc;
+    SyncBufs sb;
+    if ((rc = ensure_sync(A, sync_tiles_for(m), st, &sb))) return rc;
     char* base = (char*)A->ws.base;
     if (dtype == H2_F64) {
         if (!A->f64.built) { set_error("FP64 data not built"); return H2_E_UNSUPPORTED; }
         return dispatch_cn<double>(A, A->f64, alpha, X, ldx, Y, ldy, (int)m, st, transposed, overwrite,
-                                   (double*)base, (double*)(base + bXp), (double*)(base + bXp + bC));
+                                   (double*)base, (double*)(base + bXp), (double*)(base + bXp + bC), sb);
     }
     if (dtype == H2_F32) {
         if (!A->f32.built) { set_error("FP32 copy not built (add 1<<H2_F32 to params->precisions)"); return H2_E_UNSUPPORTED; }
         if (!transposed && A->tc.has_tf32 && !A->force_simt)
-            return dispatch_tc(A, 1, alpha, X, ldx, Y, ldy, m, st, overwrite);
+            return dispatch_tc(A, 1, alpha, X, ldx, Y, ldy, m, st, overwrite, sb);
         return dispatch_cn<float>(A, A->f32, alpha, X, ldx, Y, ldy, (int)m, st, transposed, overwrite,
-                                  (float*)base, (float*)(base + bXp), (float*)(base + bXp + bC));
+                                  (float*)base, (float*)(base + bXp), (float*)(base + bXp + bC), sb);
     }
     if (dtype == H2_BF16) {
         if (!A->tc.has_bf16) { set_error("BF16 copy not built (add 1<<H2_BF16 to params->precisions)"); return H2_E_UNSUPPORTED; }
         if (transposed) { set_error("the BF16 product supports A·X only (use H2_F32 or H2_F64 for Aᵀ)"); return H2_E_UNSUPPORTED; }
-        return dispatch_tc(A, 0, alpha, X, ldx, Y, ldy, m, st, overwrite);
+        return dispatch_tc(A, 0, alpha, X, ldx, Y, ldy, m, st, overwrite, sb);
     }
     set_error("unsupported dtype for the product");
     return H2_E_UNSUPPORTED;
@@ -528,20 +698,34 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
 
 size_t product_scratch_bytes(const h2_matrix* A, int64_t m, int32_t dtype) {
     const size_t elt = dtype == H2_F64 ? sizeof(double) : sizeof(float);
-    return align_up((size_t)A->n * m * elt) + 2 * align_up((size_t)A->nc * A->k * m * elt);
+    const int64_t tiles = sync_tiles_for(m);
+    return align_up((size_t)A->n * m * elt) + 2 * align_up((size_t)A->nc * A->k * m * elt) +
+           align_up((size_t)A->nc * tiles * (sizeof(unsigned) + sizeof(int)) + tiles * sizeof(unsigned));
 }
 
 int matmul_in_scratch(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
                       int32_t dtype, cudaStream_t st, void* scratch) {
+    int rc = check_device_error(A);
+    if (rc) return rc;
     const size_t elt = dtype == H2_F64 ? sizeof(double) : sizeof(float);
     const size_t bXp = align_up((size_t)A->n * m * elt);
     const size_t bC = align_up((size_t)A->nc * A->k * m * elt);
     char* base = (char*)scratch;
+    // transfer-pass bookkeeping lives in the scratch too; it must start at zero
+    const int64_t tiles = sync_tiles_for(m);
+    const size_t per = (size_t)A->nc * tiles;
+    SyncBufs sb;
+    sb.cnt = (unsigned*)(base + bXp + 2 * bC);
+    sb.flag = (int*)(sb.cnt + per);
+    sb.claim = (unsigned*)(sb.flag + per);
+    sb.epoch = 1;
+    sb.err = A->err_dev;
+    H2_CUDA_TRY(cudaMemsetAsync(sb.cnt, 0, per * (sizeof(unsigned) + sizeof(int)) + tiles * sizeof(unsigned), st));
     if (dtype == H2_F64)
         return dispatch_cn<double>(A, A->f64, alpha, X, ldx, Y, ldy, (int)m, st, false, false, (double*)base,
-                                   (double*)(base + bXp), (double*)(base + bXp + bC));
+                                   (double*)(base + bXp), (double*)(base + bXp + bC), sb);
     return dispatch_cn<float>(A, A->f32, alpha, X, ldx, Y, ldy, (int)m, st, false, false, (float*)base,
-                              (float*)(base + bXp), (float*)(base + bXp + bC));
+                              (float*)(base + bXp), (float*)(base + bXp + bC), sb);
 }
 
 int matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,

@@ -81,8 +81,8 @@ extern "C" int h2_matmul_noalloc(h2_matrix* A, double alpha, const double* X, in
     void* scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc) return rc;
-    // Every scratch byte this product reads (gathered X, x̂ of all clusters,
-    // ŷ of all clusters) is written earlier in the same product, so nothing
-    // has to be cleared first.
+    // The product clears the counters and flags at the end of the scratch
+    // itself; every other scratch byte it reads (gathered X, x̂ and ŷ of all
+    // clusters) is written earlier in the same product.
     return h2::matmul_in_scratch(A, alpha, X, ldx, Y, ldy, m, dtype, (cudaStream_t)stream, scratch);
 }

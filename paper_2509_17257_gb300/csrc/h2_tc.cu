@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
     __shared__ __align__(8) uint64_t full_bar[kMaxStages], split_bar[kMaxStages], empty_bar[kMaxStages];
     __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], drain_bar;
     __shared__ uint32_t tmem_slot;
+    __shared__ int stage_kp[kMaxStages];
     __shared__ int abort_shared;
     volatile int& abort_flag = abort_shared;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -239,42 +240,70 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {
-            // ---------------- producer ----------------
-            int stage = 0;
-            uint32_t phase = 0;
-            uint32_t pend_phase[kMaxStages];
-            bool pend[kMaxStages];
-            for (int s = 0; s < kMaxStages; ++s) pend[s] = false;
-            for (int w = blockIdx.x; w < p.n_work && !abort_flag; w += gridDim.x) {
-                const int id = p.work[w];
-                const int np = p.out_np ? p.out_np[id] : p.np_fixed;
-                for (int e = p.tptr[id]; e < p.tptr[id + 1]; ++e) {
-                    if (!mbar_wait(&empty_bar[stage], phase ^ 1)) {
+        // ---------------- producer ----------------
+        // The warp loads the descriptors of up to 32 terms at once (one lane
+        // each); lane 0 then issues the bulk copies stage by stage.  The
+        // contraction length of every stage goes to the MMA thread through
+        // shared memory, published by the mbarrier arrive.
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t pend_mask = 0, pend_par = 0;
+        bool aborted = false;
+        for (int w = blockIdx.x; w < p.n_work && !aborted; w += gridDim.x) {
+            aborted = abort_flag != 0;
+            const int id = p.work[w];
+            const int np = p.out_np ? p.out_np[id] : p.np_fixed;
+            const int e0 = p.tptr[id], e1 = p.tptr[id + 1];
+            for (int eb = e0; eb < e1 && !aborted; eb += 32) {
+                const int e = eb + lane;
+                int kp = 0;
+                int64_t boff = 0, asrc_off = 0;
+                int asrc = 0;
+                if (e < e1) {
+                    kp = p.t_kp[e];
+                    asrc = p.t_asrc[e];
+                    const int aid = p.t_aid[e];
+                    boff = p.t_boff[e];
+                    const int64_t* koff = asrc ? p.act1_koff : p.act0_koff;
+                    asrc_off = (koff ? koff[aid] : (int64_t)aid * p.kp_fixed) * R * ES;
+                }
+                const int cnt = min(32, e1 - eb);
+                for (int j = 0; j < cnt; ++j) {
+                    const int kpj = __shfl_sync(0xffffffffu, kp, j);
+                    const int asj = __shfl_sync(0xffffffffu, asrc, j);
+                    const int64_t bj = __shfl_sync(0xffffffffu, boff, j);
+                    const int64_t aj = __shfl_sync(0xffffffffu, asrc_off, j);
+                    int bad = 0;
+                    if (lane == 0) {
+                        if (!mbar_wait(&empty_bar[stage], phase ^ 1)) {
+                            bad = 1;
+                        } else {
+                            const uint32_t ab = (uint32_t)(R * kpj * ES);
+                            const uint32_t bb = (uint32_t)(np * kpj * ES);
+                            uint8_t* sA = smem + stage * stage_bytes;
+                            uint8_t* sB = sA + a_bytes;
+                            stage_kp[stage] = kpj;
+                            mbar_expect_tx(&full_bar[stage], ab + bb);
+                            bulk_g2s(sA, (asj ? p.act1 : p.act0) + aj, ab, &full_bar[stage]);
+                            bulk_g2s(sB, p.bmat + bj * (ES / 2), bb, &full_bar[stage]);
+                            pend_mask |= 1u << stage;
+                            pend_par = (pend_par & ~(1u << stage)) | (phase << stage);
+                        }
+                    }
+                    if (__shfl_sync(0xffffffffu, bad, 0)) {
+                        if (lane == 0) atomicExch(p.err, 1);
                         abort_flag = 1;
-                        atomicExch(p.err, 1);
+                        aborted = true;
                         break;
                     }
-                    const int kp = p.t_kp[e];
-                    const int aid = p.t_aid[e];
-                    const uint8_t* abase = p.t_asrc[e] ? p.act1 : p.act0;
-                    const int64_t* koff = p.t_asrc[e] ? p.act1_koff : p.act0_koff;
-                    const int64_t akoff = koff ? koff[aid] : (int64_t)aid * p.kp_fixed;
-                    const uint32_t ab = (uint32_t)(R * kp * ES);
-                    const uint32_t bb = (uint32_t)(np * kp * ES);
-                    uint8_t* sA = smem + stage * stage_bytes;
-                    uint8_t* sB = sA + a_bytes;
-                    mbar_expect_tx(&full_bar[stage], ab + bb);
-                    bulk_g2s(sA, abase + akoff * R * ES, ab, &full_bar[stage]);
-                    bulk_g2s(sB, p.bmat + p.t_boff[e] * (ES / 2), bb, &full_bar[stage]);
-                    pend[stage] = true;
-                    pend_phase[stage] = phase;
                     if (++stage == nst) { stage = 0; phase ^= 1; }
                 }
             }
-            for (int s = 0; s < nst; ++s)
-                if (pend[s] && !mbar_wait(&full_bar[s], pend_phase[s])) atomicExch(p.err, 2);
         }
+        if (lane == 0)  // every copy issued by this CTA lands before the CTA exits
+            for (int s2 = 0; s2 < nst; ++s2)
+                if ((pend_mask >> s2) & 1u)
+                    if (!mbar_wait(&full_bar[s2], (pend_par >> s2) & 1u)) atomicExch(p.err, 2);
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
@@ -302,7 +331,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                         break;
                     }
                     tc_fence_after();
-                    const int kp = p.t_kp[e];
+                    const int kp = stage_kp[stage];
                     const uint32_t sA = smem_u32(smem + stage * stage_bytes);
                     const uint32_t sB = sA + a_bytes;
                     const uint32_t sbo = (uint32_t)(kp * ES / 16) * 128;
@@ -394,7 +423,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             for (int e = p.tptr[id]; e < p.tptr[id + 1]; ++e) {
                 ok = __any_sync(0xffffffffu, mbar_wait(&full_bar[stage], phase));
                 if (!ok) break;
-                const int n4 = np * p.t_kp[e] / 4;  // float4 count of the B tile
+                const int n4 = np * stage_kp[stage] / 4;  // float4 count of the B tile
                 const float4* src = (const float4*)(smem + stage * stage_bytes + a_bytes);
                 float4* dst = (float4*)(smem + stage * stage_bytes + a_bytes + b_bytes);
                 for (int x = sw * 32 + lane; x < n4; x += 64) {
