@@ -186,6 +186,7 @@ typedef struct h2_cg_params {
     double inner_tol;    /* relative reduction asked of each inner solve (refinement only)          */
     int32_t max_outer;   /* cap on refinement steps                                                  */
     int32_t check_every; /* convergence test every this many iterations (>= 1)                      */
+    int32_t transposed;  /* != 0: solve Aᵀ X = B (the adjoint system), products with Aᵀ                  */
     void* stream;        /* cudaStream_t                                                            */
 } h2_cg_params;
 
@@ -206,6 +207,32 @@ typedef struct h2_cg_result {
  * last iterate and `res` is filled). */
 int h2_block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
                 const h2_cg_params* params, h2_cg_result* res);
+
+/* ---- parameters of A and the adjoint -------------------------------------
+ * The method's data that a caller may differentiate: the coupling matrices
+ * S_b (Eq. (h2_admissible)), in admissible-list order (the row-cluster lists
+ * of Alg. "prepare_addeval", see h2_tree_view.adm_*), each k×k row-major
+ * S_b[ν][μ], and the diagonal shift σ. */
+
+/* Copy the FP64 coupling matrices out (S: n_adm·k·k doubles, host or device). */
+int h2_coupling_get(h2_matrix* A, double* S, void* stream);
+/* Replace the coupling matrices (FP64 in, host or device); the FP32 / BF16
+ * copies are rebuilt from them.  Synchronises the stream. */
+int h2_coupling_set(h2_matrix* A, const double* S, void* stream);
+/* Replace the diagonal shift σ. */
+int h2_shift_set(h2_matrix* A, double sigma);
+
+/* Gradients of a loss L through X = A⁻¹B, given Λ = A⁻ᵀ ∂L/∂X (from
+ * h2_block_cg with transposed = 1) and X (both n×m device FP64):
+ *   dS_b = ∂L/∂S_b = −λ̂_t x̂_sᵀ for every admissible block b = (t, s), where
+ *          λ̂ and x̂ are the forward transformations (Alg. "forward/backward",
+ *          left part) of Λ and X: since A|_{t̂×ŝ} = V_t S_b V_sᵀ + ..., the
+ *          chain rule with ∂L/∂A = −Λ Xᵀ gives V_tᵀ(−Λ Xᵀ)|_{t̂×ŝ} V_s;
+ *   dsigma = ∂L/∂σ = −<Λ, X>_F.
+ * dS (n_adm·k·k doubles, device) and dsigma (one double, host) may each be
+ * NULL.  Computed in FP64; synchronises the stream. */
+int h2_adjoint_grads(h2_matrix* A, const double* L, int64_t ldl, const double* X, int64_t ldx, int64_t m,
+                     double* dS, double* dsigma, void* stream);
 
 /* ---- host-only topology (Sec. 2 trees; Alg. "prepare_addeval" lists) ---- */
 typedef struct h2_tree h2_tree;

@@ -56,6 +56,8 @@ __all__ = [
     "kernel_matrix",
     "block_cg",
     "CGResult",
+    "adjoint_grads",
+    "set_coupling",
 ]
 
 
@@ -512,3 +514,29 @@ def block_cg(apply_A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 
             break
     rel = np.linalg.norm(R, axis=0) / bn
     return CGResult(X=X, iterations=it, col_iterations=col_it, rel_residual=rel, status=status)
+
+
+# ---------------------------------------------------------------------------
+# Adjoint: gradients of a loss through X = A⁻¹B (not in the paper; the chain
+# rule applied to the H² representation of Sec. 2)
+# ---------------------------------------------------------------------------
+def adjoint_grads(H: H2Matrix, Lam: np.ndarray, X: np.ndarray):
+    """Given Λ = A⁻ᵀ ∂L/∂X and X, return ({(t.id, s.id): ∂L/∂S_b}, ∂L/∂σ).
+
+    ∂L/∂A = −Λ Xᵀ; an admissible block is V_t S_b V_sᵀ, so
+    ∂L/∂S_b = V_tᵀ(−Λ Xᵀ)|_{t̂×ŝ} V_s = −λ̂_t x̂_sᵀ with λ̂, x̂ the forward
+    transformations of Λ and X; σ enters as σI, so ∂L/∂σ = −<Λ, X>_F.
+    """
+    Lam = np.asarray(Lam, dtype=np.float64).reshape(H.n, -1)
+    X = np.asarray(X, dtype=np.float64).reshape(H.n, -1)
+    lhat, xhat = {}, {}
+    _forward(H, H.root, Lam, lhat)
+    _forward(H, H.root, X, xhat)
+    dS = {(b.t.id, b.s.id): -(lhat[b.t.id] @ xhat[b.s.id].T) for b in H.adm}
+    return dS, -float(np.sum(Lam * X))
+
+
+def set_coupling(H: H2Matrix, S_by_pair: dict):
+    """Replace the coupling matrices S_b, keyed by (t.id, s.id)."""
+    for b in H.adm:
+        b.S = np.array(S_by_pair[(b.t.id, b.s.id)], dtype=np.float64)

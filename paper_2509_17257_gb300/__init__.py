@@ -22,7 +22,11 @@ from .h2 import (  # noqa: F401
     H2Matrix,
     LIB_PATH,
     SolveResult,
+    h2_adjoint_grads,
     h2_block_cg,
+    h2_coupling_get,
+    h2_coupling_set,
+    h2_shift_set,
     h2_build,
     h2_free,
     h2_info,
@@ -35,3 +39,4 @@ from .h2 import (  # noqa: F401
     h2_tree_build,
     lib,
 )
+from .autograd import H2Solve, h2_solve  # noqa: E402,F401

@@ -194,8 +194,9 @@ int h2_info(const h2_matrix* A, h2_info_t* info) {
     info->flops_per_col = 2.0 * 2.0 * (double)A->n * k + 2.0 * 2.0 * (double)(A->nc - 1) * k * k +
                           2.0 * (double)A->n_adm * k * k + 2.0 * (double)A->nnz_near + 2.0 * (double)A->n;
     info->launches = A->launches_per_product;
-    // tensor-core chain: + packing of X, x̂ and ŷ, + zeroing of clusters without couplings
-    info->launches_tc = A->tc.built ? A->launches_per_product + 3 + (A->tc.c_nzero > 0 ? 1 : 0) : 0;
+    // tensor-core chain: + packing of X, x̂ and ŷ, + the scatter into Y, + zeroing of clusters without couplings
+    // (gather, pack X, forward, pack x̂, coupling, downward, pack ŷ, leaf, scatter)
+    info->launches_tc = A->tc.built ? (A->down_ptr.back() > 0 ? 9 : 8) + (A->tc.c_nzero > 0 ? 1 : 0) : 0;
     return 0;
 }
 

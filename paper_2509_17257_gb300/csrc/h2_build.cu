@@ -137,6 +137,17 @@ __global__ void k_cast_f32(const double* __restrict__ in, float* __restrict__ ou
         out[i] = (float)in[i];
 }
 
+}  // namespace
+
+int cast_f32(const double* src, float* dst, int64_t count, cudaStream_t st) {
+    if (count <= 0) return 0;
+    k_cast_f32<<<1216, 256, 0, st>>>(src, dst, count);
+    H2_LAUNCH_CHECK();
+    return 0;
+}
+
+namespace {
+
 template <typename T>
 int upload(h2_matrix* A, T** dst, const std::vector<T>& src, cudaStream_t st) {
     void* p = nullptr;
@@ -190,10 +201,15 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
     }
     A->up_ptr[L + 1] = (int64_t)up_list.size();
     A->down_ptr[L + 1] = (int64_t)down_list.size();
-    A->launches_per_product = 4;  // gather, leaf forward, coupling, leaf backward
-    for (int l = 0; l <= L; ++l) {
-        A->launches_per_product += A->up_ptr[l + 1] > A->up_ptr[l];
-        A->launches_per_product += A->down_ptr[l + 1] > A->down_ptr[l];
+    if (k <= 64) {
+        // gather, forward transformation (one launch), coupling, downward pass (one launch), leaf phase
+        A->launches_per_product = A->down_ptr[L + 1] > 0 ? 5 : 4;
+    } else {
+        A->launches_per_product = 4;  // gather, leaf forward, coupling, leaf backward, + one launch per level
+        for (int l = 0; l <= L; ++l) {
+            A->launches_per_product += A->up_ptr[l + 1] > A->up_ptr[l];
+            A->launches_per_product += A->down_ptr[l + 1] > A->down_ptr[l];
+        }
     }
     A->leaves.clear();
     std::vector<int32_t> leaf_pos(nc, -1);
@@ -410,6 +426,8 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     int rc = 0;
     TcPackTile* d_tiles = nullptr;
     if ((rc = upload(A, &d_tiles, tiles, st))) return rc;
+    D.d_tiles = d_tiles;
+    D.n_s_tiles = nS;
     for (int es = 2; es <= 4; es += 2) {
         if ((es == 2 && !bf16) || (es == 4 && !tf32)) continue;
         void* pm = nullptr;

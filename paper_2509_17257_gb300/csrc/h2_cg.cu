@@ -227,6 +227,7 @@ struct Solver {
     cudaStream_t st;
     int64_t n;
     int m;
+    bool trans = false;  // products with Aᵀ (adjoint solve)
     CgDev d{};
     double *R = nullptr, *P = nullptr, *AP = nullptr;
     int* h_summary = nullptr;  // pinned
@@ -278,7 +279,7 @@ struct Solver {
         k_copy2d<<<copy_grid(), 256, 0, st>>>(B, ldb, R, m, n, m);
         H2_LAUNCH_CHECK();
         ++h2mm_calls;
-        return matmul_device(A, -1.0, X, ldx, R, m, m, dtype, st, false, false);
+        return matmul_device(A, -1.0, X, ldx, R, m, m, dtype, st, trans, false);
     }
 
     // Column-wise block CG on A_dtype X = B with R already holding B - A X.
@@ -302,7 +303,7 @@ struct Solver {
         if (h_summary[0] > 0) {
             for (it = 1; it <= max_iter; ++it) {
                 ++h2mm_calls;
-                int rc = matmul_device(A, 1.0, P, m, AP, m, m, dtype, st, false, true);
+                int rc = matmul_device(A, 1.0, P, m, AP, m, m, dtype, st, trans, true);
                 if (rc) return rc;
                 k_cg_dots<<<grid, blk, 0, st>>>(P, AP, R, m, n, m, d);
                 H2_LAUNCH_CHECK();
@@ -385,6 +386,7 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
     int status = 0;
     {
         Solver S{A, st, n, (int)m};
+        S.trans = p->transposed != 0;
         int rc = S.init();
         if (rc) return rc;
         int total_iters = 0;

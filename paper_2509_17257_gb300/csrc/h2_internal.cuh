@@ -84,7 +84,8 @@ struct TcGemmParams {
     int kp_fixed;
     const uint8_t* bmat;
     int R, mc;
-    float* yhat;
+    float* yhat;  // coupling output [cluster][k][ldc]
+    float* zp;    // leaf output in cluster order [point][ldc]
     int k, ldc;
     const int32_t* leaves;
     const int32_t* cl_off;
@@ -131,6 +132,8 @@ struct TcData {
     int64_t xk_total = 0;
     int32_t* leaf_base = nullptr;  // first point position of each leaf
     int32_t* leaf_kdim = nullptr;  // points of each leaf
+    TcPackTile* d_tiles = nullptr; // pack descriptors (S tiles first), kept to rebuild S
+    int64_t n_s_tiles = 0;
 };
 
 // Inter-CTA bookkeeping of the one-launch transfer passes: arrival counters of
@@ -239,6 +242,12 @@ int launch_zero_clusters(const int32_t* ids, int count, float* yhat, int k, int 
 int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st);
 
 inline int round16(int x) { return (x + 15) & ~15; }
+
+// Forward transformation in FP64 (gather + leaves + upward pass): xhat_out is
+// n_c × k × m; Xp_scratch holds n × m doubles.
+int forward_transform_f64(h2_matrix* A, const double* X, int64_t ldx, int64_t m, double* Xp_scratch,
+                          double* xhat_out, cudaStream_t st);
+int cast_f32(const double* src, float* dst, int64_t count, cudaStream_t st);
 
 bool is_device_pointer(const void* p);
 int device_alloc(h2_matrix* A, void** ptr, size_t bytes);

@@ -124,6 +124,22 @@ __global__ void k_gather(const double* __restrict__ X, int64_t ldx, const int32_
     }
 }
 
+// ---- scatter of the tensor-core leaf result: Y[perm[i], :] (+)= α (Z[i, :] + σ X[perm[i], :]) ----
+__global__ void k_scatter_y(const float* __restrict__ Z, int ldz, const int32_t* __restrict__ perm, int64_t n, int m,
+                            const double* __restrict__ X, int64_t ldx, double* __restrict__ Y, int64_t ldy,
+                            double alpha, double sigma, int overwrite) {
+    const int64_t total = n * m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / m;
+        const int c = (int)(e % m);
+        const int64_t g = perm[i];
+        const double z = (double)Z[i * ldz + c] + sigma * X[g * ldx + c];
+        double* y = Y + g * ldy + c;
+        if (overwrite) *y = alpha * z; else *y += alpha * z;
+    }
+}
+
 // ---- forward transformation at the leaves: x̂_t = V_tᵀ Xp|_t̂ ----
 template <typename T, int RM, int CN>
 __global__ void __launch_bounds__(kThreads) k_leaf_fwd(const int32_t* __restrict__ leaves,
@@ -351,7 +367,7 @@ struct PhaseMarks {
     bool failed = false;
     PhaseMarks(h2_matrix* a, cudaStream_t s) : A(a), st(s) {}
     void mark() {
-        if (!A->timing.on || failed) return;
+        if (!A || !A->timing.on || failed) return;
         cudaEvent_t e;
         if (!A->timing.free_events.empty()) {
             e = A->timing.free_events.back();
@@ -364,7 +380,7 @@ struct PhaseMarks {
         ev.push_back(e);
     }
     int commit() {
-        if (!A->timing.on) return 0;
+        if (!A || !A->timing.on) return 0;
         if (failed) {
             for (auto e : ev) A->timing.free_events.push_back(e);
             set_error("timing event record failed");
@@ -601,7 +617,16 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         lp.sigma = A->sigma;
         lp.overwrite = overwrite ? 1 : 0;
         lp.err = A->err_dev;
+        lp.zp = Xp;  // the gathered FP32 X is no longer read after the forward pass and its packing
+        lp.ldc = mc;
         if ((rc = launch_tc_gemm(1, kind, lp, std::min(lp.n_work, grid_cap), st))) return rc;
+        {
+            const int64_t total = n * mc;
+            const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+            k_scatter_y<<<g, 256, 0, st>>>(Xp, mc, A->d_perm, n, mc, X + c0, ldx, Y + c0, ldy, alpha, A->sigma,
+                                           overwrite ? 1 : 0);
+            H2_LAUNCH_CHECK();
+        }
         marks.mark();
         if ((rc = marks.commit())) return rc;
     }
@@ -694,6 +719,25 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
     }
     set_error("unsupported dtype for the product");
     return H2_E_UNSUPPORTED;
+}
+
+int forward_transform_f64(h2_matrix* A, const double* X, int64_t ldx, int64_t m, double* Xp, double* xhat,
+                          cudaStream_t st) {
+    if (m <= 0) return 0;
+    SyncBufs sb;
+    int rc = ensure_sync(A, sync_tiles_for(m), st, &sb);
+    if (rc) return rc;
+    const int64_t total = A->n * m;
+    const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    k_gather<double><<<g, 256, 0, st>>>(X, ldx, A->d_perm, A->n, (int)m, Xp);
+    H2_LAUNCH_CHECK();
+    PhaseMarks none(nullptr, st);
+    const double* V = (const double*)A->f64.V;
+    const double* E = (const double*)A->f64.E;
+    const unsigned gzk = (unsigned)((A->k + 63) / 64);
+    if (m <= 16) return forward_pass<double, 4, 1>(A, V, E, Xp, xhat, (int)m, (unsigned)((m + 15) / 16), gzk, st, sb, none);
+    if (m <= 32) return forward_pass<double, 4, 2>(A, V, E, Xp, xhat, (int)m, (unsigned)((m + 31) / 32), gzk, st, sb, none);
+    return forward_pass<double, 4, 4>(A, V, E, Xp, xhat, (int)m, (unsigned)((m + 63) / 64), gzk, st, sb, none);
 }
 
 size_t product_scratch_bytes(const h2_matrix* A, int64_t m, int32_t dtype) {

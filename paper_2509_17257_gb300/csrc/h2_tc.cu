@@ -393,18 +393,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                             if (nu < p.k) out[(int64_t)nu * p.ldc + i] = v[j];
                         }
                     } else {
+                        // Z in cluster order; the scatter into Y (with α, σX) is a separate
+                        // coalesced pass, so the epilogue only stores
                         const int t = p.leaves[id];
                         const int off = p.cl_off[t], nt = p.cl_size[t];
+                        float* z = p.zp + (int64_t)off * p.ldc + i;
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int pt = c0 + j;
-                            if (pt < nt) {
-                                const int64_t g = p.perm[off + pt];
-                                const double z = (double)v[j] + p.sigma * p.X[g * p.ldx + i];
-                                double* y = p.Y + g * p.ldy + i;
-                                if (p.overwrite) *y = p.alpha * z; else *y += p.alpha * z;
-                            }
-                        }
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < nt) z[(int64_t)(c0 + j) * p.ldc] = v[j];
                     }
                 }
             }

@@ -57,7 +57,8 @@ class Info(C.Structure):
 class CGParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("variant", C.c_int32),
                 ("dtype", C.c_int32), ("refine", C.c_int32), ("inner_tol", C.c_double),
-                ("max_outer", C.c_int32), ("check_every", C.c_int32), ("stream", C.c_void_p)]
+                ("max_outer", C.c_int32), ("check_every", C.c_int32), ("transposed", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class CGResult(C.Structure):
@@ -79,7 +80,8 @@ class TreeView(C.Structure):
 
 #: every symbol include/h2.h declares
 EXPORTS = ["h2_build", "h2_free", "h2_info", "h2_matmul", "h2_matmul_transposed", "h2_matmul_noalloc", "h2_block_cg",
-           "h2_timing_enable", "h2_timing_query",
+           "h2_timing_enable", "h2_timing_query", "h2_coupling_get", "h2_coupling_set", "h2_shift_set",
+           "h2_adjoint_grads",
            "h2_tree_build", "h2_tree_view_get", "h2_tree_free", "h2_last_error_string", "h2_version"]
 H2_NPHASE = 8
 PHASES = ["gather", "leaf_fwd", "up", "coupling", "down", "leaf_bwd_near"]
@@ -102,6 +104,10 @@ def lib() -> C.CDLL:
     for f in (L.h2_matmul, L.h2_matmul_transposed, L.h2_matmul_noalloc):
         f.argtypes = [vp, dbl, vp, i64, vp, i64, i64, i32, vp]
     L.h2_block_cg.argtypes = [vp, vp, i64, vp, i64, i64, C.POINTER(CGParams), C.POINTER(CGResult)]
+    L.h2_coupling_get.argtypes = [vp, vp, vp]
+    L.h2_coupling_set.argtypes = [vp, vp, vp]
+    L.h2_shift_set.argtypes = [vp, dbl]
+    L.h2_adjoint_grads.argtypes = [vp, vp, i64, vp, i64, i64, vp, C.POINTER(C.c_double), vp]
     L.h2_timing_enable.argtypes = [vp, i32]
     L.h2_timing_query.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
     L.h2_tree_build.argtypes = [C.POINTER(BuildParams), vp, i64, C.POINTER(vp)]
@@ -236,6 +242,52 @@ def h2_matmul_noalloc(handle, alpha, X, Y, dtype="f64", stream=None):
     return _mm(lib().h2_matmul_noalloc, "h2_matmul_noalloc", handle, alpha, X, Y, dtype, stream)
 
 
+def h2_coupling_get(handle, out=None):
+    """FP64 coupling matrices S_b in admissible-list order, shape (n_adm, k, k)."""
+    info = h2_info(handle)
+    shape = (info["n_adm"], info["k"], info["k"])
+    if out is None:
+        out = np.zeros(shape)
+    ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+    _check(lib().h2_coupling_get(handle, ptr, _stream_ptr(None)), "h2_coupling_get")
+    return out
+
+
+def h2_coupling_set(handle, S):
+    """Replace the coupling matrices (FP64, shape (n_adm, k, k), host or device, contiguous)."""
+    if hasattr(S, "data_ptr"):
+        if not S.is_contiguous() or S.dtype.itemsize != 8:
+            raise ValueError("S must be a contiguous float64 tensor")
+        ptr = S.data_ptr()
+    else:
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        ptr = S.ctypes.data
+    _check(lib().h2_coupling_set(handle, ptr, _stream_ptr(None)), "h2_coupling_set")
+
+
+def h2_shift_set(handle, sigma: float):
+    _check(lib().h2_shift_set(handle, float(sigma)), "h2_shift_set")
+
+
+def h2_adjoint_grads(handle, L, X, dS=None, want_dsigma=True, stream=None):
+    """(dS, dsigma) of a loss through X = A⁻¹B, given Λ = A⁻ᵀ ∂L/∂X (CUDA tensors).
+    dS has shape (n_adm, k, k) on the device; pass dS=False to skip it."""
+    import torch
+    n = h2_info(handle)["n"]
+    lp, ldl, m, kl = _ptr_ld(L, "L", n)
+    xp, ldx, mx, kx = _ptr_ld(X, "X", n)
+    if mx != m:
+        raise ValueError("L and X must have the same number of columns")
+    info = h2_info(handle)
+    if dS is None:
+        dS = torch.empty((info["n_adm"], info["k"], info["k"]), dtype=torch.float64, device=X.device)
+    dsp = dS.data_ptr() if dS is not False else None
+    ds = C.c_double(0.0)
+    _check(lib().h2_adjoint_grads(handle, lp, ldl, xp, ldx, m, dsp, C.byref(ds) if want_dsigma else None,
+                                  _stream_ptr(stream)), "h2_adjoint_grads")
+    return (dS if dS is not False else None), (ds.value if want_dsigma else None)
+
+
 @dataclass
 class SolveResult:
     status: int
@@ -252,7 +304,8 @@ class SolveResult:
 
 
 def h2_block_cg(handle, B, X, tol=1e-8, max_iter=20000, dtype="f64", refine=True, inner_tol=1e-4,
-                max_outer=30, check_every=1, variant=H2_CG_COLUMNWISE, stream=None) -> SolveResult:
+                max_outer=30, check_every=1, variant=H2_CG_COLUMNWISE, transposed=False,
+                stream=None) -> SolveResult:
     """Solve A X = B (X: initial guess in, solution out).  ``dtype`` is the
     precision of the product; with a low precision and ``refine`` the solve is
     an FP64 iterative refinement around low-precision block CG.  Returns the
@@ -266,7 +319,7 @@ def h2_block_cg(handle, B, X, tol=1e-8, max_iter=20000, dtype="f64", refine=True
     rel = np.zeros(max(m, 1), dtype=np.float64)
     dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
     prm = CGParams(tol, max_iter, variant, dt, 1 if refine else 0, inner_tol, max_outer, check_every,
-                   _stream_ptr(stream))
+                   1 if transposed else 0, _stream_ptr(stream))
     res = CGResult(0, 0, 0, 0, it.ctypes.data_as(C.POINTER(C.c_int32)), rel.ctypes.data_as(C.POINTER(C.c_double)),
                    0.0)
     rc = lib().h2_block_cg(handle, bp, ldb, xp, ldx, m, C.byref(prm), C.byref(res))
