@@ -180,10 +180,13 @@ typedef struct h2_cg_params {
     int32_t variant;     /* h2_cg_variant                                                          */
     int32_t dtype;       /* precision of the product inside block CG (vectors are always FP64)    */
     int32_t refine;      /* dtype != H2_F64 only: 1 = iterative refinement (FP64 residual B - A X
-                            outside, block CG with the dtype product inside, X += D); 0 = plain
-                            block CG with the dtype product (converges to the dtype operator's
-                            solution only)                                                         */
-    double inner_tol;    /* relative reduction asked of each inner solve (refinement only)          */
+                            outside, block CG with the dtype product inside, X += D); 2 = one block
+                            CG with the dtype product whose recurrence residuals are replaced by the
+                            FP64 residual B - A X ("reliable updates") whenever the largest active
+                            one fell by the factor inner_tol (default 0.1); 0 = plain block CG
+                            with the dtype product (converges to the dtype operator's solution)   */
+    double inner_tol;    /* refine 1: relative reduction asked of each inner solve;
+                            refine 2: residual reduction between reliable updates                  */
     int32_t max_outer;   /* cap on refinement steps                                                  */
     int32_t check_every; /* convergence test every this many iterations (>= 1)                      */
     int32_t transposed;  /* != 0: solve Aᵀ X = B (the adjoint system), products with Aᵀ                  */
@@ -193,7 +196,7 @@ typedef struct h2_cg_params {
 typedef struct h2_cg_result {
     int32_t status;         /* H2_OK, H2_E_NOCONVERGE or H2_E_BREAKDOWN (also the return value)    */
     int32_t iterations;     /* CG iterations performed (max over columns; summed over refinement)   */
-    int32_t outer_steps;    /* refinement steps (0 for a plain FP64 solve)                          */
+    int32_t outer_steps;    /* refinement steps (refine 1) or reliable updates (refine 2)          */
     int32_t h2mm_calls;     /* H² products performed                                                */
     int32_t* col_iterations;/* optional, caller-owned [m]: iteration at which column i converged    */
     double* rel_residual;   /* optional, caller-owned [m]: |b_i - A x_i|/|b_i| recomputed in FP64     */

@@ -442,42 +442,20 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     D.has_tf32 = tf32;
 
     // ---- coupling schedule: outputs = clusters with at least one admissible block ----
-    std::vector<int32_t> c_tptr(nc + 1), c_aid(A->n_adm), c_asrc(A->n_adm, 0), c_kp(A->n_adm, KP), c_work, c_zero;
-    std::vector<int64_t> c_boff(A->n_adm);
-    for (int64_t c = 0; c <= nc; ++c) c_tptr[c] = (int32_t)T.adm_rowptr[c];
-    for (int64_t j = 0; j < A->n_adm; ++j) {
-        c_aid[j] = T.adm_col[j];
-        c_boff[j] = s_off[j];
+    std::vector<int32_t> c_zero;
+    std::vector<TcItem> c_items;
+    std::vector<TcTerm> c_terms(A->n_adm);
+    for (int64_t j = 0; j < A->n_adm; ++j)
+        c_terms[j] = TcTerm{s_off[j], (int32_t)((int64_t)T.adm_col[j] * KP), (int16_t)KP, (int16_t)0};
+    for (int64_t c = 0; c < nc; ++c) {
+        const int32_t e0 = (int32_t)T.adm_rowptr[c], e1 = (int32_t)T.adm_rowptr[c + 1];
+        if (e1 > e0) c_items.push_back(TcItem{(int32_t)c, e0, e1, NP});
+        else c_zero.push_back((int32_t)c);
     }
-    for (int64_t c = 0; c < nc; ++c) (c_tptr[c + 1] > c_tptr[c] ? c_work : c_zero).push_back((int32_t)c);
-    std::stable_sort(c_work.begin(), c_work.end(),
-                     [&](int32_t a, int32_t b) { return c_tptr[a + 1] - c_tptr[a] > c_tptr[b + 1] - c_tptr[b]; });
+    // longest lists first, dealt round-robin to the CTAs
+    std::stable_sort(c_items.begin(), c_items.end(),
+                     [](const TcItem& a, const TcItem& b) { return a.e1 - a.e0 > b.e1 - b.e0; });
     // ---- leaf schedule: outputs = leaf positions; terms = V_t ŷ_t, then G_b X|_ŝ ----
-    std::vector<int32_t> l_tptr(NL + 1), l_aid, l_asrc, l_kp, l_work(NL);
-    std::vector<int64_t> l_boff, l_cost(NL, 0);
-    {
-        int64_t j = 0;
-        for (int64_t lp = 0; lp < NL; ++lp) {
-            const int32_t t = A->leaves[lp];
-            l_tptr[lp] = (int32_t)l_aid.size();
-            l_aid.push_back(t);
-            l_asrc.push_back(1);
-            l_kp.push_back(KP);
-            l_boff.push_back(v_off[lp]);
-            l_cost[lp] += (int64_t)l_np[lp] * KP;
-            for (int64_t e = T.near_rowptr[t]; e < T.near_rowptr[t + 1]; ++e, ++j) {
-                const int32_t sc = T.near_col[e];
-                l_aid.push_back(leaf_pos[sc]);
-                l_asrc.push_back(0);
-                l_kp.push_back(round16((int)T.size[sc]));
-                l_boff.push_back(g_off[j]);
-                l_cost[lp] += (int64_t)l_np[lp] * round16((int)T.size[sc]);
-            }
-        }
-        l_tptr[NL] = (int32_t)l_aid.size();
-    }
-    for (int64_t lp = 0; lp < NL; ++lp) l_work[lp] = (int32_t)lp;
-    std::stable_sort(l_work.begin(), l_work.end(), [&](int32_t a, int32_t b) { return l_cost[a] > l_cost[b]; });
     std::vector<int64_t> xkoff(NL + 1, 0);
     std::vector<int32_t> leaf_base(NL), leaf_kdim(NL);
     for (int64_t lp = 0; lp < NL; ++lp) {
@@ -486,25 +464,37 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
         leaf_kdim[lp] = (int32_t)T.size[t];
         xkoff[lp + 1] = xkoff[lp] + round16((int)T.size[t]);
     }
+    std::vector<TcItem> l_items(NL);
+    std::vector<TcTerm> l_terms;
+    std::vector<int64_t> l_cost(NL, 0);
+    {
+        int64_t j = 0;
+        for (int64_t lp = 0; lp < NL; ++lp) {
+            const int32_t t = A->leaves[lp];
+            const int32_t e0 = (int32_t)l_terms.size();
+            l_terms.push_back(TcTerm{v_off[lp], (int32_t)((int64_t)t * KP), (int16_t)KP, (int16_t)1});
+            l_cost[lp] += (int64_t)l_np[lp] * KP;
+            for (int64_t e = T.near_rowptr[t]; e < T.near_rowptr[t + 1]; ++e, ++j) {
+                const int32_t sc = T.near_col[e];
+                const int kps = round16((int)T.size[sc]);
+                l_terms.push_back(TcTerm{g_off[j], (int32_t)xkoff[leaf_pos[sc]], (int16_t)kps, (int16_t)0});
+                l_cost[lp] += (int64_t)l_np[lp] * kps;
+            }
+            l_items[lp] = TcItem{(int32_t)lp, e0, (int32_t)l_terms.size(), l_np[lp]};
+        }
+    }
+    std::stable_sort(l_items.begin(), l_items.end(),
+                     [&](const TcItem& a, const TcItem& b) { return l_cost[a.id] > l_cost[b.id]; });
     D.xk_total = xkoff[NL];
-    D.c_nwork = (int)c_work.size();
+    D.c_nitems = (int)c_items.size();
     D.c_nzero = (int)c_zero.size();
-    D.l_nwork = (int)NL;
+    D.l_nitems = (int)NL;
 #define UP(dst, src) if ((rc = upload(A, &(dst), (src), st))) return rc
-    UP(D.c_work, c_work);
-    UP(D.c_tptr, c_tptr);
-    UP(D.c_aid, c_aid);
-    UP(D.c_asrc, c_asrc);
-    UP(D.c_kp, c_kp);
-    UP(D.c_boff, c_boff);
+    UP(D.c_items, c_items);
+    UP(D.c_terms, c_terms);
     UP(D.c_zero, c_zero);
-    UP(D.l_work, l_work);
-    UP(D.l_tptr, l_tptr);
-    UP(D.l_aid, l_aid);
-    UP(D.l_asrc, l_asrc);
-    UP(D.l_kp, l_kp);
-    UP(D.l_boff, l_boff);
-    UP(D.l_np, l_np);
+    UP(D.l_items, l_items);
+    UP(D.l_terms, l_terms);
     UP(D.xkoff, xkoff);
     UP(D.leaf_base, leaf_base);
     UP(D.leaf_kdim, leaf_kdim);

@@ -184,6 +184,59 @@ __global__ void k_cg_dir(double* __restrict__ P, const double* __restrict__ R, i
         P[i * ld + col] = fma(-g, P[i * ld + col], R[i * ld + col]);
 }
 
+// Reliable update of mixed-precision CG: the recurrence residual of every
+// column is replaced by the true FP64 residual Rt = B - A X; a column whose
+// true residual meets the tolerance is frozen, one that the recurrence had
+// frozen but whose true residual does not is restarted with p = r.  One CTA
+// column group per 32 columns; the norms are reduced in fixed order.
+__global__ void __launch_bounds__(256) k_cg_reliable(const double* __restrict__ Rt, double* __restrict__ R,
+                                                     double* __restrict__ P, int64_t ld, int64_t n, int m,
+                                                     double tol, double* __restrict__ rupd, CgDev d) {
+    __shared__ double sm[1][8][kColsPerCta];
+    const int col = blockIdx.y * kColsPerCta + threadIdx.x;
+    double v[1] = {0.0};
+    if (col < m)
+        for (int64_t i = blockIdx.x * 8 + threadIdx.y; i < n; i += (int64_t)gridDim.x * 8) {
+            const double r = Rt[i * ld + col];
+            v[0] = fma(r, r, v[0]);
+        }
+    block_reduce<1>(v, sm);
+    if (threadIdx.y == 0 && col < m) d.partial[((size_t)blockIdx.x * m + col) * 2] = v[0];
+    if (!last_cta(d.ticket)) return;
+    if (threadIdx.y == 0 && col < m) {
+        double rr = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) rr += __ldcg(&d.partial[((size_t)b * m + col) * 2]);
+        const double rn = sqrt(rr);
+        d.rnorm[col] = rn;
+        rupd[col] = rn;
+        const int now = !(rn / d.bnorm[col] <= tol);
+        const int was = d.active[col];
+        // reactivated columns restart their direction (flag 2 = copy r into p)
+        d.active[col] = now ? (was ? 1 : 2) : 0;
+        if (now) atomicAdd(&d.summary[0], 1);
+        if (!isfinite(rn)) atomicOr(&d.summary[1], 1);
+    }
+    if (threadIdx.x == 0 && threadIdx.y == 0) d.ticket[blockIdx.y] = 0;
+}
+
+// R = Rt for every column; P = R for restarted columns (active flag 2 -> 1).
+__global__ void k_cg_reliable_copy(const double* __restrict__ Rt, double* __restrict__ R, double* __restrict__ P,
+                                   int64_t ld, int64_t n, int m, CgDev d) {
+    const int col = blockIdx.y * kColsPerCta + threadIdx.x;
+    if (col >= m) return;
+    const bool restart = d.active[col] == 2;
+    for (int64_t i = blockIdx.x * 8 + threadIdx.y; i < n; i += (int64_t)gridDim.x * 8) {
+        const double r = Rt[i * ld + col];
+        R[i * ld + col] = r;
+        if (restart) P[i * ld + col] = r;
+    }
+}
+
+__global__ void k_cg_reliable_flags(int m, CgDev d) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col < m && d.active[col] == 2) d.active[col] = 1;
+}
+
 // Y[:, :] = X (2-D copy with leading dimensions), also used to zero-fill when X == nullptr.
 __global__ void k_copy2d(const double* __restrict__ X, int64_t ldx, double* __restrict__ Y, int64_t ldy, int64_t n,
                          int m) {
@@ -280,6 +333,72 @@ struct Solver {
         H2_LAUNCH_CHECK();
         ++h2mm_calls;
         return matmul_device(A, -1.0, X, ldx, R, m, m, dtype, st, trans, false);
+    }
+
+    // Mixed-precision block CG with reliable updates: products in dtype, FP64
+    // vectors; the recurrence residuals are replaced by the true FP64
+    // residual B - A X whenever the largest active one has fallen by a factor
+    // delta since the last replacement, or when every column looks converged.
+    // Convergence is decided on the true residual.  R must hold B - A X.
+    int cg_reliable(int32_t dtype, const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int max_iter,
+                    int check_every, double delta, double* Rt, double* rupd, int* iters, int* updates) {
+        const dim3 blk(kColsPerCta, 8);
+        const dim3 grid(kRowBlocks, (m + kColsPerCta - 1) / kColsPerCta);
+        H2_CUDA_TRY(cudaMemsetAsync(d.summary, 0, 4 * sizeof(int), st));
+        k_cg_init<<<(m + 63) / 64, 64, 0, st>>>(B, ldb, R, m, n, m, tol, d);
+        H2_LAUNCH_CHECK();
+        k_copy2d<<<copy_grid(), 256, 0, st>>>(R, m, P, m, n, m);
+        H2_LAUNCH_CHECK();
+        H2_CUDA_TRY(cudaMemcpyAsync(rupd, d.rnorm, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        H2_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<double> rn(m), ru(m);
+        std::vector<int> act(m);
+        int it = 0, status = 0;
+        *updates = 0;
+        if (h_summary[0] > 0) {
+            for (it = 1; it <= max_iter; ++it) {
+                ++h2mm_calls;
+                int rc = matmul_device(A, 1.0, P, m, AP, m, m, dtype, st, trans, true);
+                if (rc) return rc;
+                k_cg_dots<<<grid, blk, 0, st>>>(P, AP, R, m, n, m, d);
+                H2_LAUNCH_CHECK();
+                k_cg_update<<<grid, blk, 0, st>>>(X, ldx, P, AP, R, m, n, m, tol, it, d);
+                H2_LAUNCH_CHECK();
+                k_cg_dir<<<grid, blk, 0, st>>>(P, R, m, n, m, d);
+                H2_LAUNCH_CHECK();
+                if (it % check_every != 0 && it != max_iter) continue;
+                H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                H2_CUDA_TRY(cudaMemcpyAsync(rn.data(), d.rnorm, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+                H2_CUDA_TRY(cudaMemcpyAsync(ru.data(), rupd, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+                H2_CUDA_TRY(cudaMemcpyAsync(act.data(), d.active, m * sizeof(int), cudaMemcpyDeviceToHost, st));
+                H2_CUDA_TRY(cudaStreamSynchronize(st));
+                if (h_summary[1]) { status = H2_E_BREAKDOWN; break; }
+                bool update = h_summary[0] == 0;
+                for (int i = 0; i < m && !update; ++i) update = act[i] && rn[i] < delta * ru[i];
+                if (!update) continue;
+                // true residual in FP64, then replace
+                k_copy2d<<<copy_grid(), 256, 0, st>>>(B, ldb, Rt, m, n, m);
+                H2_LAUNCH_CHECK();
+                ++h2mm_calls;
+                ++*updates;
+                if ((rc = matmul_device(A, -1.0, X, ldx, Rt, m, m, H2_F64, st, trans, false))) return rc;
+                H2_CUDA_TRY(cudaMemsetAsync(d.summary, 0, sizeof(int), st));
+                k_cg_reliable<<<grid, blk, 0, st>>>(Rt, R, P, m, n, m, tol, rupd, d);
+                H2_LAUNCH_CHECK();
+                k_cg_reliable_copy<<<grid, blk, 0, st>>>(Rt, R, P, m, n, m, d);
+                H2_LAUNCH_CHECK();
+                k_cg_reliable_flags<<<(m + 63) / 64, 64, 0, st>>>(m, d);
+                H2_LAUNCH_CHECK();
+                H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                H2_CUDA_TRY(cudaStreamSynchronize(st));
+                if (h_summary[1]) { status = H2_E_BREAKDOWN; break; }
+                if (h_summary[0] == 0) break;
+            }
+            if (it > max_iter) { it = max_iter; status = H2_E_NOCONVERGE; }
+        }
+        *iters = it;
+        return status;
     }
 
     // Column-wise block CG on A_dtype X = B with R already holding B - A X.
@@ -390,7 +509,21 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
         int rc = S.init();
         if (rc) return rc;
         int total_iters = 0;
-        if (!refine) {
+        if (refine && p->refine == 2) {
+            // reliable updates: one CG run, FP64 true residual substituted periodically
+            double* Rt = nullptr;
+            H2_CUDA_TRY(cudaMallocAsync(&Rt, ((size_t)n * m + m) * sizeof(double), st));
+            double* rupd = Rt + (size_t)n * m;
+            if ((rc = S.residual(Bd, ldbd, Xd, ldxd))) return rc;
+            int it = 0, upd = 0;
+            const double delta = p->inner_tol > 0.0 && p->inner_tol < 1.0 ? p->inner_tol : 0.1;
+            status = S.cg_reliable(inner, Bd, ldbd, Xd, ldxd, p->tol, p->max_iter, p->check_every, delta, Rt, rupd,
+                                   &it, &upd);
+            cudaFreeAsync(Rt, st);
+            if (status < 0 && status != H2_E_BREAKDOWN && status != H2_E_NOCONVERGE) return status;
+            total_iters = it;
+            res->outer_steps = upd;
+        } else if (!refine) {
             if ((rc = S.residual(Bd, ldbd, Xd, ldxd, inner))) return rc;
             int it = 0;
             status = S.cg(inner, Bd, ldbd, Xd, ldxd, p->tol, p->max_iter, p->check_every, &it);

@@ -64,24 +64,27 @@ struct TcPackTile {
     int32_t n, k, ld, np, kp;
 };
 
-// Arguments of the tcgen05 segmented GEMM (h2_tc.cu).  An output id owns the
-// terms [tptr[id], tptr[id+1]); a term multiplies an activation tile (act0 or
-// act1, id t_aid, t_kp contraction columns) with a matrix tile (bmat + t_boff).
+// One output tile of the tcgen05 segmented GEMM: output id, its terms
+// [e0, e1), and the output width np (a multiple of 16).
+struct TcItem {
+    int32_t id, e0, e1, np;
+};
+// One term: an activation tile (act0 or act1 by asrc, at akoff·R·es bytes, kp
+// contraction columns) times a matrix tile (at boff BF16-bytes, scaled by es/2).
+struct TcTerm {
+    int64_t boff;
+    int32_t akoff;
+    int16_t kp, asrc;
+};
+
+// Arguments of the tcgen05 segmented GEMM (h2_tc.cu).  Items are processed in
+// order, item w by CTA w mod gridDim.
 struct TcGemmParams {
-    int n_work;
-    const int32_t* work;
-    const int32_t* tptr;
-    const int32_t* t_aid;
-    const int32_t* t_asrc;
-    const int32_t* t_kp;
-    const int64_t* t_boff;
-    const int32_t* out_np;
-    int np_fixed;
+    int n_items;
+    const TcItem* items;
+    const TcTerm* terms;
     const uint8_t* act0;
-    const int64_t* act0_koff;
     const uint8_t* act1;
-    const int64_t* act1_koff;
-    int kp_fixed;
     const uint8_t* bmat;
     int R, mc;
     float* yhat;  // coupling output [cluster][k][ldc]
@@ -90,13 +93,6 @@ struct TcGemmParams {
     const int32_t* leaves;
     const int32_t* cl_off;
     const int32_t* cl_size;
-    const int32_t* perm;
-    const double* X;
-    int64_t ldx;
-    double* Y;
-    int64_t ldy;
-    double alpha, sigma;
-    int overwrite;
     int* err;
     int a_stage_bytes, nstages;  // filled by launch_tc_gemm
 };
@@ -109,25 +105,16 @@ struct TcData {
     uint8_t* mat32 = nullptr;  // the same tiles in FP32 (offsets ×2), for the 3xTF32 product
     int64_t bytes = 0;
     bool has_bf16 = false, has_tf32 = false;
-    // coupling: outputs are clusters
-    int32_t* c_work = nullptr;
-    int c_nwork = 0;
-    int32_t* c_tptr = nullptr;
-    int32_t* c_aid = nullptr;
-    int32_t* c_asrc = nullptr;
-    int32_t* c_kp = nullptr;
-    int64_t* c_boff = nullptr;
+    // coupling: outputs are clusters with at least one admissible block
+    TcItem* c_items = nullptr;
+    TcTerm* c_terms = nullptr;
+    int c_nitems = 0;
     int32_t* c_zero = nullptr;
     int c_nzero = 0;
     // leaf: outputs are leaf positions
-    int32_t* l_work = nullptr;
-    int l_nwork = 0;
-    int32_t* l_tptr = nullptr;
-    int32_t* l_aid = nullptr;
-    int32_t* l_asrc = nullptr;
-    int32_t* l_kp = nullptr;
-    int64_t* l_boff = nullptr;
-    int32_t* l_np = nullptr;
+    TcItem* l_items = nullptr;
+    TcTerm* l_terms = nullptr;
+    int l_nitems = 0;
     int64_t* xkoff = nullptr;   // [n_leaves+1] prefix sums of round16(|leaf|)
     int64_t xk_total = 0;
     int32_t* leaf_base = nullptr;  // first point position of each leaf

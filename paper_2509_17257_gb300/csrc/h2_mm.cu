@@ -561,20 +561,11 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         if ((rc = launch_pack_act(xhat, mc, (int)nc, nullptr, nullptr, k, nullptr, KP, mc, R, xcm, es, st))) return rc;
         if ((rc = launch_zero_clusters(D.c_zero, D.c_nzero, yhat, k, mc, mc, st))) return rc;
         TcGemmParams cp{};
-        cp.n_work = D.c_nwork;
-        cp.work = D.c_work;
-        cp.tptr = D.c_tptr;
-        cp.t_aid = D.c_aid;
-        cp.t_asrc = D.c_asrc;
-        cp.t_kp = D.c_kp;
-        cp.t_boff = D.c_boff;
-        cp.out_np = nullptr;
-        cp.np_fixed = D.NP;
+        cp.n_items = D.c_nitems;
+        cp.items = D.c_items;
+        cp.terms = D.c_terms;
         cp.act0 = xcm;
-        cp.act0_koff = nullptr;
         cp.act1 = xcm;
-        cp.act1_koff = nullptr;
-        cp.kp_fixed = KP;
         cp.bmat = kind == 0 ? D.mat : D.mat32;
         cp.R = R;
         cp.mc = mc;
@@ -582,44 +573,27 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         cp.k = k;
         cp.ldc = mc;
         cp.err = A->err_dev;
-        if (cp.n_work > 0 && (rc = launch_tc_gemm(0, kind, cp, std::min(cp.n_work, grid_cap), st))) return rc;
+        if (cp.n_items > 0 && (rc = launch_tc_gemm(0, kind, cp, std::min(cp.n_items, grid_cap), st))) return rc;
         marks.mark();
         if ((rc = backward_pass<float, RM, CN>(A, E, yhat, mc, gy, gzk, st, sbc))) return rc;
         if ((rc = launch_pack_act(yhat, mc, (int)nc, nullptr, nullptr, k, nullptr, KP, mc, R, ycm, es, st))) return rc;
         marks.mark();
         TcGemmParams lp{};
-        lp.n_work = D.l_nwork;
-        lp.work = D.l_work;
-        lp.tptr = D.l_tptr;
-        lp.t_aid = D.l_aid;
-        lp.t_asrc = D.l_asrc;
-        lp.t_kp = D.l_kp;
-        lp.t_boff = D.l_boff;
-        lp.out_np = D.l_np;
-        lp.np_fixed = 0;
+        lp.n_items = D.l_nitems;
+        lp.items = D.l_items;
+        lp.terms = D.l_terms;
         lp.act0 = Xcm;
-        lp.act0_koff = D.xkoff;
         lp.act1 = ycm;
-        lp.act1_koff = nullptr;
-        lp.kp_fixed = KP;
         lp.bmat = kind == 0 ? D.mat : D.mat32;
         lp.R = R;
         lp.mc = mc;
         lp.leaves = A->d_leaves;
         lp.cl_off = A->d_cl_off;
         lp.cl_size = A->d_cl_size;
-        lp.perm = A->d_perm;
-        lp.X = X + c0;
-        lp.ldx = ldx;
-        lp.Y = Y + c0;
-        lp.ldy = ldy;
-        lp.alpha = alpha;
-        lp.sigma = A->sigma;
-        lp.overwrite = overwrite ? 1 : 0;
         lp.err = A->err_dev;
         lp.zp = Xp;  // the gathered FP32 X is no longer read after the forward pass and its packing
         lp.ldc = mc;
-        if ((rc = launch_tc_gemm(1, kind, lp, std::min(lp.n_work, grid_cap), st))) return rc;
+        if ((rc = launch_tc_gemm(1, kind, lp, std::min(lp.n_items, grid_cap), st))) return rc;
         {
             const int64_t total = n * mc;
             const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);

@@ -199,12 +199,13 @@ template <int MODE, int KIND>
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p) {
     constexpr int ES = KIND == 0 ? 2 : 4;
     constexpr int KSTEP = KIND == 0 ? 16 : 8;  // K of one MMA instruction
+    constexpr int F_FIRST = 1, F_LAST = 2, F_END = 4;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full_bar[kMaxStages], split_bar[kMaxStages], empty_bar[kMaxStages];
     __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], drain_bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ int stage_kp[kMaxStages];
+    __shared__ int stage_kp[kMaxStages], stage_np[kMaxStages], stage_fl[kMaxStages];
     __shared__ int abort_shared;
     volatile int& abort_flag = abort_shared;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -213,6 +214,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
     const int nst = p.nstages;
     const int a_bytes = p.a_stage_bytes, b_bytes = 64 * 64 * ES;
     const int stage_bytes = a_bytes + b_bytes * (KIND == 1 ? 2 : 1);
+    const int G = gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < nst; ++s) {
@@ -241,48 +243,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
 
     if (warp == 0) {
         // ---------------- producer ----------------
-        // The warp loads the descriptors of up to 32 terms at once (one lane
-        // each); lane 0 then issues the bulk copies stage by stage.  The
-        // contraction length of every stage goes to the MMA thread through
-        // shared memory, published by the mbarrier arrive.
+        // Item and term descriptors are packed 16-byte records; the next item's
+        // descriptors are loaded while the current item's copies are issued,
+        // so no dependent global load sits between two stages.  Stage
+        // metadata (contraction length, output width, first/last/end flags)
+        // goes to the MMA thread through shared memory, published by the
+        // mbarrier arrive.
         int stage = 0;
         uint32_t phase = 0;
         uint32_t pend_mask = 0, pend_par = 0;
         bool aborted = false;
-        for (int w = blockIdx.x; w < p.n_work && !aborted; w += gridDim.x) {
+        TcItem cur = blockIdx.x < p.n_items ? p.items[blockIdx.x] : TcItem{-1, 0, 0, 0};
+        TcTerm tcur{};
+        if (cur.id >= 0 && lane < cur.e1 - cur.e0) tcur = p.terms[cur.e0 + lane];
+        for (int w = blockIdx.x; w < p.n_items && !aborted; w += G) {
             aborted = abort_flag != 0;
-            const int id = p.work[w];
-            const int np = p.out_np ? p.out_np[id] : p.np_fixed;
-            const int e0 = p.tptr[id], e1 = p.tptr[id + 1];
-            for (int eb = e0; eb < e1 && !aborted; eb += 32) {
-                const int e = eb + lane;
-                int kp = 0;
-                int64_t boff = 0, asrc_off = 0;
-                int asrc = 0;
-                if (e < e1) {
-                    kp = p.t_kp[e];
-                    asrc = p.t_asrc[e];
-                    const int aid = p.t_aid[e];
-                    boff = p.t_boff[e];
-                    const int64_t* koff = asrc ? p.act1_koff : p.act0_koff;
-                    asrc_off = (koff ? koff[aid] : (int64_t)aid * p.kp_fixed) * R * ES;
+            const int wn = w + G;
+            const TcItem nxt = wn < p.n_items ? p.items[wn] : TcItem{-1, 0, 0, 0};
+            const int nterms = cur.e1 - cur.e0;
+            for (int base = 0; base < nterms && !aborted; base += 32) {
+                TcTerm t = tcur;
+                if (base > 0) {
+                    t = TcTerm{};
+                    if (base + lane < nterms) t = p.terms[cur.e0 + base + lane];
                 }
-                const int cnt = min(32, e1 - eb);
+                const int cnt = min(32, nterms - base);
                 for (int j = 0; j < cnt; ++j) {
-                    const int kpj = __shfl_sync(0xffffffffu, kp, j);
-                    const int asj = __shfl_sync(0xffffffffu, asrc, j);
-                    const int64_t bj = __shfl_sync(0xffffffffu, boff, j);
-                    const int64_t aj = __shfl_sync(0xffffffffu, asrc_off, j);
+                    const int kpj = __shfl_sync(0xffffffffu, (int)t.kp, j);
+                    const int asj = __shfl_sync(0xffffffffu, (int)t.asrc, j);
+                    const int64_t bj = __shfl_sync(0xffffffffu, t.boff, j);
+                    const int64_t aj = (int64_t)__shfl_sync(0xffffffffu, t.akoff, j) * R * ES;
                     int bad = 0;
                     if (lane == 0) {
                         if (!mbar_wait(&empty_bar[stage], phase ^ 1)) {
                             bad = 1;
                         } else {
                             const uint32_t ab = (uint32_t)(R * kpj * ES);
-                            const uint32_t bb = (uint32_t)(np * kpj * ES);
+                            const uint32_t bb = (uint32_t)(cur.np * kpj * ES);
                             uint8_t* sA = smem + stage * stage_bytes;
                             uint8_t* sB = sA + a_bytes;
                             stage_kp[stage] = kpj;
+                            stage_np[stage] = cur.np;
+                            stage_fl[stage] = (base + j == 0 ? F_FIRST : 0) | (base + j == nterms - 1 ? F_LAST : 0);
                             mbar_expect_tx(&full_bar[stage], ab + bb);
                             bulk_g2s(sA, (asj ? p.act1 : p.act0) + aj, ab, &full_bar[stage]);
                             bulk_g2s(sB, p.bmat + bj * (ES / 2), bb, &full_bar[stage]);
@@ -299,58 +301,73 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                     if (++stage == nst) { stage = 0; phase ^= 1; }
                 }
             }
+            tcur = TcTerm{};
+            if (nxt.id >= 0 && lane < nxt.e1 - nxt.e0) tcur = p.terms[nxt.e0 + lane];
+            cur = nxt;
         }
-        if (lane == 0)  // every copy issued by this CTA lands before the CTA exits
+        if (lane == 0) {
+            // end marker for the MMA thread (and the splitters): a stage without data
+            if (mbar_wait(&empty_bar[stage], phase ^ 1)) {
+                stage_fl[stage] = F_END;
+                mbar_arrive(&full_bar[stage]);
+            } else {
+                atomicExch(p.err, 1);
+                abort_flag = 1;
+            }
+            // every copy issued by this CTA lands before the CTA exits
             for (int s2 = 0; s2 < nst; ++s2)
                 if ((pend_mask >> s2) & 1u)
                     if (!mbar_wait(&full_bar[s2], (pend_par >> s2) & 1u)) atomicExch(p.err, 2);
+        }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------- MMA issuer ----------------
+            // ---------------- MMA issuer: driven by the stage metadata ----------------
             int stage = 0;
             uint32_t phase = 0;
-            int it = 0;
-            bool issued = false;
-            for (int w = blockIdx.x; w < p.n_work && !abort_flag; w += gridDim.x, ++it) {
-                const int id = p.work[w];
-                const int np = p.out_np ? p.out_np[id] : p.np_fixed;
-                const int acc = it & 1;
-                if (!mbar_wait(&acce_bar[acc], ((it >> 1) & 1) ^ 1)) {
+            int it = 0, acc = 0;
+            bool issued = false, first = true;
+            uint32_t d = tmem, idesc = 0;
+            while (true) {
+                if (!mbar_wait(KIND == 1 ? &split_bar[stage] : &full_bar[stage], phase)) {
                     abort_flag = 1;
-                    atomicExch(p.err, 3);
+                    atomicExch(p.err, 4);
                     break;
                 }
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(acc * kAccCols);
-                const uint32_t idesc = idesc_for<KIND>(M, np);
-                bool first = true;
-                for (int e = p.tptr[id]; e < p.tptr[id + 1]; ++e) {
-                    if (!mbar_wait(KIND == 1 ? &split_bar[stage] : &full_bar[stage], phase)) {
+                const int fl = stage_fl[stage];
+                if (fl & F_END) break;
+                if (fl & F_FIRST) {
+                    acc = it & 1;
+                    if (!mbar_wait(&acce_bar[acc], ((it >> 1) & 1) ^ 1)) {
                         abort_flag = 1;
-                        atomicExch(p.err, 4);
+                        atomicExch(p.err, 3);
                         break;
                     }
-                    tc_fence_after();
-                    const int kp = stage_kp[stage];
-                    const uint32_t sA = smem_u32(smem + stage * stage_bytes);
-                    const uint32_t sB = sA + a_bytes;
-                    const uint32_t sbo = (uint32_t)(kp * ES / 16) * 128;
-                    for (int kk = 0; kk < kp / KSTEP; ++kk) {
-                        const uint64_t ad = smem_desc(sA + kk * 256, 128, sbo);
-                        const uint64_t bd = smem_desc(sB + kk * 256, 128, sbo);
-                        mma_issue<KIND>(d, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
-                        if (KIND == 1) {
-                            const uint64_t bl = smem_desc(sB + b_bytes + kk * 256, 128, sbo);
-                            mma_issue<KIND>(d, ad, bl, idesc, 1u);
-                        }
-                    }
-                    issued = true;
-                    first = false;
-                    mma_commit(&empty_bar[stage]);
-                    if (++stage == nst) { stage = 0; phase ^= 1; }
+                    d = tmem + (uint32_t)(acc * kAccCols);
+                    idesc = idesc_for<KIND>(M, stage_np[stage]);
+                    first = true;
                 }
-                if (abort_flag) break;
-                mma_commit(&accf_bar[acc]);
+                tc_fence_after();
+                const int kp = stage_kp[stage];
+                const uint32_t sA = smem_u32(smem + stage * stage_bytes);
+                const uint32_t sB = sA + a_bytes;
+                const uint32_t sbo = (uint32_t)(kp * ES / 16) * 128;
+                for (int kk = 0; kk < kp / KSTEP; ++kk) {
+                    const uint64_t ad = smem_desc(sA + kk * 256, 128, sbo);
+                    const uint64_t bd = smem_desc(sB + kk * 256, 128, sbo);
+                    mma_issue<KIND>(d, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+                    if (KIND == 1) {
+                        const uint64_t bl = smem_desc(sB + b_bytes + kk * 256, 128, sbo);
+                        mma_issue<KIND>(d, ad, bl, idesc, 1u);
+                    }
+                }
+                issued = true;
+                first = false;
+                mma_commit(&empty_bar[stage]);
+                if (fl & F_LAST) {
+                    mma_commit(&accf_bar[acc]);
+                    ++it;
+                }
+                if (++stage == nst) { stage = 0; phase ^= 1; }
             }
             if (issued) {
                 mma_commit(&drain_bar);
@@ -366,9 +383,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
         const int i = row >> 1;
         const bool writer = row >= 0 && !(row & 1) && i < p.mc;
         int it = 0;
-        for (int w = blockIdx.x; w < p.n_work; w += gridDim.x, ++it) {
-            const int id = p.work[w];
-            const int np = p.out_np ? p.out_np[id] : p.np_fixed;
+        TcItem cur = blockIdx.x < p.n_items ? p.items[blockIdx.x] : TcItem{-1, 0, 0, 0};
+        int cur_off = 0, cur_nt = 0;
+        if (MODE == 1 && cur.id >= 0) {
+            const int t = p.leaves[cur.id];
+            cur_off = p.cl_off[t];
+            cur_nt = p.cl_size[t];
+        }
+        for (int w = blockIdx.x; w < p.n_items; w += G, ++it) {
+            // the next item's descriptor (and leaf extent) load while this one waits
+            const TcItem nxt = w + G < p.n_items ? p.items[w + G] : TcItem{-1, 0, 0, 0};
+            int nxt_off = 0, nxt_nt = 0;
+            if (MODE == 1 && nxt.id >= 0) {
+                const int t = p.leaves[nxt.id];
+                nxt_off = p.cl_off[t];
+                nxt_nt = p.cl_size[t];
+            }
+            const int id = cur.id, np = cur.np;
             const int acc = it & 1;
             // warp-uniform wait: a completed phase stays completed, so any lane's
             // success is the warp's success
@@ -379,6 +410,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                 break;
             }
             tc_fence_after();
+            const int off = cur_off, nt = cur_nt;
             for (int c0 = 0; c0 < np; c0 += 16) {
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kAccCols + c0), v);
@@ -395,8 +427,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                     } else {
                         // Z in cluster order; the scatter into Y (with α, σX) is a separate
                         // coalesced pass, so the epilogue only stores
-                        const int t = p.leaves[id];
-                        const int off = p.cl_off[t], nt = p.cl_size[t];
                         float* z = p.zp + (int64_t)off * p.ldc + i;
 #pragma unroll
                         for (int j = 0; j < 16; ++j)
@@ -406,20 +436,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             }
             tc_fence_before();
             mbar_arrive(&acce_bar[acc]);
+            cur = nxt;
+            cur_off = nxt_off;
+            cur_nt = nxt_nt;
         }
     } else if (KIND == 1) {
         // ---------------- splitter (warps 6, 7): B_lo = B - tf32(B) ----------------
         const int sw = warp - 6;  // 0 or 1
         int stage = 0;
         uint32_t phase = 0;
-        for (int w = blockIdx.x; w < p.n_work; w += gridDim.x) {
-            const int id = p.work[w];
-            const int np = p.out_np ? p.out_np[id] : p.np_fixed;
-            bool ok = true;
-            for (int e = p.tptr[id]; e < p.tptr[id + 1]; ++e) {
-                ok = __any_sync(0xffffffffu, mbar_wait(&full_bar[stage], phase));
-                if (!ok) break;
-                const int n4 = np * stage_kp[stage] / 4;  // float4 count of the B tile
+        while (true) {
+            const bool ok = __any_sync(0xffffffffu, mbar_wait(&full_bar[stage], phase));
+            if (!ok) {
+                if (lane == 0) atomicExch(p.err, 7);
+                abort_flag = 1;
+                break;
+            }
+            const int fl = stage_fl[stage];
+            if (!(fl & F_END)) {
+                const int n4 = stage_np[stage] * stage_kp[stage] / 4;  // float4 count of the B tile
                 const float4* src = (const float4*)(smem + stage * stage_bytes + a_bytes);
                 float4* dst = (float4*)(smem + stage * stage_bytes + a_bytes + b_bytes);
                 for (int x = sw * 32 + lane; x < n4; x += 64) {
@@ -431,15 +466,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                     dst[x] = l;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&split_bar[stage]);
-                if (++stage == nst) { stage = 0; phase ^= 1; }
             }
-            if (!ok) {
-                if (lane == 0) atomicExch(p.err, 7);
-                abort_flag = 1;
-                break;
-            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&split_bar[stage]);
+            if (fl & F_END) break;
+            if (++stage == nst) { stage = 0; phase ^= 1; }
         }
     }
     tc_fence_before();

@@ -318,7 +318,7 @@ def h2_block_cg(handle, B, X, tol=1e-8, max_iter=20000, dtype="f64", refine=True
     it = np.zeros(max(m, 1), dtype=np.int32)
     rel = np.zeros(max(m, 1), dtype=np.float64)
     dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
-    prm = CGParams(tol, max_iter, variant, dt, 1 if refine else 0, inner_tol, max_outer, check_every,
+    prm = CGParams(tol, max_iter, variant, dt, int(refine), inner_tol, max_outer, check_every,
                    1 if transposed else 0, _stream_ptr(stream))
     res = CGResult(0, 0, 0, 0, it.ctypes.data_as(C.POINTER(C.c_int32)), rel.ctypes.data_as(C.POINTER(C.c_double)),
                    0.0)

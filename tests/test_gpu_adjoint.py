@@ -35,8 +35,8 @@ def test_adjoint_grads_match_oracle(case):
     A = O.dense_expand(H)
     B = gaussian_rhs(N, M, 1)
     Xt = gaussian_rhs(N, M, 2)
-    X = sla.cho_solve(sla.cho_factor(A), B)
-    Lam = sla.cho_solve(sla.cho_factor(A.T), 2 * (X - Xt))
+    X = np.ascontiguousarray(sla.cho_solve(sla.cho_factor(A), B))
+    Lam = np.ascontiguousarray(sla.cho_solve(sla.cho_factor(A.T), 2 * (X - Xt)))
     dS, dsig = P.h2_adjoint_grads(G.handle, torch.from_numpy(Lam).cuda(), torch.from_numpy(X).cuda())
     dS = dS.cpu().numpy()
     ref, ref_sig = O.adjoint_grads(H, Lam, X)
