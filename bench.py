@@ -301,12 +301,13 @@ def run_ours(args):
     if not args.no_solve:
         solve = {}
         B = torch.from_numpy(gaussian_rhs(n, m, cfg["rhs_seed"] + 1000 * rank + 7)).to(dev)
-        for name, inner in (("mixed_f32", "f32"), ("fp64", "f64")):
+        for name, inner, refine, itol in (("mixed_f32", "f32", 2, 0.1), ("mixed_f32_restarted", "f32", 1, 1e-4),
+                                           ("fp64", "f64", 0, 0.0)):
             Xs = torch.zeros_like(B)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            r = G.block_cg(B, Xs, tol=1e-8, max_iter=args.solve_max_iter, dtype=inner, inner_tol=1e-4,
-                           check_every=4)
+            r = G.block_cg(B, Xs, tol=1e-8, max_iter=args.solve_max_iter, dtype=inner, refine=refine,
+                           inner_tol=itol, check_every=4)
             torch.cuda.synchronize()
             solve[name] = {"seconds": round(time.perf_counter() - t0, 3), "status": r.status_name,
                            "iterations": int(r.iterations), "outer_steps": int(r.outer_steps),

@@ -308,6 +308,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
         if (lane == 0) {
             // end marker for the MMA thread (and the splitters): a stage without data
             if (mbar_wait(&empty_bar[stage], phase ^ 1)) {
+                // the stage is free, so its earlier copy has landed and been consumed;
+                // the marker moves its barrier on, so it leaves the drain set
+                pend_mask &= ~(1u << stage);
                 stage_fl[stage] = F_END;
                 mbar_arrive(&full_bar[stage]);
             } else {

@@ -53,6 +53,24 @@ def test_block_cg_matches_dense_solve(case4096, inner):
         assert res.outer_steps >= 1
 
 
+def test_mixed_solve_with_reliable_updates(case4096):
+    """refine=2: one FP32-product block CG whose recurrence residuals are
+    replaced by the FP64 residual B - A X; reaches the FP64 tolerance."""
+    torch = require_cuda()
+    A, B, Xc, G = case4096
+    Bd = torch.from_numpy(B).cuda()
+    Xd = torch.zeros_like(Bd)
+    res = G.block_cg(Bd, Xd, tol=1e-8, max_iter=20000, dtype="f32", refine=2, inner_tol=0.1)
+    assert res.status == 0, res
+    X = Xd.cpu().numpy()
+    true_rel = np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0)
+    assert true_rel.max() <= 1e-8 * 1.5, true_rel
+    assert rel_fro(X, Xc) <= 1e-6
+    assert res.outer_steps >= 1  # at least one reliable update
+    plain = O.block_cg(lambda Z: A @ Z, B, tol=1e-8, max_iter=20000)
+    assert res.iterations <= 1.5 * plain.iterations
+
+
 def test_block_cg_host_buffers_and_initial_guess(case4096):
     A, B, Xc, G = case4096
     X0 = Xc + 1e-4 * gaussian_rhs(4096, 8, 2)
