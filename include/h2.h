@@ -237,6 +237,43 @@ int h2_shift_set(h2_matrix* A, double sigma);
 int h2_adjoint_grads(h2_matrix* A, const double* L, int64_t ldl, const double* X, int64_t ldx, int64_t m,
                      double* dS, double* dsigma, void* stream);
 
+/* ---- many independent systems ---------------------------------------------
+ * The paper solves one matrix with many right-hand sides; independent
+ * systems (Sec. 5: "the m linear systems" are independent) of different
+ * sizes can also share the GPU.  A batch groups existing matrices (it does not
+ * own them).  Its products and solver iterations run as one CUDA graph launch
+ * covering every system: each system's kernels form an independent branch of
+ * the graph, so small systems fill the GPU together.  The graph is captured on
+ * first use for a given set of pointers and column counts and replayed
+ * afterwards; everything it needs is allocated before the capture. */
+typedef struct h2_batch h2_batch;
+
+int h2_batch_create(h2_matrix* const* mats, int32_t count, h2_batch** out);
+int h2_batch_free(h2_batch* batch);
+
+/* Y_i <- Y_i + alpha·A_i·X_i for every system i (device pointers; m[i] columns,
+ * leading dimensions ldx[i] >= m[i], ldy[i] >= m[i]; m[i] = 0 skips system i).
+ * One graph launch on `stream`. */
+int h2_batch_matmul(h2_batch* batch, double alpha, const double* const* X, const int64_t* ldx, double* const* Y,
+                    const int64_t* ldy, const int64_t* m, int32_t dtype, void* stream);
+
+/* Block CG for every system (device B_i, X_i; X_i holds the initial guess).
+ * dtype H2_F64: plain FP64 block CG.  H2_F32 / H2_BF16: block CG with that
+ * product and FP64 vectors, recurrence residuals replaced by the FP64 residual
+ * B_i - A_i X_i whenever they fell by params->inner_tol (reliable updates, as
+ * h2_cg_params.refine = 2).  Every iteration of all unconverged systems is one
+ * graph launch; converged systems leave the graph.  res[i] reports system i;
+ * its col_iterations / rel_residual pointers may each be NULL or point to
+ * m[i] entries.  Returns H2_OK if every system converged. */
+int h2_batch_block_cg(h2_batch* batch, const double* const* B, const int64_t* ldb, double* const* X,
+                      const int64_t* ldx, const int64_t* m, const h2_cg_params* params, h2_cg_result* res);
+
+/* Autotuning: time the FP32 product of m columns on the tensor cores (split
+ * TF32) and on the CUDA cores for this matrix and keep the faster for later
+ * FP32 products.  ms[0], ms[1] (optional) receive the two times per product in
+ * milliseconds (ms[0] < 0 when the tensor-core copy was not built). */
+int h2_autotune(h2_matrix* A, int64_t m, void* stream, double* ms);
+
 /* ---- host-only topology (Sec. 2 trees; Alg. "prepare_addeval" lists) ---- */
 typedef struct h2_tree h2_tree;
 

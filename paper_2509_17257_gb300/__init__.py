@@ -19,7 +19,9 @@ from .h2 import (  # noqa: F401
     H2_F64,
     H2_OK,
     H2Error,
+    H2Batch,
     H2Matrix,
+    h2_autotune,
     LIB_PATH,
     SolveResult,
     h2_adjoint_grads,

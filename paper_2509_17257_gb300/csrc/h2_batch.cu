@@ -1,0 +1,191 @@
+// Batches of independent systems: products captured into one CUDA graph with
+// one branch per system, and the autotuner that picks the FP32 product path.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "h2_internal.cuh"
+
+namespace h2 {
+
+int batch_capture(h2_batch* b, cudaStream_t origin, const std::vector<int>& sys,
+                  int (*body)(void* ctx, int i, cudaStream_t st), void* ctx, cudaGraphExec_t* exec) {
+    *exec = nullptr;
+    H2_CUDA_TRY(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+    int rc = 0;
+    cudaError_t e = cudaEventRecord(b->fork, origin);
+    for (size_t j = 0; j < sys.size() && !rc && e == cudaSuccess; ++j) {
+        const int i = sys[j];
+        e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+        if (e != cudaSuccess) break;
+        rc = body(ctx, i, b->streams[i]);
+        if (rc) break;
+        e = cudaEventRecord(b->join[i], b->streams[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, b->join[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(origin, &graph);
+    if (rc || e != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (!rc) {
+            set_error(std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : ee));
+            rc = H2_E_CUDA;
+        }
+        return rc;
+    }
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
+        return H2_E_CUDA;
+    }
+    return 0;
+}
+
+namespace {
+
+struct MmCtx {
+    h2_batch* b;
+    double alpha;
+    const double* const* X;
+    const int64_t* ldx;
+    double* const* Y;
+    const int64_t* ldy;
+    const int64_t* m;
+    int32_t dtype;
+};
+
+int mm_body(void* ctx, int i, cudaStream_t st) {
+    MmCtx* c = (MmCtx*)ctx;
+    return matmul_device(c->b->mats[i], c->alpha, c->X[i], c->ldx[i], c->Y[i], c->ldy[i], c->m[i], c->dtype, st,
+                         false, false);
+}
+
+}  // namespace
+
+}  // namespace h2
+
+using namespace h2;
+
+extern "C" {
+
+int h2_batch_create(h2_matrix* const* mats, int32_t count, h2_batch** out) {
+    if (!out || !mats || count < 1) { set_error("bad batch arguments"); return H2_E_BADARG; }
+    *out = nullptr;
+    h2_batch* b = new h2_batch();
+    for (int i = 0; i < count; ++i) {
+        if (!mats[i]) { delete b; set_error("null matrix in batch"); return H2_E_BADARG; }
+        b->mats.push_back(mats[i]);
+    }
+    b->streams.resize(count, nullptr);
+    b->join.resize(count, nullptr);
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        h2_batch_free(b);
+        set_error(std::string("batch streams: ") + cudaGetErrorString(e));
+        return H2_E_CUDA;
+    }
+    *out = b;
+    return 0;
+}
+
+int h2_batch_free(h2_batch* b) {
+    if (!b) return 0;
+    if (b->mm_exec) cudaGraphExecDestroy(b->mm_exec);
+    for (auto s : b->streams) if (s) cudaStreamDestroy(s);
+    for (auto e : b->join) if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+    return 0;
+}
+
+int h2_batch_matmul(h2_batch* b, double alpha, const double* const* X, const int64_t* ldx, double* const* Y,
+                    const int64_t* ldy, const int64_t* m, int32_t dtype, void* stream) {
+    if (!b || !X || !ldx || !Y || !ldy || !m) { set_error("null argument"); return H2_E_BADARG; }
+    if (dtype != H2_F64 && dtype != H2_F32 && dtype != H2_BF16) { set_error("bad dtype"); return H2_E_BADARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int count = (int)b->mats.size();
+    std::vector<int64_t> key;
+    std::vector<int> sys;
+    int64_t abits;
+    memcpy(&abits, &alpha, sizeof(abits));
+    key.push_back(dtype);
+    key.push_back(abits);
+    for (int i = 0; i < count; ++i) {
+        if (m[i] < 0 || ldx[i] < m[i] || ldy[i] < m[i]) { set_error("bad m / leading dimension"); return H2_E_BADARG; }
+        if (m[i] == 0) continue;
+        if (!X[i] || !Y[i] || !is_device_pointer(X[i]) || !is_device_pointer(Y[i])) {
+            set_error("batched products take device X and Y");
+            return H2_E_BADARG;
+        }
+        if (b->mats[i]->timing.on) { set_error("disable timing on batched matrices"); return H2_E_UNSUPPORTED; }
+        sys.push_back(i);
+        key.insert(key.end(), {i, (int64_t)(uintptr_t)X[i], ldx[i], (int64_t)(uintptr_t)Y[i], ldy[i], m[i]});
+    }
+    if (sys.empty()) return 0;
+    if (!b->mm_exec || key != b->mm_key) {
+        if (b->mm_exec) { cudaGraphExecDestroy(b->mm_exec); b->mm_exec = nullptr; }
+        for (int i : sys) {
+            int rc = product_prepare(b->mats[i], m[i], dtype, st);
+            if (rc) return rc;
+        }
+        H2_CUDA_TRY(cudaStreamSynchronize(st));
+        MmCtx ctx{b, alpha, X, ldx, Y, ldy, m, dtype};
+        int rc = batch_capture(b, st, sys, mm_body, &ctx, &b->mm_exec);
+        if (rc) return rc;
+        b->mm_key = key;
+    }
+    H2_CUDA_TRY(cudaGraphLaunch(b->mm_exec, st));
+    return 0;
+}
+
+int h2_batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, double* const* X, const int64_t* ldx,
+                      const int64_t* m, const h2_cg_params* params, h2_cg_result* res) {
+    return batch_block_cg(b, B, ldb, X, ldx, m, params, res);
+}
+
+int h2_autotune(h2_matrix* A, int64_t m, void* stream, double* ms) {
+    if (!A || m < 1) { set_error("bad argument"); return H2_E_BADARG; }
+    if (!A->f32.built) { set_error("FP32 copy not built"); return H2_E_UNSUPPORTED; }
+    cudaStream_t st = (cudaStream_t)stream;
+    double* buf = nullptr;
+    H2_CUDA_TRY(cudaMallocAsync((void**)&buf, 2 * (size_t)A->n * m * sizeof(double), st));
+    H2_CUDA_TRY(cudaMemsetAsync(buf, 0, 2 * (size_t)A->n * m * sizeof(double), st));
+    double* Xb = buf;
+    double* Yb = buf + (size_t)A->n * m;
+    cudaEvent_t e0, e1;
+    H2_CUDA_TRY(cudaEventCreate(&e0));
+    H2_CUDA_TRY(cudaEventCreate(&e1));
+    double t[2] = {-1.0, -1.0};
+    const bool keep = A->force_simt;
+    int rc = 0;
+    for (int path = 0; path < 2 && !rc; ++path) {
+        if (path == 0 && !A->tc.has_tf32) continue;
+        A->force_simt = path == 1;
+        for (int r = 0; r < 2 && !rc; ++r) rc = matmul_device(A, 1.0, Xb, m, Yb, m, m, H2_F32, st, false, true);
+        if (rc) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 5 && !rc; ++r) rc = matmul_device(A, 1.0, Xb, m, Yb, m, m, H2_F32, st, false, true);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float f = 0.f;
+        cudaEventElapsedTime(&f, e0, e1);
+        t[path] = f / 5.0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(buf, st);
+    cudaStreamSynchronize(st);
+    if (rc) { A->force_simt = keep; return rc; }
+    A->force_simt = !(t[0] >= 0.0 && t[0] <= t[1]);
+    if (ms) { ms[0] = t[0]; ms[1] = t[1]; }
+    return 0;
+}
+
+}  // extern "C"

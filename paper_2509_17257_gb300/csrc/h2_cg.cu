@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <memory>
 #include <vector>
 
 #include "h2_internal.cuh"
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(256) k_cg_update(double* __restrict__ X, int64
         const double rn = sqrt(rr);
         d.rnorm[col] = rn;
         if (!isfinite(gamma) || !isfinite(rn)) atomicOr(&d.summary[1], 1);
-        d.conv_iter[col] = iter;
+        d.conv_iter[col] += 1;  // iterations while active (graph-replay safe, no baked counter)
         if (rn / d.bnorm[col] <= tol) {
             d.active[col] = 0;
             atomicSub(&d.summary[0], 1);
@@ -464,6 +465,210 @@ struct Solver {
 };
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Batched block CG over independent systems: every iteration of all unconverged
+// systems (product + the three column-wise kernels) is one CUDA graph launch.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchSys {
+    Solver* S = nullptr;
+    const double* B = nullptr;
+    int64_t ldb = 0;
+    double* X = nullptr;
+    int64_t ldx = 0;
+    double* Rt = nullptr;  // true residual buffer [n×m] followed by rupd [m]
+    double* rupd = nullptr;
+    bool done = false;
+    int status = 0, iters = 0, updates = 0;
+};
+
+struct BatchIterCtx {
+    std::vector<BatchSys>* sys;
+    int32_t dtype;
+    double tol;
+};
+
+int batch_iter_body(void* ctx, int i, cudaStream_t st) {
+    BatchIterCtx* c = (BatchIterCtx*)ctx;
+    Solver& S = *(*c->sys)[i].S;
+    const dim3 blk(kColsPerCta, 8);
+    const dim3 grid(kRowBlocks, (S.m + kColsPerCta - 1) / kColsPerCta);
+    int rc = matmul_device(S.A, 1.0, S.P, S.m, S.AP, S.m, S.m, c->dtype, st, false, true);
+    if (rc) return rc;
+    k_cg_dots<<<grid, blk, 0, st>>>(S.P, S.AP, S.R, S.m, S.n, S.m, S.d);
+    H2_LAUNCH_CHECK();
+    k_cg_update<<<grid, blk, 0, st>>>((*c->sys)[i].X, (*c->sys)[i].ldx, S.P, S.AP, S.R, S.m, S.n, S.m, c->tol, 0,
+                                      S.d);
+    H2_LAUNCH_CHECK();
+    k_cg_dir<<<grid, blk, 0, st>>>(S.P, S.R, S.m, S.n, S.m, S.d);
+    H2_LAUNCH_CHECK();
+    return 0;
+}
+
+}  // namespace
+
+int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, double* const* X, const int64_t* ldx,
+                   const int64_t* m, const h2_cg_params* p, h2_cg_result* res) {
+    if (!b || !B || !ldb || !X || !ldx || !m || !p || !res) { set_error("null argument"); return H2_E_BADARG; }
+    if (!(p->tol >= 0.0) || p->max_iter < 0 || p->check_every < 1) { set_error("bad solver parameters"); return H2_E_BADARG; }
+    const int32_t dtype = p->dtype;
+    if (dtype != H2_F64 && dtype != H2_F32 && dtype != H2_BF16) { set_error("bad dtype"); return H2_E_BADARG; }
+    if (p->transposed) { set_error("batched solves take A, not Aᵀ"); return H2_E_UNSUPPORTED; }
+    const int count = (int)b->mats.size();
+    cudaStream_t st = (cudaStream_t)p->stream;
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<BatchSys> sys(count);
+    std::vector<std::unique_ptr<Solver>> solvers;
+    for (int i = 0; i < count; ++i) {
+        res[i].status = 0;
+        res[i].iterations = res[i].outer_steps = res[i].h2mm_calls = 0;
+        res[i].seconds = 0.0;
+        if (m[i] < 0 || ldb[i] < m[i] || ldx[i] < m[i]) { set_error("bad m / leading dimension"); return H2_E_BADARG; }
+        if (m[i] == 0) { sys[i].done = true; continue; }
+        if (!is_device_pointer(B[i]) || !is_device_pointer(X[i])) {
+            set_error("batched solves take device B and X");
+            return H2_E_BADARG;
+        }
+        if (b->mats[i]->timing.on) { set_error("disable timing on batched matrices"); return H2_E_UNSUPPORTED; }
+    }
+    const double delta = p->inner_tol > 0.0 && p->inner_tol < 1.0 ? p->inner_tol : 0.1;
+    const bool reliable = dtype != H2_F64;
+    // set-up on each system's own stream: residual, CG state, product resources
+    for (int i = 0; i < count; ++i) {
+        if (sys[i].done) continue;
+        h2_matrix* A = b->mats[i];
+        cudaStream_t si = b->streams[i];
+        solvers.emplace_back(new Solver{A, si, A->n, (int)m[i]});
+        Solver& S = *solvers.back();
+        sys[i].S = &S;
+        sys[i].B = B[i];
+        sys[i].ldb = ldb[i];
+        sys[i].X = X[i];
+        sys[i].ldx = ldx[i];
+        int rc = S.init();
+        if (rc) return rc;
+        H2_CUDA_TRY(cudaMallocAsync((void**)&sys[i].Rt, ((size_t)A->n * m[i] + m[i]) * sizeof(double), si));
+        sys[i].rupd = sys[i].Rt + (size_t)A->n * m[i];
+        if ((rc = product_prepare(A, m[i], H2_F64, si))) return rc;
+        if (dtype != H2_F64 && (rc = product_prepare(A, m[i], dtype, si))) return rc;
+        if ((rc = S.residual(B[i], ldb[i], X[i], ldx[i]))) return rc;
+        H2_CUDA_TRY(cudaMemsetAsync(S.d.summary, 0, 4 * sizeof(int), si));
+        k_cg_init<<<(int)((m[i] + 63) / 64), 64, 0, si>>>(B[i], ldb[i], S.R, m[i], A->n, (int)m[i], p->tol, S.d);
+        H2_LAUNCH_CHECK();
+        k_copy2d<<<S.copy_grid(), 256, 0, si>>>(S.R, m[i], S.P, m[i], A->n, (int)m[i]);
+        H2_LAUNCH_CHECK();
+        H2_CUDA_TRY(cudaMemcpyAsync(sys[i].rupd, S.d.rnorm, m[i] * sizeof(double), cudaMemcpyDeviceToDevice, si));
+        H2_CUDA_TRY(cudaMemcpyAsync(S.h_summary, S.d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, si));
+    }
+    for (int i = 0; i < count; ++i) {
+        if (sys[i].done) continue;
+        H2_CUDA_TRY(cudaStreamSynchronize(b->streams[i]));
+        if (sys[i].S->h_summary[0] == 0) sys[i].done = true;
+    }
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
+    BatchIterCtx ctx{&sys, dtype, p->tol};
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> in_graph;
+    int status = 0, it = 0;
+    auto rebuild = [&]() -> int {
+        if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+        in_graph.clear();
+        for (int i = 0; i < count; ++i) if (!sys[i].done) in_graph.push_back(i);
+        if (in_graph.empty()) return 0;
+        return batch_capture(b, st, in_graph, batch_iter_body, &ctx, &exec);
+    };
+    int rc = rebuild();
+    if (rc) return rc;
+    int done_since_build = 0;
+    for (it = 1; it <= p->max_iter && !in_graph.empty(); ++it) {
+        H2_CUDA_TRY(cudaGraphLaunch(exec, st));
+        for (int i : in_graph) if (!sys[i].done) sys[i].iters = it;
+        if (it % p->check_every != 0 && it != p->max_iter) continue;
+        H2_CUDA_TRY(cudaStreamSynchronize(st));
+        bool all = true;
+        for (int i : in_graph) {
+            BatchSys& y = sys[i];
+            if (y.done) continue;
+            Solver& S = *y.S;
+            cudaStream_t si = b->streams[i];
+            const int mi = S.m;
+            std::vector<double> rn(mi), ru(mi);
+            std::vector<int> act(mi);
+            H2_CUDA_TRY(cudaMemcpyAsync(S.h_summary, S.d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, si));
+            H2_CUDA_TRY(cudaMemcpyAsync(rn.data(), S.d.rnorm, mi * sizeof(double), cudaMemcpyDeviceToHost, si));
+            H2_CUDA_TRY(cudaMemcpyAsync(ru.data(), y.rupd, mi * sizeof(double), cudaMemcpyDeviceToHost, si));
+            H2_CUDA_TRY(cudaMemcpyAsync(act.data(), S.d.active, mi * sizeof(int), cudaMemcpyDeviceToHost, si));
+            H2_CUDA_TRY(cudaStreamSynchronize(si));
+            if (S.h_summary[1]) { y.status = H2_E_BREAKDOWN; y.done = true; ++done_since_build; continue; }
+            bool update = S.h_summary[0] == 0;
+            if (reliable)
+                for (int c = 0; c < mi && !update; ++c) update = act[c] && rn[c] < delta * ru[c];
+            if (!update) { all = false; continue; }
+            if (!reliable) { y.done = true; ++done_since_build; continue; }
+            // true FP64 residual replaces the recurrence residual (eager, off the graph)
+            const dim3 blk(kColsPerCta, 8);
+            const dim3 grid(kRowBlocks, (mi + kColsPerCta - 1) / kColsPerCta);
+            k_copy2d<<<S.copy_grid(), 256, 0, si>>>(y.B, y.ldb, y.Rt, mi, S.n, mi);
+            H2_LAUNCH_CHECK();
+            ++S.h2mm_calls;
+            ++y.updates;
+            if ((rc = matmul_device(S.A, -1.0, y.X, y.ldx, y.Rt, mi, mi, H2_F64, si, false, false))) return rc;
+            H2_CUDA_TRY(cudaMemsetAsync(S.d.summary, 0, sizeof(int), si));
+            k_cg_reliable<<<grid, blk, 0, si>>>(y.Rt, S.R, S.P, mi, S.n, mi, p->tol, y.rupd, S.d);
+            H2_LAUNCH_CHECK();
+            k_cg_reliable_copy<<<grid, blk, 0, si>>>(y.Rt, S.R, S.P, mi, S.n, mi, S.d);
+            H2_LAUNCH_CHECK();
+            k_cg_reliable_flags<<<(mi + 63) / 64, 64, 0, si>>>(mi, S.d);
+            H2_LAUNCH_CHECK();
+            H2_CUDA_TRY(cudaMemcpyAsync(S.h_summary, S.d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, si));
+            H2_CUDA_TRY(cudaStreamSynchronize(si));
+            if (S.h_summary[1]) { y.status = H2_E_BREAKDOWN; y.done = true; ++done_since_build; continue; }
+            if (S.h_summary[0] == 0) { y.done = true; ++done_since_build; continue; }
+            all = false;
+        }
+        if (all) break;
+        // systems that left: rebuild the graph once a quarter of it has converged
+        if (done_since_build > 0 && done_since_build * 4 >= (int)in_graph.size()) {
+            if ((rc = rebuild())) return rc;
+            done_since_build = 0;
+        }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
+    // report: true FP64 residual per column
+    for (int i = 0; i < count; ++i) {
+        BatchSys& y = sys[i];
+        if (!y.S) continue;
+        Solver& S = *y.S;
+        cudaStream_t si = b->streams[i];
+        const int mi = S.m;
+        if (!y.done && y.status == 0) y.status = H2_E_NOCONVERGE;
+        if ((rc = S.residual(y.B, y.ldb, y.X, y.ldx))) return rc;
+        k_col_relnorm<<<(mi + 63) / 64, 64, 0, si>>>(S.R, mi, y.B, y.ldb, S.n, mi, y.rupd);
+        H2_LAUNCH_CHECK();
+        std::vector<double> rel(mi);
+        std::vector<int> ci(mi);
+        H2_CUDA_TRY(cudaMemcpyAsync(rel.data(), y.rupd, mi * sizeof(double), cudaMemcpyDeviceToHost, si));
+        H2_CUDA_TRY(cudaMemcpyAsync(ci.data(), S.d.conv_iter, mi * sizeof(int), cudaMemcpyDeviceToHost, si));
+        cudaFreeAsync(y.Rt, si);
+        H2_CUDA_TRY(cudaStreamSynchronize(si));
+        if (res[i].rel_residual) for (int c = 0; c < mi; ++c) res[i].rel_residual[c] = rel[c];
+        if (res[i].col_iterations) for (int c = 0; c < mi; ++c) res[i].col_iterations[c] = ci[c];
+        res[i].status = y.status;
+        res[i].iterations = y.iters;
+        res[i].outer_steps = y.updates;
+        res[i].h2mm_calls = S.h2mm_calls + y.iters;
+        if (y.status && !status) status = y.status;
+    }
+    solvers.clear();
+    for (auto s2 : b->streams) cudaStreamSynchronize(s2);
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int i = 0; i < count; ++i) res[i].seconds = secs;
+    if (status) set_error("some systems did not converge (see the per-system status)");
+    return status;
+}
 
 int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
              const h2_cg_params* p, h2_cg_result* res) {

@@ -124,8 +124,9 @@ struct TcData {
 };
 
 // Inter-CTA bookkeeping of the one-launch transfer passes: arrival counters of
-// the upward pass (self-resetting), ready flags of the downward pass (equal to
-// the product's epoch once set) and its claim tickets (reset per product).
+// the upward pass (self-resetting), ready flags of the downward pass and its
+// claim tickets (both cleared before every downward pass, so a captured CUDA
+// graph can replay the product).
 struct SyncBufs {
     unsigned* cnt = nullptr;
     int* flag = nullptr;
@@ -193,12 +194,28 @@ struct h2_matrix {
     int* sync_flag = nullptr;      // [nc × sync_tiles]
     unsigned* sync_claim = nullptr;// [sync_tiles]
     int64_t sync_tiles = 0;
-    int epoch = 0;
     bool force_simt = false;  // H2_FORCE_SIMT=1 at build: FP32 product on the CUDA cores only
     std::vector<void*> allocations;
 };
 
+// A group of independent systems (h2_batch.cu, h2_cg.cu).
+struct h2_batch {
+    std::vector<h2_matrix*> mats;
+    std::vector<cudaStream_t> streams;  // one per system: branches of the captured graphs
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaGraphExec_t mm_exec = nullptr;  // cached product graph
+    std::vector<int64_t> mm_key;
+};
+
 namespace h2 {
+
+// Capture body(i, stream_i) for every system i in `sys` as independent
+// branches of one CUDA graph forked from and joined into `origin`.
+int batch_capture(h2_batch* b, cudaStream_t origin, const std::vector<int>& sys,
+                  int (*body)(void* ctx, int i, cudaStream_t st), void* ctx, cudaGraphExec_t* exec);
+int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, double* const* X, const int64_t* ldx,
+                   const int64_t* m, const h2_cg_params* p, h2_cg_result* res);
 
 // Entry points implemented in h2_build.cu / h2_mm.cu / h2_cg.cu.
 int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cudaStream_t st);
@@ -220,6 +237,11 @@ int matmul_in_scratch(h2_matrix* A, double alpha, const double* X, int64_t ldx, 
 
 // tcgen05 BF16 kernels (h2_tc.cu)
 int tc_smem_bytes();
+int tc_prepare();
+// Allocate everything a product of m columns in dtype needs (workspace,
+// transfer-pass bookkeeping, kernel attributes), so that the product itself
+// allocates nothing (e.g. while it is captured into a CUDA graph).
+int product_prepare(h2_matrix* A, int64_t m, int32_t dtype, cudaStream_t st);
 int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st);
 int launch_pack_tiles(const TcPackTile* tiles, int64_t count, const double* src, uint8_t* dst, int es,
                       cudaStream_t st);

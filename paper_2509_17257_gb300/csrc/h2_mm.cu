@@ -236,7 +236,7 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // next item (atomic ticket), waits until its parent's ŷ is final (the parent
 // has a smaller ticket, so a running CTA holds it; the wait is bounded and
 // reports a timeout through err), adds E_{t'} ŷ_parent and publishes its own
-// flag (= epoch of this product).
+// ready flag (set to `epoch`; the flags are cleared before each launch).
 template <typename T, int RM, int CN>
 __global__ void __launch_bounds__(kThreads) k_down_fused(const int32_t* __restrict__ order, int n_items,
                                                          const int32_t* __restrict__ parent, const T* __restrict__ E,
@@ -431,6 +431,8 @@ int backward_pass(h2_matrix* A, const T* E, T* yhat, int m, unsigned gy, unsigne
     const int n_items = (int)A->down_ptr[A->depth + 1];
     if (n_items == 0) return 0;
     if (gzk == 1) {
+        // ready flags and claim tickets start at zero for every product (graph-replay safe)
+        H2_CUDA_TRY(cudaMemsetAsync(sb.flag, 0, (size_t)A->nc * gy * sizeof(int), st));
         H2_CUDA_TRY(cudaMemsetAsync(sb.claim, 0, gy * sizeof(unsigned), st));
         const unsigned g = (unsigned)std::min(n_items, 152 * 6);
         k_down_fused<T, RM, CN><<<dim3(g, gy), kThreads, 0, st>>>(A->d_down_list, n_items, A->d_parent, E, yhat,
@@ -533,7 +535,6 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
     SyncBufs sbc = sb;
     for (int c0 = 0; c0 < m; c0 += 64) {
         const int mc = std::min(64, m - c0);
-        if (c0 > 0) sbc.epoch = ++A->epoch;  // every chunk's downward pass needs fresh ready flags
         const int R = round16(2 * mc);
         const size_t bXp = align_up((size_t)n * mc * 4), bC = align_up((size_t)nc * k * mc * 4);
         const size_t bXcm = align_up((size_t)R * D.xk_total * es), bAct = align_up((size_t)nc * R * KP * es);
@@ -640,12 +641,11 @@ int ensure_sync(h2_matrix* A, int64_t tiles, cudaStream_t st, SyncBufs* sb) {
         A->sync_flag = (int*)(A->sync_cnt + per);
         A->sync_claim = (unsigned*)(A->sync_flag + per);
         A->sync_tiles = tiles;
-        A->epoch = 0;
     }
     sb->cnt = A->sync_cnt;
     sb->flag = A->sync_flag;
     sb->claim = A->sync_claim;
-    sb->epoch = ++A->epoch;
+    sb->epoch = 1;  // flags are cleared before every downward pass
     sb->err = A->err_dev;
     return 0;
 }
@@ -693,6 +693,30 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
     }
     set_error("unsupported dtype for the product");
     return H2_E_UNSUPPORTED;
+}
+
+int product_prepare(h2_matrix* A, int64_t m, int32_t dtype, cudaStream_t st) {
+    if (m <= 0) return 0;
+    int rc = 0;
+    const int64_t n = A->n, nc = A->nc;
+    const int k = A->k;
+    size_t need = 0;
+    const bool tc = (dtype == H2_BF16) || (dtype == H2_F32 && A->tc.has_tf32 && !A->force_simt);
+    if (tc) {
+        const TcData& D = A->tc;
+        const int es = dtype == H2_BF16 ? 2 : 4;
+        const int mc = (int)std::min<int64_t>(64, m);
+        const int R = round16(2 * mc);
+        need = align_up((size_t)n * mc * 4) + 2 * align_up((size_t)nc * k * mc * 4) +
+               align_up((size_t)R * D.xk_total * es) + 2 * align_up((size_t)nc * R * D.KP * es);
+        if ((rc = tc_prepare())) return rc;
+    } else {
+        const size_t elt = dtype == H2_F64 ? sizeof(double) : sizeof(float);
+        need = align_up((size_t)n * m * elt) + 2 * align_up((size_t)nc * k * m * elt);
+    }
+    if ((rc = ensure_workspace(A, need, st))) return rc;
+    SyncBufs sb;
+    return ensure_sync(A, sync_tiles_for(m), st, &sb);
 }
 
 int forward_transform_f64(h2_matrix* A, const double* X, int64_t ldx, int64_t m, double* Xp, double* xhat,

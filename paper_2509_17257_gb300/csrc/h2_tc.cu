@@ -62,6 +62,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
         if (mbar_try(b, parity)) return true;
     return false;
 }
+// Warp-level wait: only lane 0 polls the barrier (many polling threads slow the
+// barrier unit that the bulk copies and MMA commits also update); the result
+// and the ordering reach the other lanes through __syncwarp / a shuffle.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity) {
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(b, parity) ? 1 : 0;
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
 }
@@ -224,7 +233,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf_bar[b], 1);
-            mbar_init(&acce_bar[b], 128);
+            mbar_init(&acce_bar[b], 4);  // one arrival per epilogue warp
         }
         mbar_init(&drain_bar, 1);
         abort_flag = 0;
@@ -404,9 +413,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             }
             const int id = cur.id, np = cur.np;
             const int acc = it & 1;
-            // warp-uniform wait: a completed phase stays completed, so any lane's
-            // success is the warp's success
-            const bool ok = __any_sync(0xffffffffu, mbar_wait(&accf_bar[acc], (it >> 1) & 1));
+            const bool ok = mbar_wait_warp(&accf_bar[acc], (it >> 1) & 1);
             if (!ok) {
                 if (lane == 0) atomicExch(p.err, 6);
                 abort_flag = 1;
@@ -438,7 +445,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                 }
             }
             tc_fence_before();
-            mbar_arrive(&acce_bar[acc]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce_bar[acc]);
             cur = nxt;
             cur_off = nxt_off;
             cur_nt = nxt_nt;
@@ -449,7 +457,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
         int stage = 0;
         uint32_t phase = 0;
         while (true) {
-            const bool ok = __any_sync(0xffffffffu, mbar_wait(&full_bar[stage], phase));
+            const bool ok = mbar_wait_warp(&full_bar[stage], phase);
             if (!ok) {
                 if (lane == 0) atomicExch(p.err, 7);
                 abort_flag = 1;
@@ -503,13 +511,26 @@ void tc_stage_geometry(int R, int es, int* a_bytes, int* stage_bytes, int* nstag
 
 template <int MODE, int KIND>
 int launch_one(const TcGemmParams& p, int grid, int smem, cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
-        attr_set = true;
-    }
     k_tc_gemm<MODE, KIND><<<grid, kTcThreads, smem, st>>>(p);
     H2_LAUNCH_CHECK();
+    return 0;
+}
+
+// Set the shared-memory attribute of every tensor-core kernel instance up
+// front (needed before a product is captured into a CUDA graph).
+namespace {
+int g_tc_attr_device = -1;  // device whose kernel attributes are set
+}
+
+int tc_prepare() {
+    int dev = 0;
+    H2_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev == g_tc_attr_device) return 0;
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+    g_tc_attr_device = dev;
     return 0;
 }
 
@@ -519,6 +540,8 @@ int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st
     if (nstages < 2) { set_error("tensor-core stage does not fit in shared memory"); return H2_E_UNSUPPORTED; }
     p.a_stage_bytes = a_bytes;
     p.nstages = nstages;
+    int rc = tc_prepare();
+    if (rc) return rc;
     const int smem = nstages * stage_bytes + 1024;
     if (mode == 0 && kind == 0) return launch_one<0, 0>(p, grid, smem, st);
     if (mode == 1 && kind == 0) return launch_one<1, 0>(p, grid, smem, st);

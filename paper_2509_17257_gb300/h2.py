@@ -81,7 +81,8 @@ class TreeView(C.Structure):
 #: every symbol include/h2.h declares
 EXPORTS = ["h2_build", "h2_free", "h2_info", "h2_matmul", "h2_matmul_transposed", "h2_matmul_noalloc", "h2_block_cg",
            "h2_timing_enable", "h2_timing_query", "h2_coupling_get", "h2_coupling_set", "h2_shift_set",
-           "h2_adjoint_grads",
+           "h2_adjoint_grads", "h2_batch_create", "h2_batch_free", "h2_batch_matmul", "h2_batch_block_cg",
+           "h2_autotune",
            "h2_tree_build", "h2_tree_view_get", "h2_tree_free", "h2_last_error_string", "h2_version"]
 H2_NPHASE = 8
 PHASES = ["gather", "leaf_fwd", "up", "coupling", "down", "leaf_bwd_near"]
@@ -108,6 +109,13 @@ def lib() -> C.CDLL:
     L.h2_coupling_set.argtypes = [vp, vp, vp]
     L.h2_shift_set.argtypes = [vp, dbl]
     L.h2_adjoint_grads.argtypes = [vp, vp, i64, vp, i64, i64, vp, C.POINTER(C.c_double), vp]
+    L.h2_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp)]
+    L.h2_batch_free.argtypes = [vp]
+    L.h2_batch_matmul.argtypes = [vp, dbl, C.POINTER(vp), C.POINTER(i64), C.POINTER(vp), C.POINTER(i64),
+                                  C.POINTER(i64), i32, vp]
+    L.h2_batch_block_cg.argtypes = [vp, C.POINTER(vp), C.POINTER(i64), C.POINTER(vp), C.POINTER(i64),
+                                    C.POINTER(i64), C.POINTER(CGParams), C.POINTER(CGResult)]
+    L.h2_autotune.argtypes = [vp, i64, vp, C.POINTER(C.c_double)]
     L.h2_timing_enable.argtypes = [vp, i32]
     L.h2_timing_query.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
     L.h2_tree_build.argtypes = [C.POINTER(BuildParams), vp, i64, C.POINTER(vp)]
@@ -326,6 +334,72 @@ def h2_block_cg(handle, B, X, tol=1e-8, max_iter=20000, dtype="f64", refine=True
     _check(rc, "h2_block_cg", ok=(H2_OK, H2_E_NOCONVERGE, H2_E_BREAKDOWN))
     return SolveResult(res.status, res.iterations, res.outer_steps, res.h2mm_calls, it[:m].copy(), rel[:m].copy(),
                        res.seconds)
+
+
+def h2_autotune(handle, m: int, stream=None):
+    """Time the FP32 product on the tensor cores and on the CUDA cores and keep
+    the faster; returns (ms tensor-core, ms CUDA-core)."""
+    ms = (C.c_double * 2)()
+    _check(lib().h2_autotune(handle, int(m), _stream_ptr(stream), ms), "h2_autotune")
+    return ms[0], ms[1]
+
+
+class H2Batch:
+    """Independent systems whose products and block-CG iterations run as one
+    CUDA graph launch (h2_batch_*).  Holds references to the matrices."""
+
+    def __init__(self, mats):
+        self.mats = list(mats)
+        arr = (C.c_void_p * len(self.mats))(*[mm.handle for mm in self.mats])
+        h = C.c_void_p()
+        _check(lib().h2_batch_create(arr, len(self.mats), C.byref(h)), "h2_batch_create")
+        self.handle = h.value
+
+    def _ptrs(self, blocks, name, writable=False):
+        cnt = len(self.mats)
+        ps, lds, ms, keep = (C.c_void_p * cnt)(), (C.c_int64 * cnt)(), (C.c_int64 * cnt)(), []
+        for i, (mm, b) in enumerate(zip(self.mats, blocks)):
+            p, ld, m, k = _ptr_ld(b, f"{name}[{i}]", mm.n, writable)
+            ps[i], lds[i], ms[i] = p, ld, m
+            keep.append(k)
+        return ps, lds, ms, keep
+
+    def matmul(self, Xs, Ys, alpha=1.0, dtype="f64", stream=None):
+        xp, lx, mx, kx = self._ptrs(Xs, "X")
+        yp, ly, my, ky = self._ptrs(Ys, "Y", True)
+        dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        _check(lib().h2_batch_matmul(self.handle, float(alpha), xp, lx, yp, ly, mx, dt, _stream_ptr(stream)),
+               "h2_batch_matmul")
+        return Ys
+
+    def block_cg(self, Bs, Xs, tol=1e-8, max_iter=20000, dtype="f32", inner_tol=0.1, check_every=4,
+                 stream=None):
+        bp, lb, mb, kb = self._ptrs(Bs, "B")
+        xp, lx, mx, kx = self._ptrs(Xs, "X", True)
+        cnt = len(self.mats)
+        dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        prm = CGParams(tol, max_iter, H2_CG_COLUMNWISE, dt, 2, inner_tol, 0, check_every, 0, _stream_ptr(stream))
+        its = [np.zeros(max(int(mb[i]), 1), dtype=np.int32) for i in range(cnt)]
+        rels = [np.zeros(max(int(mb[i]), 1)) for i in range(cnt)]
+        res = (CGResult * cnt)()
+        for i in range(cnt):
+            res[i].col_iterations = its[i].ctypes.data_as(C.POINTER(C.c_int32))
+            res[i].rel_residual = rels[i].ctypes.data_as(C.POINTER(C.c_double))
+        rc = lib().h2_batch_block_cg(self.handle, bp, lb, xp, lx, mb, C.byref(prm), res)
+        _check(rc, "h2_batch_block_cg", ok=(H2_OK, H2_E_NOCONVERGE, H2_E_BREAKDOWN))
+        return [SolveResult(res[i].status, res[i].iterations, res[i].outer_steps, res[i].h2mm_calls,
+                            its[i][: mb[i]].copy(), rels[i][: mb[i]].copy(), res[i].seconds) for i in range(cnt)]
+
+    def close(self):
+        if self.handle:
+            lib().h2_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def h2_tree_build(points, leaf_size=64, eta=2.0, q=3) -> dict:

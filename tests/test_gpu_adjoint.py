@@ -83,7 +83,8 @@ def test_autograd_matches_finite_differences(case):
         O.set_coupling(H, S)
         H.sigma = sig
         A = O.dense_expand(H)
-        X = sla.cho_solve(sla.cho_factor(A), Bm)
+        # LU, not Cholesky: perturbing one S_b makes A non-symmetric
+        X = np.linalg.solve(A, Bm)
         return float(np.sum((X - Xt) ** 2))
 
     # ∂L/∂σ
