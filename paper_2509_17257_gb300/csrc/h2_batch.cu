@@ -82,6 +82,9 @@ int h2_batch_create(h2_matrix* const* mats, int32_t count, h2_batch** out) {
     b->streams.resize(count, nullptr);
     b->join.resize(count, nullptr);
     cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
         e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
@@ -101,6 +104,9 @@ int h2_batch_free(h2_batch* b) {
     for (auto s : b->streams) if (s) cudaStreamDestroy(s);
     for (auto e : b->join) if (e) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->origin) cudaStreamDestroy(b->origin);
     delete b;
     return 0;
 }
@@ -129,19 +135,24 @@ int h2_batch_matmul(h2_batch* b, double alpha, const double* const* X, const int
         key.insert(key.end(), {i, (int64_t)(uintptr_t)X[i], ldx[i], (int64_t)(uintptr_t)Y[i], ldy[i], m[i]});
     }
     if (sys.empty()) return 0;
+    // the graph runs on the batch's own stream, ordered after and before the caller's stream
+    H2_CUDA_TRY(cudaEventRecord(b->ev_in, st));
+    H2_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
     if (!b->mm_exec || key != b->mm_key) {
         if (b->mm_exec) { cudaGraphExecDestroy(b->mm_exec); b->mm_exec = nullptr; }
         for (int i : sys) {
-            int rc = product_prepare(b->mats[i], m[i], dtype, st);
+            int rc = product_prepare(b->mats[i], m[i], dtype, b->origin);
             if (rc) return rc;
         }
-        H2_CUDA_TRY(cudaStreamSynchronize(st));
+        H2_CUDA_TRY(cudaStreamSynchronize(b->origin));
         MmCtx ctx{b, alpha, X, ldx, Y, ldy, m, dtype};
-        int rc = batch_capture(b, st, sys, mm_body, &ctx, &b->mm_exec);
+        int rc = batch_capture(b, b->origin, sys, mm_body, &ctx, &b->mm_exec);
         if (rc) return rc;
         b->mm_key = key;
     }
-    H2_CUDA_TRY(cudaGraphLaunch(b->mm_exec, st));
+    H2_CUDA_TRY(cudaGraphLaunch(b->mm_exec, b->origin));
+    H2_CUDA_TRY(cudaEventRecord(b->ev_out, b->origin));
+    H2_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_out, 0));
     return 0;
 }
 

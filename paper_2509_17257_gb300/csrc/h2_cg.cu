@@ -517,7 +517,11 @@ int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, doub
     if (dtype != H2_F64 && dtype != H2_F32 && dtype != H2_BF16) { set_error("bad dtype"); return H2_E_BADARG; }
     if (p->transposed) { set_error("batched solves take A, not Aᵀ"); return H2_E_UNSUPPORTED; }
     const int count = (int)b->mats.size();
-    cudaStream_t st = (cudaStream_t)p->stream;
+    // graphs are captured on and launched from the batch's own stream, after the caller's work
+    H2_CUDA_TRY(cudaEventRecord(b->ev_in, (cudaStream_t)p->stream));
+    H2_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
+    cudaStream_t st = b->origin;
+    for (auto si : b->streams) H2_CUDA_TRY(cudaStreamWaitEvent(si, b->ev_in, 0));
     auto t0 = std::chrono::steady_clock::now();
     std::vector<BatchSys> sys(count);
     std::vector<std::unique_ptr<Solver>> solvers;

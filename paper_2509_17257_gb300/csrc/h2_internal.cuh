@@ -18,6 +18,7 @@ void set_error(const std::string& msg);
     do {                                                                                   \
         cudaError_t e_ = (expr);                                                           \
         if (e_ != cudaSuccess) {                                                           \
+            cudaGetLastError(); /* do not leave it for the next launch check */            \
             ::h2::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));            \
             return e_ == cudaErrorMemoryAllocation ? H2_E_OOM : H2_E_CUDA;                 \
         }                                                                                  \
@@ -204,6 +205,8 @@ struct h2_batch {
     std::vector<cudaStream_t> streams;  // one per system: branches of the captured graphs
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
+    cudaStream_t origin = nullptr;  // non-blocking stream the graphs are captured on and launched from
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t mm_exec = nullptr;  // cached product graph
     std::vector<int64_t> mm_key;
 };

@@ -26,7 +26,9 @@ namespace {
 constexpr int kThreads = 256;  // 16 × 16 thread grid per CTA
 constexpr int kKC = 32;        // K chunk staged in shared memory
 
-// Per-thread register tile: rows ty + 16·r (r < RM), columns tx + 16·c (c < CN).
+// Per-thread register tile: rows RM·ty + r (r < RM), columns CN·tx + c (c < CN),
+// ty = thread / 16, tx = thread % 16; the RM rows and the CN columns of one
+// thread are contiguous in shared memory, so one vector load fetches each.
 template <typename T, int RM, int CN>
 struct Acc {
     T v[RM][CN];
@@ -40,9 +42,37 @@ struct Acc {
 
 template <typename T, int RM, int CN>
 struct Smem {
-    T a[kKC][16 * RM + 1];
-    T b[kKC][16 * CN];
+    alignas(16) T a[kKC][16 * RM + 4];  // [k][row]; +4 keeps rows 16-byte aligned
+    alignas(16) T b[kKC][16 * CN];      // [k][column]
 };
+
+// Vector loads of n consecutive values from 16-byte-aligned shared memory.
+template <int N>
+__device__ __forceinline__ void lds_vec(const float* p, float (&v)[N]) {
+    if constexpr (N == 4) {
+        const float4 x = *(const float4*)p;
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else if constexpr (N == 2) {
+        const float2 x = *(const float2*)p;
+        v[0] = x.x; v[1] = x.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = p[i];
+    }
+}
+template <int N>
+__device__ __forceinline__ void lds_vec(const double* p, double (&v)[N]) {
+    if constexpr (N % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < N; i += 2) {
+            const double2 x = *(const double2*)(p + i);
+            v[i] = x.x; v[i + 1] = x.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = p[i];
+    }
+}
 
 // acc += op(A)[row0 : row0+16RM, 0:K] · B[0:K, col0 : col0+16CN]
 // op(A) = A (A is M×K row-major, leading dimension lda) or, with TA, Aᵀ
@@ -81,10 +111,8 @@ __device__ __forceinline__ void mac(Acc<T, RM, CN>& acc, Smem<T, RM, CN>& sm, co
 #pragma unroll 4
         for (int kk = 0; kk < kc; ++kk) {
             T a[RM], b[CN];
-#pragma unroll
-            for (int r = 0; r < RM; ++r) a[r] = sm.a[kk][ty + 16 * r];
-#pragma unroll
-            for (int c = 0; c < CN; ++c) b[c] = sm.b[kk][tx + 16 * c];
+            lds_vec<RM>(&sm.a[kk][RM * ty], a);
+            lds_vec<CN>(&sm.b[kk][CN * tx], b);
 #pragma unroll
             for (int r = 0; r < RM; ++r)
 #pragma unroll
@@ -99,11 +127,11 @@ __device__ __forceinline__ void store_tile(const Acc<T, RM, CN>& acc, T* __restr
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
     for (int r = 0; r < RM; ++r) {
-        const int gr = row0 + ty + 16 * r;
+        const int gr = row0 + RM * ty + r;
         if (gr >= M) continue;
 #pragma unroll
         for (int c = 0; c < CN; ++c) {
-            const int gc = col0 + tx + 16 * c;
+            const int gc = col0 + CN * tx + c;
             if (gc >= ncol) continue;
             T* p = C + (int64_t)gr * ldc + gc;
             if (ACCUM) *p += acc.v[r][c]; else *p = acc.v[r][c];
@@ -345,13 +373,13 @@ __global__ void __launch_bounds__(kThreads) k_leaf_bwd_near(
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
     for (int r = 0; r < RM; ++r) {
-        const int i = row0 + ty + 16 * r;
+        const int i = row0 + RM * ty + r;
         if (i >= nt) continue;
         double* yrow = Y + (int64_t)perm[off + i] * ldy;
         const T* xrow = Xp + (int64_t)(off + i) * m;
 #pragma unroll
         for (int c = 0; c < CN; ++c) {
-            const int gc = col0 + tx + 16 * c;
+            const int gc = col0 + CN * tx + c;
             if (gc >= m) continue;
             const double z = (double)acc.v[r][c] + sigma * (double)xrow[gc];
             if (overwrite) yrow[gc] = alpha * z; else yrow[gc] += alpha * z;

@@ -62,15 +62,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
         if (mbar_try(b, parity)) return true;
     return false;
 }
-// Warp-level wait: only lane 0 polls the barrier (many polling threads slow the
-// barrier unit that the bulk copies and MMA commits also update); the result
-// and the ordering reach the other lanes through __syncwarp / a shuffle.
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity) {
-    int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(b, parity) ? 1 : 0;
-    __syncwarp();
-    return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
 }
@@ -413,7 +404,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             }
             const int id = cur.id, np = cur.np;
             const int acc = it & 1;
-            const bool ok = mbar_wait_warp(&accf_bar[acc], (it >> 1) & 1);
+            // warp-uniform wait: a completed phase stays completed, so any lane's
+            // success is the warp's success
+            const bool ok = __any_sync(0xffffffffu, mbar_wait(&accf_bar[acc], (it >> 1) & 1));
             if (!ok) {
                 if (lane == 0) atomicExch(p.err, 6);
                 abort_flag = 1;
@@ -457,7 +450,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
         int stage = 0;
         uint32_t phase = 0;
         while (true) {
-            const bool ok = mbar_wait_warp(&full_bar[stage], phase);
+            const bool ok = __any_sync(0xffffffffu, mbar_wait(&full_bar[stage], phase));
             if (!ok) {
                 if (lane == 0) atomicExch(p.err, 7);
                 abort_flag = 1;
