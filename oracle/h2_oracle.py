@@ -58,6 +58,8 @@ __all__ = [
     "CGResult",
     "adjoint_grads",
     "set_coupling",
+    "block_jacobi",
+    "block_pcg",
 ]
 
 
@@ -540,3 +542,77 @@ def set_coupling(H: H2Matrix, S_by_pair: dict):
     """Replace the coupling matrices S_b, keyed by (t.id, s.id)."""
     for b in H.adm:
         b.S = np.array(S_by_pair[(b.t.id, b.s.id)], dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Preconditioned block CG (Sec. 5.1, Alg. "pcg block") with a block-Jacobi M
+# ---------------------------------------------------------------------------
+def block_jacobi(H: H2Matrix):
+    """M = blockdiag over the leaves t of D_t = G_{(t,t)} + σI (the diagonal
+    inadmissible blocks with the shift).  Returns a function r ↦ M⁻¹ r."""
+    diag = {}
+    for b in H.near:
+        if b.t.id == b.s.id:
+            D = b.G + H.sigma * np.eye(b.t.size)
+            diag[b.t.id] = (b.t.idx, np.linalg.inv(D))
+
+    def apply(R):
+        R = np.asarray(R, dtype=np.float64)
+        Z = np.zeros_like(R)
+        for idx, Dinv in diag.values():
+            Z[idx] = Dinv @ R[idx]
+        return Z
+
+    return apply
+
+
+def block_pcg(apply_A, apply_Minv, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8,
+              max_iter: int = 10000) -> CGResult:
+    """Alg. "pcg block": r = b - Ax, q = M⁻¹r, p = q (the listing's initial
+    p ← r is read as p ← q, the standard start); per iteration a = Ap,
+    β_i = <p_i, a_i>, α_i = <p_i, r_i>/β_i, x_i += α_i p_i, r_i -= α_i a_i,
+    q = M⁻¹ r, γ_i = <a_i, q_i>/β_i, p_i = q_i - γ_i p_i.  Stopping as in
+    block_cg (relative residual per column, converged columns frozen)."""
+    B = np.asarray(B, dtype=np.float64)
+    n, m = B.shape
+    X = np.zeros((n, m), order="F") if X0 is None else np.array(X0, dtype=np.float64, order="F")
+    R = np.asfortranarray(B - apply_A(X))
+    Q = np.asfortranarray(apply_Minv(R))
+    P = Q.copy(order="F")
+    bn = np.linalg.norm(B, axis=0)
+    bn[bn == 0.0] = 1.0
+    done = np.linalg.norm(R, axis=0) / bn <= tol
+    col_it = np.zeros(m, dtype=np.int64)
+    it = 0
+    status = "converged"
+    while not done.all():
+        if it >= max_iter:
+            status = "noconverge"
+            break
+        Aq = np.asfortranarray(apply_A(P))
+        it += 1
+        alpha = np.zeros(m)
+        beta = np.ones(m)
+        for i in range(m):
+            if done[i]:
+                continue
+            beta[i] = float(P[:, i] @ Aq[:, i])
+            if not (beta[i] > 0.0) or not math.isfinite(beta[i]):
+                status = "breakdown"
+                break
+            alpha[i] = float(P[:, i] @ R[:, i]) / beta[i]
+            X[:, i] += alpha[i] * P[:, i]
+            R[:, i] -= alpha[i] * Aq[:, i]
+            col_it[i] = it
+        if status == "breakdown":
+            break
+        Q = np.asfortranarray(apply_Minv(R))
+        for i in range(m):
+            if done[i]:
+                continue
+            gamma = float(Aq[:, i] @ Q[:, i]) / beta[i]
+            P[:, i] = Q[:, i] - gamma * P[:, i]
+            if np.linalg.norm(R[:, i]) / bn[i] <= tol:
+                done[i] = True
+    rel = np.linalg.norm(R, axis=0) / bn
+    return CGResult(X=X, iterations=it, col_iterations=col_it, rel_residual=rel, status=status)
