@@ -18,10 +18,13 @@ H²-matrices"):
   "fast_addeval", backward transformation) with the coefficient blocks of
   Sec. 4 (x̂_s, ŷ_t in K^{k×m})  -> :func:`h2mm`
 * Sec. 5.1, Alg. "block CG" (per-column α_i, β_i, γ_i) -> :func:`block_cg`
+* the same recurrences with m×m Gram matrices in place of the per-column
+  scalars (O'Leary's block CG; not in the paper)      -> :func:`block_cg_gram`
+* Sec. 5.1, Alg. "pcg block" with a block-Jacobi M  -> :func:`block_pcg`
 
 Readings where the paper is silent (split rule, diam/dist of point boxes,
 interpolation nodes, kernel, shift, stopping rule) are the ones stated in the
-docstrings below; the same readings are listed in the design doc.
+docstrings below.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute force or library routines (see each test).  The
@@ -60,6 +63,8 @@ __all__ = [
     "set_coupling",
     "block_jacobi",
     "block_pcg",
+    "block_cg_gram",
+    "GRAM_DEFLATE",
 ]
 
 
@@ -513,6 +518,117 @@ def block_cg(apply_A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 
             if np.linalg.norm(r) / bn[i] <= tol:
                 done[i] = True
         if status == "breakdown":
+            break
+    rel = np.linalg.norm(R, axis=0) / bn
+    return CGResult(X=X, iterations=it, col_iterations=col_it, rel_residual=rel, status=status)
+
+
+# ---------------------------------------------------------------------------
+# Block CG with m×m Gram matrices (O'Leary's block CG, written in the same
+# conjugacy form as Alg. "CG": the scalars become m×m matrices)
+# ---------------------------------------------------------------------------
+GRAM_DEFLATE = 1e-10  # a direction is dropped when its Cholesky pivot is below this fraction of its diagonal
+
+
+def _chol_deflate(G: np.ndarray, cols):
+    """Cholesky G_KK = L Lᵀ over the columns K ⊆ cols that survive deflation.
+
+    Pivots are taken in index order.  Column j is kept when its Schur pivot
+    d_j = G_jj − Σ_{k∈K, k<j} L_jk² exceeds GRAM_DEFLATE·G_jj (p_j is then not
+    A-dependent on the directions kept before it); otherwise it is dropped.
+    G_jj <= 0 (or non-finite) means <p_j, A p_j> <= 0: breakdown, as for the
+    scalar CG.  Returns (L restricted to K as an m×m array with zeros
+    elsewhere, K as a list, breakdown flag)."""
+    m = G.shape[0]
+    L = np.zeros((m, m))
+    K = []
+    for j in cols:
+        gjj = G[j, j]
+        if not (gjj > 0.0) or not math.isfinite(gjj):
+            return L, K, True
+        d = gjj - sum(L[j, k] ** 2 for k in K)
+        if not (d > GRAM_DEFLATE * gjj):
+            continue
+        L[j, j] = math.sqrt(d)
+        for i in range(j + 1, m):
+            L[i, j] = (G[i, j] - sum(L[i, k] * L[j, k] for k in K)) / L[j, j]
+        K.append(j)
+    return L, K, False
+
+
+def _chol_solve(L: np.ndarray, K, Wcol: np.ndarray) -> np.ndarray:
+    """y = G_KK⁻¹ w_K by forward then backward substitution; zero off K."""
+    m = L.shape[0]
+    z = np.zeros(m)
+    for a, j in enumerate(K):
+        z[j] = (Wcol[j] - sum(L[j, k] * z[k] for k in K[:a])) / L[j, j]
+    y = np.zeros(m)
+    for a in range(len(K) - 1, -1, -1):
+        j = K[a]
+        y[j] = (z[j] - sum(L[k, j] * y[k] for k in K[a + 1:])) / L[j, j]
+    return y
+
+
+def block_cg_gram(apply_A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8,
+                  max_iter: int = 10000) -> CGResult:
+    """Block CG with m×m Gram matrices (O'Leary 1980), the block form of the
+    scalar recurrences of Alg. "CG":
+
+        Q = A P,   G = Pᵀ Q,   W = Pᵀ R,   α = G⁻¹ W,
+        X += P α,  R −= Q α,   Γ = G⁻¹ (Qᵀ R),   P = R − P Γ.
+
+    G⁻¹ is applied through a Cholesky factor of G with deflation
+    (:func:`_chol_deflate`): a direction that has become A-dependent on the
+    others is dropped for this step.  The stopping rule is the one of
+    :func:`block_cg`: column i leaves the active set 𝒜 once
+    ||r_i||/||b_i|| <= tol and is frozen from then on (its columns of α and Γ
+    are zero and its direction is zero).  With m = 1 this is Alg. "CG".
+    """
+    B = np.asarray(B, dtype=np.float64)
+    n, m = B.shape
+    X = np.zeros((n, m)) if X0 is None else np.array(X0, dtype=np.float64)
+    R = B - apply_A(X)
+    P = R.copy()
+    bn = np.linalg.norm(B, axis=0)
+    bn[bn == 0.0] = 1.0
+    active = np.linalg.norm(R, axis=0) / bn > tol
+    P[:, ~active] = 0.0
+    col_it = np.zeros(m, dtype=np.int64)
+    it = 0
+    status = "converged"
+    while active.any():
+        if it >= max_iter:
+            status = "noconverge"
+            break
+        Q = apply_A(P)
+        it += 1
+        cols = [j for j in range(m) if active[j]]
+        G = P.T @ Q
+        W = P.T @ R
+        L, K, broke = _chol_deflate(G, cols)
+        if broke or not np.all(np.isfinite(G)):
+            status = "breakdown"
+            break
+        alpha = np.zeros((m, m))
+        for j in cols:
+            alpha[:, j] = _chol_solve(L, K, W[:, j])
+        X += P @ alpha
+        R -= Q @ alpha
+        rn = np.linalg.norm(R, axis=0) / bn
+        for j in cols:
+            col_it[j] = it
+            if rn[j] <= tol:
+                active[j] = False
+        C = Q.T @ R
+        Gamma = np.zeros((m, m))
+        for j in range(m):
+            if active[j]:
+                Gamma[:, j] = _chol_solve(L, K, C[:, j])
+        Pn = R - P @ Gamma
+        Pn[:, ~active] = 0.0
+        P = Pn
+        if not np.all(np.isfinite(P)):
+            status = "breakdown"
             break
     rel = np.linalg.norm(R, axis=0) / bn
     return CGResult(X=X, iterations=it, col_iterations=col_it, rel_residual=rel, status=status)
