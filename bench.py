@@ -301,13 +301,17 @@ def run_ours(args):
     if not args.no_solve:
         solve = {}
         B = torch.from_numpy(gaussian_rhs(n, m, cfg["rhs_seed"] + 1000 * rank + 7)).to(dev)
-        for name, inner, refine, itol in (("mixed_f32", "f32", 2, 0.1), ("mixed_f32_restarted", "f32", 1, 1e-4),
-                                           ("fp64", "f64", 0, 0.0)):
+        runs = (("mixed_f32", "f32", 2, 0.1, "columnwise"), ("mixed_f32_restarted", "f32", 1, 1e-4, "columnwise"),
+                ("fp64", "f64", 0, 0.0, "columnwise"), ("mixed_f32_gram", "f32", 2, 0.1, "gram"),
+                ("fp64_gram", "f64", 0, 0.0, "gram"))
+        for name, inner, refine, itol, variant in runs:
+            if variant == "gram" and m > 64:
+                continue
             Xs = torch.zeros_like(B)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             r = G.block_cg(B, Xs, tol=1e-8, max_iter=args.solve_max_iter, dtype=inner, refine=refine,
-                           inner_tol=itol, check_every=4)
+                           inner_tol=itol, check_every=4, variant=variant)
             torch.cuda.synchronize()
             solve[name] = {"seconds": round(time.perf_counter() - t0, 3), "status": r.status_name,
                            "iterations": int(r.iterations), "outer_steps": int(r.outer_steps),
@@ -315,6 +319,8 @@ def run_ours(args):
                            "max_true_rel_residual": float(np.max(r.rel_residual))}
         if solve["fp64"]["seconds"] > 0:
             solve["speedup_mixed_vs_fp64"] = round(solve["fp64"]["seconds"] / solve["mixed_f32"]["seconds"], 3)
+        if "mixed_f32_gram" in solve and solve["mixed_f32_gram"]["seconds"] > 0:
+            solve["speedup_mixed_gram_vs_fp64"] = round(solve["fp64"]["seconds"] / solve["mixed_f32_gram"]["seconds"], 3)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -171,7 +171,14 @@ int h2_timing_query(h2_matrix* A, double* ms, int64_t* calls, int32_t reset);
 
 /* ---- block CG (Sec. 5.1, Alg. "block CG") ------------------------------- */
 typedef enum h2_cg_variant {
-    H2_CG_COLUMNWISE = 0 /* the paper's block CG: per-column α_i, β_i, γ_i */
+    H2_CG_COLUMNWISE = 0, /* the paper's block CG: per-column α_i, β_i, γ_i                           */
+    H2_CG_GRAM = 1        /* O'Leary's block CG (not in the paper): the same recurrences with m×m Gram
+                             matrices, G = Pᵀ(AP), α = G⁻¹ PᵀR, X += Pα, R -= (AP)α, Γ = G⁻¹ (AP)ᵀR,
+                             P = R - PΓ; G⁻¹ through a Cholesky factor of G that drops a direction whose
+                             pivot is below 1e-10 of its diagonal (deflation).  All Gram matrices, the
+                             Cholesky factor and the step solves are FP64 on the device.  Every column
+                             searches the whole block Krylov space, so it needs fewer iterations than
+                             COLUMNWISE.  1 <= m <= 64 (H2_E_UNSUPPORTED otherwise).                 */
 } h2_cg_variant;
 
 typedef struct h2_cg_params {

@@ -28,19 +28,6 @@ namespace {
 constexpr int kRowBlocks = 304;  // CTAs along the rows: 2 per SM on a 152-SM part
 constexpr int kColsPerCta = 32;
 
-struct CgDev {
-    double* bnorm;   // [m] |b_i| (1 when 0)
-    double* alpha;   // [m]
-    double* beta;    // [m]
-    double* gamma;   // [m]
-    double* rnorm;   // [m] |r_i| after the last update
-    int* active;     // [m] 1 while column i has not converged
-    int* conv_iter;  // [m]
-    int* summary;    // [0] = active columns, [1] = breakdown flag
-    double* partial; // [kRowBlocks][m][2]
-    unsigned* ticket;// [ceil(m/32)]
-};
-
 // Column norms |B_i| and the initial activity flags.
 __global__ void k_cg_init(const double* __restrict__ B, int64_t ldb, const double* __restrict__ R, int64_t ldr,
                           int64_t n, int m, double tol, CgDev d) {
@@ -282,7 +269,9 @@ struct Solver {
     int64_t n;
     int m;
     bool trans = false;  // products with Aᵀ (adjoint solve)
+    bool gram = false;   // variant H2_CG_GRAM (m <= 64)
     CgDev d{};
+    GramDev g{};
     double *R = nullptr, *P = nullptr, *AP = nullptr;
     int* h_summary = nullptr;  // pinned
     void* mem = nullptr;
@@ -302,6 +291,15 @@ struct Solver {
         const size_t oAct = piece(m * sizeof(int)), oCi = piece(m * sizeof(int)), oSum = piece(4 * sizeof(int));
         const size_t oPart = piece((size_t)kRowBlocks * m * 2 * sizeof(double));
         const size_t oTk = piece(groups * sizeof(unsigned));
+        if (gram && m > kGramMaxCols) {
+            set_error("the Gram-matrix block CG takes at most 64 columns");
+            return H2_E_UNSUPPORTED;
+        }
+        const size_t oGram = gram ? piece(gram_scratch_bytes(m)) : 0;
+        if (gram) {
+            int rc = gram_prepare();
+            if (rc) return rc;
+        }
         H2_CUDA_TRY(cudaMallocAsync(&mem, off, st));
         char* p = (char*)mem;
         R = (double*)(p + oR);
@@ -317,6 +315,7 @@ struct Solver {
         d.summary = (int*)(p + oSum);
         d.partial = (double*)(p + oPart);
         d.ticket = (unsigned*)(p + oTk);
+        if (gram) gram_carve(&g, p + oGram, m);
         H2_CUDA_TRY(cudaMemsetAsync(d.ticket, 0, groups * sizeof(unsigned), st));
         H2_CUDA_TRY(cudaHostAlloc(&h_summary, 4 * sizeof(int), cudaHostAllocDefault));
         return 0;
@@ -343,6 +342,7 @@ struct Solver {
     // Convergence is decided on the true residual.  R must hold B - A X.
     int cg_reliable(int32_t dtype, const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int max_iter,
                     int check_every, double delta, double* Rt, double* rupd, int* iters, int* updates) {
+        if (gram) return cg_gram(dtype, B, ldb, X, ldx, tol, max_iter, check_every, delta, Rt, rupd, iters, updates);
         const dim3 blk(kColsPerCta, 8);
         const dim3 grid(kRowBlocks, (m + kColsPerCta - 1) / kColsPerCta);
         H2_CUDA_TRY(cudaMemsetAsync(d.summary, 0, 4 * sizeof(int), st));
@@ -406,6 +406,10 @@ struct Solver {
     // Returns 0 / H2_E_BREAKDOWN / H2_E_NOCONVERGE; *iters = iterations run.
     int cg(int32_t dtype, const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int max_iter,
            int check_every, int* iters) {
+        if (gram) {
+            int upd = 0;
+            return cg_gram(dtype, B, ldb, X, ldx, tol, max_iter, check_every, 0.0, nullptr, nullptr, iters, &upd);
+        }
         const dim3 blk(kColsPerCta, 8);
         const dim3 grid(kRowBlocks, (m + kColsPerCta - 1) / kColsPerCta);
         H2_CUDA_TRY(cudaMemsetAsync(d.summary, 0, 4 * sizeof(int), st));
@@ -462,6 +466,87 @@ struct Solver {
         *iters = status == 0 ? mx : it;
         return status;
     }
+
+    // Replace the recurrence residuals by the true FP64 residual Rt = B - A X
+    // (reliable update, see cg_reliable); the Gram variant also clears the
+    // directions of columns that left the active set.
+    int reliable_update(const double* B, int64_t ldb, const double* X, int64_t ldx, double tol, double* Rt,
+                        double* rupd) {
+        const dim3 blk(kColsPerCta, 8);
+        const dim3 grid(kRowBlocks, (m + kColsPerCta - 1) / kColsPerCta);
+        k_copy2d<<<copy_grid(), 256, 0, st>>>(B, ldb, Rt, m, n, m);
+        H2_LAUNCH_CHECK();
+        ++h2mm_calls;
+        int rc = matmul_device(A, -1.0, X, ldx, Rt, m, m, H2_F64, st, trans, false);
+        if (rc) return rc;
+        H2_CUDA_TRY(cudaMemsetAsync(d.summary, 0, sizeof(int), st));
+        k_cg_reliable<<<grid, blk, 0, st>>>(Rt, R, P, m, n, m, tol, rupd, d);
+        H2_LAUNCH_CHECK();
+        k_cg_reliable_copy<<<grid, blk, 0, st>>>(Rt, R, P, m, n, m, d);
+        H2_LAUNCH_CHECK();
+        k_cg_reliable_flags<<<(m + 63) / 64, 64, 0, st>>>(m, d);
+        H2_LAUNCH_CHECK();
+        if (gram && (rc = gram_mask(P, n, m, d, st))) return rc;
+        return 0;
+    }
+
+    // Gram-matrix block CG (variant H2_CG_GRAM, h2_gram.cu) on A_dtype X = B
+    // with R holding B - A X.  With Rt != nullptr the recurrence residuals are
+    // replaced by the FP64 residual as in cg_reliable (convergence is then
+    // decided on the true residual).
+    int cg_gram(int32_t dtype, const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int max_iter,
+                int check_every, double delta, double* Rt, double* rupd, int* iters, int* updates) {
+        H2_CUDA_TRY(cudaMemsetAsync(d.summary, 0, 4 * sizeof(int), st));
+        k_cg_init<<<(m + 63) / 64, 64, 0, st>>>(B, ldb, R, m, n, m, tol, d);
+        H2_LAUNCH_CHECK();
+        int rc = gram_start(P, R, n, m, g, d, st);
+        if (rc) return rc;
+        if (Rt) H2_CUDA_TRY(cudaMemcpyAsync(rupd, d.rnorm, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        H2_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<double> rn(m), ru(m);
+        std::vector<int> act(m);
+        int it = 0, status = 0;
+        *updates = 0;
+        if (h_summary[0] > 0) {
+            for (it = 1; it <= max_iter; ++it) {
+                ++h2mm_calls;
+                if ((rc = matmul_device(A, 1.0, P, m, AP, m, m, dtype, st, trans, true))) return rc;
+                if ((rc = gram_alpha(P, AP, R, n, m, g, d, st))) return rc;
+                if ((rc = gram_update_dir(X, ldx, P, AP, R, n, m, tol, g, d, st))) return rc;
+                if (it % check_every != 0 && it != max_iter) continue;
+                H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                if (Rt) {
+                    H2_CUDA_TRY(cudaMemcpyAsync(rn.data(), d.rnorm, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+                    H2_CUDA_TRY(cudaMemcpyAsync(ru.data(), rupd, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+                    H2_CUDA_TRY(cudaMemcpyAsync(act.data(), d.active, m * sizeof(int), cudaMemcpyDeviceToHost, st));
+                }
+                H2_CUDA_TRY(cudaStreamSynchronize(st));
+                if (h_summary[1]) { status = H2_E_BREAKDOWN; break; }
+                if (!Rt) {
+                    if (h_summary[0] == 0) break;
+                    continue;
+                }
+                bool update = h_summary[0] == 0;
+                for (int i = 0; i < m && !update; ++i) update = act[i] && rn[i] < delta * ru[i];
+                if (!update) continue;
+                ++*updates;
+                if ((rc = reliable_update(B, ldb, X, ldx, tol, Rt, rupd))) return rc;
+                H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                H2_CUDA_TRY(cudaStreamSynchronize(st));
+                if (h_summary[1]) { status = H2_E_BREAKDOWN; break; }
+                if (h_summary[0] == 0) break;
+            }
+            if (it > max_iter) { it = max_iter; status = H2_E_NOCONVERGE; }
+        }
+        std::vector<int> ci(m);
+        H2_CUDA_TRY(cudaMemcpyAsync(ci.data(), d.conv_iter, m * sizeof(int), cudaMemcpyDeviceToHost, st));
+        H2_CUDA_TRY(cudaStreamSynchronize(st));
+        int mx = 0;
+        for (int v : ci) mx = std::max(mx, v);
+        *iters = (status == 0 && !Rt) ? mx : it;
+        return status;
+    }
 };
 
 }  // namespace
@@ -493,6 +578,12 @@ struct BatchIterCtx {
 int batch_iter_body(void* ctx, int i, cudaStream_t st) {
     BatchIterCtx* c = (BatchIterCtx*)ctx;
     Solver& S = *(*c->sys)[i].S;
+    if (S.gram) {
+        int rc = matmul_device(S.A, 1.0, S.P, S.m, S.AP, S.m, S.m, c->dtype, st, false, true);
+        if (rc) return rc;
+        if ((rc = gram_alpha(S.P, S.AP, S.R, S.n, S.m, S.g, S.d, st))) return rc;
+        return gram_update_dir((*c->sys)[i].X, (*c->sys)[i].ldx, S.P, S.AP, S.R, S.n, S.m, c->tol, S.g, S.d, st);
+    }
     const dim3 blk(kColsPerCta, 8);
     const dim3 grid(kRowBlocks, (S.m + kColsPerCta - 1) / kColsPerCta);
     int rc = matmul_device(S.A, 1.0, S.P, S.m, S.AP, S.m, S.m, c->dtype, st, false, true);
@@ -516,6 +607,8 @@ int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, doub
     const int32_t dtype = p->dtype;
     if (dtype != H2_F64 && dtype != H2_F32 && dtype != H2_BF16) { set_error("bad dtype"); return H2_E_BADARG; }
     if (p->transposed) { set_error("batched solves take A, not Aᵀ"); return H2_E_UNSUPPORTED; }
+    if (p->variant != H2_CG_COLUMNWISE && p->variant != H2_CG_GRAM) { set_error("unsupported CG variant"); return H2_E_UNSUPPORTED; }
+    const bool gram = p->variant == H2_CG_GRAM;
     const int count = (int)b->mats.size();
     // graphs are captured on and launched from the batch's own stream, after the caller's work
     H2_CUDA_TRY(cudaEventRecord(b->ev_in, (cudaStream_t)p->stream));
@@ -536,6 +629,10 @@ int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, doub
             return H2_E_BADARG;
         }
         if (b->mats[i]->timing.on) { set_error("disable timing on batched matrices"); return H2_E_UNSUPPORTED; }
+        if (gram && m[i] > kGramMaxCols) {
+            set_error("the Gram-matrix block CG (H2_CG_GRAM) takes at most 64 columns per system");
+            return H2_E_UNSUPPORTED;
+        }
     }
     const double delta = p->inner_tol > 0.0 && p->inner_tol < 1.0 ? p->inner_tol : 0.1;
     const bool reliable = dtype != H2_F64;
@@ -546,6 +643,7 @@ int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, doub
         cudaStream_t si = b->streams[i];
         solvers.emplace_back(new Solver{A, si, A->n, (int)m[i]});
         Solver& S = *solvers.back();
+        S.gram = gram;
         sys[i].S = &S;
         sys[i].B = B[i];
         sys[i].ldb = ldb[i];
@@ -561,8 +659,12 @@ int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, doub
         H2_CUDA_TRY(cudaMemsetAsync(S.d.summary, 0, 4 * sizeof(int), si));
         k_cg_init<<<(int)((m[i] + 63) / 64), 64, 0, si>>>(B[i], ldb[i], S.R, m[i], A->n, (int)m[i], p->tol, S.d);
         H2_LAUNCH_CHECK();
-        k_copy2d<<<S.copy_grid(), 256, 0, si>>>(S.R, m[i], S.P, m[i], A->n, (int)m[i]);
-        H2_LAUNCH_CHECK();
+        if (gram) {
+            if ((rc = gram_start(S.P, S.R, A->n, (int)m[i], S.g, S.d, si))) return rc;
+        } else {
+            k_copy2d<<<S.copy_grid(), 256, 0, si>>>(S.R, m[i], S.P, m[i], A->n, (int)m[i]);
+            H2_LAUNCH_CHECK();
+        }
         H2_CUDA_TRY(cudaMemcpyAsync(sys[i].rupd, S.d.rnorm, m[i] * sizeof(double), cudaMemcpyDeviceToDevice, si));
         H2_CUDA_TRY(cudaMemcpyAsync(S.h_summary, S.d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, si));
     }
@@ -612,20 +714,8 @@ int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, doub
             if (!update) { all = false; continue; }
             if (!reliable) { y.done = true; ++done_since_build; continue; }
             // true FP64 residual replaces the recurrence residual (eager, off the graph)
-            const dim3 blk(kColsPerCta, 8);
-            const dim3 grid(kRowBlocks, (mi + kColsPerCta - 1) / kColsPerCta);
-            k_copy2d<<<S.copy_grid(), 256, 0, si>>>(y.B, y.ldb, y.Rt, mi, S.n, mi);
-            H2_LAUNCH_CHECK();
-            ++S.h2mm_calls;
             ++y.updates;
-            if ((rc = matmul_device(S.A, -1.0, y.X, y.ldx, y.Rt, mi, mi, H2_F64, si, false, false))) return rc;
-            H2_CUDA_TRY(cudaMemsetAsync(S.d.summary, 0, sizeof(int), si));
-            k_cg_reliable<<<grid, blk, 0, si>>>(y.Rt, S.R, S.P, mi, S.n, mi, p->tol, y.rupd, S.d);
-            H2_LAUNCH_CHECK();
-            k_cg_reliable_copy<<<grid, blk, 0, si>>>(y.Rt, S.R, S.P, mi, S.n, mi, S.d);
-            H2_LAUNCH_CHECK();
-            k_cg_reliable_flags<<<(mi + 63) / 64, 64, 0, si>>>(mi, S.d);
-            H2_LAUNCH_CHECK();
+            if ((rc = S.reliable_update(y.B, y.ldb, y.X, y.ldx, p->tol, y.Rt, y.rupd))) return rc;
             H2_CUDA_TRY(cudaMemcpyAsync(S.h_summary, S.d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, si));
             H2_CUDA_TRY(cudaStreamSynchronize(si));
             if (S.h_summary[1]) { y.status = H2_E_BREAKDOWN; y.done = true; ++done_since_build; continue; }
@@ -679,7 +769,11 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
     if (!A || !p || !res) { set_error("null argument"); return H2_E_BADARG; }
     if (m < 0 || (m > 0 && (!B || !X)) || ldb < m || ldx < m) { set_error("bad m / leading dimension"); return H2_E_BADARG; }
     if (!(p->tol >= 0.0) || p->max_iter < 0 || p->check_every < 1) { set_error("bad solver parameters"); return H2_E_BADARG; }
-    if (p->variant != H2_CG_COLUMNWISE) { set_error("unsupported CG variant"); return H2_E_UNSUPPORTED; }
+    if (p->variant != H2_CG_COLUMNWISE && p->variant != H2_CG_GRAM) { set_error("unsupported CG variant"); return H2_E_UNSUPPORTED; }
+    if (p->variant == H2_CG_GRAM && m > kGramMaxCols) {
+        set_error("the Gram-matrix block CG (H2_CG_GRAM) takes at most 64 columns");
+        return H2_E_UNSUPPORTED;
+    }
     const int32_t inner = p->dtype;
     if (inner != H2_F64 && inner != H2_F32 && inner != H2_BF16) { set_error("bad dtype"); return H2_E_BADARG; }
     const bool refine = inner != H2_F64 && p->refine != 0;
@@ -715,6 +809,7 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
     {
         Solver S{A, st, n, (int)m};
         S.trans = p->transposed != 0;
+        S.gram = p->variant == H2_CG_GRAM;
         int rc = S.init();
         if (rc) return rc;
         int total_iters = 0;

@@ -199,6 +199,52 @@ struct h2_matrix {
     std::vector<void*> allocations;
 };
 
+namespace h2 {
+
+// Per-column state of the device block CG (h2_cg.cu, h2_gram.cu).
+struct CgDev {
+    double* bnorm;   // [m] |b_i| (1 when 0)
+    double* alpha;   // [m]
+    double* beta;    // [m]
+    double* gamma;   // [m]
+    double* rnorm;   // [m] |r_i| after the last update
+    int* active;     // [m] 1 while column i has not converged
+    int* conv_iter;  // [m]
+    int* summary;    // [0] = active columns, [1] = breakdown flag
+    double* partial; // [kRowBlocks][m][2]
+    unsigned* ticket;// [ceil(m/32)]
+};
+
+// State of the Gram-matrix block CG (variant H2_CG_GRAM, h2_gram.cu); m <= 64.
+struct GramDev {
+    double* part;      // [kGramCtas][2m² + m] per-CTA partial sums
+    double* G;         // [m×m] Pᵀ(AP)
+    double* W;         // [m×m] PᵀR, then (AP)ᵀR after the update
+    double* L;         // [m×m] Cholesky factor of G on the kept directions (lower triangle)
+    double* alpha;     // [m×m] step  α = G⁻¹ PᵀR
+    double* gamma;     // [m×m] direction coefficients  Γ = G⁻¹ (AP)ᵀR
+    double* rr;        // [m] |r_j|² after the update
+    int* kept;         // [m] direction j kept by the deflating Cholesky
+    unsigned* ticket;  // [1]
+};
+
+constexpr int kGramMaxCols = 64;
+size_t gram_scratch_bytes(int m);
+void gram_carve(GramDev* g, void* base, int m);
+int gram_prepare();
+// P = R on active columns, 0 elsewhere (the first direction block).
+int gram_start(double* P, const double* R, int64_t n, int m, const GramDev& g, const CgDev& d, cudaStream_t st);
+// After AP = A P: G = PᵀAP, W = PᵀR, the deflating Cholesky of G and α = G⁻¹W.
+int gram_alpha(const double* P, const double* AP, const double* R, int64_t n, int m, const GramDev& g,
+               const CgDev& d, cudaStream_t st);
+// X += Pα, R -= (AP)α, column norms and convergence, Γ = G⁻¹(AP)ᵀR, P = R - PΓ.
+int gram_update_dir(double* X, int64_t ldx, double* P, const double* AP, double* R, int64_t n, int m, double tol,
+                    const GramDev& g, const CgDev& d, cudaStream_t st);
+// Zero the directions of inactive columns (after a reliable update).
+int gram_mask(double* P, int64_t n, int m, const CgDev& d, cudaStream_t st);
+
+}  // namespace h2
+
 // A group of independent systems (h2_batch.cu, h2_cg.cu).
 struct h2_batch {
     std::vector<h2_matrix*> mats;

@@ -31,6 +31,8 @@ H2_E_UNSUPPORTED = -7
 H2_F64, H2_F32, H2_BF16 = 0, 1, 2
 DTYPES = {"f64": H2_F64, "f32": H2_F32, "bf16": H2_BF16}
 H2_CG_COLUMNWISE = 0
+H2_CG_GRAM = 1
+VARIANTS = {"columnwise": H2_CG_COLUMNWISE, "gram": H2_CG_GRAM}
 
 _STATUS = {0: "ok", -1: "badarg", -2: "cuda", -3: "noconverge", -4: "breakdown", -5: "timeout", -6: "oom",
            -7: "unsupported"}
@@ -326,6 +328,7 @@ def h2_block_cg(handle, B, X, tol=1e-8, max_iter=20000, dtype="f64", refine=True
     it = np.zeros(max(m, 1), dtype=np.int32)
     rel = np.zeros(max(m, 1), dtype=np.float64)
     dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     prm = CGParams(tol, max_iter, variant, dt, int(refine), inner_tol, max_outer, check_every,
                    1 if transposed else 0, _stream_ptr(stream))
     res = CGResult(0, 0, 0, 0, it.ctypes.data_as(C.POINTER(C.c_int32)), rel.ctypes.data_as(C.POINTER(C.c_double)),
@@ -373,12 +376,13 @@ class H2Batch:
         return Ys
 
     def block_cg(self, Bs, Xs, tol=1e-8, max_iter=20000, dtype="f32", inner_tol=0.1, check_every=4,
-                 stream=None):
+                 variant="columnwise", stream=None):
         bp, lb, mb, kb = self._ptrs(Bs, "B")
         xp, lx, mx, kx = self._ptrs(Xs, "X", True)
         cnt = len(self.mats)
         dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
-        prm = CGParams(tol, max_iter, H2_CG_COLUMNWISE, dt, 2, inner_tol, 0, check_every, 0, _stream_ptr(stream))
+        var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        prm = CGParams(tol, max_iter, var, dt, 2, inner_tol, 0, check_every, 0, _stream_ptr(stream))
         its = [np.zeros(max(int(mb[i]), 1), dtype=np.int32) for i in range(cnt)]
         rels = [np.zeros(max(int(mb[i]), 1)) for i in range(cnt)]
         res = (CGResult * cnt)()

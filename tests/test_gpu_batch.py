@@ -84,3 +84,22 @@ def test_autotune_keeps_products_correct(batch):
     Yd = torch.zeros(sp["n"], sp["m"], dtype=torch.float64, device="cuda")
     mm.matmul(torch.from_numpy(X).cuda(), Yd, dtype="f32")
     assert rel_fro(Yd.cpu().numpy(), want) <= 1e-5
+
+
+def test_batched_block_cg_gram(batch):
+    """The Gram-matrix variant inside the batched graph: every system reaches
+    the FP64 tolerance with the FP32 product and reliable updates."""
+    torch = require_cuda()
+    P, specs, pts, mats = batch
+    B = P.H2Batch(mats)
+    Bs = [torch.from_numpy(gaussian_rhs(sp["n"], sp["m"], 50 + i)).cuda() for i, sp in enumerate(specs)]
+    Xs = [torch.zeros_like(b) for b in Bs]
+    res = B.block_cg(Bs, Xs, tol=1e-8, max_iter=20000, dtype="f32", inner_tol=0.1, check_every=4, variant="gram")
+    for sp, x, b, r, p in zip(specs, Xs, Bs, res, pts):
+        assert r.status == 0, (sp, r)
+        assert r.rel_residual.max() <= 1.5e-8
+        H = O.H2Matrix(p, q=sp["q"], leaf_size=64, eta=2.0, sigma=1e-2)
+        A = O.dense_expand(H)
+        Xc = np.linalg.solve(A, b.cpu().numpy())
+        assert rel_fro(x.cpu().numpy(), Xc) <= 1e-6
+    B.close()
