@@ -181,6 +181,13 @@ typedef enum h2_cg_variant {
                              COLUMNWISE.  1 <= m <= 64 (H2_E_UNSUPPORTED otherwise).                 */
 } h2_cg_variant;
 
+typedef enum h2_precond {
+    H2_PRECOND_NONE = 0,
+    H2_PRECOND_BLOCK_JACOBI = 1 /* M = blockdiag over the leaves t of G_(t,t) + σI (the diagonal nearfield
+                                   blocks with the shift), factored once per matrix and σ by FP64 Cholesky;
+                                   z = M⁻¹ r costs 2·n_t²·m flops per leaf                                  */
+} h2_precond;
+
 typedef struct h2_cg_params {
     double tol;          /* per-column relative residual target |r_i|/|b_i| (|b_i| = 0 read as 1) */
     int32_t max_iter;    /* cap on CG iterations (inner iterations summed for refinement)        */
@@ -197,6 +204,8 @@ typedef struct h2_cg_params {
     int32_t max_outer;   /* cap on refinement steps                                                  */
     int32_t check_every; /* convergence test every this many iterations (>= 1)                      */
     int32_t transposed;  /* != 0: solve Aᵀ X = B (the adjoint system), products with Aᵀ                  */
+    int32_t precond;     /* h2_precond: H2_PRECOND_BLOCK_JACOBI gives the preconditioned block CG of
+                            Sec. 5.1, Alg. "pcg block" (column-wise variant, A only)                  */
     void* stream;        /* cudaStream_t                                                            */
 } h2_cg_params;
 

@@ -258,6 +258,13 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
         near_ptr[NL] = (int32_t)j;
     }
     A->nnz_near = acc;
+    // offset of the diagonal block G_(t,t) of every leaf (always inadmissible: dist = 0)
+    std::vector<int64_t> near_diag(NL, -1);
+    for (int64_t lp = 0; lp < NL; ++lp)
+        for (int64_t j = near_ptr[lp]; j < near_ptr[lp + 1]; ++j)
+            if (near_col[j] == A->leaves[lp]) near_diag[lp] = near_off[j];
+    for (int64_t lp = 0; lp < NL; ++lp)
+        if (near_diag[lp] < 0) { set_error("internal: leaf without a diagonal nearfield block"); return H2_E_CUDA; }
     std::vector<int32_t> nearT_ptr(NL + 1, 0), nearT_row(A->n_near), nearT_blk(A->n_near);
     for (int64_t j = 0; j < A->n_near; ++j) nearT_ptr[leaf_pos[near_col[j]] + 1]++;
     for (int64_t lp = 0; lp < NL; ++lp) nearT_ptr[lp + 1] += nearT_ptr[lp];
@@ -294,6 +301,7 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
     UP(A->d_near_col, near_col);
     UP(A->d_near_row, near_row);
     UP(A->d_near_off, near_off);
+    UP(A->d_near_diag, near_diag);
     UP(A->d_nearT_ptr, nearT_ptr);
     UP(A->d_nearT_row, nearT_row);
     UP(A->d_nearT_blk, nearT_blk);

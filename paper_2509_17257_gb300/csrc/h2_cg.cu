@@ -28,25 +28,15 @@ namespace {
 constexpr int kRowBlocks = 304;  // CTAs along the rows: 2 per SM on a 152-SM part
 constexpr int kColsPerCta = 32;
 
-// Column norms |B_i| and the initial activity flags.
-__global__ void k_cg_init(const double* __restrict__ B, int64_t ldb, const double* __restrict__ R, int64_t ldr,
-                          int64_t n, int m, double tol, CgDev d) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= m) return;
-    double bb = 0.0, rr = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-        const double b = B[i * ldb + col], r = R[i * ldr + col];
-        bb = fma(b, b, bb);
-        rr = fma(r, r, rr);
-    }
-    const double bn = bb > 0.0 ? sqrt(bb) : 1.0;
-    d.bnorm[col] = bn;
-    d.rnorm[col] = sqrt(rr);
-    const int act = !(sqrt(rr) / bn <= tol);
-    d.active[col] = act;
-    d.conv_iter[col] = 0;
-    d.alpha[col] = d.beta[col] = d.gamma[col] = 0.0;
-    if (act) atomicAdd(&d.summary[0], 1);
+// Row loops: this thread visits rows i = blockIdx.x·8 + threadIdx.y + k·S with
+// S = 8·gridDim.x; f4(i, S) takes rows i, i+S, i+2S, i+3S at once (independent
+// loads in flight), f1(i) the tail.
+template <typename F4, typename F1>
+__device__ __forceinline__ void rows4(int64_t n, F4 f4, F1 f1) {
+    const int64_t S = (int64_t)gridDim.x * 8;
+    int64_t i = (int64_t)blockIdx.x * 8 + threadIdx.y;
+    for (; i + 3 * S < n; i += 4 * S) f4(i, S);
+    for (; i < n; i += S) f1(i);
 }
 
 // Reduce the block's (32 columns × 8 row lanes) partial sums over the row lanes.
@@ -80,31 +70,97 @@ __device__ __forceinline__ bool last_cta(unsigned* ticket) {
     return last;
 }
 
-__global__ void __launch_bounds__(256) k_cg_dots(const double* __restrict__ P, const double* __restrict__ AP,
-                                                 const double* __restrict__ R, int64_t ld, int64_t n, int m,
-                                                 CgDev d) {
+// Sum the per-CTA partials of `col` (two components) over the nb CTAs in the
+// last CTA: each of the 8 row lanes takes every 8th CTA, then the lanes are
+// added in fixed order.  Called by every thread; the result is in ty == 0.
+__device__ __forceinline__ void tail_sum2(const double* part, int m, int col, unsigned nb,
+                                          double (*sm)[8][kColsPerCta], double& s0, double& s1) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    double a0 = 0.0, a1 = 0.0;
+    if (col < m) {
+#pragma unroll 4
+        for (unsigned b = ty; b < nb; b += 8) {
+            a0 += __ldcg(&part[((size_t)b * m + col) * 2 + 0]);
+            a1 += __ldcg(&part[((size_t)b * m + col) * 2 + 1]);
+        }
+    }
+    __syncthreads();
+    sm[0][ty][tx] = a0;
+    sm[1][ty][tx] = a1;
+    __syncthreads();
+    s0 = s1 = 0.0;
+    if (ty == 0)
+        for (int y = 0; y < 8; ++y) {
+            s0 += sm[0][y][tx];
+            s1 += sm[1][y][tx];
+        }
+}
+
+// Column norms |B_i|, |R_i| and the initial activity flags (two-stage, fixed order).
+__global__ void __launch_bounds__(256) k_cg_init(const double* __restrict__ B, int64_t ldb,
+                                                 const double* __restrict__ R, int64_t ldr, int64_t n, int m,
+                                                 double tol, CgDev d) {
     __shared__ double sm[2][8][kColsPerCta];
     const int col = blockIdx.y * kColsPerCta + threadIdx.x;
     double v[2] = {0.0, 0.0};
-    if (col < m && d.active[col]) {
-        for (int64_t i = blockIdx.x * 8 + threadIdx.y; i < n; i += (int64_t)gridDim.x * 8) {
-            const double p = P[i * ld + col];
-            v[0] = fma(p, AP[i * ld + col], v[0]);
-            v[1] = fma(p, R[i * ld + col], v[1]);
-        }
-    }
+    if (col < m)
+        rows4(n, [&](int64_t i_, int64_t S_) {
+            double b[4], r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { b[u] = B[(i_ + u * S_) * ldb + col]; r[u] = R[(i_ + u * S_) * ldr + col]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { v[0] = fma(b[u], b[u], v[0]); v[1] = fma(r[u], r[u], v[1]); } }, [&](int64_t i_) {
+            const double b = B[i_ * ldb + col], r = R[i_ * ldr + col];
+            v[0] = fma(b, b, v[0]); v[1] = fma(r, r, v[1]); });
     block_reduce<2>(v, sm);
     if (threadIdx.y == 0 && col < m) {
         d.partial[((size_t)blockIdx.x * m + col) * 2 + 0] = v[0];
         d.partial[((size_t)blockIdx.x * m + col) * 2 + 1] = v[1];
     }
     if (!last_cta(d.ticket)) return;
+    double bb, rr;
+    tail_sum2(d.partial, m, col, gridDim.x, sm, bb, rr);
     if (threadIdx.y == 0 && col < m) {
-        double pa = 0.0, pr = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) {
-            pa += __ldcg(&d.partial[((size_t)b * m + col) * 2 + 0]);
-            pr += __ldcg(&d.partial[((size_t)b * m + col) * 2 + 1]);
-        }
+        const double bn = bb > 0.0 ? sqrt(bb) : 1.0;
+        d.bnorm[col] = bn;
+        d.rnorm[col] = sqrt(rr);
+        const int act = !(sqrt(rr) / bn <= tol);
+        d.active[col] = act;
+        d.conv_iter[col] = 0;
+        d.alpha[col] = d.beta[col] = d.gamma[col] = 0.0;
+        if (act) atomicAdd(&d.summary[0], 1);
+    }
+    if (threadIdx.x == 0 && threadIdx.y == 0) d.ticket[blockIdx.y] = 0;
+}
+
+__global__ void __launch_bounds__(256) k_cg_dots(const double* __restrict__ P, const double* __restrict__ AP,
+                                                 const double* __restrict__ R, int64_t ld, int64_t n, int m,
+                                                 CgDev d) {
+    __shared__ double sm[2][8][kColsPerCta];
+    const int col = blockIdx.y * kColsPerCta + threadIdx.x;
+    double v[2] = {0.0, 0.0};
+    if (col < m && d.active[col])
+        rows4(n, [&](int64_t i_, int64_t S_) {
+            double p[4], a[4], r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t e = (i_ + u * S_) * ld + col;
+                p[u] = P[e]; a[u] = AP[e]; r[u] = R[e];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { v[0] = fma(p[u], a[u], v[0]); v[1] = fma(p[u], r[u], v[1]); } }, [&](int64_t i_) {
+            const double p = P[i_ * ld + col];
+            v[0] = fma(p, AP[i_ * ld + col], v[0]);
+            v[1] = fma(p, R[i_ * ld + col], v[1]); });
+    block_reduce<2>(v, sm);
+    if (threadIdx.y == 0 && col < m) {
+        d.partial[((size_t)blockIdx.x * m + col) * 2 + 0] = v[0];
+        d.partial[((size_t)blockIdx.x * m + col) * 2 + 1] = v[1];
+    }
+    if (!last_cta(d.ticket)) return;
+    double pa, pr;
+    tail_sum2(d.partial, m, col, gridDim.x, sm, pa, pr);
+    if (threadIdx.y == 0 && col < m) {
         double alpha = 0.0;
         if (d.active[col]) {
             if (!(pa > 0.0) || !isfinite(pa) || !isfinite(pr)) {
@@ -127,14 +183,27 @@ __global__ void __launch_bounds__(256) k_cg_update(double* __restrict__ X, int64
     double v[2] = {0.0, 0.0};
     if (col < m && d.active[col]) {
         const double a = d.alpha[col];
-        for (int64_t i = blockIdx.x * 8 + threadIdx.y; i < n; i += (int64_t)gridDim.x * 8) {
-            const double p = P[i * ld + col], ap = AP[i * ld + col];
-            X[i * ldx + col] = fma(a, p, X[i * ldx + col]);
-            const double r = fma(-a, ap, R[i * ld + col]);
-            R[i * ld + col] = r;
+        rows4(n, [&](int64_t i_, int64_t S_) {
+            double p[4], ap[4], r[4], x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t e = (i_ + u * S_) * ld + col;
+                p[u] = P[e]; ap[u] = AP[e]; r[u] = R[e]; x[u] = X[(i_ + u * S_) * ldx + col];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                X[(i_ + u * S_) * ldx + col] = fma(a, p[u], x[u]);
+                r[u] = fma(-a, ap[u], r[u]);
+                R[(i_ + u * S_) * ld + col] = r[u];
+                v[0] = fma(ap[u], r[u], v[0]);
+                v[1] = fma(r[u], r[u], v[1]);
+            } }, [&](int64_t i_) {
+            const double p = P[i_ * ld + col], ap = AP[i_ * ld + col];
+            X[i_ * ldx + col] = fma(a, p, X[i_ * ldx + col]);
+            const double r = fma(-a, ap, R[i_ * ld + col]);
+            R[i_ * ld + col] = r;
             v[0] = fma(ap, r, v[0]);
-            v[1] = fma(r, r, v[1]);
-        }
+            v[1] = fma(r, r, v[1]); });
     }
     block_reduce<2>(v, sm);
     if (threadIdx.y == 0 && col < m) {
@@ -142,12 +211,9 @@ __global__ void __launch_bounds__(256) k_cg_update(double* __restrict__ X, int64
         d.partial[((size_t)blockIdx.x * m + col) * 2 + 1] = v[1];
     }
     if (!last_cta(d.ticket)) return;
+    double ar, rr;
+    tail_sum2(d.partial, m, col, gridDim.x, sm, ar, rr);
     if (threadIdx.y == 0 && col < m && d.active[col]) {
-        double ar = 0.0, rr = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) {
-            ar += __ldcg(&d.partial[((size_t)b * m + col) * 2 + 0]);
-            rr += __ldcg(&d.partial[((size_t)b * m + col) * 2 + 1]);
-        }
         const double gamma = ar / d.beta[col];
         d.gamma[col] = gamma;
         const double rn = sqrt(rr);
@@ -168,8 +234,13 @@ __global__ void k_cg_dir(double* __restrict__ P, const double* __restrict__ R, i
     const int col = blockIdx.y * kColsPerCta + threadIdx.x;
     if (col >= m || !d.active[col]) return;
     const double g = d.gamma[col];
-    for (int64_t i = blockIdx.x * 8 + threadIdx.y; i < n; i += (int64_t)gridDim.x * 8)
-        P[i * ld + col] = fma(-g, P[i * ld + col], R[i * ld + col]);
+    rows4(n, [&](int64_t i_, int64_t S_) {
+        double p[4], r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { p[u] = P[(i_ + u * S_) * ld + col]; r[u] = R[(i_ + u * S_) * ld + col]; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) P[(i_ + u * S_) * ld + col] = fma(-g, p[u], r[u]); }, [&](int64_t i_) {
+        P[i_ * ld + col] = fma(-g, P[i_ * ld + col], R[i_ * ld + col]); });
 }
 
 // Reliable update of mixed-precision CG: the recurrence residual of every
@@ -180,7 +251,7 @@ __global__ void k_cg_dir(double* __restrict__ P, const double* __restrict__ R, i
 __global__ void __launch_bounds__(256) k_cg_reliable(const double* __restrict__ Rt, double* __restrict__ R,
                                                      double* __restrict__ P, int64_t ld, int64_t n, int m,
                                                      double tol, double* __restrict__ rupd, CgDev d) {
-    __shared__ double sm[1][8][kColsPerCta];
+    __shared__ double sm[2][8][kColsPerCta];
     const int col = blockIdx.y * kColsPerCta + threadIdx.x;
     double v[1] = {0.0};
     if (col < m)
@@ -189,11 +260,14 @@ __global__ void __launch_bounds__(256) k_cg_reliable(const double* __restrict__ 
             v[0] = fma(r, r, v[0]);
         }
     block_reduce<1>(v, sm);
-    if (threadIdx.y == 0 && col < m) d.partial[((size_t)blockIdx.x * m + col) * 2] = v[0];
-    if (!last_cta(d.ticket)) return;
     if (threadIdx.y == 0 && col < m) {
-        double rr = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) rr += __ldcg(&d.partial[((size_t)b * m + col) * 2]);
+        d.partial[((size_t)blockIdx.x * m + col) * 2] = v[0];
+        d.partial[((size_t)blockIdx.x * m + col) * 2 + 1] = 0.0;
+    }
+    if (!last_cta(d.ticket)) return;
+    double rr, unused;
+    tail_sum2(d.partial, m, col, gridDim.x, sm, rr, unused);
+    if (threadIdx.y == 0 && col < m) {
         const double rn = sqrt(rr);
         d.rnorm[col] = rn;
         rupd[col] = rn;
@@ -218,6 +292,14 @@ __global__ void k_cg_reliable_copy(const double* __restrict__ Rt, double* __rest
         R[i * ld + col] = r;
         if (restart) P[i * ld + col] = r;
     }
+}
+
+// P = Z for restarted columns (active flag 2), preconditioned restart.
+__global__ void k_cg_restart_from(const double* __restrict__ Z, double* __restrict__ P, int64_t ld, int64_t n, int m,
+                                  CgDev d) {
+    const int col = blockIdx.y * kColsPerCta + threadIdx.x;
+    if (col >= m || d.active[col] != 2) return;
+    for (int64_t i = blockIdx.x * 8 + threadIdx.y; i < n; i += (int64_t)gridDim.x * 8) P[i * ld + col] = Z[i * ld + col];
 }
 
 __global__ void k_cg_reliable_flags(int m, CgDev d) {
@@ -249,18 +331,34 @@ __global__ void k_axpy2d(const double* __restrict__ D, int64_t ldd, double* __re
     }
 }
 
-// Relative residual per column |R_i| / |B_i| (|B_i| = 0 read as 1).
-__global__ void k_col_relnorm(const double* __restrict__ R, int64_t ldr, const double* __restrict__ B, int64_t ldb,
-                              int64_t n, int m, double* __restrict__ out) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= m) return;
-    double rr = 0.0, bb = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-        const double r = R[i * ldr + col], b = B[i * ldb + col];
-        rr = fma(r, r, rr);
-        bb = fma(b, b, bb);
+// Relative residual per column |R_i| / |B_i| (|B_i| = 0 read as 1), two-stage.
+__global__ void __launch_bounds__(256) k_col_relnorm(const double* __restrict__ R, int64_t ldr,
+                                                     const double* __restrict__ B, int64_t ldb, int64_t n, int m,
+                                                     double* __restrict__ out, CgDev d) {
+    __shared__ double sm[2][8][kColsPerCta];
+    const int col = blockIdx.y * kColsPerCta + threadIdx.x;
+    double v[2] = {0.0, 0.0};
+    if (col < m)
+        rows4(n, [&](int64_t i_, int64_t S_) {
+            double b[4], r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { b[u] = B[(i_ + u * S_) * ldb + col]; r[u] = R[(i_ + u * S_) * ldr + col]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { v[0] = fma(r[u], r[u], v[0]); v[1] = fma(b[u], b[u], v[1]); } }, [&](int64_t i_) {
+            const double b = B[i_ * ldb + col], r = R[i_ * ldr + col];
+            v[0] = fma(r, r, v[0]); v[1] = fma(b, b, v[1]); });
+    block_reduce<2>(v, sm);
+    if (threadIdx.y == 0 && col < m) {
+        d.partial[((size_t)blockIdx.x * m + col) * 2 + 0] = v[0];
+        d.partial[((size_t)blockIdx.x * m + col) * 2 + 1] = v[1];
     }
-    out[col] = sqrt(rr) / (bb > 0.0 ? sqrt(bb) : 1.0);
+    if (!last_cta(d.ticket)) return;
+    double rr, bb;
+    tail_sum2(d.partial, m, col, gridDim.x, sm, rr, bb);
+    if (threadIdx.y == 0 && col < m) {
+        out[col] = sqrt(rr) / (bb > 0.0 ? sqrt(bb) : 1.0);
+    }
+    if (threadIdx.x == 0 && threadIdx.y == 0) d.ticket[blockIdx.y] = 0;
 }
 
 struct Solver {
@@ -270,6 +368,8 @@ struct Solver {
     int m;
     bool trans = false;  // products with Aᵀ (adjoint solve)
     bool gram = false;   // variant H2_CG_GRAM (m <= 64)
+    bool pcg = false;    // block-Jacobi preconditioned block CG (Alg. "pcg block")
+    double* Z = nullptr; // [n×m] M⁻¹ R when pcg
     CgDev d{};
     GramDev g{};
     double *R = nullptr, *P = nullptr, *AP = nullptr;
@@ -296,6 +396,11 @@ struct Solver {
             return H2_E_UNSUPPORTED;
         }
         const size_t oGram = gram ? piece(gram_scratch_bytes(m)) : 0;
+        const size_t oZ = pcg ? piece(nm * sizeof(double)) : 0;
+        if (pcg) {
+            int rc = bj_prepare(A, st);
+            if (rc) return rc;
+        }
         if (gram) {
             int rc = gram_prepare();
             if (rc) return rc;
@@ -316,6 +421,7 @@ struct Solver {
         d.partial = (double*)(p + oPart);
         d.ticket = (unsigned*)(p + oTk);
         if (gram) gram_carve(&g, p + oGram, m);
+        if (pcg) Z = (double*)(p + oZ);
         H2_CUDA_TRY(cudaMemsetAsync(d.ticket, 0, groups * sizeof(unsigned), st));
         H2_CUDA_TRY(cudaHostAlloc(&h_summary, 4 * sizeof(int), cudaHostAllocDefault));
         return 0;
@@ -325,6 +431,7 @@ struct Solver {
         if (h_summary) cudaFreeHost(h_summary);
     }
 
+    dim3 grid2d() const { return dim3(kRowBlocks, (m + kColsPerCta - 1) / kColsPerCta); }
     unsigned copy_grid() const { return (unsigned)std::min<int64_t>(((int64_t)n * m + 255) / 256, 152 * 16); }
 
     // R = B - A X (product in dtype, FP64 by default)
@@ -343,10 +450,11 @@ struct Solver {
     int cg_reliable(int32_t dtype, const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int max_iter,
                     int check_every, double delta, double* Rt, double* rupd, int* iters, int* updates) {
         if (gram) return cg_gram(dtype, B, ldb, X, ldx, tol, max_iter, check_every, delta, Rt, rupd, iters, updates);
+        if (pcg) return cg_pcg(dtype, B, ldb, X, ldx, tol, max_iter, check_every, delta, Rt, rupd, iters, updates);
         const dim3 blk(kColsPerCta, 8);
         const dim3 grid(kRowBlocks, (m + kColsPerCta - 1) / kColsPerCta);
         H2_CUDA_TRY(cudaMemsetAsync(d.summary, 0, 4 * sizeof(int), st));
-        k_cg_init<<<(m + 63) / 64, 64, 0, st>>>(B, ldb, R, m, n, m, tol, d);
+        k_cg_init<<<grid2d(), dim3(kColsPerCta, 8), 0, st>>>(B, ldb, R, m, n, m, tol, d);
         H2_LAUNCH_CHECK();
         k_copy2d<<<copy_grid(), 256, 0, st>>>(R, m, P, m, n, m);
         H2_LAUNCH_CHECK();
@@ -406,14 +514,15 @@ struct Solver {
     // Returns 0 / H2_E_BREAKDOWN / H2_E_NOCONVERGE; *iters = iterations run.
     int cg(int32_t dtype, const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int max_iter,
            int check_every, int* iters) {
-        if (gram) {
+        if (gram || pcg) {
             int upd = 0;
+            if (pcg) return cg_pcg(dtype, B, ldb, X, ldx, tol, max_iter, check_every, 0.0, nullptr, nullptr, iters, &upd);
             return cg_gram(dtype, B, ldb, X, ldx, tol, max_iter, check_every, 0.0, nullptr, nullptr, iters, &upd);
         }
         const dim3 blk(kColsPerCta, 8);
         const dim3 grid(kRowBlocks, (m + kColsPerCta - 1) / kColsPerCta);
         H2_CUDA_TRY(cudaMemsetAsync(d.summary, 0, 4 * sizeof(int), st));
-        k_cg_init<<<(m + 63) / 64, 64, 0, st>>>(B, ldb, R, m, n, m, tol, d);
+        k_cg_init<<<grid2d(), dim3(kColsPerCta, 8), 0, st>>>(B, ldb, R, m, n, m, tol, d);
         H2_LAUNCH_CHECK();
         k_copy2d<<<copy_grid(), 256, 0, st>>>(R, m, P, m, n, m);
         H2_LAUNCH_CHECK();
@@ -484,10 +593,83 @@ struct Solver {
         H2_LAUNCH_CHECK();
         k_cg_reliable_copy<<<grid, blk, 0, st>>>(Rt, R, P, m, n, m, d);
         H2_LAUNCH_CHECK();
+        if (pcg) {
+            // restarted columns take the preconditioned residual as direction
+            if ((rc = bj_apply(A, R, Z, n, m, nullptr, d, st))) return rc;
+            k_cg_restart_from<<<grid, blk, 0, st>>>(Z, P, m, n, m, d);
+            H2_LAUNCH_CHECK();
+        }
         k_cg_reliable_flags<<<(m + 63) / 64, 64, 0, st>>>(m, d);
         H2_LAUNCH_CHECK();
         if (gram && (rc = gram_mask(P, n, m, d, st))) return rc;
         return 0;
+    }
+
+    // Preconditioned block CG (Alg. "pcg block") with the block-Jacobi M:
+    // per iteration a = A p; β = <p, a>, α = <p, r>/β; x += αp, r -= αa;
+    // z = M⁻¹ r; γ = <a, z>/β; p = z - γp (the paper's form with q = M⁻¹r).
+    // R holds B - A X on entry; Rt != nullptr adds reliable updates.
+    int cg_pcg(int32_t dtype, const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int max_iter,
+               int check_every, double delta, double* Rt, double* rupd, int* iters, int* updates) {
+        const dim3 blk(kColsPerCta, 8);
+        const dim3 grid(kRowBlocks, (m + kColsPerCta - 1) / kColsPerCta);
+        H2_CUDA_TRY(cudaMemsetAsync(d.summary, 0, 4 * sizeof(int), st));
+        k_cg_init<<<grid2d(), dim3(kColsPerCta, 8), 0, st>>>(B, ldb, R, m, n, m, tol, d);
+        H2_LAUNCH_CHECK();
+        int rc = bj_apply(A, R, Z, n, m, nullptr, d, st);
+        if (rc) return rc;
+        k_copy2d<<<copy_grid(), 256, 0, st>>>(Z, m, P, m, n, m);
+        H2_LAUNCH_CHECK();
+        if (Rt) H2_CUDA_TRY(cudaMemcpyAsync(rupd, d.rnorm, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        H2_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<double> rn(m), ru(m);
+        std::vector<int> act(m);
+        int it = 0, status = 0;
+        *updates = 0;
+        if (h_summary[0] > 0) {
+            for (it = 1; it <= max_iter; ++it) {
+                ++h2mm_calls;
+                if ((rc = matmul_device(A, 1.0, P, m, AP, m, m, dtype, st, trans, true))) return rc;
+                k_cg_dots<<<grid, blk, 0, st>>>(P, AP, R, m, n, m, d);
+                H2_LAUNCH_CHECK();
+                k_cg_update<<<grid, blk, 0, st>>>(X, ldx, P, AP, R, m, n, m, tol, it, d);
+                H2_LAUNCH_CHECK();
+                if ((rc = bj_apply(A, R, Z, n, m, AP, d, st))) return rc;
+                k_cg_dir<<<grid, blk, 0, st>>>(P, Z, m, n, m, d);
+                H2_LAUNCH_CHECK();
+                if (it % check_every != 0 && it != max_iter) continue;
+                H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                if (Rt) {
+                    H2_CUDA_TRY(cudaMemcpyAsync(rn.data(), d.rnorm, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+                    H2_CUDA_TRY(cudaMemcpyAsync(ru.data(), rupd, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+                    H2_CUDA_TRY(cudaMemcpyAsync(act.data(), d.active, m * sizeof(int), cudaMemcpyDeviceToHost, st));
+                }
+                H2_CUDA_TRY(cudaStreamSynchronize(st));
+                if (h_summary[1]) { status = H2_E_BREAKDOWN; break; }
+                if (!Rt) {
+                    if (h_summary[0] == 0) break;
+                    continue;
+                }
+                bool update = h_summary[0] == 0;
+                for (int i = 0; i < m && !update; ++i) update = act[i] && rn[i] < delta * ru[i];
+                if (!update) continue;
+                ++*updates;
+                if ((rc = reliable_update(B, ldb, X, ldx, tol, Rt, rupd))) return rc;
+                H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                H2_CUDA_TRY(cudaStreamSynchronize(st));
+                if (h_summary[1]) { status = H2_E_BREAKDOWN; break; }
+                if (h_summary[0] == 0) break;
+            }
+            if (it > max_iter) { it = max_iter; status = H2_E_NOCONVERGE; }
+        }
+        std::vector<int> ci(m);
+        H2_CUDA_TRY(cudaMemcpyAsync(ci.data(), d.conv_iter, m * sizeof(int), cudaMemcpyDeviceToHost, st));
+        H2_CUDA_TRY(cudaStreamSynchronize(st));
+        int mx = 0;
+        for (int v : ci) mx = std::max(mx, v);
+        *iters = (status == 0 && !Rt) ? mx : it;
+        return status;
     }
 
     // Gram-matrix block CG (variant H2_CG_GRAM, h2_gram.cu) on A_dtype X = B
@@ -497,7 +679,7 @@ struct Solver {
     int cg_gram(int32_t dtype, const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int max_iter,
                 int check_every, double delta, double* Rt, double* rupd, int* iters, int* updates) {
         H2_CUDA_TRY(cudaMemsetAsync(d.summary, 0, 4 * sizeof(int), st));
-        k_cg_init<<<(m + 63) / 64, 64, 0, st>>>(B, ldb, R, m, n, m, tol, d);
+        k_cg_init<<<grid2d(), dim3(kColsPerCta, 8), 0, st>>>(B, ldb, R, m, n, m, tol, d);
         H2_LAUNCH_CHECK();
         int rc = gram_start(P, R, n, m, g, d, st);
         if (rc) return rc;
@@ -609,6 +791,7 @@ int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, doub
     if (p->transposed) { set_error("batched solves take A, not Aᵀ"); return H2_E_UNSUPPORTED; }
     if (p->variant != H2_CG_COLUMNWISE && p->variant != H2_CG_GRAM) { set_error("unsupported CG variant"); return H2_E_UNSUPPORTED; }
     const bool gram = p->variant == H2_CG_GRAM;
+    if (p->precond != H2_PRECOND_NONE) { set_error("batched solves take no preconditioner"); return H2_E_UNSUPPORTED; }
     const int count = (int)b->mats.size();
     // graphs are captured on and launched from the batch's own stream, after the caller's work
     H2_CUDA_TRY(cudaEventRecord(b->ev_in, (cudaStream_t)p->stream));
@@ -657,7 +840,7 @@ int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, doub
         if (dtype != H2_F64 && (rc = product_prepare(A, m[i], dtype, si))) return rc;
         if ((rc = S.residual(B[i], ldb[i], X[i], ldx[i]))) return rc;
         H2_CUDA_TRY(cudaMemsetAsync(S.d.summary, 0, 4 * sizeof(int), si));
-        k_cg_init<<<(int)((m[i] + 63) / 64), 64, 0, si>>>(B[i], ldb[i], S.R, m[i], A->n, (int)m[i], p->tol, S.d);
+        k_cg_init<<<S.grid2d(), dim3(kColsPerCta, 8), 0, si>>>(B[i], ldb[i], S.R, m[i], A->n, (int)m[i], p->tol, S.d);
         H2_LAUNCH_CHECK();
         if (gram) {
             if ((rc = gram_start(S.P, S.R, A->n, (int)m[i], S.g, S.d, si))) return rc;
@@ -740,7 +923,7 @@ int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, doub
         const int mi = S.m;
         if (!y.done && y.status == 0) y.status = H2_E_NOCONVERGE;
         if ((rc = S.residual(y.B, y.ldb, y.X, y.ldx))) return rc;
-        k_col_relnorm<<<(mi + 63) / 64, 64, 0, si>>>(S.R, mi, y.B, y.ldb, S.n, mi, y.rupd);
+        k_col_relnorm<<<S.grid2d(), dim3(kColsPerCta, 8), 0, si>>>(S.R, mi, y.B, y.ldb, S.n, mi, y.rupd, S.d);
         H2_LAUNCH_CHECK();
         std::vector<double> rel(mi);
         std::vector<int> ci(mi);
@@ -770,6 +953,11 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
     if (m < 0 || (m > 0 && (!B || !X)) || ldb < m || ldx < m) { set_error("bad m / leading dimension"); return H2_E_BADARG; }
     if (!(p->tol >= 0.0) || p->max_iter < 0 || p->check_every < 1) { set_error("bad solver parameters"); return H2_E_BADARG; }
     if (p->variant != H2_CG_COLUMNWISE && p->variant != H2_CG_GRAM) { set_error("unsupported CG variant"); return H2_E_UNSUPPORTED; }
+    if (p->precond != H2_PRECOND_NONE && p->precond != H2_PRECOND_BLOCK_JACOBI) { set_error("unknown preconditioner"); return H2_E_BADARG; }
+    if (p->precond == H2_PRECOND_BLOCK_JACOBI && (p->variant != H2_CG_COLUMNWISE || p->transposed)) {
+        set_error("the block-Jacobi preconditioner is available for the column-wise block CG on A");
+        return H2_E_UNSUPPORTED;
+    }
     if (p->variant == H2_CG_GRAM && m > kGramMaxCols) {
         set_error("the Gram-matrix block CG (H2_CG_GRAM) takes at most 64 columns");
         return H2_E_UNSUPPORTED;
@@ -810,6 +998,7 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
         Solver S{A, st, n, (int)m};
         S.trans = p->transposed != 0;
         S.gram = p->variant == H2_CG_GRAM;
+        S.pcg = p->precond == H2_PRECOND_BLOCK_JACOBI;
         int rc = S.init();
         if (rc) return rc;
         int total_iters = 0;
@@ -846,7 +1035,7 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
             const int max_outer = p->max_outer > 0 ? p->max_outer : 20;
             for (int outer = 0; outer <= max_outer; ++outer) {
                 if ((rc = S.residual(Bd, ldbd, Xd, ldxd))) return rc;
-                k_col_relnorm<<<(unsigned)((m + 63) / 64), 64, 0, st>>>(S.R, m, Bd, ldbd, n, (int)m, d_rel);
+                k_col_relnorm<<<S.grid2d(), dim3(kColsPerCta, 8), 0, st>>>(S.R, m, Bd, ldbd, n, (int)m, d_rel, S.d);
                 H2_LAUNCH_CHECK();
                 H2_CUDA_TRY(cudaMemcpyAsync(rel.data(), d_rel, m * sizeof(double), cudaMemcpyDeviceToHost, st));
                 H2_CUDA_TRY(cudaStreamSynchronize(st));
@@ -877,7 +1066,7 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
         if ((rc = S.residual(Bd, ldbd, Xd, ldxd))) return rc;
         double* d_rel = nullptr;
         H2_CUDA_TRY(cudaMallocAsync(&d_rel, m * sizeof(double), st));
-        k_col_relnorm<<<(unsigned)((m + 63) / 64), 64, 0, st>>>(S.R, m, Bd, ldbd, n, (int)m, d_rel);
+        k_col_relnorm<<<S.grid2d(), dim3(kColsPerCta, 8), 0, st>>>(S.R, m, Bd, ldbd, n, (int)m, d_rel, S.d);
         H2_LAUNCH_CHECK();
         std::vector<double> rel(m);
         std::vector<int> ci(m);

@@ -156,8 +156,14 @@ __global__ void __launch_bounds__(256) k_gram_reduce(int nct, int m, double tol,
     const int nterm = PHASE == 0 ? 2 * m * m : m * m + m;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < nterm) {
-        double s = 0.0;
-        for (int c = 0; c < nct; ++c) s += __ldcg(&g.part[(size_t)c * ps + e]);
+        // four interleaved partial sums keep loads in flight; fixed order
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        int c = 0;
+        for (; c + 3 < nct; c += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s4[u] += __ldcg(&g.part[(size_t)(c + u) * ps + e]);
+        for (; c < nct; ++c) s4[0] += __ldcg(&g.part[(size_t)c * ps + e]);
+        const double s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
         if (e < m * m) (PHASE == 0 ? g.G : g.W)[e] = s;
         else if (PHASE == 0) g.W[e - m * m] = s;
         else g.rr[e - m * m] = s;

@@ -178,6 +178,7 @@ struct h2_matrix {
     int32_t* d_near_col = nullptr;   // [n_near] column cluster id
     int32_t* d_near_row = nullptr;   // [n_near] row cluster id
     int64_t* d_near_off = nullptr;   // [n_near] element offset of G_j
+    int64_t* d_near_diag = nullptr;  // [n_leaves] element offset of the diagonal block G_(t,t)
     int32_t* d_nearT_ptr = nullptr;  // [n_leaves+1] by column leaf position
     int32_t* d_nearT_row = nullptr;  // [n_near] row cluster t
     int32_t* d_nearT_blk = nullptr;  // [n_near] block index j
@@ -196,6 +197,11 @@ struct h2_matrix {
     unsigned* sync_claim = nullptr;// [sync_tiles]
     int64_t sync_tiles = 0;
     bool force_simt = false;  // H2_FORCE_SIMT=1 at build: FP32 product on the CUDA cores only
+    // block-Jacobi preconditioner (h2_precond.cu): (G_(t,t) + σI)⁻¹ per leaf, built on first use
+    double* bj_inv = nullptr;     // concatenated n_t×n_t inverses, leaf order
+    int64_t* bj_off = nullptr;    // [n_leaves] element offset of leaf t's inverse
+    double bj_sigma = 0.0;        // σ the inverses were formed with
+    bool bj_valid = false;
     std::vector<void*> allocations;
 };
 
@@ -227,6 +233,14 @@ struct GramDev {
     int* kept;         // [m] direction j kept by the deflating Cholesky
     unsigned* ticket;  // [1]
 };
+
+// Block-Jacobi preconditioner M = blockdiag_t (G_(t,t) + σI) (h2_precond.cu).
+int bj_prepare(h2_matrix* A, cudaStream_t st);
+// Z = M⁻¹ R (n×m, ld m, caller's point order).  With AP != nullptr also
+// d.gamma[i] = <AP_i, Z_i> / d.beta[i] for the active columns (fixed-order
+// reduction).
+int bj_apply(h2_matrix* A, const double* R, double* Z, int64_t n, int m, const double* AP, const CgDev& d,
+             cudaStream_t st);
 
 constexpr int kGramMaxCols = 64;
 size_t gram_scratch_bytes(int m);

@@ -1,0 +1,241 @@
+// Block-Jacobi preconditioner for the preconditioned block CG (Sec. 5.1,
+// Alg. "pcg block"): M = blockdiag over the leaves t of D_t = G_(t,t) + σI,
+// the diagonal inadmissible blocks with the shift (always present: a leaf is
+// never admissible with itself, dist = 0).  D_t is a kernel matrix of the
+// exponential kernel plus σI, symmetric positive definite; n_t <= 64.
+//
+// Setup (k_bj_invert, once per matrix and σ): one CTA per leaf factors
+// D_t = L Lᵀ in shared memory and forms D_t⁻¹ = L⁻ᵀ L⁻¹ in FP64.
+// Apply (k_bj_apply, every iteration): Z|_t̂ = D_t⁻¹ R|_t̂ per leaf, rows
+// gathered from and scattered to the caller's point order, 2 n_t² m flops per
+// leaf; optionally the per-column dots <AP_i, Z_i> for γ_i of the paper's
+// recurrence, reduced in fixed order by the last CTA.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "h2_internal.cuh"
+
+namespace h2 {
+
+namespace {
+
+constexpr int kLd = 65;           // padded row length of the 64×64 shared tiles
+constexpr int kBjCtas = 304;      // CTAs of the apply pass (two per SM)
+constexpr int kBjSmem = 2 * 64 * kLd * (int)sizeof(double);
+
+__device__ __forceinline__ bool bj_last_cta(unsigned* ticket) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+__global__ void __launch_bounds__(256) k_bj_invert(const int32_t* __restrict__ leaves, int NL,
+                                                   const int32_t* __restrict__ cl_size,
+                                                   const int64_t* __restrict__ diag_off,
+                                                   const double* __restrict__ near, double sigma,
+                                                   const int64_t* __restrict__ bj_off, double* __restrict__ inv,
+                                                   int* __restrict__ err) {
+    extern __shared__ double sm[];
+    double(*sA)[kLd] = (double(*)[kLd])sm;
+    double(*sB)[kLd] = (double(*)[kLd])(sm + 64 * kLd);
+    __shared__ int bad;
+    const int t = threadIdx.x;
+    for (int lp = blockIdx.x; lp < NL; lp += gridDim.x) {
+        const int l = cl_size[leaves[lp]];
+        const double* g = near + diag_off[lp];
+        if (t == 0) bad = 0;
+        for (int x = t; x < l * l; x += blockDim.x) {
+            const int i = x / l, j = x % l;
+            sA[i][j] = g[x] + (i == j ? sigma : 0.0);
+            sB[i][j] = i == j ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        // right-looking Cholesky D = L Lᵀ (lower triangle of sA)
+        for (int j = 0; j < l; ++j) {
+            if (t == 0) {
+                const double d = sA[j][j];
+                if (!(d > 0.0) || !isfinite(d)) {
+                    bad = 1;
+                    sA[j][j] = 1.0;
+                } else {
+                    sA[j][j] = sqrt(d);
+                }
+            }
+            __syncthreads();
+            const double piv = sA[j][j];
+            for (int i = j + 1 + t; i < l; i += blockDim.x) sA[i][j] /= piv;
+            __syncthreads();
+            const int w = l - j - 1;
+            for (int x = t; x < w * w; x += blockDim.x) {
+                const int i = j + 1 + x / w, k = j + 1 + x % w;
+                if (k <= i) sA[i][k] -= sA[i][j] * sA[k][j];
+            }
+            __syncthreads();
+        }
+        // D⁻¹ = L⁻ᵀ (L⁻¹ I): forward then backward substitution on all l columns
+        for (int j = 0; j < l; ++j) {
+            const double piv = sA[j][j];
+            for (int c = t; c < l; c += blockDim.x) sB[j][c] /= piv;
+            __syncthreads();
+            const int w = l - j - 1;
+            for (int x = t; x < w * l; x += blockDim.x) {
+                const int i = j + 1 + x / l, c = x % l;
+                sB[i][c] -= sA[i][j] * sB[j][c];
+            }
+            __syncthreads();
+        }
+        for (int j = l - 1; j >= 0; --j) {
+            const double piv = sA[j][j];
+            for (int c = t; c < l; c += blockDim.x) sB[j][c] /= piv;
+            __syncthreads();
+            for (int x = t; x < j * l; x += blockDim.x) {
+                const int i = x / l, c = x % l;
+                sB[i][c] -= sA[j][i] * sB[j][c];
+            }
+            __syncthreads();
+        }
+        double* out = inv + bj_off[lp];
+        for (int x = t; x < l * l; x += blockDim.x) out[x] = sB[x / l][x % l];
+        if (t == 0 && bad) atomicExch(err, 1);
+        __syncthreads();
+    }
+}
+
+// Z|_t̂ = D_t⁻¹ R|_t̂ for the CTA's leaves, in column chunks of 64; with AP the
+// per-column partial sums of <AP, Z> go to d.partial[cta][c][0] and the last
+// CTA forms γ_c = <AP_c, Z_c> / β_c on active columns.
+__global__ void __launch_bounds__(256) k_bj_apply(const double* __restrict__ R, double* __restrict__ Z, int m,
+                                                  const int32_t* __restrict__ perm,
+                                                  const int32_t* __restrict__ leaves, int NL,
+                                                  const int32_t* __restrict__ cl_off,
+                                                  const int32_t* __restrict__ cl_size,
+                                                  const int64_t* __restrict__ bj_off,
+                                                  const double* __restrict__ inv, const double* __restrict__ AP,
+                                                  CgDev d) {
+    extern __shared__ double sm[];
+    double(*sD)[kLd] = (double(*)[kLd])sm;
+    double(*sR)[kLd] = (double(*)[kLd])(sm + 64 * kLd);
+    __shared__ double red[4][64];
+    __shared__ int srow[64];
+    const int t = threadIdx.x, tc = t & 63, tr = t >> 6;
+    for (int c0 = 0; c0 < m; c0 += 64) {
+        const int mc = min(64, m - c0);
+        double aq = 0.0;
+        for (int lp = blockIdx.x; lp < NL; lp += gridDim.x) {
+            const int cl = leaves[lp];
+            const int off = cl_off[cl], l = cl_size[cl];
+            const double* Dt = inv + bj_off[lp];
+            __syncthreads();  // previous leaf's tiles are consumed
+            for (int a = t; a < l; a += blockDim.x) srow[a] = perm[off + a];
+            for (int x = t; x < l * l; x += blockDim.x) sD[x / l][x % l] = Dt[x];
+            __syncthreads();
+            for (int x = t; x < l * mc; x += blockDim.x) {
+                const int a = x / mc, c = x % mc;
+                sR[a][c] = R[(int64_t)srow[a] * m + c0 + c];
+            }
+            __syncthreads();
+            if (tc < mc)
+                for (int a = tr; a < l; a += 4) {
+                    double z = 0.0;
+                    for (int b = 0; b < l; ++b) z = fma(sD[a][b], sR[b][tc], z);
+                    const int64_t e = (int64_t)srow[a] * m + c0 + tc;
+                    Z[e] = z;
+                    if (AP) aq = fma(AP[e], z, aq);
+                }
+        }
+        if (AP) {
+            red[tr][tc] = aq;
+            __syncthreads();
+            if (t < mc)
+                d.partial[((size_t)blockIdx.x * m + c0 + t) * 2] = red[0][t] + red[1][t] + red[2][t] + red[3][t];
+            __syncthreads();
+        }
+    }
+    if (!AP || !bj_last_cta(d.ticket)) return;
+    for (int c = t; c < m; c += blockDim.x) {
+        if (!d.active[c]) continue;
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        unsigned b = 0;
+        for (; b + 3 < gridDim.x; b += 4)
+#pragma unroll
+            for (unsigned u = 0; u < 4; ++u) s4[u] += __ldcg(&d.partial[((size_t)(b + u) * m + c) * 2]);
+        for (; b < gridDim.x; ++b) s4[0] += __ldcg(&d.partial[((size_t)b * m + c) * 2]);
+        const double gmm = ((s4[0] + s4[1]) + (s4[2] + s4[3])) / d.beta[c];
+        d.gamma[c] = gmm;
+        if (!isfinite(gmm)) atomicOr(&d.summary[1], 1);
+    }
+    if (t == 0) d.ticket[0] = 0;
+}
+
+int g_bj_attr_device = -1;
+
+int bj_attr() {
+    int dev = 0;
+    H2_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev == g_bj_attr_device) return 0;
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_bj_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, kBjSmem));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_bj_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, kBjSmem));
+    g_bj_attr_device = dev;
+    return 0;
+}
+
+}  // namespace
+
+int bj_prepare(h2_matrix* A, cudaStream_t st) {
+    int rc = bj_attr();
+    if (rc) return rc;
+    if (A->bj_valid && A->bj_sigma == A->sigma) return 0;
+    const int NL = (int)A->leaves.size();
+    if (!A->bj_inv) {
+        std::vector<int64_t> off(NL);
+        int64_t acc = 0;
+        for (int lp = 0; lp < NL; ++lp) {
+            off[lp] = acc;
+            const int64_t l = A->T.size[A->leaves[lp]];
+            if (l > 64) { set_error("block-Jacobi preconditioner: leaf larger than 64 points"); return H2_E_UNSUPPORTED; }
+            acc += l * l;
+        }
+        if ((rc = device_alloc(A, (void**)&A->bj_off, NL * sizeof(int64_t)))) return rc;
+        if ((rc = device_alloc(A, (void**)&A->bj_inv, std::max<int64_t>(acc, 1) * sizeof(double)))) return rc;
+        H2_CUDA_TRY(cudaMemcpyAsync(A->bj_off, off.data(), NL * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        H2_CUDA_TRY(cudaStreamSynchronize(st));  // `off` is pageable host memory
+    }
+    int* d_err = nullptr;
+    H2_CUDA_TRY(cudaMallocAsync((void**)&d_err, sizeof(int), st));
+    H2_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    const unsigned g = (unsigned)std::min(NL, 152 * 4);
+    k_bj_invert<<<g, 256, kBjSmem, st>>>(A->d_leaves, NL, A->d_cl_size, A->d_near_diag, (const double*)A->f64.Near,
+                                         A->sigma, A->bj_off, A->bj_inv, d_err);
+    H2_LAUNCH_CHECK();
+    int h_err = 0;
+    H2_CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    cudaFreeAsync(d_err, st);
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_err) {
+        set_error("block-Jacobi preconditioner: a diagonal block G_(t,t) + σI is not positive definite");
+        return H2_E_BREAKDOWN;
+    }
+    A->bj_valid = true;
+    A->bj_sigma = A->sigma;
+    return 0;
+}
+
+int bj_apply(h2_matrix* A, const double* R, double* Z, int64_t n, int m, const double* AP, const CgDev& d,
+             cudaStream_t st) {
+    (void)n;
+    const int NL = (int)A->leaves.size();
+    const unsigned g = (unsigned)std::min(NL, kBjCtas);
+    k_bj_apply<<<g, 256, kBjSmem, st>>>(R, Z, m, A->d_perm, A->d_leaves, NL, A->d_cl_off, A->d_cl_size, A->bj_off,
+                                        A->bj_inv, AP, d);
+    H2_LAUNCH_CHECK();
+    return 0;
+}
+
+}  // namespace h2

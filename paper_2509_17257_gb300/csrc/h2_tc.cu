@@ -1,4 +1,4 @@
-// Tensor-core (tcgen05) kernels of the BF16 product: the coupling phase
+// Tensor-core (tcgen05) kernels of the BF16 and FP32 products: the coupling phase
 // (ŷ_t = Σ_{b∈C_t} S_b x̂_s, Sec. 3 Alg. "list_addeval" over the row-cluster
 // lists of Alg. "prepare_addeval") and the leaf phase (Y|_t̂ += α(V_t ŷ_t +
 // Σ_{b∈L-} G_b X|_ŝ + σ X|_t̂), Alg. "fast_addeval" inadmissible part + the
@@ -16,10 +16,18 @@
 // order (8 rows × 16 bytes per core matrix, row groups outermost), so one bulk
 // copy per tile lands it in shared memory ready for the MMA.
 //
-// Kernel roles (one persistent CTA per SM, 192 threads):
+// The FP32 product (KIND 1) runs the same schedule on the TF32 units with
+// split operands: the activation rows carry tf32 high and low parts, and the
+// matrix tile B is complemented in shared memory by B_lo = B - tf32(B), so
+// D = A_hi·B + A_hi·B_lo + A_lo·B + A_lo·B_lo keeps FP32 accuracy ("3xTF32",
+// the A_lo·B_lo term comes free with the row split).
+//
+// Kernel roles (one persistent CTA per SM, 256 threads):
 //   warp 0        bulk-copy producer (cp.async.bulk + mbarrier complete_tx)
-//   warp 1        TMEM owner and MMA issuer (tcgen05.mma kind::f16, FP32 accumulate)
+//   warp 1        TMEM owner and MMA issuer (tcgen05.mma kind::f16 or kind::tf32,
+//                 FP32 accumulate)
 //   warps 2..5    epilogue (tcgen05.ld, hi+lo combine, stores)
+//   warps 6..7    KIND 1 only: the B_lo splitter
 // Accumulators are double-buffered in TMEM so the epilogue of one output tile
 // overlaps the MMAs of the next.  Every wait is bounded; on a timeout the
 // kernel raises an error flag, drains its own copies and MMAs, frees TMEM and

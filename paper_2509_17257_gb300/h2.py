@@ -33,6 +33,9 @@ DTYPES = {"f64": H2_F64, "f32": H2_F32, "bf16": H2_BF16}
 H2_CG_COLUMNWISE = 0
 H2_CG_GRAM = 1
 VARIANTS = {"columnwise": H2_CG_COLUMNWISE, "gram": H2_CG_GRAM}
+H2_PRECOND_NONE = 0
+H2_PRECOND_BLOCK_JACOBI = 1
+PRECONDS = {None: H2_PRECOND_NONE, "none": H2_PRECOND_NONE, "block_jacobi": H2_PRECOND_BLOCK_JACOBI}
 
 _STATUS = {0: "ok", -1: "badarg", -2: "cuda", -3: "noconverge", -4: "breakdown", -5: "timeout", -6: "oom",
            -7: "unsupported"}
@@ -60,7 +63,7 @@ class CGParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("variant", C.c_int32),
                 ("dtype", C.c_int32), ("refine", C.c_int32), ("inner_tol", C.c_double),
                 ("max_outer", C.c_int32), ("check_every", C.c_int32), ("transposed", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("precond", C.c_int32), ("stream", C.c_void_p)]
 
 
 class CGResult(C.Structure):
@@ -314,7 +317,7 @@ class SolveResult:
 
 
 def h2_block_cg(handle, B, X, tol=1e-8, max_iter=20000, dtype="f64", refine=True, inner_tol=1e-4,
-                max_outer=30, check_every=1, variant=H2_CG_COLUMNWISE, transposed=False,
+                max_outer=30, check_every=1, variant=H2_CG_COLUMNWISE, transposed=False, precond=None,
                 stream=None) -> SolveResult:
     """Solve A X = B (X: initial guess in, solution out).  ``dtype`` is the
     precision of the product; with a low precision and ``refine`` the solve is
@@ -329,8 +332,9 @@ def h2_block_cg(handle, B, X, tol=1e-8, max_iter=20000, dtype="f64", refine=True
     rel = np.zeros(max(m, 1), dtype=np.float64)
     dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
     variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    pc = PRECONDS[precond] if precond is None or isinstance(precond, str) else int(precond)
     prm = CGParams(tol, max_iter, variant, dt, int(refine), inner_tol, max_outer, check_every,
-                   1 if transposed else 0, _stream_ptr(stream))
+                   1 if transposed else 0, pc, _stream_ptr(stream))
     res = CGResult(0, 0, 0, 0, it.ctypes.data_as(C.POINTER(C.c_int32)), rel.ctypes.data_as(C.POINTER(C.c_double)),
                    0.0)
     rc = lib().h2_block_cg(handle, bp, ldb, xp, ldx, m, C.byref(prm), C.byref(res))
@@ -382,7 +386,8 @@ class H2Batch:
         cnt = len(self.mats)
         dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
         var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
-        prm = CGParams(tol, max_iter, var, dt, 2, inner_tol, 0, check_every, 0, _stream_ptr(stream))
+        prm = CGParams(tol, max_iter, var, dt, 2, inner_tol, 0, check_every, 0, H2_PRECOND_NONE,
+                       _stream_ptr(stream))
         its = [np.zeros(max(int(mb[i]), 1), dtype=np.int32) for i in range(cnt)]
         rels = [np.zeros(max(int(mb[i]), 1)) for i in range(cnt)]
         res = (CGResult * cnt)()

@@ -100,7 +100,8 @@ def test_gram_single_column_is_scalar_cg(case4096):
         r = G.block_cg(torch.from_numpy(B).cuda(), Xd, tol=1e-8, max_iter=5000, dtype="f64", variant=var)
         assert r.status == 0
         it[var] = r.iterations
-    assert abs(it["gram"] - it["columnwise"]) <= max(5, it["columnwise"] // 50), it
+    # equal in exact arithmetic; rounding moves the counts by a few per cent
+    assert abs(it["gram"] - it["columnwise"]) <= max(5, it["columnwise"] // 20), it
 
 
 def test_gram_rank_deficient_rhs(case4096):
