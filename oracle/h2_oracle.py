@@ -570,7 +570,7 @@ def _chol_solve(L: np.ndarray, K, Wcol: np.ndarray) -> np.ndarray:
 
 
 def block_cg_gram(apply_A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8,
-                  max_iter: int = 10000) -> CGResult:
+                  max_iter: int = 10000, apply_Minv=None) -> CGResult:
     """Block CG with m×m Gram matrices (O'Leary 1980), the block form of the
     scalar recurrences of Alg. "CG":
 
@@ -583,12 +583,17 @@ def block_cg_gram(apply_A, B: np.ndarray, X0: np.ndarray | None = None, tol: flo
     :func:`block_cg`: column i leaves the active set 𝒜 once
     ||r_i||/||b_i|| <= tol and is frozen from then on (its columns of α and Γ
     are zero and its direction is zero).  With m = 1 this is Alg. "CG".
+
+    With a preconditioner (apply_Minv: R ↦ M⁻¹R) the directions are built
+    from Z = M⁻¹R as in Alg. "pcg block": P starts as Z, Γ = G⁻¹ (AP)ᵀ Z and
+    P = Z − PΓ.
     """
     B = np.asarray(B, dtype=np.float64)
     n, m = B.shape
     X = np.zeros((n, m)) if X0 is None else np.array(X0, dtype=np.float64)
     R = B - apply_A(X)
-    P = R.copy()
+    Minv = (lambda V: V) if apply_Minv is None else apply_Minv
+    P = np.array(Minv(R), dtype=np.float64)
     bn = np.linalg.norm(B, axis=0)
     bn[bn == 0.0] = 1.0
     active = np.linalg.norm(R, axis=0) / bn > tol
@@ -619,12 +624,13 @@ def block_cg_gram(apply_A, B: np.ndarray, X0: np.ndarray | None = None, tol: flo
             col_it[j] = it
             if rn[j] <= tol:
                 active[j] = False
-        C = Q.T @ R
+        Zr = R if apply_Minv is None else np.asarray(Minv(R), dtype=np.float64)
+        C = Q.T @ Zr
         Gamma = np.zeros((m, m))
         for j in range(m):
             if active[j]:
                 Gamma[:, j] = _chol_solve(L, K, C[:, j])
-        Pn = R - P @ Gamma
+        Pn = Zr - P @ Gamma
         Pn[:, ~active] = 0.0
         P = Pn
         if not np.all(np.isfinite(P)):

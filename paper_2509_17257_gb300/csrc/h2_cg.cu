@@ -516,8 +516,8 @@ struct Solver {
            int check_every, int* iters) {
         if (gram || pcg) {
             int upd = 0;
-            if (pcg) return cg_pcg(dtype, B, ldb, X, ldx, tol, max_iter, check_every, 0.0, nullptr, nullptr, iters, &upd);
-            return cg_gram(dtype, B, ldb, X, ldx, tol, max_iter, check_every, 0.0, nullptr, nullptr, iters, &upd);
+            if (gram) return cg_gram(dtype, B, ldb, X, ldx, tol, max_iter, check_every, 0.0, nullptr, nullptr, iters, &upd);
+            return cg_pcg(dtype, B, ldb, X, ldx, tol, max_iter, check_every, 0.0, nullptr, nullptr, iters, &upd);
         }
         const dim3 blk(kColsPerCta, 8);
         const dim3 grid(kRowBlocks, (m + kColsPerCta - 1) / kColsPerCta);
@@ -681,8 +681,9 @@ struct Solver {
         H2_CUDA_TRY(cudaMemsetAsync(d.summary, 0, 4 * sizeof(int), st));
         k_cg_init<<<grid2d(), dim3(kColsPerCta, 8), 0, st>>>(B, ldb, R, m, n, m, tol, d);
         H2_LAUNCH_CHECK();
-        int rc = gram_start(P, R, n, m, g, d, st);
-        if (rc) return rc;
+        int rc = 0;
+        if (pcg && (rc = bj_apply(A, R, Z, n, m, nullptr, d, st))) return rc;
+        if ((rc = gram_start(P, pcg ? Z : R, n, m, g, d, st))) return rc;
         if (Rt) H2_CUDA_TRY(cudaMemcpyAsync(rupd, d.rnorm, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
         H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         H2_CUDA_TRY(cudaStreamSynchronize(st));
@@ -695,7 +696,13 @@ struct Solver {
                 ++h2mm_calls;
                 if ((rc = matmul_device(A, 1.0, P, m, AP, m, m, dtype, st, trans, true))) return rc;
                 if ((rc = gram_alpha(P, AP, R, n, m, g, d, st))) return rc;
-                if ((rc = gram_update_dir(X, ldx, P, AP, R, n, m, tol, g, d, st))) return rc;
+                if (pcg) {
+                    if ((rc = gram_update(X, ldx, P, AP, R, n, m, g, st))) return rc;
+                    if ((rc = bj_apply(A, R, Z, n, m, nullptr, d, st))) return rc;
+                    if ((rc = gram_gamma_dir_from(P, AP, Z, n, m, tol, g, d, st))) return rc;
+                } else if ((rc = gram_update_dir(X, ldx, P, AP, R, n, m, tol, g, d, st))) {
+                    return rc;
+                }
                 if (it % check_every != 0 && it != max_iter) continue;
                 H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
                 if (Rt) {
@@ -954,8 +961,8 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
     if (!(p->tol >= 0.0) || p->max_iter < 0 || p->check_every < 1) { set_error("bad solver parameters"); return H2_E_BADARG; }
     if (p->variant != H2_CG_COLUMNWISE && p->variant != H2_CG_GRAM) { set_error("unsupported CG variant"); return H2_E_UNSUPPORTED; }
     if (p->precond != H2_PRECOND_NONE && p->precond != H2_PRECOND_BLOCK_JACOBI) { set_error("unknown preconditioner"); return H2_E_BADARG; }
-    if (p->precond == H2_PRECOND_BLOCK_JACOBI && (p->variant != H2_CG_COLUMNWISE || p->transposed)) {
-        set_error("the block-Jacobi preconditioner is available for the column-wise block CG on A");
+    if (p->precond == H2_PRECOND_BLOCK_JACOBI && p->transposed) {
+        set_error("the block-Jacobi preconditioner is available for solves with A");
         return H2_E_UNSUPPORTED;
     }
     if (p->variant == H2_CG_GRAM && m > kGramMaxCols) {

@@ -14,11 +14,11 @@
 //
 // Everything runs in FP64 on the device.  Per iteration, after the product:
 //   k_gram_partial      per-CTA partial sums of [G | W] over row tiles
-//   k_gram_reduce<0>    fixed-order sum of the partials; the last CTA factors
-//                       G and solves α
+//   k_gram_reduce<0>    fixed-order sum of the partials: G, W
+//   k_gram_solve<0>     deflating Cholesky of G and α = G⁻¹W, 4 columns per CTA
 //   k_gram_update       X += Pα, R -= (AP)α, partial sums of (AP)ᵀR and |r_j|²
-//   k_gram_reduce<1>    fixed-order sum; the last CTA updates the active set
-//                       and solves Γ
+//   k_gram_reduce<1>    fixed-order sum: (AP)ᵀR, |r_j|²
+//   k_gram_solve<1>     active set and Γ = G⁻¹(AP)ᵀR, 4 columns per CTA
 //   k_gram_dir          P = R - PΓ (zero on inactive columns)
 // The row passes are FP64-FMA bound (2m² flops per row and Gram product).
 #include <cuda_runtime.h>
@@ -37,24 +37,13 @@ constexpr int kTRg = 16;         // rows per tile in the Gram pass
 constexpr int kTRu = 8;          // rows per tile in the update and direction passes
 constexpr double kDeflate = 1e-10;
 constexpr int kSolveLd = kGramMaxCols + 1;
-constexpr int kSolveSmem = 2 * kGramMaxCols * kSolveLd * (int)sizeof(double);
-
-__device__ __forceinline__ bool gram_last_cta(unsigned* ticket) {
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (last) __threadfence();
-    return last;
-}
 
 __host__ __device__ __forceinline__ int pstride(int m) { return 2 * m * m + m; }
 
 // part[cta][0:m²] = Uᵀ V0, part[cta][m²:2m²] = Uᵀ V1 over the CTA's row tiles
 // (U, V0, V1: n×m, ld m).  MP is m rounded up to 16, 32 or 64; thread (tx, ty)
 // owns entries (ty + 16a, tx + 16b).
-template <int MP>
+template <int MP, int NT>
 __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__ U, const double* __restrict__ V0,
                                                       const double* __restrict__ V1, int64_t n, int m,
                                                       double* __restrict__ part) {
@@ -75,7 +64,7 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
             const bool ok = row < n && c < m;
             su[r][c] = ok ? U[row * m + c] : 0.0;
             s0[r][c] = ok ? V0[row * m + c] : 0.0;
-            s1[r][c] = ok ? V1[row * m + c] : 0.0;
+            if (NT == 2) s1[r][c] = ok ? V1[row * m + c] : 0.0;
         }
         __syncthreads();
 #pragma unroll 4
@@ -85,14 +74,14 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
             for (int i = 0; i < T; ++i) {
                 u[i] = su[r][ty + 16 * i];
                 v0[i] = s0[r][tx + 16 * i];
-                v1[i] = s1[r][tx + 16 * i];
+                v1[i] = NT == 2 ? s1[r][tx + 16 * i] : 0.0;
             }
 #pragma unroll
             for (int i = 0; i < T; ++i)
 #pragma unroll
                 for (int j = 0; j < T; ++j) {
                     a0[i][j] = fma(u[i], v0[j], a0[i][j]);
-                    a1[i][j] = fma(u[i], v1[j], a1[i][j]);
+                    if (NT == 2) a1[i][j] = fma(u[i], v1[j], a1[i][j]);
                 }
         }
         __syncthreads();
@@ -105,80 +94,54 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
             const int r = ty + 16 * i, c = tx + 16 * j;
             if (r < m && c < m) {
                 out[r * m + c] = a0[i][j];
-                out[m * m + r * m + c] = a1[i][j];
+                if (NT == 2) out[m * m + r * m + c] = a1[i][j];
             }
         }
 }
 
-// B[:, c] = G_KK⁻¹ B[K, c] for every column c < m, with L (lower, on K) from a
-// deflating Cholesky; rows outside K become 0.  All threads of the CTA call it.
-__device__ void tri_solve(double (*sA)[kSolveLd], double (*sB)[kSolveLd], const int* sk, int m) {
-    const int t = threadIdx.x;
-    for (int j = 0; j < m; ++j) {  // L z = b
-        if (sk[j]) {
-            const double piv = sA[j][j];
-            for (int c = t; c < m; c += blockDim.x) sB[j][c] /= piv;
-            __syncthreads();
-            const int w = m - j - 1;
-            for (int x = t; x < w * m; x += blockDim.x) {
-                const int i = j + 1 + x / m, c = x % m;
-                sB[i][c] -= sA[i][j] * sB[j][c];
-            }
-        } else {
-            for (int c = t; c < m; c += blockDim.x) sB[j][c] = 0.0;
-        }
-        __syncthreads();
-    }
-    for (int j = m - 1; j >= 0; --j) {  // Lᵀ y = z
-        if (sk[j]) {
-            const double piv = sA[j][j];
-            for (int c = t; c < m; c += blockDim.x) sB[j][c] /= piv;
-            __syncthreads();
-            for (int x = t; x < j * m; x += blockDim.x) {
-                const int i = x / m, c = x % m;
-                if (sk[i]) sB[i][c] -= sA[j][i] * sB[j][c];
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// Fixed-order sum of the per-CTA partials, then (last CTA) the m×m step:
-// PHASE 0: G, W -> deflating Cholesky of G, α = G⁻¹W on active columns;
-// PHASE 1: C = (AP)ᵀR, |r_j|² -> active set, Γ = G⁻¹C on still-active columns.
+// Fixed-order sum of the per-CTA partials: PHASE 0 gives G = Pᵀ(AP) and
+// W = PᵀR, PHASE 1 gives C = (AP)ᵀR and |r_j|².
 template <int PHASE>
-__global__ void __launch_bounds__(256) k_gram_reduce(int nct, int m, double tol, GramDev g, CgDev d) {
-    extern __shared__ double dsm[];
-    __shared__ int sk[kGramMaxCols], sa[kGramMaxCols];
-    __shared__ double sdg[kGramMaxCols];
-    __shared__ int sbrk;
+__global__ void __launch_bounds__(256) k_gram_reduce(int nct, int m, GramDev g) {
     const int ps = pstride(m);
     const int nterm = PHASE == 0 ? 2 * m * m : m * m + m;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < nterm) {
-        // four interleaved partial sums keep loads in flight; fixed order
-        double s4[4] = {0.0, 0.0, 0.0, 0.0};
-        int c = 0;
-        for (; c + 3 < nct; c += 4)
+    if (e >= nterm) return;
+    // four interleaved partial sums keep loads in flight; fixed order
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    int c = 0;
+    for (; c + 3 < nct; c += 4)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) s4[u] += __ldcg(&g.part[(size_t)(c + u) * ps + e]);
-        for (; c < nct; ++c) s4[0] += __ldcg(&g.part[(size_t)c * ps + e]);
-        const double s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
-        if (e < m * m) (PHASE == 0 ? g.G : g.W)[e] = s;
-        else if (PHASE == 0) g.W[e - m * m] = s;
-        else g.rr[e - m * m] = s;
-    }
-    if (!gram_last_cta(g.ticket)) return;
-    double(*sA)[kSolveLd] = (double(*)[kSolveLd])dsm;
-    double(*sB)[kSolveLd] = (double(*)[kSolveLd])(dsm + kGramMaxCols * kSolveLd);
+        for (int u = 0; u < 4; ++u) s4[u] += __ldcg(&g.part[(size_t)(c + u) * ps + e]);
+    for (; c < nct; ++c) s4[0] += __ldcg(&g.part[(size_t)c * ps + e]);
+    const double s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+    if (e < m * m) (PHASE == 0 ? g.G : g.W)[e] = s;
+    else if (PHASE == 0) g.W[e - m * m] = s;
+    else g.rr[e - m * m] = s;
+}
+
+constexpr int kSolveCols = 4;     // right-hand-side columns of the m×m solve per CTA
+constexpr int kSolveThreads = 128;
+
+// The m×m step, kSolveCols columns per CTA.
+// PHASE 0: every CTA factors G (deflating Cholesky, identical in all CTAs) and
+//   solves α[:, c] = G_KK⁻¹ W[K, c] for its active columns c; CTA 0 keeps L and
+//   the kept set for PHASE 1.
+// PHASE 1: each CTA updates the active set of its columns from |r_c| and solves
+//   Γ[:, c] = G_KK⁻¹ C[K, c] for those still active.
+template <int PHASE>
+__global__ void __launch_bounds__(kSolveThreads) k_gram_solve(int m, double tol, GramDev g, CgDev d) {
+    __shared__ double sA[kGramMaxCols][kSolveLd];
+    __shared__ double sB[kGramMaxCols][kSolveCols];
+    __shared__ double sdg[kGramMaxCols];
+    __shared__ int sk[kGramMaxCols], sa[kGramMaxCols], sown[kSolveCols];
+    __shared__ int sbrk;
     const int t = threadIdx.x;
+    const int c0 = blockIdx.x * kSolveCols;
+    const int nc = min(kSolveCols, m - c0);
     if (t == 0) sbrk = 0;
     if (PHASE == 0) {
-        for (int x = t; x < m * m; x += blockDim.x) {
-            const int i = x / m, j = x % m;
-            sA[i][j] = __ldcg(&g.G[x]);
-            sB[i][j] = __ldcg(&g.W[x]);
-        }
+        for (int x = t; x < m * m; x += blockDim.x) sA[x / m][x % m] = __ldcg(&g.G[x]);
         for (int j = t; j < m; j += blockDim.x) {
             sa[j] = d.active[j] != 0;
             sdg[j] = __ldcg(&g.G[j * m + j]);
@@ -215,56 +178,77 @@ __global__ void __launch_bounds__(256) k_gram_reduce(int nct, int m, double tol,
             }
             __syncthreads();
         }
-        tri_solve(sA, sB, sk, m);
-        for (int x = t; x < m * m; x += blockDim.x) {
-            const int i = x / m, c = x % m;
-            const double a = sB[i][c];
-            g.alpha[x] = (sa[c] && !sbrk && isfinite(a)) ? a : 0.0;
-            g.L[x] = sA[i][c];
-            if (sa[c] && !isfinite(a)) sbrk = 1;
+        for (int c = t; c < nc; c += blockDim.x) sown[c] = sa[c0 + c];
+        for (int x = t; x < m * nc; x += blockDim.x) sB[x / nc][x % nc] = __ldcg(&g.W[(x / nc) * m + c0 + x % nc]);
+        if (blockIdx.x == 0) {
+            for (int x = t; x < m * m; x += blockDim.x) g.L[x] = sA[x / m][x % m];
+            for (int j = t; j < m; j += blockDim.x) g.kept[j] = sk[j];
         }
-        for (int j = t; j < m; j += blockDim.x) g.kept[j] = sk[j];
-        __syncthreads();
-        if (t == 0 && sbrk) atomicOr(&d.summary[1], 1);
     } else {
-        for (int x = t; x < m * m; x += blockDim.x) {
-            const int i = x / m, j = x % m;
-            sA[i][j] = __ldcg(&g.L[x]);
-            sB[i][j] = __ldcg(&g.W[x]);
-        }
-        for (int j = t; j < m; j += blockDim.x) {
-            sk[j] = __ldcg(&g.kept[j]);
-            int act = d.active[j] != 0;
+        for (int x = t; x < m * m; x += blockDim.x) sA[x / m][x % m] = __ldcg(&g.L[x]);
+        for (int j = t; j < m; j += blockDim.x) sk[j] = __ldcg(&g.kept[j]);
+        for (int c = t; c < nc; c += blockDim.x) {
+            const int col = c0 + c;
+            int act = d.active[col] != 0;
             if (act) {
-                const double rn = sqrt(__ldcg(&g.rr[j]));
-                d.rnorm[j] = rn;
-                d.conv_iter[j] += 1;  // iterations while active
+                const double rn = sqrt(__ldcg(&g.rr[col]));
+                d.rnorm[col] = rn;
+                d.conv_iter[col] += 1;  // iterations while active
                 if (!isfinite(rn)) atomicOr(&d.summary[1], 1);
-                if (rn / d.bnorm[j] <= tol) {
+                if (rn / d.bnorm[col] <= tol) {
                     act = 0;
-                    d.active[j] = 0;
+                    d.active[col] = 0;
                     atomicSub(&d.summary[0], 1);
                 }
             }
-            sa[j] = act;
+            sown[c] = act;
         }
-        __syncthreads();
-        tri_solve(sA, sB, sk, m);
-        for (int x = t; x < m * m; x += blockDim.x) {
-            const int c = x % m;
-            const double v = sB[x / m][c];
-            g.gamma[x] = (sa[c] && isfinite(v)) ? v : 0.0;
-            if (sa[c] && !isfinite(v)) sbrk = 1;
-        }
-        __syncthreads();
-        if (t == 0 && sbrk) atomicOr(&d.summary[1], 1);
+        for (int x = t; x < m * nc; x += blockDim.x) sB[x / nc][x % nc] = __ldcg(&g.W[(x / nc) * m + c0 + x % nc]);
     }
-    if (t == 0) *g.ticket = 0;
+    __syncthreads();
+    // sB[:, c] = G_KK⁻¹ sB[K, c]: L z = b, then Lᵀ y = z; rows outside K are 0
+    for (int j = 0; j < m; ++j) {
+        if (sk[j]) {
+            const double piv = sA[j][j];
+            if (t < nc) sB[j][t] /= piv;
+            __syncthreads();
+            const int w = m - j - 1;
+            for (int x = t; x < w * nc; x += blockDim.x) {
+                const int i = j + 1 + x / nc, c = x % nc;
+                sB[i][c] -= sA[i][j] * sB[j][c];
+            }
+        } else if (t < nc) {
+            sB[j][t] = 0.0;
+        }
+        __syncthreads();
+    }
+    for (int j = m - 1; j >= 0; --j) {
+        if (sk[j]) {
+            const double piv = sA[j][j];
+            if (t < nc) sB[j][t] /= piv;
+            __syncthreads();
+            for (int x = t; x < j * nc; x += blockDim.x) {
+                const int i = x / nc, c = x % nc;
+                if (sk[i]) sB[i][c] -= sA[j][i] * sB[j][c];
+            }
+        }
+        __syncthreads();
+    }
+    double* out = PHASE == 0 ? g.alpha : g.gamma;
+    for (int x = t; x < m * nc; x += blockDim.x) {
+        const int i = x / nc, c = x % nc;
+        const double v = sB[i][c];
+        const bool ok = sown[c] && isfinite(v);
+        if (sown[c] && !isfinite(v)) sbrk = 1;
+        out[i * m + c0 + c] = (ok && !(PHASE == 0 && sbrk)) ? v : 0.0;
+    }
+    __syncthreads();
+    if (t == 0 && sbrk) atomicOr(&d.summary[1], 1);
 }
 
 // X += Pα, R -= Qα (Q = AP) over the CTA's row tiles, then the partial sums of
 // QᵀR_new and |r_j|² for k_gram_reduce<1>.
-template <int MP>
+template <int MP, bool WITH_C>
 __global__ void __launch_bounds__(256) k_gram_update(double* __restrict__ X, int64_t ldx, const double* __restrict__ P,
                                                      const double* __restrict__ Q, double* __restrict__ R, int64_t n,
                                                      int m, const double* __restrict__ alpha,
@@ -313,6 +297,7 @@ __global__ void __launch_bounds__(256) k_gram_update(double* __restrict__ X, int
             }
         }
         __syncthreads();
+        if (WITH_C)
 #pragma unroll
         for (int r = 0; r < kTRu; ++r) {
             double u[T], v[T];
@@ -336,7 +321,7 @@ __global__ void __launch_bounds__(256) k_gram_update(double* __restrict__ X, int
 #pragma unroll
         for (int j = 0; j < T; ++j) {
             const int r = ty + 16 * i, c = tx + 16 * j;
-            if (r < m && c < m) out[r * m + c] = acc[i][j];
+            if (r < m && c < m) out[r * m + c] = WITH_C ? acc[i][j] : 0.0;
         }
     if (t < m) out[m * m + t] = rr;
 }
@@ -394,24 +379,45 @@ template <int MP>
 int launch_alpha(const double* P, const double* AP, const double* R, int64_t n, int m, const GramDev& g,
                  const CgDev& d, cudaStream_t st) {
     const unsigned gp = row_grid(n, kTRg);
-    k_gram_partial<MP><<<gp, 256, 0, st>>>(P, AP, R, n, m, g.part);
+    k_gram_partial<MP, 2><<<gp, 256, 0, st>>>(P, AP, R, n, m, g.part);
     H2_LAUNCH_CHECK();
     const unsigned gr = (unsigned)((2 * m * m + 255) / 256);
-    k_gram_reduce<0><<<gr, 256, kSolveSmem, st>>>((int)gp, m, 0.0, g, d);
+    k_gram_reduce<0><<<gr, 256, 0, st>>>((int)gp, m, g);
+    H2_LAUNCH_CHECK();
+    k_gram_solve<0><<<(unsigned)((m + kSolveCols - 1) / kSolveCols), kSolveThreads, 0, st>>>(m, 0.0, g, d);
     H2_LAUNCH_CHECK();
     return 0;
 }
 
 template <int MP>
-int launch_update_dir(double* X, int64_t ldx, double* P, const double* AP, double* R, int64_t n, int m, double tol,
-                      const GramDev& g, const CgDev& d, cudaStream_t st) {
+int launch_update(double* X, int64_t ldx, const double* P, const double* AP, double* R, int64_t n, int m,
+                  bool with_c, const GramDev& g, cudaStream_t st) {
     const unsigned gu = row_grid(n, kTRu);
-    k_gram_update<MP><<<gu, 256, 0, st>>>(X, ldx, P, AP, R, n, m, g.alpha, g.part);
+    if (with_c) k_gram_update<MP, true><<<gu, 256, 0, st>>>(X, ldx, P, AP, R, n, m, g.alpha, g.part);
+    else k_gram_update<MP, false><<<gu, 256, 0, st>>>(X, ldx, P, AP, R, n, m, g.alpha, g.part);
     H2_LAUNCH_CHECK();
+    return 0;
+}
+
+template <int MP>
+int launch_c_partial(const double* AP, const double* Z, int64_t n, int m, const GramDev& g, cudaStream_t st) {
+    // the partials of the update pass hold zeros in the C slots of its CTAs;
+    // this pass (no more CTAs than the update pass) overwrites them
+    k_gram_partial<MP, 1><<<row_grid(n, kTRg), 256, 0, st>>>(AP, Z, nullptr, n, m, g.part);
+    H2_LAUNCH_CHECK();
+    return 0;
+}
+
+template <int MP>
+int launch_gamma_dir(double* P, const double* D, int64_t n, int m, double tol, const GramDev& g, const CgDev& d,
+                     cudaStream_t st) {
+    const unsigned gu = row_grid(n, kTRu);
     const unsigned gr = (unsigned)((m * m + m + 255) / 256);
-    k_gram_reduce<1><<<gr, 256, kSolveSmem, st>>>((int)gu, m, tol, g, d);
+    k_gram_reduce<1><<<gr, 256, 0, st>>>((int)gu, m, g);
     H2_LAUNCH_CHECK();
-    k_gram_dir<MP><<<gu, 256, 0, st>>>(P, R, n, m, g.gamma, d.active);
+    k_gram_solve<1><<<(unsigned)((m + kSolveCols - 1) / kSolveCols), kSolveThreads, 0, st>>>(m, tol, g, d);
+    H2_LAUNCH_CHECK();
+    k_gram_dir<MP><<<gu, 256, 0, st>>>(P, D, n, m, g.gamma, d.active);
     H2_LAUNCH_CHECK();
     return 0;
 }
@@ -456,8 +462,6 @@ int gram_prepare() {
     int dev = 0;
     H2_CUDA_TRY(cudaGetDevice(&dev));
     if (dev == g_gram_attr_device) return 0;
-    H2_CUDA_TRY(cudaFuncSetAttribute(k_gram_reduce<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmem));
-    H2_CUDA_TRY(cudaFuncSetAttribute(k_gram_reduce<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmem));
     g_gram_attr_device = dev;
     return 0;
 }
@@ -482,11 +486,25 @@ int gram_alpha(const double* P, const double* AP, const double* R, int64_t n, in
     return launch_alpha<64>(P, AP, R, n, m, g, d, st);
 }
 
+#define H2_GRAM_DISPATCH(call) (m <= 16 ? call<16> : m <= 32 ? call<32> : call<64>)
+
 int gram_update_dir(double* X, int64_t ldx, double* P, const double* AP, double* R, int64_t n, int m, double tol,
                     const GramDev& g, const CgDev& d, cudaStream_t st) {
-    if (m <= 16) return launch_update_dir<16>(X, ldx, P, AP, R, n, m, tol, g, d, st);
-    if (m <= 32) return launch_update_dir<32>(X, ldx, P, AP, R, n, m, tol, g, d, st);
-    return launch_update_dir<64>(X, ldx, P, AP, R, n, m, tol, g, d, st);
+    int rc = H2_GRAM_DISPATCH(launch_update)(X, ldx, P, AP, R, n, m, true, g, st);
+    if (rc) return rc;
+    return H2_GRAM_DISPATCH(launch_gamma_dir)(P, R, n, m, tol, g, d, st);
+}
+
+int gram_update(double* X, int64_t ldx, const double* P, const double* AP, double* R, int64_t n, int m,
+                const GramDev& g, cudaStream_t st) {
+    return H2_GRAM_DISPATCH(launch_update)(X, ldx, P, AP, R, n, m, false, g, st);
+}
+
+int gram_gamma_dir_from(double* P, const double* AP, const double* Z, int64_t n, int m, double tol,
+                        const GramDev& g, const CgDev& d, cudaStream_t st) {
+    int rc = H2_GRAM_DISPATCH(launch_c_partial)(AP, Z, n, m, g, st);
+    if (rc) return rc;
+    return H2_GRAM_DISPATCH(launch_gamma_dir)(P, Z, n, m, tol, g, d, st);
 }
 
 int gram_mask(double* P, int64_t n, int m, const CgDev& d, cudaStream_t st) {

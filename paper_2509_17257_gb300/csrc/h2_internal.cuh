@@ -217,7 +217,7 @@ struct CgDev {
     int* active;     // [m] 1 while column i has not converged
     int* conv_iter;  // [m]
     int* summary;    // [0] = active columns, [1] = breakdown flag
-    double* partial; // [kRowBlocks][m][2]
+    double* partial; // [kRowBlocks = 304][m][2]; the block-Jacobi apply uses it as [456][m]
     unsigned* ticket;// [ceil(m/32)]
 };
 
@@ -254,6 +254,12 @@ int gram_alpha(const double* P, const double* AP, const double* R, int64_t n, in
 // X += Pα, R -= (AP)α, column norms and convergence, Γ = G⁻¹(AP)ᵀR, P = R - PΓ.
 int gram_update_dir(double* X, int64_t ldx, double* P, const double* AP, double* R, int64_t n, int m, double tol,
                     const GramDev& g, const CgDev& d, cudaStream_t st);
+// Preconditioned form: X += Pα, R -= (AP)α and |r_j|² only; then, with
+// Z = M⁻¹R, Γ = G⁻¹(AP)ᵀZ and P = Z - PΓ.
+int gram_update(double* X, int64_t ldx, const double* P, const double* AP, double* R, int64_t n, int m,
+                const GramDev& g, cudaStream_t st);
+int gram_gamma_dir_from(double* P, const double* AP, const double* Z, int64_t n, int m, double tol,
+                        const GramDev& g, const CgDev& d, cudaStream_t st);
 // Zero the directions of inactive columns (after a reliable update).
 int gram_mask(double* P, int64_t n, int m, const CgDev& d, cudaStream_t st);
 

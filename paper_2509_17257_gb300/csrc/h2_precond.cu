@@ -23,7 +23,7 @@ namespace h2 {
 namespace {
 
 constexpr int kLd = 65;           // padded row length of the 64×64 shared tiles
-constexpr int kBjCtas = 304;      // CTAs of the apply pass (two per SM)
+constexpr int kBjCtas = 456;      // CTAs of the apply pass (three per SM)
 constexpr int kBjSmem = 2 * 64 * kLd * (int)sizeof(double);
 
 __device__ __forceinline__ bool bj_last_cta(unsigned* ticket) {
@@ -109,8 +109,10 @@ __global__ void __launch_bounds__(256) k_bj_invert(const int32_t* __restrict__ l
 }
 
 // Z|_t̂ = D_t⁻¹ R|_t̂ for the CTA's leaves, in column chunks of 64; with AP the
-// per-column partial sums of <AP, Z> go to d.partial[cta][c][0] and the last
-// CTA forms γ_c = <AP_c, Z_c> / β_c on active columns.
+// per-column partial sums of <AP, Z> go to d.partial[cta·m + c] and the last
+// CTA forms γ_c = <AP_c, Z_c> / β_c on active columns.  Thread t owns column
+// t mod cw of the chunk (cw = chunk width rounded up to 32 or 64) and every
+// (256/cw)-th row of the leaf.  Three CTAs fit on an SM (66.5 KB of tiles each).
 __global__ void __launch_bounds__(256) k_bj_apply(const double* __restrict__ R, double* __restrict__ Z, int m,
                                                   const int32_t* __restrict__ perm,
                                                   const int32_t* __restrict__ leaves, int NL,
@@ -122,11 +124,13 @@ __global__ void __launch_bounds__(256) k_bj_apply(const double* __restrict__ R, 
     extern __shared__ double sm[];
     double(*sD)[kLd] = (double(*)[kLd])sm;
     double(*sR)[kLd] = (double(*)[kLd])(sm + 64 * kLd);
-    __shared__ double red[4][64];
+    __shared__ double red[8][64];
     __shared__ int srow[64];
-    const int t = threadIdx.x, tc = t & 63, tr = t >> 6;
+    const int t = threadIdx.x;
     for (int c0 = 0; c0 < m; c0 += 64) {
         const int mc = min(64, m - c0);
+        const int cw = mc <= 32 ? 32 : 64;
+        const int tc = t % cw, tr = t / cw, nr = 256 / cw;
         double aq = 0.0;
         for (int lp = blockIdx.x; lp < NL; lp += gridDim.x) {
             const int cl = leaves[lp];
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(256) k_bj_apply(const double* __restrict__ R, 
             }
             __syncthreads();
             if (tc < mc)
-                for (int a = tr; a < l; a += 4) {
+                for (int a = tr; a < l; a += nr) {
                     double z = 0.0;
                     for (int b = 0; b < l; ++b) z = fma(sD[a][b], sR[b][tc], z);
                     const int64_t e = (int64_t)srow[a] * m + c0 + tc;
@@ -153,8 +157,11 @@ __global__ void __launch_bounds__(256) k_bj_apply(const double* __restrict__ R, 
         if (AP) {
             red[tr][tc] = aq;
             __syncthreads();
-            if (t < mc)
-                d.partial[((size_t)blockIdx.x * m + c0 + t) * 2] = red[0][t] + red[1][t] + red[2][t] + red[3][t];
+            if (t < mc) {
+                double sum = 0.0;
+                for (int y = 0; y < nr; ++y) sum += red[y][t];
+                d.partial[(size_t)blockIdx.x * m + c0 + t] = sum;
+            }
             __syncthreads();
         }
     }
@@ -165,8 +172,8 @@ __global__ void __launch_bounds__(256) k_bj_apply(const double* __restrict__ R, 
         unsigned b = 0;
         for (; b + 3 < gridDim.x; b += 4)
 #pragma unroll
-            for (unsigned u = 0; u < 4; ++u) s4[u] += __ldcg(&d.partial[((size_t)(b + u) * m + c) * 2]);
-        for (; b < gridDim.x; ++b) s4[0] += __ldcg(&d.partial[((size_t)b * m + c) * 2]);
+            for (unsigned u = 0; u < 4; ++u) s4[u] += __ldcg(&d.partial[(size_t)(b + u) * m + c]);
+        for (; b < gridDim.x; ++b) s4[0] += __ldcg(&d.partial[(size_t)b * m + c]);
         const double gmm = ((s4[0] + s4[1]) + (s4[2] + s4[3])) / d.beta[c];
         d.gamma[c] = gmm;
         if (!isfinite(gmm)) atomicOr(&d.summary[1], 1);

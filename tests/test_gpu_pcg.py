@@ -99,7 +99,26 @@ def test_pcg_unsupported_combinations(case4096, P):
     torch = require_cuda()
     H, A, cf, G = case4096
     B = torch.zeros(4096, 2, dtype=torch.float64, device="cuda")
-    for kw in ({"variant": "gram"}, {"transposed": True}):
-        with pytest.raises(P.H2Error) as e:
-            G.block_cg(B, torch.zeros_like(B), precond="block_jacobi", **kw)
-        assert e.value.code == P.H2_E_UNSUPPORTED
+    with pytest.raises(P.H2Error) as e:
+        G.block_cg(B, torch.zeros_like(B), precond="block_jacobi", transposed=True)
+    assert e.value.code == P.H2_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("dtype,refine", [("f64", 0), ("f32", 2)])
+def test_preconditioned_gram(case4096, dtype, refine):
+    """Gram-matrix block CG with the block-Jacobi preconditioner: the oracle's
+    block_cg_gram(apply_Minv=...) iteration count within 20 % (FP64) and the
+    FP64 tolerance for the mixed solve."""
+    torch = require_cuda()
+    H, A, cf, G = case4096
+    B = gaussian_rhs(4096, 32, 5)
+    Xd = torch.zeros(4096, 32, dtype=torch.float64, device="cuda")
+    res = G.block_cg(torch.from_numpy(B).cuda(), Xd, tol=1e-8, max_iter=5000, dtype=dtype, refine=refine,
+                     inner_tol=0.1, variant="gram", precond="block_jacobi", check_every=1)
+    assert res.status == 0, res
+    X = Xd.cpu().numpy()
+    assert _true_rel(A, B, X).max() <= 1.5e-8
+    assert rel_fro(X, sla.cho_solve(cf, B)) <= 1e-6
+    if dtype == "f64":
+        ref = O.block_cg_gram(lambda Z: A @ Z, B, tol=1e-8, max_iter=5000, apply_Minv=O.block_jacobi(H))
+        assert abs(res.iterations - ref.iterations) <= max(5, ref.iterations // 5), (res.iterations, ref.iterations)

@@ -124,3 +124,27 @@ def test_chol_deflate_drops_dependent_directions():
     G2 = G.copy()
     G2[5, 5] = -1.0
     assert O._chol_deflate(G2, list(range(6)))[2]
+
+
+def test_preconditioned_gram_single_column_is_pcg():
+    """With m = 1 the preconditioned Gram form is Alg. "pcg block"."""
+    H = O.H2Matrix(sphere_points(800, 3), q=3, leaf_size=48, eta=2.0, sigma=1e-2)
+    A = O.dense_expand(H)
+    Minv = O.block_jacobi(H)
+    b = gaussian_rhs(800, 1, 9)
+    for k in (1, 4, 9):
+        g = O.block_cg_gram(lambda X: A @ X, b, tol=0.0, max_iter=k, apply_Minv=Minv)
+        c = O.block_pcg(lambda X: A @ X, Minv, b, tol=0.0, max_iter=k)
+        assert np.linalg.norm(g.X - c.X) <= 1e-10 * np.linalg.norm(c.X), k
+
+
+def test_preconditioned_gram_solves_with_fewer_iterations():
+    H = O.H2Matrix(sphere_points(1500, 2), q=3, leaf_size=48, eta=2.0, sigma=1e-2)
+    A = O.dense_expand(H)
+    B = gaussian_rhs(1500, 8, 1)
+    r = O.block_cg_gram(lambda X: A @ X, B, tol=1e-8, apply_Minv=O.block_jacobi(H))
+    g = O.block_cg_gram(lambda X: A @ X, B, tol=1e-8)
+    assert r.status == "converged"
+    Xc = sla.cho_solve(sla.cho_factor(A), B)
+    assert np.linalg.norm(r.X - Xc) <= 1e-6 * np.linalg.norm(Xc)
+    assert r.iterations < g.iterations
