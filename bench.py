@@ -249,7 +249,8 @@ def run_ours(args):
     n_adm, nc = info["n_adm"], info["n_clusters"]
     coup_bytes = elt * (n_adm * k * k + 2 * nc * k * m)
     coup_flops = 2.0 * n_adm * k * k * m
-    coup_ms = phases["coupling"]
+    # the coupling kernel's own launch (events around it alone; the phase also packs x̂)
+    coup_ms = phases.get("coupling_kernel") or phases["coupling"]
     clock_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     hbm_peak = peaks["hbm_gbs"]
     tensor_path = dtype in ("f32", "bf16") and info["launches_tc"] > 0
@@ -377,6 +378,55 @@ def run_ours(args):
     return 0
 
 
+def run_mvm_vs_mm(args):
+    """The MVM-vs-MM experiment of Sec. 4 on one GPU: m products with one
+    column each against one product with m columns, same matrix (the
+    precision workload), for m in {10, 50, 100, 200}, FP64 and FP32.  Prints
+    one JSON line; not a bench line."""
+    import torch
+    import paper_2509_17257_gb300 as P
+    cfg = CONFIGS[WORKLOAD]
+    n = cfg["n"]
+    G = P.H2Matrix(sphere_points(n, cfg["point_seed"]), q=cfg["q"], leaf_size=cfg["leaf"], eta=cfg["eta"],
+                   sigma=cfg["sigma"], precisions=("f32",))
+    out = {"experiment": "mvm_vs_mm", "workload": WORKLOAD, "n": n, "q": cfg["q"], "rows": []}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def clock(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    for dtype in ("f64", "f32"):
+        for m in (10, 50, 100, 200):
+            X = torch.from_numpy(gaussian_rhs(n, m, 5)).cuda()
+            Y = torch.zeros_like(X)
+            cols = [X[:, j:j + 1].contiguous() for j in range(m)]
+            ycols = [Y[:, j:j + 1].contiguous() for j in range(m)]
+
+            def mm():
+                G.matmul(X, Y, dtype=dtype)
+
+            def mvm():
+                for j in range(m):
+                    G.matmul(cols[j], ycols[j], dtype=dtype)
+
+            reps = 3 if dtype == "f64" else 5
+            t_mm = clock(mm, reps)
+            t_mvm = clock(mvm, 1 if dtype == "f64" else 2)
+            out["rows"].append({"dtype": dtype, "m": m, "ms_mm": round(t_mm, 3), "ms_m_mvm": round(t_mvm, 3),
+                                "speedup": round(t_mvm / t_mm, 2),
+                                "mm_gflops": round(G.flops(m) / (t_mm * 1e-3) / 1e9, 1)})
+    print(json.dumps(out), flush=True)
+    G.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -387,9 +437,13 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve-max-iter", type=int, default=8000)
+    ap.add_argument("--mvm-vs-mm", action="store_true",
+                    help="run the MVM-vs-MM experiment (m single-column products vs one m-column product)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.mvm_vs_mm:
+        return run_mvm_vs_mm(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -160,7 +160,10 @@ int h2_matmul_noalloc(h2_matrix* A, double alpha, const double* X, int64_t ldx, 
  * multiplication phase), 4 downward transfer pass, 5 leaf backward
  * transformation + nearfield + shift (scatter into Y).  When enabled, every
  * product records CUDA events on its stream between the phases; the times are
- * resolved when queried.  Slots 6..7 are reserved (0). */
+ * resolved when queried.  Slot 6 is the coupling kernel launch alone (phase 3
+ * without the packing of x̂ for the tensor cores); slot 7 is reserved (0).
+ * In the tensor-core chain the upward pass is fused into the leaf forward
+ * transformation (phase 1, phase 2 ≈ 0) and the packing of x̂ is in phase 3. */
 #define H2_NPHASE 8
 /* enable != 0 turns recording on, 0 turns it off; pending records are kept. */
 int h2_timing_enable(h2_matrix* A, int32_t enable);

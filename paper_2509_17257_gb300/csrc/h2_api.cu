@@ -59,8 +59,11 @@ int check_params(const h2_build_params* p) {
 
 void free_matrix(h2_matrix* A) {
     if (!A) return;
-    for (auto& ev : A->timing.pending)
-        for (auto e : ev) cudaEventDestroy(e);
+    for (auto& r : A->timing.pending) {
+        for (auto e : r.ev) cudaEventDestroy(e);
+        if (r.k0) cudaEventDestroy(r.k0);
+        if (r.k1) cudaEventDestroy(r.k1);
+    }
     for (auto e : A->timing.free_events) cudaEventDestroy(e);
     for (void* p : A->allocations) cudaFree(p);
     if (A->ws.base) cudaFree(A->ws.base);
@@ -209,16 +212,24 @@ int h2_timing_enable(h2_matrix* A, int32_t enable) {
 int h2_timing_query(h2_matrix* A, double* ms, int64_t* calls, int32_t reset) {
     if (!A) { h2::set_error("null argument"); return H2_E_BADARG; }
     auto& Tm = A->timing;
-    for (auto& ev : Tm.pending) {
+    for (auto& r : Tm.pending) {
+        const auto& ev = r.ev;
         if (!ev.empty()) {
             cudaError_t e = cudaEventSynchronize(ev.back());
             if (e != cudaSuccess) { h2::set_error(cudaGetErrorString(e)); return H2_E_CUDA; }
         }
-        for (size_t i = 0; i + 1 < ev.size() && i < H2_NPHASE; ++i) {
+        for (size_t i = 0; i + 1 < ev.size() && i < 6; ++i) {
             float t = 0.f;
             if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) Tm.ms[i] += t;
         }
+        if (r.k0 && r.k1) {
+            float t = 0.f;
+            if (cudaEventSynchronize(r.k1) == cudaSuccess && cudaEventElapsedTime(&t, r.k0, r.k1) == cudaSuccess)
+                Tm.ms[6] += t;
+        }
         for (auto e : ev) Tm.free_events.push_back(e);
+        if (r.k0) Tm.free_events.push_back(r.k0);
+        if (r.k1) Tm.free_events.push_back(r.k1);
         Tm.calls += 1;
     }
     Tm.pending.clear();

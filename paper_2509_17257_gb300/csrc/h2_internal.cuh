@@ -49,10 +49,14 @@ struct MatData {
 };
 
 // Per-phase event timing of the product (h2_timing_enable / h2_timing_query).
+struct TimingRecord {
+    std::vector<cudaEvent_t> ev;       // phase boundaries (7 per product)
+    cudaEvent_t k0 = nullptr, k1 = nullptr;  // around the coupling kernel launch alone
+};
 struct Timing {
     bool on = false;
     std::vector<cudaEvent_t> free_events;
-    std::vector<std::vector<cudaEvent_t>> pending;  // 7 events per recorded product
+    std::vector<TimingRecord> pending;
     double ms[H2_NPHASE] = {0};
     int64_t calls = 0;
 };

@@ -391,31 +391,40 @@ __global__ void __launch_bounds__(kThreads) k_leaf_bwd_near(
 struct PhaseMarks {
     h2_matrix* A;
     cudaStream_t st;
-    std::vector<cudaEvent_t> ev;
+    TimingRecord rec;
     bool failed = false;
     PhaseMarks(h2_matrix* a, cudaStream_t s) : A(a), st(s) {}
-    void mark() {
-        if (!A || !A->timing.on || failed) return;
+    cudaEvent_t record() {
+        if (!A || !A->timing.on || failed) return nullptr;
         cudaEvent_t e;
         if (!A->timing.free_events.empty()) {
             e = A->timing.free_events.back();
             A->timing.free_events.pop_back();
         } else if (cudaEventCreate(&e) != cudaSuccess) {
             failed = true;
-            return;
+            return nullptr;
         }
         if (cudaEventRecord(e, st) != cudaSuccess) failed = true;
-        ev.push_back(e);
+        return e;
     }
+    void mark() {
+        cudaEvent_t e = record();
+        if (e) rec.ev.push_back(e);
+    }
+    // events around the coupling kernel alone (phase slot 6)
+    void kernel_begin() { if (!rec.k0) rec.k0 = record(); }
+    void kernel_end() { if (rec.k0 && !rec.k1) rec.k1 = record(); }
     int commit() {
         if (!A || !A->timing.on) return 0;
         if (failed) {
-            for (auto e : ev) A->timing.free_events.push_back(e);
+            for (auto e : rec.ev) A->timing.free_events.push_back(e);
+            if (rec.k0) A->timing.free_events.push_back(rec.k0);
+            if (rec.k1) A->timing.free_events.push_back(rec.k1);
             set_error("timing event record failed");
             return H2_E_CUDA;
         }
-        A->timing.pending.push_back(ev);
-        ev.clear();
+        A->timing.pending.push_back(rec);
+        rec = TimingRecord();
         return 0;
     }
 };
@@ -502,6 +511,7 @@ int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int
     marks.mark();
     const unsigned NL = (unsigned)A->leaves.size();
     if ((rc = forward_pass<T, RM, CN>(A, V, E, Xp, xhat, m, gy, gzk, st, sb, marks))) return rc;
+    marks.kernel_begin();
     if (transposed)
         k_coupling<T, RM, CN, true><<<dim3((unsigned)A->nc, gy, gzk), kThreads, 0, st>>>(
             A->d_admT_rowptr, A->d_admT_row, A->d_admT_blk, S, xhat, yhat, k, m);
@@ -509,6 +519,7 @@ int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int
         k_coupling<T, RM, CN, false><<<dim3((unsigned)A->nc, gy, gzk), kThreads, 0, st>>>(
             A->d_adm_rowptr, A->d_adm_col, nullptr, S, xhat, yhat, k, m);
     H2_LAUNCH_CHECK();
+    marks.kernel_end();
     marks.mark();
     if ((rc = backward_pass<T, RM, CN>(A, E, yhat, m, gy, gzk, st, sb))) return rc;
     marks.mark();
@@ -602,7 +613,9 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         cp.k = k;
         cp.ldc = mc;
         cp.err = A->err_dev;
+        marks.kernel_begin();
         if (cp.n_items > 0 && (rc = launch_tc_gemm(0, kind, cp, std::min(cp.n_items, grid_cap), st))) return rc;
+        marks.kernel_end();
         marks.mark();
         if ((rc = backward_pass<float, RM, CN>(A, E, yhat, mc, gy, gzk, st, sbc))) return rc;
         if ((rc = launch_pack_act(yhat, mc, (int)nc, nullptr, nullptr, k, nullptr, KP, mc, R, ycm, es, st))) return rc;

@@ -90,7 +90,7 @@ EXPORTS = ["h2_build", "h2_free", "h2_info", "h2_matmul", "h2_matmul_transposed"
            "h2_autotune",
            "h2_tree_build", "h2_tree_view_get", "h2_tree_free", "h2_last_error_string", "h2_version"]
 H2_NPHASE = 8
-PHASES = ["gather", "leaf_fwd", "up", "coupling", "down", "leaf_bwd_near"]
+PHASES = ["gather", "leaf_fwd", "up", "coupling", "down", "leaf_bwd_near", "coupling_kernel"]
 
 _lib = None
 
