@@ -181,9 +181,12 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    cfg = CONFIGS[WORKLOAD]
+    workload = args.workload
+    cfg = CONFIGS[workload]
     n, m = cfg["n"], cfg["m"]
     peaks, peak_kind = _peaks()
+    metric = METRIC if workload == WORKLOAD else (
+        f"H2MM GFLOP/s (n={n}, q={cfg['q']}, m={m} per GPU; block-CG time to 1e-8 mixed vs FP64 reported alongside)")
 
     pts = sphere_points(n, cfg["point_seed"])
     t0 = time.perf_counter()
@@ -313,25 +316,35 @@ def run_ours(args):
                 ("fp64_pcg", "f64", 0, 0.0, "columnwise", "block_jacobi"),
                 ("mixed_f32_gram_pcg", "f32", 2, 0.1, "gram", "block_jacobi"),
                 ("fp64_gram_pcg", "f64", 0, 0.0, "gram", "block_jacobi"))
+        big = workload != WORKLOAD
         for name, inner, refine, itol, variant, pc in runs:
             if variant == "gram" and m > 64:
                 continue
+            if big and name in ("mixed_f32_restarted",):
+                continue
+            # on the larger workloads the FP64 solves (~1 h) are run for a capped number of
+            # iterations and reported per iteration
+            cap = args.fp64_iter_cap if (big and inner == "f64") else args.solve_max_iter
             Xs = torch.zeros_like(B)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            r = G.block_cg(B, Xs, tol=1e-8, max_iter=args.solve_max_iter, dtype=inner, refine=refine,
+            r = G.block_cg(B, Xs, tol=1e-8, max_iter=cap, dtype=inner, refine=refine,
                            inner_tol=itol, check_every=4, variant=variant, precond=pc)
             torch.cuda.synchronize()
-            solve[name] = {"seconds": round(time.perf_counter() - t0, 3), "status": r.status_name,
+            secs = time.perf_counter() - t0
+            solve[name] = {"seconds": round(secs, 3), "status": r.status_name,
                            "iterations": int(r.iterations), "outer_steps": int(r.outer_steps),
                            "h2mm_calls": int(r.h2mm_calls),
                            "max_true_rel_residual": float(np.max(r.rel_residual))}
-        if solve["fp64"]["seconds"] > 0:
+            if big and inner == "f64":
+                solve[name]["status"] = "capped" if r.status_name != "ok" else "ok"
+                solve[name]["seconds_per_iteration"] = round(secs / max(int(r.iterations), 1), 5)
+        if solve["fp64"]["status"] == "ok" and solve["mixed_f32"]["status"] == "ok":
             solve["speedup_mixed_vs_fp64"] = round(solve["fp64"]["seconds"] / solve["mixed_f32"]["seconds"], 3)
         # the fastest mixed solve against the paper's FP64 block CG and against the fastest FP64 solve
         mixed = {k: v["seconds"] for k, v in solve.items() if k.startswith("mixed") and v["status"] == "ok"}
         fp64 = {k: v["seconds"] for k, v in solve.items() if k.startswith("fp64") and v["status"] == "ok"}
-        if mixed and fp64:
+        if mixed and fp64 and "fp64" in fp64:
             best_m, best_f = min(mixed, key=mixed.get), min(fp64, key=fp64.get)
             solve["fastest_mixed"] = best_m
             solve["fastest_fp64"] = best_f
@@ -339,18 +352,19 @@ def run_ours(args):
             solve["speedup_fastest_mixed_vs_fastest_fp64"] = round(fp64[best_f] / mixed[best_m], 3)
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        c_flops, c_times, c_build = oracle_products(CONFIGS[WORKLOAD], steps=3, warmup=0)
+    # the oracle holds every block in host memory: timed on the default workload only
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and workload == WORKLOAD:
+        c_flops, c_times, c_build = oracle_products(cfg, steps=3, warmup=0)
         ct = sum(c_times) / len(c_times)
         cpu = {"value": round(c_flops / ct / 1e9, 3), "unit": "GFLOP/s", "cores": _cpu_cores(), "kind": "oracle",
                "sample": f"3 FP64 oracle products at n={n}, q={cfg['q']}, m={m}; oracle build {c_build:.1f} s "
                          f"untimed"}
 
     line = {
-        "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "metric": metric, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "q": cfg["q"], "k": k, "m_per_gpu": m, "leaf": cfg["leaf"],
+        "config": {"workload": workload, "n": n, "q": cfg["q"], "k": k, "m_per_gpu": m, "leaf": cfg["leaf"],
                    "eta": cfg["eta"], "kernel": "exp(-r/0.5)+1e-2*I", "parallelism": f"column shards x{ws}",
                    "l2": f"inputs larger than L2 (matrix data {info['bytes_f32'] / 1e9:.2f} GB FP32, "
                          f"{info['bytes_f64'] / 1e9:.2f} GB FP64)",
@@ -427,6 +441,64 @@ def run_mvm_vs_mm(args):
     return 0
 
 
+def run_batch(args):
+    """The batch workload on one GPU: 64 ellipsoid systems, n log-uniform in
+    [2048, 32768], m in {1..64}, q in {3, 4}.  Times the FP32 product of all
+    systems as one CUDA-graph launch against a loop of per-system products,
+    after the autotuner picked each matrix's FP32 path, and the batched mixed
+    solve (Gram variant).  Prints one JSON line; not a bench line."""
+    import torch
+    import paper_2509_17257_gb300 as P
+    from workloads import batch_specs, ellipsoid_points
+    specs = batch_specs(64, 3, 2048, 32768)
+    mats = [P.H2Matrix(ellipsoid_points(sp["n"], sp["axes"], sp["point_seed"]), q=sp["q"], leaf_size=64, eta=2.0,
+                       sigma=1e-2, precisions=("f32",)) for sp in specs]
+    tuned = [P.h2_autotune(mm.handle, sp["m"]) for mm, sp in zip(mats, specs)]
+    Xs = [torch.from_numpy(gaussian_rhs(sp["n"], sp["m"], sp["rhs_seed"])).cuda() for sp in specs]
+    Ys = [torch.zeros_like(x) for x in Xs]
+    flops = sum(mm.flops(sp["m"]) for mm, sp in zip(mats, specs))
+    Bt = P.H2Batch(mats)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def clock(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    def loop():
+        for mm, x, y in zip(mats, Xs, Ys):
+            mm.matmul(x, y, dtype="f32")
+
+    t_loop = clock(loop, 10)
+    t_graph = clock(lambda: Bt.matmul(Xs, Ys, dtype="f32"), 10)
+    Bs = [torch.from_numpy(gaussian_rhs(sp["n"], sp["m"], sp["rhs_seed"] + 7)).cuda() for sp in specs]
+    Xb = [torch.zeros_like(b) for b in Bs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = Bt.block_cg(Bs, Xb, tol=1e-8, max_iter=3000, dtype="f32", inner_tol=0.1, check_every=4, variant="gram")
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    out = {"experiment": "batch", "systems": len(specs), "total_n": sum(sp["n"] for sp in specs),
+           "total_columns": sum(sp["m"] for sp in specs), "gflop_per_batched_product": round(flops / 1e9, 3),
+           "ms_loop": round(t_loop, 3), "ms_graph": round(t_graph, 3),
+           "gflops_graph": round(flops / (t_graph * 1e-3) / 1e9, 1), "graph_speedup": round(t_loop / t_graph, 2),
+           "tensor_core_systems": sum(1 for a, b in tuned if 0 <= a <= b),
+           "solve_seconds": round(t_solve, 3),
+           "solve_status": {str(k): v for k, v in
+                            __import__("collections").Counter(r.status_name for r in res).items()},
+           "solve_max_iterations": max(r.iterations for r in res),
+           "max_true_rel_residual_ok": max(float(r.rel_residual.max()) for r in res if r.status == 0)}
+    print(json.dumps(out), flush=True)
+    Bt.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -437,6 +509,11 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve-max-iter", type=int, default=8000)
+    ap.add_argument("--workload", choices=sorted(CONFIGS), default=WORKLOAD,
+                    help="workload of the bench line (default: the precision workload, n = 65536)")
+    ap.add_argument("--fp64-iter-cap", type=int, default=60,
+                    help="iteration cap of the FP64 solves on workloads other than the default")
+    ap.add_argument("--batch", action="store_true", help="run the batch workload (64 systems) experiment")
     ap.add_argument("--mvm-vs-mm", action="store_true",
                     help="run the MVM-vs-MM experiment (m single-column products vs one m-column product)")
     args = ap.parse_args()
@@ -444,6 +521,8 @@ def main():
         args.warmup = 3
     if args.mvm_vs_mm:
         return run_mvm_vs_mm(args)
+    if args.batch:
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

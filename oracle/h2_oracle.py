@@ -65,6 +65,7 @@ __all__ = [
     "block_pcg",
     "block_cg_gram",
     "GRAM_DEFLATE",
+    "H2Rows",
 ]
 
 
@@ -452,6 +453,99 @@ def kernel_matrix(points: np.ndarray, g, sigma: float = 0.0) -> np.ndarray:
     K = g(points[:, None, :], points[None, :, :])
     K[np.diag_indices(points.shape[0])] += sigma
     return K
+
+
+# ---------------------------------------------------------------------------
+# Selected rows of the product for large n (same H² matrix, built lazily)
+# ---------------------------------------------------------------------------
+class H2Rows:
+    """The H² matrix of :class:`H2Matrix` without its stored blocks, for sizes
+    where those do not fit (n up to 2²⁰): the trees and nodes are built, the
+    forward transformation of Alg. "forward/backward" is run with V_t and
+    E_{t'} formed on the fly, and rows i of  α(Â + σI)X  are assembled one by
+    one from the definition of Â (Def. "H²-matrix"):
+
+        (ÂX)_i = Σ_{t ∋ i} V_t[i, :] Σ_{b=(t,s)∈L+} S_b x̂_s  +  Σ_{b=(t_i,s)∈L-} G_b[i, :] X|_ŝ,
+
+    where t runs over the ancestors of the leaf t_i that holds i and
+    V_t[i, :] = V_{t_i}[i, :] E_{t_i} E_{father(t_i)} … (the nesting
+    V_t|_{t̂'} = V_{t'} E_{t'}).  S_b and G_b are formed only for the blocks
+    that touch the requested rows.
+    """
+
+    def __init__(self, points, q=3, leaf_size=64, eta=2.0, sigma=0.0, length=0.5):
+        self.points = np.ascontiguousarray(points, dtype=np.float64)
+        self.n = self.points.shape[0]
+        self.q, self.k, self.eta, self.sigma = q, q ** 3, eta, float(sigma)
+        self.g = exp_kernel(length)
+        self.root = build_cluster_tree(self.points, leaf_size)
+        self.clusters = clusters_preorder(self.root)
+        self.nodes = {c.id: cluster_nodes(c, q) for c in self.clusters}
+        self.tnodes = {c.id: tensor_nodes(self.nodes[c.id]) for c in self.clusters}
+        adm, near = leaf_blocks(build_block_tree(self.root, self.root, eta))
+        self.adm_of, self.near_of = {}, {}
+        for b in adm:
+            self.adm_of.setdefault(b.t.id, []).append(b.s)
+        for b in near:
+            self.near_of.setdefault(b.t.id, []).append(b.s)
+        self.n_adm, self.n_near = len(adm), len(near)
+        # leaf holding each original index, and the position inside it
+        self.leaf_of = np.empty(self.n, dtype=np.int64)
+        self.pos_in_leaf = np.empty(self.n, dtype=np.int64)
+        self.by_id = {c.id: c for c in self.clusters}
+        for c in self.clusters:
+            if c.is_leaf:
+                self.leaf_of[c.idx] = c.id
+                self.pos_in_leaf[c.idx] = np.arange(c.size)
+
+    def V(self, c):
+        return tensor_lagrange(self.nodes[c.id], self.points[c.idx])
+
+    def E(self, c):
+        return tensor_lagrange(self.nodes[c.parent.id], self.tnodes[c.id])
+
+    def forward(self, X):
+        """x̂_s for every cluster (Alg. "forward/backward", forward part)."""
+        X = np.asarray(X, dtype=np.float64)
+        xhat = {}
+        for c in reversed(self.clusters):  # sons before fathers
+            if c.is_leaf:
+                xhat[c.id] = self.V(c).T @ X[c.idx]
+            else:
+                acc = np.zeros((self.k, X.shape[1]))
+                for c2 in c.sons:
+                    acc += self.E(c2).T @ xhat[c2.id]
+                xhat[c.id] = acc
+        return xhat
+
+    def rows(self, alpha, X, rows, xhat=None):
+        """Rows ``rows`` (original indices) of α(Â + σI)X, shape (len(rows), m)."""
+        X = np.asarray(X, dtype=np.float64)
+        if xhat is None:
+            xhat = self.forward(X)
+        out = np.zeros((len(rows), X.shape[1]))
+        for r, i in enumerate(rows):
+            t = self.by_id[int(self.leaf_of[i])]
+            a = int(self.pos_in_leaf[i])
+            v = self.V(t)[a]  # V_t[i, :] at the leaf
+            acc = np.zeros(X.shape[1])
+            for s in self.near_of.get(t.id, []):
+                acc += self.g(self.points[i][None, :], self.points[s.idx]) @ X[s.idx]
+            c = t
+            while c is not None:
+                for s in self.adm_of.get(c.id, []):
+                    S = self.g(self.tnodes[c.id][:, None, :], self.tnodes[s.id][None, :, :])
+                    acc += v @ (S @ xhat[s.id])
+                if c.parent is not None:
+                    v = v @ self.E(c)
+                c = c.parent
+            out[r] = alpha * (acc + self.sigma * X[i])
+        return out
+
+    def coupling_grads(self, Lam, X, pairs):
+        """−λ̂_t x̂_sᵀ for the admissible pairs (t.id, s.id) (see adjoint_grads)."""
+        lh, xh = self.forward(Lam), self.forward(X)
+        return {(t, s): -(lh[t] @ xh[s].T) for t, s in pairs}
 
 
 # ---------------------------------------------------------------------------
