@@ -21,6 +21,7 @@ H²-matrices"):
 * the same recurrences with m×m Gram matrices in place of the per-column
   scalars (O'Leary's block CG; not in the paper)      -> :func:`block_cg_gram`
 * Sec. 5.1, Alg. "pcg block" with a block-Jacobi M  -> :func:`block_pcg`
+* Sec. 5.2, Alg. "pgmres block" (restarted, per column) -> :func:`block_gmres`
 
 Readings where the paper is silent (split rule, diam/dist of point boxes,
 interpolation nodes, kernel, shift, stopping rule) are the ones stated in the
@@ -66,6 +67,8 @@ __all__ = [
     "block_cg_gram",
     "GRAM_DEFLATE",
     "H2Rows",
+    "block_gmres",
+    "GMRESResult",
 ]
 
 
@@ -732,6 +735,123 @@ def block_cg_gram(apply_A, B: np.ndarray, X0: np.ndarray | None = None, tol: flo
             break
     rel = np.linalg.norm(R, axis=0) / bn
     return CGResult(X=X, iterations=it, col_iterations=col_it, rel_residual=rel, status=status)
+
+
+# ---------------------------------------------------------------------------
+# Block GMRES (Sec. 5.2, Alg. "pgmres block"): every column runs restarted
+# GMRES(ℓ) on its own Krylov space; one block product per step
+# ---------------------------------------------------------------------------
+@dataclass
+class GMRESResult:
+    X: np.ndarray
+    iterations: int            # Arnoldi steps, summed over restart cycles (max over columns)
+    cycles: int
+    col_iterations: np.ndarray
+    rel_residual: np.ndarray   # |M⁻¹(b - Ax)| / |M⁻¹ b| estimate at exit (the Givens residual)
+    status: str
+
+
+def _givens(a: float, b: float):
+    """(c, s) with [c s; -s c] [a; b] = [r; 0], r = hypot(a, b) ≥ 0."""
+    if b == 0.0:
+        return 1.0, 0.0
+    r = math.hypot(a, b)
+    return a / r, b / r
+
+
+def block_gmres(apply_A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, restart: int = 30,
+                max_iter: int = 10000, apply_Minv=None) -> GMRESResult:
+    """Alg. "pgmres block": left-preconditioned GMRES(ℓ = restart) per column.
+
+    One cycle, for every column i at once (the block product a = M⁻¹A q is
+    the only coupling):  r = M⁻¹(b − Ax), β_i = |r_i|, q_0 = r/β, r̂ = β e_1;
+    for k = 0, 1, …:  a = M⁻¹A q_k;  h_{0..k} = V_kᵀ a (all at once, as
+    printed: classical Gram–Schmidt);  a −= V_k h;  h_{k+1,k} = |a|;
+    q_{k+1} = a / h_{k+1,k};  the earlier Givens rotations are applied to the
+    new column of H, a new rotation G_k removes h_{k+1,k} and is applied to r̂.
+    The cycle ends after ℓ steps or when every column has |r̂_{k+1}| ≤ tol·|r̂⁰|
+    (reading of the stopping test: relative to the column's initial
+    preconditioned residual of the first cycle, the GMRES analogue of the CG
+    rule); then x_i += V y_i with R y_i = r̂ (back substitution), and the
+    next cycle restarts from the new x.  Columns that met the tolerance stop
+    expanding their basis (frozen), as in block CG.  A zero h_{k+1,k} is a
+    lucky breakdown: the column's Krylov space is invariant and its solution
+    exact after the update.
+    """
+    B = np.asarray(B, dtype=np.float64)
+    n, m = B.shape
+    Minv = (lambda V: V) if apply_Minv is None else apply_Minv
+    X = np.zeros((n, m)) if X0 is None else np.array(X0, dtype=np.float64)
+    bn = np.linalg.norm(np.asarray(Minv(B)), axis=0)
+    bn[bn == 0.0] = 1.0
+    col_it = np.zeros(m, dtype=np.int64)
+    done = np.zeros(m, dtype=bool)
+    rel = np.ones(m)
+    total, cycles = 0, 0
+    status = "converged"
+    while True:
+        R = np.asarray(Minv(B - apply_A(X)), dtype=np.float64)
+        beta = np.linalg.norm(R, axis=0)
+        rel = beta / bn
+        done = rel <= tol
+        if done.all():
+            break
+        if total >= max_iter:
+            status = "noconverge"
+            break
+        cycles += 1
+        V = np.zeros((restart + 1, n, m))
+        H = np.zeros((restart + 1, restart, m))
+        cs = np.zeros((restart, m))
+        sn = np.zeros((restart, m))
+        rh = np.zeros((restart + 1, m))
+        act = ~done
+        for i in range(m):
+            if act[i]:
+                V[0, :, i] = R[:, i] / beta[i]
+                rh[0, i] = beta[i]
+        steps = np.zeros(m, dtype=np.int64)
+        k = 0
+        while k < restart and act.any() and total < max_iter:
+            Q = np.where(act[None, :], V[k], 0.0)
+            Aq = np.asarray(Minv(apply_A(Q)), dtype=np.float64)
+            total += 1
+            for i in range(m):
+                if not act[i]:
+                    continue
+                a = Aq[:, i].copy()
+                h = V[:k + 1, :, i] @ a            # all inner products first (CGS)
+                a -= V[:k + 1, :, i].T @ h
+                hn = float(np.linalg.norm(a))
+                H[:k + 1, k, i] = h
+                H[k + 1, k, i] = hn
+                if hn > 0.0:
+                    V[k + 1, :, i] = a / hn
+                for j in range(k):                 # earlier rotations on the new column
+                    t = cs[j, i] * H[j, k, i] + sn[j, i] * H[j + 1, k, i]
+                    H[j + 1, k, i] = -sn[j, i] * H[j, k, i] + cs[j, i] * H[j + 1, k, i]
+                    H[j, k, i] = t
+                c, s_ = _givens(H[k, k, i], H[k + 1, k, i])
+                cs[k, i], sn[k, i] = c, s_
+                H[k, k, i] = c * H[k, k, i] + s_ * H[k + 1, k, i]
+                H[k + 1, k, i] = 0.0
+                rh[k + 1, i] = -s_ * rh[k, i]
+                rh[k, i] = c * rh[k, i]
+                steps[i] = k + 1
+                col_it[i] += 1
+                if abs(rh[k + 1, i]) / bn[i] <= tol or hn == 0.0:
+                    act[i] = False
+            k += 1
+        for i in range(m):
+            kk = int(steps[i])
+            if kk == 0:
+                continue
+            y = np.zeros(kk)
+            for j in range(kk - 1, -1, -1):        # R y = r̂ (upper triangular)
+                y[j] = (rh[j, i] - H[j, j + 1:kk, i] @ y[j + 1:kk]) / H[j, j, i]
+            X[:, i] += V[:kk, :, i].T @ y
+    return GMRESResult(X=X, iterations=int(col_it.max()) if m else 0, cycles=cycles, col_iterations=col_it,
+                       rel_residual=rel, status=status)
 
 
 # ---------------------------------------------------------------------------
