@@ -230,6 +230,34 @@ typedef struct h2_cg_result {
 int h2_block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
                 const h2_cg_params* params, h2_cg_result* res);
 
+/* ---- block GMRES (Sec. 5.2, Alg. "pgmres block") -------------------------
+ * Every column runs restarted, left-preconditioned GMRES(restart) on its own
+ * Krylov space; one block product a = M⁻¹ A q per step (in `dtype`); the
+ * Arnoldi step orthogonalises with all inner products first (classical
+ * Gram–Schmidt, as the algorithm prints it) and eliminates the new subdiagonal
+ * entry with a Givens rotation.  Every restart recomputes r = M⁻¹(b − A x)
+ * with the FP64 product, so a low-precision `dtype` gives a mixed-precision
+ * solve refined in FP64.  Column i stops extending its basis once its Givens
+ * residual |r̂| ≤ tol·|M⁻¹ b_i|; the solve ends when every column's FP64
+ * preconditioned residual at a restart meets that bound.  For any A (no
+ * symmetry needed). */
+typedef struct h2_gmres_params {
+    double tol;          /* per-column relative (preconditioned) residual target                 */
+    int32_t max_iter;    /* cap on Arnoldi steps (block products), summed over restarts          */
+    int32_t restart;     /* ℓ: basis size of one cycle, 1..64                                     */
+    int32_t dtype;       /* precision of the product inside a cycle                              */
+    int32_t precond;     /* h2_precond (H2_PRECOND_BLOCK_JACOBI: left preconditioning)             */
+    void* stream;        /* cudaStream_t                                                          */
+} h2_gmres_params;
+
+/* Solve A X = B (device B and X, n×m, ldb/ldx >= m; X holds the initial guess
+ * and receives the solution).  res: iterations = Arnoldi steps of the slowest
+ * column, outer_steps = restart cycles, rel_residual = |b − A x|/|b| in FP64
+ * at exit.  Returns H2_OK or H2_E_NOCONVERGE (res filled either way).  Device
+ * memory: (restart + 3)·n·m doubles plus O(m·restart²). */
+int h2_block_gmres(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
+                   const h2_gmres_params* params, h2_cg_result* res);
+
 /* ---- parameters of A and the adjoint -------------------------------------
  * The method's data that a caller may differentiate: the coupling matrices
  * S_b (Eq. (h2_admissible)), in admissible-list order (the row-cluster lists

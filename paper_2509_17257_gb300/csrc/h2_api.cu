@@ -257,4 +257,9 @@ int h2_block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t l
     return h2::block_cg(A, B, ldb, X, ldx, m, params, res);
 }
 
+int h2_block_gmres(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
+                   const h2_gmres_params* params, h2_cg_result* res) {
+    return h2::block_gmres(A, B, ldb, X, ldx, m, params, res);
+}
+
 }  // extern "C"

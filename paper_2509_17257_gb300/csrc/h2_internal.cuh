@@ -300,6 +300,8 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
                   bool overwrite);
 int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
              const h2_cg_params* p, h2_cg_result* res);
+int block_gmres(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
+                const h2_gmres_params* p, h2_cg_result* res);
 
 // Bytes of scratch one product needs (gathered X, x̂, ŷ, transfer-pass
 // bookkeeping), and the product run in caller-provided scratch of at least
@@ -318,8 +320,9 @@ int product_prepare(h2_matrix* A, int64_t m, int32_t dtype, cudaStream_t st);
 int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st);
 int launch_pack_tiles(const TcPackTile* tiles, int64_t count, const double* src, uint8_t* dst, int es,
                       cudaStream_t st);
-int launch_pack_act(const float* src, int64_t ld, int ids, const int32_t* base, const int32_t* kdim, int kdim_fixed,
-                    const int64_t* koff, int kp_fixed, int mc, int R, uint8_t* dst, int es, cudaStream_t st);
+int launch_pack_act(const float* src, int64_t ld, int ids, const int32_t* idmap, const int32_t* base,
+                    const int32_t* kdim, int kdim_fixed, const int64_t* koff, int kp_fixed, int mc, int R,
+                    uint8_t* dst, int es, cudaStream_t st);
 int launch_zero_clusters(const int32_t* ids, int count, float* yhat, int k, int ldc, int mc, cudaStream_t st);
 int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st);
 

@@ -595,10 +595,10 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
             k_gather<float><<<g, 256, 0, st>>>(X + c0, ldx, A->d_perm, n, mc, Xp);
             H2_LAUNCH_CHECK();
         }
-        if ((rc = launch_pack_act(Xp, mc, NL, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, R, Xcm, es, st))) return rc;
+        if ((rc = launch_pack_act(Xp, mc, NL, nullptr, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, R, Xcm, es, st))) return rc;
         marks.mark();
         if ((rc = forward_pass<float, RM, CN>(A, V, E, Xp, xhat, mc, gy, gzk, st, sbc, marks))) return rc;
-        if ((rc = launch_pack_act(xhat, mc, (int)nc, nullptr, nullptr, k, nullptr, KP, mc, R, xcm, es, st))) return rc;
+        if ((rc = launch_pack_act(xhat, mc, (int)nc, nullptr, nullptr, nullptr, k, nullptr, KP, mc, R, xcm, es, st))) return rc;
         if ((rc = launch_zero_clusters(D.c_zero, D.c_nzero, yhat, k, mc, mc, st))) return rc;
         TcGemmParams cp{};
         cp.n_items = D.c_nitems;
@@ -618,7 +618,7 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         marks.kernel_end();
         marks.mark();
         if ((rc = backward_pass<float, RM, CN>(A, E, yhat, mc, gy, gzk, st, sbc))) return rc;
-        if ((rc = launch_pack_act(yhat, mc, (int)nc, nullptr, nullptr, k, nullptr, KP, mc, R, ycm, es, st))) return rc;
+        if ((rc = launch_pack_act(yhat, mc, NL, A->d_leaves, nullptr, nullptr, k, nullptr, KP, mc, R, ycm, es, st))) return rc;
         marks.mark();
         TcGemmParams lp{};
         lp.n_items = D.l_nitems;

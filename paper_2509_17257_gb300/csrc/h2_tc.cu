@@ -166,27 +166,47 @@ __global__ void k_pack_tiles(const TcPackTile* __restrict__ tiles, int64_t count
 // remainder (h = 1): BF16 (es = 2): bf16(x) and bf16(x - bf16(x)); TF32 (es = 4):
 // x itself (the MMA reads tf32(x)) and x - tf32(x).  Columns κ < kdim(id) read
 // src[(base(id) + κ) * ld + i]; zero padding to R rows and kp(id) columns;
-// kp(id) = kp_fixed, or koff[id+1] - koff[id].
-__global__ void k_pack_act(const float* __restrict__ src, int64_t ld, int ids, const int32_t* __restrict__ base,
-                           const int32_t* __restrict__ kdim, int kdim_fixed, const int64_t* __restrict__ koff,
-                           int kp_fixed, int mc, int R, uint8_t* __restrict__ dst, int es) {
-    for (int id = blockIdx.x; id < ids; id += gridDim.x) {
+// kp(id) = kp_fixed, or koff[id+1] - koff[id].  With idmap only the ids
+// idmap[0..ids) are packed.
+// Threads walk the tile in its memory order, 4 bytes each, so a warp writes one
+// whole 128-byte core matrix (8 rows × 16 bytes).
+__global__ void k_pack_act(const float* __restrict__ src, int64_t ld, int ids, const int32_t* __restrict__ idmap,
+                           const int32_t* __restrict__ base, const int32_t* __restrict__ kdim, int kdim_fixed,
+                           const int64_t* __restrict__ koff, int kp_fixed, int mc, int R, uint8_t* __restrict__ dst,
+                           int es) {
+    const int per = 16 / es;  // elements of one core-matrix row
+    for (int j = blockIdx.x; j < ids; j += gridDim.x) {
+        const int id = idmap ? idmap[j] : j;
         const int kp = koff ? (int)(koff[id + 1] - koff[id]) : kp_fixed;
         const int64_t tile = (koff ? koff[id] : (int64_t)id * kp_fixed) * (int64_t)R * es;
         const int kd = kdim ? kdim[id] : kdim_fixed;
         const int64_t b = base ? (int64_t)base[id] : (int64_t)id * kdim_fixed;
-        for (int e = threadIdx.x; e < R * kp; e += blockDim.x) {
-            const int r = e % R, c = e / R;
+        const int cgroups = kp / per;
+        const int words = R * kp * es / 4;  // 4-byte words of the tile
+        uint32_t* out = (uint32_t*)(dst + tile);
+        for (int w = threadIdx.x; w < words; w += blockDim.x) {
+            const int cmi = w >> 5, within = (w & 31) * 4;  // core matrix, byte inside it
+            const int r = (cmi / cgroups) * 8 + (within >> 4);
+            const int c0 = (cmi % cgroups) * per + ((within & 15) / es);
             const int i = r >> 1;
-            float x = 0.f;
-            if (i < mc && c < kd) x = src[(b + c) * ld + i];
-            if (es == 2) {
-                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                const float v = (r & 1) ? x - __bfloat162float(hi) : x;
-                *(__nv_bfloat16*)(dst + tile + cm_off(r, c, kp, 2)) = __float2bfloat16_rn(v);
+            const bool lo = r & 1;
+            if (es == 4) {
+                float x = 0.f;
+                if (i < mc && c0 < kd) x = src[(b + c0) * ld + i];
+                const float v = lo ? x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u) : x;
+                out[w] = __float_as_uint(v);
             } else {
-                const float v = (r & 1) ? x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u) : x;
-                *(float*)(dst + tile + cm_off(r, c, kp, 4)) = v;
+                uint32_t pk = 0;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int c = c0 + u;
+                    float x = 0.f;
+                    if (i < mc && c < kd) x = src[(b + c) * ld + i];
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                    const __nv_bfloat16 v = lo ? __float2bfloat16_rn(x - __bfloat162float(hi)) : hi;
+                    pk |= (uint32_t)__bfloat16_as_ushort(v) << (16 * u);
+                }
+                out[w] = pk;
             }
         }
     }
@@ -559,11 +579,12 @@ int launch_pack_tiles(const TcPackTile* tiles, int64_t count, const double* src,
     return 0;
 }
 
-int launch_pack_act(const float* src, int64_t ld, int ids, const int32_t* base, const int32_t* kdim, int kdim_fixed,
-                    const int64_t* koff, int kp_fixed, int mc, int R, uint8_t* dst, int es, cudaStream_t st) {
+int launch_pack_act(const float* src, int64_t ld, int ids, const int32_t* idmap, const int32_t* base,
+                    const int32_t* kdim, int kdim_fixed, const int64_t* koff, int kp_fixed, int mc, int R,
+                    uint8_t* dst, int es, cudaStream_t st) {
     if (ids <= 0) return 0;
     const unsigned g = (unsigned)std::min(ids, 152 * 8);
-    k_pack_act<<<g, 256, 0, st>>>(src, ld, ids, base, kdim, kdim_fixed, koff, kp_fixed, mc, R, dst, es);
+    k_pack_act<<<g, 256, 0, st>>>(src, ld, ids, idmap, base, kdim, kdim_fixed, koff, kp_fixed, mc, R, dst, es);
     H2_LAUNCH_CHECK();
     return 0;
 }

@@ -66,6 +66,11 @@ class CGParams(C.Structure):
                 ("precond", C.c_int32), ("stream", C.c_void_p)]
 
 
+class GMRESParams(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("restart", C.c_int32), ("dtype", C.c_int32),
+                ("precond", C.c_int32), ("stream", C.c_void_p)]
+
+
 class CGResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("outer_steps", C.c_int32),
                 ("h2mm_calls", C.c_int32), ("col_iterations", C.POINTER(C.c_int32)),
@@ -84,7 +89,7 @@ class TreeView(C.Structure):
 
 
 #: every symbol include/h2.h declares
-EXPORTS = ["h2_build", "h2_free", "h2_info", "h2_matmul", "h2_matmul_transposed", "h2_matmul_noalloc", "h2_block_cg",
+EXPORTS = ["h2_build", "h2_free", "h2_info", "h2_matmul", "h2_matmul_transposed", "h2_matmul_noalloc", "h2_block_cg", "h2_block_gmres",
            "h2_timing_enable", "h2_timing_query", "h2_coupling_get", "h2_coupling_set", "h2_shift_set",
            "h2_adjoint_grads", "h2_batch_create", "h2_batch_free", "h2_batch_matmul", "h2_batch_block_cg",
            "h2_autotune",
@@ -343,6 +348,29 @@ def h2_block_cg(handle, B, X, tol=1e-8, max_iter=20000, dtype="f64", refine=True
                        res.seconds)
 
 
+def h2_block_gmres(handle, B, X, tol=1e-8, max_iter=20000, restart=30, dtype="f64", precond=None,
+                   stream=None) -> SolveResult:
+    """Block GMRES (restarted, per column, left-preconditioned): solve A X = B
+    for device B and X (X: initial guess in, solution out).  Non-convergence is
+    reported in ``status``, not raised."""
+    n = h2_info(handle)["n"]
+    bp, ldb, m, kb = _ptr_ld(B, "B", n)
+    xp, ldx, mx, kx = _ptr_ld(X, "X", n, writable=True)
+    if mx != m:
+        raise ValueError("B and X must have the same number of columns")
+    it = np.zeros(max(m, 1), dtype=np.int32)
+    rel = np.zeros(max(m, 1), dtype=np.float64)
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    pc = PRECONDS[precond] if precond is None or isinstance(precond, str) else int(precond)
+    prm = GMRESParams(tol, max_iter, restart, dt, pc, _stream_ptr(stream))
+    res = CGResult(0, 0, 0, 0, it.ctypes.data_as(C.POINTER(C.c_int32)), rel.ctypes.data_as(C.POINTER(C.c_double)),
+                   0.0)
+    rc = lib().h2_block_gmres(handle, bp, ldb, xp, ldx, m, C.byref(prm), C.byref(res))
+    _check(rc, "h2_block_gmres", ok=(H2_OK, H2_E_NOCONVERGE))
+    return SolveResult(res.status, res.iterations, res.outer_steps, res.h2mm_calls, it[:m].copy(), rel[:m].copy(),
+                       res.seconds)
+
+
 def h2_autotune(handle, m: int, stream=None):
     """Time the FP32 product on the tensor cores and on the CUDA cores and keep
     the faster; returns (ms tensor-core, ms CUDA-core)."""
@@ -454,6 +482,9 @@ class H2Matrix:
 
     def block_cg(self, B, X, **kw) -> SolveResult:
         return h2_block_cg(self.handle, B, X, **kw)
+
+    def block_gmres(self, B, X, **kw) -> SolveResult:
+        return h2_block_gmres(self.handle, B, X, **kw)
 
     def flops(self, m: int) -> float:
         return self.info["flops_per_col"] * m
