@@ -247,6 +247,7 @@ typedef struct h2_gmres_params {
     int32_t restart;     /* ℓ: basis size of one cycle, 1..64                                     */
     int32_t dtype;       /* precision of the product inside a cycle                              */
     int32_t precond;     /* h2_precond (H2_PRECOND_BLOCK_JACOBI: left preconditioning)             */
+    int32_t transposed;  /* != 0: solve Aᵀ X = B (products with Aᵀ; M is symmetric)                  */
     void* stream;        /* cudaStream_t                                                          */
 } h2_gmres_params;
 

@@ -159,6 +159,16 @@ int upload(h2_matrix* A, T** dst, const std::vector<T>& src, cudaStream_t st) {
     return 0;
 }
 
+// Et[c][μ][ν] = E[c][ν][μ] in FP32 (k×k per cluster).
+__global__ void k_transpose_f32(const double* __restrict__ E, float* __restrict__ Et, int64_t nc, int k) {
+    const int64_t kk = (int64_t)k * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc * kk; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / kk;
+        const int r = (int)((e % kk) / k), q = (int)(e % k);
+        Et[c * kk + (int64_t)q * k + r] = (float)E[e];
+    }
+}
+
 int cast_copy(h2_matrix* A, const double* src, void** dst, int64_t count, cudaStream_t st) {
     int rc = device_alloc(A, dst, (size_t)(count > 0 ? count : 1) * sizeof(float));
     if (rc) return rc;
@@ -372,6 +382,12 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
             // the tensor-core products run their transfer passes on the FP32 copies of V and E
             if ((rc = cast_copy(A, (const double*)A->f64.V, &A->f32.V, (int64_t)n * k, st))) return rc;
             if ((rc = cast_copy(A, (const double*)A->f64.E, &A->f32.E, nc * k * k, st))) return rc;
+        }
+        if (k % 4 == 0) {
+            // transposed transfer matrices for the row-staged downward pass
+            if ((rc = device_alloc(A, &A->f32.Et, (size_t)nc * k * k * sizeof(float)))) return rc;
+            k_transpose_f32<<<1216, 256, 0, st>>>((const double*)A->f64.E, (float*)A->f32.Et, nc, k);
+            H2_LAUNCH_CHECK();
         }
         if ((rc = build_tc(A, want_bf16, want_tf32, st))) return rc;
     }

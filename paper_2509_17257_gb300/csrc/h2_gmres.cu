@@ -308,6 +308,7 @@ int block_gmres(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t l
     }
     if (p->dtype != H2_F64 && p->dtype != H2_F32 && p->dtype != H2_BF16) { set_error("bad dtype"); return H2_E_BADARG; }
     if (p->precond != H2_PRECOND_NONE && p->precond != H2_PRECOND_BLOCK_JACOBI) { set_error("unknown preconditioner"); return H2_E_BADARG; }
+    if (p->transposed && p->dtype == H2_BF16) { set_error("the BF16 product supports A·X only"); return H2_E_UNSUPPORTED; }
     res->status = 0;
     res->iterations = res->outer_steps = res->h2mm_calls = 0;
     res->seconds = 0.0;
@@ -321,6 +322,7 @@ int block_gmres(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t l
     const int64_t n = A->n;
     const int L = p->restart;
     const bool pc = p->precond == H2_PRECOND_BLOCK_JACOBI;
+    const bool tr = p->transposed != 0;
     int rc = 0;
     if (pc && (rc = bj_prepare(A, st))) return rc;
 
@@ -388,7 +390,7 @@ int block_gmres(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t l
         // r = M⁻¹(B − A X) with the FP64 product
         k_gm_copy<<<cg, 256, 0, st>>>(B, ldb, a, n, (int)m);
         ++h2mm;
-        if ((rc = matmul_device(A, -1.0, X, ldx, a, m, m, H2_F64, st, false, false))) return fail(rc);
+        if ((rc = matmul_device(A, -1.0, X, ldx, a, m, m, H2_F64, st, tr, false))) return fail(rc);
         double* R = a;
         if (pc) {
             if ((rc = bj_apply(A, a, Z, n, (int)m, nullptr, dummy, st))) return fail(rc);
@@ -411,7 +413,7 @@ int block_gmres(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t l
             ++h2mm;
             ++total;
             const size_t vk = (size_t)k * nm;
-            if ((rc = matmul_device(A, 1.0, g.V + vk, m, a, m, m, p->dtype, st, false, true))) return fail(rc);
+            if ((rc = matmul_device(A, 1.0, g.V + vk, m, a, m, m, p->dtype, st, tr, true))) return fail(rc);
             double* av = a;
             if (pc) {
                 if ((rc = bj_apply(A, a, Z, n, (int)m, nullptr, dummy, st))) return fail(rc);
@@ -436,7 +438,7 @@ int block_gmres(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t l
     // true FP64 residual per column
     k_gm_copy<<<cg, 256, 0, st>>>(B, ldb, a, n, (int)m);
     ++h2mm;
-    if ((rc = matmul_device(A, -1.0, X, ldx, a, m, m, H2_F64, st, false, false))) return fail(rc);
+    if ((rc = matmul_device(A, -1.0, X, ldx, a, m, m, H2_F64, st, tr, false))) return fail(rc);
     k_gm_relnorm<<<grid, blk, 0, st>>>(a, B, ldb, g, g.rel);
     std::vector<double> rel(m);
     std::vector<int> it(m);

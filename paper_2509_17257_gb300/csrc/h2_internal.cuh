@@ -42,6 +42,7 @@ void set_error(const std::string& msg);
 struct MatData {
     void* V = nullptr;
     void* E = nullptr;
+    void* Et = nullptr;  // FP32 only, k % 4 == 0: E_{t'}ᵀ per cluster (the downward pass reads rows)
     void* S = nullptr;
     void* Near = nullptr;
     int64_t bytes = 0;

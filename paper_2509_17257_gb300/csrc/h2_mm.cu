@@ -388,6 +388,214 @@ __global__ void __launch_bounds__(kThreads) k_leaf_bwd_near(
 }
 
 // Records an event between phases when timing is enabled (h2_timing_enable).
+// ---------------------------------------------------------------------------
+// FP32 transfer passes with the whole contraction staged at once (k % 4 == 0,
+// k <= 64, m % 4 == 0): cp.async moves every operand row of a step (V_t and
+// X|_t̂ at a leaf; E_{s0}, E_{s1}, x̂_{s0}, x̂_{s1} at a father; Eᵀ_c and ŷ_father
+// downwards) into shared memory in 16-byte pieces, then one barrier, then the
+// register-tiled contraction.  The data another CTA of the same launch wrote
+// (x̂ of the sons, ŷ of the father) is copied with .cg (L2, not L1).  The
+// downward pass issues the copy of its (static) transfer matrix before it
+// waits for the father's ready flag.
+// ---------------------------------------------------------------------------
+constexpr int kFastK = 128;  // contraction rows staged at most (two sons of k = 64)
+constexpr int kFastLdA = 68;  // 64 output rows + 4: rows stay 16-byte aligned
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp16_cg(void* s, const void* g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_commit_wait() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// rows [0, rows) of a row-major source (row stride ld floats, `width` floats
+// from column c0, width % 4 == 0) into dst rows of stride dld, from row r0.
+__device__ __forceinline__ void stage_rows(float* dst, int dld, int r0, const float* src, int64_t ld, int rows,
+                                           int width) {
+    const int per = width >> 2;
+    for (int e = threadIdx.x; e < rows * per; e += blockDim.x) {
+        const int r = e / per, q = e % per;
+        cp16_cg(dst + (r0 + r) * dld + 4 * q, src + (int64_t)r * ld + 4 * q);
+    }
+}
+
+// acc[4×CN] += a[0:K][rows 4ty..] ᵀ-contracted with b[0:K][cols CN·tx..]
+template <int CN>
+__device__ __forceinline__ void fast_contract(float (&acc)[4][CN], const float* a, const float* b, int K) {
+    constexpr int NT = 16 * CN;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll 8
+    for (int kk = 0; kk < K; ++kk) {
+        const float4 av = *(const float4*)(a + kk * kFastLdA + 4 * ty);
+        float bv[CN];
+        lds_vec<CN>(b + kk * NT + CN * tx, bv);
+#pragma unroll
+        for (int c = 0; c < CN; ++c) {
+            acc[0][c] = fmaf(av.x, bv[c], acc[0][c]);
+            acc[1][c] = fmaf(av.y, bv[c], acc[1][c]);
+            acc[2][c] = fmaf(av.z, bv[c], acc[2][c]);
+            acc[3][c] = fmaf(av.w, bv[c], acc[3][c]);
+        }
+    }
+}
+
+template <int CN, bool ACCUM>
+__device__ __forceinline__ void fast_store(const float (&acc)[4][CN], float* C, int m, int k, int col0) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int gr = 4 * ty + r;
+        if (gr >= k) continue;
+#pragma unroll
+        for (int c = 0; c < CN; ++c) {
+            const int gc = col0 + CN * tx + c;
+            if (gc >= m) continue;
+            float* p = C + (int64_t)gr * m + gc;
+            if (ACCUM) *p += acc[r][c]; else *p = acc[r][c];
+        }
+    }
+}
+
+template <int CN>
+__global__ void __launch_bounds__(kThreads) k_up_fast(const int32_t* __restrict__ leaves,
+                                                      const int32_t* __restrict__ cl_off,
+                                                      const int32_t* __restrict__ cl_size,
+                                                      const int32_t* __restrict__ parent,
+                                                      const int32_t* __restrict__ son0,
+                                                      const int32_t* __restrict__ son1, const float* __restrict__ V,
+                                                      const float* __restrict__ E, const float* __restrict__ Xp,
+                                                      float* xhat, unsigned* __restrict__ cnt, int k, int m) {
+    constexpr int NT = 16 * CN;
+    extern __shared__ __align__(16) float fsm[];
+    float* a = fsm;                      // [kFastK][kFastLdA]
+    float* b = fsm + kFastK * kFastLdA;  // [kFastK][NT]
+    __shared__ int s_go;
+    const int tile = blockIdx.y, gy = gridDim.y;
+    const int col0 = tile * NT, w = min(NT, m - col0);
+    const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
+    int c = leaves[blockIdx.x];
+    const int off = cl_off[c], nt = cl_size[c];
+    stage_rows(a, kFastLdA, 0, V + (int64_t)off * k, k, nt, k);
+    stage_rows(b, NT, 0, Xp + (int64_t)off * m + col0, m, nt, w);
+    cp_commit_wait();
+    __syncthreads();
+    float acc[4][CN];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < CN; ++q) acc[r][q] = 0.f;
+    fast_contract<CN>(acc, a, b, nt);
+    fast_store<CN, false>(acc, xhat + (int64_t)c * km, m, k, col0);
+    while (true) {
+        const int par = parent[c];
+        if (par < 0) break;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned old = atomicAdd(&cnt[(int64_t)par * gy + tile], 1u);
+            s_go = old == 1u;
+            if (old == 1u) cnt[(int64_t)par * gy + tile] = 0u;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        __threadfence();
+        c = par;
+        const int s0 = son0[c], s1 = son1[c];
+        // x̂_c = E_{s0}ᵀ x̂_{s0} + E_{s1}ᵀ x̂_{s1}: one contraction over 2k rows
+        stage_rows(a, kFastLdA, 0, E + s0 * kk, k, k, k);
+        stage_rows(a, kFastLdA, k, E + s1 * kk, k, k, k);
+        stage_rows(b, NT, 0, xhat + s0 * km + col0, m, k, w);
+        stage_rows(b, NT, k, xhat + s1 * km + col0, m, k, w);
+        cp_commit_wait();
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < CN; ++q) acc[r][q] = 0.f;
+        fast_contract<CN>(acc, a, b, 2 * k);
+        fast_store<CN, false>(acc, xhat + (int64_t)c * km, m, k, col0);
+    }
+}
+
+template <int CN>
+__global__ void __launch_bounds__(kThreads) k_down_fast(const int32_t* __restrict__ order, int n_items,
+                                                        const int32_t* __restrict__ parent,
+                                                        const float* __restrict__ Et, float* yhat,
+                                                        unsigned* __restrict__ claim, int* flag, int epoch,
+                                                        int* __restrict__ err, int k, int m) {
+    constexpr int NT = 16 * CN;
+    extern __shared__ __align__(16) float fsm[];
+    float* a = fsm;
+    float* b = fsm + kFastK * kFastLdA;
+    __shared__ int s_item, s_ok;
+    const int tile = blockIdx.y, gy = gridDim.y;
+    const int col0 = tile * NT, w = min(NT, m - col0);
+    const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(&claim[tile], 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items) break;
+        const int c = order[item];
+        const int par = parent[c];
+        // the transfer matrix does not depend on the father: start its copy first
+        stage_rows(a, kFastLdA, 0, Et + (int64_t)c * kk, k, k, k);
+        cp_commit();
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            if (parent[par] >= 0) {  // the root's ŷ is final after the coupling phase
+                const int* f = flag + (int64_t)par * gy + tile;
+                uint32_t spins = 0;
+                while (ld_acquire(f) != epoch) {
+                    if (++spins > (1u << 24)) { ok = 0; break; }
+                    __nanosleep(32);
+                }
+            }
+            s_ok = ok;
+            if (!ok) atomicExch(err, 8);
+        }
+        __syncthreads();
+        if (!s_ok) {
+            cp_commit_wait();  // no copy of this CTA is left in flight
+            break;
+        }
+        stage_rows(b, NT, 0, yhat + (int64_t)par * km + col0, m, k, w);
+        cp_commit_wait();
+        __syncthreads();
+        float acc[4][CN];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < CN; ++q) acc[r][q] = 0.f;
+        fast_contract<CN>(acc, a, b, k);
+        fast_store<CN, true>(acc, yhat + (int64_t)c * km, m, k, col0);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) st_release(flag + (int64_t)c * gy + tile, epoch);
+    }
+}
+
+int fast_smem_bytes(int cn) { return (kFastK * kFastLdA + kFastK * 16 * cn) * (int)sizeof(float); }
+
+int g_fast_attr_device = -1;
+
+int fast_prepare() {
+    int dev = 0;
+    H2_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev == g_fast_attr_device) return 0;
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_up_fast<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(1)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_up_fast<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(2)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_up_fast<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(4)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_down_fast<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(1)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_down_fast<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(2)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_down_fast<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(4)));
+    g_fast_attr_device = dev;
+    return 0;
+}
+
 struct PhaseMarks {
     h2_matrix* A;
     cudaStream_t st;
@@ -597,7 +805,21 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         }
         if ((rc = launch_pack_act(Xp, mc, NL, nullptr, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, R, Xcm, es, st))) return rc;
         marks.mark();
-        if ((rc = forward_pass<float, RM, CN>(A, V, E, Xp, xhat, mc, gy, gzk, st, sbc, marks))) return rc;
+        // staged transfer passes when the rows are 16-byte multiples (k, mc % 4 == 0, k <= 64)
+        const bool fast = A->f32.Et && k % 4 == 0 && k <= 64 && mc % 4 == 0;
+        const int fcn = mc <= 16 ? 1 : (mc <= 32 ? 2 : 4);
+        if (fast) {
+            if ((rc = fast_prepare())) return rc;
+            const unsigned NLu = (unsigned)NL;
+            if (fcn == 1) k_up_fast<1><<<dim3(NLu, 1), kThreads, fast_smem_bytes(1), st>>>(A->d_leaves, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, k, mc);
+            else if (fcn == 2) k_up_fast<2><<<dim3(NLu, 1), kThreads, fast_smem_bytes(2), st>>>(A->d_leaves, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, k, mc);
+            else k_up_fast<4><<<dim3(NLu, 1), kThreads, fast_smem_bytes(4), st>>>(A->d_leaves, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, k, mc);
+            H2_LAUNCH_CHECK();
+            marks.mark();
+            marks.mark();
+        } else if ((rc = forward_pass<float, RM, CN>(A, V, E, Xp, xhat, mc, gy, gzk, st, sbc, marks))) {
+            return rc;
+        }
         if ((rc = launch_pack_act(xhat, mc, (int)nc, nullptr, nullptr, nullptr, k, nullptr, KP, mc, R, xcm, es, st))) return rc;
         if ((rc = launch_zero_clusters(D.c_zero, D.c_nzero, yhat, k, mc, mc, st))) return rc;
         TcGemmParams cp{};
@@ -617,7 +839,21 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         if (cp.n_items > 0 && (rc = launch_tc_gemm(0, kind, cp, std::min(cp.n_items, grid_cap), st))) return rc;
         marks.kernel_end();
         marks.mark();
-        if ((rc = backward_pass<float, RM, CN>(A, E, yhat, mc, gy, gzk, st, sbc))) return rc;
+        if (fast) {
+            const int n_items = (int)A->down_ptr[A->depth + 1];
+            if (n_items > 0) {
+                H2_CUDA_TRY(cudaMemsetAsync(sbc.flag, 0, (size_t)A->nc * sizeof(int), st));
+                H2_CUDA_TRY(cudaMemsetAsync(sbc.claim, 0, sizeof(unsigned), st));
+                const unsigned g = (unsigned)std::min(n_items, 152 * 4);
+                const float* Et = (const float*)A->f32.Et;
+                if (fcn == 1) k_down_fast<1><<<dim3(g, 1), kThreads, fast_smem_bytes(1), st>>>(A->d_down_list, n_items, A->d_parent, Et, yhat, sbc.claim, sbc.flag, sbc.epoch, sbc.err, k, mc);
+                else if (fcn == 2) k_down_fast<2><<<dim3(g, 1), kThreads, fast_smem_bytes(2), st>>>(A->d_down_list, n_items, A->d_parent, Et, yhat, sbc.claim, sbc.flag, sbc.epoch, sbc.err, k, mc);
+                else k_down_fast<4><<<dim3(g, 1), kThreads, fast_smem_bytes(4), st>>>(A->d_down_list, n_items, A->d_parent, Et, yhat, sbc.claim, sbc.flag, sbc.epoch, sbc.err, k, mc);
+                H2_LAUNCH_CHECK();
+            }
+        } else if ((rc = backward_pass<float, RM, CN>(A, E, yhat, mc, gy, gzk, st, sbc))) {
+            return rc;
+        }
         if ((rc = launch_pack_act(yhat, mc, NL, A->d_leaves, nullptr, nullptr, k, nullptr, KP, mc, R, ycm, es, st))) return rc;
         marks.mark();
         TcGemmParams lp{};

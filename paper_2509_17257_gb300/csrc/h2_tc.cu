@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             int stage = 0;
             uint32_t phase = 0;
             int it = 0, acc = 0;
-            bool issued = false, first = true;
+            bool issued = false;
             uint32_t d = tmem, idesc = 0;
             while (true) {
                 if (!mbar_wait(KIND == 1 ? &split_bar[stage] : &full_bar[stage], phase)) {
@@ -366,17 +366,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                 }
                 const int fl = stage_fl[stage];
                 if (fl & F_END) break;
-                if (fl & F_FIRST) {
-                    acc = it & 1;
-                    if (!mbar_wait(&acce_bar[acc], ((it >> 1) & 1) ^ 1)) {
-                        abort_flag = 1;
-                        atomicExch(p.err, 3);
-                        break;
-                    }
-                    d = tmem + (uint32_t)(acc * kAccCols);
-                    idesc = idesc_for<KIND>(M, stage_np[stage]);
-                    first = true;
+                // every term accumulates from zero in its own TMEM buffer; the epilogue
+                // adds the terms of an item in FP32 registers (round to nearest), so
+                // the tensor-core accumulator never sums more than one term's K steps
+                acc = it & 1;
+                if (!mbar_wait(&acce_bar[acc], ((it >> 1) & 1) ^ 1)) {
+                    abort_flag = 1;
+                    atomicExch(p.err, 3);
+                    break;
                 }
+                d = tmem + (uint32_t)(acc * kAccCols);
+                idesc = idesc_for<KIND>(M, stage_np[stage]);
                 tc_fence_after();
                 const int kp = stage_kp[stage];
                 const uint32_t sA = smem_u32(smem + stage * stage_bytes);
@@ -385,19 +385,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                 for (int kk = 0; kk < kp / KSTEP; ++kk) {
                     const uint64_t ad = smem_desc(sA + kk * 256, 128, sbo);
                     const uint64_t bd = smem_desc(sB + kk * 256, 128, sbo);
-                    mma_issue<KIND>(d, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+                    mma_issue<KIND>(d, ad, bd, idesc, kk == 0 ? 0u : 1u);
                     if (KIND == 1) {
                         const uint64_t bl = smem_desc(sB + b_bytes + kk * 256, 128, sbo);
                         mma_issue<KIND>(d, ad, bl, idesc, 1u);
                     }
                 }
                 issued = true;
-                first = false;
                 mma_commit(&empty_bar[stage]);
-                if (fl & F_LAST) {
-                    mma_commit(&accf_bar[acc]);
-                    ++it;
-                }
+                mma_commit(&accf_bar[acc]);
+                ++it;
                 if (++stage == nst) { stage = 0; phase ^= 1; }
             }
             if (issued) {
@@ -421,7 +418,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             cur_off = p.cl_off[t];
             cur_nt = p.cl_size[t];
         }
-        for (int w = blockIdx.x; w < p.n_items; w += G, ++it) {
+        for (int w = blockIdx.x; w < p.n_items; w += G) {
             // the next item's descriptor (and leaf extent) load while this one waits
             const TcItem nxt = w + G < p.n_items ? p.items[w + G] : TcItem{-1, 0, 0, 0};
             int nxt_off = 0, nxt_nt = 0;
@@ -430,44 +427,53 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                 nxt_off = p.cl_off[t];
                 nxt_nt = p.cl_size[t];
             }
-            const int id = cur.id, np = cur.np;
-            const int acc = it & 1;
-            // warp-uniform wait: a completed phase stays completed, so any lane's
-            // success is the warp's success
-            const bool ok = __any_sync(0xffffffffu, mbar_wait(&accf_bar[acc], (it >> 1) & 1));
-            if (!ok) {
+            const int id = cur.id, np = cur.np, nterms = cur.e1 - cur.e0;
+            float sum[kAccCols];
+#pragma unroll
+            for (int j = 0; j < kAccCols; ++j) sum[j] = 0.f;
+            bool failed = false;
+            for (int term = 0; term < nterms; ++term, ++it) {
+                const int acc = it & 1;
+                // warp-uniform wait: a completed phase stays completed, so any lane's
+                // success is the warp's success
+                const bool ok = __any_sync(0xffffffffu, mbar_wait(&accf_bar[acc], (it >> 1) & 1));
+                if (!ok) {
+                    failed = true;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int cc = 0; cc < kAccCols / 16; ++cc) {
+                    if (16 * cc >= np) break;
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kAccCols + 16 * cc), v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) sum[16 * cc + j] += v[j] + __shfl_xor_sync(0xffffffffu, v[j], 1);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce_bar[acc]);
+            }
+            if (failed) {
                 if (lane == 0) atomicExch(p.err, 6);
                 abort_flag = 1;
                 break;
             }
-            tc_fence_after();
-            const int off = cur_off, nt = cur_nt;
-            for (int c0 = 0; c0 < np; c0 += 16) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kAccCols + c0), v);
+            if (writer) {
+                if (MODE == 0) {
+                    float* out = p.yhat + (int64_t)id * p.k * p.ldc;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 1);
-                if (writer) {
-                    if (MODE == 0) {
-                        float* out = p.yhat + (int64_t)id * p.k * p.ldc;
+                    for (int j = 0; j < kAccCols; ++j)
+                        if (j < np && j < p.k) out[(int64_t)j * p.ldc + i] = sum[j];
+                } else {
+                    // Z in cluster order; the scatter into Y (with α, σX) is a separate
+                    // coalesced pass, so the epilogue only stores
+                    float* z = p.zp + (int64_t)cur_off * p.ldc + i;
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int nu = c0 + j;
-                            if (nu < p.k) out[(int64_t)nu * p.ldc + i] = v[j];
-                        }
-                    } else {
-                        // Z in cluster order; the scatter into Y (with α, σX) is a separate
-                        // coalesced pass, so the epilogue only stores
-                        float* z = p.zp + (int64_t)off * p.ldc + i;
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (c0 + j < nt) z[(int64_t)(c0 + j) * p.ldc] = v[j];
-                    }
+                    for (int j = 0; j < kAccCols; ++j)
+                        if (j < cur_nt) z[(int64_t)j * p.ldc] = sum[j];
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce_bar[acc]);
             cur = nxt;
             cur_off = nxt_off;
             cur_nt = nxt_nt;

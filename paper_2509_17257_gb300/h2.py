@@ -68,7 +68,7 @@ class CGParams(C.Structure):
 
 class GMRESParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("restart", C.c_int32), ("dtype", C.c_int32),
-                ("precond", C.c_int32), ("stream", C.c_void_p)]
+                ("precond", C.c_int32), ("transposed", C.c_int32), ("stream", C.c_void_p)]
 
 
 class CGResult(C.Structure):
@@ -115,6 +115,7 @@ def lib() -> C.CDLL:
     for f in (L.h2_matmul, L.h2_matmul_transposed, L.h2_matmul_noalloc):
         f.argtypes = [vp, dbl, vp, i64, vp, i64, i64, i32, vp]
     L.h2_block_cg.argtypes = [vp, vp, i64, vp, i64, i64, C.POINTER(CGParams), C.POINTER(CGResult)]
+    L.h2_block_gmres.argtypes = [vp, vp, i64, vp, i64, i64, C.POINTER(GMRESParams), C.POINTER(CGResult)]
     L.h2_coupling_get.argtypes = [vp, vp, vp]
     L.h2_coupling_set.argtypes = [vp, vp, vp]
     L.h2_shift_set.argtypes = [vp, dbl]
@@ -349,7 +350,7 @@ def h2_block_cg(handle, B, X, tol=1e-8, max_iter=20000, dtype="f64", refine=True
 
 
 def h2_block_gmres(handle, B, X, tol=1e-8, max_iter=20000, restart=30, dtype="f64", precond=None,
-                   stream=None) -> SolveResult:
+                   transposed=False, stream=None) -> SolveResult:
     """Block GMRES (restarted, per column, left-preconditioned): solve A X = B
     for device B and X (X: initial guess in, solution out).  Non-convergence is
     reported in ``status``, not raised."""
@@ -362,7 +363,7 @@ def h2_block_gmres(handle, B, X, tol=1e-8, max_iter=20000, restart=30, dtype="f6
     rel = np.zeros(max(m, 1), dtype=np.float64)
     dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
     pc = PRECONDS[precond] if precond is None or isinstance(precond, str) else int(precond)
-    prm = GMRESParams(tol, max_iter, restart, dt, pc, _stream_ptr(stream))
+    prm = GMRESParams(tol, max_iter, restart, dt, pc, 1 if transposed else 0, _stream_ptr(stream))
     res = CGResult(0, 0, 0, 0, it.ctypes.data_as(C.POINTER(C.c_int32)), rel.ctypes.data_as(C.POINTER(C.c_double)),
                    0.0)
     rc = lib().h2_block_gmres(handle, bp, ldb, xp, ldx, m, C.byref(prm), C.byref(res))

@@ -125,3 +125,13 @@ def test_tree_argument_errors(h2lib):
     with pytest.raises(h2lib.H2Error) as e:
         h2lib.h2_tree_build(sphere_points(100, 1), eta=0.0)
     assert e.value.code == h2lib.H2_E_BADARG
+
+
+def test_every_export_has_argtypes():
+    """ctypes passes untyped Python ints as 32-bit C ints: every entry point
+    that takes arguments declares them."""
+    import paper_2509_17257_gb300.h2 as H
+    L = H.lib()
+    missing = [name for name in H.EXPORTS
+               if name not in ("h2_last_error_string", "h2_version") and getattr(L, name).argtypes is None]
+    assert not missing, missing
