@@ -200,8 +200,11 @@ typedef struct h2_cg_params {
                             outside, block CG with the dtype product inside, X += D); 2 = one block
                             CG with the dtype product whose recurrence residuals are replaced by the
                             FP64 residual B - A X ("reliable updates") whenever the largest active
-                            one fell by the factor inner_tol (default 0.1); 0 = plain block CG
-                            with the dtype product (converges to the dtype operator's solution)   */
+                            one fell by the factor inner_tol (default 0.1); a step whose low-
+                            precision <p, Ap> is not positive restarts every direction from the
+                            FP64 residual (at most max(10, max_iter/50) times, then
+                            H2_E_BREAKDOWN); 0 = plain block CG with the dtype product (converges
+                            to the dtype operator's solution)                                       */
     double inner_tol;    /* refine 1: relative reduction asked of each inner solve;
                             refine 2: residual reduction between reliable updates                  */
     int32_t max_outer;   /* cap on refinement steps                                                  */

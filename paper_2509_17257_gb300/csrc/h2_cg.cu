@@ -463,7 +463,8 @@ struct Solver {
         H2_CUDA_TRY(cudaStreamSynchronize(st));
         std::vector<double> rn(m), ru(m);
         std::vector<int> act(m);
-        int it = 0, status = 0;
+        int it = 0, status = 0, restarts = 0;
+        const int max_restarts = std::max(10, max_iter / 50);
         *updates = 0;
         if (h_summary[0] > 0) {
             for (it = 1; it <= max_iter; ++it) {
@@ -482,7 +483,15 @@ struct Solver {
                 H2_CUDA_TRY(cudaMemcpyAsync(ru.data(), rupd, m * sizeof(double), cudaMemcpyDeviceToHost, st));
                 H2_CUDA_TRY(cudaMemcpyAsync(act.data(), d.active, m * sizeof(int), cudaMemcpyDeviceToHost, st));
                 H2_CUDA_TRY(cudaStreamSynchronize(st));
-                if (h_summary[1]) { status = H2_E_BREAKDOWN; break; }
+                if (h_summary[1]) {
+                    if (++restarts > max_restarts) { status = H2_E_BREAKDOWN; break; }
+                    ++*updates;
+                    if ((rc = restart_all(B, ldb, X, ldx, tol, Rt, rupd))) return rc;
+                    H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                    H2_CUDA_TRY(cudaStreamSynchronize(st));
+                    if (h_summary[0] == 0) break;
+                    continue;
+                }
                 bool update = h_summary[0] == 0;
                 for (int i = 0; i < m && !update; ++i) update = act[i] && rn[i] < delta * ru[i];
                 if (!update) continue;
@@ -605,6 +614,26 @@ struct Solver {
         return 0;
     }
 
+    // After a low-precision step lost positive curvature (<p, A_dtype p> <= 0:
+    // the product's error exceeds the smallest eigenvalue on p), replace the
+    // residual by the FP64 one and restart every direction from it (M⁻¹r with
+    // a preconditioner).  X is untouched by the failed step (α = 0 there).
+    int restart_all(const double* B, int64_t ldb, const double* X, int64_t ldx, double tol, double* Rt,
+                    double* rupd) {
+        H2_CUDA_TRY(cudaMemsetAsync(d.summary + 1, 0, sizeof(int), st));
+        int rc = reliable_update(B, ldb, X, ldx, tol, Rt, rupd);
+        if (rc) return rc;
+        const double* src = R;
+        if (pcg) {
+            if ((rc = bj_apply(A, R, Z, n, m, nullptr, d, st))) return rc;
+            src = Z;
+        }
+        if (gram) return gram_start(P, src, n, m, g, d, st);
+        k_copy2d<<<copy_grid(), 256, 0, st>>>(src, m, P, m, n, m);
+        H2_LAUNCH_CHECK();
+        return 0;
+    }
+
     // Preconditioned block CG (Alg. "pcg block") with the block-Jacobi M:
     // per iteration a = A p; β = <p, a>, α = <p, r>/β; x += αp, r -= αa;
     // z = M⁻¹ r; γ = <a, z>/β; p = z - γp (the paper's form with q = M⁻¹r).
@@ -625,7 +654,8 @@ struct Solver {
         H2_CUDA_TRY(cudaStreamSynchronize(st));
         std::vector<double> rn(m), ru(m);
         std::vector<int> act(m);
-        int it = 0, status = 0;
+        int it = 0, status = 0, restarts = 0;
+        const int max_restarts = std::max(10, max_iter / 50);
         *updates = 0;
         if (h_summary[0] > 0) {
             for (it = 1; it <= max_iter; ++it) {
@@ -646,7 +676,15 @@ struct Solver {
                     H2_CUDA_TRY(cudaMemcpyAsync(act.data(), d.active, m * sizeof(int), cudaMemcpyDeviceToHost, st));
                 }
                 H2_CUDA_TRY(cudaStreamSynchronize(st));
-                if (h_summary[1]) { status = H2_E_BREAKDOWN; break; }
+                if (h_summary[1]) {
+                    if (!Rt || ++restarts > max_restarts) { status = H2_E_BREAKDOWN; break; }
+                    ++*updates;
+                    if ((rc = restart_all(B, ldb, X, ldx, tol, Rt, rupd))) return rc;
+                    H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                    H2_CUDA_TRY(cudaStreamSynchronize(st));
+                    if (h_summary[0] == 0) break;
+                    continue;
+                }
                 if (!Rt) {
                     if (h_summary[0] == 0) break;
                     continue;
@@ -689,7 +727,8 @@ struct Solver {
         H2_CUDA_TRY(cudaStreamSynchronize(st));
         std::vector<double> rn(m), ru(m);
         std::vector<int> act(m);
-        int it = 0, status = 0;
+        int it = 0, status = 0, restarts = 0;
+        const int max_restarts = std::max(10, max_iter / 50);
         *updates = 0;
         if (h_summary[0] > 0) {
             for (it = 1; it <= max_iter; ++it) {
@@ -711,7 +750,15 @@ struct Solver {
                     H2_CUDA_TRY(cudaMemcpyAsync(act.data(), d.active, m * sizeof(int), cudaMemcpyDeviceToHost, st));
                 }
                 H2_CUDA_TRY(cudaStreamSynchronize(st));
-                if (h_summary[1]) { status = H2_E_BREAKDOWN; break; }
+                if (h_summary[1]) {
+                    if (!Rt || ++restarts > max_restarts) { status = H2_E_BREAKDOWN; break; }
+                    ++*updates;
+                    if ((rc = restart_all(B, ldb, X, ldx, tol, Rt, rupd))) return rc;
+                    H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                    H2_CUDA_TRY(cudaStreamSynchronize(st));
+                    if (h_summary[0] == 0) break;
+                    continue;
+                }
                 if (!Rt) {
                     if (h_summary[0] == 0) break;
                     continue;
