@@ -28,8 +28,8 @@
 //                 FP32 accumulate)
 //   warps 2..5    epilogue (tcgen05.ld, hi+lo combine, stores)
 //   warps 6..7    KIND 1 only: the B_lo splitter
-// Accumulators are double-buffered in TMEM so the epilogue of one output tile
-// overlaps the MMAs of the next.  Every wait is bounded; on a timeout the
+// Every term accumulates in one of kAccBufs TMEM buffers (round robin), so the
+// epilogue's FP32 sum of earlier terms overlaps the MMAs of the next ones.  Every wait is bounded; on a timeout the
 // kernel raises an error flag, drains its own copies and MMAs, frees TMEM and
 // returns.
 #include <cuda_bf16.h>
@@ -49,6 +49,7 @@ constexpr int kMaxStages = 16;
 constexpr int kSmemBudget = 225 * 1024;  // dynamic shared memory per CTA (one CTA per SM)
 constexpr int kTcThreads = 256;
 constexpr int kAccCols = 64;                // TMEM columns per accumulator buffer
+constexpr int kAccBufs = 4;                 // accumulator buffers: MMAs of a term overlap the epilogue of the 3 before
 constexpr uint32_t kSpinLimit = 1u << 25;   // bounded mbarrier waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -118,17 +119,19 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 32 consecutive TMEM columns of this warp's 32 lanes, without waiting: the
+// caller issues several and then one tcgen05.wait::ld.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Byte offset of element (row r, column c) of a core-matrix tile whose rows hold
 // kp values of es bytes (kp·es a multiple of 16): 8-row groups outermost, then
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full_bar[kMaxStages], split_bar[kMaxStages], empty_bar[kMaxStages];
-    __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], drain_bar;
+    __shared__ __align__(8) uint64_t accf_bar[kAccBufs], acce_bar[kAccBufs], drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int stage_kp[kMaxStages], stage_np[kMaxStages], stage_fl[kMaxStages];
     __shared__ int abort_shared;
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             mbar_init(&split_bar[s], 2);
             mbar_init(&empty_bar[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kAccBufs; ++b) {
             mbar_init(&accf_bar[b], 1);
             mbar_init(&acce_bar[b], 4);  // one arrival per epilogue warp
         }
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(2 * kAccCols)
+                     "r"(kAccBufs * kAccCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -369,8 +372,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                 // every term accumulates from zero in its own TMEM buffer; the epilogue
                 // adds the terms of an item in FP32 registers (round to nearest), so
                 // the tensor-core accumulator never sums more than one term's K steps
-                acc = it & 1;
-                if (!mbar_wait(&acce_bar[acc], ((it >> 1) & 1) ^ 1)) {
+                acc = it % kAccBufs;
+                if (!mbar_wait(&acce_bar[acc], ((it / kAccBufs) & 1) ^ 1)) {
                     abort_flag = 1;
                     atomicExch(p.err, 3);
                     break;
@@ -433,22 +436,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             for (int j = 0; j < kAccCols; ++j) sum[j] = 0.f;
             bool failed = false;
             for (int term = 0; term < nterms; ++term, ++it) {
-                const int acc = it & 1;
+                const int acc = it % kAccBufs;
                 // warp-uniform wait: a completed phase stays completed, so any lane's
                 // success is the warp's success
-                const bool ok = __any_sync(0xffffffffu, mbar_wait(&accf_bar[acc], (it >> 1) & 1));
+                const bool ok = __any_sync(0xffffffffu, mbar_wait(&accf_bar[acc], (it / kAccBufs) & 1));
                 if (!ok) {
                     failed = true;
                     break;
                 }
                 tc_fence_after();
+                // both halves of the accumulator in flight, one wait
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kAccCols);
+                uint32_t r0[32], r1[32];
+                tmem_ld32_async(ta, r0);
+                if (np > 32) tmem_ld32_async(ta + 32, r1);
+                tmem_wait_ld();
 #pragma unroll
-                for (int cc = 0; cc < kAccCols / 16; ++cc) {
-                    if (16 * cc >= np) break;
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kAccCols + 16 * cc), v);
+                for (int j = 0; j < 32; ++j) {
+                    const float v = __uint_as_float(r0[j]);
+                    sum[j] += v + __shfl_xor_sync(0xffffffffu, v, 1);
+                }
+                if (np > 32) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) sum[16 * cc + j] += v[j] + __shfl_xor_sync(0xffffffffu, v[j], 1);
+                    for (int j = 0; j < 32; ++j) {
+                        const float v = __uint_as_float(r1[j]);
+                        sum[32 + j] += v + __shfl_xor_sync(0xffffffffu, v, 1);
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -515,7 +528,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
     __syncthreads();
     tc_fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kAccCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAccBufs * kAccCols) : "memory");
 }
 
 // Zero ŷ of clusters whose coupling list is empty.
