@@ -48,7 +48,7 @@ namespace {
 constexpr int kMaxStages = 16;
 constexpr int kSmemBudget = 225 * 1024;  // dynamic shared memory per CTA (one CTA per SM)
 constexpr int kTcThreads = 256;
-constexpr int kAccCols = 64;                // TMEM columns per accumulator buffer
+constexpr int kAccCols = 64;                // output columns of one term (the matrix tile's rows)
 constexpr int kAccBufs = 4;                 // accumulator buffers: MMAs of a term overlap the epilogue of the 3 before
 constexpr uint32_t kSpinLimit = 1u << 25;   // bounded mbarrier waits
 
@@ -118,6 +118,17 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// x - tf32(x) per component: what the TF32 MMA drops from an FP32 operand
+// (it reads the top 19 bits).
+__device__ __forceinline__ float4 tf32_lo(const float4 v) {
+    float4 l;
+    l.x = v.x - __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+    l.y = v.y - __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+    l.z = v.z - __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+    l.w = v.w - __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+    return l;
+}
 
 // 32 consecutive TMEM columns of this warp's 32 lanes, without waiting: the
 // caller issues several and then one tcgen05.wait::ld.
@@ -231,6 +242,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
     constexpr int ES = KIND == 0 ? 2 : 4;
     constexpr int KSTEP = KIND == 0 ? 16 : 8;  // K of one MMA instruction
     constexpr int F_FIRST = 1, F_LAST = 2, F_END = 4;
+    // TMEM columns per accumulator buffer: KIND 1 multiplies by [B; B_lo] in one
+    // N = 128 MMA, so its buffer holds A·Bᵀ in columns 0..63 and A·B_loᵀ in 64..127
+    constexpr int ACC = KIND == 1 ? 2 * kAccCols : kAccCols;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full_bar[kMaxStages], split_bar[kMaxStages], empty_bar[kMaxStages];
@@ -263,7 +277,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(kAccBufs * kAccCols)
+                     "r"(kAccBufs * ACC)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -378,21 +392,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                     atomicExch(p.err, 3);
                     break;
                 }
-                d = tmem + (uint32_t)(acc * kAccCols);
-                idesc = idesc_for<KIND>(M, stage_np[stage]);
+                d = tmem + (uint32_t)(acc * ACC);
+                // KIND 1: N = 128 covers B (rows 0..63) and B_lo (rows 64..127, which
+                // the splitter writes 64·kp elements after B's start); rows np..63 of
+                // either part hold stale data whose output columns the epilogue ignores
+                idesc = idesc_for<KIND>(M, KIND == 1 ? 128 : stage_np[stage]);
                 tc_fence_after();
                 const int kp = stage_kp[stage];
                 const uint32_t sA = smem_u32(smem + stage * stage_bytes);
                 const uint32_t sB = sA + a_bytes;
                 const uint32_t sbo = (uint32_t)(kp * ES / 16) * 128;
-                for (int kk = 0; kk < kp / KSTEP; ++kk) {
-                    const uint64_t ad = smem_desc(sA + kk * 256, 128, sbo);
-                    const uint64_t bd = smem_desc(sB + kk * 256, 128, sbo);
-                    mma_issue<KIND>(d, ad, bd, idesc, kk == 0 ? 0u : 1u);
-                    if (KIND == 1) {
-                        const uint64_t bl = smem_desc(sB + b_bytes + kk * 256, 128, sbo);
-                        mma_issue<KIND>(d, ad, bl, idesc, 1u);
-                    }
+                // descriptors of K step kk: the start address field moves by 256 bytes
+                // (two core matrices along K), i.e. 16 in its 16-byte units
+                const uint64_t ad0 = smem_desc(sA, 128, sbo), bd0 = smem_desc(sB, 128, sbo);
+                const int nk = kp / KSTEP;
+#pragma unroll
+                for (int kk = 0; kk < 64 / KSTEP; ++kk) {
+                    if (kk >= nk) break;
+                    const uint64_t off = (uint64_t)(kk * 16);
+                    mma_issue<KIND>(d, ad0 + off, bd0 + off, idesc, kk == 0 ? 0u : 1u);
                 }
                 issued = true;
                 mma_commit(&empty_bar[stage]);
@@ -445,21 +463,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                     break;
                 }
                 tc_fence_after();
-                // both halves of the accumulator in flight, one wait
-                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kAccCols);
-                uint32_t r0[32], r1[32];
+                // the accumulator in flight (both halves, and for KIND 1 the B_lo
+                // products as well), one wait
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * ACC);
+                uint32_t r0[32], r1[32], l0[32], l1[32];
                 tmem_ld32_async(ta, r0);
                 if (np > 32) tmem_ld32_async(ta + 32, r1);
+                if (KIND == 1) {
+                    tmem_ld32_async(ta + kAccCols, l0);
+                    if (np > 32) tmem_ld32_async(ta + kAccCols + 32, l1);
+                }
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float v = __uint_as_float(r0[j]);
+                    float v = __uint_as_float(r0[j]);
+                    if (KIND == 1) v += __uint_as_float(l0[j]);
                     sum[j] += v + __shfl_xor_sync(0xffffffffu, v, 1);
                 }
                 if (np > 32) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const float v = __uint_as_float(r1[j]);
+                        float v = __uint_as_float(r1[j]);
+                        if (KIND == 1) v += __uint_as_float(l1[j]);
                         sum[32 + j] += v + __shfl_xor_sync(0xffffffffu, v, 1);
                     }
                 }
@@ -506,16 +531,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             const int fl = stage_fl[stage];
             if (!(fl & F_END)) {
                 const int n4 = stage_np[stage] * stage_kp[stage] / 4;  // float4 count of the B tile
-                const float4* src = (const float4*)(smem + stage * stage_bytes + a_bytes);
-                float4* dst = (float4*)(smem + stage * stage_bytes + a_bytes + b_bytes);
-                for (int x = sw * 32 + lane; x < n4; x += 64) {
-                    float4 v = src[x], l;
-                    l.x = v.x - __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-                    l.y = v.y - __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-                    l.z = v.z - __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-                    l.w = v.w - __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
-                    dst[x] = l;
+                const float4* __restrict__ src = (const float4*)(smem + stage * stage_bytes + a_bytes);
+                // B_lo goes where rows 64..127 of the same core-matrix layout start, so
+                // one N = 128 MMA reads [B; B_lo] (8-row groups are kp·4/16 core
+                // matrices apart)
+                float4* __restrict__ dst =
+                    (float4*)(smem + stage * stage_bytes + a_bytes + 64 * stage_kp[stage] * 4);
+                // four loads in flight per thread, then the four stores
+                int x = sw * 32 + lane;
+                for (; x + 3 * 64 < n4; x += 4 * 64) {
+                    float4 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[u] = src[x + 64 * u];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) dst[x + 64 * u] = tf32_lo(v[u]);
                 }
+                for (; x < n4; x += 64) dst[x] = tf32_lo(src[x]);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             }
             __syncwarp();
@@ -528,7 +559,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
     __syncthreads();
     tc_fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAccBufs * kAccCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAccBufs * ACC) : "memory");
 }
 
 // Zero ŷ of clusters whose coupling list is empty.
