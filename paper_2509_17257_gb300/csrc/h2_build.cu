@@ -169,6 +169,83 @@ __global__ void k_transpose_f32(const double* __restrict__ E, float* __restrict_
     }
 }
 
+// Schedule of the subtree-owning downward pass.  The tree is cut at level Ls:
+// the cut clusters (level Ls, and leaves above it) are the tasks.  A task
+// recomputes ŷ of the clusters on the path from the root to its cut cluster
+// t (ŷ_a += E_a ŷ_parent(a) in path order; the sum is the same for every
+// task that shares the path), then walks the subtree of t in pre-order (the
+// contiguous cluster range t .. t + |subtree| - 1).  No task reads what
+// another task writes, so the pass needs no synchronisation between CTAs.
+// Stack entries 0 and 1 alternate along the path; a node of relative depth
+// d >= 1 below t keeps its ŷ in entry d + 1 (its father's is in entry d, or
+// in the entry holding t's for d = 1).  Ls is the shallowest level with at
+// least `target` tasks whose subtrees are at most kMaxSubDepth deep and whose
+// step lists fit kDownMaxSteps (at the deepest level every task is a leaf's
+// path, at most depth + 1 steps).
+void down_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std::vector<DownStep>& steps,
+                   int32_t& ntasks, int32_t& entries) {
+    constexpr int kMaxSubDepth = 6;
+    const int64_t nc = T.n_clusters();
+    task_ptr.assign(1, 0);
+    steps.clear();
+    ntasks = 0;
+    entries = 2;
+    if (nc <= 1) return;
+    std::vector<int64_t> nsub(nc, 1);  // subtree sizes (pre-order: sons follow their father)
+    std::vector<int32_t> hsub(nc, 0);  // subtree heights
+    for (int64_t c = nc - 1; c >= 1; --c) {
+        nsub[T.parent[c]] += nsub[c];
+        hsub[T.parent[c]] = std::max(hsub[T.parent[c]], hsub[c] + 1);
+    }
+    int Ls = T.depth;
+    for (int l = 1; l <= T.depth; ++l) {
+        int64_t count = 0, size = 0;
+        int32_t h = 0;
+        for (int64_t c = 0; c < nc; ++c)
+            if (T.level[c] == l || (T.level[c] < l && T.is_leaf((int32_t)c))) {
+                ++count;
+                h = std::max(h, hsub[c]);
+                size = std::max(size, nsub[c]);
+            }
+        // a task has 1 + l + (subtree size - 1) steps
+        if (count >= target && h <= kMaxSubDepth && l + size <= kDownMaxSteps) { Ls = l; break; }
+    }
+    std::vector<int32_t> cut;
+    for (int64_t c = 0; c < nc; ++c)
+        if (T.level[c] == Ls || (T.level[c] < Ls && T.level[c] > 0 && T.is_leaf((int32_t)c))) cut.push_back((int32_t)c);
+    std::vector<std::vector<DownStep>> task_steps(cut.size());
+    int32_t dmax = 0;
+    for (size_t i = 0; i < cut.size(); ++i) {
+        const int32_t t = cut[i];
+        std::vector<DownStep>& v = task_steps[i];
+        std::vector<int32_t> path;
+        for (int32_t a = t; T.parent[a] >= 0; a = T.parent[a]) path.push_back(a);
+        std::reverse(path.begin(), path.end());
+        v.push_back(DownStep{0, -1, 0, kDownLoad});  // the root's ŷ is final after the coupling phase
+        int cur = 0;
+        for (int32_t a : path) {
+            v.push_back(DownStep{a, cur, cur ^ 1, (a == t && T.is_leaf(a)) ? kDownStore : 0});
+            cur ^= 1;
+        }
+        for (int64_t c = t + 1; c < t + nsub[t]; ++c) {
+            const int32_t d = T.level[c] - T.level[t];
+            dmax = std::max(dmax, d);
+            v.push_back(DownStep{(int32_t)c, d == 1 ? cur : d, d + 1, T.is_leaf((int32_t)c) ? kDownStore : 0});
+        }
+    }
+    // longest tasks first: CTAs claim them in this order
+    std::vector<size_t> order(cut.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return task_steps[a].size() > task_steps[b].size(); });
+    for (size_t i : order) {
+        steps.insert(steps.end(), task_steps[i].begin(), task_steps[i].end());
+        task_ptr.push_back((int32_t)steps.size());
+    }
+    ntasks = (int32_t)cut.size();
+    entries = 2 + dmax;
+}
+
 int cast_copy(h2_matrix* A, const double* src, void** dst, int64_t count, cudaStream_t st) {
     int rc = device_alloc(A, dst, (size_t)(count > 0 ? count : 1) * sizeof(float));
     if (rc) return rc;
@@ -301,6 +378,13 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
     UP(A->d_leaves, A->leaves);
     UP(A->d_up_list, up_list);
     UP(A->d_down_list, down_list);
+    {
+        std::vector<int32_t> task_ptr;
+        std::vector<DownStep> dsteps;
+        down_schedule(T, 256, task_ptr, dsteps, A->dn_ntasks, A->dn_entries);
+        UP(A->d_dn_task_ptr, task_ptr);
+        UP(A->d_dn_steps, dsteps);
+    }
     UP(A->d_adm_rowptr, adm_rowptr);
     UP(A->d_adm_col, adm_col);
     UP(A->d_adm_row, adm_row);

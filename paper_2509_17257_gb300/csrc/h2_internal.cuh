@@ -133,6 +133,17 @@ struct TcData {
 // the upward pass (self-resetting), ready flags of the downward pass and its
 // claim tickets (both cleared before every downward pass, so a captured CUDA
 // graph can replay the product).
+// One step of the subtree-owning downward pass (k_down_own, h2_mm.cu): cluster c
+// gets ŷ_c = ŷ_c + E_c ŷ_parent with ŷ_parent read from shared-memory stack
+// entry rd and the result kept in entry wr; kDownLoad marks the first step of a
+// task (entry wr ← the root's ŷ, no product), kDownStore a leaf whose ŷ goes
+// back to global memory.
+struct DownStep {
+    int32_t c, rd, wr, flags;
+};
+constexpr int kDownLoad = 1, kDownStore = 2;
+constexpr int kDownMaxSteps = 192;  // steps of one task at most (the schedule keeps to it)
+
 struct SyncBufs {
     unsigned* cnt = nullptr;
     int* flag = nullptr;
@@ -173,6 +184,10 @@ struct h2_matrix {
     int32_t* d_son0 = nullptr;       // [nc]
     int32_t* d_son1 = nullptr;       // [nc]
     int32_t* d_down_list = nullptr;  // non-root clusters by level
+    // subtree-owning downward pass: task t runs steps dn_steps[dn_task_ptr[t]..dn_task_ptr[t+1])
+    int32_t* d_dn_task_ptr = nullptr;
+    h2::DownStep* d_dn_steps = nullptr;
+    int32_t dn_ntasks = 0, dn_entries = 0;
     int32_t* d_adm_rowptr = nullptr; // [nc+1] by row cluster
     int32_t* d_adm_col = nullptr;    // [n_adm]
     int32_t* d_adm_row = nullptr;    // [n_adm]

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "h2_async.cuh"
 #include "h2_internal.cuh"
 
 namespace h2 {
@@ -394,9 +395,8 @@ __global__ void __launch_bounds__(kThreads) k_leaf_bwd_near(
 // X|_t̂ at a leaf; E_{s0}, E_{s1}, x̂_{s0}, x̂_{s1} at a father; Eᵀ_c and ŷ_father
 // downwards) into shared memory in 16-byte pieces, then one barrier, then the
 // register-tiled contraction.  The data another CTA of the same launch wrote
-// (x̂ of the sons, ŷ of the father) is copied with .cg (L2, not L1).  The
-// downward pass issues the copy of its (static) transfer matrix before it
-// waits for the father's ready flag.
+// (x̂ of the sons) is copied with .cg (L2, not L1).  The downward pass
+// (k_down_own) gives each CTA whole subtrees and needs no flags.
 // ---------------------------------------------------------------------------
 constexpr int kFastK = 128;  // contraction rows staged at most (two sons of k = 64)
 constexpr int kFastLdA = 68;  // 64 output rows + 4: rows stay 16-byte aligned
@@ -519,66 +519,124 @@ __global__ void __launch_bounds__(kThreads) k_up_fast(const int32_t* __restrict_
     }
 }
 
+// acc[4×CN] += a[0:K][rows 4ty..]  contracted with b[0:K][cols CN·tx..], row
+// strides lda and ldb (multiples of 4 floats; rows and columns past the valid
+// ones read neighbouring data and give outputs nobody stores).
 template <int CN>
-__global__ void __launch_bounds__(kThreads) k_down_fast(const int32_t* __restrict__ order, int n_items,
-                                                        const int32_t* __restrict__ parent,
-                                                        const float* __restrict__ Et, float* yhat,
-                                                        unsigned* __restrict__ claim, int* flag, int epoch,
-                                                        int* __restrict__ err, int k, int m) {
+__device__ __forceinline__ void own_contract(float (&acc)[4][CN], const float* a, int lda, const float* b, int ldb,
+                                             int K) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll 8
+    for (int kk = 0; kk < K; ++kk) {
+        const float4 av = *(const float4*)(a + kk * lda + 4 * ty);
+        float bv[CN];
+        lds_vec<CN>(b + kk * ldb + CN * tx, bv);
+#pragma unroll
+        for (int c = 0; c < CN; ++c) {
+            acc[0][c] = fmaf(av.x, bv[c], acc[0][c]);
+            acc[1][c] = fmaf(av.y, bv[c], acc[1][c]);
+            acc[2][c] = fmaf(av.z, bv[c], acc[2][c]);
+            acc[3][c] = fmaf(av.w, bv[c], acc[3][c]);
+        }
+    }
+}
+
+// Downward pass with subtree ownership (schedule: down_schedule, h2_build.cu).
+// A CTA claims tasks in the stored order; a task is a list of steps, each
+// ŷ_c += E_c ŷ_father (Sec. 3, the downward transformation of
+// Alg. "fast_addeval"), with ŷ_father in a shared-memory stack entry written by
+// an earlier step of the same task, so no step waits for another CTA.  The
+// static operands of step s + 1 (Eᵀ_c, k×k, and the coupling result ŷ_c, k×m,
+// both contiguous) arrive by two bulk copies, issued by one thread while step
+// s computes.  All ŷ buffers keep rows of m floats.
+template <int CN>
+__global__ void __launch_bounds__(kThreads) k_down_own(const int32_t* __restrict__ task_ptr, int ntasks,
+                                                       const DownStep* __restrict__ steps,
+                                                       const float* __restrict__ Et, float* yhat,
+                                                       unsigned* __restrict__ claim, int* __restrict__ err, int k,
+                                                       int m) {
     constexpr int NT = 16 * CN;
     extern __shared__ __align__(16) float fsm[];
-    float* a = fsm;
-    float* b = fsm + kFastK * kFastLdA;
-    __shared__ int s_item, s_ok;
-    const int tile = blockIdx.y, gy = gridDim.y;
-    const int col0 = tile * NT, w = min(NT, m - col0);
+    float* ebuf = fsm;                  // [2][64·64]       Eᵀ_c
+    float* cbuf = ebuf + 2 * 64 * 64;   // [2][64·NT]       ŷ_c from the coupling phase
+    float* stk = cbuf + 2 * 64 * NT;    // [entries][64·NT] final ŷ along the current path
+    __shared__ int s_task;
+    __shared__ DownStep s_steps[kDownMaxSteps];  // the task's steps: no global load between two steps
+    __shared__ __align__(8) uint64_t bar[2];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
-    while (true) {
+    const uint32_t ebytes = (uint32_t)(kk * 4), ybytes = (uint32_t)(km * 4);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    uint32_t phase = 0;  // bit b: parity of the next completion of bar[b]
+    bool failed = false;
+    while (!failed) {
         __syncthreads();
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(&claim[tile], 1u);
+        if (threadIdx.x == 0) s_task = (int)atomicAdd(claim, 1u);
         __syncthreads();
-        const int item = s_item;
-        if (item >= n_items) break;
-        const int c = order[item];
-        const int par = parent[c];
-        // the transfer matrix does not depend on the father: start its copy first
-        stage_rows(a, kFastLdA, 0, Et + (int64_t)c * kk, k, k, k);
-        cp_commit();
-        if (threadIdx.x == 0) {
-            int ok = 1;
-            if (parent[par] >= 0) {  // the root's ŷ is final after the coupling phase
-                const int* f = flag + (int64_t)par * gy + tile;
-                uint32_t spins = 0;
-                while (ld_acquire(f) != epoch) {
-                    if (++spins > (1u << 24)) { ok = 0; break; }
-                    __nanosleep(32);
-                }
+        const int task = s_task;
+        if (task >= ntasks) break;
+        const int s0 = task_ptr[task], s1 = min(task_ptr[task + 1], s0 + kDownMaxSteps);
+        for (int i = threadIdx.x; i < s1 - s0; i += blockDim.x) s_steps[i] = steps[s0 + i];
+        __syncthreads();
+        // one thread arms the buffer's barrier and starts the step's copies
+        auto issue = [&](int s, int b) {
+            if (threadIdx.x != 0) return;
+            const DownStep d = s_steps[s - s0];
+            if (d.flags & kDownLoad) {
+                mbar_expect_tx(&bar[b], ybytes);
+                bulk_g2s(stk + d.wr * 64 * NT, yhat + (int64_t)d.c * km, ybytes, &bar[b]);
+            } else {
+                mbar_expect_tx(&bar[b], ebytes + ybytes);
+                bulk_g2s(ebuf + b * 64 * 64, Et + (int64_t)d.c * kk, ebytes, &bar[b]);
+                bulk_g2s(cbuf + b * 64 * NT, yhat + (int64_t)d.c * km, ybytes, &bar[b]);
             }
-            s_ok = ok;
-            if (!ok) atomicExch(err, 8);
-        }
-        __syncthreads();
-        if (!s_ok) {
-            cp_commit_wait();  // no copy of this CTA is left in flight
-            break;
-        }
-        stage_rows(b, NT, 0, yhat + (int64_t)par * km + col0, m, k, w);
-        cp_commit_wait();
-        __syncthreads();
-        float acc[4][CN];
+        };
+        issue(s0, 0);
+        for (int s = s0; s < s1; ++s) {
+            const int b = (s - s0) & 1;
+            if (s + 1 < s1) issue(s + 1, b ^ 1);
+            const bool ok = mbar_wait(&bar[b], (phase >> b) & 1u);
+            phase ^= 1u << b;
+            if (__syncthreads_or(!ok)) {
+                // a copy did not land in time: report, let the copies in flight
+                // finish (bounded), stop
+                if (threadIdx.x == 0) {
+                    atomicExch(err, 9);
+                    mbar_wait(&bar[b], ((phase >> b) & 1u) ^ 1u);
+                    if (s + 1 < s1) mbar_wait(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
+                }
+                failed = true;
+                break;
+            }
+            const DownStep d = s_steps[s - s0];
+            if (!(d.flags & kDownLoad)) {
+                const float* cb = cbuf + b * 64 * NT;
+                float acc[4][CN];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int q = 0; q < CN; ++q) acc[r][q] = 0.f;
-        fast_contract<CN>(acc, a, b, k);
-        fast_store<CN, true>(acc, yhat + (int64_t)c * km, m, k, col0);
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) st_release(flag + (int64_t)c * gy + tile, epoch);
+                    for (int q = 0; q < CN; ++q) acc[r][q] = cb[(4 * ty + r) * m + CN * tx + q];
+                own_contract<CN>(acc, ebuf + b * 64 * 64, k, stk + d.rd * 64 * NT, m, k);
+                float* out = stk + d.wr * 64 * NT;
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < CN; ++q)
+                        if (CN * tx + q < m) out[(4 * ty + r) * m + CN * tx + q] = acc[r][q];
+                if (d.flags & kDownStore) fast_store<CN, false>(acc, yhat + (int64_t)d.c * km, m, k, 0);
+            }
+            __syncthreads();
+        }
     }
 }
 
 int fast_smem_bytes(int cn) { return (kFastK * kFastLdA + kFastK * 16 * cn) * (int)sizeof(float); }
+// k_down_own: two Eᵀ and two ŷ buffers plus the stack (at most 8 entries)
+int down_own_smem_bytes(int cn, int entries) { return (2 * 64 * 64 + (2 + entries) * 64 * 16 * cn) * (int)sizeof(float); }
 
 int g_fast_attr_device = -1;
 
@@ -589,9 +647,9 @@ int fast_prepare() {
     H2_CUDA_TRY(cudaFuncSetAttribute(k_up_fast<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(1)));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_up_fast<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(2)));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_up_fast<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(4)));
-    H2_CUDA_TRY(cudaFuncSetAttribute(k_down_fast<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(1)));
-    H2_CUDA_TRY(cudaFuncSetAttribute(k_down_fast<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(2)));
-    H2_CUDA_TRY(cudaFuncSetAttribute(k_down_fast<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(4)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_down_own<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_own_smem_bytes(1, 8)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_down_own<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_own_smem_bytes(2, 8)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_down_own<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_own_smem_bytes(4, 8)));
     g_fast_attr_device = dev;
     return 0;
 }
@@ -842,13 +900,13 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         if (fast) {
             const int n_items = (int)A->down_ptr[A->depth + 1];
             if (n_items > 0) {
-                H2_CUDA_TRY(cudaMemsetAsync(sbc.flag, 0, (size_t)A->nc * sizeof(int), st));
                 H2_CUDA_TRY(cudaMemsetAsync(sbc.claim, 0, sizeof(unsigned), st));
-                const unsigned g = (unsigned)std::min(n_items, 152 * 4);
                 const float* Et = (const float*)A->f32.Et;
-                if (fcn == 1) k_down_fast<1><<<dim3(g, 1), kThreads, fast_smem_bytes(1), st>>>(A->d_down_list, n_items, A->d_parent, Et, yhat, sbc.claim, sbc.flag, sbc.epoch, sbc.err, k, mc);
-                else if (fcn == 2) k_down_fast<2><<<dim3(g, 1), kThreads, fast_smem_bytes(2), st>>>(A->d_down_list, n_items, A->d_parent, Et, yhat, sbc.claim, sbc.flag, sbc.epoch, sbc.err, k, mc);
-                else k_down_fast<4><<<dim3(g, 1), kThreads, fast_smem_bytes(4), st>>>(A->d_down_list, n_items, A->d_parent, Et, yhat, sbc.claim, sbc.flag, sbc.epoch, sbc.err, k, mc);
+                const int smem = down_own_smem_bytes(fcn, A->dn_entries);
+                const unsigned g = (unsigned)std::min(A->dn_ntasks, 152 * std::max(1, (227 * 1024) / (smem + 4096)));
+                if (fcn == 1) k_down_own<1><<<g, kThreads, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc);
+                else if (fcn == 2) k_down_own<2><<<g, kThreads, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc);
+                else k_down_own<4><<<g, kThreads, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc);
                 H2_LAUNCH_CHECK();
             }
         } else if ((rc = backward_pass<float, RM, CN>(A, E, yhat, mc, gy, gzk, st, sbc))) {

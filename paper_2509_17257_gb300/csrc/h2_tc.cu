@@ -19,19 +19,23 @@
 // The FP32 product (KIND 1) runs the same schedule on the TF32 units with
 // split operands: the activation rows carry tf32 high and low parts, and the
 // matrix tile B is complemented in shared memory by B_lo = B - tf32(B), so
-// D = A_hi·B + A_hi·B_lo + A_lo·B + A_lo·B_lo keeps FP32 accuracy ("3xTF32",
-// the A_lo·B_lo term comes free with the row split).
+// A_hi·B + A_hi·B_lo + A_lo·B + A_lo·B_lo keeps FP32 accuracy ("3xTF32", the
+// A_lo·B_lo term comes free with the row split).  Its MMA runs the other way
+// round, D[n, r] = Σ_k [B; B_lo][n, k] · act[r, k] with M = 128 ([B; B_lo]) and
+// N = R: a tcgen05 MMA takes time in proportion to N and the same time for
+// M = 64 as for M = 128, so B_lo rides along in M at no cost.
 //
 // Kernel roles (one persistent CTA per SM, 256 threads):
 //   warp 0        bulk-copy producer (cp.async.bulk + mbarrier complete_tx)
 //   warp 1        TMEM owner and MMA issuer (tcgen05.mma kind::f16 or kind::tf32,
-//                 FP32 accumulate)
+//                 FP32 accumulate); the converged warp runs the loop and
+//                 elect.sync issues, which keeps its operands warp-uniform
 //   warps 2..5    epilogue (tcgen05.ld, hi+lo combine, stores)
 //   warps 6..7    KIND 1 only: the B_lo splitter
 // Every term accumulates in one of kAccBufs TMEM buffers (round robin), so the
-// epilogue's FP32 sum of earlier terms overlaps the MMAs of the next ones.  Every wait is bounded; on a timeout the
-// kernel raises an error flag, drains its own copies and MMAs, frees TMEM and
-// returns.
+// epilogue's FP32 sum of earlier terms overlaps the MMAs of the next ones.
+// Every wait is bounded; on a timeout the kernel raises an error flag, drains
+// its own copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -39,6 +43,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "h2_async.cuh"
 #include "h2_internal.cuh"
 
 namespace h2 {
@@ -50,40 +55,8 @@ constexpr int kSmemBudget = 225 * 1024;  // dynamic shared memory per CTA (one C
 constexpr int kTcThreads = 256;
 constexpr int kAccCols = 64;                // output columns of one term (the matrix tile's rows)
 constexpr int kAccBufs = 4;                 // accumulator buffers: MMAs of a term overlap the epilogue of the 3 before
-constexpr uint32_t kSpinLimit = 1u << 25;   // bounded mbarrier waits
+constexpr int kXchBytes = 2 * 64 * 64 * 4;  // TF32 epilogue: remainder sums handed over, two items deep
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
-        if (mbar_try(b, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
 // Shared-memory matrix descriptor, no swizzle, K-major: LBO = byte distance of
 // core matrices adjacent along K, SBO = byte distance of adjacent 8-row groups.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -97,24 +70,39 @@ __device__ __forceinline__ uint32_t idesc_for(int M, int N) {
     const uint32_t fmt = KIND == 0 ? 1u : 2u;
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// One tcgen05.mma (D = A·Bᵀ, or D += A·Bᵀ when acc != 0) from a converged warp:
+// elect.sync hands it to the lowest active lane, so every MMA and commit of the
+// warp comes from one thread, as tcgen05.commit requires.
 template <int KIND>
-__device__ __forceinline__ void mma_issue(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_issue_elect(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     if (KIND == 0)
         asm volatile(
-            "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
-                d),
+            "{ .reg .pred p, e; setp.ne.b32 p, %4, 0; elect.sync _|e, 0xffffffff;\n"
+            "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
             "l"(a), "l"(b), "r"(idesc), "r"(acc)
             : "memory");
     else
         asm volatile(
-            "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(
-                d),
+            "{ .reg .pred p, e; setp.ne.b32 p, %4, 0; elect.sync _|e, 0xffffffff;\n"
+            "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(d),
             "l"(a), "l"(b), "r"(idesc), "r"(acc)
             : "memory");
 }
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+__device__ __forceinline__ void mma_commit_elect(uint64_t* bar) {
+    asm volatile(
+        "{ .reg .pred e; elect.sync _|e, 0xffffffff;\n"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0]; }" ::"r"(smem_u32(bar))
+        : "memory");
+}
+// Named barrier over `count` threads that also ORs a predicate across them.
+__device__ __forceinline__ bool bar_red_or(int id, int count, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{ .reg .pred pi, po; setp.ne.u32 pi, %1, 0; bar.red.or.pred po, %2, %3, pi; selp.u32 %0, 1, 0, po; }"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
 }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -368,63 +356,178 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                     if (!mbar_wait(&full_bar[s2], (pend_par >> s2) & 1u)) atomicExch(p.err, 2);
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            // ---------------- MMA issuer: driven by the stage metadata ----------------
-            int stage = 0;
-            uint32_t phase = 0;
-            int it = 0, acc = 0;
-            bool issued = false;
-            uint32_t d = tmem, idesc = 0;
-            while (true) {
-                if (!mbar_wait(KIND == 1 ? &split_bar[stage] : &full_bar[stage], phase)) {
-                    abort_flag = 1;
-                    atomicExch(p.err, 4);
-                    break;
-                }
-                const int fl = stage_fl[stage];
-                if (fl & F_END) break;
-                // every term accumulates from zero in its own TMEM buffer; the epilogue
-                // adds the terms of an item in FP32 registers (round to nearest), so
-                // the tensor-core accumulator never sums more than one term's K steps
-                acc = it % kAccBufs;
-                if (!mbar_wait(&acce_bar[acc], ((it / kAccBufs) & 1) ^ 1)) {
-                    abort_flag = 1;
-                    atomicExch(p.err, 3);
-                    break;
-                }
-                d = tmem + (uint32_t)(acc * ACC);
-                // KIND 1: N = 128 covers B (rows 0..63) and B_lo (rows 64..127, which
-                // the splitter writes 64·kp elements after B's start); rows np..63 of
-                // either part hold stale data whose output columns the epilogue ignores
-                idesc = idesc_for<KIND>(M, KIND == 1 ? 128 : stage_np[stage]);
-                tc_fence_after();
-                const int kp = stage_kp[stage];
-                const uint32_t sA = smem_u32(smem + stage * stage_bytes);
-                const uint32_t sB = sA + a_bytes;
-                const uint32_t sbo = (uint32_t)(kp * ES / 16) * 128;
-                // descriptors of K step kk: the start address field moves by 256 bytes
-                // (two core matrices along K), i.e. 16 in its 16-byte units
-                const uint64_t ad0 = smem_desc(sA, 128, sbo), bd0 = smem_desc(sB, 128, sbo);
-                const int nk = kp / KSTEP;
+        // ---------------- MMA issuer: driven by the stage metadata ----------------
+        // The whole warp runs the loop (its waits and descriptors are warp-uniform);
+        // elect.sync hands each MMA and commit to one lane.
+        int stage = 0;
+        uint32_t phase = 0;
+        int it = 0;
+        bool issued = false;
+        while (true) {
+            if (!__any_sync(0xffffffffu, mbar_wait(KIND == 1 ? &split_bar[stage] : &full_bar[stage], phase))) {
+                abort_flag = 1;
+                if (lane == 0) atomicExch(p.err, 4);
+                break;
+            }
+            const int fl = stage_fl[stage];
+            if (fl & F_END) break;
+            // every term accumulates from zero in its own TMEM buffer; the epilogue
+            // adds the terms of an item in FP32 registers (round to nearest), so
+            // the tensor-core accumulator never sums more than one term's K steps
+            const int acc = it % kAccBufs;
+            if (!__any_sync(0xffffffffu, mbar_wait(&acce_bar[acc], ((it / kAccBufs) & 1) ^ 1))) {
+                abort_flag = 1;
+                if (lane == 0) atomicExch(p.err, 3);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(acc * ACC);
+            const int kp = stage_kp[stage];
+            const uint32_t sA = smem_u32(smem + stage * stage_bytes);
+            const uint32_t sB = sA + a_bytes;
+            const uint32_t sbo = (uint32_t)(kp * ES / 16) * 128;
+            // KIND 0: D[r, n] = act · matᵀ (M = activation rows, N = the tile's rows).
+            // KIND 1: D[n, r] = [mat; mat_lo] · actᵀ: M = 128 rows, the tile (rows
+            // 0..63) and its TF32 remainder (rows 64..127, which the splitter writes
+            // 64·kp elements after the tile's start), N = R activation rows.  The
+            // MMA time grows with N, not with M up to 128, so the split costs no
+            // extra instructions.  Rows np..63 of either part hold stale data whose
+            // TMEM lanes the epilogue ignores.
+            const uint32_t idesc = KIND == 1 ? idesc_for<KIND>(128, R) : idesc_for<KIND>(M, stage_np[stage]);
+            // descriptors of K step kk: the start address field moves by 256 bytes
+            // (two core matrices along K), i.e. 16 in its 16-byte units
+            const uint64_t ad0 = smem_desc(KIND == 1 ? sB : sA, 128, sbo);
+            const uint64_t bd0 = smem_desc(KIND == 1 ? sA : sB, 128, sbo);
+            const int nk = kp / KSTEP;
 #pragma unroll
-                for (int kk = 0; kk < 64 / KSTEP; ++kk) {
-                    if (kk >= nk) break;
-                    const uint64_t off = (uint64_t)(kk * 16);
-                    mma_issue<KIND>(d, ad0 + off, bd0 + off, idesc, kk == 0 ? 0u : 1u);
+            for (int kk = 0; kk < 64 / KSTEP; ++kk) {
+                if (kk >= nk) break;
+                const uint64_t off = (uint64_t)(kk * 16);
+                mma_issue_elect<KIND>(d, ad0 + off, bd0 + off, idesc, kk == 0 ? 0u : 1u);
+            }
+            issued = true;
+            mma_commit_elect(&empty_bar[stage]);
+            mma_commit_elect(&accf_bar[acc]);
+            ++it;
+            if (++stage == nst) { stage = 0; phase ^= 1; }
+        }
+        if (issued) {
+            mma_commit_elect(&drain_bar);
+            if (!__any_sync(0xffffffffu, mbar_wait(&drain_bar, 0)) && lane == 0) atomicExch(p.err, 5);
+        }
+    } else if (warp < 6 && KIND == 1) {
+        // ---------------- epilogue, KIND 1 (warps 2..5, TMEM lane quadrant warp % 4) ----------------
+        // TMEM lane 32q + lane holds row n = 32(q & 1) + lane of the tile (q = 0, 1)
+        // or of its remainder (q = 2, 3); column r = 2i + h of that lane is the
+        // product with the high (h = 0) or low (h = 1) part of right-hand-side
+        // column i.  Each thread adds its two columns per i over the item's terms;
+        // at the item's end the remainder warps hand their sums to the tile warps
+        // through shared memory (double buffered by item parity, one barrier per
+        // item), which add them and store row n.
+        const int q = warp & 3;
+        const int n = 32 * (q & 1) + lane;
+        const bool lo_part = q >= 2;
+        float* xch = reinterpret_cast<float*>(smem + nst * stage_bytes);  // [2][64 i][64 n]
+        const bool wide = R > 64;
+        const bool vec4 = (p.mc & 3) == 0 && (p.ldc & 3) == 0;
+        int it = 0, par = 0;
+        TcItem cur = blockIdx.x < p.n_items ? p.items[blockIdx.x] : TcItem{-1, 0, 0, 0};
+        int cur_off = 0, cur_nt = 0;
+        if (MODE == 1 && cur.id >= 0) {
+            const int t = p.leaves[cur.id];
+            cur_off = p.cl_off[t];
+            cur_nt = p.cl_size[t];
+        }
+        for (int w = blockIdx.x; w < p.n_items; w += G) {
+            const TcItem nxt = w + G < p.n_items ? p.items[w + G] : TcItem{-1, 0, 0, 0};
+            int nxt_off = 0, nxt_nt = 0;
+            if (MODE == 1 && nxt.id >= 0) {
+                const int t = p.leaves[nxt.id];
+                nxt_off = p.cl_off[t];
+                nxt_nt = p.cl_size[t];
+            }
+            const int id = cur.id, np = cur.np, nterms = cur.e1 - cur.e0;
+            float sum[kAccCols];
+#pragma unroll
+            for (int j = 0; j < kAccCols; ++j) sum[j] = 0.f;
+            bool failed = false;
+            for (int term = 0; term < nterms; ++term, ++it) {
+                const int acc = it % kAccBufs;
+                if (!__any_sync(0xffffffffu, mbar_wait(&accf_bar[acc], (it / kAccBufs) & 1))) {
+                    failed = true;
+                    break;
                 }
-                issued = true;
-                mma_commit(&empty_bar[stage]);
-                mma_commit(&accf_bar[acc]);
-                ++it;
-                if (++stage == nst) { stage = 0; phase ^= 1; }
+                tc_fence_after();
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * ACC);
+                uint32_t r0[32], r1[32], r2[32], r3[32];
+                tmem_ld32_async(ta, r0);
+                tmem_ld32_async(ta + 32, r1);
+                if (wide) {
+                    tmem_ld32_async(ta + 64, r2);
+                    tmem_ld32_async(ta + 96, r3);
+                }
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    sum[j] += __uint_as_float(r0[2 * j]) + __uint_as_float(r0[2 * j + 1]);
+                    sum[16 + j] += __uint_as_float(r1[2 * j]) + __uint_as_float(r1[2 * j + 1]);
+                }
+                if (wide) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        sum[32 + j] += __uint_as_float(r2[2 * j]) + __uint_as_float(r2[2 * j + 1]);
+                        sum[48 + j] += __uint_as_float(r3[2 * j]) + __uint_as_float(r3[2 * j + 1]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce_bar[acc]);
             }
-            if (issued) {
-                mma_commit(&drain_bar);
-                if (!mbar_wait(&drain_bar, 0)) atomicExch(p.err, 5);
+            float* xb = xch + par * (64 * 64);
+            if (lo_part && !failed) {
+#pragma unroll
+                for (int i = 0; i < kAccCols; ++i)
+                    if (i < p.mc) xb[i * 64 + n] = sum[i];
             }
+            // every epilogue warp reaches this barrier once per item, failed or not,
+            // and all of them learn whether any failed
+            if (bar_red_or(1, 128, failed)) {
+                if (lane == 0) atomicExch(p.err, 6);
+                abort_flag = 1;
+                break;
+            }
+            if (!lo_part) {
+#pragma unroll
+                for (int i = 0; i < kAccCols; ++i)
+                    if (i < p.mc) sum[i] += xb[i * 64 + n];
+                float* out = nullptr;
+                if (MODE == 0) {
+                    if (n < np && n < p.k) out = p.yhat + ((int64_t)id * p.k + n) * p.ldc;
+                } else {
+                    // Z in cluster order; the scatter into Y (with α, σX) is a separate
+                    // coalesced pass, so the epilogue only stores
+                    if (n < cur_nt) out = p.zp + ((int64_t)cur_off + n) * p.ldc;
+                }
+                if (out) {
+                    if (vec4) {
+#pragma unroll
+                        for (int i = 0; i < kAccCols; i += 4)
+                            if (i < p.mc)
+                                *reinterpret_cast<float4*>(out + i) = make_float4(sum[i], sum[i + 1], sum[i + 2], sum[i + 3]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < kAccCols; ++i)
+                            if (i < p.mc) out[i] = sum[i];
+                    }
+                }
+            }
+            par ^= 1;
+            cur = nxt;
+            cur_off = nxt_off;
+            cur_nt = nxt_nt;
         }
     } else if (warp < 6) {
-        // ---------------- epilogue (warps 2..5, TMEM lane quadrant warp % 4) ----------------
+        // ---------------- epilogue, KIND 0 (warps 2..5, TMEM lane quadrant warp % 4) ----------------
         const int q = warp & 3;
         int row;
         if (M == 128) row = 32 * q + lane;
@@ -463,28 +566,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                     break;
                 }
                 tc_fence_after();
-                // the accumulator in flight (both halves, and for KIND 1 the B_lo
-                // products as well), one wait
+                // both halves of the accumulator in flight, one wait; the row pair
+                // (2i, 2i + 1) is adjacent lanes, added by one shuffle
                 const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * ACC);
-                uint32_t r0[32], r1[32], l0[32], l1[32];
+                uint32_t r0[32], r1[32];
                 tmem_ld32_async(ta, r0);
                 if (np > 32) tmem_ld32_async(ta + 32, r1);
-                if (KIND == 1) {
-                    tmem_ld32_async(ta + kAccCols, l0);
-                    if (np > 32) tmem_ld32_async(ta + kAccCols + 32, l1);
-                }
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    float v = __uint_as_float(r0[j]);
-                    if (KIND == 1) v += __uint_as_float(l0[j]);
+                    const float v = __uint_as_float(r0[j]);
                     sum[j] += v + __shfl_xor_sync(0xffffffffu, v, 1);
                 }
                 if (np > 32) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        float v = __uint_as_float(r1[j]);
-                        if (KIND == 1) v += __uint_as_float(l1[j]);
+                        const float v = __uint_as_float(r1[j]);
                         sum[32 + j] += v + __shfl_xor_sync(0xffffffffu, v, 1);
                     }
                 }
@@ -572,12 +669,13 @@ __global__ void k_zero_clusters(const int32_t* __restrict__ ids, int count, floa
 }
 
 // Stage geometry for R activation rows and element size es: A holds R rows,
-// B (and B_lo for TF32) 64 rows, all with up to 64 contraction columns.
+// B (and B_lo for TF32) 64 rows, all with up to 64 contraction columns.  The
+// TF32 kernel keeps its epilogue exchange tile (kXchBytes) after the stages.
 void tc_stage_geometry(int R, int es, int* a_bytes, int* stage_bytes, int* nstages) {
-    const int rows = R <= 64 ? 64 : 128;  // the MMA reads M = 64 or 128 rows
+    const int rows = R <= 64 ? 64 : 128;  // the BF16 MMA reads M = 64 or 128 activation rows
     *a_bytes = rows * 64 * es;
     *stage_bytes = *a_bytes + 64 * 64 * es * (es == 4 ? 2 : 1);
-    *nstages = std::min(kMaxStages, (kSmemBudget - 1024) / *stage_bytes);
+    *nstages = std::min(kMaxStages, (kSmemBudget - 1024 - (es == 4 ? kXchBytes : 0)) / *stage_bytes);
 }
 
 template <int MODE, int KIND>
@@ -613,7 +711,7 @@ int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st
     p.nstages = nstages;
     int rc = tc_prepare();
     if (rc) return rc;
-    const int smem = nstages * stage_bytes + 1024;
+    const int smem = nstages * stage_bytes + (kind == 1 ? kXchBytes : 0) + 1024;
     if (mode == 0 && kind == 0) return launch_one<0, 0>(p, grid, smem, st);
     if (mode == 1 && kind == 0) return launch_one<1, 0>(p, grid, smem, st);
     if (mode == 0 && kind == 1) return launch_one<0, 1>(p, grid, smem, st);
