@@ -246,6 +246,101 @@ void down_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, st
     entries = 2 + dmax;
 }
 
+// Schedule of the subtree-owning upward pass.  The tree is cut at level Lu as
+// for the downward pass; a task evaluates the subtree of its cut cluster t in
+// post-order (sons before their father), keeping each x̂ in a shared-memory
+// stack entry until its father has used it, so no step waits for another
+// CTA.  Entries come from a free list; at least three exist, for the climb
+// above the cut (own x̂, the brother's x̂, the father's).  Lu is the shallowest
+// level with at least `target` tasks whose step lists fit kUpMaxSteps and
+// whose stacks fit kUpMaxEntries.
+void up_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std::vector<UpStep>& steps,
+                 int32_t& ntasks, int32_t& entries) {
+    const int64_t nc = T.n_clusters();
+    task_ptr.assign(1, 0);
+    steps.clear();
+    ntasks = 0;
+    entries = 3;
+    if (nc < 1) return;
+    std::vector<int64_t> nsub(nc, 1);
+    for (int64_t c = nc - 1; c >= 1; --c) nsub[T.parent[c]] += nsub[c];
+    // post-order step list of the subtree of t and the number of entries it needs
+    auto build = [&](int32_t t, std::vector<UpStep>& v) {
+        v.clear();
+        std::vector<int32_t> free_list;
+        int32_t next_new = 0, used = 0, max_used = 0;
+        auto take = [&]() {
+            int32_t e;
+            if (!free_list.empty()) { e = free_list.back(); free_list.pop_back(); }
+            else e = next_new++;
+            max_used = std::max(max_used, ++used);
+            return e;
+        };
+        auto give = [&](int32_t e) { free_list.push_back(e); --used; };
+        // iterative post-order over the pre-order range of t
+        std::vector<std::pair<int32_t, int>> st{{t, 0}};
+        std::vector<int32_t> entry_of;  // entry holding x̂ of the cluster at the same stack position
+        std::vector<int32_t> done;      // x̂ entries waiting for their father, in order
+        while (!st.empty()) {
+            auto& [c, state] = st.back();
+            if (!T.is_leaf(c) && state == 0) {
+                state = 1;
+                st.push_back({T.son0[c], 0});
+                continue;
+            }
+            if (!T.is_leaf(c) && state == 1) {
+                state = 2;
+                st.push_back({T.son1[c], 0});
+                continue;
+            }
+            if (T.is_leaf(c)) {
+                const int32_t e = take();
+                v.push_back(UpStep{c, -1, -1, e});
+                done.push_back(e);
+            } else {
+                const int32_t e1 = done.back(); done.pop_back();
+                const int32_t e0 = done.back(); done.pop_back();
+                const int32_t e = take();
+                v.push_back(UpStep{c, e0, e1, e});
+                give(e0);
+                give(e1);
+                done.push_back(e);
+            }
+            st.pop_back();
+        }
+        return std::max<int32_t>(max_used, 3);
+    };
+    std::vector<UpStep> tmp;
+    int Lu = T.depth;
+    for (int l = 0; l <= T.depth; ++l) {
+        int64_t count = 0, size = 0;
+        int32_t ent = 0;
+        for (int64_t c = 0; c < nc; ++c)
+            if (T.level[c] == l || (T.level[c] < l && T.is_leaf((int32_t)c))) {
+                ++count;
+                size = std::max(size, nsub[c]);
+                ent = std::max(ent, build((int32_t)c, tmp));
+            }
+        if ((count >= target || l == T.depth) && size <= kUpMaxSteps && ent <= kUpMaxEntries) { Lu = l; break; }
+    }
+    std::vector<std::vector<UpStep>> task_steps;
+    for (int64_t c = 0; c < nc; ++c)
+        if (T.level[c] == Lu || (T.level[c] < Lu && T.is_leaf((int32_t)c))) {
+            task_steps.emplace_back();
+            entries = std::max(entries, build((int32_t)c, task_steps.back()));
+        }
+    // longest tasks first
+    std::vector<size_t> order(task_steps.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return task_steps[a].size() > task_steps[b].size(); });
+    for (size_t i : order) {
+        steps.insert(steps.end(), task_steps[i].begin(), task_steps[i].end());
+        task_ptr.push_back((int32_t)steps.size());
+    }
+    ntasks = (int32_t)task_steps.size();
+}
+
 int cast_copy(h2_matrix* A, const double* src, void** dst, int64_t count, cudaStream_t st) {
     int rc = device_alloc(A, dst, (size_t)(count > 0 ? count : 1) * sizeof(float));
     if (rc) return rc;
@@ -384,6 +479,10 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
         down_schedule(T, 256, task_ptr, dsteps, A->dn_ntasks, A->dn_entries);
         UP(A->d_dn_task_ptr, task_ptr);
         UP(A->d_dn_steps, dsteps);
+        std::vector<UpStep> usteps;
+        up_schedule(T, 256, task_ptr, usteps, A->up_ntasks, A->up_entries);
+        UP(A->d_up_task_ptr, task_ptr);
+        UP(A->d_up_steps, usteps);
     }
     UP(A->d_adm_rowptr, adm_rowptr);
     UP(A->d_adm_col, adm_col);

@@ -144,6 +144,16 @@ struct DownStep {
 constexpr int kDownLoad = 1, kDownStore = 2;
 constexpr int kDownMaxSteps = 192;  // steps of one task at most (the schedule keeps to it)
 
+// One step of the subtree-owning upward pass (k_up_own, h2_mm.cu): a leaf c
+// (rd0 < 0) gets x̂_c = V_cᵀ X|_ĉ; an inner cluster gets x̂_c = E_s0ᵀ x̂_s0 +
+// E_s1ᵀ x̂_s1 with the sons' x̂ in shared-memory stack entries rd0 and rd1.
+// x̂_c goes to global memory and to entry wr.
+struct UpStep {
+    int32_t c, rd0, rd1, wr;
+};
+constexpr int kUpMaxSteps = 64;    // steps of one task at most
+constexpr int kUpMaxEntries = 5;   // stack entries at most (three of them serve the climb above the cut)
+
 struct SyncBufs {
     unsigned* cnt = nullptr;
     int* flag = nullptr;
@@ -188,6 +198,10 @@ struct h2_matrix {
     int32_t* d_dn_task_ptr = nullptr;
     h2::DownStep* d_dn_steps = nullptr;
     int32_t dn_ntasks = 0, dn_entries = 0;
+    // subtree-owning upward pass: task t runs up_steps[up_task_ptr[t]..up_task_ptr[t+1]), then climbs
+    int32_t* d_up_task_ptr = nullptr;
+    h2::UpStep* d_up_steps = nullptr;
+    int32_t up_ntasks = 0, up_entries = 0;
     int32_t* d_adm_rowptr = nullptr; // [nc+1] by row cluster
     int32_t* d_adm_col = nullptr;    // [n_adm]
     int32_t* d_adm_row = nullptr;    // [n_adm]

@@ -388,19 +388,15 @@ __global__ void __launch_bounds__(kThreads) k_leaf_bwd_near(
     }
 }
 
-// Records an event between phases when timing is enabled (h2_timing_enable).
 // ---------------------------------------------------------------------------
-// FP32 transfer passes with the whole contraction staged at once (k % 4 == 0,
-// k <= 64, m % 4 == 0): cp.async moves every operand row of a step (V_t and
-// X|_t̂ at a leaf; E_{s0}, E_{s1}, x̂_{s0}, x̂_{s1} at a father; Eᵀ_c and ŷ_father
-// downwards) into shared memory in 16-byte pieces, then one barrier, then the
-// register-tiled contraction.  The data another CTA of the same launch wrote
-// (x̂ of the sons) is copied with .cg (L2, not L1).  The downward pass
-// (k_down_own) gives each CTA whole subtrees and needs no flags.
+// FP32 transfer passes for k % 4 == 0, k <= 64, m % 4 == 0, leaves of at most
+// 64 points.  The tree is cut at one level; each task (a cut cluster) is owned
+// by one CTA, which evaluates its subtree with every intermediate x̂ or ŷ kept
+// in shared memory.  Static operands (V_t, X|_t̂, the transfer matrices, the
+// coupling results) arrive by bulk copies one step ahead.  Only the clusters
+// above the cut in the upward pass are shared between CTAs (last arriver of
+// two brothers computes the father).
 // ---------------------------------------------------------------------------
-constexpr int kFastK = 128;  // contraction rows staged at most (two sons of k = 64)
-constexpr int kFastLdA = 68;  // 64 output rows + 4: rows stay 16-byte aligned
-
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp16_cg(void* s, const void* g) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(s)), "l"(g) : "memory");
@@ -408,135 +404,184 @@ __device__ __forceinline__ void cp16_cg(void* s, const void* g) {
 __device__ __forceinline__ void cp_commit_wait() {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
-// rows [0, rows) of a row-major source (row stride ld floats, `width` floats
-// from column c0, width % 4 == 0) into dst rows of stride dld, from row r0.
-__device__ __forceinline__ void stage_rows(float* dst, int dld, int r0, const float* src, int64_t ld, int rows,
-                                           int width) {
-    const int per = width >> 2;
-    for (int e = threadIdx.x; e < rows * per; e += blockDim.x) {
-        const int r = e / per, q = e % per;
-        cp16_cg(dst + (r0 + r) * dld + 4 * q, src + (int64_t)r * ld + 4 * q);
-    }
-}
-
-// acc[4×CN] += a[0:K][rows 4ty..] ᵀ-contracted with b[0:K][cols CN·tx..]
-template <int CN>
-__device__ __forceinline__ void fast_contract(float (&acc)[4][CN], const float* a, const float* b, int K) {
-    constexpr int NT = 16 * CN;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-#pragma unroll 8
+// acc[4][4] += a[0:K][rows 4ty..4ty+3] contracted with b[0:K][cols 4tx..4tx+3],
+// row strides lda and ldb floats (multiples of 4): two 16-byte shared loads
+// per 16 FMAs.  Rows and columns past the valid ones read neighbouring data
+// and give outputs nobody stores.
+__device__ __forceinline__ void contract44(float (&acc)[4][4], const float* a, int lda, const float* b, int ldb, int K,
+                                           int tx, int ty) {
+    const float* pa = a + 4 * ty;
+    const float* pb = b + 4 * tx;
+#pragma unroll 4
     for (int kk = 0; kk < K; ++kk) {
-        const float4 av = *(const float4*)(a + kk * kFastLdA + 4 * ty);
-        float bv[CN];
-        lds_vec<CN>(b + kk * NT + CN * tx, bv);
-#pragma unroll
-        for (int c = 0; c < CN; ++c) {
-            acc[0][c] = fmaf(av.x, bv[c], acc[0][c]);
-            acc[1][c] = fmaf(av.y, bv[c], acc[1][c]);
-            acc[2][c] = fmaf(av.z, bv[c], acc[2][c]);
-            acc[3][c] = fmaf(av.w, bv[c], acc[3][c]);
-        }
-    }
-}
-
-template <int CN, bool ACCUM>
-__device__ __forceinline__ void fast_store(const float (&acc)[4][CN], float* C, int m, int k, int col0) {
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int gr = 4 * ty + r;
-        if (gr >= k) continue;
-#pragma unroll
-        for (int c = 0; c < CN; ++c) {
-            const int gc = col0 + CN * tx + c;
-            if (gc >= m) continue;
-            float* p = C + (int64_t)gr * m + gc;
-            if (ACCUM) *p += acc[r][c]; else *p = acc[r][c];
-        }
-    }
-}
-
-template <int CN>
-__global__ void __launch_bounds__(kThreads) k_up_fast(const int32_t* __restrict__ leaves,
-                                                      const int32_t* __restrict__ cl_off,
-                                                      const int32_t* __restrict__ cl_size,
-                                                      const int32_t* __restrict__ parent,
-                                                      const int32_t* __restrict__ son0,
-                                                      const int32_t* __restrict__ son1, const float* __restrict__ V,
-                                                      const float* __restrict__ E, const float* __restrict__ Xp,
-                                                      float* xhat, unsigned* __restrict__ cnt, int k, int m) {
-    constexpr int NT = 16 * CN;
-    extern __shared__ __align__(16) float fsm[];
-    float* a = fsm;                      // [kFastK][kFastLdA]
-    float* b = fsm + kFastK * kFastLdA;  // [kFastK][NT]
-    __shared__ int s_go;
-    const int tile = blockIdx.y, gy = gridDim.y;
-    const int col0 = tile * NT, w = min(NT, m - col0);
-    const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
-    int c = leaves[blockIdx.x];
-    const int off = cl_off[c], nt = cl_size[c];
-    stage_rows(a, kFastLdA, 0, V + (int64_t)off * k, k, nt, k);
-    stage_rows(b, NT, 0, Xp + (int64_t)off * m + col0, m, nt, w);
-    cp_commit_wait();
-    __syncthreads();
-    float acc[4][CN];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int q = 0; q < CN; ++q) acc[r][q] = 0.f;
-    fast_contract<CN>(acc, a, b, nt);
-    fast_store<CN, false>(acc, xhat + (int64_t)c * km, m, k, col0);
-    while (true) {
-        const int par = parent[c];
-        if (par < 0) break;
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const unsigned old = atomicAdd(&cnt[(int64_t)par * gy + tile], 1u);
-            s_go = old == 1u;
-            if (old == 1u) cnt[(int64_t)par * gy + tile] = 0u;
-        }
-        __syncthreads();
-        if (!s_go) break;
-        __threadfence();
-        c = par;
-        const int s0 = son0[c], s1 = son1[c];
-        // x̂_c = E_{s0}ᵀ x̂_{s0} + E_{s1}ᵀ x̂_{s1}: one contraction over 2k rows
-        stage_rows(a, kFastLdA, 0, E + s0 * kk, k, k, k);
-        stage_rows(a, kFastLdA, k, E + s1 * kk, k, k, k);
-        stage_rows(b, NT, 0, xhat + s0 * km + col0, m, k, w);
-        stage_rows(b, NT, k, xhat + s1 * km + col0, m, k, w);
-        cp_commit_wait();
-        __syncthreads();
+        const float4 x = *(const float4*)(pa + kk * lda);
+        const float4 y = *(const float4*)(pb + kk * ldb);
+        const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int q = 0; q < CN; ++q) acc[r][q] = 0.f;
-        fast_contract<CN>(acc, a, b, 2 * k);
-        fast_store<CN, false>(acc, xhat + (int64_t)c * km, m, k, col0);
+            for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(xv[r], yv[c], acc[r][c]);
     }
 }
 
-// acc[4×CN] += a[0:K][rows 4ty..]  contracted with b[0:K][cols CN·tx..], row
-// strides lda and ldb (multiples of 4 floats; rows and columns past the valid
-// ones read neighbouring data and give outputs nobody stores).
+// Upward pass with subtree ownership (schedule: up_schedule, h2_build.cu), the
+// forward transformation of Alg. "fast_addeval" (Sec. 3): x̂_t = V_tᵀ X|_t̂ at
+// the leaves and x̂_t = E_s0ᵀ x̂_s0 + E_s1ᵀ x̂_s1 above.  A CTA claims a task and
+// evaluates its subtree in post-order; the static operands of step s + 1 (V_c
+// and X|_ĉ, or E_s0 and E_s1) arrive by bulk copies while step s computes, the
+// sons' x̂ come from the shared-memory stack.  Above the cut the last of two
+// brothers to finish computes their father (an atomic counter per cluster,
+// reset by the last arriver); it prefetches both transfer matrices before it
+// knows whether it is last.  Sons are always added in the order s0, s1, so the
+// result does not depend on which brother arrives last.  64·CN threads, thread
+// (tx, ty) owns rows 4ty.. and columns 4tx.. of the k×m result.
 template <int CN>
-__device__ __forceinline__ void own_contract(float (&acc)[4][CN], const float* a, int lda, const float* b, int ldb,
-                                             int K) {
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-#pragma unroll 8
-    for (int kk = 0; kk < K; ++kk) {
-        const float4 av = *(const float4*)(a + kk * lda + 4 * ty);
-        float bv[CN];
-        lds_vec<CN>(b + kk * ldb + CN * tx, bv);
+__global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ task_ptr, int ntasks,
+                                                    const UpStep* __restrict__ steps,
+                                                    const int32_t* __restrict__ cl_off,
+                                                    const int32_t* __restrict__ cl_size,
+                                                    const int32_t* __restrict__ parent,
+                                                    const int32_t* __restrict__ son0,
+                                                    const int32_t* __restrict__ son1, const float* __restrict__ V,
+                                                    const float* __restrict__ E, const float* __restrict__ Xp,
+                                                    float* xhat, unsigned* __restrict__ cnt, unsigned* __restrict__ claim,
+                                                    int* __restrict__ err, int nent, int k, int m) {
+    constexpr int NT = 16 * CN;
+    extern __shared__ __align__(16) float fsm[];
+    float* sbuf = fsm;                 // [2 slots][2][64·64]  V_c and X|_ĉ, or E_s0 and E_s1
+    float* stk = sbuf + 4 * 64 * 64;   // [entries][64·NT]     x̂ waiting for the father
+    __shared__ int s_task, s_go;
+    __shared__ UpStep s_steps[kUpMaxSteps];
+    __shared__ int s_off[kUpMaxSteps], s_nt[kUpMaxSteps];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int tx = threadIdx.x % (4 * CN), ty = threadIdx.x / (4 * CN);
+    const bool colv = 4 * tx < m;
+    const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    uint32_t phase = 0;
+    bool failed = false;
+    auto slot = [&](int b, int h) { return sbuf + (2 * b + h) * 64 * 64; };
+    auto ent = [&](int e) { return stk + e * 64 * NT; };
+    // acc → stack entry e and x̂_c in global memory
+    auto put = [&](const float (&acc)[4][4], int e, int c) {
+        if (!colv) return;
+        float* out = ent(e);
+        float* g = xhat + (int64_t)c * km;
 #pragma unroll
-        for (int c = 0; c < CN; ++c) {
-            acc[0][c] = fmaf(av.x, bv[c], acc[0][c]);
-            acc[1][c] = fmaf(av.y, bv[c], acc[1][c]);
-            acc[2][c] = fmaf(av.z, bv[c], acc[2][c]);
-            acc[3][c] = fmaf(av.w, bv[c], acc[3][c]);
+        for (int r = 0; r < 4; ++r) {
+            const float4 v = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+            *(float4*)(out + (4 * ty + r) * m + 4 * tx) = v;
+            if (4 * ty + r < k) *(float4*)(g + (4 * ty + r) * m + 4 * tx) = v;
+        }
+    };
+    auto wait_slot = [&](int b) {
+        const bool ok = mbar_wait(&bar[b], (phase >> b) & 1u);
+        phase ^= 1u << b;
+        return ok;
+    };
+    while (!failed) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_task = (int)atomicAdd(claim, 1u);
+        __syncthreads();
+        const int task = s_task;
+        if (task >= ntasks) break;
+        const int s0 = task_ptr[task], s1 = min(task_ptr[task + 1], s0 + kUpMaxSteps);
+        for (int i = threadIdx.x; i < s1 - s0; i += blockDim.x) {
+            const UpStep u = steps[s0 + i];
+            s_steps[i] = u;
+            s_off[i] = cl_off[u.c];
+            s_nt[i] = cl_size[u.c];
+        }
+        __syncthreads();
+        auto issue = [&](int s, int b) {
+            if (threadIdx.x != 0) return;
+            const UpStep u = s_steps[s - s0];
+            if (u.rd0 < 0) {
+                const int off = s_off[s - s0], nt = s_nt[s - s0];
+                const uint32_t vb = (uint32_t)nt * k * 4, xb = (uint32_t)nt * m * 4;
+                mbar_expect_tx(&bar[b], vb + xb);
+                bulk_g2s(slot(b, 0), V + (int64_t)off * k, vb, &bar[b]);
+                bulk_g2s(slot(b, 1), Xp + (int64_t)off * m, xb, &bar[b]);
+            } else {
+                mbar_expect_tx(&bar[b], (uint32_t)(2 * kk * 4));
+                bulk_g2s(slot(b, 0), E + (int64_t)son0[u.c] * kk, (uint32_t)(kk * 4), &bar[b]);
+                bulk_g2s(slot(b, 1), E + (int64_t)son1[u.c] * kk, (uint32_t)(kk * 4), &bar[b]);
+            }
+        };
+        issue(s0, 0);
+        int cur = -1;
+        for (int s = s0; s < s1; ++s) {
+            const int b = (s - s0) & 1;
+            if (s + 1 < s1) issue(s + 1, b ^ 1);
+            const bool ok = wait_slot(b);
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) {
+                    atomicExch(err, 10);
+                    mbar_wait(&bar[b], ((phase >> b) & 1u) ^ 1u);
+                    if (s + 1 < s1) mbar_wait(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
+                }
+                failed = true;
+                break;
+            }
+            const UpStep u = s_steps[s - s0];
+            float acc[4][4] = {};
+            if (u.rd0 < 0) {
+                contract44(acc, slot(b, 0), k, slot(b, 1), m, s_nt[s - s0], tx, ty);
+            } else {
+                contract44(acc, slot(b, 0), k, ent(u.rd0), m, k, tx, ty);
+                contract44(acc, slot(b, 1), k, ent(u.rd1), m, k, tx, ty);
+            }
+            put(acc, u.wr, u.c);
+            cur = u.wr;
+            __syncthreads();
+        }
+        if (failed || cur < 0) break;
+        // ---- climb above the cut ----
+        int c = s_steps[s1 - 1 - s0].c;
+        while (true) {
+            const int par = parent[c];
+            if (par < 0) break;
+            const int a0 = son0[par], a1 = son1[par];
+            __syncthreads();  // every read of slot 0 and every store of x̂_c is done
+            if (threadIdx.x == 0) {
+                mbar_expect_tx(&bar[0], (uint32_t)(2 * kk * 4));
+                bulk_g2s(slot(0, 0), E + (int64_t)a0 * kk, (uint32_t)(kk * 4), &bar[0]);
+                bulk_g2s(slot(0, 1), E + (int64_t)a1 * kk, (uint32_t)(kk * 4), &bar[0]);
+            }
+            if (threadIdx.x == 0) {
+                __threadfence();
+                const unsigned old = atomicAdd(&cnt[par], 1u);
+                s_go = old == 1u;
+                if (old == 1u) {
+                    cnt[par] = 0u;
+                    __threadfence();
+                }
+            }
+            const bool ok = wait_slot(0);  // the prefetch lands either way: nothing stays in flight
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicExch(err, 10);
+                failed = true;
+                break;
+            }
+            if (!s_go) break;
+            // the brother's x̂ (written by another CTA) through the generic proxy
+            const int bro = a0 == c ? a1 : a0;
+            const int eb = (cur + 1) % 3, er = (cur + 2) % 3;
+            const float* gsrc = xhat + (int64_t)bro * km;
+            for (int e = threadIdx.x; e < (int)(km / 4); e += blockDim.x) cp16_cg(ent(eb) + 4 * e, gsrc + 4 * e);
+            cp_commit_wait();
+            __syncthreads();
+            float acc[4][4] = {};
+            contract44(acc, slot(0, 0), k, ent(a0 == c ? cur : eb), m, k, tx, ty);
+            contract44(acc, slot(0, 1), k, ent(a1 == c ? cur : eb), m, k, tx, ty);
+            put(acc, er, par);
+            cur = er;
+            c = par;
         }
     }
 }
@@ -548,9 +593,11 @@ __device__ __forceinline__ void own_contract(float (&acc)[4][CN], const float* a
 // an earlier step of the same task, so no step waits for another CTA.  The
 // static operands of step s + 1 (Eᵀ_c, k×k, and the coupling result ŷ_c, k×m,
 // both contiguous) arrive by two bulk copies, issued by one thread while step
-// s computes.  All ŷ buffers keep rows of m floats.
+// s computes.  All ŷ buffers keep rows of m floats.  64·CN threads: thread
+// (tx, ty) = (tid mod 4CN, tid div 4CN) owns rows 4ty.. and columns 4tx.. of
+// the k×m result.
 template <int CN>
-__global__ void __launch_bounds__(kThreads) k_down_own(const int32_t* __restrict__ task_ptr, int ntasks,
+__global__ void __launch_bounds__(64 * CN) k_down_own(const int32_t* __restrict__ task_ptr, int ntasks,
                                                        const DownStep* __restrict__ steps,
                                                        const float* __restrict__ Et, float* yhat,
                                                        unsigned* __restrict__ claim, int* __restrict__ err, int k,
@@ -563,7 +610,8 @@ __global__ void __launch_bounds__(kThreads) k_down_own(const int32_t* __restrict
     __shared__ int s_task;
     __shared__ DownStep s_steps[kDownMaxSteps];  // the task's steps: no global load between two steps
     __shared__ __align__(8) uint64_t bar[2];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int tx = threadIdx.x % (4 * CN), ty = threadIdx.x / (4 * CN);
+    const bool colv = 4 * tx < m;  // m % 4 == 0: the thread's four columns are valid together
     const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
     const uint32_t ebytes = (uint32_t)(kk * 4), ybytes = (uint32_t)(km * 4);
     if (threadIdx.x == 0) {
@@ -615,26 +663,31 @@ __global__ void __launch_bounds__(kThreads) k_down_own(const int32_t* __restrict
             const DownStep d = s_steps[s - s0];
             if (!(d.flags & kDownLoad)) {
                 const float* cb = cbuf + b * 64 * NT;
-                float acc[4][CN];
+                float acc[4][4];
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int q = 0; q < CN; ++q) acc[r][q] = cb[(4 * ty + r) * m + CN * tx + q];
-                own_contract<CN>(acc, ebuf + b * 64 * 64, k, stk + d.rd * 64 * NT, m, k);
+                for (int r = 0; r < 4; ++r) {
+                    const float4 v = *(const float4*)(cb + (4 * ty + r) * m + 4 * tx);
+                    acc[r][0] = v.x; acc[r][1] = v.y; acc[r][2] = v.z; acc[r][3] = v.w;
+                }
+                contract44(acc, ebuf + b * 64 * 64, k, stk + d.rd * 64 * NT, m, k, tx, ty);
                 float* out = stk + d.wr * 64 * NT;
+                float* gout = yhat + (int64_t)d.c * km;
+                if (colv) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int q = 0; q < CN; ++q)
-                        if (CN * tx + q < m) out[(4 * ty + r) * m + CN * tx + q] = acc[r][q];
-                if (d.flags & kDownStore) fast_store<CN, false>(acc, yhat + (int64_t)d.c * km, m, k, 0);
+                    for (int r = 0; r < 4; ++r) {
+                        const float4 v = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+                        *(float4*)(out + (4 * ty + r) * m + 4 * tx) = v;
+                        if ((d.flags & kDownStore) && 4 * ty + r < k) *(float4*)(gout + (4 * ty + r) * m + 4 * tx) = v;
+                    }
+                }
             }
             __syncthreads();
         }
     }
 }
 
-int fast_smem_bytes(int cn) { return (kFastK * kFastLdA + kFastK * 16 * cn) * (int)sizeof(float); }
+// k_up_own: two slots of two 64×64 blocks plus the stack
+int up_own_smem_bytes(int cn, int entries) { return (4 * 64 * 64 + entries * 64 * 16 * cn) * (int)sizeof(float); }
 // k_down_own: two Eᵀ and two ŷ buffers plus the stack (at most 8 entries)
 int down_own_smem_bytes(int cn, int entries) { return (2 * 64 * 64 + (2 + entries) * 64 * 16 * cn) * (int)sizeof(float); }
 
@@ -644,9 +697,9 @@ int fast_prepare() {
     int dev = 0;
     H2_CUDA_TRY(cudaGetDevice(&dev));
     if (dev == g_fast_attr_device) return 0;
-    H2_CUDA_TRY(cudaFuncSetAttribute(k_up_fast<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(1)));
-    H2_CUDA_TRY(cudaFuncSetAttribute(k_up_fast<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(2)));
-    H2_CUDA_TRY(cudaFuncSetAttribute(k_up_fast<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem_bytes(4)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_up_own<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, up_own_smem_bytes(1, kUpMaxEntries)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_up_own<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, up_own_smem_bytes(2, kUpMaxEntries)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_up_own<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, up_own_smem_bytes(4, kUpMaxEntries)));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_down_own<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_own_smem_bytes(1, 8)));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_down_own<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_own_smem_bytes(2, 8)));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_down_own<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_own_smem_bytes(4, 8)));
@@ -864,14 +917,17 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         if ((rc = launch_pack_act(Xp, mc, NL, nullptr, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, R, Xcm, es, st))) return rc;
         marks.mark();
         // staged transfer passes when the rows are 16-byte multiples (k, mc % 4 == 0, k <= 64)
-        const bool fast = A->f32.Et && k % 4 == 0 && k <= 64 && mc % 4 == 0;
+        const bool fast = A->f32.Et && k % 4 == 0 && k <= 64 && mc % 4 == 0 && A->T.leaf_size <= 64;
         const int fcn = mc <= 16 ? 1 : (mc <= 32 ? 2 : 4);
         if (fast) {
             if ((rc = fast_prepare())) return rc;
-            const unsigned NLu = (unsigned)NL;
-            if (fcn == 1) k_up_fast<1><<<dim3(NLu, 1), kThreads, fast_smem_bytes(1), st>>>(A->d_leaves, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, k, mc);
-            else if (fcn == 2) k_up_fast<2><<<dim3(NLu, 1), kThreads, fast_smem_bytes(2), st>>>(A->d_leaves, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, k, mc);
-            else k_up_fast<4><<<dim3(NLu, 1), kThreads, fast_smem_bytes(4), st>>>(A->d_leaves, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, k, mc);
+            const int usm = up_own_smem_bytes(fcn, A->up_entries);
+            const unsigned g = (unsigned)std::min(A->up_ntasks, 152 * std::max(1, (227 * 1024) / (usm + 2048)));
+            H2_CUDA_TRY(cudaMemsetAsync(sbc.cnt, 0, (size_t)nc * sizeof(unsigned), st));
+            H2_CUDA_TRY(cudaMemsetAsync(sbc.claim, 0, sizeof(unsigned), st));
+            if (fcn == 1) k_up_own<1><<<g, 64, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc);
+            else if (fcn == 2) k_up_own<2><<<g, 128, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc);
+            else k_up_own<4><<<g, 256, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc);
             H2_LAUNCH_CHECK();
             marks.mark();
             marks.mark();
@@ -904,9 +960,9 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
                 const float* Et = (const float*)A->f32.Et;
                 const int smem = down_own_smem_bytes(fcn, A->dn_entries);
                 const unsigned g = (unsigned)std::min(A->dn_ntasks, 152 * std::max(1, (227 * 1024) / (smem + 4096)));
-                if (fcn == 1) k_down_own<1><<<g, kThreads, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc);
-                else if (fcn == 2) k_down_own<2><<<g, kThreads, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc);
-                else k_down_own<4><<<g, kThreads, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc);
+                if (fcn == 1) k_down_own<1><<<g, 64 * 1, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc);
+                else if (fcn == 2) k_down_own<2><<<g, 64 * 2, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc);
+                else k_down_own<4><<<g, 64 * 4, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc);
                 H2_LAUNCH_CHECK();
             }
         } else if ((rc = backward_pass<float, RM, CN>(A, E, yhat, mc, gy, gzk, st, sbc))) {
