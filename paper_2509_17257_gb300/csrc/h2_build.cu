@@ -264,6 +264,9 @@ void up_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std:
     if (nc < 1) return;
     std::vector<int64_t> nsub(nc, 1);
     for (int64_t c = nc - 1; c >= 1; --c) nsub[T.parent[c]] += nsub[c];
+    std::vector<int32_t> leaf_pos(nc, -1);  // position among the leaves in cluster order
+    for (int64_t c = 0, lp = 0; c < nc; ++c)
+        if (T.is_leaf((int32_t)c)) leaf_pos[c] = (int32_t)lp++;
     // post-order step list of the subtree of t and the number of entries it needs
     auto build = [&](int32_t t, std::vector<UpStep>& v) {
         v.clear();
@@ -295,7 +298,7 @@ void up_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std:
             }
             if (T.is_leaf(c)) {
                 const int32_t e = take();
-                v.push_back(UpStep{c, -1, -1, e});
+                v.push_back(UpStep{c, -1, leaf_pos[c], e});
                 done.push_back(e);
             } else {
                 const int32_t e1 = done.back(); done.pop_back();

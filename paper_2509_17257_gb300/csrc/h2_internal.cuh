@@ -145,9 +145,10 @@ constexpr int kDownLoad = 1, kDownStore = 2;
 constexpr int kDownMaxSteps = 192;  // steps of one task at most (the schedule keeps to it)
 
 // One step of the subtree-owning upward pass (k_up_own, h2_mm.cu): a leaf c
-// (rd0 < 0) gets x̂_c = V_cᵀ X|_ĉ; an inner cluster gets x̂_c = E_s0ᵀ x̂_s0 +
-// E_s1ᵀ x̂_s1 with the sons' x̂ in shared-memory stack entries rd0 and rd1.
-// x̂_c goes to global memory and to entry wr.
+// (rd0 < 0, rd1 = its position among the leaves) gets x̂_c = V_cᵀ X|_ĉ; an
+// inner cluster gets x̂_c = E_s0ᵀ x̂_s0 + E_s1ᵀ x̂_s1 with the sons' x̂ in
+// shared-memory stack entries rd0 and rd1.  x̂_c goes to global memory and to
+// entry wr.
 struct UpStep {
     int32_t c, rd0, rd1, wr;
 };

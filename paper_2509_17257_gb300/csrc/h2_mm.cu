@@ -425,6 +425,47 @@ __device__ __forceinline__ void contract44(float (&acc)[4][4], const float* a, i
     }
 }
 
+// Split activation tiles written by the transfer passes for the tensor-core
+// phases (the layout k_pack_act writes): act holds one R×KP tile per cluster
+// (x̂ in the upward pass, leaf ŷ in the downward pass), leafX one R×kp tile per
+// leaf (kp = xkoff[l+1] - xkoff[l]) of the leaf's X rows.
+struct PackOut {
+    uint8_t* act;
+    uint8_t* leafX;
+    const int64_t* xkoff;
+    int KP, R, es;
+};
+
+// The thread's 4×4 block of a k×m result (rows 4ty.., columns 4tx..) into a
+// cluster's tile, zeros in the padding rows (columns i >= m) and columns
+// (κ >= k).
+__device__ __forceinline__ void pack_rows(const PackOut& pk, uint8_t* tile, const float (&acc)[4][4], int tx, int ty,
+                                          int k, int m) {
+    if (4 * ty >= pk.KP) return;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int i = 4 * tx + c;
+        if (2 * i >= pk.R) continue;
+        float v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = (i < m && 4 * ty + r < k) ? acc[r][c] : 0.f;
+        put_act4(tile, pk.KP, pk.es, i, 4 * ty, v);
+    }
+}
+
+// A leaf's X rows (nt points × m columns in shared memory, row stride m) into
+// its tile of kp contraction columns (the points), zero padded.
+__device__ __forceinline__ void pack_points(const PackOut& pk, uint8_t* tile, int kp, const float* x, int nt, int m) {
+    const int half = pk.R >> 1;
+    for (int it = threadIdx.x; it < (kp >> 2) * half; it += blockDim.x) {
+        const int q0 = 4 * (it / half), i = it % half;
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = (i < m && q0 + u < nt) ? x[(q0 + u) * m + i] : 0.f;
+        put_act4(tile, kp, pk.es, i, q0, v);
+    }
+}
+
 // Upward pass with subtree ownership (schedule: up_schedule, h2_build.cu), the
 // forward transformation of Alg. "fast_addeval" (Sec. 3): x̂_t = V_tᵀ X|_t̂ at
 // the leaves and x̂_t = E_s0ᵀ x̂_s0 + E_s1ᵀ x̂_s1 above.  A CTA claims a task and
@@ -446,7 +487,7 @@ __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ 
                                                     const int32_t* __restrict__ son1, const float* __restrict__ V,
                                                     const float* __restrict__ E, const float* __restrict__ Xp,
                                                     float* xhat, unsigned* __restrict__ cnt, unsigned* __restrict__ claim,
-                                                    int* __restrict__ err, int nent, int k, int m) {
+                                                    int* __restrict__ err, int nent, int k, int m, PackOut pk) {
     constexpr int NT = 16 * CN;
     extern __shared__ __align__(16) float fsm[];
     float* sbuf = fsm;                 // [2 slots][2][64·64]  V_c and X|_ĉ, or E_s0 and E_s1
@@ -467,8 +508,9 @@ __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ 
     bool failed = false;
     auto slot = [&](int b, int h) { return sbuf + (2 * b + h) * 64 * 64; };
     auto ent = [&](int e) { return stk + e * 64 * NT; };
-    // acc → stack entry e and x̂_c in global memory
+    // acc → stack entry e, x̂_c in global memory and its split tile for the coupling phase
     auto put = [&](const float (&acc)[4][4], int e, int c) {
+        pack_rows(pk, pk.act + (int64_t)c * pk.KP * pk.R * pk.es, acc, tx, ty, k, m);
         if (!colv) return;
         float* out = ent(e);
         float* g = xhat + (int64_t)c * km;
@@ -531,7 +573,11 @@ __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ 
             const UpStep u = s_steps[s - s0];
             float acc[4][4] = {};
             if (u.rd0 < 0) {
-                contract44(acc, slot(b, 0), k, slot(b, 1), m, s_nt[s - s0], tx, ty);
+                const int nt = s_nt[s - s0];
+                contract44(acc, slot(b, 0), k, slot(b, 1), m, nt, tx, ty);
+                // X|_ĉ (in shared memory) as the leaf's split tile for the nearfield phase
+                const int64_t x0 = pk.xkoff[u.rd1];
+                pack_points(pk, pk.leafX + x0 * pk.R * pk.es, (int)(pk.xkoff[u.rd1 + 1] - x0), slot(b, 1), nt, m);
             } else {
                 contract44(acc, slot(b, 0), k, ent(u.rd0), m, k, tx, ty);
                 contract44(acc, slot(b, 1), k, ent(u.rd1), m, k, tx, ty);
@@ -601,7 +647,7 @@ __global__ void __launch_bounds__(64 * CN) k_down_own(const int32_t* __restrict_
                                                        const DownStep* __restrict__ steps,
                                                        const float* __restrict__ Et, float* yhat,
                                                        unsigned* __restrict__ claim, int* __restrict__ err, int k,
-                                                       int m) {
+                                                       int m, PackOut pk) {
     constexpr int NT = 16 * CN;
     extern __shared__ __align__(16) float fsm[];
     float* ebuf = fsm;                  // [2][64·64]       Eᵀ_c
@@ -672,6 +718,7 @@ __global__ void __launch_bounds__(64 * CN) k_down_own(const int32_t* __restrict_
                 contract44(acc, ebuf + b * 64 * 64, k, stk + d.rd * 64 * NT, m, k, tx, ty);
                 float* out = stk + d.wr * 64 * NT;
                 float* gout = yhat + (int64_t)d.c * km;
+                if (d.flags & kDownStore) pack_rows(pk, pk.act + (int64_t)d.c * pk.KP * pk.R * pk.es, acc, tx, ty, k, m);
                 if (colv) {
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
@@ -914,27 +961,31 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
             k_gather<float><<<g, 256, 0, st>>>(X + c0, ldx, A->d_perm, n, mc, Xp);
             H2_LAUNCH_CHECK();
         }
-        if ((rc = launch_pack_act(Xp, mc, NL, nullptr, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, R, Xcm, es, st))) return rc;
-        marks.mark();
-        // staged transfer passes when the rows are 16-byte multiples (k, mc % 4 == 0, k <= 64)
+        // subtree-owning transfer passes when the rows are 16-byte multiples (k, mc % 4 == 0, k <= 64);
+        // they also write the split tiles of X (leaves), x̂ and leaf ŷ
         const bool fast = A->f32.Et && k % 4 == 0 && k <= 64 && mc % 4 == 0 && A->T.leaf_size <= 64;
+        if (!fast && (rc = launch_pack_act(Xp, mc, NL, nullptr, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, R, Xcm, es, st)))
+            return rc;
+        marks.mark();
         const int fcn = mc <= 16 ? 1 : (mc <= 32 ? 2 : 4);
         if (fast) {
             if ((rc = fast_prepare())) return rc;
+            const PackOut pk{xcm, Xcm, D.xkoff, KP, R, es};
             const int usm = up_own_smem_bytes(fcn, A->up_entries);
             const unsigned g = (unsigned)std::min(A->up_ntasks, 152 * std::max(1, (227 * 1024) / (usm + 2048)));
             H2_CUDA_TRY(cudaMemsetAsync(sbc.cnt, 0, (size_t)nc * sizeof(unsigned), st));
             H2_CUDA_TRY(cudaMemsetAsync(sbc.claim, 0, sizeof(unsigned), st));
-            if (fcn == 1) k_up_own<1><<<g, 64, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc);
-            else if (fcn == 2) k_up_own<2><<<g, 128, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc);
-            else k_up_own<4><<<g, 256, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc);
+            if (fcn == 1) k_up_own<1><<<g, 64, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk);
+            else if (fcn == 2) k_up_own<2><<<g, 128, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk);
+            else k_up_own<4><<<g, 256, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk);
             H2_LAUNCH_CHECK();
             marks.mark();
             marks.mark();
         } else if ((rc = forward_pass<float, RM, CN>(A, V, E, Xp, xhat, mc, gy, gzk, st, sbc, marks))) {
             return rc;
         }
-        if ((rc = launch_pack_act(xhat, mc, (int)nc, nullptr, nullptr, nullptr, k, nullptr, KP, mc, R, xcm, es, st))) return rc;
+        if (!fast && (rc = launch_pack_act(xhat, mc, (int)nc, nullptr, nullptr, nullptr, k, nullptr, KP, mc, R, xcm, es, st)))
+            return rc;
         if ((rc = launch_zero_clusters(D.c_zero, D.c_nzero, yhat, k, mc, mc, st))) return rc;
         TcGemmParams cp{};
         cp.n_items = D.c_nitems;
@@ -953,22 +1004,27 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         if (cp.n_items > 0 && (rc = launch_tc_gemm(0, kind, cp, std::min(cp.n_items, grid_cap), st))) return rc;
         marks.kernel_end();
         marks.mark();
+        bool leaf_y_packed = false;
         if (fast) {
             const int n_items = (int)A->down_ptr[A->depth + 1];
             if (n_items > 0) {
+                const PackOut pk{ycm, nullptr, nullptr, KP, R, es};
+                leaf_y_packed = true;
                 H2_CUDA_TRY(cudaMemsetAsync(sbc.claim, 0, sizeof(unsigned), st));
                 const float* Et = (const float*)A->f32.Et;
                 const int smem = down_own_smem_bytes(fcn, A->dn_entries);
                 const unsigned g = (unsigned)std::min(A->dn_ntasks, 152 * std::max(1, (227 * 1024) / (smem + 4096)));
-                if (fcn == 1) k_down_own<1><<<g, 64 * 1, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc);
-                else if (fcn == 2) k_down_own<2><<<g, 64 * 2, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc);
-                else k_down_own<4><<<g, 64 * 4, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc);
+                if (fcn == 1) k_down_own<1><<<g, 64 * 1, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
+                else if (fcn == 2) k_down_own<2><<<g, 64 * 2, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
+                else k_down_own<4><<<g, 64 * 4, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
                 H2_LAUNCH_CHECK();
             }
         } else if ((rc = backward_pass<float, RM, CN>(A, E, yhat, mc, gy, gzk, st, sbc))) {
             return rc;
         }
-        if ((rc = launch_pack_act(yhat, mc, NL, A->d_leaves, nullptr, nullptr, k, nullptr, KP, mc, R, ycm, es, st))) return rc;
+        if (!leaf_y_packed &&
+            (rc = launch_pack_act(yhat, mc, NL, A->d_leaves, nullptr, nullptr, k, nullptr, KP, mc, R, ycm, es, st)))
+            return rc;
         marks.mark();
         TcGemmParams lp{};
         lp.n_items = D.l_nitems;

@@ -132,13 +132,6 @@ __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Byte offset of element (row r, column c) of a core-matrix tile whose rows hold
-// kp values of es bytes (kp·es a multiple of 16): 8-row groups outermost, then
-// 16-byte column chunks, then the 8 rows of 16 bytes of one core matrix.
-__host__ __device__ __forceinline__ int64_t cm_off(int r, int c, int kp, int es) {
-    const int per = 16 / es;
-    return ((int64_t)(r >> 3) * (kp / per) + (c / per)) * 128 + (r & 7) * 16 + (c % per) * es;
-}
 
 }  // namespace
 
