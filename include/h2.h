@@ -91,7 +91,10 @@ typedef struct h2_info_t {
     int64_t bytes_bf16;   /* device bytes of the BF16 copy (0 if none) */
     double flops_per_col; /* algorithmic flops of one product per column of X */
     int32_t launches;     /* kernel launches of one product on the CUDA cores (FP64, Aᵀ) */
-    int32_t launches_tc;  /* kernel launches of one tensor-core product (FP32, BF16)     */
+    int32_t launches_tc;  /* kernel launches of one tensor-core product (FP32, BF16) of at
+                             most 64 columns, a multiple of 4 of them; with k % 4 == 0 and
+                             k <= 64 the transfer passes pack the tensor-core operands
+                             themselves, otherwise three packing launches are counted  */
 } h2_info_t;
 
 /* Build A from n points (pts: n×3 row-major doubles, host or device).  On

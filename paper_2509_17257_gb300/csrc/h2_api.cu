@@ -197,9 +197,13 @@ int h2_info(const h2_matrix* A, h2_info_t* info) {
     info->flops_per_col = 2.0 * 2.0 * (double)A->n * k + 2.0 * 2.0 * (double)(A->nc - 1) * k * k +
                           2.0 * (double)A->n_adm * k * k + 2.0 * (double)A->nnz_near + 2.0 * (double)A->n;
     info->launches = A->launches_per_product;
-    // tensor-core chain: + packing of X, x̂ and ŷ, + the scatter into Y, + zeroing of clusters without couplings
-    // (gather, pack X, forward, pack x̂, coupling, downward, pack ŷ, leaf, scatter)
-    info->launches_tc = A->tc.built ? (A->down_ptr.back() > 0 ? 9 : 8) + (A->tc.c_nzero > 0 ? 1 : 0) : 0;
+    // tensor-core chain: gather, upward pass, coupling, downward pass, leaf phase, scatter into Y, + zeroing of
+    // clusters without couplings; where the subtree-owning transfer passes do not apply (k % 4 != 0 or
+    // k > 64) also the packing of X, x̂ and ŷ
+    const bool own_passes = A->f32.Et && A->k % 4 == 0 && A->k <= 64;
+    info->launches_tc = A->tc.built ? (own_passes ? 5 : 8) + (A->down_ptr.back() > 0 ? 1 : 0) +
+                                          (A->tc.c_nzero > 0 ? 1 : 0)
+                                    : 0;
     return 0;
 }
 
