@@ -344,6 +344,22 @@ void up_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std:
     ntasks = (int32_t)task_steps.size();
 }
 
+// Lays out a work list sorted by decreasing cost for a kernel whose CTA b
+// takes positions b, b + G, b + 2G, ...: round r of G items goes to the CTAs
+// in order for even r and in reverse for odd r (the last, partial round in
+// order), so no CTA takes the largest item of every round.
+void snake_order(std::vector<TcItem>& v, int G) {
+    const size_t n = v.size();
+    if (G < 2 || n <= (size_t)G) return;
+    std::vector<TcItem> out(n);
+    for (size_t i = 0; i < n; ++i) {
+        const size_t r = i / G, j = i % G;
+        const bool full = (r + 1) * G <= n;
+        out[r * G + ((r & 1) && full ? G - 1 - j : j)] = v[i];
+    }
+    v.swap(out);
+}
+
 int cast_copy(h2_matrix* A, const double* src, void** dst, int64_t count, cudaStream_t st) {
     int rc = device_alloc(A, dst, (size_t)(count > 0 ? count : 1) * sizeof(float));
     if (rc) return rc;
@@ -662,9 +678,10 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
         if (e1 > e0) c_items.push_back(TcItem{(int32_t)c, e0, e1, NP});
         else c_zero.push_back((int32_t)c);
     }
-    // longest lists first, dealt round-robin to the CTAs
+    // longest lists first, dealt to the CTAs in snake order
     std::stable_sort(c_items.begin(), c_items.end(),
                      [](const TcItem& a, const TcItem& b) { return a.e1 - a.e0 > b.e1 - b.e0; });
+    snake_order(c_items, kTcGrid);
     // ---- leaf schedule: outputs = leaf positions; terms = V_t ŷ_t, then G_b X|_ŝ ----
     std::vector<int64_t> xkoff(NL + 1, 0);
     std::vector<int32_t> leaf_base(NL), leaf_kdim(NL);
@@ -695,6 +712,7 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     }
     std::stable_sort(l_items.begin(), l_items.end(),
                      [&](const TcItem& a, const TcItem& b) { return l_cost[a.id] > l_cost[b.id]; });
+    snake_order(l_items, kTcGrid);
     D.xk_total = xkoff[NL];
     D.c_nitems = (int)c_items.size();
     D.c_nzero = (int)c_zero.size();

@@ -142,6 +142,7 @@ struct DownStep {
     int32_t c, rd, wr, flags;
 };
 constexpr int kDownLoad = 1, kDownStore = 2;
+constexpr int kTcGrid = 152;  // CTAs of the tensor-core kernels (one per SM); their work lists are laid out for it
 constexpr int kDownMaxSteps = 192;  // steps of one task at most (the schedule keeps to it)
 
 // One step of the subtree-owning upward pass (k_up_own, h2_mm.cu): a leaf c

@@ -978,7 +978,7 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
     const float* V = (const float*)A->f32.V;
     const float* E = (const float*)A->f32.E;
 
-    const int grid_cap = 152;
+    const int grid_cap = kTcGrid;
     SyncBufs sbc = sb;
     for (int c0 = 0; c0 < m; c0 += 64) {
         const int mc = std::min(64, m - c0);

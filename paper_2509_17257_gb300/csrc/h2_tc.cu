@@ -52,7 +52,10 @@ namespace {
 
 constexpr int kMaxStages = 16;
 constexpr int kSmemBudget = 225 * 1024;  // dynamic shared memory per CTA (one CTA per SM)
-constexpr int kTcThreads = 256;
+constexpr int kSplitWarps = 4;  // KIND 1: warps 6..9 write [B; B_lo] into TMEM, one lane quadrant each
+constexpr int kASlots = 4;      // KIND 1: TMEM slots of the MMA's A operand (64 columns each, after the accumulators)
+template <int KIND>
+constexpr int tc_threads() { return KIND == 1 ? 32 * (6 + kSplitWarps) : 192; }
 constexpr int kAccCols = 64;                // output columns of one term (the matrix tile's rows)
 constexpr int kAccBufs = 4;                 // accumulator buffers: MMAs of a term overlap the epilogue of the 3 before
 constexpr int kXchBytes = 2 * 64 * 64 * 4;  // TF32 epilogue: remainder sums handed over, two items deep
@@ -87,6 +90,16 @@ __device__ __forceinline__ void mma_issue_elect(uint32_t d, uint64_t a, uint64_t
             "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(d),
             "l"(a), "l"(b), "r"(idesc), "r"(acc)
             : "memory");
+}
+// The TF32 MMA with its A operand (M = 128 rows, K = 8 columns) in TMEM at
+// column address a_tmem, lanes 0..127.
+__device__ __forceinline__ void mma_tf32_ta_elect(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                                  uint32_t acc) {
+    asm volatile(
+        "{ .reg .pred p, e; setp.ne.b32 p, %4, 0; elect.sync _|e, 0xffffffff;\n"
+        "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p; }" ::"r"(d),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
 }
 __device__ __forceinline__ void mma_commit_elect(uint64_t* bar) {
     asm volatile(
@@ -131,6 +144,24 @@ __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 64 consecutive TMEM columns of this warp's 32 lanes from registers; the
+// caller waits with tmem_wait_st before signalling the MMA.
+__device__ __forceinline__ void tmem_st64(uint32_t taddr, const uint32_t (&v)[64]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,"
+        "%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63,%64};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]), "r"(v[32]), "r"(v[33]), "r"(v[34]), "r"(v[35]), "r"(v[36]),
+        "r"(v[37]), "r"(v[38]), "r"(v[39]), "r"(v[40]), "r"(v[41]), "r"(v[42]), "r"(v[43]), "r"(v[44]), "r"(v[45]),
+        "r"(v[46]), "r"(v[47]), "r"(v[48]), "r"(v[49]), "r"(v[50]), "r"(v[51]), "r"(v[52]), "r"(v[53]), "r"(v[54]),
+        "r"(v[55]), "r"(v[56]), "r"(v[57]), "r"(v[58]), "r"(v[59]), "r"(v[60]), "r"(v[61]), "r"(v[62]), "r"(v[63])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 
 }  // namespace
@@ -219,17 +250,19 @@ __global__ void k_pack_act(const float* __restrict__ src, int64_t ld, int ids, c
 // Stage layout: [A: R rows | B: 64 rows | B_lo: 64 rows (KIND 1)], element size
 // es = 2 (KIND 0) or 4 (KIND 1), 64 contraction columns at most.
 template <int MODE, int KIND>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p) {
+__global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmParams p) {
     constexpr int ES = KIND == 0 ? 2 : 4;
     constexpr int KSTEP = KIND == 0 ? 16 : 8;  // K of one MMA instruction
     constexpr int F_FIRST = 1, F_LAST = 2, F_END = 4;
-    // TMEM columns per accumulator buffer: KIND 1 multiplies by [B; B_lo] in one
-    // N = 128 MMA, so its buffer holds A·Bᵀ in columns 0..63 and A·B_loᵀ in 64..127
-    constexpr int ACC = KIND == 1 ? 2 * kAccCols : kAccCols;
+    // TMEM: KIND 0 has kAccBufs accumulators of 64 columns.  KIND 1 has
+    // accumulators of R columns (64 or 128: 4 or 2 of them, 256 columns) and
+    // after them kASlots slots of 64 columns for the MMA's A operand [B; B_lo].
+    constexpr int TMEM_COLS = KIND == 1 ? 512 : kAccBufs * kAccCols;
+    constexpr int A_BASE = 256;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full_bar[kMaxStages], split_bar[kMaxStages], empty_bar[kMaxStages];
-    __shared__ __align__(8) uint64_t accf_bar[kAccBufs], acce_bar[kAccBufs], drain_bar;
+    __shared__ __align__(8) uint64_t accf_bar[kAccBufs], acce_bar[kAccBufs], drain_bar, aempty_bar[kASlots];
     __shared__ uint32_t tmem_slot;
     __shared__ int stage_kp[kMaxStages], stage_np[kMaxStages], stage_fl[kMaxStages];
     __shared__ int abort_shared;
@@ -239,13 +272,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
     const int M = R <= 64 ? 64 : 128;
     const int nst = p.nstages;
     const int a_bytes = p.a_stage_bytes, b_bytes = 64 * 64 * ES;
-    const int stage_bytes = a_bytes + b_bytes * (KIND == 1 ? 2 : 1);
+    const int stage_bytes = a_bytes + b_bytes;
     const int G = gridDim.x;
+    const int acc_cols = KIND == 1 ? (R <= 64 ? 64 : 128) : kAccCols;  // TMEM columns of one accumulator
+    const int nacc = KIND == 1 ? 256 / acc_cols : kAccBufs;             // accumulator buffers
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < nst; ++s) {
             mbar_init(&full_bar[s], 1);
-            mbar_init(&split_bar[s], 2);
+            mbar_init(&split_bar[s], kSplitWarps);
             mbar_init(&empty_bar[s], 1);
         }
         for (int b = 0; b < kAccBufs; ++b) {
@@ -253,12 +288,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             mbar_init(&acce_bar[b], 4);  // one arrival per epilogue warp
         }
         mbar_init(&drain_bar, 1);
+        for (int a = 0; a < kASlots; ++a) mbar_init(&aempty_bar[a], 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(kAccBufs * ACC)
+                     "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -367,39 +403,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             // every term accumulates from zero in its own TMEM buffer; the epilogue
             // adds the terms of an item in FP32 registers (round to nearest), so
             // the tensor-core accumulator never sums more than one term's K steps
-            const int acc = it % kAccBufs;
-            if (!__any_sync(0xffffffffu, mbar_wait(&acce_bar[acc], ((it / kAccBufs) & 1) ^ 1))) {
+            const int acc = it % nacc;
+            if (!__any_sync(0xffffffffu, mbar_wait(&acce_bar[acc], ((it / nacc) & 1) ^ 1))) {
                 abort_flag = 1;
                 if (lane == 0) atomicExch(p.err, 3);
                 break;
             }
             tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)(acc * ACC);
+            const uint32_t d = tmem + (uint32_t)(acc * acc_cols);
             const int kp = stage_kp[stage];
             const uint32_t sA = smem_u32(smem + stage * stage_bytes);
             const uint32_t sB = sA + a_bytes;
             const uint32_t sbo = (uint32_t)(kp * ES / 16) * 128;
-            // KIND 0: D[r, n] = act · matᵀ (M = activation rows, N = the tile's rows).
-            // KIND 1: D[n, r] = [mat; mat_lo] · actᵀ: M = 128 rows, the tile (rows
-            // 0..63) and its TF32 remainder (rows 64..127, which the splitter writes
-            // 64·kp elements after the tile's start), N = R activation rows.  The
-            // MMA time grows with N, not with M up to 128, so the split costs no
-            // extra instructions.  Rows np..63 of either part hold stale data whose
-            // TMEM lanes the epilogue ignores.
+            // KIND 0: D[r, n] = act · matᵀ (M = activation rows, N = the tile's rows),
+            // both operands in shared memory.
+            // KIND 1: D[n, r] = [mat; mat_lo] · actᵀ: M = 128, the tile (rows 0..63)
+            // and its TF32 remainder (rows 64..127), which the splitter warps have
+            // put into TMEM slot `as`; N = R activation rows from shared memory.
+            // The MMA time grows with N, not with M up to 128, so the remainder
+            // costs no extra instructions.  Rows np..63 of either part hold stale
+            // data whose TMEM lanes the epilogue ignores.
             const uint32_t idesc = KIND == 1 ? idesc_for<KIND>(128, R) : idesc_for<KIND>(M, stage_np[stage]);
             // descriptors of K step kk: the start address field moves by 256 bytes
-            // (two core matrices along K), i.e. 16 in its 16-byte units
-            const uint64_t ad0 = smem_desc(KIND == 1 ? sB : sA, 128, sbo);
-            const uint64_t bd0 = smem_desc(KIND == 1 ? sA : sB, 128, sbo);
+            // (two core matrices along K), i.e. 16 in its 16-byte units; a TMEM
+            // operand moves by KSTEP columns
+            const uint64_t ad0 = smem_desc(sA, 128, sbo);
+            const uint64_t bd0 = smem_desc(sB, 128, sbo);
+            const int as = it % kASlots;
+            const uint32_t a_tmem = tmem + (uint32_t)(A_BASE + 64 * as);
             const int nk = kp / KSTEP;
 #pragma unroll
             for (int kk = 0; kk < 64 / KSTEP; ++kk) {
                 if (kk >= nk) break;
                 const uint64_t off = (uint64_t)(kk * 16);
-                mma_issue_elect<KIND>(d, ad0 + off, bd0 + off, idesc, kk == 0 ? 0u : 1u);
+                if (KIND == 1) mma_tf32_ta_elect(d, a_tmem + (uint32_t)(kk * KSTEP), ad0 + off, idesc, kk == 0 ? 0u : 1u);
+                else mma_issue_elect<KIND>(d, ad0 + off, bd0 + off, idesc, kk == 0 ? 0u : 1u);
             }
             issued = true;
             mma_commit_elect(&empty_bar[stage]);
+            if (KIND == 1) mma_commit_elect(&aempty_bar[as]);
             mma_commit_elect(&accf_bar[acc]);
             ++it;
             if (++stage == nst) { stage = 0; phase ^= 1; }
@@ -445,31 +487,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             for (int j = 0; j < kAccCols; ++j) sum[j] = 0.f;
             bool failed = false;
             for (int term = 0; term < nterms; ++term, ++it) {
-                const int acc = it % kAccBufs;
-                if (!__any_sync(0xffffffffu, mbar_wait(&accf_bar[acc], (it / kAccBufs) & 1))) {
+                const int acc = it % nacc;
+                if (!__any_sync(0xffffffffu, mbar_wait(&accf_bar[acc], (it / nacc) & 1))) {
                     failed = true;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * ACC);
-                uint32_t r0[32], r1[32], r2[32], r3[32];
-                tmem_ld32_async(ta, r0);
-                tmem_ld32_async(ta + 32, r1);
-                if (wide) {
-                    tmem_ld32_async(ta + 64, r2);
-                    tmem_ld32_async(ta + 96, r3);
-                }
-                tmem_wait_ld();
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * acc_cols);
+                // 64 columns per read (two loads in flight, one wait); R > 64 takes two
+                uint32_t r0[32], r1[32];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    sum[j] += __uint_as_float(r0[2 * j]) + __uint_as_float(r0[2 * j + 1]);
-                    sum[16 + j] += __uint_as_float(r1[2 * j]) + __uint_as_float(r1[2 * j + 1]);
-                }
-                if (wide) {
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && !wide) break;
+                    tmem_ld32_async(ta + 64 * h, r0);
+                    tmem_ld32_async(ta + 64 * h + 32, r1);
+                    tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        sum[32 + j] += __uint_as_float(r2[2 * j]) + __uint_as_float(r2[2 * j + 1]);
-                        sum[48 + j] += __uint_as_float(r3[2 * j]) + __uint_as_float(r3[2 * j + 1]);
+                        sum[32 * h + j] += __uint_as_float(r0[2 * j]) + __uint_as_float(r0[2 * j + 1]);
+                        sum[32 * h + 16 + j] += __uint_as_float(r1[2 * j]) + __uint_as_float(r1[2 * j + 1]);
                     }
                 }
                 tc_fence_before();
@@ -561,7 +597,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
                 tc_fence_after();
                 // both halves of the accumulator in flight, one wait; the row pair
                 // (2i, 2i + 1) is adjacent lanes, added by one shuffle
-                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * ACC);
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * acc_cols);
                 uint32_t r0[32], r1[32];
                 tmem_ld32_async(ta, r0);
                 if (np > 32) tmem_ld32_async(ta + 32, r1);
@@ -607,37 +643,49 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
             cur_nt = nxt_nt;
         }
     } else if (KIND == 1) {
-        // ---------------- splitter (warps 6, 7): B_lo = B - tf32(B) ----------------
-        const int sw = warp - 6;  // 0 or 1
-        int stage = 0;
+        // ---------------- splitter (warps 6..9): [B; B_lo] into TMEM ----------------
+        // Warp w owns TMEM lanes 32q..32q+31 (q = w mod 4): row n = 32(q & 1) + lane
+        // of the tile B (q = 0, 1) or of its remainder B_lo = B - tf32(B) (q = 2, 3).
+        // Each thread reads its row (kp values, 16 bytes per core matrix) from the
+        // stage and writes it to TMEM slot `as` of the MMA's A operand.
+        const int q = warp & 3;
+        const int n = 32 * (q & 1) + lane;
+        const bool lo_part = q >= 2;
+        int stage = 0, sit = 0;
         uint32_t phase = 0;
         while (true) {
-            const bool ok = __any_sync(0xffffffffu, mbar_wait(&full_bar[stage], phase));
-            if (!ok) {
+            if (!__any_sync(0xffffffffu, mbar_wait(&full_bar[stage], phase))) {
                 if (lane == 0) atomicExch(p.err, 7);
                 abort_flag = 1;
                 break;
             }
             const int fl = stage_fl[stage];
             if (!(fl & F_END)) {
-                const int n4 = stage_np[stage] * stage_kp[stage] / 4;  // float4 count of the B tile
-                const float4* __restrict__ src = (const float4*)(smem + stage * stage_bytes + a_bytes);
-                // B_lo goes where rows 64..127 of the same core-matrix layout start, so
-                // one N = 128 MMA reads [B; B_lo] (8-row groups are kp·4/16 core
-                // matrices apart)
-                float4* __restrict__ dst =
-                    (float4*)(smem + stage * stage_bytes + a_bytes + 64 * stage_kp[stage] * 4);
-                // four loads in flight per thread, then the four stores
-                int x = sw * 32 + lane;
-                for (; x + 3 * 64 < n4; x += 4 * 64) {
-                    float4 v[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) v[u] = src[x + 64 * u];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) dst[x + 64 * u] = tf32_lo(v[u]);
+                const int as = sit % kASlots;
+                // the slot is free once the MMAs of term sit - kASlots have completed
+                if (!__any_sync(0xffffffffu, mbar_wait(&aempty_bar[as], ((sit / kASlots) & 1) ^ 1))) {
+                    if (lane == 0) atomicExch(p.err, 8);
+                    abort_flag = 1;
+                    break;
                 }
-                for (; x < n4; x += 64) dst[x] = tf32_lo(src[x]);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tc_fence_after();
+                const int kp = stage_kp[stage];
+                const uint8_t* row = smem + stage * stage_bytes + a_bytes + (n >> 3) * (kp >> 2) * 128 + (n & 7) * 16;
+                uint32_t v[64];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (4 * c < kp) x = *(const float4*)(row + c * 128);
+                    if (lo_part) x = tf32_lo(x);
+                    v[4 * c] = __float_as_uint(x.x);
+                    v[4 * c + 1] = __float_as_uint(x.y);
+                    v[4 * c + 2] = __float_as_uint(x.z);
+                    v[4 * c + 3] = __float_as_uint(x.w);
+                }
+                tmem_st64(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(A_BASE + 64 * as), v);
+                tmem_wait_st();
+                tc_fence_before();
+                ++sit;
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&split_bar[stage]);
@@ -649,7 +697,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmParams p)
     __syncthreads();
     tc_fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAccBufs * ACC) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
 // Zero ŷ of clusters whose coupling list is empty.
@@ -662,18 +710,19 @@ __global__ void k_zero_clusters(const int32_t* __restrict__ ids, int count, floa
 }
 
 // Stage geometry for R activation rows and element size es: A holds R rows,
-// B (and B_lo for TF32) 64 rows, all with up to 64 contraction columns.  The
-// TF32 kernel keeps its epilogue exchange tile (kXchBytes) after the stages.
+// B 64 rows, both with up to 64 contraction columns.  The TF32 kernel keeps
+// its epilogue exchange tile (kXchBytes) after the stages (its B_lo lives in
+// TMEM).
 void tc_stage_geometry(int R, int es, int* a_bytes, int* stage_bytes, int* nstages) {
     const int rows = R <= 64 ? 64 : 128;  // the BF16 MMA reads M = 64 or 128 activation rows
     *a_bytes = rows * 64 * es;
-    *stage_bytes = *a_bytes + 64 * 64 * es * (es == 4 ? 2 : 1);
+    *stage_bytes = *a_bytes + 64 * 64 * es;
     *nstages = std::min(kMaxStages, (kSmemBudget - 1024 - (es == 4 ? kXchBytes : 0)) / *stage_bytes);
 }
 
 template <int MODE, int KIND>
 int launch_one(const TcGemmParams& p, int grid, int smem, cudaStream_t st) {
-    k_tc_gemm<MODE, KIND><<<grid, kTcThreads, smem, st>>>(p);
+    k_tc_gemm<MODE, KIND><<<grid, tc_threads<KIND>(), smem, st>>>(p);
     H2_LAUNCH_CHECK();
     return 0;
 }
