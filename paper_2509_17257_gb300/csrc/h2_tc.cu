@@ -54,8 +54,12 @@ constexpr int kMaxStages = 16;
 constexpr int kSmemBudget = 225 * 1024;  // dynamic shared memory per CTA (one CTA per SM)
 constexpr int kSplitWarps = 4;  // KIND 1: warps 6..9 write [B; B_lo] into TMEM, one lane quadrant each
 constexpr int kASlots = 4;      // KIND 1: TMEM slots of the MMA's A operand (64 columns each, after the accumulators)
+// warps: 0 producer, 1 and kIssuer2 MMA issuers (even and odd terms), 2..5
+// epilogue, KIND 1: 6..9 splitter
 template <int KIND>
-constexpr int tc_threads() { return KIND == 1 ? 32 * (6 + kSplitWarps) : 192; }
+__host__ __device__ constexpr int tc_issuer2() { return KIND == 1 ? 6 + kSplitWarps : 6; }
+template <int KIND>
+__host__ __device__ constexpr int tc_threads() { return 32 * (tc_issuer2<KIND>() + 1); }
 constexpr int kAccCols = 64;                // output columns of one term (the matrix tile's rows)
 constexpr int kAccBufs = 4;                 // accumulator buffers: MMAs of a term overlap the epilogue of the 3 before
 constexpr int kXchBytes = 2 * 64 * 64 * 4;  // TF32 epilogue: remainder sums handed over, two items deep
@@ -262,7 +266,8 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full_bar[kMaxStages], split_bar[kMaxStages], empty_bar[kMaxStages];
-    __shared__ __align__(8) uint64_t accf_bar[kAccBufs], acce_bar[kAccBufs], drain_bar, aempty_bar[kASlots];
+    __shared__ __align__(8) uint64_t accf_bar[kAccBufs], acce_bar[kAccBufs], drain_bar[2], aempty_bar[kASlots];
+    __shared__ int s_total;  // terms of this CTA
     __shared__ uint32_t tmem_slot;
     __shared__ int stage_kp[kMaxStages], stage_np[kMaxStages], stage_fl[kMaxStages];
     __shared__ int abort_shared;
@@ -287,10 +292,19 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
             mbar_init(&accf_bar[b], 1);
             mbar_init(&acce_bar[b], 4);  // one arrival per epilogue warp
         }
-        mbar_init(&drain_bar, 1);
+        mbar_init(&drain_bar[0], 1);
+        mbar_init(&drain_bar[1], 1);
         for (int a = 0; a < kASlots; ++a) mbar_init(&aempty_bar[a], 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        // the CTA's term count: the two issuers split the terms by parity and stop there
+        int tot = 0;
+        for (int w = blockIdx.x + lane * G; w < p.n_items; w += 32 * G) tot += p.items[w].e1 - p.items[w].e0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        if (lane == 0) s_total = tot;
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -384,22 +398,25 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 if ((pend_mask >> s2) & 1u)
                     if (!mbar_wait(&full_bar[s2], (pend_par >> s2) & 1u)) atomicExch(p.err, 2);
         }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer: driven by the stage metadata ----------------
-        // The whole warp runs the loop (its waits and descriptors are warp-uniform);
-        // elect.sync hands each MMA and commit to one lane.
-        int stage = 0;
-        uint32_t phase = 0;
-        int it = 0;
+    } else if (warp == 1 || warp == tc_issuer2<KIND>()) {
+        // ---------------- MMA issuers: driven by the stage metadata ----------------
+        // Two warps take the terms by parity (term t uses stage t mod nst,
+        // accumulator t mod nacc and A slot t mod kASlots; nacc and kASlots are
+        // even, so each accumulator and slot stays with one issuer and its
+        // barriers complete in order), so one warp's waits overlap the other's
+        // MMAs.  Each converged warp runs its loop (waits and descriptors are
+        // warp-uniform); elect.sync hands each MMA and commit to one lane.
+        const int j = warp == 1 ? 0 : 1;
+        const int T = s_total;
         bool issued = false;
-        while (true) {
+        for (int it = j; it < T; it += 2) {
+            const int stage = it % nst;
+            const uint32_t phase = (uint32_t)(it / nst) & 1u;
             if (!__any_sync(0xffffffffu, mbar_wait(KIND == 1 ? &split_bar[stage] : &full_bar[stage], phase))) {
                 abort_flag = 1;
                 if (lane == 0) atomicExch(p.err, 4);
                 break;
             }
-            const int fl = stage_fl[stage];
-            if (fl & F_END) break;
             // every term accumulates from zero in its own TMEM buffer; the epilogue
             // adds the terms of an item in FP32 registers (round to nearest), so
             // the tensor-core accumulator never sums more than one term's K steps
@@ -443,12 +460,10 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
             mma_commit_elect(&empty_bar[stage]);
             if (KIND == 1) mma_commit_elect(&aempty_bar[as]);
             mma_commit_elect(&accf_bar[acc]);
-            ++it;
-            if (++stage == nst) { stage = 0; phase ^= 1; }
         }
         if (issued) {
-            mma_commit_elect(&drain_bar);
-            if (!__any_sync(0xffffffffu, mbar_wait(&drain_bar, 0)) && lane == 0) atomicExch(p.err, 5);
+            mma_commit_elect(&drain_bar[j]);
+            if (!__any_sync(0xffffffffu, mbar_wait(&drain_bar[j], 0)) && lane == 0) atomicExch(p.err, 5);
         }
     } else if (warp < 6 && KIND == 1) {
         // ---------------- epilogue, KIND 1 (warps 2..5, TMEM lane quadrant warp % 4) ----------------
@@ -642,7 +657,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
             cur_off = nxt_off;
             cur_nt = nxt_nt;
         }
-    } else if (KIND == 1) {
+    } else if (KIND == 1 && warp < 6 + kSplitWarps) {
         // ---------------- splitter (warps 6..9): [B; B_lo] into TMEM ----------------
         // Warp w owns TMEM lanes 32q..32q+31 (q = w mod 4): row n = 32(q & 1) + lane
         // of the tile B (q = 0, 1) or of its remainder B_lo = B - tf32(B) (q = 2, 3).
