@@ -42,6 +42,9 @@ FALLBACK_HBM_GBS = 6800.0
 SM_COUNT = 152
 FP32_FMA_PER_CLK_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_tc_gemm<0,1> launch (FP32 coupling)
+# on precision_n65536 (732.272 MB + 20.379 MB); valid for the kernel as of that capture only
+TC_F32_COUPLING_DRAM_BYTES = 752651008
 
 
 def _peaks():
@@ -274,8 +277,13 @@ def run_ours(args):
                 "kernel": "k_coupling", "peak_source": alu_note}
     else:
         achieved = coup_bytes / (coup_ms * 1e-3) / 1e9
+        # DRAM bytes (read + write) of one launch of the coupling kernel on this workload,
+        # from the ncu capture summarised in profiles/coupling_and_transfer_kernels_n65536_full.md;
+        # only for the FP32 tensor-core kernel and the workload it was taken on
+        measured = TC_F32_COUPLING_DRAM_BYTES if (tensor_path and dtype == "f32" and
+                                                  args.workload == WORKLOAD) else None
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                "frac": round(achieved / hbm_peak, 4), "traffic": measured,
                 "kernel": "k_tc_gemm<0,1> (coupling, split TF32)" if tensor_path else "k_coupling",
                 "peak_source": f"{peak_kind} hbm_gbs"}
     roof["algorithmic_bytes_per_launch"] = int(coup_bytes)
