@@ -249,9 +249,10 @@ void down_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, st
 // Schedule of the subtree-owning upward pass.  The tree is cut at level Lu as
 // for the downward pass; a task evaluates the subtree of its cut cluster t in
 // post-order (sons before their father), keeping each x̂ in a shared-memory
-// stack entry until its father has used it, so no step waits for another
-// CTA.  Entries come from a free list; at least three exist, for the climb
-// above the cut (own x̂, the brother's x̂, the father's).  Lu is the shallowest
+// stack entry until its father has used it (the father's x̂ then takes its
+// first son's entry), so no step waits for another CTA.  Entries come from a
+// free list (a subtree of height h needs h + 1); at least three exist, for the
+// climb above the cut (own x̂, the brother's contribution, the father's x̂).  Lu is the shallowest
 // level with at least `target` tasks whose step lists fit kUpMaxSteps and
 // whose stacks fit kUpMaxEntries.
 void up_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std::vector<UpStep>& steps,
@@ -301,13 +302,13 @@ void up_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std:
                 v.push_back(UpStep{c, -1, leaf_pos[c], e});
                 done.push_back(e);
             } else {
+                // the father's x̂ replaces its first son's (the kernel waits for
+                // every read of both sons before it writes)
                 const int32_t e1 = done.back(); done.pop_back();
                 const int32_t e0 = done.back(); done.pop_back();
-                const int32_t e = take();
-                v.push_back(UpStep{c, e0, e1, e});
-                give(e0);
+                v.push_back(UpStep{c, e0, e1, e0});
                 give(e1);
-                done.push_back(e);
+                done.push_back(e0);
             }
             st.pop_back();
         }
@@ -499,7 +500,10 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
         UP(A->d_dn_task_ptr, task_ptr);
         UP(A->d_dn_steps, dsteps);
         std::vector<UpStep> usteps;
-        up_schedule(T, 256, task_ptr, usteps, A->up_ntasks, A->up_entries);
+        // about 1.7 tasks per CTA slot (two per SM): the longest subtree, walked
+        // by one CTA, bounds the task phase, so the cut sits one level deeper
+        // than for the downward pass
+        up_schedule(T, 400, task_ptr, usteps, A->up_ntasks, A->up_entries);
         UP(A->d_up_task_ptr, task_ptr);
         UP(A->d_up_steps, usteps);
     }

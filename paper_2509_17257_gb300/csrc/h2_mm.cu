@@ -600,6 +600,7 @@ __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ 
             } else {
                 contract44(acc, slot(b, 0), k, ent(u.rd0), m, k, tx, ty);
                 contract44(acc, slot(b, 1), k, ent(u.rd1), m, k, tx, ty);
+                __syncthreads();  // x̂ of the father goes into its first son's entry
             }
             put(acc, u.wr, u.c);
             cur = u.wr;
