@@ -48,7 +48,11 @@ extern "C" {
 typedef enum h2_dtype {
     H2_F64 = 0,  /* all arithmetic in FP64 */
     H2_F32 = 1,  /* FP32 matrices and coefficients, FP32 accumulation */
-    H2_BF16 = 2  /* BF16 matrices on the tensor cores, FP32 accumulation */
+    H2_BF16 = 2, /* BF16 matrices on the tensor cores, FP32 accumulation */
+    H2_F32_MF = 3 /* as H2_F32 on the tensor cores, but the coupling matrices are not read:
+                     the coupling kernel evaluates S_b[ν, μ] = g(ξ_{t,ν}, ξ_{s,μ}) (Eq. (h2_admissible))
+                     in FP32 from the Chebyshev nodes.  A·X only; H2_E_UNSUPPORTED without the
+                     TF32 tiles or after h2_coupling_set (the couplings are then no longer g's) */
 } h2_dtype;
 
 /* ---- construction ------------------------------------------------------ */

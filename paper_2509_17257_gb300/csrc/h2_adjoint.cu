@@ -118,6 +118,7 @@ int h2_coupling_set(h2_matrix* A, const double* S, void* stream) {
     const int64_t count = A->n_adm * A->k * A->k;
     if (count == 0) return 0;
     H2_CUDA_TRY(cudaMemcpyAsync(A->f64.S, S, (size_t)count * sizeof(double), cudaMemcpyDefault, st));
+    A->s_replaced = true;  // the matrix-free product (H2_F32_MF) no longer applies
     int rc = 0;
     if (A->f32.built && A->f32.S) {
         if ((rc = cast_f32((const double*)A->f64.S, (float*)A->f32.S, count, st))) return rc;

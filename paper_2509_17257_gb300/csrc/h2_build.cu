@@ -115,6 +115,23 @@ __global__ void k_coupling_entries(const int32_t* __restrict__ adm_row, const in
     }
 }
 
+// FP32 tensor nodes for the matrix-free coupling: nodes4[c·KP + ν] = ξ_{c,ν}
+// (x, y, z, 0) for ν < k, zero for k <= ν < KP.
+__global__ void k_nodes4(const double* __restrict__ nodes, int64_t nc, int q, int KP, float4* __restrict__ nodes4) {
+    const int k = q * q * q;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc * KP; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / KP;
+        const int nu = (int)(e % KP);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (nu < k) {
+            double x[3];
+            tensor_node(nodes + (size_t)c * 3 * q, q, nu, x);
+            v = make_float4((float)x[0], (float)x[1], (float)x[2], 0.f);
+        }
+        nodes4[e] = v;
+    }
+}
+
 // G_b[i, j] = g(x_i, x_j) for inadmissible blocks.
 __global__ void k_near_entries(const int32_t* __restrict__ near_row, const int32_t* __restrict__ near_col,
                                const int64_t* __restrict__ near_off, int64_t n_near,
@@ -670,6 +687,12 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     }
     D.has_bf16 = bf16;
     D.has_tf32 = tf32;
+    if (tf32) {
+        if ((rc = device_alloc(A, (void**)&D.nodes4, (size_t)nc * KP * sizeof(float4)))) return rc;
+        const unsigned g = (unsigned)std::min<int64_t>((nc * KP + 255) / 256, 152 * 16);
+        k_nodes4<<<g, 256, 0, st>>>(A->d_nodes, nc, A->q, KP, D.nodes4);
+        H2_LAUNCH_CHECK();
+    }
 
     // ---- coupling schedule: outputs = clusters with at least one admissible block ----
     std::vector<int32_t> c_zero;

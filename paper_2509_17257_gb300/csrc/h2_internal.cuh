@@ -101,6 +101,11 @@ struct TcGemmParams {
     const int32_t* cl_size;
     int* err;
     int a_stage_bytes, nstages;  // filled by launch_tc_gemm
+    // matrix-free coupling (mode 2): Chebyshev nodes [cluster][KP] (x, y, z, 0) and
+    // the kernel's 1/length; S_b[ν, μ] = exp(-|ξ_{t,ν} - ξ_{s,μ}| / length) for ν, μ < k
+    const float4* nodes;
+    float inv_len;
+    int KP;
 };
 
 // BF16 tensor-core copy of the matrix data and the schedules of its kernels.
@@ -109,6 +114,7 @@ struct TcData {
     int KP = 0, NP = 0;
     uint8_t* mat = nullptr;    // BF16 core-matrix tiles: S (list order), V (leaf order), G (near order)
     uint8_t* mat32 = nullptr;  // the same tiles in FP32 (offsets ×2), for the 3xTF32 product
+    float4* nodes4 = nullptr;  // [n_clusters][KP] Chebyshev tensor nodes (x, y, z, 0), zero past k (matrix-free coupling)
     int64_t bytes = 0;
     bool has_bf16 = false, has_tf32 = false;
     // coupling: outputs are clusters with at least one admissible block
@@ -232,7 +238,8 @@ struct h2_matrix {
     int* sync_flag = nullptr;      // [nc × sync_tiles]
     unsigned* sync_claim = nullptr;// [sync_tiles]
     int64_t sync_tiles = 0;
-    bool force_simt = false;  // H2_FORCE_SIMT=1 at build: FP32 product on the CUDA cores only
+    bool force_simt = false;
+    bool s_replaced = false;  // h2_coupling_set was called: S_b are no longer g's values  // H2_FORCE_SIMT=1 at build: FP32 product on the CUDA cores only
     // block-Jacobi preconditioner (h2_precond.cu): (G_(t,t) + σI)⁻¹ per leaf, built on first use
     double* bj_inv = nullptr;     // concatenated n_t×n_t inverses, leaf order
     int64_t* bj_off = nullptr;    // [n_leaves] element offset of leaf t's inverse

@@ -970,6 +970,9 @@ int ensure_workspace(h2_matrix* A, size_t bytes, cudaStream_t st) {
 template <int CN>
 int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int m,
                  cudaStream_t st, bool overwrite, const SyncBufs& sb) {
+    // kind 2: the TF32 product with the matrix-free coupling (tensor-core kernel mode 2)
+    const bool mf = kind == 2;
+    if (mf) kind = 1;
     const int es = kind == 0 ? 2 : 4;
     constexpr int RM = 4, MT = 16 * RM, NT = 16 * CN;
     const TcData& D = A->tc;
@@ -1043,8 +1046,11 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         cp.k = k;
         cp.ldc = mc;
         cp.err = A->err_dev;
+        cp.nodes = D.nodes4;
+        cp.inv_len = (float)(1.0 / A->length);
+        cp.KP = KP;
         marks.kernel_begin();
-        if (cp.n_items > 0 && (rc = launch_tc_gemm(0, kind, cp, std::min(cp.n_items, grid_cap), st))) return rc;
+        if (cp.n_items > 0 && (rc = launch_tc_gemm(mf ? 2 : 0, kind, cp, std::min(cp.n_items, grid_cap), st))) return rc;
         marks.kernel_end();
         marks.mark();
         bool leaf_y_packed = false;
@@ -1176,6 +1182,18 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
         return dispatch_cn<float>(A, A->f32, alpha, X, ldx, Y, ldy, (int)m, st, transposed, overwrite,
                                   (float*)base, (float*)(base + bXp), (float*)(base + bXp + bC), sb);
     }
+    if (dtype == H2_F32_MF) {
+        if (!A->tc.has_tf32 || !A->tc.nodes4 || A->force_simt) {
+            set_error("matrix-free product: TF32 tiles not built (add 1<<H2_F32 to params->precisions)");
+            return H2_E_UNSUPPORTED;
+        }
+        if (transposed) { set_error("the matrix-free product supports A·X only"); return H2_E_UNSUPPORTED; }
+        if (A->s_replaced) {
+            set_error("matrix-free product: the coupling matrices were replaced (h2_coupling_set), they are no longer g's values");
+            return H2_E_UNSUPPORTED;
+        }
+        return dispatch_tc(A, 2, alpha, X, ldx, Y, ldy, m, st, overwrite, sb);
+    }
     if (dtype == H2_BF16) {
         if (!A->tc.has_bf16) { set_error("BF16 copy not built (add 1<<H2_BF16 to params->precisions)"); return H2_E_UNSUPPORTED; }
         if (transposed) { set_error("the BF16 product supports A·X only (use H2_F32 or H2_F64 for Aᵀ)"); return H2_E_UNSUPPORTED; }
@@ -1191,7 +1209,7 @@ int product_prepare(h2_matrix* A, int64_t m, int32_t dtype, cudaStream_t st) {
     const int64_t n = A->n, nc = A->nc;
     const int k = A->k;
     size_t need = 0;
-    const bool tc = (dtype == H2_BF16) || (dtype == H2_F32 && A->tc.has_tf32 && !A->force_simt);
+    const bool tc = (dtype == H2_BF16) || ((dtype == H2_F32 || dtype == H2_F32_MF) && A->tc.has_tf32 && !A->force_simt);
     if (tc) {
         const TcData& D = A->tc;
         const int es = dtype == H2_BF16 ? 2 : 4;
@@ -1264,7 +1282,10 @@ int matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, 
            int32_t dtype, cudaStream_t st, bool transposed) {
     if (!A || (!X && m > 0) || (!Y && m > 0)) { set_error("null argument"); return H2_E_BADARG; }
     if (m < 0 || ldx < m || ldy < m || m > (int64_t)1 << 20) { set_error("bad m / leading dimension"); return H2_E_BADARG; }
-    if (dtype != H2_F64 && dtype != H2_F32 && dtype != H2_BF16) { set_error("bad dtype"); return H2_E_BADARG; }
+    if (dtype != H2_F64 && dtype != H2_F32 && dtype != H2_BF16 && dtype != H2_F32_MF) {
+        set_error("bad dtype");
+        return H2_E_BADARG;
+    }
     if (m == 0) return 0;
     const bool dx = is_device_pointer(X), dy = is_device_pointer(Y);
     if (dx && dy) return matmul_device(A, alpha, X, ldx, Y, ldy, m, dtype, st, transposed, false);

@@ -253,8 +253,13 @@ __global__ void k_pack_act(const float* __restrict__ src, int64_t ld, int ids, c
 //   D = x·tf32(S) + x·(S - tf32(S)) with both parts of x reaches FP32 accuracy.
 // Stage layout: [A: R rows | B: 64 rows | B_lo: 64 rows (KIND 1)], element size
 // es = 2 (KIND 0) or 4 (KIND 1), 64 contraction columns at most.
+// MODE 0: coupling (outputs ŷ_t); MODE 1: leaf phase (outputs Z); MODE 2 (KIND 1
+// only): coupling without the stored S_b, whose rows the splitter warps evaluate
+// from the Chebyshev nodes (Eq. (h2_admissible)): only the activation tile is
+// copied.
 template <int MODE, int KIND>
 __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmParams p) {
+    constexpr bool MF = MODE == 2;
     constexpr int ES = KIND == 0 ? 2 : 4;
     constexpr int KSTEP = KIND == 0 ? 16 : 8;  // K of one MMA instruction
     constexpr int F_FIRST = 1, F_LAST = 2, F_END = 4;
@@ -270,6 +275,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
     __shared__ int s_total;  // terms of this CTA
     __shared__ uint32_t tmem_slot;
     __shared__ int stage_kp[kMaxStages], stage_np[kMaxStages], stage_fl[kMaxStages];
+    __shared__ int stage_t[kMaxStages], stage_s[kMaxStages];  // MODE 2: target and source cluster
     __shared__ int abort_shared;
     volatile int& abort_flag = abort_shared;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -361,9 +367,17 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                             stage_kp[stage] = kpj;
                             stage_np[stage] = cur.np;
                             stage_fl[stage] = (base + j == 0 ? F_FIRST : 0) | (base + j == nterms - 1 ? F_LAST : 0);
-                            mbar_expect_tx(&full_bar[stage], ab + bb);
-                            bulk_g2s(sA, (asj ? p.act1 : p.act0) + aj, ab, &full_bar[stage]);
-                            bulk_g2s(sB, p.bmat + bj * (ES / 2), bb, &full_bar[stage]);
+                            if (MF) {
+                                // the source cluster: the activation rows of cluster s start at s·KP
+                                stage_t[stage] = cur.id;
+                                stage_s[stage] = (int)(aj / ((int64_t)R * ES) / p.KP);
+                                mbar_expect_tx(&full_bar[stage], ab);
+                                bulk_g2s(sA, (asj ? p.act1 : p.act0) + aj, ab, &full_bar[stage]);
+                            } else {
+                                mbar_expect_tx(&full_bar[stage], ab + bb);
+                                bulk_g2s(sA, (asj ? p.act1 : p.act0) + aj, ab, &full_bar[stage]);
+                                bulk_g2s(sB, p.bmat + bj * (ES / 2), bb, &full_bar[stage]);
+                            }
                             pend_mask |= 1u << stage;
                             pend_par = (pend_par & ~(1u << stage)) | (phase << stage);
                         }
@@ -545,7 +559,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 for (int i = 0; i < kAccCols; ++i)
                     if (i < p.mc) sum[i] += xb[i * 64 + n];
                 float* out = nullptr;
-                if (MODE == 0) {
+                if (MODE != 1) {
                     if (n < np && n < p.k) out = p.yhat + ((int64_t)id * p.k + n) * p.ldc;
                 } else {
                     // Z in cluster order; the scatter into Y (with α, σX) is a separate
@@ -639,7 +653,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 break;
             }
             if (writer) {
-                if (MODE == 0) {
+                if (MODE != 1) {
                     float* out = p.yhat + (int64_t)id * p.k * p.ldc;
 #pragma unroll
                     for (int j = 0; j < kAccCols; ++j)
@@ -685,17 +699,37 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 }
                 tc_fence_after();
                 const int kp = stage_kp[stage];
-                const uint8_t* row = smem + stage * stage_bytes + a_bytes + (n >> 3) * (kp >> 2) * 128 + (n & 7) * 16;
                 uint32_t v[64];
+                if (MF) {
+                    // row n of S_b: g(ξ_{t,n}, ξ_{s,μ}) = exp(-|ξ_{t,n} - ξ_{s,μ}| / length) for
+                    // n, μ < k, zero in the padding; every lane of the warp reads the same ξ_{s,μ}
+                    const bool rv = n < p.k;
+                    const float4 xt = p.nodes[(int64_t)stage_t[stage] * p.KP + (rv ? n : 0)];
+                    const float4* xs = p.nodes + (int64_t)stage_s[stage] * p.KP;
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (4 * c < kp) x = *(const float4*)(row + c * 128);
-                    if (lo_part) x = tf32_lo(x);
-                    v[4 * c] = __float_as_uint(x.x);
-                    v[4 * c + 1] = __float_as_uint(x.y);
-                    v[4 * c + 2] = __float_as_uint(x.z);
-                    v[4 * c + 3] = __float_as_uint(x.w);
+                    for (int mu = 0; mu < 64; ++mu) {
+                        float g = 0.f;
+                        if (mu < kp) {
+                            const float4 y = xs[mu];
+                            const float d0 = xt.x - y.x, d1 = xt.y - y.y, d2 = xt.z - y.z;
+                            g = (rv && mu < p.k) ? __expf(-sqrtf(fmaf(d2, d2, fmaf(d1, d1, d0 * d0))) * p.inv_len) : 0.f;
+                        }
+                        if (lo_part) g -= __uint_as_float(__float_as_uint(g) & 0xFFFFE000u);
+                        v[mu] = __float_as_uint(g);
+                    }
+                } else {
+                    const uint8_t* row =
+                        smem + stage * stage_bytes + a_bytes + (n >> 3) * (kp >> 2) * 128 + (n & 7) * 16;
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (4 * c < kp) x = *(const float4*)(row + c * 128);
+                        if (lo_part) x = tf32_lo(x);
+                        v[4 * c] = __float_as_uint(x.x);
+                        v[4 * c + 1] = __float_as_uint(x.y);
+                        v[4 * c + 2] = __float_as_uint(x.z);
+                        v[4 * c + 3] = __float_as_uint(x.w);
+                    }
                 }
                 tmem_st64(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(A_BASE + 64 * as), v);
                 tmem_wait_st();
@@ -756,6 +790,7 @@ int tc_prepare() {
     H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     g_tc_attr_device = dev;
     return 0;
 }
@@ -769,6 +804,10 @@ int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st
     int rc = tc_prepare();
     if (rc) return rc;
     const int smem = nstages * stage_bytes + (kind == 1 ? kXchBytes : 0) + 1024;
+    if (mode == 2) {
+        if (kind != 1) { set_error("matrix-free coupling runs on the TF32 path only"); return H2_E_UNSUPPORTED; }
+        return launch_one<2, 1>(p, grid, smem, st);
+    }
     if (mode == 0 && kind == 0) return launch_one<0, 0>(p, grid, smem, st);
     if (mode == 1 && kind == 0) return launch_one<1, 0>(p, grid, smem, st);
     if (mode == 0 && kind == 1) return launch_one<0, 1>(p, grid, smem, st);

@@ -28,8 +28,10 @@ H2_E_TIMEOUT = -5
 H2_E_OOM = -6
 H2_E_UNSUPPORTED = -7
 
-H2_F64, H2_F32, H2_BF16 = 0, 1, 2
-DTYPES = {"f64": H2_F64, "f32": H2_F32, "bf16": H2_BF16}
+H2_F64, H2_F32, H2_BF16, H2_F32_MF = 0, 1, 2, 3
+DTYPES = {"f64": H2_F64, "f32": H2_F32, "bf16": H2_BF16}  # also the precisions a build can add
+# product dtypes: "f32mf" is the FP32 tensor-core product with the matrix-free coupling
+PRODUCT_DTYPES = dict(DTYPES, f32mf=H2_F32_MF)
 H2_CG_COLUMNWISE = 0
 H2_CG_GRAM = 1
 VARIANTS = {"columnwise": H2_CG_COLUMNWISE, "gram": H2_CG_GRAM}
@@ -226,7 +228,7 @@ def _mm(fn, where, handle, alpha, X, Y, dtype, stream):
     yp, ldy, my, ky = _ptr_ld(Y, "Y", info_n, writable=True)
     if my != m:
         raise ValueError("X and Y must have the same number of columns")
-    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    dt = PRODUCT_DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
     _check(fn(handle, float(alpha), xp, ldx, yp, ldy, m, dt, _stream_ptr(stream)), where)
     return Y
 
