@@ -683,37 +683,60 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
         int stage = 0, sit = 0;
         uint32_t phase = 0;
         while (true) {
-            if (!__any_sync(0xffffffffu, mbar_wait(&full_bar[stage], phase))) {
-                if (lane == 0) atomicExch(p.err, 7);
-                abort_flag = 1;
-                break;
-            }
-            const int fl = stage_fl[stage];
-            if (!(fl & F_END)) {
-                const int as = sit % kASlots;
-                // the slot is free once the MMAs of term sit - kASlots have completed
-                if (!__any_sync(0xffffffffu, mbar_wait(&aempty_bar[as], ((sit / kASlots) & 1) ^ 1))) {
+            bool ok = __any_sync(0xffffffffu, mbar_wait(&full_bar[stage], phase));
+            const int fl = ok ? stage_fl[stage] : 0;
+            const bool end = ok && (fl & F_END);
+            const int as = sit % kASlots;
+            // the slot is free once the MMAs of term sit - kASlots have completed
+            if (ok && !end) ok = __any_sync(0xffffffffu, mbar_wait(&aempty_bar[as], ((sit / kASlots) & 1) ^ 1));
+            if (ok && !end) tc_fence_after();
+            const int kp = ok ? stage_kp[stage] : 0;
+            float* xbuf = (float*)(smem + stage * stage_bytes + a_bytes);  // MODE 2: [64 μ][64 rows]
+            if (MF) {
+                // row n of S_b: g(ξ_{t,n}, ξ_{s,μ}) = exp(-|ξ_{t,n} - ξ_{s,μ}| / length) for
+                // n, μ < k, zero in the padding.  The tile warp (q < 2) and the remainder
+                // warp (q + 2) of the same rows each evaluate half of the columns and
+                // swap halves through the stage's (unused) matrix region.  The exponential
+                // is 2^(-r·log2(e)/length) with r = d²·rsqrt(d²) (hardware approximations,
+                // relative error below 1e-6).
+                if (ok && !end) {
+                    const bool rv = n < p.k;
+                    const float4 xt = p.nodes[(int64_t)stage_t[stage] * p.KP + (rv ? n : 0)];
+                    const float4* xs = p.nodes + (int64_t)stage_s[stage] * p.KP;
+                    const int mu0 = lo_part ? 32 : 0;
+                    const float sc = -p.inv_len * 1.4426950408889634f;
+#pragma unroll 8
+                    for (int j = 0; j < 32; ++j) {
+                        const int mu = mu0 + j;
+                        float g = 0.f;
+                        if (rv && mu < p.k) {
+                            const float4 y = xs[mu];
+                            const float d0 = xt.x - y.x, d1 = xt.y - y.y, d2 = xt.z - y.z;
+                            const float r2 = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+                            const float e = r2 * rsqrtf(r2) * sc;
+                            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(e));
+                        }
+                        xbuf[mu * 64 + n] = g;
+                    }
+                }
+                // the pair (quadrants q and q ^ 2, named barrier 2 or 3) meets once per
+                // stage, end marker and failures included, and both learn whether to stop
+                if (bar_red_or(2 + (q & 1), 64, !ok)) {
                     if (lane == 0) atomicExch(p.err, 8);
                     abort_flag = 1;
                     break;
                 }
-                tc_fence_after();
-                const int kp = stage_kp[stage];
+            } else if (!ok) {
+                if (lane == 0) atomicExch(p.err, 7);
+                abort_flag = 1;
+                break;
+            }
+            if (!end) {
                 uint32_t v[64];
                 if (MF) {
-                    // row n of S_b: g(ξ_{t,n}, ξ_{s,μ}) = exp(-|ξ_{t,n} - ξ_{s,μ}| / length) for
-                    // n, μ < k, zero in the padding; every lane of the warp reads the same ξ_{s,μ}
-                    const bool rv = n < p.k;
-                    const float4 xt = p.nodes[(int64_t)stage_t[stage] * p.KP + (rv ? n : 0)];
-                    const float4* xs = p.nodes + (int64_t)stage_s[stage] * p.KP;
 #pragma unroll
                     for (int mu = 0; mu < 64; ++mu) {
-                        float g = 0.f;
-                        if (mu < kp) {
-                            const float4 y = xs[mu];
-                            const float d0 = xt.x - y.x, d1 = xt.y - y.y, d2 = xt.z - y.z;
-                            g = (rv && mu < p.k) ? __expf(-sqrtf(fmaf(d2, d2, fmaf(d1, d1, d0 * d0))) * p.inv_len) : 0.f;
-                        }
+                        float g = mu < kp ? xbuf[mu * 64 + n] : 0.f;
                         if (lo_part) g -= __uint_as_float(__float_as_uint(g) & 0xFFFFE000u);
                         v[mu] = __float_as_uint(g);
                     }
