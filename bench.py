@@ -250,6 +250,16 @@ def run_ours(args):
     msbf, phasesbf = timed("bf16", args.steps, 3, timing=True)
     valuebf = flops_step * ws / (msbf * 1e-3) / 1e9
 
+    # FP32 product with the matrix-free coupling (S_b evaluated from the nodes in the kernel)
+    mf = None
+    if dtype == "f32" and info["launches_tc"] > 0:
+        kmf = max(3, min(args.steps, 10))
+        msmf, phasesmf = timed("f32mf", kmf, 3, timing=True)
+        mf = {"value": round(flops_step * ws / (msmf * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+              "ms_per_step": round(msmf, 4), "coupling_kernel_ms": round(phasesmf["coupling_kernel"], 4),
+              "kernel_evaluations_per_step": int(info["n_adm"] * info["k"] * info["k"]),
+              "s_bytes_not_read": int(info["n_adm"] * info["k"] * info["k"] * 4)}
+
     # roofline of the dominant kernel: the coupling phase (one launch per product)
     elt = 8 if dtype == "f64" else 4
     n_adm, nc = info["n_adm"], info["n_clusters"]
@@ -385,6 +395,7 @@ def run_ours(args):
         "h2mm_bf16": {"value": round(valuebf, 3), "unit": "GFLOP/s", "ms_per_step": round(msbf, 4),
                       "coupling_GBps": round(n_adm * info["k"] * info["k"] * 2 / (phasesbf["coupling"] * 1e-3) / 1e9, 1),
                       "phases_ms": {kk: round(v, 4) for kk, v in phasesbf.items()}},
+        "h2mm_f32_matrix_free": mf,
         "roofline": roof,
         "e2e": e2e,
         "solve": solve,
