@@ -358,6 +358,18 @@ int h2_tree_build(const h2_build_params* params, const double* pts, int64_t n, h
 /* Pointers stay valid until h2_tree_free. */
 int h2_tree_view_get(const h2_tree* T, h2_tree_view* view);
 int h2_tree_free(h2_tree* T);
+/* The schedules of the FP32/BF16 transfer passes for this tree (each CTA owns
+ * the subtrees of cut clusters; the same builder serves h2_build), for
+ * inspection and tests.  which = 0: downward pass, steps (c, rd, wr, flags)
+ * with flags 1 = load the root's ŷ into entry wr, 2 = store ŷ_c (a leaf);
+ * which = 1: upward pass, steps (c, rd0, rd1, wr), a leaf having rd0 = -1 and
+ * rd1 = its position among the leaves.  Entries index a per-task stack of
+ * *entries k×m blocks.  Call with task_ptr = steps = NULL for *ntasks,
+ * *nsteps and *entries; then task_ptr holds ntasks + 1 int32 (task t runs
+ * steps task_ptr[t] .. task_ptr[t+1]-1) and steps 4·nsteps int32.
+ * Errors: H2_E_BADARG (null T or counts, which not 0 or 1). */
+int h2_tree_schedule(const h2_tree* T, int32_t which, int32_t* ntasks, int32_t* nsteps, int32_t* entries,
+                     int32_t* task_ptr, int32_t* steps);
 
 /* Description of the last error on the calling thread ("" if none). */
 const char* h2_last_error_string(void);

@@ -122,6 +122,32 @@ int h2_tree_view_get(const h2_tree* T, h2_tree_view* v) {
     return 0;
 }
 
+int h2_tree_schedule(const h2_tree* T, int32_t which, int32_t* ntasks, int32_t* nsteps, int32_t* entries,
+                     int32_t* task_ptr, int32_t* steps) {
+    if (!T || !ntasks || !nsteps || !entries || (which != 0 && which != 1)) {
+        h2::set_error("h2_tree_schedule: null argument or which not 0/1");
+        return H2_E_BADARG;
+    }
+    std::vector<int32_t> ptr;
+    std::vector<int32_t> flat;
+    int32_t nt = 0, ent = 0;
+    if (which == 0) {
+        std::vector<h2::DownStep> v;
+        h2::down_schedule(T->T, h2::kDownTasks, ptr, v, nt, ent);
+        for (const auto& d : v) flat.insert(flat.end(), {d.c, d.rd, d.wr, d.flags});
+    } else {
+        std::vector<h2::UpStep> v;
+        h2::up_schedule(T->T, h2::kUpTasks, ptr, v, nt, ent);
+        for (const auto& u : v) flat.insert(flat.end(), {u.c, u.rd0, u.rd1, u.wr});
+    }
+    *ntasks = nt;
+    *nsteps = (int32_t)(flat.size() / 4);
+    *entries = ent;
+    if (task_ptr) std::copy(ptr.begin(), ptr.end(), task_ptr);
+    if (steps) std::copy(flat.begin(), flat.end(), steps);
+    return 0;
+}
+
 int h2_tree_free(h2_tree* T) {
     delete T;
     return 0;

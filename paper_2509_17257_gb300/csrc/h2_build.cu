@@ -186,6 +186,34 @@ __global__ void k_transpose_f32(const double* __restrict__ E, float* __restrict_
     }
 }
 
+// Lays out a work list sorted by decreasing cost for a kernel whose CTA b
+// takes positions b, b + G, b + 2G, ...: round r of G items goes to the CTAs
+// in order for even r and in reverse for odd r (the last, partial round in
+// order), so no CTA takes the largest item of every round.
+void snake_order(std::vector<TcItem>& v, int G) {
+    const size_t n = v.size();
+    if (G < 2 || n <= (size_t)G) return;
+    std::vector<TcItem> out(n);
+    for (size_t i = 0; i < n; ++i) {
+        const size_t r = i / G, j = i % G;
+        const bool full = (r + 1) * G <= n;
+        out[r * G + ((r & 1) && full ? G - 1 - j : j)] = v[i];
+    }
+    v.swap(out);
+}
+
+int cast_copy(h2_matrix* A, const double* src, void** dst, int64_t count, cudaStream_t st) {
+    int rc = device_alloc(A, dst, (size_t)(count > 0 ? count : 1) * sizeof(float));
+    if (rc) return rc;
+    if (count > 0) {
+        k_cast_f32<<<1216, 256, 0, st>>>(src, (float*)*dst, count);
+        H2_LAUNCH_CHECK();
+    }
+    return 0;
+}
+
+}  // namespace
+
 // Schedule of the subtree-owning downward pass.  The tree is cut at level Ls:
 // the cut clusters (level Ls, and leaves above it) are the tasks.  A task
 // recomputes ŷ of the clusters on the path from the root to its cut cluster
@@ -362,34 +390,6 @@ void up_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std:
     ntasks = (int32_t)task_steps.size();
 }
 
-// Lays out a work list sorted by decreasing cost for a kernel whose CTA b
-// takes positions b, b + G, b + 2G, ...: round r of G items goes to the CTAs
-// in order for even r and in reverse for odd r (the last, partial round in
-// order), so no CTA takes the largest item of every round.
-void snake_order(std::vector<TcItem>& v, int G) {
-    const size_t n = v.size();
-    if (G < 2 || n <= (size_t)G) return;
-    std::vector<TcItem> out(n);
-    for (size_t i = 0; i < n; ++i) {
-        const size_t r = i / G, j = i % G;
-        const bool full = (r + 1) * G <= n;
-        out[r * G + ((r & 1) && full ? G - 1 - j : j)] = v[i];
-    }
-    v.swap(out);
-}
-
-int cast_copy(h2_matrix* A, const double* src, void** dst, int64_t count, cudaStream_t st) {
-    int rc = device_alloc(A, dst, (size_t)(count > 0 ? count : 1) * sizeof(float));
-    if (rc) return rc;
-    if (count > 0) {
-        k_cast_f32<<<1216, 256, 0, st>>>(src, (float*)*dst, count);
-        H2_LAUNCH_CHECK();
-    }
-    return 0;
-}
-
-}  // namespace
-
 int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cudaStream_t st) {
     const Tree& T = A->T;
     const int64_t n = A->n, nc = A->nc;
@@ -513,14 +513,11 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
     {
         std::vector<int32_t> task_ptr;
         std::vector<DownStep> dsteps;
-        down_schedule(T, 256, task_ptr, dsteps, A->dn_ntasks, A->dn_entries);
+        down_schedule(T, kDownTasks, task_ptr, dsteps, A->dn_ntasks, A->dn_entries);
         UP(A->d_dn_task_ptr, task_ptr);
         UP(A->d_dn_steps, dsteps);
         std::vector<UpStep> usteps;
-        // about 1.7 tasks per CTA slot (two per SM): the longest subtree, walked
-        // by one CTA, bounds the task phase, so the cut sits one level deeper
-        // than for the downward pass
-        up_schedule(T, 400, task_ptr, usteps, A->up_ntasks, A->up_entries);
+        up_schedule(T, kUpTasks, task_ptr, usteps, A->up_ntasks, A->up_entries);
         UP(A->d_up_task_ptr, task_ptr);
         UP(A->d_up_steps, usteps);
     }

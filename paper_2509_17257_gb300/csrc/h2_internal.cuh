@@ -160,7 +160,18 @@ struct UpStep {
     int32_t c, rd0, rd1, wr;
 };
 constexpr int kUpMaxSteps = 64;    // steps of one task at most
+// Task counts the cut levels aim at: the downward pass takes the shallowest level
+// with at least kDownTasks subtrees; the upward pass, whose longest subtree bounds
+// its task phase, about 1.7 tasks per CTA slot (two per SM)
+constexpr int kDownTasks = 256, kUpTasks = 400;
 constexpr int kUpMaxEntries = 5;   // stack entries at most (three of them serve the climb above the cut)
+
+struct Tree;
+// Transfer-pass schedules (h2_build.cu), host only
+void down_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std::vector<DownStep>& steps,
+                   int32_t& ntasks, int32_t& entries);
+void up_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std::vector<UpStep>& steps,
+                 int32_t& ntasks, int32_t& entries);
 
 struct SyncBufs {
     unsigned* cnt = nullptr;

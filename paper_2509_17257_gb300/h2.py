@@ -95,7 +95,8 @@ EXPORTS = ["h2_build", "h2_free", "h2_info", "h2_matmul", "h2_matmul_transposed"
            "h2_timing_enable", "h2_timing_query", "h2_coupling_get", "h2_coupling_set", "h2_shift_set",
            "h2_adjoint_grads", "h2_batch_create", "h2_batch_free", "h2_batch_matmul", "h2_batch_block_cg",
            "h2_autotune",
-           "h2_tree_build", "h2_tree_view_get", "h2_tree_free", "h2_last_error_string", "h2_version"]
+           "h2_tree_build", "h2_tree_view_get", "h2_tree_free", "h2_tree_schedule", "h2_last_error_string",
+           "h2_version"]
 H2_NPHASE = 8
 PHASES = ["gather", "leaf_fwd", "up", "coupling", "down", "leaf_bwd_near", "coupling_kernel"]
 
@@ -134,6 +135,7 @@ def lib() -> C.CDLL:
     L.h2_tree_build.argtypes = [C.POINTER(BuildParams), vp, i64, C.POINTER(vp)]
     L.h2_tree_view_get.argtypes = [vp, C.POINTER(TreeView)]
     L.h2_tree_free.argtypes = [vp]
+    L.h2_tree_schedule.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), vp, vp]
     L.h2_last_error_string.restype = C.c_char_p
     L.h2_version.restype = C.c_char_p
     for name in EXPORTS:
@@ -464,6 +466,27 @@ def h2_tree_build(points, leaf_size=64, eta=2.0, q=3) -> dict:
             adm_rowptr=arr(v.adm_rowptr, nc + 1), adm_col=arr(v.adm_col, v.n_adm),
             near_rowptr=arr(v.near_rowptr, nc + 1), near_col=arr(v.near_col, v.n_near),
         )
+    finally:
+        lib().h2_tree_free(h)
+
+
+def h2_tree_schedule(points, which, leaf_size=64, eta=2.0, q=3) -> dict:
+    """Host-only: the FP32/BF16 transfer-pass schedule of the tree of `points`
+    (which = "down" or "up"): task_ptr [ntasks+1], steps [nsteps, 4] and the
+    stack depth, as h2_build uses them."""
+    w = {"down": 0, "up": 1}[which]
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64))
+    bp = BuildParams(q, leaf_size, eta, 0.5, 0.0, 0, None)
+    h = C.c_void_p()
+    _check(lib().h2_tree_build(C.byref(bp), pts.ctypes.data, pts.shape[0], C.byref(h)), "h2_tree_build")
+    try:
+        nt, ns, ent = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().h2_tree_schedule(h, w, C.byref(nt), C.byref(ns), C.byref(ent), None, None), "h2_tree_schedule")
+        ptr = np.zeros(nt.value + 1, dtype=np.int32)
+        steps = np.zeros((ns.value, 4), dtype=np.int32)
+        _check(lib().h2_tree_schedule(h, w, C.byref(nt), C.byref(ns), C.byref(ent), ptr.ctypes.data,
+                                      steps.ctypes.data), "h2_tree_schedule")
+        return dict(task_ptr=ptr, steps=steps, entries=ent.value)
     finally:
         lib().h2_tree_free(h)
 
