@@ -226,7 +226,7 @@ int h2_info(const h2_matrix* A, h2_info_t* info) {
     // tensor-core chain: gather, upward pass, coupling, downward pass, leaf phase, scatter into Y, + zeroing of
     // clusters without couplings; where the subtree-owning transfer passes do not apply (k % 4 != 0 or
     // k > 64) also the packing of X, x̂ and ŷ
-    const bool own_passes = A->f32.Et && A->k % 4 == 0 && A->k <= 64;
+    const bool own_passes = A->f32.Et && A->k % 8 == 0 && A->k <= 64;
     info->launches_tc = A->tc.built ? (own_passes ? 5 : 8) + (A->down_ptr.back() > 0 ? 1 : 0) +
                                           (A->tc.c_nzero > 0 ? 1 : 0)
                                     : 0;

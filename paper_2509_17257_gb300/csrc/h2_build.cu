@@ -176,13 +176,15 @@ int upload(h2_matrix* A, T** dst, const std::vector<T>& src, cudaStream_t st) {
     return 0;
 }
 
-// Et[c][μ][ν] = E[c][ν][μ] in FP32 (k×k per cluster).
+// Et[c][μ][ν] = E[c][ν][μ] in FP32, rows of kEtLd floats (k×kEtLd per cluster, zero
+// past column k): one bulk copy lands a cluster's block with the row stride the
+// downward pass's warp-MMA fragment loads want (≡ 8 mod 32, no bank conflicts).
 __global__ void k_transpose_f32(const double* __restrict__ E, float* __restrict__ Et, int64_t nc, int k) {
-    const int64_t kk = (int64_t)k * k;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc * kk; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = e / kk;
-        const int r = (int)((e % kk) / k), q = (int)(e % k);
-        Et[c * kk + (int64_t)q * k + r] = (float)E[e];
+    const int64_t per = (int64_t)k * kEtLd;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc * per; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / per;
+        const int q = (int)((e % per) / kEtLd), r = (int)(e % kEtLd);
+        Et[e] = r < k ? (float)E[c * k * k + (int64_t)r * k + q] : 0.f;
     }
 }
 
@@ -603,9 +605,9 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
             if ((rc = cast_copy(A, (const double*)A->f64.V, &A->f32.V, (int64_t)n * k, st))) return rc;
             if ((rc = cast_copy(A, (const double*)A->f64.E, &A->f32.E, nc * k * k, st))) return rc;
         }
-        if (k % 4 == 0) {
-            // transposed transfer matrices for the row-staged downward pass
-            if ((rc = device_alloc(A, &A->f32.Et, (size_t)nc * k * k * sizeof(float)))) return rc;
+        if (k % 8 == 0 && k <= 64) {
+            // transposed transfer matrices for the subtree-owning downward pass
+            if ((rc = device_alloc(A, &A->f32.Et, (size_t)nc * k * kEtLd * sizeof(float)))) return rc;
             k_transpose_f32<<<1216, 256, 0, st>>>((const double*)A->f64.E, (float*)A->f32.Et, nc, k);
             H2_LAUNCH_CHECK();
         }

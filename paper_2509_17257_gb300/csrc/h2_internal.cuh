@@ -42,7 +42,7 @@ void set_error(const std::string& msg);
 struct MatData {
     void* V = nullptr;
     void* E = nullptr;
-    void* Et = nullptr;  // FP32 only, k % 4 == 0: E_{t'}ᵀ per cluster (the downward pass reads rows)
+    void* Et = nullptr;  // FP32 only, k % 8 == 0, k <= 64: E_{t'}ᵀ per cluster, rows of kEtLd floats
     void* S = nullptr;
     void* Near = nullptr;
     int64_t bytes = 0;
@@ -148,6 +148,7 @@ struct DownStep {
     int32_t c, rd, wr, flags;
 };
 constexpr int kDownLoad = 1, kDownStore = 2;
+constexpr int kEtLd = 72;  // row stride of the FP32 Eᵀ blocks (≡ 8 mod 32)
 constexpr int kTcGrid = 152;  // CTAs of the tensor-core kernels (one per SM); their work lists are laid out for it
 constexpr int kDownMaxSteps = 192;  // steps of one task at most (the schedule keeps to it)
 

@@ -675,34 +675,79 @@ __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ 
     }
 }
 
+// ---- 3xTF32 warp MMAs (mma.sync m16n8k8) for the transfer passes ----
+// A 16×8 TF32 A fragment and 8×8 B fragment per thread (g = lane / 4,
+// t = lane % 4): a0 = A[g][t], a1 = A[g+8][t], a2 = A[g][t+4], a3 = A[g+8][t+4];
+// b0 = B[t][g], b1 = B[t+4][g]; D: d0 = D[g][2t], d1 = D[g][2t+1], d2 = D[g+8][2t],
+// d3 = D[g+8][2t+1].  An FP32 operand x is split into hi = tf32(x) (rounded)
+// and lo = x - hi; D += A_lo·B_hi + A_hi·B_lo + A_hi·B_hi keeps FP32 accuracy.
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    hi = h;
+    lo = __float_as_uint(x - __uint_as_float(h));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// d[nt] (N-tile nt: columns 8nt..8nt+7) += A·B over K = kdim (a multiple of 8)
+// for the warp's 16 rows m0..m0+15, with A[i][j] = a[j·lda + i] (a transposed
+// K-major block) and B[j][n] = b[j·ldb + n]; lda, ldb ≡ 8 (mod 32) keep the
+// fragment loads free of bank conflicts.
+template <int NTILES>
+__device__ __forceinline__ void mma_contract(float (&d)[NTILES][4], const float* a, int lda, const float* b, int ldb,
+                                             int kdim, int m0) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    for (int k0 = 0; k0 < kdim; k0 += 8) {
+        const float* ar = a + (k0 + t) * lda + m0 + g;
+        uint32_t ah[4], al[4];
+        tf32_split(ar[0], ah[0], al[0]);
+        tf32_split(ar[8], ah[1], al[1]);
+        tf32_split(ar[4 * lda], ah[2], al[2]);
+        tf32_split(ar[4 * lda + 8], ah[3], al[3]);
+        const float* br = b + (k0 + t) * ldb + g;
+#pragma unroll
+        for (int nt = 0; nt < NTILES; ++nt) {
+            uint32_t bh0, bl0, bh1, bl1;
+            tf32_split(br[8 * nt], bh0, bl0);
+            tf32_split(br[4 * ldb + 8 * nt], bh1, bl1);
+            mma_tf32(d[nt], al, bh0, bh1);
+            mma_tf32(d[nt], ah, bl0, bl1);
+            mma_tf32(d[nt], ah, bh0, bh1);
+        }
+    }
+}
+
 // Downward pass with subtree ownership (schedule: down_schedule, h2_build.cu).
 // A CTA claims tasks in the stored order; a task is a list of steps, each
 // ŷ_c += E_c ŷ_father (Sec. 3, the downward transformation of
 // Alg. "fast_addeval"), with ŷ_father in a shared-memory stack entry written by
-// an earlier step of the same task, so no step waits for another CTA.  The
-// static operands of step s + 1 (Eᵀ_c, k×k, and the coupling result ŷ_c, k×m,
-// both contiguous) arrive by two bulk copies, issued by one thread while step
-// s computes.  All ŷ buffers keep rows of m floats.  64·CN threads: thread
-// (tx, ty) = (tid mod 4CN, tid div 4CN) owns rows 4ty.. and columns 4tx.. of
-// the k×m result.
+// an earlier step of the same task, so no step waits for another CTA.
+// Four warps, warp w computing rows 16w..16w+15 of the k×m result with 3xTF32
+// warp MMAs (mma_contract).  Eᵀ_c of step s + 1 (stored with rows of kEtLd
+// floats) arrives by one bulk copy while step s computes; the coupling result
+// ŷ_c of step s + 1 is loaded into the fragment registers meanwhile.  Stack
+// rows have stride NT + 8; the root's ŷ of a task's first step is copied into
+// its entry row by row (warp 0's lanes).
 template <int CN>
-__global__ void __launch_bounds__(64 * CN) k_down_own(const int32_t* __restrict__ task_ptr, int ntasks,
-                                                       const DownStep* __restrict__ steps,
-                                                       const float* __restrict__ Et, float* yhat,
-                                                       unsigned* __restrict__ claim, int* __restrict__ err, int k,
-                                                       int m, PackOut pk) {
-    constexpr int NT = 16 * CN;
+__global__ void __launch_bounds__(128) k_down_own(const int32_t* __restrict__ task_ptr, int ntasks,
+                                                  const DownStep* __restrict__ steps,
+                                                  const float* __restrict__ Et, float* yhat,
+                                                  unsigned* __restrict__ claim, int* __restrict__ err, int k, int m,
+                                                  PackOut pk) {
+    constexpr int NT = 16 * CN, NTILES = 2 * CN, LDA = kEtLd, LDY = NT + 8;
     extern __shared__ __align__(16) float fsm[];
-    float* ebuf = fsm;                  // [2][64·64]       Eᵀ_c
-    float* cbuf = ebuf + 2 * 64 * 64;   // [2][64·NT]       ŷ_c from the coupling phase
-    float* stk = cbuf + 2 * 64 * NT;    // [entries][64·NT] final ŷ along the current path
+    float* ebuf = fsm;                 // [2][64 rows j][LDA]   Eᵀ_c
+    float* stk = ebuf + 2 * 64 * LDA;  // [entries][64][LDY]    final ŷ along the current path
     __shared__ int s_task;
     __shared__ DownStep s_steps[kDownMaxSteps];  // the task's steps: no global load between two steps
     __shared__ __align__(8) uint64_t bar[2];
-    const int tx = threadIdx.x % (4 * CN), ty = threadIdx.x / (4 * CN);
-    const bool colv = 4 * tx < m;  // m % 4 == 0: the thread's four columns are valid together
-    const int64_t kk = (int64_t)k * k, km = (int64_t)k * m;
-    const uint32_t ebytes = (uint32_t)(kk * 4), ybytes = (uint32_t)(km * 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int m0 = 16 * warp;
+    const int64_t ke = (int64_t)k * LDA, km = (int64_t)k * m;
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -710,6 +755,21 @@ __global__ void __launch_bounds__(64 * CN) k_down_own(const int32_t* __restrict_
     }
     uint32_t phase = 0;  // bit b: parity of the next completion of bar[b]
     bool failed = false;
+    // the thread's fragment positions of a k×m block: rows m0+g, m0+g+8; columns 8nt+2t, +1
+    auto load_frag = [&](float (&v)[NTILES][4], const float* src) {
+#pragma unroll
+        for (int nt = 0; nt < NTILES; ++nt) {
+            const int c = 8 * nt + 2 * t;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = m0 + g + 8 * h;
+                float2 x = make_float2(0.f, 0.f);
+                if (r < k && c < m) x = __ldcg((const float2*)(src + (int64_t)r * m + c));
+                v[nt][2 * h] = x.x;
+                v[nt][2 * h + 1] = x.y;
+            }
+        }
+    };
     while (!failed) {
         __syncthreads();
         if (threadIdx.x == 0) s_task = (int)atomicAdd(claim, 1u);
@@ -719,23 +779,31 @@ __global__ void __launch_bounds__(64 * CN) k_down_own(const int32_t* __restrict_
         const int s0 = task_ptr[task], s1 = min(task_ptr[task + 1], s0 + kDownMaxSteps);
         for (int i = threadIdx.x; i < s1 - s0; i += blockDim.x) s_steps[i] = steps[s0 + i];
         __syncthreads();
-        // one thread arms the buffer's barrier and starts the step's copies
+        // warp 0 arms the buffer's barrier and starts the step's copies: one of
+        // Eᵀ_c, or the root's rows into the stack entry (lane l: rows l, l + 32)
         auto issue = [&](int s, int b) {
-            if (threadIdx.x != 0) return;
+            if (warp != 0) return;
             const DownStep d = s_steps[s - s0];
             if (d.flags & kDownLoad) {
-                mbar_expect_tx(&bar[b], ybytes);
-                bulk_g2s(stk + d.wr * 64 * NT, yhat + (int64_t)d.c * km, ybytes, &bar[b]);
-            } else {
-                mbar_expect_tx(&bar[b], ebytes + ybytes);
-                bulk_g2s(ebuf + b * 64 * 64, Et + (int64_t)d.c * kk, ebytes, &bar[b]);
-                bulk_g2s(cbuf + b * 64 * NT, yhat + (int64_t)d.c * km, ybytes, &bar[b]);
+                const uint32_t rowb = (uint32_t)m * 4;
+                if (lane == 0) mbar_expect_tx(&bar[b], rowb * (uint32_t)k);
+                __syncwarp();
+                for (int r = lane; r < k; r += 32)
+                    bulk_g2s(stk + (d.wr * 64 + r) * LDY, yhat + (int64_t)d.c * km + (int64_t)r * m, rowb, &bar[b]);
+            } else if (lane == 0) {
+                mbar_expect_tx(&bar[b], (uint32_t)(ke * 4));
+                bulk_g2s(ebuf + b * 64 * LDA, Et + (int64_t)d.c * ke, (uint32_t)(ke * 4), &bar[b]);
             }
         };
+        float ccur[NTILES][4], cnext[NTILES][4];
         issue(s0, 0);
         for (int s = s0; s < s1; ++s) {
             const int b = (s - s0) & 1;
-            if (s + 1 < s1) issue(s + 1, b ^ 1);
+            if (s + 1 < s1) {
+                issue(s + 1, b ^ 1);
+                const DownStep dn = s_steps[s + 1 - s0];
+                if (!(dn.flags & kDownLoad)) load_frag(cnext, yhat + (int64_t)dn.c * km);
+            }
             const bool ok = mbar_wait(&bar[b], (phase >> b) & 1u);
             phase ^= 1u << b;
             if (__syncthreads_or(!ok)) {
@@ -751,25 +819,38 @@ __global__ void __launch_bounds__(64 * CN) k_down_own(const int32_t* __restrict_
             }
             const DownStep d = s_steps[s - s0];
             if (!(d.flags & kDownLoad)) {
-                const float* cb = cbuf + b * 64 * NT;
-                float acc[4][4];
+                mma_contract<NTILES>(ccur, ebuf + b * 64 * LDA, LDA, stk + d.rd * 64 * LDY, LDY, k, m0);
+                float* out = stk + d.wr * 64 * LDY;
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const float4 v = *(const float4*)(cb + (4 * ty + r) * m + 4 * tx);
-                    acc[r][0] = v.x; acc[r][1] = v.y; acc[r][2] = v.z; acc[r][3] = v.w;
-                }
-                contract44(acc, ebuf + b * 64 * 64, k, stk + d.rd * 64 * NT, m, k, tx, ty);
-                float* out = stk + d.wr * 64 * NT;
-                float* gout = yhat + (int64_t)d.c * km;
-                if (d.flags & kDownStore) pack_rows(pk, pk.act + (int64_t)d.c * pk.KP * pk.R * pk.es, acc, tx, ty, k, m);
-                if (colv) {
+                for (int nt = 0; nt < NTILES; ++nt)
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const float4 v = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-                        *(float4*)(out + (4 * ty + r) * m + 4 * tx) = v;
-                        if ((d.flags & kDownStore) && 4 * ty + r < k) *(float4*)(gout + (4 * ty + r) * m + 4 * tx) = v;
+                    for (int h = 0; h < 2; ++h)
+                        *(float2*)(out + (m0 + g + 8 * h) * LDY + 8 * nt + 2 * t) =
+                            make_float2(ccur[nt][2 * h], ccur[nt][2 * h + 1]);
+                if (d.flags & kDownStore) {
+                    // a leaf: ŷ_c to global memory and into its split tile, read back
+                    // from the stack entry in 4×4 blocks
+                    __syncthreads();
+                    float* gout = yhat + (int64_t)d.c * km;
+                    uint8_t* tile = pk.act + (int64_t)d.c * pk.KP * pk.R * pk.es;
+                    for (int blk = threadIdx.x; blk < 16 * (NT / 4); blk += blockDim.x) {
+                        const int ty = blk / (NT / 4), tx = blk % (NT / 4);
+                        float acc[4][4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const float4 v = *(const float4*)(out + (4 * ty + r) * LDY + 4 * tx);
+                            acc[r][0] = v.x; acc[r][1] = v.y; acc[r][2] = v.z; acc[r][3] = v.w;
+                            if (4 * ty + r < k && 4 * tx < m) *(float4*)(gout + (4 * ty + r) * m + 4 * tx) = v;
+                        }
+                        pack_rows(pk, tile, acc, tx, ty, k, m);
                     }
                 }
+            }
+            if (s + 1 < s1) {
+#pragma unroll
+                for (int nt = 0; nt < NTILES; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) ccur[nt][e] = cnext[nt][e];
             }
             __syncthreads();
         }
@@ -778,8 +859,8 @@ __global__ void __launch_bounds__(64 * CN) k_down_own(const int32_t* __restrict_
 
 // k_up_own: two slots of two 64×64 blocks plus the stack
 int up_own_smem_bytes(int cn, int entries) { return (4 * 64 * 64 + entries * 64 * 16 * cn) * (int)sizeof(float); }
-// k_down_own: two Eᵀ and two ŷ buffers plus the stack (at most 8 entries)
-int down_own_smem_bytes(int cn, int entries) { return (2 * 64 * 64 + (2 + entries) * 64 * 16 * cn) * (int)sizeof(float); }
+// k_down_own: two Eᵀ buffers (rows of 72) plus the stack (rows of 16·cn + 8, at most 8 entries)
+int down_own_smem_bytes(int cn, int entries) { return (2 * 64 * 72 + entries * 64 * (16 * cn + 8)) * (int)sizeof(float); }
 
 int g_fast_attr_device = -1;
 
@@ -1009,7 +1090,7 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         }
         // subtree-owning transfer passes when the rows are 16-byte multiples (k, mc % 4 == 0, k <= 64);
         // they also write the split tiles of X (leaves), x̂ and leaf ŷ
-        const bool fast = A->f32.Et && k % 4 == 0 && k <= 64 && mc % 4 == 0 && A->T.leaf_size <= 64;
+        const bool fast = A->f32.Et && k % 8 == 0 && k <= 64 && mc % 4 == 0 && A->T.leaf_size <= 64;
         if (!fast && (rc = launch_pack_act(Xp, mc, NL, nullptr, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, R, Xcm, es, st)))
             return rc;
         marks.mark();
@@ -1063,9 +1144,9 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
                 const float* Et = (const float*)A->f32.Et;
                 const int smem = down_own_smem_bytes(fcn, A->dn_entries);
                 const unsigned g = (unsigned)std::min(A->dn_ntasks, 152 * std::max(1, (227 * 1024) / (smem + 4096)));
-                if (fcn == 1) k_down_own<1><<<g, 64 * 1, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
-                else if (fcn == 2) k_down_own<2><<<g, 64 * 2, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
-                else k_down_own<4><<<g, 64 * 4, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
+                if (fcn == 1) k_down_own<1><<<g, 128, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
+                else if (fcn == 2) k_down_own<2><<<g, 128, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
+                else k_down_own<4><<<g, 128, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
                 H2_LAUNCH_CHECK();
             }
         } else if ((rc = backward_pass<float, RM, CN>(A, E, yhat, mc, gy, gzk, st, sbc))) {
