@@ -26,6 +26,16 @@ bool is_device_pointer(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Pinned host memory the device can address (mapped): its device pointer, else nullptr.
+const void* mapped_host_pointer(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int device_alloc(h2_matrix* A, void** ptr, size_t bytes) {
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);

@@ -386,6 +386,7 @@ int forward_transform_f64(h2_matrix* A, const double* X, int64_t ldx, int64_t m,
 int cast_f32(const double* src, float* dst, int64_t count, cudaStream_t st);
 
 bool is_device_pointer(const void* p);
+const void* mapped_host_pointer(const void* p);
 int device_alloc(h2_matrix* A, void** ptr, size_t bytes);
 
 }  // namespace h2

@@ -1370,6 +1370,19 @@ int matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, 
     if (m == 0) return 0;
     const bool dx = is_device_pointer(X), dy = is_device_pointer(Y);
     if (dx && dy) return matmul_device(A, alpha, X, ldx, Y, ldy, m, dtype, st, transposed, false);
+    // pinned host buffers the device can address: the product's gather reads X and
+    // its final pass updates Y where they are, over the host link, with no staging
+    // copies; the call returns when Y is complete, as for staged buffers
+    {
+        const double* Xm = dx ? X : (const double*)mapped_host_pointer(X);
+        double* Ym = dy ? Y : (double*)mapped_host_pointer(Y);
+        if (Xm && Ym) {
+            int rc = matmul_device(A, alpha, Xm, ldx, Ym, ldy, m, dtype, st, transposed, false);
+            if (rc) return rc;
+            H2_CUDA_TRY(cudaStreamSynchronize(st));
+            return 0;
+        }
+    }
     // host blocks: stage through device buffers (packed, ld = m)
     const size_t bytes = (size_t)A->n * m * sizeof(double);
     if (A->ws.stage_bytes < bytes) {

@@ -99,6 +99,30 @@ def test_host_buffers_and_leading_dimension(P, sphere4096):
     G.matmul(np.zeros((4096, 0)), np.zeros((4096, 0)))
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_pinned_host_buffers_in_place(P, dtype):
+    """Pinned host X and Y (device-mapped) are read and updated where they are;
+    the result equals the product on device copies, columns outside the views
+    untouched.  A q = 4 tree, so the FP32 and BF16 products take the
+    subtree-owning transfer passes."""
+    torch = require_cuda()
+    n = 3000
+    pts = sphere_points(n, 8)
+    G = P.H2Matrix(pts, q=4, leaf_size=64, eta=2.0, sigma=1e-2, length=0.5, precisions=("f32", "bf16"))
+    X = gaussian_rhs(n, 40, 7)
+    Y0 = gaussian_rhs(n, 40, 8)
+    Xh = torch.from_numpy(X).pin_memory()
+    Yh = torch.from_numpy(Y0).pin_memory()
+    G.matmul(Xh[:, 3:35], Yh[:, 5:37], alpha=0.5, dtype=dtype)  # ld = 40 > m = 32
+    Xd = torch.from_numpy(X).cuda()
+    Yd = torch.from_numpy(Y0).cuda()
+    G.matmul(Xd[:, 3:35], Yd[:, 5:37], alpha=0.5, dtype=dtype)
+    torch.cuda.synchronize()
+    got, ref = Yh.numpy(), Yd.cpu().numpy()
+    assert np.array_equal(got, ref)
+    assert np.array_equal(got[:, :5], Y0[:, :5]) and np.array_equal(got[:, 37:], Y0[:, 37:])
+
+
 @pytest.mark.parametrize("case", ["n1", "n64", "n65", "coincident", "planar", "q1", "q2", "q4", "q5",
                                   "ellipsoid_leaf17"])
 def test_edge_cases(P, case):
