@@ -680,15 +680,20 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
         const int q = warp & 3;
         const int n = 32 * (q & 1) + lane;
         const bool lo_part = q >= 2;
+        // The splitter is the one serial stage of the pipeline, so it tests the next
+        // term's barriers while it works on the current one: a phase seen complete
+        // then costs no wait at the top of the next iteration.
         int stage = 0, sit = 0;
         uint32_t phase = 0;
+        bool pre = false;  // the next iteration's stage and A-slot phases were seen complete
         while (true) {
-            bool ok = __any_sync(0xffffffffu, mbar_wait(&full_bar[stage], phase));
+            bool ok = pre || __any_sync(0xffffffffu, mbar_wait(&full_bar[stage], phase));
             const int fl = ok ? stage_fl[stage] : 0;
             const bool end = ok && (fl & F_END);
             const int as = sit % kASlots;
             // the slot is free once the MMAs of term sit - kASlots have completed
-            if (ok && !end) ok = __any_sync(0xffffffffu, mbar_wait(&aempty_bar[as], ((sit / kASlots) & 1) ^ 1));
+            if (ok && !end && !pre) ok = __any_sync(0xffffffffu, mbar_wait(&aempty_bar[as], ((sit / kASlots) & 1) ^ 1));
+            pre = false;
             if (ok && !end) tc_fence_after();
             const int kp = ok ? stage_kp[stage] : 0;
             float* xbuf = (float*)(smem + stage * stage_bytes + a_bytes);  // MODE 2: [64 μ][64 rows]
@@ -732,6 +737,10 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 break;
             }
             if (!end) {
+                const int nstage = stage + 1 == nst ? 0 : stage + 1;
+                const uint32_t nphase = stage + 1 == nst ? phase ^ 1u : phase;
+                const bool pf = mbar_test(&full_bar[nstage], nphase);
+                const bool pa = mbar_test(&aempty_bar[(sit + 1) % kASlots], (((sit + 1) / kASlots) & 1) ^ 1);
                 uint32_t v[64];
                 if (MF) {
 #pragma unroll
@@ -758,6 +767,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 tmem_wait_st();
                 tc_fence_before();
                 ++sit;
+                pre = __all_sync(0xffffffffu, pf && pa);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&split_bar[stage]);
