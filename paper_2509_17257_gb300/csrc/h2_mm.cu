@@ -140,16 +140,26 @@ __device__ __forceinline__ void store_tile(const Acc<T, RM, CN>& acc, T* __restr
     }
 }
 
+// Lanes per row for m columns: the power of two ≥ m, at most 32, so a warp
+// covers 32 / P rows per step, each with one perm lookup and contiguous columns
+// (no per-element division).
+__device__ __forceinline__ int row_lanes(int m) {
+    int P = 1;
+    while (P < m && P < 32) P <<= 1;
+    return P;
+}
+
 // ---- gather: Xp[i, :] = X[perm[i], :] in the compute type ----
 template <typename T>
 __global__ void k_gather(const double* __restrict__ X, int64_t ldx, const int32_t* __restrict__ perm, int64_t n,
                          int m, T* __restrict__ Xp) {
-    const int64_t total = n * m;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / m;
-        const int c = (int)(e % m);
-        Xp[e] = (T)X[(int64_t)perm[i] * ldx + c];
+    const int P = row_lanes(m), R = 32 / P;
+    const int lane = threadIdx.x & 31, sub = lane / P, cl = lane % P;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * R + sub; i < n; i += nw * R) {
+        const double* x = X + (int64_t)perm[i] * ldx;
+        T* o = Xp + i * m;
+        for (int c = cl; c < m; c += P) o[c] = (T)x[c];
     }
 }
 
@@ -157,15 +167,18 @@ __global__ void k_gather(const double* __restrict__ X, int64_t ldx, const int32_
 __global__ void k_scatter_y(const float* __restrict__ Z, int ldz, const int32_t* __restrict__ perm, int64_t n, int m,
                             const double* __restrict__ X, int64_t ldx, double* __restrict__ Y, int64_t ldy,
                             double alpha, double sigma, int overwrite) {
-    const int64_t total = n * m;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / m;
-        const int c = (int)(e % m);
+    const int P = row_lanes(m), R = 32 / P;
+    const int lane = threadIdx.x & 31, sub = lane / P, cl = lane % P;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * R + sub; i < n; i += nw * R) {
         const int64_t g = perm[i];
-        const double z = (double)Z[i * ldz + c] + sigma * X[g * ldx + c];
-        double* y = Y + g * ldy + c;
-        if (overwrite) *y = alpha * z; else *y += alpha * z;
+        const float* z = Z + i * ldz;
+        const double* x = X + g * ldx;
+        double* y = Y + g * ldy;
+        for (int c = cl; c < m; c += P) {
+            const double v = alpha * ((double)z[c] + sigma * x[c]);
+            if (overwrite) y[c] = v; else y[c] += v;
+        }
     }
 }
 
