@@ -17,25 +17,28 @@
 // copy per tile lands it in shared memory ready for the MMA.
 //
 // The FP32 product (KIND 1) runs the same schedule on the TF32 units with
-// split operands: the activation rows carry tf32 high and low parts, and the
-// matrix tile B is complemented in shared memory by B_lo = B - tf32(B), so
-// A_hi·B + A_hi·B_lo + A_lo·B + A_lo·B_lo keeps FP32 accuracy ("3xTF32", the
-// A_lo·B_lo term comes free with the row split).  Its MMA runs the other way
-// round, D[n, r] = Σ_k [B; B_lo][n, k] · act[r, k] with M = 128 ([B; B_lo]) and
-// N = R: a tcgen05 MMA takes time in proportion to N and the same time for
-// M = 64 as for M = 128, so B_lo rides along in M at no cost.
+// split operands: the activation rows carry x and x - tf32(x), the matrix tiles
+// are stored in FP32, and the splitter warps write each tile B together with
+// its remainder B_lo = B - tf32(B) into TMEM, so A_hi·B + A_hi·B_lo + A_lo·B +
+// A_lo·B_lo keeps FP32 accuracy ("3xTF32", the A_lo·B_lo term comes free with
+// the row split).  Its MMA runs the other way round, D[n, r] = Σ_k [B; B_lo][n, k]
+// · act[r, k] with M = 128 ([B; B_lo], the A operand in TMEM) and N = R: a
+// tcgen05 MMA takes time in proportion to N and the same time for M = 64 as for
+// M = 128, so B_lo rides along in M at no cost.
 //
-// Kernel roles (one persistent CTA per SM, 256 threads):
-//   warp 0        bulk-copy producer (cp.async.bulk + mbarrier complete_tx)
-//   warp 1        TMEM owner and MMA issuer (tcgen05.mma kind::f16 or kind::tf32,
-//                 FP32 accumulate); the converged warp runs the loop and
-//                 elect.sync issues, which keeps its operands warp-uniform
-//   warps 2..5    epilogue (tcgen05.ld, hi+lo combine, stores)
-//   warps 6..7    KIND 1 only: the B_lo splitter
-// Every term accumulates in one of kAccBufs TMEM buffers (round robin), so the
-// epilogue's FP32 sum of earlier terms overlaps the MMAs of the next ones.
-// Every wait is bounded; on a timeout the kernel raises an error flag, drains
-// its own copies and MMAs, frees TMEM and returns.
+// Kernel roles (one persistent CTA per SM; 7 warps for KIND 0, 11 for KIND 1):
+//   warp 0          bulk-copy producer (cp.async.bulk + mbarrier complete_tx)
+//   warp 1          TMEM owner and MMA issuer of the even terms (tcgen05.mma
+//                   kind::f16 or kind::tf32, FP32 accumulate); the converged warp
+//                   runs the loop and elect.sync issues, which keeps its operands
+//                   warp-uniform
+//   warps 2..5      epilogue (tcgen05.ld, hi+lo combine, stores)
+//   warps 6..9      KIND 1 only: the splitter, [B; B_lo] into TMEM
+//   last warp       MMA issuer of the odd terms (warp 6, or 10 for KIND 1)
+// Every term accumulates in its own TMEM buffer (round robin over the
+// accumulators), so the epilogue's FP32 sum of earlier terms overlaps the MMAs
+// of the next ones.  Every wait is bounded; on a timeout the kernel raises an
+// error flag, drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -249,10 +252,11 @@ __global__ void k_pack_act(const float* __restrict__ src, int64_t ld, int ids, c
 // KIND 1: FP32 data on the TF32 units with split operands ("3xTF32"): the
 //   activation rows carry x and x - tf32(x); the matrix tile is read once as
 //   tf32(S) (the MMA drops the low 13 mantissa bits) and once as the remainder
-//   S - tf32(S), which the splitter warps write next to it in shared memory, so
-//   D = x·tf32(S) + x·(S - tf32(S)) with both parts of x reaches FP32 accuracy.
-// Stage layout: [A: R rows | B: 64 rows | B_lo: 64 rows (KIND 1)], element size
-// es = 2 (KIND 0) or 4 (KIND 1), 64 contraction columns at most.
+//   S - tf32(S): the splitter warps write both into TMEM as the MMA's A operand
+//   [S; S - tf32(S)], so D = x·tf32(S) + x·(S - tf32(S)) with both parts of x
+//   reaches FP32 accuracy.
+// Stage layout: [A: R activation rows | B: 64 matrix rows], element size es = 2
+// (KIND 0) or 4 (KIND 1), 64 contraction columns at most.
 // MODE 0: coupling (outputs ŷ_t); MODE 1: leaf phase (outputs Z); MODE 2 (KIND 1
 // only): coupling without the stored S_b, whose rows the splitter warps evaluate
 // from the Chebyshev nodes (Eq. (h2_admissible)): only the activation tile is
