@@ -114,6 +114,28 @@ def _dist():
     return ws, rank, local
 
 
+def rank_rhs(n: int, m: int, seed: int, rank: int) -> np.ndarray:
+    """Rank `rank`'s m right-hand sides: its own column shard of the job's block
+    (weak scaling; the columns of a block product never interact)."""
+    return gaussian_rhs(n, m, seed + 1000 * rank)
+
+
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The slowest rank's value, on every rank (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gflops(flops_per_rank_step: float, seconds_per_step: float, world_size: int) -> float:
+    """Whole-job rate: the flops of every rank's step over the slowest rank's step time."""
+    return flops_per_rank_step * world_size / seconds_per_step / 1e9
+
+
 def _cpu_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -199,7 +221,7 @@ def run_ours(args):
     build_s = time.perf_counter() - t0
     info = G.info
     k = info["k"]
-    X = torch.from_numpy(gaussian_rhs(n, m, cfg["rhs_seed"] + 1000 * rank)).to(dev)
+    X = torch.from_numpy(rank_rhs(n, m, cfg["rhs_seed"], rank)).to(dev)
     Y = torch.zeros_like(X)
     flops_step = G.flops(m)
     stream = torch.cuda.current_stream()
@@ -228,10 +250,7 @@ def run_ours(args):
             P.h2_timing_enable(G.handle, False)
             phases, calls = P.h2_timing_query(G.handle, reset=True)
             phases = {kk: v / max(calls, 1) for kk, v in phases.items()}
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         return ms, phases
 
     dtype = args.dtype
@@ -239,23 +258,23 @@ def run_ours(args):
     clocks.start()
     ms, phases = timed(dtype, args.steps, args.warmup, timing=True)
     clk = clocks.stop()
-    value = flops_step * ws / (ms * 1e-3) / 1e9
+    value = job_gflops(flops_step, ms * 1e-3, ws)
 
     # FP64 product rate (fewer steps: it is ~50x slower)
     k64 = max(3, min(args.steps, 10))
     ms64, phases64 = timed("f64", k64, 3, timing=True)
-    value64 = flops_step * ws / (ms64 * 1e-3) / 1e9
+    value64 = job_gflops(flops_step, ms64 * 1e-3, ws)
 
     # BF16 tensor-core product rate
     msbf, phasesbf = timed("bf16", args.steps, 3, timing=True)
-    valuebf = flops_step * ws / (msbf * 1e-3) / 1e9
+    valuebf = job_gflops(flops_step, msbf * 1e-3, ws)
 
     # FP32 product with the matrix-free coupling (S_b evaluated from the nodes in the kernel)
     mf = None
     if dtype == "f32" and info["launches_tc"] > 0:
         kmf = max(3, min(args.steps, 10))
         msmf, phasesmf = timed("f32mf", kmf, 3, timing=True)
-        mf = {"value": round(flops_step * ws / (msmf * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+        mf = {"value": round(job_gflops(flops_step, msmf * 1e-3, ws), 3), "unit": "GFLOP/s",
               "ms_per_step": round(msmf, 4), "coupling_kernel_ms": round(phasesmf["coupling_kernel"], 4),
               "kernel_evaluations_per_step": int(info["n_adm"] * info["k"] * info["k"]),
               "s_bytes_not_read": int(info["n_adm"] * info["k"] * info["k"] * 4)}
@@ -313,8 +332,8 @@ def run_ours(args):
     for _ in range(ke):
         G.matmul(Xh, Yh, dtype=dtype)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / ke
-    e2e = {"value": round(flops_step * ws / e2e_s / 1e9, 3), "unit": "GFLOP/s",
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / ke, dist, dev)
+    e2e = {"value": round(job_gflops(flops_step, e2e_s, ws), 3), "unit": "GFLOP/s",
            "h2d_bytes_per_step": 2 * n * m * 8, "d2h_bytes_per_step": n * m * 8,
            "ms_per_step": round(e2e_s * 1e3, 3)}
 
@@ -322,7 +341,7 @@ def run_ours(args):
     solve = None
     if not args.no_solve:
         solve = {}
-        B = torch.from_numpy(gaussian_rhs(n, m, cfg["rhs_seed"] + 1000 * rank + 7)).to(dev)
+        B = torch.from_numpy(rank_rhs(n, m, cfg["rhs_seed"] + 7, rank)).to(dev)
         # name, product precision, refine (2 = reliable updates, 1 = restarted refinement), inner tol,
         # variant, preconditioner
         runs = (("mixed_f32", "f32", 2, 0.1, "columnwise", None),
@@ -349,7 +368,7 @@ def run_ours(args):
             r = G.block_cg(B, Xs, tol=1e-8, max_iter=cap, dtype=inner, refine=refine,
                            inner_tol=itol, check_every=4, variant=variant, precond=pc)
             torch.cuda.synchronize()
-            secs = time.perf_counter() - t0
+            secs = max_over_ranks(time.perf_counter() - t0, dist, dev)
             solve[name] = {"seconds": round(secs, 3), "status": r.status_name,
                            "iterations": int(r.iterations), "outer_steps": int(r.outer_steps),
                            "h2mm_calls": int(r.h2mm_calls),
