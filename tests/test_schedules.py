@@ -146,3 +146,30 @@ def test_schedule_limits(case):
     for s in (down, up):
         lens = np.diff(s["task_ptr"])
         assert np.all(lens[:-1] >= lens[1:])
+
+
+def test_schedule_argument_errors():
+    import ctypes as C
+
+    import paper_2509_17257_gb300.h2 as H
+    L = H.lib()
+    pts = np.ascontiguousarray(sphere_points(500, 3))
+    bp = H.BuildParams(3, 64, 2.0, 0.5, 0.0, 0, None)
+    h = C.c_void_p()
+    assert L.h2_tree_build(C.byref(bp), pts.ctypes.data, pts.shape[0], C.byref(h)) == 0
+    try:
+        nt, ns, ent = C.c_int32(), C.c_int32(), C.c_int32()
+        assert L.h2_tree_schedule(h, 2, C.byref(nt), C.byref(ns), C.byref(ent), None, None) == P.H2_E_BADARG
+        assert L.h2_tree_schedule(None, 0, C.byref(nt), C.byref(ns), C.byref(ent), None, None) == P.H2_E_BADARG
+        assert L.h2_tree_schedule(h, 0, None, C.byref(ns), C.byref(ent), None, None) == P.H2_E_BADARG
+        # sizes first, then the arrays: both calls agree
+        assert L.h2_tree_schedule(h, 1, C.byref(nt), C.byref(ns), C.byref(ent), None, None) == 0
+        ptr = np.zeros(nt.value + 1, dtype=np.int32)
+        steps = np.zeros((ns.value, 4), dtype=np.int32)
+        nt2, ns2 = C.c_int32(), C.c_int32()
+        assert L.h2_tree_schedule(h, 1, C.byref(nt2), C.byref(ns2), C.byref(ent), ptr.ctypes.data,
+                                  steps.ctypes.data) == 0
+        assert (nt2.value, ns2.value) == (nt.value, ns.value)
+        assert ptr[0] == 0 and ptr[-1] == ns.value and np.all(np.diff(ptr) > 0)
+    finally:
+        L.h2_tree_free(h)
