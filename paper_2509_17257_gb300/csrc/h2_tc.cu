@@ -419,10 +419,10 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
     } else if (warp == 1 || warp == tc_issuer2<KIND>()) {
         // ---------------- MMA issuers: driven by the stage metadata ----------------
         // Two warps take the terms by parity (term t uses stage t mod nst,
-        // accumulator t mod nacc and A slot t mod kASlots; nacc and kASlots are
-        // even, so each accumulator and slot stays with one issuer and its
-        // barriers complete in order), so one warp's waits overlap the other's
-        // MMAs.  Each converged warp runs its loop (waits and descriptors are
+        // accumulator t mod nacc and A slot t mod kASlots), so one warp's waits
+        // overlap the other's MMAs.  Each reuse of a stage, slot or accumulator
+        // waits for the consumer of its previous use, so every barrier's
+        // arrivals come in order whichever issuer commits them.  Each converged warp runs its loop (waits and descriptors are
         // warp-uniform); elect.sync hands each MMA and commit to one lane.
         const int j = warp == 1 ? 0 : 1;
         const int T = s_total;
