@@ -835,6 +835,14 @@ int tc_prepare() {
 int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st) {
     int a_bytes, stage_bytes, nstages;
     tc_stage_geometry(p.R, kind == 0 ? 2 : 4, &a_bytes, &stage_bytes, &nstages);
+    // A parity wait is exact only while its waiter cannot get two uses of a stage
+    // ahead (the protocol model in tests/test_pipeline_protocol.py checks this).
+    // The FP32 issuers wait on the in-order splitter, which keeps them in step.
+    // The BF16 issuers wait on the copies themselves: safe with an even stage
+    // count (each stage stays with one issuer) or with at least kAccBufs + 2
+    // stages (the accumulator wait for an issuer's previous term covers the
+    // stage's earlier use).  The BF16 counts here are 14, or 9 for R > 64.
+    if (kind == 0 && (nstages & 1) && nstages < kAccBufs + 2) nstages &= ~1;
     if (nstages < 2) { set_error("tensor-core stage does not fit in shared memory"); return H2_E_UNSUPPORTED; }
     p.a_stage_bytes = a_bytes;
     p.nstages = nstages;

@@ -58,8 +58,9 @@ class Hazard(AssertionError):
     pass
 
 
-def run_pipeline(T, nst=6, nacc=4, nslots=4, seed=0, mutate=None, max_steps=200000):
-    """Simulate one CTA on T terms; raises Hazard or returns normally."""
+def run_pipeline(T, nst=6, nacc=4, nslots=4, seed=0, mutate=None, max_steps=200000, splitter_warps=True):
+    """Simulate one CTA on T terms; raises Hazard or returns normally.  Without
+    splitter warps (the BF16 kernel) the issuers wait on the copies directly."""
     rng = random.Random(seed)
     full = [Barrier(1) for _ in range(nst)]
     split = [Barrier(4) for _ in range(nst)]
@@ -145,13 +146,13 @@ def run_pipeline(T, nst=6, nacc=4, nslots=4, seed=0, mutate=None, max_steps=2000
     def issuer(j):
         for it in range(j, T, 2):
             stage = it % nst
-            yield W(split[stage], (it // nst) & 1)
+            yield W(split[stage] if splitter_warps else full[stage], (it // nst) & 1)
             acc = it % nacc
             yield W(acce[acc], ((it // nacc) & 1) ^ (0 if mutate == "issuer_acce_parity" else 1))
             a = it % nslots
             if stage_term[stage] != it or not stage_landed[stage]:
                 raise Hazard(f"MMA of term {it} found stage {stage} holding {stage_term[stage]}")
-            if any(x != it for x in slot_term[a]):
+            if splitter_warps and any(x != it for x in slot_term[a]):
                 raise Hazard(f"MMA of term {it} found A slot {a} holding {slot_term[a]}")
             if acc_unread[acc]:
                 raise Hazard(f"MMA of term {it} overwrites accumulator {acc} before its epilogue read")
@@ -185,7 +186,8 @@ def run_pipeline(T, nst=6, nacc=4, nslots=4, seed=0, mutate=None, max_steps=2000
             acc_unread[acc] -= 1
             acce[acc].arrive()
 
-    agents = [producer()] + [splitter(w) for w in range(4)] + [issuer(0), issuer(1)] + [epilogue(e) for e in range(4)]
+    agents = ([producer()] + ([splitter(w) for w in range(4)] if splitter_warps else []) + [issuer(0), issuer(1)]
+              + [epilogue(e) for e in range(4)])
     state = [None] * len(agents)   # the pending request of each agent
     done = [False] * len(agents)
     for step in range(max_steps):
@@ -240,3 +242,28 @@ def test_planted_protocol_mistakes_are_caught(mutate):
             caught = True
             break
     assert caught, mutate
+
+
+# The BF16 kernel has no splitter: each issuer waits on the copy of its own
+# term, and the stage's previous use may belong to the other issuer.  A parity
+# wait is then safe only while that earlier copy is known to have landed.  It
+# is when the stage count is even (each stage stays with one issuer), and when
+# nst >= nacc + 2 (the issuer's accumulator wait for its previous term covers
+# the earlier copy).  The kernel's BF16 stage counts are 14, and 9 for R > 64.
+@pytest.mark.parametrize("nst", [4, 6, 7, 9, 14])
+def test_bf16_protocol_with_its_stage_counts(nst):
+    for T in (1, 7, 40):
+        for seed in range(12):
+            run_pipeline(T, nst=nst, seed=seed, splitter_warps=False)
+
+
+@pytest.mark.parametrize("nst", [3, 5])
+def test_bf16_protocol_unsafe_with_few_odd_stages(nst):
+    caught = False
+    for seed in range(80):
+        try:
+            run_pipeline(40, nst=nst, seed=seed, splitter_warps=False)
+        except Hazard:
+            caught = True
+            break
+    assert caught
