@@ -135,3 +135,37 @@ def test_every_export_has_argtypes():
     missing = [name for name in H.EXPORTS
                if name not in ("h2_last_error_string", "h2_version") and getattr(L, name).argtypes is None]
     assert not missing, missing
+
+
+def test_matrix_entry_points_reject_bad_arguments_before_any_device_work(h2lib):
+    """Null handles, bad sizes and bad parameters come back as statuses (and a
+    message), checked before any CUDA call, so this runs without a GPU."""
+    import ctypes as C
+
+    import paper_2509_17257_gb300.h2 as H
+    L = H.lib()
+    BAD, UNSUP = h2lib.H2_E_BADARG, h2lib.H2_E_UNSUPPORTED
+    x = np.zeros((4, 2))
+    for f in (L.h2_matmul, L.h2_matmul_transposed):
+        assert f(None, 1.0, x.ctypes.data, 2, x.ctypes.data, 2, 2, h2lib.H2_F64, None) == BAD
+    assert L.h2_info(None, C.byref(H.Info())) == BAD
+    assert L.h2_timing_enable(None, 1) == BAD
+    cp = H.CGParams(1e-8, 100, h2lib.H2_CG_COLUMNWISE, h2lib.H2_F64, 0, 0.1, 10, 1, 0, h2lib.H2_PRECOND_NONE, None)
+    res = H.CGResult()
+    assert L.h2_block_cg(None, x.ctypes.data, 2, x.ctypes.data, 2, 2, C.byref(cp), C.byref(res)) == BAD
+    gp = H.GMRESParams(1e-8, 100, 30, h2lib.H2_F64, h2lib.H2_PRECOND_NONE, 0, None)
+    assert L.h2_block_gmres(None, x.ctypes.data, 2, x.ctypes.data, 2, 2, C.byref(gp), C.byref(res)) == BAD
+    assert "null" in L.h2_last_error_string().decode()
+    pts = np.ascontiguousarray(sphere_points(50, 1))
+    h = C.c_void_p()
+    for params, code in ((H.BuildParams(3, 64, 0.0, 0.5, 0.0, 1, None), BAD),       # eta
+                         (H.BuildParams(3, 64, 2.0, -1.0, 0.0, 1, None), BAD),      # length
+                         (H.BuildParams(3, 64, 2.0, 0.5, np.nan, 1, None), BAD),    # sigma
+                         (H.BuildParams(6, 64, 2.0, 0.5, 0.0, 1, None), UNSUP),     # q
+                         (H.BuildParams(3, 65, 2.0, 0.5, 0.0, 1, None), UNSUP)):    # leaf size
+        assert L.h2_build(C.byref(params), pts.ctypes.data, 50, C.byref(h)) == code
+        assert not h.value
+    ok = H.BuildParams(3, 64, 2.0, 0.5, 0.0, 1, None)
+    assert L.h2_build(C.byref(ok), None, 50, C.byref(h)) == BAD
+    assert L.h2_build(C.byref(ok), pts.ctypes.data, 0, C.byref(h)) == BAD
+    assert L.h2_build(C.byref(ok), pts.ctypes.data, 50, None) == BAD
