@@ -42,9 +42,84 @@ FALLBACK_HBM_GBS = 6800.0
 SM_COUNT = 152
 FP32_FMA_PER_CLK_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_tc_gemm<0,1> launch (FP32 coupling)
-# on precision_n65536 (734.359 MB + 20.040 MB); valid for the kernel as of that capture only
-TC_F32_COUPLING_DRAM_BYTES = 754399488
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_tc_gemm<0,1> launch (the FP32
+# coupling kernel) on precision_n65536, with the SHA-256 (first 16 hex digits) of the kernel's
+# sources when the counters were taken.  The line reports the bytes only while the sources
+# still hash to that value; after a change to the kernel they are stale and `traffic` is null.
+TC_F32_COUPLING_DRAM = {
+    "bytes": 754399488,  # 734.359 MB read + 20.040 MB written
+    "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+               "--clock-control none -k regex:k_tc_gemm<(int)0, (int)1> -c 1 python bench.py --steps 2 "
+               "--warmup 1 --no-solve --no-cpu-baseline",
+    "sources": ("paper_2509_17257_gb300/csrc/h2_tc.cu", "paper_2509_17257_gb300/csrc/h2_async.cuh"),
+    "source_sha16": None,
+}
+
+
+def _sources_sha16(paths) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU baseline."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def workload_counts_from_info(info) -> dict:
+    return {key: int(info[key]) for key in ("n_clusters", "n_adm", "n_near", "nnz_near", "depth")}
+
+
+def bench_config(workload: str, cfg: dict, counts: dict, ws: int) -> dict:
+    """The `config` dict of the bench line; both arms build it from the workload and the
+    tree counts only, so the two lines name the same configuration."""
+    k = cfg["q"] ** 3
+    f32_bytes = 4 * (cfg["n"] * k + counts["n_clusters"] * k * k + counts["n_adm"] * k * k + counts["nnz_near"])
+    return {"workload": workload, "n": cfg["n"], "q": cfg["q"], "k": k, "m_per_gpu": cfg["m"], "leaf": cfg["leaf"],
+            "eta": cfg["eta"], "kernel": "exp(-r/0.5)+1e-2*I", "parallelism": f"column shards x{ws}",
+            "l2": f"inputs larger than L2 (matrix data {f32_bytes / 1e9:.2f} GB FP32, "
+                  f"{2 * f32_bytes / 1e9:.2f} GB FP64)",
+            **counts}
+
+
+def product_bytes(n, k, m, nc, n_adm, nnz_near, elt, elt_x=8, elt_acc=4):
+    """Algorithmic bytes of one product: every matrix once (V twice: forward and backward),
+    X read and Y read and written once, and the coefficient blocks x̂ and ŷ each written and
+    read once."""
+    return (elt * (2 * n * k + (nc - 1) * k * k + n_adm * k * k + nnz_near) + elt_x * 3 * n * m
+            + 4 * nc * k * m * elt_acc)
+
+
+def phase_bytes(n, k, m, nc, n_leaves, n_adm, nnz_near, elt):
+    """Algorithmic bytes of each phase of the tensor-core FP32/BF16 product, as timed by
+    h2_timing (coefficients, gathered X and leaf results in FP32; the caller's X, Y in FP64)."""
+    a = 4  # coefficient / gathered-block element size
+    return {
+        "gather": 8 * n * m + a * n * m,
+        "leaf_fwd": elt * (n * k + (nc - 1) * k * k) + a * n * m + a * nc * k * m,  # upward pass fused in
+        "coupling": elt * n_adm * k * k + 2 * a * nc * k * m,
+        "down": elt * (nc - 1) * k * k + 2 * a * nc * k * m,
+        "leaf_bwd_near": (elt * (n * k + nnz_near) + a * n_leaves * k * m + 2 * a * n * m
+                          + a * n * m + 8 * n * m + 2 * 8 * n * m),  # leaf kernel, then the scatter into Y
+    }
 
 
 def _peaks():
@@ -143,8 +218,15 @@ def _cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
+def _oracle_flops(cfg, c) -> float:
+    k = cfg["q"] ** 3
+    return cfg["m"] * (4.0 * c["n"] * k + 4.0 * (c["n_clusters"] - 1) * k * k + 2.0 * c["n_adm"] * k * k
+                       + 2.0 * c["nnz_near"] + 2.0 * c["n"])
+
+
 def oracle_products(cfg, steps: int, warmup: int):
-    """Time the FP64 CPU oracle's product on the workload (build untimed)."""
+    """Time the FP64 CPU oracle's product on the workload (build untimed).
+    Returns (flops per product, list of seconds, build seconds, oracle matrix)."""
     from oracle import h2_oracle as O
 
     pts = sphere_points(cfg["n"], cfg["point_seed"])
@@ -160,36 +242,99 @@ def oracle_products(cfg, steps: int, warmup: int):
         t0 = time.perf_counter()
         O.h2mm(H, 1.0, X)
         times.append(time.perf_counter() - t0)
-    c = H.counts()
-    k = cfg["q"] ** 3
-    flops = cfg["m"] * (4.0 * c["n"] * k + 4.0 * (c["n_clusters"] - 1) * k * k + 2.0 * c["n_adm"] * k * k
-                        + 2.0 * c["nnz_near"] + 2.0 * c["n"])
-    return flops, times, build_s
+    return _oracle_flops(cfg, H.counts()), times, build_s, H
+
+
+_SINGLE_THREAD_SNIPPET = """
+import json, statistics, sys, time
+sys.path.insert(0, {root!r})
+from oracle import h2_oracle as O
+from workloads import CONFIGS, gaussian_rhs, sphere_points
+cfg = CONFIGS["fp64_n4096"]
+H = O.H2Matrix(sphere_points(cfg["n"], cfg["point_seed"]), q=cfg["q"], leaf_size=cfg["leaf"], eta=cfg["eta"],
+               sigma=cfg["sigma"], length=cfg["length"])
+X = gaussian_rhs(cfg["n"], cfg["m"], cfg["rhs_seed"])
+O.h2mm(H, 1.0, X)
+ts = []
+for _ in range(5):
+    t0 = time.perf_counter(); O.h2mm(H, 1.0, X); ts.append(time.perf_counter() - t0)
+print(json.dumps({{"median_s": statistics.median(ts), "counts": H.counts()}}))
+"""
+
+
+def cpu_baseline_extras(H2, cfg2, fp64_iterations):
+    """The oracle's block CG and single-thread figures beside the product rate:
+    the block CG to 1e-8 on the n = 4096 workload (full solve), the per-iteration
+    cost on the bench workload (3 iterations, extrapolated to the iteration count of
+    the GPU FP64 column-wise solve when one ran), and the n = 4096 product on one
+    thread (a child process with every BLAS / OpenMP pool at one thread)."""
+    from oracle import h2_oracle as O
+
+    out = {}
+    c1 = CONFIGS["fp64_n4096"]
+    H1 = O.H2Matrix(sphere_points(c1["n"], c1["point_seed"]), q=c1["q"], leaf_size=c1["leaf"], eta=c1["eta"],
+                    sigma=c1["sigma"], length=c1["length"])
+    B1 = gaussian_rhs(c1["n"], c1["m"], c1["rhs_seed"] + 7)
+    t0 = time.perf_counter()
+    r1 = O.block_cg(lambda Z: O.h2mm(H1, 1.0, Z), B1, tol=1e-8, max_iter=5000)
+    out["block_cg_fp64_n4096"] = {"seconds": round(time.perf_counter() - t0, 3), "iterations": int(r1.iterations),
+                                  "status": r1.status, "m": c1["m"], "kind": "measured"}
+    B2 = gaussian_rhs(cfg2["n"], cfg2["m"], cfg2["rhs_seed"] + 7)
+    t0 = time.perf_counter()
+    r2 = O.block_cg(lambda Z: O.h2mm(H2, 1.0, Z), B2, tol=1e-8, max_iter=3)
+    per_it = (time.perf_counter() - t0) / max(int(r2.iterations), 1)
+    row = {"seconds_per_iteration": round(per_it, 4), "iterations_timed": int(r2.iterations), "m": cfg2["m"]}
+    if fp64_iterations:
+        row.update(iterations=int(fp64_iterations), seconds=round(per_it * fp64_iterations, 1),
+                   kind="extrapolated: oracle seconds per iteration x the GPU FP64 column-wise solve's "
+                        "iteration count")
+    out[f"block_cg_fp64_n{cfg2['n']}"] = row
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", _SINGLE_THREAD_SNIPPET.format(root=ROOT)], env=env,
+                           capture_output=True, text=True, timeout=600)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        f1 = _oracle_flops(c1, d["counts"])
+        out["single_thread_n4096"] = {"value": round(f1 / d["median_s"] / 1e9, 3), "unit": "GFLOP/s",
+                                      "cores": 1, "sample": "median of 5 FP64 oracle products at n=4096, q=3, m=8"}
+    except Exception as e:  # reported, not fatal: the main baseline stands
+        out["single_thread_n4096"] = {"error": str(e)[:200]}
+    return out
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    cfg = CONFIGS[WORKLOAD]
-    flops, times, build_s = oracle_products(cfg, args.steps, args.warmup)
-    t = sum(times) / len(times)
+    workload = args.workload
+    cfg = CONFIGS[workload]
+    flops, times, build_s, H = oracle_products(cfg, args.steps, args.warmup)
+    t = statistics.median(times)
     v = flops / t / 1e9
     cores = _cpu_cores()
-    sample = (f"{args.steps} FP64 oracle products at n={cfg['n']}, q={cfg['q']}, m={cfg['m']} after "
-              f"{args.warmup} warm-up; oracle build {build_s:.1f} s untimed")
+    c = H.counts()
+    sample = (f"median of {args.steps} FP64 oracle products at n={cfg['n']}, q={cfg['q']}, m={cfg['m']} after "
+              f"{args.warmup} warm-up; oracle build {build_s:.1f} s untimed; CPU {_cpu_model()}")
     line = {
-        "metric": METRIC, "value": round(v, 3), "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD, "n": cfg["n"], "q": cfg["q"], "m": cfg["m"], "leaf": cfg["leaf"],
-                   "eta": cfg["eta"], "kernel": "exp(-r/0.5)+1e-2*I", "parallelism": "cpu"},
+        "metric": _metric(workload, cfg), "value": round(v, 3), "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": bench_config(workload, cfg, {key: int(c[key]) for key in
+                                               ("n_clusters", "n_adm", "n_near", "nnz_near", "depth")}, args.gpus),
         "cpu_baseline": {"value": round(v, 3), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": _cpu_model()},
         "e2e": {"value": round(v, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _metric(workload, cfg):
+    if workload == WORKLOAD:
+        return METRIC
+    return (f"H2MM GFLOP/s (n={cfg['n']}, q={cfg['q']}, m={cfg['m']} per GPU; block-CG time to 1e-8 mixed vs FP64 "
+            f"reported alongside)")
 
 
 def run_ours(args):
@@ -210,8 +355,7 @@ def run_ours(args):
     cfg = CONFIGS[workload]
     n, m = cfg["n"], cfg["m"]
     peaks, peak_kind = _peaks()
-    metric = METRIC if workload == WORKLOAD else (
-        f"H2MM GFLOP/s (n={n}, q={cfg['q']}, m={m} per GPU; block-CG time to 1e-8 mixed vs FP64 reported alongside)")
+    metric = _metric(workload, cfg)
 
     pts = sphere_points(n, cfg["point_seed"])
     t0 = time.perf_counter()
@@ -306,18 +450,42 @@ def run_ours(args):
                 "kernel": "k_coupling", "peak_source": alu_note}
     else:
         achieved = coup_bytes / (coup_ms * 1e-3) / 1e9
-        # DRAM bytes (read + write) of one launch of the coupling kernel on this workload,
-        # from the ncu capture summarised in profiles/coupling_and_transfer_kernels_n65536_full.md;
-        # only for the FP32 tensor-core kernel and the workload it was taken on
-        measured = TC_F32_COUPLING_DRAM_BYTES if (tensor_path and dtype == "f32" and
-                                                  args.workload == WORKLOAD) else None
+        # DRAM bytes (read + write) of one launch of the FP32 tensor-core coupling kernel on this
+        # workload from an earlier ncu capture, reported only while the kernel's sources are the
+        # ones it was taken on
+        cap = TC_F32_COUPLING_DRAM
+        sha_now = _sources_sha16(cap["sources"])
+        fresh = sha_now == cap["source_sha16"]
+        applies = tensor_path and dtype == "f32" and args.workload == WORKLOAD
+        measured = cap["bytes"] if (applies and fresh) else None
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4), "traffic": measured,
                 "kernel": "k_tc_gemm<0,1> (coupling, split TF32)" if tensor_path else "k_coupling",
                 "peak_source": f"{peak_kind} hbm_gbs"}
+        if applies:
+            roof["traffic_source"] = {"capture": cap["capture"], "bytes": cap["bytes"],
+                                      "kernel_source_sha16_at_capture": cap["source_sha16"],
+                                      "kernel_source_sha16_now": sha_now,
+                                      "state": "current" if fresh else "stale: kernel changed since the capture"}
     roof["algorithmic_bytes_per_launch"] = int(coup_bytes)
     roof["algorithmic_flops_per_launch"] = coup_flops
     roof["ms_per_launch"] = round(coup_ms, 4)
+
+    # the whole product against its own HBM roofline, and each timed phase against its bytes
+    n_leaves = int(info["n_leaves"])
+    pbytes = product_bytes(n, k, m, nc, n_adm, info["nnz_near"], elt)
+    roof_product = {"algorithmic_bytes": int(pbytes), "ms": round(ms, 4),
+                    "achieved_GBps": round(pbytes / (ms * 1e-3) / 1e9, 1), "peak": hbm_peak,
+                    "frac": round(pbytes / (ms * 1e-3) / 1e9 / hbm_peak, 4),
+                    "formula": "elt*(2nk + (N_c-1)k^2 + N_adm k^2 + nnz_near) + 8*3nm + 4*N_c*k*m*4"}
+    per_phase = None
+    if tensor_path:
+        per_phase = {}
+        for ph, b in phase_bytes(n, k, m, nc, n_leaves, n_adm, info["nnz_near"], elt).items():
+            t = phases.get(ph)
+            if t and t > 0:
+                per_phase[ph] = {"ms": round(t, 4), "algorithmic_bytes": int(b),
+                                 "frac_hbm": round(b / (t * 1e-3) / 1e9 / hbm_peak, 4)}
 
     # end to end through the C ABI on pinned host buffers
     Xh = X.cpu().pin_memory()
@@ -391,22 +559,24 @@ def run_ours(args):
     cpu = None
     # the oracle holds every block in host memory: timed on the default workload only
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and workload == WORKLOAD:
-        c_flops, c_times, c_build = oracle_products(cfg, steps=3, warmup=0)
-        ct = sum(c_times) / len(c_times)
+        c_flops, c_times, c_build, H2o = oracle_products(cfg, steps=5, warmup=0)
+        ct = statistics.median(c_times)
         cpu = {"value": round(c_flops / ct / 1e9, 3), "unit": "GFLOP/s", "cores": _cpu_cores(), "kind": "oracle",
-               "sample": f"3 FP64 oracle products at n={n}, q={cfg['q']}, m={m}; oracle build {c_build:.1f} s "
-                         f"untimed"}
+               "cpu_model": _cpu_model(),
+               "sample": f"median of 5 FP64 oracle products at n={n}, q={cfg['q']}, m={m}; oracle build "
+                         f"{c_build:.1f} s untimed"}
+        fp64_it = None
+        if solve and solve.get("fp64", {}).get("status") == "ok":
+            fp64_it = solve["fp64"]["iterations"]
+        cpu.update(cpu_baseline_extras(H2o, cfg, fp64_it))
+        del H2o
 
     line = {
         "metric": metric, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "config": {"workload": workload, "n": n, "q": cfg["q"], "k": k, "m_per_gpu": m, "leaf": cfg["leaf"],
-                   "eta": cfg["eta"], "kernel": "exp(-r/0.5)+1e-2*I", "parallelism": f"column shards x{ws}",
-                   "l2": f"inputs larger than L2 (matrix data {info['bytes_f32'] / 1e9:.2f} GB FP32, "
-                         f"{info['bytes_f64'] / 1e9:.2f} GB FP64)",
-                   "n_clusters": nc, "n_adm": n_adm, "n_near": info["n_near"], "nnz_near": info["nnz_near"],
-                   "depth": info["depth"], "build_s": round(build_s, 2)},
+        "config": bench_config(workload, cfg, workload_counts_from_info(info), ws),
+        "build_s": round(build_s, 2),
         "gflop_per_step": round(flops_step / 1e9, 4),
         "h2mm_f64": {"value": round(value64, 3), "unit": "GFLOP/s", "ms_per_step": round(ms64, 4)},
         "phases_ms": {kk: round(v, 4) for kk, v in phases.items()},
@@ -416,6 +586,8 @@ def run_ours(args):
                       "phases_ms": {kk: round(v, 4) for kk, v in phasesbf.items()}},
         "h2mm_f32_matrix_free": mf,
         "roofline": roof,
+        "roofline_product": roof_product,
+        "phases_roofline": per_phase,
         "e2e": e2e,
         "solve": solve,
         "cpu_baseline": cpu,

@@ -15,9 +15,12 @@
  *  - Dense blocks are row-major n×m arrays of double with a leading
  *    dimension (ld >= m, in elements); row i belongs to point i in the
  *    caller's original order.  A pointer may be device memory or host
- *    memory (pageable or pinned); host blocks are staged through device
- *    memory on the call's stream and the call returns after the result is
- *    back on the host.
+ *    memory.  Pinned host memory that the device can address (mapped, as
+ *    cudaHostAlloc / cudaHostRegister give on this platform) is read and
+ *    updated in place by the product's kernels over the host link, with no
+ *    staging copy; pageable host blocks are copied through device buffers
+ *    on the call's stream.  Either way a call given a host block returns
+ *    after the result is complete on the host.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls on
  *    device pointers are asynchronous with respect to the host unless stated.
  *  - The library owns every h2_matrix / h2_tree it returns; free them with
@@ -138,7 +141,13 @@ int h2_matmul_transposed(h2_matrix* A, double alpha, const double* X, int64_t ld
  * never calls cudaMalloc, cudaFree or any allocating routine.
  *
  * Same operation and arguments as h2_matmul (Y <- Y + alpha·A·X), except:
- *  - X and Y must be device memory (no host staging); dtype H2_F64 or H2_F32.
+ *  - X and Y must be device memory (no host staging); dtype H2_F64 or H2_F32;
+ *    m <= 2^20 (H2_E_BADARG beyond).
+ *  - Both precisions run the product on the CUDA cores (the FP32 product of
+ *    h2_matmul runs split-TF32 tensor cores where they are built, whose
+ *    operand tiles need more scratch): the result equals h2_matmul's to the
+ *    precision's tolerance (1e-12 relative for FP64, 1e-5 for FP32), not bit
+ *    for bit, and the FP32 product is slower than h2_matmul's.
  *  - Its scratch (X gathered into cluster order, x̂ and ŷ of every cluster) is a
  *    fixed array of H2_NOALLOC_SCRATCH_BYTES (32 MiB) compiled into the
  *    library, reserved on every GPU that loads it until the process exits.
@@ -149,7 +158,10 @@ int h2_matmul_transposed(h2_matrix* A, double alpha, const double* X, int64_t ld
  *    fewer columns per call.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) and caches it; make that first call before any
- *    stream capture.
+ *    stream capture.  The cache remembers the context it was filled in; after
+ *    cudaDeviceReset the next call looks the address up again (matrices
+ *    built before the reset are invalid anyway: their memory went with the
+ *    old context).
  *  - All calls share the one array, which keeps the last call's contents.
  *    Each call first clears the small region of counters and flags its
  *    transfer passes start from (a stream-ordered memset, not an allocation)
@@ -370,6 +382,28 @@ int h2_tree_free(h2_tree* T);
  * Errors: H2_E_BADARG (null T or counts, which not 0 or 1). */
 int h2_tree_schedule(const h2_tree* T, int32_t which, int32_t* ntasks, int32_t* nsteps, int32_t* entries,
                      int32_t* task_ptr, int32_t* steps);
+
+/* ---- limits (process-wide; for callers that budget device memory, and for
+ * tests of the failure paths) ------------------------------------------------
+ * h2_set_alloc_limit: cap on the device bytes that all live matrices of the
+ * process hold for their stored data (what h2_build allocates, and the
+ * block-Jacobi factors a preconditioned solve adds); 0 (the default) removes
+ * the cap.  An allocation past the cap fails as an out-of-memory cudaMalloc
+ * would: the call returns H2_E_OOM, and a failed h2_build releases everything
+ * it had allocated.  Workspace grown by products and solves is not counted.
+ * h2_alloc_bytes: the bytes currently held that way (the count the cap is
+ * checked against).
+ * h2_set_wait_limit: poll limit of the bounded device-side waits on another
+ * CTA's ready flag (the FP64 downward transfer pass, Alg. "forward/backward"
+ * in one launch); each poll sleeps about 32 ns.  0 restores the default (2^24
+ * polls); a negative value makes every such wait give up at once without
+ * looking at the flag, so that a test can exercise the timeout path: the
+ * product's kernel then returns early and the next call on that matrix
+ * returns H2_E_TIMEOUT (its result is invalid).  Errors: H2_E_BADARG
+ * (negative bytes, null pointer). */
+int h2_set_alloc_limit(int64_t bytes);
+int h2_alloc_bytes(int64_t* bytes);
+int h2_set_wait_limit(int64_t polls);
 
 /* Description of the last error on the calling thread ("" if none). */
 const char* h2_last_error_string(void);

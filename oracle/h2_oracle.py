@@ -17,6 +17,8 @@ H²-matrices"):
 * Sec. 3, Alg. "H2_mvm" (forward transformation, multiplication phase
   "fast_addeval", backward transformation) with the coefficient blocks of
   Sec. 4 (x̂_s, ŷ_t in K^{k×m})  -> :func:`h2mm`
+* the same product with BF16 operands and FP32 accumulation, the error
+  budget of the BF16 product (not in the paper) -> :func:`h2mm_bf16`
 * Sec. 5.1, Alg. "block CG" (per-column α_i, β_i, γ_i) -> :func:`block_cg`
 * the same recurrences with m×m Gram matrices in place of the per-column
   scalars (O'Leary's block CG; not in the paper)      -> :func:`block_cg_gram`
@@ -69,6 +71,9 @@ __all__ = [
     "H2Rows",
     "block_gmres",
     "GMRESResult",
+    "round_bf16",
+    "BF16_OPERANDS",
+    "h2mm_bf16",
 ]
 
 
@@ -423,6 +428,106 @@ def h2mm(H: H2Matrix, alpha: float, X: np.ndarray, Y: np.ndarray | None = None,
     _fast_addeval(H, alpha, H.btree, xhat, yhat, X, Yo, transposed)
     _backward(H, H.root, Yo, yhat)
     Yo += (alpha * H.sigma) * X
+    return Yo[:, 0] if squeeze else Yo
+
+
+# ---------------------------------------------------------------------------
+# BF16 error budget: the same product with BF16 operands, FP32 accumulation
+# ---------------------------------------------------------------------------
+def round_bf16(a) -> np.ndarray:
+    """Round to the nearest bfloat16 value, ties to even, returned as FP64.
+
+    bfloat16 keeps 8 significant bits (the implicit leading one and seven
+    stored ones) and the FP32 exponent range.  Writing a = f·2^e with
+    0.5 <= |f| < 1, the rounded value is rint(f·2^8)·2^(e-8), where rint
+    rounds half to even; a carry to 2^8 lands on the next power of two, as it
+    should.  The value is rounded once, from FP64 (no FP32 step, whose own
+    rounding could move a value onto a bfloat16 midpoint).  Valid for
+    magnitudes in the normal range (>= 2^-126); zero stays zero."""
+    a = np.asarray(a, dtype=np.float64)
+    f, e = np.frexp(a)
+    return np.ldexp(np.rint(np.ldexp(f, 8)), e - 8)
+
+
+#: operands the BF16 error budget rounds by default: the leaf bases (forward
+#: "Vf" and backward "Vb"), the transfer matrices "E", the couplings "S", the
+#: nearfield blocks "G" and the input block "X"
+BF16_OPERANDS = ("Vf", "Vb", "E", "S", "G", "X")
+
+
+def h2mm_bf16(H: H2Matrix, alpha: float, X: np.ndarray, Y: np.ndarray | None = None,
+              rounded=BF16_OPERANDS, transposed: bool = False) -> np.ndarray:
+    """Y + α·A·X (or Aᵀ) with the named operands rounded to bfloat16 and every
+    matrix product accumulated in FP32: the BF16 error budget of the product.
+
+    The steps are those of :func:`h2mm` (Alg. "H2_mvm": forward
+    transformation, coupling and nearfield blocks, backward transformation)
+    on a plain per-operand reading of "BF16 operands, FP32 accumulation":
+
+    * each operand named in ``rounded`` is rounded to BF16 once
+      (:func:`round_bf16`); "V" names both "Vf" and "Vb";
+    * the coefficient blocks x̂_s, ŷ_t and the leaf results stay FP32: they
+      are the accumulators, not operands read from memory;
+    * every product is a float32 matmul (a product of two BF16 values is
+      exact in FP32; the sums round in FP32);
+    * α is applied once at the end and the shift uses the FP64 X:
+      Y + α·(Z + σX) in FP64, where Z is the FP32 result.
+
+    With ``rounded=()`` this is the product in FP32 arithmetic."""
+    ops = set()
+    for name in rounded:
+        ops.update(("Vf", "Vb") if name == "V" else (name,))
+    unknown = ops - set(BF16_OPERANDS)
+    if unknown:
+        raise ValueError(f"unknown operand names {sorted(unknown)}")
+    f32 = np.float32
+
+    def op(name, a):
+        return (round_bf16(a) if name in ops else np.asarray(a, dtype=np.float64)).astype(f32)
+
+    X = np.asarray(X, dtype=np.float64)
+    squeeze = X.ndim == 1
+    if squeeze:
+        X = X[:, None]
+    m = X.shape[1]
+    Xo = op("X", X)
+    xhat = {}
+
+    def forward(s):
+        if s.is_leaf:
+            xhat[s.id] = op("Vf", H.V[s.id]).T @ Xo[s.idx]
+        else:
+            acc = np.zeros((H.k, m), dtype=f32)
+            for s2 in s.sons:
+                forward(s2)
+                acc = acc + op("E", H.E[s2.id]).T @ xhat[s2.id]
+            xhat[s.id] = acc
+
+    forward(H.root)
+    yhat = {c.id: np.zeros((H.k, m), dtype=f32) for c in H.clusters}
+    Z = np.zeros((H.n, m), dtype=f32)
+    for b in H.adm:
+        if transposed:
+            yhat[b.s.id] = yhat[b.s.id] + op("S", b.S).T @ xhat[b.t.id]
+        else:
+            yhat[b.t.id] = yhat[b.t.id] + op("S", b.S) @ xhat[b.s.id]
+    for b in H.near:
+        if transposed:
+            Z[b.s.idx] = Z[b.s.idx] + op("G", b.G).T @ Xo[b.t.idx]
+        else:
+            Z[b.t.idx] = Z[b.t.idx] + op("G", b.G) @ Xo[b.s.idx]
+
+    def backward(t):
+        if t.is_leaf:
+            Z[t.idx] = Z[t.idx] + op("Vb", H.V[t.id]) @ yhat[t.id]
+        else:
+            for t2 in t.sons:
+                yhat[t2.id] = yhat[t2.id] + op("E", H.E[t2.id]) @ yhat[t.id]
+                backward(t2)
+
+    backward(H.root)
+    Yo = np.zeros((H.n, m)) if Y is None else np.array(Y, dtype=np.float64).reshape(H.n, m)
+    Yo = Yo + alpha * (Z.astype(np.float64) + H.sigma * X)
     return Yo[:, 0] if squeeze else Yo
 
 

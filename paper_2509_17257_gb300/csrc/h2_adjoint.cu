@@ -130,6 +130,12 @@ int h2_coupling_set(h2_matrix* A, const double* S, void* stream) {
         if (D.has_tf32 && (rc = launch_pack_tiles(D.d_tiles, D.n_s_tiles, (const double*)A->f64.S, D.mat32, 4, st)))
             return rc;
     }
+    if (D.t_built) {  // the S_bᵀ tiles of the product with Aᵀ come first in its descriptor list
+        if (D.matT && (rc = launch_pack_tiles(D.d_tilesT, D.n_s_tiles, (const double*)A->f64.S, D.matT, 2, st)))
+            return rc;
+        if (D.matT32 && (rc = launch_pack_tiles(D.d_tilesT, D.n_s_tiles, (const double*)A->f64.S, D.matT32, 4, st)))
+            return rc;
+    }
     H2_CUDA_TRY(cudaStreamSynchronize(st));
     return 0;
 }

@@ -1,6 +1,7 @@
 // The extern "C" entry points declared in include/h2.h.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <new>
@@ -36,17 +37,46 @@ const void* mapped_host_pointer(const void* p) {
     return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
+namespace {
+constexpr long long kDefaultWaitLimit = 1ll << 24;
+std::atomic<long long> g_wait_limit{kDefaultWaitLimit};
+std::atomic<int64_t> g_alloc_limit{0};  // 0: no cap
+std::atomic<int64_t> g_alloc_live{0};   // bytes held through device_alloc by live matrices
+}  // namespace
+
+long long wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+
+// Every allocation of a matrix's stored data (h2_build, the block-Jacobi
+// factors) comes through here: it is counted against h2_set_alloc_limit and
+// released with the matrix.
 int device_alloc(h2_matrix* A, void** ptr, size_t bytes) {
+    const int64_t cap = g_alloc_limit.load();
+    const int64_t live = g_alloc_live.fetch_add((int64_t)bytes) + (int64_t)bytes;
+    if (cap > 0 && live > cap) {
+        g_alloc_live.fetch_sub((int64_t)bytes);
+        set_error("device allocation of " + std::to_string(bytes) + " bytes refused: the library's cap of " +
+                  std::to_string(cap) + " bytes (h2_set_alloc_limit) would be exceeded");
+        return H2_E_OOM;
+    }
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
+        g_alloc_live.fetch_sub((int64_t)bytes);
         cudaGetLastError();
         set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? H2_E_OOM : H2_E_CUDA;
     }
     A->allocations.push_back(p);
+    A->alloc_bytes += (int64_t)bytes;
     *ptr = p;
     return 0;
+}
+
+void release_allocations(h2_matrix* A) {
+    for (void* p : A->allocations) cudaFree(p);
+    A->allocations.clear();
+    g_alloc_live.fetch_sub(A->alloc_bytes);
+    A->alloc_bytes = 0;
 }
 
 }  // namespace h2
@@ -75,7 +105,7 @@ void free_matrix(h2_matrix* A) {
         if (r.k1) cudaEventDestroy(r.k1);
     }
     for (auto e : A->timing.free_events) cudaEventDestroy(e);
-    for (void* p : A->allocations) cudaFree(p);
+    h2::release_allocations(A);
     if (A->ws.base) cudaFree(A->ws.base);
     if (A->ws.stage_x) cudaFree(A->ws.stage_x);
     if (A->ws.stage_y) cudaFree(A->ws.stage_y);
@@ -295,6 +325,23 @@ int h2_matmul_transposed(h2_matrix* A, double alpha, const double* X, int64_t ld
 int h2_block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
                 const h2_cg_params* params, h2_cg_result* res) {
     return h2::block_cg(A, B, ldb, X, ldx, m, params, res);
+}
+
+int h2_set_alloc_limit(int64_t bytes) {
+    if (bytes < 0) { h2::set_error("h2_set_alloc_limit: bytes must be >= 0"); return H2_E_BADARG; }
+    h2::g_alloc_limit.store(bytes);
+    return 0;
+}
+
+int h2_alloc_bytes(int64_t* bytes) {
+    if (!bytes) { h2::set_error("h2_alloc_bytes: null argument"); return H2_E_BADARG; }
+    *bytes = h2::g_alloc_live.load();
+    return 0;
+}
+
+int h2_set_wait_limit(int64_t polls) {
+    h2::g_wait_limit.store(polls == 0 ? h2::kDefaultWaitLimit : (long long)polls);
+    return 0;
 }
 
 int h2_block_gmres(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,

@@ -636,7 +636,7 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     tiles.reserve(A->n_adm + NL + A->n_near);
     int64_t off = 0;
     auto add = [&](int64_t src, int n, int kk, int ld, int np, int kp) {
-        tiles.push_back(TcPackTile{src, off, n, kk, ld, np, kp});
+        tiles.push_back(TcPackTile{src, off, n, kk, ld, np, kp, 0});
         const int64_t b = (int64_t)np * kp * 2;
         off += b;
         return off - b;
@@ -754,6 +754,135 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     UP(D.leaf_kdim, leaf_kdim);
 #undef UP
     D.built = true;
+    return 0;
+}
+
+// The tensor-core product with Aᵀ (Alg. "H2_mvm" with the roles of row and
+// column clusters swapped: ŷ_s = Σ_{b=(t,s)} S_bᵀ x̂_t, and y|_ŝ += G_bᵀ x|_t̂ on
+// the inadmissible blocks; W = V, so the transfer passes are those of A).  Its
+// tiles hold S_bᵀ, V_t and G_bᵀ in the layout of build_tc (V repeated so one
+// base pointer serves the leaf phase), its coupling list runs over column
+// clusters and its leaf list over column leaves.
+int build_tc_transposed(h2_matrix* A, cudaStream_t st) {
+    TcData& D = A->tc;
+    if (D.t_built) return 0;
+    if (!D.built) { set_error("tensor-core tiles not built"); return H2_E_UNSUPPORTED; }
+    const Tree& T = A->T;
+    const int k = A->k, KP = D.KP, NP = D.NP;
+    const int64_t nc = A->nc, NL = (int64_t)A->leaves.size();
+    std::vector<int32_t> leaf_pos(nc, -1);
+    for (int64_t lp = 0; lp < NL; ++lp) leaf_pos[A->leaves[lp]] = (int32_t)lp;
+    std::vector<TcPackTile> tiles;
+    tiles.reserve(A->n_adm + NL + A->n_near);
+    int64_t off = 0;
+    auto add = [&](int64_t src, int n, int kk, int ld, int np, int kp, int tr) {
+        tiles.push_back(TcPackTile{src, off, n, kk, ld, np, kp, tr});
+        const int64_t b = (int64_t)np * kp * 2;
+        off += b;
+        return off - b;
+    };
+    // S_bᵀ: tile row μ, contraction ν (S_b[ν][μ] at j·k² + ν·k + μ)
+    std::vector<int64_t> s_off(A->n_adm), v_off(NL), g_off(A->n_near);
+    for (int64_t j = 0; j < A->n_adm; ++j) s_off[j] = add(j * k * k, k, k, k, NP, KP, 1);
+    const int64_t nS = (int64_t)tiles.size();
+    for (int64_t lp = 0; lp < NL; ++lp) {
+        const int32_t t = A->leaves[lp];
+        v_off[lp] = add(T.off[t] * k, (int)T.size[t], k, k, round16((int)T.size[t]), KP, 0);
+    }
+    // G_bᵀ for b = (t, s): tile row j of ŝ, contraction over t̂ (G_b[i][j] at near_src + i·|ŝ| + j)
+    std::vector<int32_t> near_t(A->n_near), near_s(A->n_near);
+    {
+        int64_t j = 0, acc = 0;
+        for (int64_t lp = 0; lp < NL; ++lp) {
+            const int32_t t = A->leaves[lp];
+            const int nt = (int)T.size[t];
+            for (int64_t e = T.near_rowptr[t]; e < T.near_rowptr[t + 1]; ++e, ++j) {
+                const int32_t sc = T.near_col[e];
+                const int ns = (int)T.size[sc];
+                g_off[j] = add(acc, ns, nt, ns, round16(ns), round16(nt), 1);
+                near_t[j] = t;
+                near_s[j] = sc;
+                acc += (int64_t)nt * ns;
+            }
+        }
+    }
+    int rc = 0;
+    TcPackTile* d_tiles = nullptr;
+    if ((rc = upload(A, &d_tiles, tiles, st))) return rc;
+    D.d_tilesT = d_tiles;
+    const int64_t nV = NL, nG = A->n_near;
+    for (int es = 2; es <= 4; es += 2) {
+        if ((es == 2 && !D.has_bf16) || (es == 4 && !D.has_tf32)) continue;
+        void* pm = nullptr;
+        if ((rc = device_alloc(A, &pm, (size_t)std::max<int64_t>(off * (es / 2), 128)))) return rc;
+        uint8_t* dst = (uint8_t*)pm;
+        if ((rc = launch_pack_tiles(d_tiles, nS, (const double*)A->f64.S, dst, es, st))) return rc;
+        if ((rc = launch_pack_tiles(d_tiles + nS, nV, (const double*)A->f64.V, dst, es, st))) return rc;
+        if ((rc = launch_pack_tiles(d_tiles + nS + nV, nG, (const double*)A->f64.Near, dst, es, st))) return rc;
+        if (es == 2) D.matT = dst; else D.matT32 = dst;
+    }
+    // ---- coupling list over column clusters: item s, terms S_bᵀ x̂_t ----
+    std::vector<std::vector<int64_t>> by_col(nc);
+    for (int64_t t = 0; t < nc; ++t)
+        for (int64_t j = T.adm_rowptr[t]; j < T.adm_rowptr[t + 1]; ++j) by_col[T.adm_col[j]].push_back(j);
+    std::vector<TcItem> c_items;
+    std::vector<TcTerm> c_terms;
+    std::vector<int32_t> c_zero;
+    c_terms.reserve(A->n_adm);
+    {
+        // the row cluster of every admissible block
+        std::vector<int32_t> row_of(A->n_adm);
+        for (int64_t t = 0; t < nc; ++t)
+            for (int64_t j = T.adm_rowptr[t]; j < T.adm_rowptr[t + 1]; ++j) row_of[j] = (int32_t)t;
+        for (int64_t sc = 0; sc < nc; ++sc) {
+            const int32_t e0 = (int32_t)c_terms.size();
+            for (int64_t j : by_col[sc])
+                c_terms.push_back(TcTerm{s_off[j], (int32_t)((int64_t)row_of[j] * KP), (int16_t)KP, (int16_t)0});
+            const int32_t e1 = (int32_t)c_terms.size();
+            if (e1 > e0) c_items.push_back(TcItem{(int32_t)sc, e0, e1, NP});
+            else c_zero.push_back((int32_t)sc);
+        }
+    }
+    std::stable_sort(c_items.begin(), c_items.end(),
+                     [](const TcItem& a, const TcItem& b) { return a.e1 - a.e0 > b.e1 - b.e0; });
+    snake_order(c_items, kTcGrid);
+    // ---- leaf list over column leaves: item s, terms V_s ŷ_s, then G_bᵀ x|_t̂ ----
+    std::vector<int64_t> xkoff(NL + 1, 0);
+    for (int64_t lp = 0; lp < NL; ++lp) xkoff[lp + 1] = xkoff[lp] + round16((int)T.size[A->leaves[lp]]);
+    std::vector<std::vector<int64_t>> near_by_col(NL);
+    for (int64_t j = 0; j < A->n_near; ++j) near_by_col[leaf_pos[near_s[j]]].push_back(j);
+    std::vector<TcItem> l_items(NL);
+    std::vector<TcTerm> l_terms;
+    std::vector<int64_t> l_cost(NL, 0);
+    for (int64_t lp = 0; lp < NL; ++lp) {
+        const int32_t sc = A->leaves[lp];
+        const int np = round16((int)T.size[sc]);
+        const int32_t e0 = (int32_t)l_terms.size();
+        l_terms.push_back(TcTerm{v_off[lp], (int32_t)((int64_t)sc * KP), (int16_t)KP, (int16_t)1});
+        l_cost[lp] += (int64_t)np * KP;
+        for (int64_t j : near_by_col[lp]) {
+            const int32_t t = near_t[j];
+            const int kpt = round16((int)T.size[t]);
+            l_terms.push_back(TcTerm{g_off[j], (int32_t)xkoff[leaf_pos[t]], (int16_t)kpt, (int16_t)0});
+            l_cost[lp] += (int64_t)np * kpt;
+        }
+        l_items[lp] = TcItem{(int32_t)lp, e0, (int32_t)l_terms.size(), np};
+    }
+    std::stable_sort(l_items.begin(), l_items.end(),
+                     [&](const TcItem& a, const TcItem& b) { return l_cost[a.id] > l_cost[b.id]; });
+    snake_order(l_items, kTcGrid);
+    D.ct_nitems = (int)c_items.size();
+    D.ct_nzero = (int)c_zero.size();
+    D.lt_nitems = (int)NL;
+#define UP(dst, src) if ((rc = upload(A, &(dst), (src), st))) return rc
+    UP(D.ct_items, c_items);
+    UP(D.ct_terms, c_terms);
+    UP(D.ct_zero, c_zero);
+    UP(D.lt_items, l_items);
+    UP(D.lt_terms, l_terms);
+#undef UP
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
+    D.t_built = true;
     return 0;
 }
 

@@ -68,6 +68,7 @@ struct Timing {
 struct TcPackTile {
     int64_t src, dst;
     int32_t n, k, ld, np, kp;
+    int32_t tr;  // 1: the tile holds the transpose, row r column c = src[c·ld + r]
 };
 
 // One output tile of the tcgen05 segmented GEMM: output id, its terms
@@ -133,6 +134,21 @@ struct TcData {
     int32_t* leaf_kdim = nullptr;  // points of each leaf
     TcPackTile* d_tiles = nullptr; // pack descriptors (S tiles first), kept to rebuild S
     int64_t n_s_tiles = 0;
+    // the product with Aᵀ (built on its first use, build_tc_transposed): S_bᵀ, V and
+    // G_bᵀ tiles in the same layout, a coupling list over column clusters and a leaf
+    // list over column leaves
+    bool t_built = false;
+    uint8_t* matT = nullptr;
+    uint8_t* matT32 = nullptr;
+    TcPackTile* d_tilesT = nullptr;  // S_bᵀ tiles first (rebuilt with S)
+    TcItem* ct_items = nullptr;
+    TcTerm* ct_terms = nullptr;
+    int ct_nitems = 0;
+    int32_t* ct_zero = nullptr;
+    int ct_nzero = 0;
+    TcItem* lt_items = nullptr;
+    TcTerm* lt_terms = nullptr;
+    int lt_nitems = 0;
 };
 
 // Inter-CTA bookkeeping of the one-launch transfer passes: arrival counters of
@@ -258,6 +274,7 @@ struct h2_matrix {
     double bj_sigma = 0.0;        // σ the inverses were formed with
     bool bj_valid = false;
     std::vector<void*> allocations;
+    int64_t alloc_bytes = 0;  // bytes of `allocations` (counted against h2_set_alloc_limit)
 };
 
 namespace h2 {
@@ -376,6 +393,8 @@ int launch_pack_act(const float* src, int64_t ld, int ids, const int32_t* idmap,
                     uint8_t* dst, int es, cudaStream_t st);
 int launch_zero_clusters(const int32_t* ids, int count, float* yhat, int k, int ldc, int mc, cudaStream_t st);
 int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st);
+// Tiles and work lists of the tensor-core product with Aᵀ (once per matrix; allocates).
+int build_tc_transposed(h2_matrix* A, cudaStream_t st);
 
 inline int round16(int x) { return (x + 15) & ~15; }
 
@@ -385,8 +404,14 @@ int forward_transform_f64(h2_matrix* A, const double* X, int64_t ldx, int64_t m,
                           double* xhat_out, cudaStream_t st);
 int cast_f32(const double* src, float* dst, int64_t count, cudaStream_t st);
 
+// Poll limit of the device-side waits on another CTA's ready flag (FP64
+// downward pass); negative: give up at once (h2_set_wait_limit).
+long long wait_limit();
+
 bool is_device_pointer(const void* p);
 const void* mapped_host_pointer(const void* p);
 int device_alloc(h2_matrix* A, void** ptr, size_t bytes);
+// Free every device_alloc allocation of A (and take it off the library's count).
+void release_allocations(h2_matrix* A);
 
 }  // namespace h2

@@ -283,7 +283,7 @@ template <typename T, int RM, int CN>
 __global__ void __launch_bounds__(kThreads) k_down_fused(const int32_t* __restrict__ order, int n_items,
                                                          const int32_t* __restrict__ parent, const T* __restrict__ E,
                                                          T* yhat, unsigned* __restrict__ claim, int* flag, int epoch,
-                                                         int* __restrict__ err, int k, int m) {
+                                                         int* __restrict__ err, int k, int m, long long spin_limit) {
     __shared__ Smem<T, RM, CN> sm;
     __shared__ int s_item, s_ok;
     const int tile = blockIdx.y, gy = gridDim.y;
@@ -301,9 +301,11 @@ __global__ void __launch_bounds__(kThreads) k_down_fused(const int32_t* __restri
             int ok = 1;
             if (parent[par] >= 0) {  // the root's ŷ is final after the coupling phase
                 const int* f = flag + (int64_t)par * gy + tile;
-                uint32_t spins = 0;
-                while (ld_acquire(f) != epoch) {
-                    if (++spins > (1u << 24)) { ok = 0; break; }
+                // spin_limit < 0: give up without looking at the flag (the timeout
+                // path's test setting, h2_set_wait_limit)
+                long long spins = 0;
+                while (spin_limit < 0 || ld_acquire(f) != epoch) {
+                    if (spin_limit < 0 || ++spins > spin_limit) { ok = 0; break; }
                     __nanosleep(32);
                 }
             }
@@ -976,7 +978,8 @@ int backward_pass(h2_matrix* A, const T* E, T* yhat, int m, unsigned gy, unsigne
         H2_CUDA_TRY(cudaMemsetAsync(sb.claim, 0, gy * sizeof(unsigned), st));
         const unsigned g = (unsigned)std::min(n_items, 152 * 6);
         k_down_fused<T, RM, CN><<<dim3(g, gy), kThreads, 0, st>>>(A->d_down_list, n_items, A->d_parent, E, yhat,
-                                                                 sb.claim, sb.flag, sb.epoch, sb.err, k, m);
+                                                                 sb.claim, sb.flag, sb.epoch, sb.err, k, m,
+                                                                 wait_limit());
         H2_LAUNCH_CHECK();
         return 0;
     }
@@ -1063,7 +1066,7 @@ int ensure_workspace(h2_matrix* A, size_t bytes, cudaStream_t st) {
 // high and low parts of each column).
 template <int CN>
 int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int m,
-                 cudaStream_t st, bool overwrite, const SyncBufs& sb) {
+                 cudaStream_t st, bool overwrite, const SyncBufs& sb, bool trans) {
     // kind 2: the TF32 product with the matrix-free coupling (tensor-core kernel mode 2)
     const bool mf = kind == 2;
     if (mf) kind = 1;
@@ -1126,14 +1129,19 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         }
         if (!fast && (rc = launch_pack_act(xhat, mc, (int)nc, nullptr, nullptr, nullptr, k, nullptr, KP, mc, R, xcm, es, st)))
             return rc;
-        if ((rc = launch_zero_clusters(D.c_zero, D.c_nzero, yhat, k, mc, mc, st))) return rc;
+        // Aᵀ: the coupling runs over column clusters with S_bᵀ, the leaf phase over
+        // column leaves with G_bᵀ (tiles and lists of build_tc_transposed)
+        const uint8_t* bmat = trans ? (kind == 0 ? D.matT : D.matT32) : (kind == 0 ? D.mat : D.mat32);
+        if ((rc = launch_zero_clusters(trans ? D.ct_zero : D.c_zero, trans ? D.ct_nzero : D.c_nzero, yhat, k, mc,
+                                       mc, st)))
+            return rc;
         TcGemmParams cp{};
-        cp.n_items = D.c_nitems;
-        cp.items = D.c_items;
-        cp.terms = D.c_terms;
+        cp.n_items = trans ? D.ct_nitems : D.c_nitems;
+        cp.items = trans ? D.ct_items : D.c_items;
+        cp.terms = trans ? D.ct_terms : D.c_terms;
         cp.act0 = xcm;
         cp.act1 = xcm;
-        cp.bmat = kind == 0 ? D.mat : D.mat32;
+        cp.bmat = bmat;
         cp.R = R;
         cp.mc = mc;
         cp.yhat = yhat;
@@ -1170,12 +1178,12 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
             return rc;
         marks.mark();
         TcGemmParams lp{};
-        lp.n_items = D.l_nitems;
-        lp.items = D.l_items;
-        lp.terms = D.l_terms;
+        lp.n_items = trans ? D.lt_nitems : D.l_nitems;
+        lp.items = trans ? D.lt_items : D.l_items;
+        lp.terms = trans ? D.lt_terms : D.l_terms;
         lp.act0 = Xcm;
         lp.act1 = ycm;
-        lp.bmat = kind == 0 ? D.mat : D.mat32;
+        lp.bmat = bmat;
         lp.R = R;
         lp.mc = mc;
         lp.leaves = A->d_leaves;
@@ -1199,10 +1207,14 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
 }
 
 int dispatch_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
-                int64_t m, cudaStream_t st, bool overwrite, const SyncBufs& sb) {
-    if (m <= 16) return run_chain_tc<1>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb);
-    if (m <= 32) return run_chain_tc<2>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb);
-    return run_chain_tc<4>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb);
+                int64_t m, cudaStream_t st, bool overwrite, const SyncBufs& sb, bool trans = false) {
+    if (trans) {
+        int rc = build_tc_transposed(A, st);
+        if (rc) return rc;
+    }
+    if (m <= 16) return run_chain_tc<1>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb, trans);
+    if (m <= 32) return run_chain_tc<2>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb, trans);
+    return run_chain_tc<4>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb, trans);
 }
 
 template <typename T>
@@ -1271,8 +1283,8 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
     }
     if (dtype == H2_F32) {
         if (!A->f32.built) { set_error("FP32 copy not built (add 1<<H2_F32 to params->precisions)"); return H2_E_UNSUPPORTED; }
-        if (!transposed && A->tc.has_tf32 && !A->force_simt)
-            return dispatch_tc(A, 1, alpha, X, ldx, Y, ldy, m, st, overwrite, sb);
+        if (A->tc.has_tf32 && !A->force_simt)
+            return dispatch_tc(A, 1, alpha, X, ldx, Y, ldy, m, st, overwrite, sb, transposed);
         return dispatch_cn<float>(A, A->f32, alpha, X, ldx, Y, ldy, (int)m, st, transposed, overwrite,
                                   (float*)base, (float*)(base + bXp), (float*)(base + bXp + bC), sb);
     }
@@ -1290,8 +1302,7 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
     }
     if (dtype == H2_BF16) {
         if (!A->tc.has_bf16) { set_error("BF16 copy not built (add 1<<H2_BF16 to params->precisions)"); return H2_E_UNSUPPORTED; }
-        if (transposed) { set_error("the BF16 product supports A·X only (use H2_F32 or H2_F64 for Aᵀ)"); return H2_E_UNSUPPORTED; }
-        return dispatch_tc(A, 0, alpha, X, ldx, Y, ldy, m, st, overwrite, sb);
+        return dispatch_tc(A, 0, alpha, X, ldx, Y, ldy, m, st, overwrite, sb, transposed);
     }
     set_error("unsupported dtype for the product");
     return H2_E_UNSUPPORTED;

@@ -19,10 +19,43 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};  // context the cached address belongs to
+
+// Unique id of the calling thread's current context (0 if it cannot be
+// read).  cudaDeviceReset destroys a device's primary context and the next
+// runtime call creates a new one with a new id, in which the array has a new
+// address; comparing ids keeps the cache from handing out the old one.  The
+// driver functions come through the runtime's entry-point query, so the
+// library does not link libcuda directly.
+unsigned long long current_context_id() {
+    using GetCurrent = int (*)(void**);
+    using GetId = int (*)(void*, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = (GetCurrent)f1;
+            get_id = (GetId)f2;
+        }
+        cudaGetLastError();
+        looked_up = true;
+    }
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 // Device address of g_noalloc_scratch on the current device.  In host code
 // the array's name is only a host-side stand-in, so the device address is
-// looked up once per device (with that device current) and cached.
+// looked up (with that device current) on the first call in a context and
+// cached for that device until its context changes.
 int scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -35,14 +68,18 @@ int scratch_address(void** out) {
         return H2_E_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    // ctx is 0 while no context is current on this thread yet, and always 0
+    // where the driver's ids cannot be read (then the cache is per device)
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_addr[dev] || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the device's context current if needed
         if (e != cudaSuccess || !p) {
             h2::set_error(std::string("h2_matmul_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             return H2_E_CUDA;
         }
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = current_context_id();
     }
     *out = g_scratch_addr[dev];
     return 0;
@@ -53,7 +90,10 @@ int scratch_address(void** out) {
 extern "C" int h2_matmul_noalloc(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
                                  int64_t m, int32_t dtype, void* stream) {
     if (!A || (m > 0 && (!X || !Y))) { h2::set_error("h2_matmul_noalloc: null argument"); return H2_E_BADARG; }
-    if (m < 0 || ldx < m || ldy < m) { h2::set_error("h2_matmul_noalloc: bad m / leading dimension"); return H2_E_BADARG; }
+    if (m < 0 || ldx < m || ldy < m || m > ((int64_t)1 << 20)) {
+        h2::set_error("h2_matmul_noalloc: bad m / leading dimension (0 <= m <= 2^20, ld >= m)");
+        return H2_E_BADARG;
+    }
     if (dtype != H2_F64 && dtype != H2_F32) {
         h2::set_error("h2_matmul_noalloc: dtype must be H2_F64 or H2_F32");
         return H2_E_UNSUPPORTED;

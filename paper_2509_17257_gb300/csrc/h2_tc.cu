@@ -187,7 +187,9 @@ __global__ void k_pack_tiles(const TcPackTile* __restrict__ tiles, int64_t count
         uint8_t* base = dst + d.dst * (es / 2);
         for (int e = threadIdx.x; e < d.np * d.kp; e += blockDim.x) {
             const int r = e / d.kp, c = e % d.kp;
-            const double v = (r < d.n && c < d.k) ? src[d.src + (int64_t)r * d.ld + c] : 0.0;
+            const double v = (r < d.n && c < d.k)
+                                 ? src[d.src + (d.tr ? (int64_t)c * d.ld + r : (int64_t)r * d.ld + c)]
+                                 : 0.0;
             if (es == 2) *(__nv_bfloat16*)(base + cm_off(r, c, d.kp, 2)) = __double2bfloat16(v);
             else *(float*)(base + cm_off(r, c, d.kp, 4)) = (float)v;
         }

@@ -95,8 +95,8 @@ EXPORTS = ["h2_build", "h2_free", "h2_info", "h2_matmul", "h2_matmul_transposed"
            "h2_timing_enable", "h2_timing_query", "h2_coupling_get", "h2_coupling_set", "h2_shift_set",
            "h2_adjoint_grads", "h2_batch_create", "h2_batch_free", "h2_batch_matmul", "h2_batch_block_cg",
            "h2_autotune",
-           "h2_tree_build", "h2_tree_view_get", "h2_tree_free", "h2_tree_schedule", "h2_last_error_string",
-           "h2_version"]
+           "h2_tree_build", "h2_tree_view_get", "h2_tree_free", "h2_tree_schedule", "h2_set_alloc_limit",
+           "h2_alloc_bytes", "h2_set_wait_limit", "h2_last_error_string", "h2_version"]
 H2_NPHASE = 8
 PHASES = ["gather", "leaf_fwd", "up", "coupling", "down", "leaf_bwd_near", "coupling_kernel"]
 
@@ -136,6 +136,9 @@ def lib() -> C.CDLL:
     L.h2_tree_view_get.argtypes = [vp, C.POINTER(TreeView)]
     L.h2_tree_free.argtypes = [vp]
     L.h2_tree_schedule.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), vp, vp]
+    L.h2_set_alloc_limit.argtypes = [i64]
+    L.h2_alloc_bytes.argtypes = [C.POINTER(i64)]
+    L.h2_set_wait_limit.argtypes = [i64]
     L.h2_last_error_string.restype = C.c_char_p
     L.h2_version.restype = C.c_char_p
     for name in EXPORTS:
@@ -263,6 +266,23 @@ def h2_matmul_noalloc(handle, alpha, X, Y, dtype="f64", stream=None):
     cannot allocate at call time; see include/h2.h for the size limit and the
     rules on concurrent calls."""
     return _mm(lib().h2_matmul_noalloc, "h2_matmul_noalloc", handle, alpha, X, Y, dtype, stream)
+
+
+def h2_set_alloc_limit(nbytes: int) -> None:
+    """Cap the device bytes the process's matrices hold for their stored data (0: no cap)."""
+    _check(lib().h2_set_alloc_limit(int(nbytes)), "h2_set_alloc_limit")
+
+
+def h2_alloc_bytes() -> int:
+    """Device bytes the live matrices hold for their stored data."""
+    v = C.c_int64()
+    _check(lib().h2_alloc_bytes(C.byref(v)), "h2_alloc_bytes")
+    return v.value
+
+
+def h2_set_wait_limit(polls: int) -> None:
+    """Poll limit of the device-side flag waits (0: default; < 0: give up at once)."""
+    _check(lib().h2_set_wait_limit(int(polls)), "h2_set_wait_limit")
 
 
 def h2_coupling_get(handle, out=None):

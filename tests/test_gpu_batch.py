@@ -63,7 +63,7 @@ def test_batched_block_cg(batch):
     res = B.block_cg(Bs, Xs, tol=1e-8, max_iter=20000, dtype="f32", inner_tol=0.1, check_every=4)
     for sp, x, b, r, p in zip(specs, Xs, Bs, res, pts):
         assert r.status == 0, (sp, r)
-        assert r.rel_residual.max() <= 1.5e-8
+        assert r.rel_residual.max() <= 1e-8  # the solver decides on this FP64 residual
         H = O.H2Matrix(p, q=sp["q"], leaf_size=64, eta=2.0, sigma=1e-2)
         A = O.dense_expand(H)
         bn = b.cpu().numpy()
@@ -97,7 +97,7 @@ def test_batched_block_cg_gram(batch):
     res = B.block_cg(Bs, Xs, tol=1e-8, max_iter=20000, dtype="f32", inner_tol=0.1, check_every=4, variant="gram")
     for sp, x, b, r, p in zip(specs, Xs, Bs, res, pts):
         assert r.status == 0, (sp, r)
-        assert r.rel_residual.max() <= 1.5e-8
+        assert r.rel_residual.max() <= 1e-8  # the solver decides on this FP64 residual
         H = O.H2Matrix(p, q=sp["q"], leaf_size=64, eta=2.0, sigma=1e-2)
         A = O.dense_expand(H)
         Xc = np.linalg.solve(A, b.cpu().numpy())

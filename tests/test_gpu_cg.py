@@ -42,7 +42,7 @@ def test_block_cg_matches_dense_solve(case4096, inner):
     X = Xd.cpu().numpy()
     true_rel = np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0)
     assert true_rel.max() <= 1e-8 * 1.5, true_rel
-    assert res.rel_residual.max() <= 1e-8 * 1.5
+    assert res.rel_residual.max() <= 1e-8  # the solver confirms convergence on this FP64 residual
     assert rel_fro(X, Xc) <= 1e-6
     if inner == "f64":
         ref = O.block_cg(lambda Z: A @ Z, B, tol=1e-8, max_iter=20000)
@@ -65,6 +65,7 @@ def test_mixed_solve_with_reliable_updates(case4096):
     X = Xd.cpu().numpy()
     true_rel = np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0)
     assert true_rel.max() <= 1e-8 * 1.5, true_rel
+    assert res.rel_residual.max() <= 1e-8  # the solver decides on this FP64 residual
     assert rel_fro(X, Xc) <= 1e-6
     assert res.outer_steps >= 1  # at least one reliable update
     # the FP32 operator costs some iterations against FP64 CG (loss of

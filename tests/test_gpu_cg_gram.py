@@ -44,7 +44,8 @@ def test_gram_fp64_matches_oracle_and_dense_solve(case4096, m):
     res = G.block_cg(Bd, Xd, tol=1e-8, max_iter=5000, dtype="f64", variant="gram", check_every=1)
     assert res.status == 0, res
     X = Xd.cpu().numpy()
-    assert _true_rel(A, B, X).max() <= 1.5e-8
+    assert _true_rel(A, B, X).max() <= 1.5e-8  # dense recomputation in another rounding order
+    assert res.rel_residual.max() <= 1e-8  # the solver confirms convergence on this FP64 residual
     assert rel_fro(X, sla.cho_solve(cf, B)) <= 1e-6
     ref = O.block_cg_gram(lambda Z: A @ Z, B, tol=1e-8, max_iter=5000)
     assert ref.status == "converged"
@@ -85,7 +86,7 @@ def test_gram_mixed_precision_reaches_fp64_tolerance(case4096, refine):
     assert res.status == 0, res
     X = Xd.cpu().numpy()
     assert _true_rel(A, B, X).max() <= 1.5e-8
-    assert res.rel_residual.max() <= 1.5e-8
+    assert res.rel_residual.max() <= 1e-8  # the solver decides on this FP64 residual
     assert rel_fro(X, sla.cho_solve(cf, B)) <= 1e-6
     assert res.outer_steps >= 1
 

@@ -67,14 +67,43 @@ def test_matmul_matches_oracle(sphere4096, dtype, m):
     assert rel_fro(got, want) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_transposed_matches_oracle(sphere4096, dtype):
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("m", [5, 40, 70])
+def test_transposed_matches_oracle(sphere4096, dtype, m):
     H, G = sphere4096
-    X = gaussian_rhs(4096, 5, 3)
-    Y0 = gaussian_rhs(4096, 5, 4)
+    X = gaussian_rhs(4096, m, 3)
+    Y0 = gaussian_rhs(4096, m, 4)
     want = O.h2mm(H, 1.5, X, Y0, transposed=True)
     got = _gpu_apply(G, X, Y0, 1.5, dtype, transposed=True)
     assert rel_fro(got, want) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_transposed_of_a_nonsymmetric_matrix(P, dtype):
+    """After the couplings are replaced by non-symmetric ones (S_(s,t) no longer
+    S_(t,s)ᵀ), Aᵀ differs from A; the tensor-core product with Aᵀ (S_bᵀ tiles,
+    column-cluster lists) must follow, including the tiles rebuilt by
+    h2_coupling_set.  A q = 4 tree so the subtree-owning transfer passes run."""
+    torch = require_cuda()
+    pts = sphere_points(3000, 11)
+    H, G = _pair(P, pts, q=4)
+    X = gaussian_rhs(3000, 24, 1)
+    Y0 = gaussian_rhs(3000, 24, 2)
+    _gpu_apply(G, X, Y0, 1.0, dtype, transposed=True)  # build the Aᵀ tiles before the change
+    rng = np.random.default_rng(5)
+    S = P.h2_coupling_get(G.handle)  # host copy, list order
+    S = np.ascontiguousarray(S * (1.0 + 0.3 * rng.standard_normal(S.shape)))
+    P.h2_coupling_set(G.handle, torch.from_numpy(S).cuda())
+    T = P.h2_tree_build(pts, leaf_size=64, eta=2.0, q=4)
+    order = [(t, int(T["adm_col"][j])) for t in range(T["n_clusters"])
+             for j in range(T["adm_rowptr"][t], T["adm_rowptr"][t + 1])]
+    O.set_coupling(H, {pair: S[j] for j, pair in enumerate(order)})
+    for trans in (False, True):
+        want = O.h2mm(H, -0.5, X, Y0, transposed=trans)
+        got = _gpu_apply(G, X, Y0, -0.5, dtype, transposed=trans)
+        assert rel_fro(got, want) <= TOL[dtype], trans
+    assert rel_fro(O.h2mm(H, 1.0, X, transposed=True), O.h2mm(H, 1.0, X)) > 1e-2
+
 
 
 def test_host_buffers_and_leading_dimension(P, sphere4096):
@@ -154,8 +183,6 @@ def test_edge_cases(P, case):
         want = O.h2mm(H, 0.75, X, Y0)
         got = _gpu_apply(G, X, Y0, 0.75, dtype)
         assert rel_fro(got, want) <= TOL[dtype], (case, dtype)
-        if dtype == "bf16":
-            continue  # the BF16 product is A·X only
         want_t = O.h2mm(H, 0.75, X, Y0, transposed=True)
         got_t = _gpu_apply(G, X, Y0, 0.75, dtype, transposed=True)
         assert rel_fro(got_t, want_t) <= TOL[dtype], (case, dtype, "T")
@@ -191,9 +218,6 @@ def test_errors(P, sphere4096):
     G32 = P.H2Matrix(sphere_points(1000, 3), q=3, precisions=("f32",))
     with pytest.raises(P.H2Error) as e:
         G32.matmul(np.zeros((1000, 2)), np.zeros((1000, 2)), dtype="bf16")
-    assert e.value.code == P.H2_E_UNSUPPORTED
-    with pytest.raises(P.H2Error) as e:
-        G.matmul_transposed(X, X.copy(), dtype="bf16")
     assert e.value.code == P.H2_E_UNSUPPORTED
     with pytest.raises(P.H2Error) as e:
         P.h2_build(sphere_points(1000, 3), q=5, precisions=("bf16",))

@@ -41,7 +41,8 @@ def test_pcg_fp64_matches_oracle_and_dense_solve(case4096):
     res = G.block_cg(torch.from_numpy(B).cuda(), Xd, tol=1e-8, max_iter=5000, dtype="f64", precond="block_jacobi")
     assert res.status == 0, res
     X = Xd.cpu().numpy()
-    assert _true_rel(A, B, X).max() <= 1.5e-8
+    assert _true_rel(A, B, X).max() <= 1.5e-8  # dense recomputation in another rounding order
+    assert res.rel_residual.max() <= 1e-8  # the solver confirms convergence on this FP64 residual
     assert rel_fro(X, sla.cho_solve(cf, B)) <= 1e-6
     ref = O.block_pcg(lambda Z: A @ Z, O.block_jacobi(H), B, tol=1e-8, max_iter=5000)
     assert ref.status == "converged"
@@ -73,7 +74,8 @@ def test_pcg_mixed_precision(case4096, refine):
                      inner_tol=0.1 if refine == 2 else 1e-4, precond="block_jacobi", check_every=2)
     assert res.status == 0, res
     X = Xd.cpu().numpy()
-    assert _true_rel(A, B, X).max() <= 1.5e-8
+    assert _true_rel(A, B, X).max() <= 1.5e-8  # dense recomputation in another rounding order
+    assert res.rel_residual.max() <= 1e-8  # the solver confirms convergence on this FP64 residual
     assert rel_fro(X, sla.cho_solve(cf, B)) <= 1e-6
 
 
@@ -117,7 +119,8 @@ def test_preconditioned_gram(case4096, dtype, refine):
                      inner_tol=0.1, variant="gram", precond="block_jacobi", check_every=1)
     assert res.status == 0, res
     X = Xd.cpu().numpy()
-    assert _true_rel(A, B, X).max() <= 1.5e-8
+    assert _true_rel(A, B, X).max() <= 1.5e-8  # dense recomputation in another rounding order
+    assert res.rel_residual.max() <= 1e-8  # the solver confirms convergence on this FP64 residual
     assert rel_fro(X, sla.cho_solve(cf, B)) <= 1e-6
     if dtype == "f64":
         ref = O.block_cg_gram(lambda Z: A @ Z, B, tol=1e-8, max_iter=5000, apply_Minv=O.block_jacobi(H))

@@ -58,3 +58,9 @@ def test_noalloc_rejects_what_it_cannot_do(setup):
     with pytest.raises(P.H2Error) as e:
         P.h2_matmul_noalloc(G.handle, 1.0, Xd, Xd.clone(), dtype="bf16")
     assert e.value.code == P.H2_E_UNSUPPORTED
+    # more than 2^20 columns is refused before any size arithmetic (a huge m
+    # could otherwise wrap the scratch size); the buffers are never touched
+    big = (1 << 20) + 1
+    L = P.lib()
+    assert L.h2_matmul_noalloc(G.handle, 1.0, Xd.data_ptr(), big, Xd.data_ptr(), big, big, P.H2_F64,
+                               None) == P.H2_E_BADARG
