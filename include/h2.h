@@ -338,10 +338,41 @@ int h2_batch_matmul(h2_batch* batch, double alpha, const double* const* X, const
 int h2_batch_block_cg(h2_batch* batch, const double* const* B, const int64_t* ldb, double* const* X,
                       const int64_t* ldx, const int64_t* m, const h2_cg_params* params, h2_cg_result* res);
 
-/* Autotuning: time the FP32 product of m columns on the tensor cores (split
- * TF32) and on the CUDA cores for this matrix and keep the faster for later
- * FP32 products.  ms[0], ms[1] (optional) receive the two times per product in
- * milliseconds (ms[0] < 0 when the tensor-core copy was not built). */
+/* Autotuning of the product for this matrix and m columns (not in the paper;
+ * the product's kernels have shapes and schedules that the fastest choice
+ * depends on).  h2_autotune_ex times, for the precision dtype (H2_F32 or
+ * H2_BF16), with 2 warm-up and 5 timed products each on zero blocks:
+ *   1. the product path: tensor cores with the CUDA-core transfer passes
+ *      (path 1), tensor cores with the tensor-core transfer passes (Alg.
+ *      "forward/backward" as work lists in dependency order: one launch per
+ *      phase, path 2, or sharing the coupling's and the leaf phase's launches,
+ *      path 3; FP32 only), CUDA cores only (path 4; FP32 only);
+ *   2. on the best path, the pipeline stage count of the tensor-core kernels
+ *      (4 and 5 against as many as fit);
+ *   3. on path 1, the cut targets of the CUDA-core subtree passes (the task
+ *      counts that the upward and the downward schedules aim at: half and
+ *      twice the default, upward first).
+ * The fastest variant is kept for later products of this precision whose
+ * column chunks fall in the same class (at most 8, 16, 32 or 64 columns per
+ * 64-column chunk); the cut targets are per matrix.  Synchronises the stream;
+ * allocates two n×m blocks for the duration; not inside a stream capture
+ * (H2_E_BADARG).  out (optional) receives the candidates and the choice. */
+typedef struct h2_tune_result {
+    int32_t dtype, m;
+    int32_t path;          /* chosen path (1..4, as above)                          */
+    int32_t stages;        /* chosen stage count (0: as many as fit)                */
+    int32_t up_target;     /* chosen cut targets of the CUDA-core transfer passes   */
+    int32_t down_target;
+    int32_t n_candidates;  /* candidates timed, in the order above (at most 16)     */
+    double ms_best;        /* time per product of the choice, milliseconds           */
+    double ms[16];
+    int32_t cand_path[16], cand_stages[16], cand_up[16], cand_down[16];
+} h2_tune_result;
+int h2_autotune_ex(h2_matrix* A, int64_t m, int32_t dtype, void* stream, h2_tune_result* out);
+
+/* h2_autotune_ex for H2_F32; ms[0], ms[1] (optional) receive the fastest
+ * tensor-core time and the CUDA-core time per product in milliseconds (ms[0] <
+ * 0 when the tensor-core copy was not built). */
 int h2_autotune(h2_matrix* A, int64_t m, void* stream, double* ms);
 
 /* ---- host-only topology (Sec. 2 trees; Alg. "prepare_addeval" lists) ---- */

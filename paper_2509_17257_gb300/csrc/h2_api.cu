@@ -49,6 +49,15 @@ long long wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
 // Every allocation of a matrix's stored data (h2_build, the block-Jacobi
 // factors) comes through here: it is counted against h2_set_alloc_limit and
 // released with the matrix.
+bool stream_capture_active(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return true;  // unknown: take the path that is safe in a capture
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
 int device_alloc(h2_matrix* A, void** ptr, size_t bytes) {
     const int64_t cap = g_alloc_limit.load();
     const int64_t live = g_alloc_live.fetch_add((int64_t)bytes) + (int64_t)bytes;
@@ -66,17 +75,28 @@ int device_alloc(h2_matrix* A, void** ptr, size_t bytes) {
         set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? H2_E_OOM : H2_E_CUDA;
     }
-    A->allocations.push_back(p);
+    A->allocations.push_back({p, bytes});
     A->alloc_bytes += (int64_t)bytes;
     *ptr = p;
     return 0;
 }
 
 void release_allocations(h2_matrix* A) {
-    for (void* p : A->allocations) cudaFree(p);
+    for (auto& a : A->allocations) cudaFree(a.first);
     A->allocations.clear();
     g_alloc_live.fetch_sub(A->alloc_bytes);
     A->alloc_bytes = 0;
+}
+
+void release_allocation(h2_matrix* A, void* p) {
+    for (size_t i = 0; i < A->allocations.size(); ++i) {
+        if (A->allocations[i].first != p) continue;
+        cudaFree(p);
+        A->alloc_bytes -= (int64_t)A->allocations[i].second;
+        g_alloc_live.fetch_sub((int64_t)A->allocations[i].second);
+        A->allocations.erase(A->allocations.begin() + (long)i);
+        return;
+    }
 }
 
 }  // namespace h2
@@ -230,6 +250,8 @@ int h2_build(const h2_build_params* params, const double* pts, int64_t n, h2_mat
     A->n_leaves = nl;
     const char* fs = getenv("H2_FORCE_SIMT");
     A->force_simt = fs && fs[0] == '1';
+    const char* ft = getenv("H2_TC_TRANSFER");
+    A->use_flow = ft && ft[0] == '1' ? 1 : (ft && ft[0] == '0' ? 0 : -1);
     rc = h2::build_device(A, hp, params->precisions, st);
     if (rc) {
         free_matrix(A);

@@ -2,6 +2,7 @@
 // one branch per system, and the autotuner that picks the FP32 product path.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -161,41 +162,120 @@ int h2_batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, d
     return batch_block_cg(b, B, ldb, X, ldx, m, params, res);
 }
 
-int h2_autotune(h2_matrix* A, int64_t m, void* stream, double* ms) {
-    if (!A || m < 1) { set_error("bad argument"); return H2_E_BADARG; }
-    if (!A->f32.built) { set_error("FP32 copy not built"); return H2_E_UNSUPPORTED; }
+namespace {
+
+// Time one product variant (2 warm-up, 5 timed products on zero blocks).
+int time_variant(h2_matrix* A, int64_t m, int32_t dtype, cudaStream_t st, double* Xb, double* Yb, cudaEvent_t e0,
+                 cudaEvent_t e1, double* ms) {
+    int rc = 0;
+    for (int r = 0; r < 2 && !rc; ++r) rc = matmul_device(A, 1.0, Xb, m, Yb, m, m, dtype, st, false, true);
+    if (rc) return rc;
+    H2_CUDA_TRY(cudaEventRecord(e0, st));
+    for (int r = 0; r < 5 && !rc; ++r) rc = matmul_device(A, 1.0, Xb, m, Yb, m, m, dtype, st, false, true);
+    if (rc) return rc;
+    H2_CUDA_TRY(cudaEventRecord(e1, st));
+    H2_CUDA_TRY(cudaEventSynchronize(e1));
+    float f = 0.f;
+    H2_CUDA_TRY(cudaEventElapsedTime(&f, e0, e1));
+    *ms = f / 5.0;
+    return 0;
+}
+
+}  // namespace
+
+int h2_autotune_ex(h2_matrix* A, int64_t m, int32_t dtype, void* stream, h2_tune_result* out) {
+    if (!A || m < 1 || (dtype != H2_F32 && dtype != H2_BF16)) { set_error("h2_autotune_ex: bad argument"); return H2_E_BADARG; }
+    if (dtype == H2_F32 && !A->f32.built) { set_error("FP32 copy not built"); return H2_E_UNSUPPORTED; }
+    if (dtype == H2_BF16 && !A->tc.has_bf16) { set_error("BF16 copy not built"); return H2_E_UNSUPPORTED; }
     cudaStream_t st = (cudaStream_t)stream;
+    if (stream_capture_active(st)) { set_error("h2_autotune_ex: not inside a stream capture"); return H2_E_BADARG; }
+    const int mc = (int)std::min<int64_t>(m, 64);
+    const int cls = column_class(mc);
+    const int di = dtype == H2_BF16 ? 1 : 0;
+    const Tune keep = A->tune[di][cls];
+    const int keep_flow = A->use_flow;
+    const int keep_up = A->up_target, keep_down = A->down_target;
+    A->use_flow = -1;  // the candidates set the path themselves
     double* buf = nullptr;
     H2_CUDA_TRY(cudaMallocAsync((void**)&buf, 2 * (size_t)A->n * m * sizeof(double), st));
     H2_CUDA_TRY(cudaMemsetAsync(buf, 0, 2 * (size_t)A->n * m * sizeof(double), st));
     double* Xb = buf;
     double* Yb = buf + (size_t)A->n * m;
-    cudaEvent_t e0, e1;
-    H2_CUDA_TRY(cudaEventCreate(&e0));
-    H2_CUDA_TRY(cudaEventCreate(&e1));
-    double t[2] = {-1.0, -1.0};
-    const bool keep = A->force_simt;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    h2_tune_result r{};
+    r.dtype = dtype;
+    r.m = (int32_t)m;
     int rc = 0;
-    for (int path = 0; path < 2 && !rc; ++path) {
-        if (path == 0 && !A->tc.has_tf32) continue;
-        A->force_simt = path == 1;
-        for (int r = 0; r < 2 && !rc; ++r) rc = matmul_device(A, 1.0, Xb, m, Yb, m, m, H2_F32, st, false, true);
-        if (rc) break;
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < 5 && !rc; ++r) rc = matmul_device(A, 1.0, Xb, m, Yb, m, m, H2_F32, st, false, true);
-        cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
-        float f = 0.f;
-        cudaEventElapsedTime(&f, e0, e1);
-        t[path] = f / 5.0;
+    double best = -1.0;
+    Tune best_t = keep;
+    int best_up = keep_up, best_down = keep_down;
+    auto trial = [&](Tune t, int up, int down) {
+        if (rc || r.n_candidates >= 16) return;
+        A->tune[di][cls] = t;
+        if ((rc = set_transfer_targets(A, up, down, st))) return;
+        double ms = -1.0;
+        if ((rc = time_variant(A, m, dtype, st, Xb, Yb, e0, e1, &ms))) return;
+        const int i = r.n_candidates++;
+        r.ms[i] = ms;
+        r.cand_path[i] = t.path;
+        r.cand_stages[i] = t.stages;
+        r.cand_up[i] = up;
+        r.cand_down[i] = down;
+        if (best < 0.0 || ms < best) { best = ms; best_t = t; best_up = up; best_down = down; }
+    };
+    // 1. the product path
+    const bool tc = dtype == H2_BF16 || A->tc.has_tf32;
+    if (tc) trial(Tune{kPathTcOwn, 0}, keep_up, keep_down);
+    if (dtype == H2_F32 && A->tc.flow) {
+        trial(Tune{kPathTcFlow, 0}, keep_up, keep_down);
+        trial(Tune{kPathTcFused, 0}, keep_up, keep_down);
+    }
+    if (dtype == H2_F32) trial(Tune{kPathSimt, 0}, keep_up, keep_down);
+    // 2. the stage count of the tensor-core kernels on the best path
+    if (!rc && best_t.path != kPathSimt)
+        for (int sc : {4, 5}) trial(Tune{best_t.path, (int8_t)sc}, best_up, best_down);
+    // 3. the cut of the CUDA-core subtree passes, upward then downward
+    const bool subtree = A->f32.Et && A->k % 8 == 0 && A->k <= 64 && mc % 4 == 0 && A->T.leaf_size <= 64;
+    if (!rc && best_t.path == kPathTcOwn && subtree) {
+        const int up0 = best_up;
+        for (int u : {kUpTasks / 2, kUpTasks * 2}) trial(best_t, u, best_down);
+        (void)up0;
+        for (int d : {kDownTasks / 2, kDownTasks * 2}) trial(best_t, best_up, d);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFreeAsync(buf, st);
     cudaStreamSynchronize(st);
-    if (rc) { A->force_simt = keep; return rc; }
-    A->force_simt = !(t[0] >= 0.0 && t[0] <= t[1]);
-    if (ms) { ms[0] = t[0]; ms[1] = t[1]; }
+    A->use_flow = keep_flow;
+    if (rc) {
+        A->tune[di][cls] = keep;
+        set_transfer_targets(A, keep_up, keep_down, st);
+        return rc;
+    }
+    A->tune[di][cls] = best_t;
+    if ((rc = set_transfer_targets(A, best_up, best_down, st))) return rc;
+    r.path = best_t.path;
+    r.stages = best_t.stages;
+    r.up_target = best_up;
+    r.down_target = best_down;
+    r.ms_best = best;
+    if (out) *out = r;
+    return 0;
+}
+
+int h2_autotune(h2_matrix* A, int64_t m, void* stream, double* ms) {
+    h2_tune_result r{};
+    const int rc = h2_autotune_ex(A, m, H2_F32, stream, &r);
+    if (rc) return rc;
+    if (ms) {
+        ms[0] = ms[1] = -1.0;
+        for (int i = 0; i < r.n_candidates; ++i) {
+            if (r.cand_path[i] == kPathSimt) ms[1] = r.ms[i];
+            else if (ms[0] < 0.0 || r.ms[i] < ms[0]) ms[0] = r.ms[i];
+        }
+    }
     return 0;
 }
 

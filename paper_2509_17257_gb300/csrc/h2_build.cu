@@ -9,6 +9,7 @@
 #include <cstring>
 #include <vector>
 
+#include "h2_async.cuh"
 #include "h2_internal.cuh"
 
 namespace h2 {
@@ -515,11 +516,11 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
     {
         std::vector<int32_t> task_ptr;
         std::vector<DownStep> dsteps;
-        down_schedule(T, kDownTasks, task_ptr, dsteps, A->dn_ntasks, A->dn_entries);
+        down_schedule(T, A->down_target, task_ptr, dsteps, A->dn_ntasks, A->dn_entries);
         UP(A->d_dn_task_ptr, task_ptr);
         UP(A->d_dn_steps, dsteps);
         std::vector<UpStep> usteps;
-        up_schedule(T, kUpTasks, task_ptr, usteps, A->up_ntasks, A->up_entries);
+        up_schedule(T, A->up_target, task_ptr, usteps, A->up_ntasks, A->up_entries);
         UP(A->d_up_task_ptr, task_ptr);
         UP(A->d_up_steps, usteps);
     }
@@ -617,6 +618,179 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
     return 0;
 }
 
+// ---- the transfer passes of Alg. "forward/backward" on the tensor cores ----
+// Every cluster is one item of a work list whose terms are matrix tile ×
+// activation tile, as in the coupling phase:
+//   upward:   x̂_t = V_tᵀ X|_t̂ (a leaf: V_tᵀ × the leaf's X tile) or
+//             x̂_t = E_s0ᵀ x̂_s0 + E_s1ᵀ x̂_s1 (the sons' x̂ tiles);
+//   downward: ŷ_s = I·ŷ_s + E_s ŷ_t: the coupling result enters through an
+//             identity tile (the coupling writes its results as split tiles,
+//             and zero tiles for clusters without couplings), t the father
+//             (the root has no father term).
+// Items are ordered so that every item's terms read tiles of earlier items;
+// the kernel keeps every CTA's items in that order, and a term marked
+// kTermWait waits for its source's ready flag.  With A the upward pass shares
+// one launch with the coupling phase (f1: all upward items, then the coupling
+// items) and the downward pass one with the leaf phase (f2: all downward
+// items, then the leaf items, each with its nearfield terms first).
+struct FlowTiles {
+    std::vector<int64_t> et_off, vt_off, e_off;  // Eᵀ_c, V_tᵀ (by leaf position), E_c
+    int64_t id_off = 0;                          // the identity tile
+    std::vector<float> ident;
+    int64_t n_et = 0, n_vt = 0, n_e = 0;
+};
+
+void flow_tiles(h2_matrix* A, std::vector<TcPackTile>& tiles, int64_t& off, FlowTiles& ft) {
+    const Tree& T = A->T;
+    const TcData& D = A->tc;
+    const int k = A->k, KP = D.KP, NP = D.NP;
+    const int64_t nc = A->nc, NL = (int64_t)A->leaves.size();
+    auto add = [&](int64_t src, int n, int kk, int ld, int np, int kp, int tr) {
+        tiles.push_back(TcPackTile{src, off, n, kk, ld, np, kp, tr});
+        const int64_t b = (int64_t)np * kp * 2;
+        off += b;
+        return off - b;
+    };
+    ft.et_off.assign(nc, -1);
+    ft.e_off.assign(nc, -1);
+    ft.vt_off.assign(NL, -1);
+    for (int64_t c = 1; c < nc; ++c) ft.et_off[c] = add(c * k * k, k, k, k, NP, KP, 1);  // row ν, column μ
+    ft.n_et = nc - 1;
+    for (int64_t lp = 0; lp < NL; ++lp) {                                              // row ν, column p
+        const int32_t t = A->leaves[lp];
+        ft.vt_off[lp] = add(T.off[t] * k, k, (int)T.size[t], k, NP, round16((int)T.size[t]), 1);
+    }
+    ft.n_vt = NL;
+    for (int64_t c = 1; c < nc; ++c) ft.e_off[c] = add(c * k * k, k, k, k, NP, KP, 0);  // row μ, column ν
+    ft.n_e = nc - 1;
+    ft.id_off = off;
+    ft.ident.assign((size_t)NP * KP, 0.f);
+    for (int r = 0; r < k; ++r) ft.ident[(size_t)(cm_off(r, r, KP, 4) / 4)] = 1.f;
+    off += (int64_t)NP * KP * 2;
+}
+
+// Items with their sort keys, dealt in snake order over the CTAs within each key.
+struct KeyedItem {
+    int32_t key;
+    TcItem it;
+};
+void order_by_key(std::vector<KeyedItem>& v, std::vector<TcItem>& out) {
+    std::stable_sort(v.begin(), v.end(), [](const KeyedItem& a, const KeyedItem& b) { return a.key < b.key; });
+    out.clear();
+    std::vector<TcItem> group;
+    for (size_t i = 0; i < v.size();) {
+        size_t j = i;
+        group.clear();
+        while (j < v.size() && v[j].key == v[i].key) group.push_back(v[j++].it);
+        snake_order(group, kTcGrid);
+        out.insert(out.end(), group.begin(), group.end());
+        i = j;
+    }
+}
+
+int flow_lists(h2_matrix* A, const FlowTiles& ft, const std::vector<int64_t>& s_off,
+               const std::vector<int64_t>& v_off, const std::vector<int64_t>& g_off,
+               const std::vector<int64_t>& xkoff, cudaStream_t st) {
+    TcData& D = A->tc;
+    const Tree& T = A->T;
+    const int KP = D.KP, NP = D.NP;
+    const int64_t nc = A->nc, NL = (int64_t)A->leaves.size();
+    std::vector<int32_t> leaf_pos(nc, -1);
+    for (int64_t lp = 0; lp < NL; ++lp) leaf_pos[A->leaves[lp]] = (int32_t)lp;
+    std::vector<int32_t> height(nc, 0);
+    for (int64_t c = nc - 1; c >= 0; --c)  // pre-order: sons follow their father
+        if (!T.is_leaf((int32_t)c)) height[c] = 1 + std::max(height[T.son0[c]], height[T.son1[c]]);
+    const int16_t kAct0Wait = (int16_t)(0 | kTermWait);
+    auto np_role = [](int np, int32_t role) { return (int32_t)(np | (role << 16)); };
+    // upward items (activations: act0 the x̂ tiles of this launch, act1 the X tiles)
+    std::vector<TcTerm> up_terms;
+    std::vector<KeyedItem> up_k;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int32_t e0 = (int32_t)up_terms.size();
+        if (T.is_leaf((int32_t)c)) {
+            const int32_t lp = leaf_pos[c];
+            up_terms.push_back(TcTerm{ft.vt_off[lp], (int32_t)xkoff[lp], (int16_t)round16((int)T.size[c]), (int16_t)1});
+        } else {
+            for (int32_t s : {T.son0[c], T.son1[c]})
+                up_terms.push_back(TcTerm{ft.et_off[s], (int32_t)((int64_t)s * KP), (int16_t)KP, kAct0Wait});
+        }
+        up_k.push_back(KeyedItem{height[c], TcItem{(int32_t)c, e0, (int32_t)up_terms.size(),
+                                                       np_role(NP, kRoleTransfer)}});
+    }
+    // downward items (act0 the ŷ tiles of this launch, act1 the coupling results)
+    std::vector<TcTerm> dn_terms;
+    std::vector<KeyedItem> dn_k;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int32_t e0 = (int32_t)dn_terms.size();
+        dn_terms.push_back(TcTerm{ft.id_off, (int32_t)((int64_t)c * KP), (int16_t)KP, (int16_t)1});
+        if (c != 0)
+            dn_terms.push_back(TcTerm{ft.e_off[c], (int32_t)((int64_t)T.parent[c] * KP), (int16_t)KP, kAct0Wait});
+        dn_k.push_back(KeyedItem{T.level[c], TcItem{(int32_t)c, e0, (int32_t)dn_terms.size(),
+                                                        np_role(NP, kRoleTransfer)}});
+    }
+    std::vector<TcItem> up_items, dn_items;
+    order_by_key(up_k, up_items);
+    order_by_key(dn_k, dn_items);
+    // f1: every CTA takes its upward items first (they form the dependency chain),
+    // then its coupling items, those whose sources are ready earliest first
+    const int32_t hmax_all = height[0];
+    std::vector<TcTerm> f1_terms = up_terms;
+    std::vector<KeyedItem> f1_k = up_k;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int64_t j0 = T.adm_rowptr[c], j1 = T.adm_rowptr[c + 1];
+        if (j1 == j0) continue;
+        const int32_t e0 = (int32_t)f1_terms.size();
+        int32_t hmax = 0;
+        for (int64_t j = j0; j < j1; ++j) {
+            const int32_t sc = T.adm_col[j];
+            hmax = std::max(hmax, height[sc]);
+            f1_terms.push_back(TcTerm{s_off[j], (int32_t)((int64_t)sc * KP), (int16_t)KP, kAct0Wait});
+        }
+        f1_k.push_back(KeyedItem{hmax_all + 1 + hmax, TcItem{(int32_t)c, e0, (int32_t)f1_terms.size(),
+                                                      np_role(NP, kRoleCoupling)}});
+    }
+    // f2: the downward items first, then the leaf items, shallow leaves (ready first)
+    // first; a leaf item's nearfield terms come first (act2, the X tiles; no wait),
+    // V_t ŷ_t last (act0, waits)
+    std::vector<TcTerm> f2_terms = dn_terms;
+    std::vector<KeyedItem> f2_k = dn_k;
+    {
+        int64_t j = 0;
+        for (int64_t lp = 0; lp < NL; ++lp) {
+            const int32_t t = A->leaves[lp];
+            const int32_t e0 = (int32_t)f2_terms.size();
+            for (int64_t e = T.near_rowptr[t]; e < T.near_rowptr[t + 1]; ++e, ++j) {
+                const int32_t sc = T.near_col[e];
+                f2_terms.push_back(TcTerm{g_off[j], (int32_t)xkoff[leaf_pos[sc]],
+                                          (int16_t)round16((int)T.size[sc]), (int16_t)2});
+            }
+            f2_terms.push_back(TcTerm{v_off[lp], (int32_t)((int64_t)t * KP), (int16_t)KP, kAct0Wait});
+            f2_k.push_back(KeyedItem{A->depth + 1 + T.level[t], TcItem{(int32_t)lp, e0, (int32_t)f2_terms.size(),
+                                                                np_role(round16((int)T.size[t]), kRoleLeaf)}});
+        }
+    }
+    std::vector<TcItem> f1_items, f2_items;
+    order_by_key(f1_k, f1_items);
+    order_by_key(f2_k, f2_items);
+    D.up_nitems = (int)up_items.size();
+    D.dn_nitems = (int)dn_items.size();
+    D.f1_nitems = (int)f1_items.size();
+    D.f2_nitems = (int)f2_items.size();
+    int rc = 0;
+#define UP(dst, src) if ((rc = upload(A, &(dst), (src), st))) return rc
+    UP(D.up_items, up_items);
+    UP(D.up_terms, up_terms);
+    UP(D.dn_items, dn_items);
+    UP(D.dn_terms, dn_terms);
+    UP(D.f1_items, f1_items);
+    UP(D.f1_terms, f1_terms);
+    UP(D.f2_items, f2_items);
+    UP(D.f2_terms, f2_terms);
+#undef UP
+    D.flow = true;
+    return 0;
+}
+
 // Core-matrix copies of S, V and G for the tensor cores (BF16 and/or FP32 for
 // the split-TF32 product), and the schedules of the two tcgen05 kernels
 // (coupling over row clusters, leaf phase over row leaves).
@@ -669,6 +843,11 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     }
     const int64_t nG = (int64_t)tiles.size() - nS - nV;
     D.bytes = off;  // BF16 bytes; the FP32 copy is twice that
+    // the transfer passes' tiles follow in the FP32 copy only
+    FlowTiles ft;
+    const bool flow = tf32 && k <= 64 && T.leaf_size <= 64;
+    if (flow) flow_tiles(A, tiles, off, ft);
+    const int64_t off32 = off;
     int rc = 0;
     TcPackTile* d_tiles = nullptr;
     if ((rc = upload(A, &d_tiles, tiles, st))) return rc;
@@ -677,11 +856,22 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     for (int es = 2; es <= 4; es += 2) {
         if ((es == 2 && !bf16) || (es == 4 && !tf32)) continue;
         void* pm = nullptr;
-        if ((rc = device_alloc(A, &pm, (size_t)std::max<int64_t>(off * (es / 2), 128)))) return rc;
+        const int64_t total = es == 4 ? off32 : D.bytes;
+        if ((rc = device_alloc(A, &pm, (size_t)std::max<int64_t>(total * (es / 2), 128)))) return rc;
         uint8_t* dst = (uint8_t*)pm;
         if ((rc = launch_pack_tiles(d_tiles, nS, (const double*)A->f64.S, dst, es, st))) return rc;
         if ((rc = launch_pack_tiles(d_tiles + nS, nV, (const double*)A->f64.V, dst, es, st))) return rc;
         if ((rc = launch_pack_tiles(d_tiles + nS + nV, nG, (const double*)A->f64.Near, dst, es, st))) return rc;
+        if (es == 4 && flow) {
+            const int64_t f0 = nS + nV + nG;
+            if ((rc = launch_pack_tiles(d_tiles + f0, ft.n_et, (const double*)A->f64.E, dst, es, st))) return rc;
+            if ((rc = launch_pack_tiles(d_tiles + f0 + ft.n_et, ft.n_vt, (const double*)A->f64.V, dst, es, st)))
+                return rc;
+            if ((rc = launch_pack_tiles(d_tiles + f0 + ft.n_et + ft.n_vt, ft.n_e, (const double*)A->f64.E, dst, es, st)))
+                return rc;
+            H2_CUDA_TRY(cudaMemcpyAsync(dst + ft.id_off * 2, ft.ident.data(), ft.ident.size() * sizeof(float),
+                                        cudaMemcpyHostToDevice, st));
+        }
         if (es == 2) D.mat = dst; else D.mat32 = dst;
     }
     D.has_bf16 = bf16;
@@ -739,6 +929,7 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     std::stable_sort(l_items.begin(), l_items.end(),
                      [&](const TcItem& a, const TcItem& b) { return l_cost[a.id] > l_cost[b.id]; });
     snake_order(l_items, kTcGrid);
+    if (flow && (rc = flow_lists(A, ft, s_off, v_off, g_off, xkoff, st))) return rc;
     D.xk_total = xkoff[NL];
     D.c_nitems = (int)c_items.size();
     D.c_nzero = (int)c_zero.size();
@@ -883,6 +1074,46 @@ int build_tc_transposed(h2_matrix* A, cudaStream_t st) {
 #undef UP
     H2_CUDA_TRY(cudaStreamSynchronize(st));
     D.t_built = true;
+    return 0;
+}
+
+// New cut targets for the subtree schedules of the CUDA-core transfer passes
+// (h2_autotune): the schedules are rebuilt and replace the old ones, which are
+// freed once the stream has finished with them.
+int set_transfer_targets(h2_matrix* A, int up_target, int down_target, cudaStream_t st) {
+    if (up_target == A->up_target && down_target == A->down_target) return 0;
+    std::vector<int32_t> dptr, uptr;
+    std::vector<DownStep> dsteps;
+    std::vector<UpStep> usteps;
+    int32_t dn_ntasks = 0, dn_entries = 0, up_ntasks = 0, up_entries = 0;
+    down_schedule(A->T, down_target, dptr, dsteps, dn_ntasks, dn_entries);
+    up_schedule(A->T, up_target, uptr, usteps, up_ntasks, up_entries);
+    if (up_entries > kUpMaxEntries || dn_entries > 8) {
+        set_error("transfer-pass schedule needs more stack entries than the kernels hold");
+        return H2_E_UNSUPPORTED;
+    }
+    int32_t *d_dptr = nullptr, *d_uptr = nullptr;
+    DownStep* d_ds = nullptr;
+    UpStep* d_us = nullptr;
+    int rc = 0;
+    if ((rc = upload(A, &d_dptr, dptr, st)) || (rc = upload(A, &d_ds, dsteps, st)) || (rc = upload(A, &d_uptr, uptr, st)) ||
+        (rc = upload(A, &d_us, usteps, st)))
+        return rc;
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
+    release_allocation(A, A->d_dn_task_ptr);
+    release_allocation(A, A->d_dn_steps);
+    release_allocation(A, A->d_up_task_ptr);
+    release_allocation(A, A->d_up_steps);
+    A->d_dn_task_ptr = d_dptr;
+    A->d_dn_steps = d_ds;
+    A->dn_ntasks = dn_ntasks;
+    A->dn_entries = dn_entries;
+    A->d_up_task_ptr = d_uptr;
+    A->d_up_steps = d_us;
+    A->up_ntasks = up_ntasks;
+    A->up_entries = up_entries;
+    A->up_target = up_target;
+    A->down_target = down_target;
     return 0;
 }
 

@@ -72,17 +72,26 @@ struct TcPackTile {
 };
 
 // One output tile of the tcgen05 segmented GEMM: output id, its terms
-// [e0, e1), and the output width np (a multiple of 16).
+// [e0, e1), and the output width np (a multiple of 16) in the low 16 bits of
+// np; in the transfer-pass launches (mode 3) bits 16-17 give the item's role:
+// kRoleTransfer (split tile into out_act, then the ready flag), kRoleCoupling
+// (split tile into out_act2) or kRoleLeaf (FP32 rows into zp).
 struct TcItem {
     int32_t id, e0, e1, np;
 };
-// One term: an activation tile (act0 or act1 by asrc, at akoff·R·es bytes, kp
-// contraction columns) times a matrix tile (at boff BF16-bytes, scaled by es/2).
+constexpr int32_t kRoleTransfer = 1, kRoleCoupling = 2, kRoleLeaf = 3;
+__host__ __device__ inline int32_t item_np(const TcItem& t) { return t.np & 0xFFFF; }
+__host__ __device__ inline int32_t item_role(const TcItem& t) { return t.np >> 16; }
+// One term: an activation tile (act0, act1 or act2 by asrc & 3, at akoff·R·es
+// bytes, kp contraction columns) times a matrix tile (at boff BF16-bytes, scaled
+// by es/2).  In mode 3, asrc & kTermWait makes the copy wait for the ready flag
+// of cluster akoff / KP.
 struct TcTerm {
     int64_t boff;
     int32_t akoff;
     int16_t kp, asrc;
 };
+constexpr int16_t kTermWait = 4;
 
 // Arguments of the tcgen05 segmented GEMM (h2_tc.cu).  Items are processed in
 // order, item w by CTA w mod gridDim.
@@ -92,6 +101,7 @@ struct TcGemmParams {
     const TcTerm* terms;
     const uint8_t* act0;
     const uint8_t* act1;
+    const uint8_t* act2;
     const uint8_t* bmat;
     int R, mc;
     float* yhat;  // coupling output [cluster][k][ldc]
@@ -102,6 +112,14 @@ struct TcGemmParams {
     const int32_t* cl_size;
     int* err;
     int a_stage_bytes, nstages;  // filled by launch_tc_gemm
+    // transfer passes (modes 3 and 4): each item's result goes, split as the
+    // activations are, into its tile of out_act (TF32 pairs); then flag[id] = epoch
+    // tells the CTAs whose terms read that tile (mode 4 adds the coupling result
+    // yhat[id] first).  A term with asrc == 0 waits for flag[akoff / KP].
+    uint8_t* out_act;
+    uint8_t* out_act2;  // kRoleCoupling items
+    int* flag;
+    int epoch;
     // matrix-free coupling (mode 2): Chebyshev nodes [cluster][KP] (x, y, z, 0) and
     // the kernel's 1/length; S_b[ν, μ] = exp(-|ξ_{t,ν} - ξ_{s,μ}| / length) for ν, μ < k
     const float4* nodes;
@@ -149,6 +167,24 @@ struct TcData {
     TcItem* lt_items = nullptr;
     TcTerm* lt_terms = nullptr;
     int lt_nitems = 0;
+    // the transfer passes on the tensor cores (built with the TF32 copy, k <= 64):
+    // Eᵀ_s, V_tᵀ, E_s and an identity tile appended to mat32, and work lists in
+    // dependency order: the upward and the downward pass alone (used with Aᵀ),
+    // the upward pass with the coupling phase (f1) and the downward pass with the
+    // leaf phase (f2) in one launch each (used with A)
+    bool flow = false;
+    TcItem* up_items = nullptr;  // clusters by height above the leaves (sons first)
+    TcTerm* up_terms = nullptr;
+    int up_nitems = 0;
+    TcItem* dn_items = nullptr;  // clusters by level (fathers first)
+    TcTerm* dn_terms = nullptr;
+    int dn_nitems = 0;
+    TcItem* f1_items = nullptr;
+    TcTerm* f1_terms = nullptr;
+    int f1_nitems = 0;
+    TcItem* f2_items = nullptr;
+    TcTerm* f2_terms = nullptr;
+    int f2_nitems = 0;
 };
 
 // Inter-CTA bookkeeping of the one-launch transfer passes: arrival counters of
@@ -190,12 +226,28 @@ void down_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, st
 void up_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std::vector<UpStep>& steps,
                  int32_t& ntasks, int32_t& entries);
 
+// Product variants the autotuner chooses among (h2_autotune).
+enum ProductPath : int8_t {
+    kPathDefault = 0,  // built-in rule: tensor cores where built; their transfer passes where the
+                       // CUDA-core subtree passes do not apply (k % 8 != 0 or columns % 4 != 0)
+    kPathTcOwn = 1,    // tensor cores, CUDA-core transfer passes
+    kPathTcFlow = 2,   // tensor cores, tensor-core transfer passes, one launch per phase
+    kPathTcFused = 3,  // tensor cores, transfer passes sharing launches with coupling and leaf phases
+    kPathSimt = 4      // CUDA cores only (FP32)
+};
+struct Tune {
+    int8_t path = kPathDefault;
+    int8_t stages = 0;  // pipeline stages of the tensor-core kernels (0: as many as fit)
+};
+inline int column_class(int mc) { return mc <= 8 ? 0 : (mc <= 16 ? 1 : (mc <= 32 ? 2 : 3)); }
+
 struct SyncBufs {
     unsigned* cnt = nullptr;
     int* flag = nullptr;
     unsigned* claim = nullptr;
     int epoch = 0;
     int* err = nullptr;
+    int* fflag = nullptr;  // [2 × n_clusters] ready flags of the tensor-core upward and downward passes
 };
 
 struct Workspace {
@@ -265,15 +317,23 @@ struct h2_matrix {
     unsigned* sync_cnt = nullptr;  // [nc × sync_tiles]
     int* sync_flag = nullptr;      // [nc × sync_tiles]
     unsigned* sync_claim = nullptr;// [sync_tiles]
+    int* sync_fflag = nullptr;     // [2 × nc] tensor-core transfer-pass flags
     int64_t sync_tiles = 0;
     bool force_simt = false;
+    // H2_TC_TRANSFER at build: 1 forces the tensor-core transfer passes on the FP32
+    // product, 0 the CUDA-core ones; unset leaves the choice to the tuning below
+    int use_flow = -1;
+    // choices of h2_autotune per precision (0: FP32, 1: BF16) and column class
+    // (columns per 64-column chunk: <= 8, <= 16, <= 32, <= 64)
+    h2::Tune tune[2][4];
+    int32_t up_target = h2::kUpTasks, down_target = h2::kDownTasks;  // transfer-pass cut targets
     bool s_replaced = false;  // h2_coupling_set was called: S_b are no longer g's values  // H2_FORCE_SIMT=1 at build: FP32 product on the CUDA cores only
     // block-Jacobi preconditioner (h2_precond.cu): (G_(t,t) + σI)⁻¹ per leaf, built on first use
     double* bj_inv = nullptr;     // concatenated n_t×n_t inverses, leaf order
     int64_t* bj_off = nullptr;    // [n_leaves] element offset of leaf t's inverse
     double bj_sigma = 0.0;        // σ the inverses were formed with
     bool bj_valid = false;
-    std::vector<void*> allocations;
+    std::vector<std::pair<void*, size_t>> allocations;
     int64_t alloc_bytes = 0;  // bytes of `allocations` (counted against h2_set_alloc_limit)
 };
 
@@ -385,16 +445,20 @@ int tc_prepare();
 // transfer-pass bookkeeping, kernel attributes), so that the product itself
 // allocates nothing (e.g. while it is captured into a CUDA graph).
 int product_prepare(h2_matrix* A, int64_t m, int32_t dtype, cudaStream_t st);
-int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st);
+int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st, int stages = 0);
+// Rebuild the subtree schedules of the CUDA-core transfer passes for other cut targets.
+int set_transfer_targets(h2_matrix* A, int up_target, int down_target, cudaStream_t st);
 int launch_pack_tiles(const TcPackTile* tiles, int64_t count, const double* src, uint8_t* dst, int es,
                       cudaStream_t st);
 int launch_pack_act(const float* src, int64_t ld, int ids, const int32_t* idmap, const int32_t* base,
                     const int32_t* kdim, int kdim_fixed, const int64_t* koff, int kp_fixed, int mc, int R,
                     uint8_t* dst, int es, cudaStream_t st);
 int launch_zero_clusters(const int32_t* ids, int count, float* yhat, int k, int ldc, int mc, cudaStream_t st);
+int launch_zero_tiles(const int32_t* ids, int count, uint8_t* buf, int64_t tile_bytes, cudaStream_t st);
 int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st);
 // Tiles and work lists of the tensor-core product with Aᵀ (once per matrix; allocates).
 int build_tc_transposed(h2_matrix* A, cudaStream_t st);
+
 
 inline int round16(int x) { return (x + 15) & ~15; }
 
@@ -409,9 +473,13 @@ int cast_f32(const double* src, float* dst, int64_t count, cudaStream_t st);
 long long wait_limit();
 
 bool is_device_pointer(const void* p);
+// The stream is being captured into a CUDA graph (or its state cannot be read).
+bool stream_capture_active(cudaStream_t st);
 const void* mapped_host_pointer(const void* p);
 int device_alloc(h2_matrix* A, void** ptr, size_t bytes);
 // Free every device_alloc allocation of A (and take it off the library's count).
 void release_allocations(h2_matrix* A);
+// Free one of them (no-op for a pointer that is not one).
+void release_allocation(h2_matrix* A, void* p);
 
 }  // namespace h2

@@ -1044,6 +1044,8 @@ int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+
+
 int ensure_workspace(h2_matrix* A, size_t bytes, cudaStream_t st) {
     if (A->ws.bytes >= bytes) return 0;
     if (A->ws.base) {
@@ -1086,7 +1088,20 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         const int R = round16(2 * mc);
         const size_t bXp = align_up((size_t)n * mc * 4), bC = align_up((size_t)nc * k * mc * 4);
         const size_t bXcm = align_up((size_t)R * D.xk_total * es), bAct = align_up((size_t)nc * R * KP * es);
-        int rc = ensure_workspace(A, bXp + 2 * bC + bXcm + 2 * bAct, st);
+        // The variant of this column chunk: the autotuner's choice, else the built-in
+        // rule (the tensor-core transfer passes where the CUDA-core subtree passes do
+        // not apply).  The tensor-core transfer passes are FP32 only, and not used
+        // inside a stream capture, whose concurrent branches could keep some of their
+        // CTAs from being resident.
+        const Tune tn = A->tune[kind == 0 ? 1 : 0][column_class(mc)];
+        const int stg = tn.stages;
+        const bool fast = A->f32.Et && k % 8 == 0 && k <= 64 && mc % 4 == 0 && A->T.leaf_size <= 64;
+        bool want_flow = !fast;
+        if (tn.path == kPathTcOwn) want_flow = false;
+        if (tn.path == kPathTcFlow || tn.path == kPathTcFused) want_flow = true;
+        if (A->use_flow >= 0) want_flow = A->use_flow == 1;
+        const bool flow = kind == 1 && D.flow && want_flow && !stream_capture_active(st);
+        int rc = ensure_workspace(A, bXp + 2 * bC + bXcm + 3 * bAct, st);
         if (rc) return rc;
         char* base = (char*)A->ws.base;
         float* Xp = (float*)base;
@@ -1095,6 +1110,7 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         uint8_t* Xcm = (uint8_t*)(base + bXp + 2 * bC);
         uint8_t* xcm = Xcm + bXcm;
         uint8_t* ycm = xcm + bAct;
+        uint8_t* ycp = ycm + bAct;  // flow: the coupling results as split tiles
         const unsigned gy = (unsigned)((mc + NT - 1) / NT), gzk = (unsigned)((k + MT - 1) / MT);
         PhaseMarks marks(A, st);
         marks.mark();
@@ -1104,13 +1120,126 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
             k_gather<float><<<g, 256, 0, st>>>(X + c0, ldx, A->d_perm, n, mc, Xp);
             H2_LAUNCH_CHECK();
         }
-        // subtree-owning transfer passes when the rows are 16-byte multiples (k, mc % 4 == 0, k <= 64);
-        // they also write the split tiles of X (leaves), x̂ and leaf ŷ
-        const bool fast = A->f32.Et && k % 8 == 0 && k <= 64 && mc % 4 == 0 && A->T.leaf_size <= 64;
-        if (!fast && (rc = launch_pack_act(Xp, mc, NL, nullptr, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, R, Xcm, es, st)))
+        // (fast: the subtree-owning CUDA-core transfer passes apply, rows of 16-byte
+        // multiples; they also write the split tiles of X (leaves), x̂ and leaf ŷ)
+        if ((!fast || flow) &&
+            (rc = launch_pack_act(Xp, mc, NL, nullptr, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, R, Xcm, es, st)))
             return rc;
         marks.mark();
         const int fcn = mc <= 16 ? 1 : (mc <= 32 ? 2 : 4);
+        if (flow) {
+            // Both transfer passes on the tensor cores.  With A (and the stored
+            // couplings) the upward pass shares one launch with the coupling phase
+            // and the downward pass one with the leaf phase; with Aᵀ, or the
+            // matrix-free coupling, the four phases are launched one by one.
+            H2_CUDA_TRY(cudaMemsetAsync(sbc.fflag, 0, 2 * (size_t)nc * sizeof(int), st));
+            if ((rc = launch_zero_tiles(trans ? D.ct_zero : D.c_zero, trans ? D.ct_nzero : D.c_nzero, ycp,
+                                        (int64_t)KP * R * es, st)))
+                return rc;
+            TcGemmParams fp{};
+            fp.bmat = D.mat32;
+            fp.R = R;
+            fp.mc = mc;
+            fp.k = k;
+            fp.ldc = mc;
+            fp.err = A->err_dev;
+            fp.KP = KP;
+            fp.epoch = 1;
+            fp.leaves = A->d_leaves;
+            fp.cl_off = A->d_cl_off;
+            fp.cl_size = A->d_cl_size;
+            TcGemmParams f1 = fp, f2 = fp;
+            // upward items: act0 the x̂ tiles of the launch, act1 the X tiles; coupling items
+            // write the ŷ tiles of the coupling results (ycp)
+            f1.act0 = xcm;
+            f1.act1 = Xcm;
+            f1.out_act = xcm;
+            f1.out_act2 = ycp;
+            f1.flag = sbc.fflag;
+            // downward items: act0 the ŷ tiles of the launch, act1 the coupling results; leaf
+            // items: act2 the X tiles, output the rows of Z (over the gathered X)
+            f2.act0 = ycm;
+            f2.act1 = ycp;
+            f2.act2 = Xcm;
+            f2.out_act = ycm;
+            f2.flag = sbc.fflag + nc;
+            f2.zp = Xp;
+            const bool fused = !trans && !mf && tn.path != kPathTcFlow;
+            if (fused) {
+                f1.n_items = D.f1_nitems;
+                f1.items = D.f1_items;
+                f1.terms = D.f1_terms;
+                f2.n_items = D.f2_nitems;
+                f2.items = D.f2_items;
+                f2.terms = D.f2_terms;
+                marks.kernel_begin();
+                if ((rc = launch_tc_gemm(3, 1, f1, std::min(f1.n_items, grid_cap), st, stg))) return rc;
+                marks.kernel_end();
+                marks.mark();
+                marks.mark();
+                marks.mark();
+                if ((rc = launch_tc_gemm(3, 1, f2, std::min(f2.n_items, grid_cap), st, stg))) return rc;
+                marks.mark();
+            } else {
+                f1.n_items = D.up_nitems;
+                f1.items = D.up_items;
+                f1.terms = D.up_terms;
+                if ((rc = launch_tc_gemm(3, 1, f1, std::min(f1.n_items, grid_cap), st, stg))) return rc;
+                marks.mark();
+                marks.mark();
+                TcGemmParams cp{};
+                cp.n_items = trans ? D.ct_nitems : D.c_nitems;
+                cp.items = trans ? D.ct_items : D.c_items;
+                cp.terms = trans ? D.ct_terms : D.c_terms;
+                cp.act0 = xcm;
+                cp.act1 = xcm;
+                cp.bmat = trans ? D.matT32 : D.mat32;
+                cp.R = R;
+                cp.mc = mc;
+                cp.yhat = yhat;
+                cp.k = k;
+                cp.ldc = mc;
+                cp.err = A->err_dev;
+                cp.nodes = D.nodes4;
+                cp.inv_len = (float)(1.0 / A->length);
+                cp.KP = KP;
+                cp.out_act = ycp;  // split tiles for the downward pass's identity terms
+                marks.kernel_begin();
+                if (cp.n_items > 0 && (rc = launch_tc_gemm(mf ? 2 : 0, 1, cp, std::min(cp.n_items, grid_cap), st, stg)))
+                    return rc;
+                marks.kernel_end();
+                marks.mark();
+                f2.n_items = D.dn_nitems;
+                f2.items = D.dn_items;
+                f2.terms = D.dn_terms;
+                if ((rc = launch_tc_gemm(3, 1, f2, std::min(f2.n_items, grid_cap), st, stg))) return rc;
+                marks.mark();
+                TcGemmParams lp{};
+                lp.n_items = trans ? D.lt_nitems : D.l_nitems;
+                lp.items = trans ? D.lt_items : D.l_items;
+                lp.terms = trans ? D.lt_terms : D.l_terms;
+                lp.act0 = Xcm;
+                lp.act1 = ycm;
+                lp.bmat = trans ? D.matT32 : D.mat32;
+                lp.R = R;
+                lp.mc = mc;
+                lp.leaves = A->d_leaves;
+                lp.cl_off = A->d_cl_off;
+                lp.cl_size = A->d_cl_size;
+                lp.err = A->err_dev;
+                lp.zp = Xp;
+                lp.ldc = mc;
+                if ((rc = launch_tc_gemm(1, 1, lp, std::min(lp.n_items, grid_cap), st, stg))) return rc;
+            }
+            const int64_t total = n * mc;
+            const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+            k_scatter_y<<<g, 256, 0, st>>>(Xp, mc, A->d_perm, n, mc, X + c0, ldx, Y + c0, ldy, alpha, A->sigma,
+                                           overwrite ? 1 : 0);
+            H2_LAUNCH_CHECK();
+            marks.mark();
+            if ((rc = marks.commit())) return rc;
+            continue;
+        }
         if (fast) {
             if ((rc = fast_prepare())) return rc;
             const PackOut pk{xcm, Xcm, D.xkoff, KP, R, es};
@@ -1127,13 +1256,14 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         } else if ((rc = forward_pass<float, RM, CN>(A, V, E, Xp, xhat, mc, gy, gzk, st, sbc, marks))) {
             return rc;
         }
-        if (!fast && (rc = launch_pack_act(xhat, mc, (int)nc, nullptr, nullptr, nullptr, k, nullptr, KP, mc, R, xcm, es, st)))
+        if (!fast &&
+            (rc = launch_pack_act(xhat, mc, (int)nc, nullptr, nullptr, nullptr, k, nullptr, KP, mc, R, xcm, es, st)))
             return rc;
         // Aᵀ: the coupling runs over column clusters with S_bᵀ, the leaf phase over
         // column leaves with G_bᵀ (tiles and lists of build_tc_transposed)
         const uint8_t* bmat = trans ? (kind == 0 ? D.matT : D.matT32) : (kind == 0 ? D.mat : D.mat32);
-        if ((rc = launch_zero_clusters(trans ? D.ct_zero : D.c_zero, trans ? D.ct_nzero : D.c_nzero, yhat, k, mc,
-                                       mc, st)))
+        if ((rc = launch_zero_clusters(trans ? D.ct_zero : D.c_zero, trans ? D.ct_nzero : D.c_nzero, yhat, k, mc, mc,
+                                       st)))
             return rc;
         TcGemmParams cp{};
         cp.n_items = trans ? D.ct_nitems : D.c_nitems;
@@ -1152,7 +1282,8 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         cp.inv_len = (float)(1.0 / A->length);
         cp.KP = KP;
         marks.kernel_begin();
-        if (cp.n_items > 0 && (rc = launch_tc_gemm(mf ? 2 : 0, kind, cp, std::min(cp.n_items, grid_cap), st))) return rc;
+        if (cp.n_items > 0 && (rc = launch_tc_gemm(mf ? 2 : 0, kind, cp, std::min(cp.n_items, grid_cap), st, stg)))
+            return rc;
         marks.kernel_end();
         marks.mark();
         bool leaf_y_packed = false;
@@ -1192,7 +1323,7 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         lp.err = A->err_dev;
         lp.zp = Xp;  // the gathered FP32 X is no longer read after the forward pass and its packing
         lp.ldc = mc;
-        if ((rc = launch_tc_gemm(1, kind, lp, std::min(lp.n_items, grid_cap), st))) return rc;
+        if ((rc = launch_tc_gemm(1, kind, lp, std::min(lp.n_items, grid_cap), st, stg))) return rc;
         {
             const int64_t total = n * mc;
             const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
@@ -1237,16 +1368,19 @@ int ensure_sync(h2_matrix* A, int64_t tiles, cudaStream_t st, SyncBufs* sb) {
         A->sync_cnt = nullptr;
         A->sync_tiles = 0;
         const size_t per = (size_t)A->nc * tiles;
-        const size_t bytes = per * (sizeof(unsigned) + sizeof(int)) + tiles * sizeof(unsigned);
+        const size_t bytes = per * (sizeof(unsigned) + sizeof(int)) + tiles * sizeof(unsigned) +
+                             2 * (size_t)A->nc * sizeof(int);
         H2_CUDA_TRY(cudaMalloc(&A->sync_cnt, bytes));
         H2_CUDA_TRY(cudaMemsetAsync(A->sync_cnt, 0, bytes, st));
         A->sync_flag = (int*)(A->sync_cnt + per);
         A->sync_claim = (unsigned*)(A->sync_flag + per);
+        A->sync_fflag = (int*)(A->sync_claim + tiles);
         A->sync_tiles = tiles;
     }
     sb->cnt = A->sync_cnt;
     sb->flag = A->sync_flag;
     sb->claim = A->sync_claim;
+    sb->fflag = A->sync_fflag;
     sb->epoch = 1;  // flags are cleared before every downward pass
     sb->err = A->err_dev;
     return 0;
@@ -1283,7 +1417,8 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
     }
     if (dtype == H2_F32) {
         if (!A->f32.built) { set_error("FP32 copy not built (add 1<<H2_F32 to params->precisions)"); return H2_E_UNSUPPORTED; }
-        if (A->tc.has_tf32 && !A->force_simt)
+        const Tune& tn = A->tune[0][column_class((int)std::min<int64_t>(m, 64))];
+        if (A->tc.has_tf32 && !A->force_simt && tn.path != kPathSimt)
             return dispatch_tc(A, 1, alpha, X, ldx, Y, ldy, m, st, overwrite, sb, transposed);
         return dispatch_cn<float>(A, A->f32, alpha, X, ldx, Y, ldy, (int)m, st, transposed, overwrite,
                                   (float*)base, (float*)(base + bXp), (float*)(base + bXp + bC), sb);
@@ -1314,14 +1449,15 @@ int product_prepare(h2_matrix* A, int64_t m, int32_t dtype, cudaStream_t st) {
     const int64_t n = A->n, nc = A->nc;
     const int k = A->k;
     size_t need = 0;
-    const bool tc = (dtype == H2_BF16) || ((dtype == H2_F32 || dtype == H2_F32_MF) && A->tc.has_tf32 && !A->force_simt);
+    const bool tc = (dtype == H2_BF16) || ((dtype == H2_F32 || dtype == H2_F32_MF) && A->tc.has_tf32 && !A->force_simt &&
+                                           A->tune[0][column_class((int)std::min<int64_t>(m, 64))].path != kPathSimt);
     if (tc) {
         const TcData& D = A->tc;
         const int es = dtype == H2_BF16 ? 2 : 4;
         const int mc = (int)std::min<int64_t>(64, m);
         const int R = round16(2 * mc);
         need = align_up((size_t)n * mc * 4) + 2 * align_up((size_t)nc * k * mc * 4) +
-               align_up((size_t)R * D.xk_total * es) + 2 * align_up((size_t)nc * R * D.KP * es);
+               align_up((size_t)R * D.xk_total * es) + 3 * align_up((size_t)nc * R * D.KP * es);
         if ((rc = tc_prepare())) return rc;
     } else {
         const size_t elt = dtype == H2_F64 ? sizeof(double) : sizeof(float);

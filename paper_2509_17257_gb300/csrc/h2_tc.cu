@@ -125,6 +125,25 @@ __device__ __forceinline__ bool bar_red_or(int id, int count, bool pred) {
     return r != 0;
 }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// Ready flags of the transfer passes: the writer's generic stores are made
+// visible to the bulk copies (async proxy) of other CTAs by a proxy fence and a
+// release store; the reader acquires the flag and fences again before copying.
+__device__ __forceinline__ int flag_acquire(const int* f) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+    return v;
+}
+__device__ __forceinline__ void flag_release(int* f, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
 // x - tf32(x) per component: what the TF32 MMA drops from an FP32 operand
@@ -262,10 +281,19 @@ __global__ void k_pack_act(const float* __restrict__ src, int64_t ld, int ids, c
 // MODE 0: coupling (outputs ŷ_t); MODE 1: leaf phase (outputs Z); MODE 2 (KIND 1
 // only): coupling without the stored S_b, whose rows the splitter warps evaluate
 // from the Chebyshev nodes (Eq. (h2_admissible)): only the activation tile is
-// copied.
+// copied.  MODE 3 (KIND 1 only): a work list in dependency order whose items
+// carry their role (item_role): transfer-pass items (Alg. "forward/backward",
+// one per cluster) put their result, split, into the cluster's activation tile
+// and release it with a ready flag; coupling items write split tiles; leaf items
+// write rows of Z.  A term marked kTermWait waits (bounded) for the ready flag
+// of the tile it reads before its copy.
 template <int MODE, int KIND>
 __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmParams p) {
     constexpr bool MF = MODE == 2;
+    constexpr bool FLOW = MODE == 3;
+    // the coupling writes its result as split tiles when the downward pass runs on
+    // the tensor cores (p.out_act set)
+    const bool COUP_SPLIT = (MODE == 0 || MODE == 2) && p.out_act != nullptr;
     constexpr int ES = KIND == 0 ? 2 : 4;
     constexpr int KSTEP = KIND == 0 ? 16 : 8;  // K of one MMA instruction
     constexpr int F_FIRST = 1, F_LAST = 2, F_END = 4;
@@ -356,22 +384,50 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                     if (base + lane < nterms) t = p.terms[cur.e0 + base + lane];
                 }
                 const int cnt = min(32, nterms - base);
+                // Terms that read a tile of this launch wait for its ready flag.  The
+                // lanes poll the flags of the batch's terms together (one round trip
+                // for all), and lane 0 issues a term's copies once its bit is set.
+                uint32_t ready_mask = 0xffffffffu;
+                const int* my_flag = nullptr;
+                if (FLOW) {
+                    if (lane < cnt && (t.asrc & kTermWait)) my_flag = p.flag + t.akoff / p.KP;
+                    ready_mask = __ballot_sync(0xffffffffu, !my_flag || flag_acquire(my_flag) == p.epoch);
+                    __syncwarp();
+                }
+                const uint64_t t_batch = FLOW ? global_ns() : 0;
                 for (int j = 0; j < cnt; ++j) {
                     const int kpj = __shfl_sync(0xffffffffu, (int)t.kp, j);
                     const int asj = __shfl_sync(0xffffffffu, (int)t.asrc, j);
                     const int64_t bj = __shfl_sync(0xffffffffu, t.boff, j);
-                    const int64_t aj = (int64_t)__shfl_sync(0xffffffffu, t.akoff, j) * R * ES;
+                    const int akj = __shfl_sync(0xffffffffu, t.akoff, j);
+                    const int64_t aj = (int64_t)akj * R * ES;
+                    bool ready = true;
+                    if (FLOW && !((ready_mask >> j) & 1u)) {
+                        // poll again (bounded: gives up after about one second)
+                        while (true) {
+                            __nanosleep(32);
+                            ready_mask |= __ballot_sync(0xffffffffu, my_flag && flag_acquire(my_flag) == p.epoch);
+                            __syncwarp();
+                            if ((ready_mask >> j) & 1u) break;
+                            if (__any_sync(0xffffffffu, abort_flag || global_ns() - t_batch > 1000000000ull)) {
+                                ready = false;  // warp-uniform: every lane leaves together
+                                break;
+                            }
+                        }
+                    }
                     int bad = 0;
                     if (lane == 0) {
-                        if (!mbar_wait(&empty_bar[stage], phase ^ 1)) {
+                        // the flags acquired by the warp order the tiles' writes before this copy
+                        if (FLOW && (asj & kTermWait)) fence_proxy_async_global();
+                        if (!ready || !mbar_wait(&empty_bar[stage], phase ^ 1)) {
                             bad = 1;
                         } else {
                             const uint32_t ab = (uint32_t)(R * kpj * ES);
-                            const uint32_t bb = (uint32_t)(cur.np * kpj * ES);
+                            const uint32_t bb = (uint32_t)(item_np(cur) * kpj * ES);
                             uint8_t* sA = smem + stage * stage_bytes;
                             uint8_t* sB = sA + a_bytes;
                             stage_kp[stage] = kpj;
-                            stage_np[stage] = cur.np;
+                            stage_np[stage] = item_np(cur);
                             stage_fl[stage] = (base + j == 0 ? F_FIRST : 0) | (base + j == nterms - 1 ? F_LAST : 0);
                             if (MF) {
                                 // the source cluster: the activation rows of cluster s start at s·KP
@@ -381,7 +437,8 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                                 bulk_g2s(sA, (asj ? p.act1 : p.act0) + aj, ab, &full_bar[stage]);
                             } else {
                                 mbar_expect_tx(&full_bar[stage], ab + bb);
-                                bulk_g2s(sA, (asj ? p.act1 : p.act0) + aj, ab, &full_bar[stage]);
+                                const uint8_t* asrc = (asj & 3) == 0 ? p.act0 : ((asj & 3) == 1 ? p.act1 : p.act2);
+                                bulk_g2s(sA, asrc + aj, ab, &full_bar[stage]);
                                 bulk_g2s(sB, p.bmat + bj * (ES / 2), bb, &full_bar[stage]);
                             }
                             pend_mask |= 1u << stage;
@@ -501,9 +558,11 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
         const bool wide = R > 64;
         const bool vec4 = (p.mc & 3) == 0 && (p.ldc & 3) == 0;
         int it = 0, par = 0;
+        // rows of Z: the leaf phase, and the leaf items of a transfer-pass launch
+        auto leaf_rows = [&](const TcItem& t) { return MODE == 1 || (FLOW && item_role(t) == kRoleLeaf); };
         TcItem cur = blockIdx.x < p.n_items ? p.items[blockIdx.x] : TcItem{-1, 0, 0, 0};
         int cur_off = 0, cur_nt = 0;
-        if (MODE == 1 && cur.id >= 0) {
+        if (cur.id >= 0 && leaf_rows(cur)) {
             const int t = p.leaves[cur.id];
             cur_off = p.cl_off[t];
             cur_nt = p.cl_size[t];
@@ -511,12 +570,14 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
         for (int w = blockIdx.x; w < p.n_items; w += G) {
             const TcItem nxt = w + G < p.n_items ? p.items[w + G] : TcItem{-1, 0, 0, 0};
             int nxt_off = 0, nxt_nt = 0;
-            if (MODE == 1 && nxt.id >= 0) {
+            if (nxt.id >= 0 && leaf_rows(nxt)) {
                 const int t = p.leaves[nxt.id];
                 nxt_off = p.cl_off[t];
                 nxt_nt = p.cl_size[t];
             }
-            const int id = cur.id, np = cur.np, nterms = cur.e1 - cur.e0;
+            const int id = cur.id, np = item_np(cur), nterms = cur.e1 - cur.e0;
+            const int role = FLOW ? item_role(cur) : 0;
+            const bool split_out = COUP_SPLIT || (FLOW && role != kRoleLeaf);
             float sum[kAccCols];
 #pragma unroll
             for (int j = 0; j < kAccCols; ++j) sum[j] = 0.f;
@@ -560,12 +621,57 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 abort_flag = 1;
                 break;
             }
-            if (!lo_part) {
+            if (!lo_part && split_out) {
+#pragma unroll
+                for (int i = 0; i < kAccCols; ++i)
+                    if (i < p.mc) sum[i] += xb[i * 64 + n];
+                // The result goes, split as the activations are (rows 2i: x; 2i + 1: x -
+                // tf32(x); zero past the columns and past column k), into the cluster's
+                // tile: staged in this item's exchange buffer (free once both tile warps
+                // have read it) and stored by one bulk copy per 64 rows.
+                asm volatile("bar.sync 4, 64;" ::: "memory");
+                uint8_t* gtile = (role == kRoleCoupling ? p.out_act2 : p.out_act) + (int64_t)id * p.KP * R * 4;
+                const bool nv = n < p.k;
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int h0 = 64 * hh;
+                    if (h0 >= R) break;
+                    const int rows = min(64, R - h0);
+                    if (h0 > 0) asm volatile("bar.sync 4, 64;" ::: "memory");  // the last store read the buffer
+                    if (n < p.KP) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            if (2 * i >= rows) break;
+                            const int ii = 32 * hh + i;
+                            const float v = (nv && ii < p.mc) ? sum[ii] : 0.f;
+                            const float lo = v - __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+                            *(float*)((uint8_t*)xb + cm_off(2 * i, n, p.KP, 4)) = v;
+                            *(float*)((uint8_t*)xb + cm_off(2 * i + 1, n, p.KP, 4)) = lo;
+                        }
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("bar.sync 4, 64;" ::: "memory");
+                    if (q == 0 && lane == 0) {
+                        const uint32_t bytes = (uint32_t)(rows * p.KP * 4);
+                        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
+                                         gtile + (int64_t)h0 * p.KP * 4),
+                                     "r"(smem_u32(xb)), "r"(bytes)
+                                     : "memory");
+                        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+                    }
+                }
+                // the tile is in global memory: release it to the CTAs that wait for it
+                if (FLOW && role == kRoleTransfer && q == 0 && lane == 0) {
+                    fence_proxy_async_global();
+                    flag_release(p.flag + id, p.epoch);
+                }
+            } else if (!lo_part) {
 #pragma unroll
                 for (int i = 0; i < kAccCols; ++i)
                     if (i < p.mc) sum[i] += xb[i * 64 + n];
                 float* out = nullptr;
-                if (MODE != 1) {
+                if (!leaf_rows(cur)) {
                     if (n < np && n < p.k) out = p.yhat + ((int64_t)id * p.k + n) * p.ldc;
                 } else {
                     // Z in cluster order; the scatter into Y (with α, σX) is a separate
@@ -797,6 +903,14 @@ __global__ void k_zero_clusters(const int32_t* __restrict__ ids, int count, floa
     }
 }
 
+// Zero the activation tiles (bytes each, a multiple of 16) of the clusters ids[0..count).
+__global__ void k_zero_tiles(const int32_t* __restrict__ ids, int count, uint8_t* __restrict__ buf, int64_t bytes) {
+    for (int c = blockIdx.x; c < count; c += gridDim.x) {
+        uint4* t = reinterpret_cast<uint4*>(buf + (int64_t)ids[c] * bytes);
+        for (int64_t e = threadIdx.x; e < bytes / 16; e += blockDim.x) t[e] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
 // Stage geometry for R activation rows and element size es: A holds R rows,
 // B 64 rows, both with up to 64 contraction columns.  The TF32 kernel keeps
 // its epilogue exchange tile (kXchBytes) after the stages (its B_lo lives in
@@ -830,13 +944,16 @@ int tc_prepare() {
     H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     g_tc_attr_device = dev;
     return 0;
 }
 
-int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st) {
+int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st, int stages) {
     int a_bytes, stage_bytes, nstages;
     tc_stage_geometry(p.R, kind == 0 ? 2 : 4, &a_bytes, &stage_bytes, &nstages);
+    // a tuned stage count (h2_autotune) below the number that fits
+    if (stages >= 2 && stages < nstages) nstages = stages;
     // A parity wait is exact only while its waiter cannot get two uses of a stage
     // ahead (the protocol model in tests/test_pipeline_protocol.py checks this).
     // The FP32 issuers wait on the in-order splitter, which keeps them in step.
@@ -854,6 +971,12 @@ int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st
     if (mode == 2) {
         if (kind != 1) { set_error("matrix-free coupling runs on the TF32 path only"); return H2_E_UNSUPPORTED; }
         return launch_one<2, 1>(p, grid, smem, st);
+    }
+    if (mode == 3) {
+        if (kind != 1) { set_error("the tensor-core transfer passes run on the TF32 path only"); return H2_E_UNSUPPORTED; }
+        // its CTAs wait on each other's ready flags: one CTA per SM, at most one per SM
+        // of the device, so that every CTA is resident (the waits are bounded in any case)
+        return launch_one<3, 1>(p, grid, smem, st);
     }
     if (mode == 0 && kind == 0) return launch_one<0, 0>(p, grid, smem, st);
     if (mode == 1 && kind == 0) return launch_one<1, 0>(p, grid, smem, st);
@@ -876,6 +999,13 @@ int launch_pack_act(const float* src, int64_t ld, int ids, const int32_t* idmap,
     if (ids <= 0) return 0;
     const unsigned g = (unsigned)std::min(ids, 152 * 8);
     k_pack_act<<<g, 256, 0, st>>>(src, ld, ids, idmap, base, kdim, kdim_fixed, koff, kp_fixed, mc, R, dst, es);
+    H2_LAUNCH_CHECK();
+    return 0;
+}
+
+int launch_zero_tiles(const int32_t* ids, int count, uint8_t* buf, int64_t tile_bytes, cudaStream_t st) {
+    if (count <= 0) return 0;
+    k_zero_tiles<<<(unsigned)std::min(count, 152 * 8), 256, 0, st>>>(ids, count, buf, tile_bytes);
     H2_LAUNCH_CHECK();
     return 0;
 }

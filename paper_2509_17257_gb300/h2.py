@@ -79,6 +79,18 @@ class CGResult(C.Structure):
                 ("rel_residual", C.POINTER(C.c_double)), ("seconds", C.c_double)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("dtype", C.c_int32), ("m", C.c_int32), ("path", C.c_int32), ("stages", C.c_int32),
+                ("up_target", C.c_int32), ("down_target", C.c_int32), ("n_candidates", C.c_int32),
+                ("ms_best", C.c_double), ("ms", C.c_double * 16), ("cand_path", C.c_int32 * 16),
+                ("cand_stages", C.c_int32 * 16), ("cand_up", C.c_int32 * 16), ("cand_down", C.c_int32 * 16)]
+
+
+#: product paths of h2_autotune_ex
+TUNE_PATHS = {1: "tensor cores, CUDA-core transfer passes", 2: "tensor cores, tensor-core transfer passes",
+              3: "tensor cores, transfer passes fused with coupling and leaf phases", 4: "CUDA cores"}
+
+
 class TreeView(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_clusters", C.c_int64), ("n_adm", C.c_int64), ("n_near", C.c_int64),
                 ("depth", C.c_int32),
@@ -94,7 +106,7 @@ class TreeView(C.Structure):
 EXPORTS = ["h2_build", "h2_free", "h2_info", "h2_matmul", "h2_matmul_transposed", "h2_matmul_noalloc", "h2_block_cg", "h2_block_gmres",
            "h2_timing_enable", "h2_timing_query", "h2_coupling_get", "h2_coupling_set", "h2_shift_set",
            "h2_adjoint_grads", "h2_batch_create", "h2_batch_free", "h2_batch_matmul", "h2_batch_block_cg",
-           "h2_autotune",
+           "h2_autotune", "h2_autotune_ex",
            "h2_tree_build", "h2_tree_view_get", "h2_tree_free", "h2_tree_schedule", "h2_set_alloc_limit",
            "h2_alloc_bytes", "h2_set_wait_limit", "h2_last_error_string", "h2_version"]
 H2_NPHASE = 8
@@ -130,6 +142,7 @@ def lib() -> C.CDLL:
     L.h2_batch_block_cg.argtypes = [vp, C.POINTER(vp), C.POINTER(i64), C.POINTER(vp), C.POINTER(i64),
                                     C.POINTER(i64), C.POINTER(CGParams), C.POINTER(CGResult)]
     L.h2_autotune.argtypes = [vp, i64, vp, C.POINTER(C.c_double)]
+    L.h2_autotune_ex.argtypes = [vp, i64, i32, vp, C.POINTER(TuneResult)]
     L.h2_timing_enable.argtypes = [vp, i32]
     L.h2_timing_query.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
     L.h2_tree_build.argtypes = [C.POINTER(BuildParams), vp, i64, C.POINTER(vp)]
@@ -402,6 +415,17 @@ def h2_autotune(handle, m: int, stream=None):
     ms = (C.c_double * 2)()
     _check(lib().h2_autotune(handle, int(m), _stream_ptr(stream), ms), "h2_autotune")
     return ms[0], ms[1]
+
+
+def h2_autotune_ex(handle, m: int, dtype="f32", stream=None) -> dict:
+    """Tune the product of m columns in dtype for this matrix (path, stage count,
+    transfer-pass cuts); returns the choice and every candidate's time."""
+    r = TuneResult()
+    _check(lib().h2_autotune_ex(handle, int(m), DTYPES[dtype], _stream_ptr(stream), C.byref(r)), "h2_autotune_ex")
+    cands = [dict(path=r.cand_path[i], stages=r.cand_stages[i], up_target=r.cand_up[i], down_target=r.cand_down[i],
+                  ms=r.ms[i]) for i in range(r.n_candidates)]
+    return dict(path=r.path, path_name=TUNE_PATHS.get(r.path, "?"), stages=r.stages, up_target=r.up_target,
+                down_target=r.down_target, ms=r.ms_best, candidates=cands)
 
 
 class H2Batch:
