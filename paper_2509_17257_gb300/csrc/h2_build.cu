@@ -688,6 +688,14 @@ void order_by_key(std::vector<KeyedItem>& v, std::vector<TcItem>& out) {
     }
 }
 
+// Items of several work lists merged by key (snake order over the CTAs within a
+// key), for the multi-system launches of h2_batch_matmul.
+void merge_by_key(const std::vector<int32_t>& keys, const std::vector<TcItem>& items, std::vector<TcItem>& out) {
+    std::vector<KeyedItem> v(keys.size());
+    for (size_t i = 0; i < keys.size(); ++i) v[i] = KeyedItem{keys[i], items[i]};
+    order_by_key(v, out);
+}
+
 int flow_lists(h2_matrix* A, const FlowTiles& ft, const std::vector<int64_t>& s_off,
                const std::vector<int64_t>& v_off, const std::vector<int64_t>& g_off,
                const std::vector<int64_t>& xkoff, cudaStream_t st) {
@@ -732,8 +740,9 @@ int flow_lists(h2_matrix* A, const FlowTiles& ft, const std::vector<int64_t>& s_
     order_by_key(up_k, up_items);
     order_by_key(dn_k, dn_items);
     // f1: every CTA takes its upward items first (they form the dependency chain),
-    // then its coupling items, those whose sources are ready earliest first
-    const int32_t hmax_all = height[0];
+    // then its coupling items, those whose sources are ready earliest first (keys
+    // from kLateKey on; heights and levels stay below it, trees being shallower)
+    constexpr int32_t kLateKey = 4096;
     std::vector<TcTerm> f1_terms = up_terms;
     std::vector<KeyedItem> f1_k = up_k;
     for (int64_t c = 0; c < nc; ++c) {
@@ -746,7 +755,7 @@ int flow_lists(h2_matrix* A, const FlowTiles& ft, const std::vector<int64_t>& s_
             hmax = std::max(hmax, height[sc]);
             f1_terms.push_back(TcTerm{s_off[j], (int32_t)((int64_t)sc * KP), (int16_t)KP, kAct0Wait});
         }
-        f1_k.push_back(KeyedItem{hmax_all + 1 + hmax, TcItem{(int32_t)c, e0, (int32_t)f1_terms.size(),
+        f1_k.push_back(KeyedItem{kLateKey + hmax, TcItem{(int32_t)c, e0, (int32_t)f1_terms.size(),
                                                       np_role(NP, kRoleCoupling)}});
     }
     // f2: the downward items first, then the leaf items, shallow leaves (ready first)
@@ -765,10 +774,16 @@ int flow_lists(h2_matrix* A, const FlowTiles& ft, const std::vector<int64_t>& s_
                                           (int16_t)round16((int)T.size[sc]), (int16_t)2});
             }
             f2_terms.push_back(TcTerm{v_off[lp], (int32_t)((int64_t)t * KP), (int16_t)KP, kAct0Wait});
-            f2_k.push_back(KeyedItem{A->depth + 1 + T.level[t], TcItem{(int32_t)lp, e0, (int32_t)f2_terms.size(),
+            f2_k.push_back(KeyedItem{kLateKey + T.level[t], TcItem{(int32_t)lp, e0, (int32_t)f2_terms.size(),
                                                                 np_role(round16((int)T.size[t]), kRoleLeaf)}});
         }
     }
+    D.f1_keys.clear();
+    D.f1_host.clear();
+    for (const auto& ki : f1_k) { D.f1_keys.push_back(ki.key); D.f1_host.push_back(ki.it); }
+    D.f2_keys.clear();
+    D.f2_host.clear();
+    for (const auto& ki : f2_k) { D.f2_keys.push_back(ki.key); D.f2_host.push_back(ki.it); }
     std::vector<TcItem> f1_items, f2_items;
     order_by_key(f1_k, f1_items);
     order_by_key(f2_k, f2_items);

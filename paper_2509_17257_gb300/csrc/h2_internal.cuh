@@ -81,7 +81,7 @@ struct TcItem {
 };
 constexpr int32_t kRoleTransfer = 1, kRoleCoupling = 2, kRoleLeaf = 3;
 __host__ __device__ inline int32_t item_np(const TcItem& t) { return t.np & 0xFFFF; }
-__host__ __device__ inline int32_t item_role(const TcItem& t) { return t.np >> 16; }
+__host__ __device__ inline int32_t item_role(const TcItem& t) { return (t.np >> 16) & 3; }
 // One term: an activation tile (act0, act1 or act2 by asrc & 3, at akoff·R·es
 // bytes, kp contraction columns) times a matrix tile (at boff BF16-bytes, scaled
 // by es/2).  In mode 3, asrc & kTermWait makes the copy wait for the ready flag
@@ -92,6 +92,26 @@ struct TcTerm {
     int16_t kp, asrc;
 };
 constexpr int16_t kTermWait = 4;
+
+// The per-system arguments of a multi-system launch of the tcgen05 segmented
+// GEMM (one launch serving several H² matrices, h2_batch_matmul): an item's
+// system index (item_sys) selects its terms, buffers and sizes.
+struct TcSys {
+    const TcTerm* terms;
+    const uint8_t* act0;
+    const uint8_t* act1;
+    const uint8_t* act2;
+    const uint8_t* bmat;
+    uint8_t* out_act;
+    uint8_t* out_act2;
+    int* flag;
+    float* zp;
+    const int32_t* leaves;
+    const int32_t* cl_off;
+    const int32_t* cl_size;
+    int R, mc, k, KP, ldc, pad;
+};
+__host__ __device__ inline int32_t item_sys(const TcItem& t) { return (int32_t)((uint32_t)t.np >> 18); }
 
 // Arguments of the tcgen05 segmented GEMM (h2_tc.cu).  Items are processed in
 // order, item w by CTA w mod gridDim.
@@ -120,6 +140,9 @@ struct TcGemmParams {
     uint8_t* out_act2;  // kRoleCoupling items
     int* flag;
     int epoch;
+    // mode 3 with several systems: per-system arguments (items carry their system in
+    // bits 18.. of np); the launch-wide R is the largest system's
+    const TcSys* sys;
     // matrix-free coupling (mode 2): Chebyshev nodes [cluster][KP] (x, y, z, 0) and
     // the kernel's 1/length; S_b[ν, μ] = exp(-|ξ_{t,ν} - ξ_{s,μ}| / length) for ν, μ < k
     const float4* nodes;
@@ -185,6 +208,10 @@ struct TcData {
     TcItem* f2_items = nullptr;
     TcTerm* f2_terms = nullptr;
     int f2_nitems = 0;
+    // the f1 and f2 items with their sort keys, on the host, for the work lists of
+    // launches that serve several matrices (h2_batch_matmul)
+    std::vector<int32_t> f1_keys, f2_keys;
+    std::vector<TcItem> f1_host, f2_host;
 };
 
 // Inter-CTA bookkeeping of the one-launch transfer passes: arrival counters of
@@ -407,6 +434,13 @@ struct h2_batch {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t mm_exec = nullptr;  // cached product graph
     std::vector<int64_t> mm_key;
+    // FP32 products whose upward/coupling and downward/leaf phases run as one
+    // launch each over the items of every system (multi-system work lists)
+    bool multi_launch = true;  // H2_BATCH_MULTI=0 at h2_batch_create: one graph branch per system instead
+    cudaGraphExec_t flow_exec = nullptr;
+    std::vector<int64_t> flow_key;
+    void* flow_mem = nullptr;  // merged item lists and system tables on the device
+    size_t flow_bytes = 0;
 };
 
 namespace h2 {
@@ -430,6 +464,23 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
              const h2_cg_params* p, h2_cg_result* res);
 int block_gmres(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
                 const h2_gmres_params* p, h2_cg_result* res);
+
+// Buffers of one matrix's FP32 tensor-core product of m <= 64 columns whose
+// upward/coupling and downward/leaf phases run in multi-system launches
+// (h2_batch_matmul): flow_prepare sizes them, flow_pre gathers X, packs its
+// tiles and clears the flags, flow_post scatters Y += α(Z + σX).
+struct FlowBufs {
+    float* Xp;
+    uint8_t *Xcm, *xcm, *ycm, *ycp;
+    int* fflag;
+    int R, mc;
+};
+bool flow_batchable(const h2_matrix* A, int64_t m);
+void merge_by_key(const std::vector<int32_t>& keys, const std::vector<TcItem>& items, std::vector<TcItem>& out);
+int flow_prepare(h2_matrix* A, int m, cudaStream_t st, FlowBufs* fb);
+int flow_pre(h2_matrix* A, const double* X, int64_t ldx, const FlowBufs& fb, cudaStream_t st);
+int flow_post(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, const FlowBufs& fb,
+              cudaStream_t st);
 
 // Bytes of scratch one product needs (gathered X, x̂, ŷ, transfer-pass
 // bookkeeping), and the product run in caller-provided scratch of at least

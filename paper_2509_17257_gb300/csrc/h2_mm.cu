@@ -1468,6 +1468,63 @@ int product_prepare(h2_matrix* A, int64_t m, int32_t dtype, cudaStream_t st) {
     return ensure_sync(A, sync_tiles_for(m), st, &sb);
 }
 
+bool flow_batchable(const h2_matrix* A, int64_t m) {
+    return m >= 1 && m <= 64 && A->f32.built && A->tc.has_tf32 && A->tc.flow && !A->force_simt;
+}
+
+// The workspace layout of run_chain_tc for one chunk of m <= 64 columns (FP32).
+int flow_prepare(h2_matrix* A, int m, cudaStream_t st, FlowBufs* fb) {
+    const TcData& D = A->tc;
+    const int k = A->k, KP = D.KP, es = 4;
+    const int64_t n = A->n, nc = A->nc;
+    const int R = round16(2 * m);
+    const size_t bXp = align_up((size_t)n * m * 4), bC = align_up((size_t)nc * k * m * 4);
+    const size_t bXcm = align_up((size_t)R * D.xk_total * es), bAct = align_up((size_t)nc * R * KP * es);
+    int rc = ensure_workspace(A, bXp + 2 * bC + bXcm + 3 * bAct, st);
+    if (rc) return rc;
+    SyncBufs sb;
+    if ((rc = ensure_sync(A, 1, st, &sb))) return rc;
+    if ((rc = tc_prepare())) return rc;
+    char* base = (char*)A->ws.base;
+    fb->Xp = (float*)base;
+    fb->Xcm = (uint8_t*)(base + bXp + 2 * bC);
+    fb->xcm = fb->Xcm + bXcm;
+    fb->ycm = fb->xcm + bAct;
+    fb->ycp = fb->ycm + bAct;
+    fb->fflag = sb.fflag;
+    fb->R = R;
+    fb->mc = m;
+    return 0;
+}
+
+// Before the multi-system launches: X into cluster order and its leaf tiles, the
+// ready flags cleared, zero coupling tiles for clusters without couplings.
+int flow_pre(h2_matrix* A, const double* X, int64_t ldx, const FlowBufs& fb, cudaStream_t st) {
+    const TcData& D = A->tc;
+    const int64_t n = A->n, nc = A->nc;
+    const int mc = fb.mc, NL = (int)A->leaves.size();
+    const int64_t total = n * mc;
+    const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    k_gather<float><<<g, 256, 0, st>>>(X, ldx, A->d_perm, n, mc, fb.Xp);
+    H2_LAUNCH_CHECK();
+    int rc = launch_pack_act(fb.Xp, mc, NL, nullptr, D.leaf_base, D.leaf_kdim, 0, D.xkoff, 0, mc, fb.R, fb.Xcm, 4, st);
+    if (rc) return rc;
+    H2_CUDA_TRY(cudaMemsetAsync(fb.fflag, 0, 2 * (size_t)nc * sizeof(int), st));
+    return launch_zero_tiles(D.c_zero, D.c_nzero, fb.ycp, (int64_t)D.KP * fb.R * 4, st);
+}
+
+// After them: Y += α(Z + σX) in the caller's order.
+int flow_post(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, const FlowBufs& fb,
+              cudaStream_t st) {
+    const int64_t n = A->n;
+    const int mc = fb.mc;
+    const int64_t total = n * mc;
+    const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    k_scatter_y<<<g, 256, 0, st>>>(fb.Xp, mc, A->d_perm, n, mc, X, ldx, Y, ldy, alpha, A->sigma, 0);
+    H2_LAUNCH_CHECK();
+    return 0;
+}
+
 int forward_transform_f64(h2_matrix* A, const double* X, int64_t ldx, int64_t m, double* Xp, double* xhat,
                           cudaStream_t st) {
     if (m <= 0) return 0;

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
     __shared__ __align__(8) uint64_t accf_bar[kAccBufs], acce_bar[kAccBufs], drain_bar[2], aempty_bar[kASlots];
     __shared__ int s_total;  // terms of this CTA
     __shared__ uint32_t tmem_slot;
-    __shared__ int stage_kp[kMaxStages], stage_np[kMaxStages], stage_fl[kMaxStages];
+    __shared__ int stage_kp[kMaxStages], stage_np[kMaxStages], stage_fl[kMaxStages], stage_R[kMaxStages];
     __shared__ int stage_t[kMaxStages], stage_s[kMaxStages];  // MODE 2: target and source cluster
     __shared__ int abort_shared;
     volatile int& abort_flag = abort_shared;
@@ -369,19 +369,23 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
         uint32_t phase = 0;
         uint32_t pend_mask = 0, pend_par = 0;
         bool aborted = false;
+        // an item's system: its terms, buffers and sizes (PSYS reads a field of the
+        // system table of a multi-system launch, else of the launch's own arguments)
+#define PSYS(it_, f_) ((FLOW && p.sys) ? p.sys[item_sys(it_)].f_ : p.f_)
         TcItem cur = blockIdx.x < p.n_items ? p.items[blockIdx.x] : TcItem{-1, 0, 0, 0};
         TcTerm tcur{};
-        if (cur.id >= 0 && lane < cur.e1 - cur.e0) tcur = p.terms[cur.e0 + lane];
+        if (cur.id >= 0 && lane < cur.e1 - cur.e0) tcur = PSYS(cur, terms)[cur.e0 + lane];
         for (int w = blockIdx.x; w < p.n_items && !aborted; w += G) {
             aborted = abort_flag != 0;
             const int wn = w + G;
             const TcItem nxt = wn < p.n_items ? p.items[wn] : TcItem{-1, 0, 0, 0};
             const int nterms = cur.e1 - cur.e0;
+            const int Ri = PSYS(cur, R);
             for (int base = 0; base < nterms && !aborted; base += 32) {
                 TcTerm t = tcur;
                 if (base > 0) {
                     t = TcTerm{};
-                    if (base + lane < nterms) t = p.terms[cur.e0 + base + lane];
+                    if (base + lane < nterms) t = PSYS(cur, terms)[cur.e0 + base + lane];
                 }
                 const int cnt = min(32, nterms - base);
                 // Terms that read a tile of this launch wait for its ready flag.  The
@@ -390,7 +394,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 uint32_t ready_mask = 0xffffffffu;
                 const int* my_flag = nullptr;
                 if (FLOW) {
-                    if (lane < cnt && (t.asrc & kTermWait)) my_flag = p.flag + t.akoff / p.KP;
+                    if (lane < cnt && (t.asrc & kTermWait)) my_flag = PSYS(cur, flag) + t.akoff / PSYS(cur, KP);
                     ready_mask = __ballot_sync(0xffffffffu, !my_flag || flag_acquire(my_flag) == p.epoch);
                     __syncwarp();
                 }
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                     const int asj = __shfl_sync(0xffffffffu, (int)t.asrc, j);
                     const int64_t bj = __shfl_sync(0xffffffffu, t.boff, j);
                     const int akj = __shfl_sync(0xffffffffu, t.akoff, j);
-                    const int64_t aj = (int64_t)akj * R * ES;
+                    const int64_t aj = (int64_t)akj * Ri * ES;
                     bool ready = true;
                     if (FLOW && !((ready_mask >> j) & 1u)) {
                         // poll again (bounded: gives up after about one second)
@@ -422,12 +426,13 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                         if (!ready || !mbar_wait(&empty_bar[stage], phase ^ 1)) {
                             bad = 1;
                         } else {
-                            const uint32_t ab = (uint32_t)(R * kpj * ES);
+                            const uint32_t ab = (uint32_t)(Ri * kpj * ES);
                             const uint32_t bb = (uint32_t)(item_np(cur) * kpj * ES);
                             uint8_t* sA = smem + stage * stage_bytes;
                             uint8_t* sB = sA + a_bytes;
                             stage_kp[stage] = kpj;
                             stage_np[stage] = item_np(cur);
+                            stage_R[stage] = Ri;
                             stage_fl[stage] = (base + j == 0 ? F_FIRST : 0) | (base + j == nterms - 1 ? F_LAST : 0);
                             if (MF) {
                                 // the source cluster: the activation rows of cluster s start at s·KP
@@ -437,9 +442,10 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                                 bulk_g2s(sA, (asj ? p.act1 : p.act0) + aj, ab, &full_bar[stage]);
                             } else {
                                 mbar_expect_tx(&full_bar[stage], ab + bb);
-                                const uint8_t* asrc = (asj & 3) == 0 ? p.act0 : ((asj & 3) == 1 ? p.act1 : p.act2);
+                                const uint8_t* asrc = (asj & 3) == 0 ? PSYS(cur, act0)
+                                                                     : ((asj & 3) == 1 ? PSYS(cur, act1) : PSYS(cur, act2));
                                 bulk_g2s(sA, asrc + aj, ab, &full_bar[stage]);
-                                bulk_g2s(sB, p.bmat + bj * (ES / 2), bb, &full_bar[stage]);
+                                bulk_g2s(sB, PSYS(cur, bmat) + bj * (ES / 2), bb, &full_bar[stage]);
                             }
                             pend_mask |= 1u << stage;
                             pend_par = (pend_par & ~(1u << stage)) | (phase << stage);
@@ -455,7 +461,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 }
             }
             tcur = TcTerm{};
-            if (nxt.id >= 0 && lane < nxt.e1 - nxt.e0) tcur = p.terms[nxt.e0 + lane];
+            if (nxt.id >= 0 && lane < nxt.e1 - nxt.e0) tcur = PSYS(nxt, terms)[nxt.e0 + lane];
             cur = nxt;
         }
         if (lane == 0) {
@@ -475,6 +481,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 if ((pend_mask >> s2) & 1u)
                     if (!mbar_wait(&full_bar[s2], (pend_par >> s2) & 1u)) atomicExch(p.err, 2);
         }
+#undef PSYS
     } else if (warp == 1 || warp == tc_issuer2<KIND>()) {
         // ---------------- MMA issuers: driven by the stage metadata ----------------
         // Two warps take the terms by parity (term t uses stage t mod nst,
@@ -517,7 +524,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
             // The MMA time grows with N, not with M up to 128, so the remainder
             // costs no extra instructions.  Rows np..63 of either part hold stale
             // data whose TMEM lanes the epilogue ignores.
-            const uint32_t idesc = KIND == 1 ? idesc_for<KIND>(128, R) : idesc_for<KIND>(M, stage_np[stage]);
+            const uint32_t idesc = KIND == 1 ? idesc_for<KIND>(128, stage_R[stage]) : idesc_for<KIND>(M, stage_np[stage]);
             // descriptors of K step kk: the start address field moves by 256 bytes
             // (two core matrices along K), i.e. 16 in its 16-byte units; a TMEM
             // operand moves by KSTEP columns
@@ -555,27 +562,32 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
         const int n = 32 * (q & 1) + lane;
         const bool lo_part = q >= 2;
         float* xch = reinterpret_cast<float*>(smem + nst * stage_bytes);  // [2][64 i][64 n]
-        const bool wide = R > 64;
-        const bool vec4 = (p.mc & 3) == 0 && (p.ldc & 3) == 0;
         int it = 0, par = 0;
         // rows of Z: the leaf phase, and the leaf items of a transfer-pass launch
         auto leaf_rows = [&](const TcItem& t) { return MODE == 1 || (FLOW && item_role(t) == kRoleLeaf); };
         TcItem cur = blockIdx.x < p.n_items ? p.items[blockIdx.x] : TcItem{-1, 0, 0, 0};
+        // an item's system: its sizes and buffers (SYSF reads a field of the system
+        // table of a multi-system launch, else of the launch's own arguments)
+#define SYSF(it_, f_) ((FLOW && p.sys) ? p.sys[item_sys(it_)].f_ : p.f_)
         int cur_off = 0, cur_nt = 0;
         if (cur.id >= 0 && leaf_rows(cur)) {
-            const int t = p.leaves[cur.id];
-            cur_off = p.cl_off[t];
-            cur_nt = p.cl_size[t];
+            const int t = SYSF(cur, leaves)[cur.id];
+            cur_off = SYSF(cur, cl_off)[t];
+            cur_nt = SYSF(cur, cl_size)[t];
         }
         for (int w = blockIdx.x; w < p.n_items; w += G) {
             const TcItem nxt = w + G < p.n_items ? p.items[w + G] : TcItem{-1, 0, 0, 0};
             int nxt_off = 0, nxt_nt = 0;
             if (nxt.id >= 0 && leaf_rows(nxt)) {
-                const int t = p.leaves[nxt.id];
-                nxt_off = p.cl_off[t];
-                nxt_nt = p.cl_size[t];
+                const int t = SYSF(nxt, leaves)[nxt.id];
+                nxt_off = SYSF(nxt, cl_off)[t];
+                nxt_nt = SYSF(nxt, cl_size)[t];
             }
             const int id = cur.id, np = item_np(cur), nterms = cur.e1 - cur.e0;
+            const int Ri = SYSF(cur, R), mci = SYSF(cur, mc), ki = SYSF(cur, k), KPi = SYSF(cur, KP),
+                      ldci = SYSF(cur, ldc);
+            const bool wide = Ri > 64;
+            const bool vec4 = (mci & 3) == 0 && (ldci & 3) == 0;
             const int role = FLOW ? item_role(cur) : 0;
             const bool split_out = COUP_SPLIT || (FLOW && role != kRoleLeaf);
             float sum[kAccCols];
@@ -590,18 +602,33 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 }
                 tc_fence_after();
                 const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * acc_cols);
-                // 64 columns per read (two loads in flight, one wait); R > 64 takes two
-                uint32_t r0[32], r1[32];
+                if constexpr (FLOW) {
+                    // 32 columns per read (16 right-hand-side columns; R > 64 takes four):
+                    // one register buffer, which the multi-system bookkeeping needs room for
+                    uint32_t r0[32];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (h == 1 && !wide) break;
-                    tmem_ld32_async(ta + 64 * h, r0);
-                    tmem_ld32_async(ta + 64 * h + 32, r1);
-                    tmem_wait_ld();
+                    for (int h = 0; h < 4; ++h) {
+                        if (h >= 2 && !wide) break;
+                        tmem_ld32_async(ta + 32 * h, r0);
+                        tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        sum[32 * h + j] += __uint_as_float(r0[2 * j]) + __uint_as_float(r0[2 * j + 1]);
-                        sum[32 * h + 16 + j] += __uint_as_float(r1[2 * j]) + __uint_as_float(r1[2 * j + 1]);
+                        for (int j = 0; j < 16; ++j)
+                            sum[16 * h + j] += __uint_as_float(r0[2 * j]) + __uint_as_float(r0[2 * j + 1]);
+                    }
+                } else {
+                    // 64 columns per read (two loads in flight, one wait); R > 64 takes two
+                    uint32_t r0[32], r1[32];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (h == 1 && !wide) break;
+                        tmem_ld32_async(ta + 64 * h, r0);
+                        tmem_ld32_async(ta + 64 * h + 32, r1);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            sum[32 * h + j] += __uint_as_float(r0[2 * j]) + __uint_as_float(r0[2 * j + 1]);
+                            sum[32 * h + 16 + j] += __uint_as_float(r1[2 * j]) + __uint_as_float(r1[2 * j + 1]);
+                        }
                     }
                 }
                 tc_fence_before();
@@ -612,7 +639,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
             if (lo_part && !failed) {
 #pragma unroll
                 for (int i = 0; i < kAccCols; ++i)
-                    if (i < p.mc) xb[i * 64 + n] = sum[i];
+                    if (i < mci) xb[i * 64 + n] = sum[i];
             }
             // every epilogue warp reaches this barrier once per item, failed or not,
             // and all of them learn whether any failed
@@ -624,37 +651,37 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
             if (!lo_part && split_out) {
 #pragma unroll
                 for (int i = 0; i < kAccCols; ++i)
-                    if (i < p.mc) sum[i] += xb[i * 64 + n];
+                    if (i < mci) sum[i] += xb[i * 64 + n];
                 // The result goes, split as the activations are (rows 2i: x; 2i + 1: x -
                 // tf32(x); zero past the columns and past column k), into the cluster's
                 // tile: staged in this item's exchange buffer (free once both tile warps
                 // have read it) and stored by one bulk copy per 64 rows.
                 asm volatile("bar.sync 4, 64;" ::: "memory");
-                uint8_t* gtile = (role == kRoleCoupling ? p.out_act2 : p.out_act) + (int64_t)id * p.KP * R * 4;
-                const bool nv = n < p.k;
+                uint8_t* gtile = (role == kRoleCoupling ? SYSF(cur, out_act2) : SYSF(cur, out_act)) + (int64_t)id * KPi * Ri * 4;
+                const bool nv = n < ki;
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     const int h0 = 64 * hh;
-                    if (h0 >= R) break;
-                    const int rows = min(64, R - h0);
+                    if (h0 >= Ri) break;
+                    const int rows = min(64, Ri - h0);
                     if (h0 > 0) asm volatile("bar.sync 4, 64;" ::: "memory");  // the last store read the buffer
-                    if (n < p.KP) {
+                    if (n < KPi) {
 #pragma unroll
                         for (int i = 0; i < 32; ++i) {
                             if (2 * i >= rows) break;
                             const int ii = 32 * hh + i;
-                            const float v = (nv && ii < p.mc) ? sum[ii] : 0.f;
+                            const float v = (nv && ii < mci) ? sum[ii] : 0.f;
                             const float lo = v - __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-                            *(float*)((uint8_t*)xb + cm_off(2 * i, n, p.KP, 4)) = v;
-                            *(float*)((uint8_t*)xb + cm_off(2 * i + 1, n, p.KP, 4)) = lo;
+                            *(float*)((uint8_t*)xb + cm_off(2 * i, n, KPi, 4)) = v;
+                            *(float*)((uint8_t*)xb + cm_off(2 * i + 1, n, KPi, 4)) = lo;
                         }
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     asm volatile("bar.sync 4, 64;" ::: "memory");
                     if (q == 0 && lane == 0) {
-                        const uint32_t bytes = (uint32_t)(rows * p.KP * 4);
+                        const uint32_t bytes = (uint32_t)(rows * KPi * 4);
                         asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
-                                         gtile + (int64_t)h0 * p.KP * 4),
+                                         gtile + (int64_t)h0 * KPi * 4),
                                      "r"(smem_u32(xb)), "r"(bytes)
                                      : "memory");
                         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
@@ -664,30 +691,30 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 // the tile is in global memory: release it to the CTAs that wait for it
                 if (FLOW && role == kRoleTransfer && q == 0 && lane == 0) {
                     fence_proxy_async_global();
-                    flag_release(p.flag + id, p.epoch);
+                    flag_release(SYSF(cur, flag) + id, p.epoch);
                 }
             } else if (!lo_part) {
 #pragma unroll
                 for (int i = 0; i < kAccCols; ++i)
-                    if (i < p.mc) sum[i] += xb[i * 64 + n];
+                    if (i < mci) sum[i] += xb[i * 64 + n];
                 float* out = nullptr;
                 if (!leaf_rows(cur)) {
-                    if (n < np && n < p.k) out = p.yhat + ((int64_t)id * p.k + n) * p.ldc;
+                    if (n < np && n < ki) out = p.yhat + ((int64_t)id * ki + n) * ldci;
                 } else {
                     // Z in cluster order; the scatter into Y (with α, σX) is a separate
                     // coalesced pass, so the epilogue only stores
-                    if (n < cur_nt) out = p.zp + ((int64_t)cur_off + n) * p.ldc;
+                    if (n < cur_nt) out = SYSF(cur, zp) + ((int64_t)cur_off + n) * ldci;
                 }
                 if (out) {
                     if (vec4) {
 #pragma unroll
                         for (int i = 0; i < kAccCols; i += 4)
-                            if (i < p.mc)
+                            if (i < mci)
                                 *reinterpret_cast<float4*>(out + i) = make_float4(sum[i], sum[i + 1], sum[i + 2], sum[i + 3]);
                     } else {
 #pragma unroll
                         for (int i = 0; i < kAccCols; ++i)
-                            if (i < p.mc) out[i] = sum[i];
+                            if (i < mci) out[i] = sum[i];
                     }
                 }
             }
@@ -696,6 +723,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
             cur_off = nxt_off;
             cur_nt = nxt_nt;
         }
+#undef SYSF
     } else if (warp < 6) {
         // ---------------- epilogue, KIND 0 (warps 2..5, TMEM lane quadrant warp % 4) ----------------
         const int q = warp & 3;

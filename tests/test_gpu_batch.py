@@ -31,7 +31,10 @@ def test_batched_product_equals_single_products(batch):
     torch = require_cuda()
     P, specs, pts, mats = batch
     B = P.H2Batch(mats)
-    for dtype, tol in (("f64", 1e-12), ("f32", 1e-6)):
+    # FP32: the batch runs every system's product in two multi-system launches; the
+    # single products may take other (equally accurate) paths, so they agree to a few
+    # FP32 roundings
+    for dtype, tol in (("f64", 1e-12), ("f32", 3e-6)):
         Xs = [torch.from_numpy(gaussian_rhs(sp["n"], sp["m"], 10 + i)).cuda() for i, sp in enumerate(specs)]
         Ys = [torch.from_numpy(gaussian_rhs(sp["n"], sp["m"], 20 + i)).cuda() for i, sp in enumerate(specs)]
         ref = [y.clone() for y in Ys]
@@ -103,3 +106,42 @@ def test_batched_block_cg_gram(batch):
         Xc = np.linalg.solve(A, b.cpu().numpy())
         assert rel_fro(x.cpu().numpy(), Xc) <= 1e-6
     B.close()
+
+
+def test_multi_system_launches_match_single_products_bit_for_bit():
+    """With the tensor-core transfer passes on every matrix, a single product runs
+    the same items (upward+coupling, downward+leaf work lists) as the batch's two
+    multi-system launches, each with the same terms in the same order: the results
+    agree bit for bit, and with the FP64 oracle to the FP32 tolerance.  Column
+    counts 1..64 across the systems (R from 16 to 128 in one launch), q = 3 and 4."""
+    torch = require_cuda()
+    import os
+    import paper_2509_17257_gb300 as P
+    specs = batch_specs(count=7, seed=11, n_lo=700, n_hi=5000)
+    specs[0]["m"], specs[1]["m"], specs[2]["m"] = 1, 64, 33
+    os.environ["H2_TC_TRANSFER"] = "1"
+    try:
+        pts = [ellipsoid_points(sp["n"], sp["axes"], sp["point_seed"]) for sp in specs]
+        mats = [P.H2Matrix(x, q=sp["q"], leaf_size=64, eta=2.0, sigma=1e-2, precisions=("f32",))
+                for x, sp in zip(pts, specs)]
+    finally:
+        del os.environ["H2_TC_TRANSFER"]
+    B = P.H2Batch(mats)
+    Xs = [torch.from_numpy(gaussian_rhs(sp["n"], sp["m"], 60 + i)).cuda() for i, sp in enumerate(specs)]
+    Y0 = [gaussian_rhs(sp["n"], sp["m"], 70 + i) for i, sp in enumerate(specs)]
+    for rep in range(2):  # capture, then replay
+        Ys = [torch.from_numpy(y).cuda() for y in Y0]
+        ref = [torch.from_numpy(y).cuda() for y in Y0]
+        B.matmul(Xs, Ys, alpha=-0.25, dtype="f32")
+        for mm, x, y in zip(mats, Xs, ref):
+            mm.matmul(x, y, alpha=-0.25, dtype="f32")
+        torch.cuda.synchronize()
+        for i, (y, r) in enumerate(zip(Ys, ref)):
+            assert torch.equal(y, r), (rep, i)
+    for sp, p, x, y, y0 in zip(specs, pts, Xs, Ys, Y0):
+        H = O.H2Matrix(p, q=sp["q"], leaf_size=64, eta=2.0, sigma=1e-2)
+        assert rel_fro(y.cpu().numpy(), O.h2mm(H, -0.25, x.cpu().numpy(), y0)) <= 1e-5, sp
+    B.close()
+    for mm in mats:
+        mm.close()
+
