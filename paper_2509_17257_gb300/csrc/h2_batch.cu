@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "h2_internal.cuh"
@@ -65,20 +66,140 @@ int mm_body(void* ctx, int i, cudaStream_t st) {
                          false, false);
 }
 
-// One FP32 product of every system with two multi-system launches: the upward
-// pass with the coupling phase, and the downward pass with the leaf phase, each
-// a single work list over the items of all systems (merged by dependency key),
-// captured into one graph with the systems' gathers and scatters as branches.
+}  // namespace
+
+// The two multi-system launches of an FP32 product of the systems `sys` (with
+// their buffers fb): the upward pass with the coupling phase and the downward
+// pass with the leaf phase, each one work list over the items of all systems,
+// merged by dependency key (system index in bits 18.. of np), with the systems'
+// argument tables.  Lists and tables go to *mem (grown to *bytes as needed);
+// p1 and p2 receive the launch arguments.
+int flow_tables(h2_batch* b, const std::vector<int>& sys, const std::vector<FlowBufs>& fb, void** mem, size_t* bytes,
+                TcGemmParams* p1, TcGemmParams* p2, cudaStream_t st) {
+    const int ns = (int)sys.size();
+    int Rmax = 16;
+    std::vector<int32_t> k1, k2;
+    std::vector<TcItem> i1, i2;
+    std::vector<TcSys> t1(ns), t2(ns);
+    for (int j = 0; j < ns; ++j) {
+        h2_matrix* A = b->mats[sys[j]];
+        const TcData& D = A->tc;
+        const int32_t tag = (int32_t)((uint32_t)j << 18);
+        for (size_t e = 0; e < D.f1_host.size(); ++e) {
+            TcItem it = D.f1_host[e];
+            it.np |= tag;
+            k1.push_back(D.f1_keys[e]);
+            i1.push_back(it);
+        }
+        for (size_t e = 0; e < D.f2_host.size(); ++e) {
+            TcItem it = D.f2_host[e];
+            it.np |= tag;
+            k2.push_back(D.f2_keys[e]);
+            i2.push_back(it);
+        }
+        const FlowBufs& f = fb[j];
+        Rmax = std::max(Rmax, f.R);
+        t1[j] = TcSys{D.f1_terms, f.xcm, f.Xcm, nullptr, D.mat32, f.xcm, f.ycp, f.fflag, f.Xp,
+                      A->d_leaves, A->d_cl_off, A->d_cl_size, f.R, f.mc, A->k, D.KP, f.mc, 0};
+        t2[j] = TcSys{D.f2_terms, f.ycm, f.ycp, f.Xcm, D.mat32, f.ycm, nullptr, f.fflag + A->nc, f.Xp,
+                      A->d_leaves, A->d_cl_off, A->d_cl_size, f.R, f.mc, A->k, D.KP, f.mc, 0};
+    }
+    std::vector<TcItem> m1, m2;
+    merge_by_key(k1, i1, m1);
+    merge_by_key(k2, i2, m2);
+    const size_t o1 = 0, o2 = o1 + m1.size() * sizeof(TcItem), o3 = o2 + m2.size() * sizeof(TcItem),
+                 o4 = o3 + ns * sizeof(TcSys), need = o4 + ns * sizeof(TcSys);
+    if (*bytes < need) {
+        H2_CUDA_TRY(cudaStreamSynchronize(st));
+        if (*mem) cudaFree(*mem);
+        *mem = nullptr;
+        *bytes = 0;
+        H2_CUDA_TRY(cudaMalloc(mem, need));
+        *bytes = need;
+    }
+    char* dm = (char*)*mem;
+    H2_CUDA_TRY(cudaMemcpyAsync(dm + o1, m1.data(), m1.size() * sizeof(TcItem), cudaMemcpyHostToDevice, st));
+    H2_CUDA_TRY(cudaMemcpyAsync(dm + o2, m2.data(), m2.size() * sizeof(TcItem), cudaMemcpyHostToDevice, st));
+    H2_CUDA_TRY(cudaMemcpyAsync(dm + o3, t1.data(), ns * sizeof(TcSys), cudaMemcpyHostToDevice, st));
+    H2_CUDA_TRY(cudaMemcpyAsync(dm + o4, t2.data(), ns * sizeof(TcSys), cudaMemcpyHostToDevice, st));
+    H2_CUDA_TRY(cudaStreamSynchronize(st));
+    *p1 = TcGemmParams{};
+    p1->n_items = (int)m1.size();
+    p1->items = (const TcItem*)(dm + o1);
+    p1->sys = (const TcSys*)(dm + o3);
+    p1->R = Rmax;
+    p1->epoch = 1;
+    p1->err = b->mats[sys[0]]->err_dev;
+    *p2 = *p1;
+    p2->n_items = (int)m2.size();
+    p2->items = (const TcItem*)(dm + o2);
+    p2->sys = (const TcSys*)(dm + o4);
+    return 0;
+}
+
+// Capture into *exec: pre(j) on every system's branch, the two launches, then
+// post(j) on every system's branch, all forked from and joined into b->origin.
+int flow_capture(h2_batch* b, const std::vector<int>& sys, const TcGemmParams& p1, const TcGemmParams& p2,
+                 const std::function<int(int, cudaStream_t)>& pre, const std::function<int(int, cudaStream_t)>& post,
+                 cudaGraphExec_t* exec) {
+    *exec = nullptr;
+    const int ns = (int)sys.size();
+    H2_CUDA_TRY(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+    int rc = 0;
+    cudaError_t e = cudaEventRecord(b->fork, b->origin);
+    for (int j = 0; j < ns && !rc && e == cudaSuccess; ++j) {
+        const int i = sys[j];
+        if ((e = cudaStreamWaitEvent(b->streams[i], b->fork, 0)) != cudaSuccess) break;
+        if ((rc = pre(j, b->streams[i]))) break;
+        if ((e = cudaEventRecord(b->join[i], b->streams[i])) != cudaSuccess) break;
+        e = cudaStreamWaitEvent(b->origin, b->join[i], 0);
+    }
+    if (!rc && e == cudaSuccess) rc = launch_tc_gemm(3, 1, p1, std::min(p1.n_items, kTcGrid), b->origin);
+    if (!rc && e == cudaSuccess) rc = launch_tc_gemm(3, 1, p2, std::min(p2.n_items, kTcGrid), b->origin);
+    if (!rc && e == cudaSuccess) e = cudaEventRecord(b->fork, b->origin);
+    for (int j = 0; j < ns && !rc && e == cudaSuccess; ++j) {
+        const int i = sys[j];
+        if ((e = cudaStreamWaitEvent(b->streams[i], b->fork, 0)) != cudaSuccess) break;
+        if ((rc = post(j, b->streams[i]))) break;
+        if ((e = cudaEventRecord(b->join[i], b->streams[i])) != cudaSuccess) break;
+        e = cudaStreamWaitEvent(b->origin, b->join[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->origin, &graph);
+    if (rc || e != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (!rc) {
+            set_error(std::string("batch graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : ee));
+            rc = H2_E_CUDA;
+        }
+        return rc;
+    }
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        set_error(std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+        return H2_E_CUDA;
+    }
+    return 0;
+}
+
+bool flow_batch_ok(h2_batch* b, const std::vector<int>& sys, const int64_t* m, int32_t dtype) {
+    bool multi = dtype == H2_F32 && b->multi_launch;
+    for (int i : sys) multi = multi && flow_batchable(b->mats[i], m[i]) && b->mats[i]->use_flow != 0;
+    return multi;
+}
+
+namespace {
+
+// One FP32 product of every system with the two multi-system launches, captured
+// into one graph with the systems' gathers and scatters as branches.
 int batch_flow_matmul(h2_batch* b, double alpha, const double* const* X, const int64_t* ldx, double* const* Y,
-                      const int64_t* ldy, const int64_t* m, const std::vector<int>& sys, cudaStream_t st) {
+                      const int64_t* ldy, const int64_t* m, const std::vector<int>& sys) {
     const int ns = (int)sys.size();
     std::vector<FlowBufs> fb(ns);
     int rc = 0;
-    int Rmax = 16;
-    for (int j = 0; j < ns && !rc; ++j) {
-        rc = flow_prepare(b->mats[sys[j]], (int)m[sys[j]], b->origin, &fb[j]);
-        Rmax = std::max(Rmax, fb[j].R);
-    }
+    for (int j = 0; j < ns && !rc; ++j) rc = flow_prepare(b->mats[sys[j]], (int)m[sys[j]], b->origin, &fb[j]);
     if (rc) return rc;
     std::vector<int64_t> key;
     int64_t abits;
@@ -91,99 +212,14 @@ int batch_flow_matmul(h2_batch* b, double alpha, const double* const* X, const i
     }
     if (!b->flow_exec || key != b->flow_key) {
         if (b->flow_exec) { cudaGraphExecDestroy(b->flow_exec); b->flow_exec = nullptr; }
-        // the merged work lists (system index in bits 18.. of np) and the system tables
-        std::vector<int32_t> k1, k2;
-        std::vector<TcItem> i1, i2;
-        std::vector<TcSys> t1(ns), t2(ns);
-        for (int j = 0; j < ns; ++j) {
-            h2_matrix* A = b->mats[sys[j]];
-            const TcData& D = A->tc;
-            const int32_t tag = (int32_t)((uint32_t)j << 18);
-            for (size_t e = 0; e < D.f1_host.size(); ++e) {
-                TcItem it = D.f1_host[e];
-                it.np |= tag;
-                k1.push_back(D.f1_keys[e]);
-                i1.push_back(it);
-            }
-            for (size_t e = 0; e < D.f2_host.size(); ++e) {
-                TcItem it = D.f2_host[e];
-                it.np |= tag;
-                k2.push_back(D.f2_keys[e]);
-                i2.push_back(it);
-            }
-            const FlowBufs& f = fb[j];
-            t1[j] = TcSys{D.f1_terms, f.xcm, f.Xcm, nullptr, D.mat32, f.xcm, f.ycp, f.fflag, f.Xp,
-                          A->d_leaves, A->d_cl_off, A->d_cl_size, f.R, f.mc, A->k, D.KP, f.mc, 0};
-            t2[j] = TcSys{D.f2_terms, f.ycm, f.ycp, f.Xcm, D.mat32, f.ycm, nullptr, f.fflag + A->nc, f.Xp,
-                          A->d_leaves, A->d_cl_off, A->d_cl_size, f.R, f.mc, A->k, D.KP, f.mc, 0};
-        }
-        std::vector<TcItem> m1, m2;
-        merge_by_key(k1, i1, m1);
-        merge_by_key(k2, i2, m2);
-        const size_t o1 = 0, o2 = o1 + m1.size() * sizeof(TcItem), o3 = o2 + m2.size() * sizeof(TcItem),
-                     o4 = o3 + ns * sizeof(TcSys), need = o4 + ns * sizeof(TcSys);
-        if (b->flow_bytes < need) {
-            H2_CUDA_TRY(cudaStreamSynchronize(b->origin));
-            if (b->flow_mem) cudaFree(b->flow_mem);
-            b->flow_mem = nullptr;
-            b->flow_bytes = 0;
-            H2_CUDA_TRY(cudaMalloc(&b->flow_mem, need));
-            b->flow_bytes = need;
-        }
-        char* dm = (char*)b->flow_mem;
-        H2_CUDA_TRY(cudaMemcpyAsync(dm + o1, m1.data(), m1.size() * sizeof(TcItem), cudaMemcpyHostToDevice, b->origin));
-        H2_CUDA_TRY(cudaMemcpyAsync(dm + o2, m2.data(), m2.size() * sizeof(TcItem), cudaMemcpyHostToDevice, b->origin));
-        H2_CUDA_TRY(cudaMemcpyAsync(dm + o3, t1.data(), ns * sizeof(TcSys), cudaMemcpyHostToDevice, b->origin));
-        H2_CUDA_TRY(cudaMemcpyAsync(dm + o4, t2.data(), ns * sizeof(TcSys), cudaMemcpyHostToDevice, b->origin));
-        H2_CUDA_TRY(cudaStreamSynchronize(b->origin));
-        TcGemmParams p1{}, p2{};
-        p1.n_items = (int)m1.size();
-        p1.items = (const TcItem*)(dm + o1);
-        p1.sys = (const TcSys*)(dm + o3);
-        p1.R = Rmax;
-        p1.epoch = 1;
-        p1.err = b->mats[sys[0]]->err_dev;
-        p2 = p1;
-        p2.n_items = (int)m2.size();
-        p2.items = (const TcItem*)(dm + o2);
-        p2.sys = (const TcSys*)(dm + o4);
-        // capture: the gathers as branches, the two launches, the scatters as branches
-        H2_CUDA_TRY(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaEventRecord(b->fork, b->origin);
-        for (int j = 0; j < ns && !rc && e == cudaSuccess; ++j) {
+        TcGemmParams p1, p2;
+        if ((rc = flow_tables(b, sys, fb, &b->flow_mem, &b->flow_bytes, &p1, &p2, b->origin))) return rc;
+        auto pre = [&](int j, cudaStream_t s) { const int i = sys[j]; return flow_pre(b->mats[i], X[i], ldx[i], fb[j], s); };
+        auto post = [&](int j, cudaStream_t s) {
             const int i = sys[j];
-            if ((e = cudaStreamWaitEvent(b->streams[i], b->fork, 0)) != cudaSuccess) break;
-            if ((rc = flow_pre(b->mats[i], X[i], ldx[i], fb[j], b->streams[i]))) break;
-            if ((e = cudaEventRecord(b->join[i], b->streams[i])) != cudaSuccess) break;
-            e = cudaStreamWaitEvent(b->origin, b->join[i], 0);
-        }
-        if (!rc && e == cudaSuccess) rc = launch_tc_gemm(3, 1, p1, std::min(p1.n_items, kTcGrid), b->origin);
-        if (!rc && e == cudaSuccess) rc = launch_tc_gemm(3, 1, p2, std::min(p2.n_items, kTcGrid), b->origin);
-        if (!rc && e == cudaSuccess) e = cudaEventRecord(b->fork, b->origin);
-        for (int j = 0; j < ns && !rc && e == cudaSuccess; ++j) {
-            const int i = sys[j];
-            if ((e = cudaStreamWaitEvent(b->streams[i], b->fork, 0)) != cudaSuccess) break;
-            if ((rc = flow_post(b->mats[i], alpha, X[i], ldx[i], Y[i], ldy[i], fb[j], b->streams[i]))) break;
-            if ((e = cudaEventRecord(b->join[i], b->streams[i])) != cudaSuccess) break;
-            e = cudaStreamWaitEvent(b->origin, b->join[i], 0);
-        }
-        cudaGraph_t graph = nullptr;
-        const cudaError_t ee = cudaStreamEndCapture(b->origin, &graph);
-        if (rc || e != cudaSuccess || ee != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            cudaGetLastError();
-            if (!rc) {
-                set_error(std::string("batch graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : ee));
-                rc = H2_E_CUDA;
-            }
-            return rc;
-        }
-        e = cudaGraphInstantiate(&b->flow_exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            set_error(std::string("batch graph instantiate: ") + cudaGetErrorString(e));
-            return H2_E_CUDA;
-        }
+            return flow_post(b->mats[i], alpha, X[i], ldx[i], Y[i], ldy[i], fb[j], false, s);
+        };
+        if ((rc = flow_capture(b, sys, p1, p2, pre, post, &b->flow_exec))) return rc;
         b->flow_key = key;
     }
     H2_CUDA_TRY(cudaGraphLaunch(b->flow_exec, b->origin));
@@ -269,11 +305,9 @@ int h2_batch_matmul(h2_batch* b, double alpha, const double* const* X, const int
     // the graph runs on the batch's own stream, ordered after and before the caller's stream
     H2_CUDA_TRY(cudaEventRecord(b->ev_in, st));
     // FP32 with the tensor-core transfer passes on every system: multi-system launches
-    bool multi = dtype == H2_F32 && b->multi_launch;
-    for (int i : sys) multi = multi && flow_batchable(b->mats[i], m[i]) && b->mats[i]->use_flow != 0;
-    if (multi) {
+    if (flow_batch_ok(b, sys, m, dtype)) {
         H2_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
-        int rc = batch_flow_matmul(b, alpha, X, ldx, Y, ldy, m, sys, st);
+        int rc = batch_flow_matmul(b, alpha, X, ldx, Y, ldy, m, sys);
         if (rc) return rc;
         H2_CUDA_TRY(cudaEventRecord(b->ev_out, b->origin));
         H2_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_out, 0));

@@ -828,19 +828,16 @@ struct BatchIterCtx {
     double tol;
 };
 
-int batch_iter_body(void* ctx, int i, cudaStream_t st) {
-    BatchIterCtx* c = (BatchIterCtx*)ctx;
+// The iteration's vector work after AP = A·P (Gram or column-wise).
+int batch_iter_after_product(BatchIterCtx* c, int i, cudaStream_t st) {
     Solver& S = *(*c->sys)[i].S;
     if (S.gram) {
-        int rc = matmul_device(S.A, 1.0, S.P, S.m, S.AP, S.m, S.m, c->dtype, st, false, true);
+        int rc = gram_alpha(S.P, S.AP, S.R, S.n, S.m, S.g, S.d, st);
         if (rc) return rc;
-        if ((rc = gram_alpha(S.P, S.AP, S.R, S.n, S.m, S.g, S.d, st))) return rc;
         return gram_update_dir((*c->sys)[i].X, (*c->sys)[i].ldx, S.P, S.AP, S.R, S.n, S.m, c->tol, S.g, S.d, st);
     }
     const dim3 blk(kColsPerCta, 8);
     const dim3 grid(kRowBlocks, (S.m + kColsPerCta - 1) / kColsPerCta);
-    int rc = matmul_device(S.A, 1.0, S.P, S.m, S.AP, S.m, S.m, c->dtype, st, false, true);
-    if (rc) return rc;
     k_cg_dots<<<grid, blk, 0, st>>>(S.P, S.AP, S.R, S.m, S.n, S.m, S.d);
     H2_LAUNCH_CHECK();
     k_cg_update<<<grid, blk, 0, st>>>((*c->sys)[i].X, (*c->sys)[i].ldx, S.P, S.AP, S.R, S.m, S.n, S.m, c->tol, 0,
@@ -849,6 +846,14 @@ int batch_iter_body(void* ctx, int i, cudaStream_t st) {
     k_cg_dir<<<grid, blk, 0, st>>>(S.P, S.R, S.m, S.n, S.m, S.d);
     H2_LAUNCH_CHECK();
     return 0;
+}
+
+int batch_iter_body(void* ctx, int i, cudaStream_t st) {
+    BatchIterCtx* c = (BatchIterCtx*)ctx;
+    Solver& S = *(*c->sys)[i].S;
+    int rc = matmul_device(S.A, 1.0, S.P, S.m, S.AP, S.m, S.m, c->dtype, st, false, true);
+    if (rc) return rc;
+    return batch_iter_after_product(c, i, st);
 }
 
 }  // namespace
@@ -932,12 +937,44 @@ int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, doub
     cudaGraphExec_t exec = nullptr;
     std::vector<int> in_graph;
     int status = 0, it = 0;
+    // FP32 products of every system in two multi-system launches per iteration
+    // (the upward pass with the coupling phase, the downward pass with the leaf
+    // phase), when every system can take them; their buffers are sized once here
+    std::vector<int> all_active;
+    for (int i = 0; i < count; ++i) if (!sys[i].done) all_active.push_back(i);
+    const bool multi = !all_active.empty() && flow_batch_ok(b, all_active, m, dtype);
+    std::vector<FlowBufs> fbs(count);
+    void* fmem = nullptr;
+    size_t fbytes = 0;
+    if (multi)
+        for (int i : all_active) {
+            int rc = flow_prepare(b->mats[i], (int)m[i], b->streams[i], &fbs[i]);
+            if (rc) return rc;
+        }
     auto rebuild = [&]() -> int {
         if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
         in_graph.clear();
         for (int i = 0; i < count; ++i) if (!sys[i].done) in_graph.push_back(i);
         if (in_graph.empty()) return 0;
-        return batch_capture(b, st, in_graph, batch_iter_body, &ctx, &exec);
+        if (!multi) return batch_capture(b, st, in_graph, batch_iter_body, &ctx, &exec);
+        std::vector<FlowBufs> fb;
+        for (int i : in_graph) fb.push_back(fbs[i]);
+        TcGemmParams p1, p2;
+        int rc = flow_tables(b, in_graph, fb, &fmem, &fbytes, &p1, &p2, st);
+        if (rc) return rc;
+        auto pre = [&](int j, cudaStream_t s) {
+            const int i = in_graph[j];
+            Solver& S = *sys[i].S;
+            return flow_pre(S.A, S.P, S.m, fbs[i], s);
+        };
+        auto post = [&](int j, cudaStream_t s) {
+            const int i = in_graph[j];
+            Solver& S = *sys[i].S;
+            int rc2 = flow_post(S.A, 1.0, S.P, S.m, S.AP, S.m, fbs[i], true, s);
+            if (rc2) return rc2;
+            return batch_iter_after_product(&ctx, i, s);
+        };
+        return flow_capture(b, in_graph, p1, p2, pre, post, &exec);
     };
     int rc = rebuild();
     if (rc) return rc;
@@ -985,6 +1022,7 @@ int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, doub
     }
     if (exec) cudaGraphExecDestroy(exec);
     H2_CUDA_TRY(cudaStreamSynchronize(st));
+    if (fmem) cudaFree(fmem);
     // report: true FP64 residual per column
     for (int i = 0; i < count; ++i) {
         BatchSys& y = sys[i];

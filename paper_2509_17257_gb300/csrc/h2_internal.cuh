@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -480,7 +481,15 @@ void merge_by_key(const std::vector<int32_t>& keys, const std::vector<TcItem>& i
 int flow_prepare(h2_matrix* A, int m, cudaStream_t st, FlowBufs* fb);
 int flow_pre(h2_matrix* A, const double* X, int64_t ldx, const FlowBufs& fb, cudaStream_t st);
 int flow_post(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, const FlowBufs& fb,
-              cudaStream_t st);
+              bool overwrite, cudaStream_t st);
+// Multi-system FP32 products of a batch (h2_batch.cu): whether every system of
+// sys can take them, their work lists and tables, and their graph capture.
+bool flow_batch_ok(h2_batch* b, const std::vector<int>& sys, const int64_t* m, int32_t dtype);
+int flow_tables(h2_batch* b, const std::vector<int>& sys, const std::vector<FlowBufs>& fb, void** mem, size_t* bytes,
+                TcGemmParams* p1, TcGemmParams* p2, cudaStream_t st);
+int flow_capture(h2_batch* b, const std::vector<int>& sys, const TcGemmParams& p1, const TcGemmParams& p2,
+                 const std::function<int(int, cudaStream_t)>& pre, const std::function<int(int, cudaStream_t)>& post,
+                 cudaGraphExec_t* exec);
 
 // Bytes of scratch one product needs (gathered X, x̂, ŷ, transfer-pass
 // bookkeeping), and the product run in caller-provided scratch of at least

@@ -1513,14 +1513,14 @@ int flow_pre(h2_matrix* A, const double* X, int64_t ldx, const FlowBufs& fb, cud
     return launch_zero_tiles(D.c_zero, D.c_nzero, fb.ycp, (int64_t)D.KP * fb.R * 4, st);
 }
 
-// After them: Y += α(Z + σX) in the caller's order.
+// After them: Y += α(Z + σX) in the caller's order (Y = α(Z + σX) with overwrite).
 int flow_post(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, const FlowBufs& fb,
-              cudaStream_t st) {
+              bool overwrite, cudaStream_t st) {
     const int64_t n = A->n;
     const int mc = fb.mc;
     const int64_t total = n * mc;
     const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
-    k_scatter_y<<<g, 256, 0, st>>>(fb.Xp, mc, A->d_perm, n, mc, X, ldx, Y, ldy, alpha, A->sigma, 0);
+    k_scatter_y<<<g, 256, 0, st>>>(fb.Xp, mc, A->d_perm, n, mc, X, ldx, Y, ldy, alpha, A->sigma, overwrite ? 1 : 0);
     H2_LAUNCH_CHECK();
     return 0;
 }
