@@ -556,6 +556,13 @@ def run_ours(args):
             solve["speedup_fastest_mixed_vs_fp64"] = round(solve["fp64"]["seconds"] / mixed[best_m], 3)
             solve["speedup_fastest_mixed_vs_fastest_fp64"] = round(fp64[best_f] / mixed[best_m], 3)
 
+    # the batch workload: 64 independent systems (ellipsoids, n log-uniform in [2048, 32768],
+    # m in 1..64, q in {3, 4}); one FP32 product of all of them per step, in two multi-system
+    # launches (upward + coupling, downward + leaf) between the systems' gathers and scatters
+    batch = None
+    if not args.no_batch and workload == WORKLOAD:
+        batch = batch_products(P, torch, dev, steps=max(5, min(args.steps, 20)), dist=dist)
+
     cpu = None
     # the oracle holds every block in host memory: timed on the default workload only
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and workload == WORKLOAD:
@@ -585,6 +592,7 @@ def run_ours(args):
                       "coupling_GBps": round(n_adm * info["k"] * info["k"] * 2 / (phasesbf["coupling"] * 1e-3) / 1e9, 1),
                       "phases_ms": {kk: round(v, 4) for kk, v in phasesbf.items()}},
         "h2mm_f32_matrix_free": mf,
+        "batch": batch,
         "roofline": roof,
         "roofline_product": roof_product,
         "phases_roofline": per_phase,
@@ -600,6 +608,40 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def batch_products(P, torch, dev, steps: int, dist=None) -> dict:
+    """Time the batched FP32 product of the 64-system batch workload (CUDA events)."""
+    from workloads import batch_specs, ellipsoid_points
+    specs = batch_specs(64, 3, 2048, 32768)
+    mats = [P.H2Matrix(ellipsoid_points(sp["n"], sp["axes"], sp["point_seed"]), q=sp["q"], leaf_size=64, eta=2.0,
+                       sigma=1e-2, precisions=("f32",)) for sp in specs]
+    Xs = [torch.from_numpy(gaussian_rhs(sp["n"], sp["m"], sp["rhs_seed"])).to(dev) for sp in specs]
+    Ys = [torch.zeros_like(x) for x in Xs]
+    flops = sum(mm.flops(sp["m"]) for mm, sp in zip(mats, specs))
+    Bt = P.H2Batch(mats)
+    for _ in range(3):
+        Bt.matmul(Xs, Ys, dtype="f32")
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream()
+    e0.record(st)
+    for _ in range(steps):
+        Bt.matmul(Xs, Ys, dtype="f32")
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev)
+    out = {"systems": len(specs), "total_n": sum(sp["n"] for sp in specs),
+           "total_columns": sum(sp["m"] for sp in specs), "gflop_per_product": round(flops / 1e9, 3),
+           "ms_per_product": round(ms, 4), "value": round(flops / (ms * 1e-3) / 1e9, 1), "unit": "GFLOP/s",
+           "steps": steps, "launch": "two multi-system tensor-core launches per product (upward pass + coupling, "
+                                     "downward pass + leaf phase) plus per-system gathers and scatters, one CUDA graph"}
+    Bt.close()
+    for mm in mats:
+        mm.close()
+    return out
 
 
 def run_mvm_vs_mm(args):
@@ -718,6 +760,7 @@ def main():
     ap.add_argument("--dtype", choices=["f32", "f64", "bf16"], default="f32")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-system batched product in the bench line")
     ap.add_argument("--solve-max-iter", type=int, default=8000)
     ap.add_argument("--workload", choices=sorted(CONFIGS), default=WORKLOAD,
                     help="workload of the bench line (default: the precision workload, n = 65536)")

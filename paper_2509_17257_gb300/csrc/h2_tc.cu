@@ -28,16 +28,17 @@
 //
 // Kernel roles (one persistent CTA per SM; 7 warps for KIND 0, 11 for KIND 1):
 //   warp 0          bulk-copy producer (cp.async.bulk + mbarrier complete_tx)
-//   warp 1          TMEM owner and MMA issuer of the even terms (tcgen05.mma
-//                   kind::f16 or kind::tf32, FP32 accumulate); the converged warp
-//                   runs the loop and elect.sync issues, which keeps its operands
-//                   warp-uniform
+//   warp 1          TMEM owner and MMA issuer (tcgen05.mma kind::f16 or
+//                   kind::tf32, FP32 accumulate): KIND 0 all terms, KIND 1 the
+//                   even terms; the converged warp runs the loop and elect.sync
+//                   issues, which keeps its operands warp-uniform
 //   warps 2..5      epilogue (tcgen05.ld, hi+lo combine, stores)
 //   warps 6..9      KIND 1 only: the splitter, [B; B_lo] into TMEM
-//   last warp       MMA issuer of the odd terms (warp 6, or 10 for KIND 1)
-// Every term accumulates in its own TMEM buffer (round robin over the
+//   last warp       KIND 1: MMA issuer of the odd terms (warp 10); KIND 0: idle
+// KIND 1: every term accumulates in its own TMEM buffer (round robin over the
 // accumulators), so the epilogue's FP32 sum of earlier terms overlaps the MMAs
-// of the next ones.  Every wait is bounded; on a timeout the kernel raises an
+// of the next ones and keeps FP32 accuracy.  KIND 0 (BF16): all terms of an
+// item accumulate in one buffer, read once per item.  Every wait is bounded; on a timeout the kernel raises an
 // error flag, drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -493,7 +494,59 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
         const int j = warp == 1 ? 0 : 1;
         const int T = s_total;
         bool issued = false;
-        for (int it = j; it < T; it += 2) {
+        if (KIND == 0 && j == 0) {
+            // BF16: one issuer takes every term in order and accumulates all terms of
+            // an item in one TMEM accumulator (an item's first term starts it from
+            // zero); the epilogue reads each accumulator once per item.  The FP32
+            // accumulation of the tensor cores is far finer than the BF16 operands.
+            int item_idx = 0, acc = 0;
+            for (int it = 0; it < T; ++it) {
+                const int stage = it % nst;
+                const uint32_t phase = (uint32_t)(it / nst) & 1u;
+                if (!__any_sync(0xffffffffu, mbar_wait(&full_bar[stage], phase))) {
+                    abort_flag = 1;
+                    if (lane == 0) atomicExch(p.err, 4);
+                    break;
+                }
+                const int fl = stage_fl[stage];
+                if (fl & F_FIRST) {
+                    acc = item_idx % kAccBufs;
+                    if (!__any_sync(0xffffffffu, mbar_wait(&acce_bar[acc], ((item_idx / kAccBufs) & 1) ^ 1))) {
+                        abort_flag = 1;
+                        if (lane == 0) atomicExch(p.err, 3);
+                        break;
+                    }
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * acc_cols);
+                const int kp = stage_kp[stage];
+                const uint32_t sA = smem_u32(smem + stage * stage_bytes);
+                const uint32_t sB = sA + a_bytes;
+                const uint32_t sbo = (uint32_t)(kp * ES / 16) * 128;
+                const uint32_t idesc = idesc_for<KIND>(M, stage_np[stage]);
+                const uint64_t ad0 = smem_desc(sA, 128, sbo);
+                const uint64_t bd0 = smem_desc(sB, 128, sbo);
+                const int nk = kp / KSTEP;
+#pragma unroll
+                for (int kk = 0; kk < 64 / KSTEP; ++kk) {
+                    if (kk >= nk) break;
+                    const uint64_t off = (uint64_t)(kk * 16);
+                    mma_issue_elect<KIND>(d, ad0 + off, bd0 + off, idesc, (kk == 0 && (fl & F_FIRST)) ? 0u : 1u);
+                }
+                issued = true;
+                mma_commit_elect(&empty_bar[stage]);
+                if (fl & F_LAST) {
+                    mma_commit_elect(&accf_bar[acc]);
+                    ++item_idx;
+                }
+            }
+            if (issued) {
+                mma_commit_elect(&drain_bar[0]);
+                if (!__any_sync(0xffffffffu, mbar_wait(&drain_bar[0], 0)) && lane == 0) atomicExch(p.err, 5);
+                issued = false;  // drained
+            }
+        }
+        for (int it = j; it < T && KIND == 1; it += 2) {
             const int stage = it % nst;
             const uint32_t phase = (uint32_t)(it / nst) & 1u;
             if (!__any_sync(0xffffffffu, mbar_wait(KIND == 1 ? &split_bar[stage] : &full_bar[stage], phase))) {
@@ -749,20 +802,24 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 nxt_off = p.cl_off[t];
                 nxt_nt = p.cl_size[t];
             }
-            const int id = cur.id, np = cur.np, nterms = cur.e1 - cur.e0;
+            const int id = cur.id, np = item_np(cur);
             float sum[kAccCols];
 #pragma unroll
             for (int j = 0; j < kAccCols; ++j) sum[j] = 0.f;
             bool failed = false;
-            for (int term = 0; term < nterms; ++term, ++it) {
+            {
+                // the item's terms accumulate in one accumulator (`it` counts items)
                 const int acc = it % kAccBufs;
                 // warp-uniform wait: a completed phase stays completed, so any lane's
                 // success is the warp's success
                 const bool ok = __any_sync(0xffffffffu, mbar_wait(&accf_bar[acc], (it / kAccBufs) & 1));
+                ++it;
                 if (!ok) {
                     failed = true;
-                    break;
                 }
+            }
+            if (!failed) {
+                const int acc = (it - 1) % kAccBufs;
                 tc_fence_after();
                 // both halves of the accumulator in flight, one wait; the row pair
                 // (2i, 2i + 1) is adjacent lanes, added by one shuffle
@@ -984,12 +1041,8 @@ int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st
     if (stages >= 2 && stages < nstages) nstages = stages;
     // A parity wait is exact only while its waiter cannot get two uses of a stage
     // ahead (the protocol model in tests/test_pipeline_protocol.py checks this).
-    // The FP32 issuers wait on the in-order splitter, which keeps them in step.
-    // The BF16 issuers wait on the copies themselves: safe with an even stage
-    // count (each stage stays with one issuer) or with at least kAccBufs + 2
-    // stages (the accumulator wait for an issuer's previous term covers the
-    // stage's earlier use).  The BF16 counts here are 14, or 9 for R > 64.
-    if (kind == 0 && (nstages & 1) && nstages < kAccBufs + 2) nstages &= ~1;
+    // The FP32 issuers wait on the in-order splitter, which keeps them in step;
+    // the BF16 kernel has one issuer, which waits on every stage in order.
     if (nstages < 2) { set_error("tensor-core stage does not fit in shared memory"); return H2_E_UNSUPPORTED; }
     p.a_stage_bytes = a_bytes;
     p.nstages = nstages;

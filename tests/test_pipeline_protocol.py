@@ -58,9 +58,16 @@ class Hazard(AssertionError):
     pass
 
 
-def run_pipeline(T, nst=6, nacc=4, nslots=4, seed=0, mutate=None, max_steps=200000, splitter_warps=True):
+def run_pipeline(T, nst=6, nacc=4, nslots=4, seed=0, mutate=None, max_steps=200000, splitter_warps=True,
+                 items=None):
     """Simulate one CTA on T terms; raises Hazard or returns normally.  Without
-    splitter warps (the BF16 kernel) the issuers wait on the copies directly."""
+    splitter warps (the BF16 kernel) the issuers wait on the copies directly.
+    With `items` (term counts of the CTA's items; the BF16 kernel's protocol)
+    one issuer accumulates all terms of an item into one accumulator and the
+    epilogue reads each accumulator once per item."""
+    if items is not None:
+        T = sum(items)
+        splitter_warps = False
     rng = random.Random(seed)
     full = [Barrier(1) for _ in range(nst)]
     split = [Barrier(4) for _ in range(nst)]
@@ -186,8 +193,55 @@ def run_pipeline(T, nst=6, nacc=4, nslots=4, seed=0, mutate=None, max_steps=2000
             acc_unread[acc] -= 1
             acce[acc].arrive()
 
-    agents = ([producer()] + ([splitter(w) for w in range(4)] if splitter_warps else []) + [issuer(0), issuer(1)]
-              + [epilogue(e) for e in range(4)])
+    # ---------------- per-item accumulation (BF16): one issuer, one accumulator per item ----------------
+    def issuer_items():
+        it = 0
+        for idx, cnt in enumerate(items):
+            acc = (it if mutate == "acc_by_term" else idx) % nacc
+            for t in range(cnt):
+                stage = it % nst
+                yield W(full[stage], (it // nst) & 1)
+                if t == 0:
+                    yield W(acce[acc], ((idx // nacc) & 1) ^ (0 if mutate == "issuer_acce_parity" else 1))
+                    if acc_unread[acc]:
+                        raise Hazard(f"item {idx} overwrites accumulator {acc} before its epilogue read")
+                    acc_term[acc] = None
+                if stage_term[stage] != it or not stage_landed[stage]:
+                    raise Hazard(f"MMA of term {it} found stage {stage} holding {stage_term[stage]}")
+                if acc_term[acc] is not None:
+                    raise Hazard(f"term {it} accumulates into accumulator {acc} that holds item {acc_term[acc]}")
+                stage_readers[stage] += 1
+                last = t == cnt - 1
+                mma_queue[0].append((it, acc, idx, last))
+
+                def finish():
+                    t2, c2, i2, l2 = mma_queue[0].pop(0)
+                    s2 = t2 % nst
+                    stage_readers[s2] -= 1
+                    consumed[t2] = True
+                    empty[s2].arrive()
+                    if l2:
+                        acc_term[c2], acc_unread[c2] = i2, 4
+                        accf[c2].arrive()
+                later(finish, 1, 8)
+                it += 1
+                yield ("step",)
+
+    def epilogue_items(e):
+        for idx in range(len(items)):
+            acc = idx % nacc
+            yield W(accf[acc], ((idx // nacc) & 1) ^ (1 if mutate == "epilogue_parity" else 0))
+            if acc_term[acc] != idx:
+                raise Hazard(f"epilogue {e} expected item {idx} in accumulator {acc}, found {acc_term[acc]}")
+            yield ("step",)
+            acc_unread[acc] -= 1
+            acce[acc].arrive()
+
+    if items is not None:
+        agents = [producer(), issuer_items()] + [epilogue_items(e) for e in range(4)]
+    else:
+        agents = ([producer()] + ([splitter(w) for w in range(4)] if splitter_warps else []) + [issuer(0), issuer(1)]
+                  + [epilogue(e) for e in range(4)])
     state = [None] * len(agents)   # the pending request of each agent
     done = [False] * len(agents)
     for step in range(max_steps):
@@ -267,3 +321,31 @@ def test_bf16_protocol_unsafe_with_few_odd_stages(nst):
             caught = True
             break
     assert caught
+
+
+# The BF16 kernel accumulates all terms of an item in one TMEM accumulator (its
+# error budget is far above the accumulator's rounding): one issuer takes every
+# term in order, and the epilogue reads one accumulator per item.  One issuer
+# waits on every stage in order, so any stage count is safe.
+ITEM_SHAPES = [[1], [3], [1, 1, 1, 1, 1, 1, 1], [5, 1, 7, 2, 13, 1, 1, 4], [2] * 20, [17, 3, 9]]
+
+
+@pytest.mark.parametrize("nst", [2, 3, 4, 5, 9, 14])
+@pytest.mark.parametrize("shape", range(len(ITEM_SHAPES)))
+def test_bf16_item_protocol_is_hazard_and_deadlock_free(nst, shape):
+    for nacc in (2, 3, 4):
+        for seed in range(8):
+            run_pipeline(0, nst=nst, nacc=nacc, seed=seed, items=ITEM_SHAPES[shape])
+
+
+@pytest.mark.parametrize("mutate", ["producer_parity", "issuer_acce_parity", "epilogue_parity", "acc_by_term"])
+def test_bf16_item_protocol_planted_mistakes_are_caught(mutate):
+    caught = False
+    for seed in range(80):
+        try:
+            run_pipeline(0, nst=4, seed=seed, mutate=mutate, items=[5, 1, 7, 2, 13, 1, 1, 4, 3, 3])
+        except Hazard:
+            caught = True
+            break
+    assert caught, mutate
+
