@@ -15,12 +15,11 @@
  *  - Dense blocks are row-major n×m arrays of double with a leading
  *    dimension (ld >= m, in elements); row i belongs to point i in the
  *    caller's original order.  A pointer may be device memory or host
- *    memory.  Pinned host memory that the device can address (mapped, as
- *    cudaHostAlloc / cudaHostRegister give on this platform) is read and
- *    updated in place by the product's kernels over the host link, with no
- *    staging copy; pageable host blocks are copied through device buffers
- *    on the call's stream.  Either way a call given a host block returns
- *    after the result is complete on the host.
+ *    memory (pageable or pinned).  A product given host blocks copies them
+ *    through device buffers owned by the matrix: X in on the call's stream
+ *    before the product, Y in on a stream of the matrix's own while the
+ *    product computes (the pass that updates Y waits for it), Y back out
+ *    after it; the call returns after the result is complete on the host.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls on
  *    device pointers are asynchronous with respect to the host unless stated.
  *  - The library owns every h2_matrix / h2_tree it returns; free them with

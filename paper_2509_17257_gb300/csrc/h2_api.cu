@@ -129,6 +129,10 @@ void free_matrix(h2_matrix* A) {
     if (A->ws.base) cudaFree(A->ws.base);
     if (A->ws.stage_x) cudaFree(A->ws.stage_x);
     if (A->ws.stage_y) cudaFree(A->ws.stage_y);
+    if (A->ws.side) cudaStreamDestroy(A->ws.side);
+    if (A->ws.y_in) cudaEventDestroy(A->ws.y_in);
+    if (A->ws.st_mark) cudaEventDestroy(A->ws.st_mark);
+
     if (A->err_host) cudaFreeHost(A->err_host);
     if (A->sync_cnt) cudaFree(A->sync_cnt);
     delete A;

@@ -284,7 +284,18 @@ struct Workspace {
     double* stage_x = nullptr;  // host-pointer staging (n×m doubles each)
     double* stage_y = nullptr;
     size_t stage_bytes = 0;
+    // a product on host blocks copies Y in on a side stream while it computes;
+    // the pass that updates Y first waits for y_in (once, when y_wait is set)
+    cudaStream_t side = nullptr;
+    cudaEvent_t y_in = nullptr, st_mark = nullptr;
+    bool y_wait = false;
 };
+// Make st wait for a pending copy of Y into its staging buffer (see Workspace).
+inline int wait_y_staged(Workspace& ws, cudaStream_t st) {
+    if (!ws.y_wait) return 0;
+    ws.y_wait = false;
+    return cudaStreamWaitEvent(st, ws.y_in, 0) == cudaSuccess ? 0 : H2_E_CUDA;
+}
 
 }  // namespace h2
 

@@ -1029,6 +1029,7 @@ int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int
     marks.mark();
     if ((rc = backward_pass<T, RM, CN>(A, E, yhat, m, gy, gzk, st, sb))) return rc;
     marks.mark();
+    if ((rc = wait_y_staged(A->ws, st))) return rc;
     if (transposed)
         k_leaf_bwd_near<T, RM, CN, true><<<dim3(NL, gy, gzl), kThreads, 0, st>>>(
             A->d_leaves, A->d_cl_off, A->d_cl_size, A->d_perm, V, yhat, A->d_nearT_ptr, A->d_nearT_row,
@@ -1233,6 +1234,7 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
             }
             const int64_t total = n * mc;
             const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+            if ((rc = wait_y_staged(A->ws, st))) return rc;
             k_scatter_y<<<g, 256, 0, st>>>(Xp, mc, A->d_perm, n, mc, X + c0, ldx, Y + c0, ldy, alpha, A->sigma,
                                            overwrite ? 1 : 0);
             H2_LAUNCH_CHECK();
@@ -1327,6 +1329,7 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         {
             const int64_t total = n * mc;
             const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+            if ((rc = wait_y_staged(A->ws, st))) return rc;
             k_scatter_y<<<g, 256, 0, st>>>(Xp, mc, A->d_perm, n, mc, X + c0, ldx, Y + c0, ldy, alpha, A->sigma,
                                            overwrite ? 1 : 0);
             H2_LAUNCH_CHECK();
@@ -1587,19 +1590,10 @@ int matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, 
     if (m == 0) return 0;
     const bool dx = is_device_pointer(X), dy = is_device_pointer(Y);
     if (dx && dy) return matmul_device(A, alpha, X, ldx, Y, ldy, m, dtype, st, transposed, false);
-    // pinned host buffers the device can address: the product's gather reads X and
-    // its final pass updates Y where they are, over the host link, with no staging
-    // copies; the call returns when Y is complete, as for staged buffers
-    {
-        const double* Xm = dx ? X : (const double*)mapped_host_pointer(X);
-        double* Ym = dy ? Y : (double*)mapped_host_pointer(Y);
-        if (Xm && Ym) {
-            int rc = matmul_device(A, alpha, Xm, ldx, Ym, ldy, m, dtype, st, transposed, false);
-            if (rc) return rc;
-            H2_CUDA_TRY(cudaStreamSynchronize(st));
-            return 0;
-        }
-    }
+    // Host blocks go through device staging buffers by the copy engines: X in on the
+    // call's stream before the product, Y in on a side stream while the product
+    // computes (its final pass waits for that copy), Y back out after it.  The call
+    // returns when Y is complete on the host.
     // host blocks: stage through device buffers (packed, ld = m)
     const size_t bytes = (size_t)A->n * m * sizeof(double);
     if (A->ws.stage_bytes < bytes) {
@@ -1612,27 +1606,45 @@ int matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, 
         H2_CUDA_TRY(cudaMalloc(&A->ws.stage_y, bytes));
         A->ws.stage_bytes = bytes;
     }
+    Workspace& W = A->ws;
+    if (!W.side) {
+        H2_CUDA_TRY(cudaStreamCreateWithFlags(&W.side, cudaStreamNonBlocking));
+        H2_CUDA_TRY(cudaEventCreateWithFlags(&W.y_in, cudaEventDisableTiming));
+        H2_CUDA_TRY(cudaEventCreateWithFlags(&W.st_mark, cudaEventDisableTiming));
+    }
+    int rc = 0;
     const double* Xd = X;
     int64_t ldxd = ldx;
     if (!dx) {
-        H2_CUDA_TRY(cudaMemcpy2DAsync(A->ws.stage_x, m * sizeof(double), X, ldx * sizeof(double),
-                                      m * sizeof(double), A->n, cudaMemcpyHostToDevice, st));
-        Xd = A->ws.stage_x;
+        H2_CUDA_TRY(cudaMemcpy2DAsync(W.stage_x, m * sizeof(double), X, ldx * sizeof(double), m * sizeof(double), A->n,
+                                      cudaMemcpyHostToDevice, st));
+        Xd = W.stage_x;
         ldxd = m;
     }
     double* Yd = Y;
     int64_t ldyd = ldy;
     if (!dy) {
-        H2_CUDA_TRY(cudaMemcpy2DAsync(A->ws.stage_y, m * sizeof(double), Y, ldy * sizeof(double),
-                                      m * sizeof(double), A->n, cudaMemcpyHostToDevice, st));
-        Yd = A->ws.stage_y;
+        // Y comes in on the side stream while the product computes; its final pass
+        // waits for y_in.  The copy starts after the call's earlier work on st (which
+        // may still read stage_y).
+        H2_CUDA_TRY(cudaEventRecord(W.st_mark, st));
+        H2_CUDA_TRY(cudaStreamWaitEvent(W.side, W.st_mark, 0));
+        H2_CUDA_TRY(cudaMemcpy2DAsync(W.stage_y, m * sizeof(double), Y, ldy * sizeof(double), m * sizeof(double), A->n,
+                                      cudaMemcpyHostToDevice, W.side));
+        H2_CUDA_TRY(cudaEventRecord(W.y_in, W.side));
+        W.y_wait = true;
+        Yd = W.stage_y;
         ldyd = m;
     }
-    int rc = matmul_device(A, alpha, Xd, ldxd, Yd, ldyd, m, dtype, st, transposed, false);
-    if (rc) return rc;
+    rc = matmul_device(A, alpha, Xd, ldxd, Yd, ldyd, m, dtype, st, transposed, false);
+    if (!rc) rc = wait_y_staged(W, st);  // a path that never reached its final pass
+    if (rc) {
+        W.y_wait = false;
+        return rc;
+    }
     if (!dy) {
-        H2_CUDA_TRY(cudaMemcpy2DAsync(Y, ldy * sizeof(double), A->ws.stage_y, m * sizeof(double),
-                                      m * sizeof(double), A->n, cudaMemcpyDeviceToHost, st));
+        H2_CUDA_TRY(cudaMemcpy2DAsync(Y, ldy * sizeof(double), W.stage_y, m * sizeof(double), m * sizeof(double), A->n,
+                                      cudaMemcpyDeviceToHost, st));
         H2_CUDA_TRY(cudaStreamSynchronize(st));
     }
     return 0;
