@@ -47,12 +47,12 @@ FP64_NOMINAL_TFLOPS = 1.25
 # sources when the counters were taken.  The line reports the bytes only while the sources
 # still hash to that value; after a change to the kernel they are stale and `traffic` is null.
 TC_F32_COUPLING_DRAM = {
-    "bytes": 754399488,  # 734.359 MB read + 20.040 MB written
+    "bytes": 754010112,  # 733.855 MB read + 20.155 MB written
     "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-               "--clock-control none -k regex:k_tc_gemm<(int)0, (int)1> -c 1 python bench.py --steps 2 "
-               "--warmup 1 --no-solve --no-cpu-baseline",
+               "--clock-control none --kernel-name-base demangled -k regex:k_tc_gemm<(int)0, (int)1> -c 1 "
+               "python bench.py --steps 2 --warmup 1 --no-solve --no-cpu-baseline --no-batch",
     "sources": ("paper_2509_17257_gb300/csrc/h2_tc.cu", "paper_2509_17257_gb300/csrc/h2_async.cuh"),
-    "source_sha16": None,
+    "source_sha16": "3e70e236f81751ca",
 }
 
 
@@ -541,8 +541,12 @@ def run_ours(args):
                            "iterations": int(r.iterations), "outer_steps": int(r.outer_steps),
                            "h2mm_calls": int(r.h2mm_calls),
                            "max_true_rel_residual": float(np.max(r.rel_residual))}
-            if big and inner == "f64":
-                solve[name]["status"] = "capped" if r.status_name != "ok" else "ok"
+            if big:
+                # on the larger workloads every solve reports its cost per iteration; the
+                # FP64 ones are capped, and as specified (q = 4, sigma = 1e-2) the matrix is
+                # not definite there, so no solve can reach the tolerance
+                if inner == "f64":
+                    solve[name]["status"] = "capped" if r.status_name != "ok" else "ok"
                 solve[name]["seconds_per_iteration"] = round(secs / max(int(r.iterations), 1), 5)
         if solve["fp64"]["status"] == "ok" and solve["mixed_f32"]["status"] == "ok":
             solve["speedup_mixed_vs_fp64"] = round(solve["fp64"]["seconds"] / solve["mixed_f32"]["seconds"], 3)
