@@ -37,8 +37,12 @@ def test_noalloc_matches_h2_matmul_on_consecutive_calls(setup, dtype):
         Y_ref = Y0.clone()
         Y_new = Y0.clone()
         P.h2_matmul(G.handle, -0.5, X, Y_ref, dtype=dtype)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         P.h2_matmul_noalloc(G.handle, -0.5, X, Y_new, dtype=dtype)
         torch.cuda.synchronize()
+        if call == 1:  # the first call may load the module that holds the scratch array
+            assert torch.cuda.mem_get_info()[0] == free0, "the product allocated device memory"
         assert rel_fro(Y_new.cpu().numpy(), Y_ref.cpu().numpy()) <= TOL[dtype], (dtype, call)
 
 
