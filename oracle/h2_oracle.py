@@ -16,7 +16,9 @@ H²-matrices"):
   the constructions Sec. 2 names   -> :class:`H2Matrix`
 * Sec. 3, Alg. "H2_mvm" (forward transformation, multiplication phase
   "fast_addeval", backward transformation) with the coefficient blocks of
-  Sec. 4 (x̂_s, ŷ_t in K^{k×m})  -> :func:`h2mm`
+  Sec. 4 (x̂_s, ŷ_t in K^{k×m})  -> :func:`h2mm`, over K = R and, for the
+  complex Helmholtz kernel of Sec. 2 (with a smooth regularisation at
+  r = 0), over K = C                       -> :func:`helmholtz_kernel`
 * the same product with BF16 operands and FP32 accumulation, the error
   budget of the BF16 product (not in the paper) -> :func:`h2mm_bf16`
 * Sec. 5.1, Alg. "block CG" (per-column α_i, β_i, γ_i) -> :func:`block_cg`
@@ -52,6 +54,7 @@ __all__ = [
     "build_block_tree",
     "leaf_blocks",
     "exp_kernel",
+    "helmholtz_kernel",
     "cluster_nodes",
     "tensor_nodes",
     "lagrange_1d",
@@ -258,6 +261,24 @@ def exp_kernel(length: float = 0.5):
     return g
 
 
+def helmholtz_kernel(kappa: float = 1.0, delta: float = 0.05):
+    """The Helmholtz kernel of Sec. 2 (K = C), g(x, y) = exp(i κ r) / (4π r) with
+    r = ||x - y||_2, regularised at r = 0 as
+
+        g_{κ,δ}(x, y) = exp(i κ r) / (4π sqrt(r² + δ²)),
+
+    which is smooth everywhere (the diagonal entries are 1 / (4π δ)) and equals
+    the paper's kernel up to a relative O(δ²/r²) away from the diagonal; δ = 0
+    gives the paper's kernel for r > 0.  Broadcasts over leading axes."""
+
+    def g(x, y):
+        d = x - y
+        r = np.sqrt((d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2])
+        return np.exp(1j * kappa * r) / (4.0 * np.pi * np.sqrt(r * r + delta * delta))
+
+    return g
+
+
 def cluster_nodes(c: Cluster, q: int) -> np.ndarray:
     """Chebyshev points of the first kind mapped to the cluster's box, shape (3, q).
 
@@ -313,7 +334,7 @@ def tensor_lagrange(nodes: np.ndarray, pts: np.ndarray) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# The H² matrix (Sec. 2, Def. "H²-matrix"; W = V since I = J and g is real)
+# The H² matrix (Sec. 2, Def. "H²-matrix"; W = V since I = J and the bases are real)
 # ---------------------------------------------------------------------------
 class H2Matrix:
     """Interpolation-based H² matrix A = Â + σI for a point cloud.
@@ -325,7 +346,11 @@ class H2Matrix:
     * nearfield       G_b[i, j] = g(x_i, x_j), b ∈ L-  (stored explicitly, Sec. 2)
     * shift           σ on the diagonal only, applied separately.
 
-    Over R the paper's W_s* and E* become transposes, and W = V.
+    Over R the paper's W_s* and E* become transposes, and W = V.  With a
+    complex kernel (K = C) the bases stay real (Lagrange polynomials of real
+    nodes), S_b and G_b are complex, and the product is A X, not A* X; the
+    transposed product is Aᵀ X (no conjugation).  ``dtype`` is float64 or
+    complex128, the type of the stored entries.
     """
 
     def __init__(self, points, q=3, leaf_size=64, eta=2.0, kernel=None, sigma=0.0, length=0.5):
@@ -354,6 +379,7 @@ class H2Matrix:
             b.S = self.g(self.tnodes[b.t.id][:, None, :], self.tnodes[b.s.id][None, :, :])
         for b in self.near:
             b.G = self.g(self.points[b.t.idx][:, None, :], self.points[b.s.idx][None, :, :])
+        self.dtype = np.result_type(np.float64, *[b.S.dtype for b in self.adm], *[b.G.dtype for b in self.near])
 
     # -- sizes -----------------------------------------------------------
     def counts(self):
@@ -377,7 +403,7 @@ def _forward(H: H2Matrix, s: Cluster, X: np.ndarray, xhat: dict):
     if s.is_leaf:
         xhat[s.id] = H.V[s.id].T @ X[s.idx]
     else:
-        acc = np.zeros((H.k, X.shape[1]))
+        acc = np.zeros((H.k, X.shape[1]), dtype=X.dtype)
         for s2 in s.sons:
             _forward(H, s2, X, xhat)
             acc = acc + H.E[s2.id].T @ xhat[s2.id]
@@ -415,15 +441,19 @@ def h2mm(H: H2Matrix, alpha: float, X: np.ndarray, Y: np.ndarray | None = None,
          transposed: bool = False) -> np.ndarray:
     """Return Y + α·A·X (or Y + α·Aᵀ·X) for A = Â + σI; X, Y are n×m in the
     caller's point order.  Follows Alg. "H2_mvm": forward, fast_addeval,
-    backward, then the diagonal shift."""
-    X = np.asarray(X, dtype=np.float64)
+    backward, then the diagonal shift.  The arithmetic is complex when the
+    matrix, X, Y or α is (K = C), FP64 otherwise."""
+    cplx = (np.dtype(H.dtype).kind == "c" or np.iscomplexobj(X) or np.iscomplexobj(alpha)
+            or (Y is not None and np.iscomplexobj(Y)))
+    dt = np.complex128 if cplx else np.float64
+    X = np.asarray(X, dtype=dt)
     squeeze = X.ndim == 1
     if squeeze:
         X = X[:, None]
     m = X.shape[1]
-    Yo = np.zeros((H.n, m)) if Y is None else np.array(Y, dtype=np.float64).reshape(H.n, m)
+    Yo = np.zeros((H.n, m), dtype=dt) if Y is None else np.array(Y, dtype=dt).reshape(H.n, m)
     xhat = {}
-    yhat = {c.id: np.zeros((H.k, m)) for c in H.clusters}
+    yhat = {c.id: np.zeros((H.k, m), dtype=dt) for c in H.clusters}
     _forward(H, H.root, X, xhat)
     _fast_addeval(H, alpha, H.btree, xhat, yhat, X, Yo, transposed)
     _backward(H, H.root, Yo, yhat)
@@ -540,7 +570,7 @@ def _expanded_basis(H: H2Matrix, c: Cluster) -> np.ndarray:
 
 def dense_expand(H: H2Matrix) -> np.ndarray:
     """The dense n×n matrix Â + σI represented by H (caller's point order)."""
-    A = np.zeros((H.n, H.n))
+    A = np.zeros((H.n, H.n), dtype=H.dtype)
     cache = {}
 
     def vb(c):
