@@ -67,7 +67,23 @@ typedef enum h2_dtype {
  * 0) or leaf × leaf.  Cluster bases: tensor Chebyshev interpolation of order
  * q per axis, rank k = q³, nested through transfer matrices (Def. "Cluster
  * basis"); coupling matrices S_b = [g(ξ_t,ν, ξ_s,μ)] (Eq. (h2_admissible));
- * inadmissible leaves stored densely. */
+ * inadmissible leaves stored densely.
+ *
+ * kernel selects g.  H2_KERNEL_EXP (0, the default of a zeroed struct) is the
+ * real kernel above.  H2_KERNEL_HELMHOLTZ (1) is the complex Helmholtz kernel
+ * of Sec. 2 (K = C, g_κ(x, y) = exp(iκr)/(4πr), r = |x - y|_2), regularised
+ * at r = 0 as
+ *   g(x, y) = exp(i·kappa·r) / (4π·sqrt(r² + delta²)),   delta > 0,
+ * with sigma still a real shift.  The bases V and E stay real (interpolation
+ * of real nodes); S_b and the nearfield blocks are complex, stored as a plane
+ * of real parts followed by a plane of imaginary parts.  A complex matrix is
+ * multiplied with h2_matmul_complex only (H2_F64, or H2_F32 with the FP32
+ * copy, both on the CUDA cores); every other entry point that computes with
+ * A returns H2_E_UNSUPPORTED for it, and precisions may not ask for BF16. */
+typedef enum h2_kernel {
+    H2_KERNEL_EXP = 0,       /* exp(-r / length), real                              */
+    H2_KERNEL_HELMHOLTZ = 1  /* exp(i·kappa·r) / (4π·sqrt(r² + delta²)), complex     */
+} h2_kernel;
 typedef struct h2_build_params {
     int32_t q;           /* interpolation order per axis, 1 <= q <= 5 (k = q³)   */
     int32_t leaf_size;   /* maximum points per leaf cluster, 1 <= leaf_size <= 64 */
@@ -77,6 +93,9 @@ typedef struct h2_build_params {
     uint32_t precisions; /* bit mask of extra copies to build: (1u<<H2_F32) | (1u<<H2_BF16);
                             the FP64 copy is always built                         */
     void* stream;        /* cudaStream_t used for the device part of the build    */
+    int32_t kernel;      /* h2_kernel                                              */
+    double kappa;        /* H2_KERNEL_HELMHOLTZ: wave number, finite               */
+    double delta;        /* H2_KERNEL_HELMHOLTZ: regularisation length, > 0        */
 } h2_build_params;
 
 typedef struct h2_matrix h2_matrix;
@@ -124,6 +143,21 @@ int h2_info(const h2_matrix* A, h2_info_t* info);
  * m = 0 is a no-op.  Not re-entrant on the same A. */
 int h2_matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
               int64_t m, int32_t dtype, void* stream);
+
+/* Y <- Y + alpha·A·X over K = C for a matrix built with H2_KERNEL_HELMHOLTZ
+ * (Sec. 2 "unless stated otherwise, K = C"; the product of Sec. 3–4 with
+ * complex coupling and nearfield blocks).  X and Y are n×m complex blocks,
+ * row-major, each element two doubles (real part, imaginary part): the
+ * layout of C99 double _Complex, std::complex<double> and complex128 arrays.
+ * ldx, ldy count complex elements (>= m); m <= 2^19.  alpha = alpha_re +
+ * i·alpha_im.  Host or device, like h2_matmul.  The forward and backward
+ * transformations run the real kernels on the 2m real columns; the coupling
+ * and nearfield kernels apply S_b = S_re + i·S_im as S_re·x̂ + S_im·(i·x̂).
+ * dtype H2_F64 or H2_F32 (the FP32 copy of the build; FP64 in and out).
+ * A real matrix gives H2_E_UNSUPPORTED.  A complex symmetric kernel gives
+ * Aᵀ = A, so no transposed complex product is provided. */
+int h2_matmul_complex(h2_matrix* A, double alpha_re, double alpha_im, const double* X, int64_t ldx,
+                      double* Y, int64_t ldy, int64_t m, int32_t dtype, void* stream);
 
 /* Y <- Y + alpha·Aᵀ·X: the same traversal with the roles of row and column
  * clusters swapped (S_bᵀ on admissible blocks, G_bᵀ on inadmissible ones). */

@@ -608,14 +608,15 @@ class H2Rows:
     where t runs over the ancestors of the leaf t_i that holds i and
     V_t[i, :] = V_{t_i}[i, :] E_{t_i} E_{father(t_i)} … (the nesting
     V_t|_{t̂'} = V_{t'} E_{t'}).  S_b and G_b are formed only for the blocks
-    that touch the requested rows.
+    that touch the requested rows.  ``kernel`` as for :class:`H2Matrix` (a
+    complex kernel gives complex rows, K = C).
     """
 
-    def __init__(self, points, q=3, leaf_size=64, eta=2.0, sigma=0.0, length=0.5):
+    def __init__(self, points, q=3, leaf_size=64, eta=2.0, sigma=0.0, length=0.5, kernel=None):
         self.points = np.ascontiguousarray(points, dtype=np.float64)
         self.n = self.points.shape[0]
         self.q, self.k, self.eta, self.sigma = q, q ** 3, eta, float(sigma)
-        self.g = exp_kernel(length)
+        self.g = kernel if kernel is not None else exp_kernel(length)
         self.root = build_cluster_tree(self.points, leaf_size)
         self.clusters = clusters_preorder(self.root)
         self.nodes = {c.id: cluster_nodes(c, q) for c in self.clusters}
@@ -644,13 +645,14 @@ class H2Rows:
 
     def forward(self, X):
         """x̂_s for every cluster (Alg. "forward/backward", forward part)."""
-        X = np.asarray(X, dtype=np.float64)
+        X = np.asarray(X)
+        X = X.astype(np.complex128 if np.iscomplexobj(X) else np.float64)
         xhat = {}
         for c in reversed(self.clusters):  # sons before fathers
             if c.is_leaf:
                 xhat[c.id] = self.V(c).T @ X[c.idx]
             else:
-                acc = np.zeros((self.k, X.shape[1]))
+                acc = np.zeros((self.k, X.shape[1]), dtype=X.dtype)
                 for c2 in c.sons:
                     acc += self.E(c2).T @ xhat[c2.id]
                 xhat[c.id] = acc
@@ -658,15 +660,18 @@ class H2Rows:
 
     def rows(self, alpha, X, rows, xhat=None):
         """Rows ``rows`` (original indices) of α(Â + σI)X, shape (len(rows), m)."""
-        X = np.asarray(X, dtype=np.float64)
+        X = np.asarray(X)
+        X = X.astype(np.complex128 if np.iscomplexobj(X) else np.float64)
         if xhat is None:
             xhat = self.forward(X)
-        out = np.zeros((len(rows), X.shape[1]))
+        gi = self.g(self.points[:1], self.points[:1])
+        dt = np.result_type(X.dtype, gi.dtype, np.asarray(alpha).dtype, np.float64)
+        out = np.zeros((len(rows), X.shape[1]), dtype=dt)
         for r, i in enumerate(rows):
             t = self.by_id[int(self.leaf_of[i])]
             a = int(self.pos_in_leaf[i])
             v = self.V(t)[a]  # V_t[i, :] at the leaf
-            acc = np.zeros(X.shape[1])
+            acc = np.zeros(X.shape[1], dtype=dt)
             for s in self.near_of.get(t.id, []):
                 acc += self.g(self.points[i][None, :], self.points[s.idx]) @ X[s.idx]
             c = t

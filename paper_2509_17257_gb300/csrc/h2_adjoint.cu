@@ -105,6 +105,7 @@ extern "C" {
 
 int h2_coupling_get(h2_matrix* A, double* S, void* stream) {
     if (!A || (!S && A->n_adm > 0)) { set_error("null argument"); return H2_E_BADARG; }
+    if (int rc = refuse_complex(A, "h2_coupling_get")) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)A->n_adm * A->k * A->k * sizeof(double);
     if (bytes) H2_CUDA_TRY(cudaMemcpyAsync(S, A->f64.S, bytes, cudaMemcpyDefault, st));
@@ -114,6 +115,7 @@ int h2_coupling_get(h2_matrix* A, double* S, void* stream) {
 
 int h2_coupling_set(h2_matrix* A, const double* S, void* stream) {
     if (!A || (!S && A->n_adm > 0)) { set_error("null argument"); return H2_E_BADARG; }
+    if (int rc = refuse_complex(A, "h2_coupling_set")) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t count = A->n_adm * A->k * A->k;
     if (count == 0) return 0;
@@ -148,6 +150,7 @@ int h2_shift_set(h2_matrix* A, double sigma) {
 
 int h2_adjoint_grads(h2_matrix* A, const double* L, int64_t ldl, const double* X, int64_t ldx, int64_t m,
                      double* dS, double* dsigma, void* stream) {
+    if (int rc = refuse_complex(A, "h2_adjoint_grads")) return rc;
     if (!A || (m > 0 && (!L || !X)) || m < 0 || ldl < m || ldx < m) {
         set_error("bad argument");
         return H2_E_BADARG;

@@ -114,6 +114,17 @@ int check_params(const h2_build_params* p) {
     if (!(p->eta > 0.0) || !std::isfinite(p->eta)) { h2::set_error("eta must be finite and > 0"); return H2_E_BADARG; }
     if (!(p->length > 0.0) || !std::isfinite(p->length)) { h2::set_error("length must be finite and > 0"); return H2_E_BADARG; }
     if (!std::isfinite(p->sigma)) { h2::set_error("sigma must be finite"); return H2_E_BADARG; }
+    if (p->kernel != H2_KERNEL_EXP && p->kernel != H2_KERNEL_HELMHOLTZ) {
+        h2::set_error("kernel must be H2_KERNEL_EXP or H2_KERNEL_HELMHOLTZ");
+        return H2_E_BADARG;
+    }
+    if (p->kernel == H2_KERNEL_HELMHOLTZ) {
+        if (!std::isfinite(p->kappa)) { h2::set_error("kappa must be finite"); return H2_E_BADARG; }
+        if (!(p->delta > 0.0) || !std::isfinite(p->delta)) {
+            h2::set_error("delta must be finite and > 0 (the regularisation of the Helmholtz kernel at r = 0)");
+            return H2_E_BADARG;
+        }
+    }
     return 0;
 }
 
@@ -223,6 +234,10 @@ int h2_build(const h2_build_params* params, const double* pts, int64_t n, h2_mat
     int rc = check_params(params);
     if (rc) return rc;
     if (!pts || n < 1) { h2::set_error("need n >= 1 points"); return H2_E_BADARG; }
+    if (params->kernel == H2_KERNEL_HELMHOLTZ && (params->precisions & (1u << H2_BF16))) {
+        h2::set_error("a complex kernel has no BF16 product");
+        return H2_E_UNSUPPORTED;
+    }
     cudaStream_t st = (cudaStream_t)params->stream;
     std::vector<double> host;
     const double* hp = pts;
@@ -244,6 +259,10 @@ int h2_build(const h2_build_params* params, const double* pts, int64_t n, h2_mat
     A->k = params->q * params->q * params->q;
     A->length = params->length;
     A->sigma = params->sigma;
+    A->kernel = params->kernel;
+    A->cplx = params->kernel == H2_KERNEL_HELMHOLTZ;
+    A->kappa = A->cplx ? params->kappa : 0.0;
+    A->delta = A->cplx ? params->delta : 0.0;
     A->n = n;
     A->nc = A->T.n_clusters();
     A->n_adm = A->T.n_adm();
@@ -288,6 +307,9 @@ int h2_info(const h2_matrix* A, h2_info_t* info) {
     // leaf forward + leaf backward, up + down transfers, coupling, nearfield, shift
     info->flops_per_col = 2.0 * 2.0 * (double)A->n * k + 2.0 * 2.0 * (double)(A->nc - 1) * k * k +
                           2.0 * (double)A->n_adm * k * k + 2.0 * (double)A->nnz_near + 2.0 * (double)A->n;
+    if (A->cplx)  // per complex column: real transfers on two real columns, 8 flops per complex multiply-add
+        info->flops_per_col = 2.0 * (2.0 * 2.0 * (double)A->n * k + 2.0 * 2.0 * (double)(A->nc - 1) * k * k) +
+                              8.0 * ((double)A->n_adm * k * k + (double)A->nnz_near) + 4.0 * (double)A->n;
     info->launches = A->launches_per_product;
     // tensor-core chain: gather, upward pass, coupling, downward pass, leaf phase, scatter into Y, + zeroing of
     // clusters without couplings; where the subtree-owning transfer passes do not apply (k % 4 != 0 or
@@ -348,8 +370,28 @@ int h2_matmul_transposed(h2_matrix* A, double alpha, const double* X, int64_t ld
     return h2::matmul(A, alpha, X, ldx, Y, ldy, m, dtype, (cudaStream_t)stream, true);
 }
 
+int h2_matmul_complex(h2_matrix* A, double alpha_re, double alpha_im, const double* X, int64_t ldx, double* Y,
+                      int64_t ldy, int64_t m, int32_t dtype, void* stream) {
+    if (!A) { h2::set_error("null argument"); return H2_E_BADARG; }
+    if (m < 0 || m > ((int64_t)1 << 19) || ldx < m || ldy < m || ldx > INT64_MAX / 2 || ldy > INT64_MAX / 2) {
+        h2::set_error("h2_matmul_complex: bad m / leading dimension (m <= 2^19 complex columns)");
+        return H2_E_BADARG;
+    }
+    if (dtype != H2_F64 && dtype != H2_F32) {
+        h2::set_error("h2_matmul_complex: dtype H2_F64 or H2_F32");
+        return H2_E_UNSUPPORTED;
+    }
+    if (!std::isfinite(alpha_re) || !std::isfinite(alpha_im)) {
+        h2::set_error("h2_matmul_complex: alpha must be finite");
+        return H2_E_BADARG;
+    }
+    // interleaved complex blocks as doubles: 2m real columns, leading dimensions 2·ld
+    return h2::matmul(A, alpha_re, X, 2 * ldx, Y, 2 * ldy, 2 * m, dtype, (cudaStream_t)stream, false, &alpha_im);
+}
+
 int h2_block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
                 const h2_cg_params* params, h2_cg_result* res) {
+    if (int rc = h2::refuse_complex(A, "h2_block_cg")) return rc;
     return h2::block_cg(A, B, ldb, X, ldx, m, params, res);
 }
 
@@ -372,6 +414,7 @@ int h2_set_wait_limit(int64_t polls) {
 
 int h2_block_gmres(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
                    const h2_gmres_params* params, h2_cg_result* res) {
+    if (int rc = h2::refuse_complex(A, "h2_block_gmres")) return rc;
     return h2::block_gmres(A, B, ldb, X, ldx, m, params, res);
 }
 

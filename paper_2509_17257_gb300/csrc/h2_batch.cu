@@ -240,6 +240,7 @@ int h2_batch_create(h2_matrix* const* mats, int32_t count, h2_batch** out) {
     h2_batch* b = new h2_batch();
     for (int i = 0; i < count; ++i) {
         if (!mats[i]) { delete b; set_error("null matrix in batch"); return H2_E_BADARG; }
+        if (int rc = refuse_complex(mats[i], "h2_batch_create")) { delete b; return rc; }
         b->mats.push_back(mats[i]);
     }
     const char* mv = getenv("H2_BATCH_MULTI");
@@ -360,6 +361,7 @@ int time_variant(h2_matrix* A, int64_t m, int32_t dtype, cudaStream_t st, double
 
 int h2_autotune_ex(h2_matrix* A, int64_t m, int32_t dtype, void* stream, h2_tune_result* out) {
     if (!A || m < 1 || (dtype != H2_F32 && dtype != H2_BF16)) { set_error("h2_autotune_ex: bad argument"); return H2_E_BADARG; }
+    if (int rc = refuse_complex(A, "h2_autotune_ex")) return rc;
     if (dtype == H2_F32 && !A->f32.built) { set_error("FP32 copy not built"); return H2_E_UNSUPPORTED; }
     if (dtype == H2_BF16 && !A->tc.has_bf16) { set_error("BF16 copy not built"); return H2_E_UNSUPPORTED; }
     cudaStream_t st = (cudaStream_t)stream;

@@ -67,6 +67,31 @@ __device__ __forceinline__ double kernel_g(const double* x, const double* y, dou
     return exp(-sqrt((d0 * d0 + d1 * d1) + d2 * d2) * inv_len);
 }
 
+// The kernel of a build: exp(-r / length) (real), or the Helmholtz kernel of
+// Sec. 2 regularised at r = 0, exp(i κ r) / (4π sqrt(r² + δ²)) (complex).
+struct KernelSpec {
+    int cplx;
+    double inv_len, kappa, delta;
+};
+
+// g(x, y) into (re, im); im = 0 for the real kernel.
+__device__ __forceinline__ void kernel_eval(const KernelSpec& ks, const double* x, const double* y, double* re,
+                                            double* im) {
+    if (!ks.cplx) {
+        *re = kernel_g(x, y, ks.inv_len);
+        *im = 0.0;
+        return;
+    }
+    const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+    const double r2 = (d0 * d0 + d1 * d1) + d2 * d2;
+    const double r = sqrt(r2);
+    double sn, cs;
+    sincos(ks.kappa * r, &sn, &cs);
+    const double scale = 1.0 / (4.0 * 3.141592653589793 * sqrt(r2 + ks.delta * ks.delta));
+    *re = cs * scale;
+    *im = sn * scale;
+}
+
 // V_t[i, ν] = L_{t,ν}(x_i) for the points i of leaf t (one CTA per leaf).
 __global__ void k_leaf_basis(const int32_t* __restrict__ leaves, const int32_t* __restrict__ cl_off,
                              const int32_t* __restrict__ cl_size, const double* __restrict__ pts,
@@ -98,9 +123,10 @@ __global__ void k_transfer(const int32_t* __restrict__ parent, const double* __r
     }
 }
 
-// S_b[ν, μ] = g(ξ_{t,ν}, ξ_{s,μ}) for admissible blocks in list order.
+// S_b[ν, μ] = g(ξ_{t,ν}, ξ_{s,μ}) for admissible blocks in list order (a complex
+// kernel: imaginary parts in a second plane, n_adm·k² elements further on).
 __global__ void k_coupling_entries(const int32_t* __restrict__ adm_row, const int32_t* __restrict__ adm_col,
-                                   int64_t n_adm, const double* __restrict__ nodes, int q, double inv_len,
+                                   int64_t n_adm, const double* __restrict__ nodes, int q, KernelSpec ks,
                                    double* __restrict__ S) {
     const int k = q * q * q;
     for (int64_t j = blockIdx.x; j < n_adm; j += gridDim.x) {
@@ -111,7 +137,10 @@ __global__ void k_coupling_entries(const int32_t* __restrict__ adm_row, const in
             double a[3], b[3];
             tensor_node(nt, q, nu, a);
             tensor_node(ns, q, mu, b);
-            S[(size_t)j * k * k + e] = kernel_g(a, b, inv_len);
+            double re, im;
+            kernel_eval(ks, a, b, &re, &im);
+            S[(size_t)j * k * k + e] = re;
+            if (ks.cplx) S[((size_t)n_adm + j) * k * k + e] = im;
         }
     }
 }
@@ -133,18 +162,23 @@ __global__ void k_nodes4(const double* __restrict__ nodes, int64_t nc, int q, in
     }
 }
 
-// G_b[i, j] = g(x_i, x_j) for inadmissible blocks.
+// G_b[i, j] = g(x_i, x_j) for inadmissible blocks (a complex kernel: imaginary
+// parts in a second plane, im_off = nnz_near elements further on).
 __global__ void k_near_entries(const int32_t* __restrict__ near_row, const int32_t* __restrict__ near_col,
                                const int64_t* __restrict__ near_off, int64_t n_near,
                                const int32_t* __restrict__ cl_off, const int32_t* __restrict__ cl_size,
-                               const double* __restrict__ pts, double inv_len, double* __restrict__ G) {
+                               const double* __restrict__ pts, KernelSpec ks, int64_t im_off,
+                               double* __restrict__ G) {
     for (int64_t j = blockIdx.x; j < n_near; j += gridDim.x) {
         const int t = near_row[j], s = near_col[j];
         const int ot = cl_off[t], nt = cl_size[t], os = cl_off[s], ns = cl_size[s];
         double* g = G + near_off[j];
         for (int e = threadIdx.x; e < nt * ns; e += blockDim.x) {
             const int r = e / ns, c = e % ns;
-            g[e] = kernel_g(pts + 3 * (size_t)(ot + r), pts + 3 * (size_t)(os + c), inv_len);
+            double re, im;
+            kernel_eval(ks, pts + 3 * (size_t)(ot + r), pts + 3 * (size_t)(os + c), &re, &im);
+            g[e] = re;
+            if (ks.cplx) g[im_off + e] = im;
         }
     }
 }
@@ -552,8 +586,9 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
 
     const size_t bV = (size_t)n * k * sizeof(double);
     const size_t bE = (size_t)nc * k * k * sizeof(double);
-    const size_t bS = (size_t)A->n_adm * k * k * sizeof(double);
-    const size_t bN = (size_t)A->nnz_near * sizeof(double);
+    const size_t planes = A->cplx ? 2 : 1;  // complex S and nearfield: real and imaginary planes
+    const size_t bS = planes * (size_t)A->n_adm * k * k * sizeof(double);
+    const size_t bN = planes * (size_t)A->nnz_near * sizeof(double);
     if ((rc = device_alloc(A, &A->f64.V, bV))) return rc;
     if ((rc = device_alloc(A, &A->f64.E, bE))) return rc;
     if ((rc = device_alloc(A, &A->f64.S, bS > 0 ? bS : 8))) return rc;
@@ -561,7 +596,7 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
     A->f64.bytes = (int64_t)(bV + bE + bS + bN);
     H2_CUDA_TRY(cudaMemsetAsync(A->f64.E, 0, bE, st));
 
-    const double inv_len = 1.0 / A->length;
+    const KernelSpec ks{A->cplx ? 1 : 0, 1.0 / A->length, A->kappa, A->delta};
     k_leaf_basis<<<(unsigned)NL, 256, 0, st>>>(A->d_leaves, A->d_cl_off, A->d_cl_size, A->d_pts, A->d_nodes,
                                                q, (double*)A->f64.V);
     H2_LAUNCH_CHECK();
@@ -569,14 +604,14 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
     H2_LAUNCH_CHECK();
     if (A->n_adm > 0) {
         const unsigned g = (unsigned)std::min<int64_t>(A->n_adm, 152 * 64);
-        k_coupling_entries<<<g, 256, 0, st>>>(A->d_adm_row, A->d_adm_col, A->n_adm, A->d_nodes, q, inv_len,
+        k_coupling_entries<<<g, 256, 0, st>>>(A->d_adm_row, A->d_adm_col, A->n_adm, A->d_nodes, q, ks,
                                               (double*)A->f64.S);
         H2_LAUNCH_CHECK();
     }
     if (A->n_near > 0) {
         const unsigned g = (unsigned)std::min<int64_t>(A->n_near, 152 * 64);
         k_near_entries<<<g, 256, 0, st>>>(A->d_near_row, A->d_near_col, A->d_near_off, A->n_near, A->d_cl_off,
-                                          A->d_cl_size, A->d_pts, inv_len, (double*)A->f64.Near);
+                                          A->d_cl_size, A->d_pts, ks, A->nnz_near, (double*)A->f64.Near);
         H2_LAUNCH_CHECK();
     }
     A->f64.built = true;
@@ -584,8 +619,10 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
     if (precisions & (1u << H2_F32)) {
         if ((rc = cast_copy(A, (const double*)A->f64.V, &A->f32.V, (int64_t)n * k, st))) return rc;
         if ((rc = cast_copy(A, (const double*)A->f64.E, &A->f32.E, nc * k * k, st))) return rc;
-        if ((rc = cast_copy(A, (const double*)A->f64.S, &A->f32.S, A->n_adm * k * k, st))) return rc;
-        if ((rc = cast_copy(A, (const double*)A->f64.Near, &A->f32.Near, A->nnz_near, st))) return rc;
+        if ((rc = cast_copy(A, (const double*)A->f64.S, &A->f32.S, (int64_t)planes * A->n_adm * k * k, st)))
+            return rc;
+        if ((rc = cast_copy(A, (const double*)A->f64.Near, &A->f32.Near, (int64_t)planes * A->nnz_near, st)))
+            return rc;
         A->f32.bytes = A->f64.bytes / 2;
         A->f32.built = true;
     }
@@ -595,7 +632,12 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
         H2_CUDA_TRY(cudaHostGetDevicePointer((void**)&A->err_dev, A->err_host, 0));
     }
     const bool want_bf16 = (precisions & (1u << H2_BF16)) != 0;
-    const bool want_tf32 = (precisions & (1u << H2_F32)) != 0 && k <= 64;
+    // the complex product runs on the CUDA cores only: no tensor-core tiles
+    const bool want_tf32 = (precisions & (1u << H2_F32)) != 0 && k <= 64 && !A->cplx;
+    if (want_bf16 && A->cplx) {
+        set_error("a complex kernel has no BF16 product");
+        return H2_E_UNSUPPORTED;
+    }
     if (want_bf16 && k > 64) {
         set_error("the BF16 tensor-core product supports q <= 4 (k <= 64)");
         return H2_E_UNSUPPORTED;

@@ -303,6 +303,12 @@ struct h2_matrix {
     h2::Tree T;
     int q = 0, k = 0;
     double length = 0, sigma = 0;
+    // kernel g: H2_KERNEL_EXP (real) or H2_KERNEL_HELMHOLTZ (complex; kappa, delta).  A
+    // complex matrix (cplx) stores S and the nearfield blocks of f64 / f32 as two planes,
+    // real parts then imaginary parts; V and E are real.
+    int32_t kernel = 0;
+    double kappa = 0, delta = 0;
+    bool cplx = false;
     int64_t n = 0, nc = 0, n_leaves = 0, n_adm = 0, n_near = 0, nnz_near = 0;
     int32_t depth = 0;
 
@@ -466,12 +472,19 @@ int batch_block_cg(h2_batch* b, const double* const* B, const int64_t* ldb, doub
 
 // Entry points implemented in h2_build.cu / h2_mm.cu / h2_cg.cu.
 int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cudaStream_t st);
+// With alpha_im (the complex product of a complex matrix, h2_matmul_complex) X and
+// Y are interleaved complex blocks seen as doubles: m, ldx and ldy count doubles
+// (twice the complex counts) and α = alpha + i·*alpha_im.  Without it the matrix
+// must be real.
 int matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
-           int64_t m, int32_t dtype, cudaStream_t st, bool transposed);
+           int64_t m, int32_t dtype, cudaStream_t st, bool transposed, const double* alpha_im = nullptr);
+// H2_E_UNSUPPORTED (with a message naming `what`) for a complex matrix: the
+// entry points other than h2_matmul_complex compute over R only.
+int refuse_complex(const h2_matrix* A, const char* what);
 // Device-pointer product used by the solvers: Y = overwrite ? alpha·A·X : Y + alpha·A·X.
 int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y,
                   int64_t ldy, int64_t m, int32_t dtype, cudaStream_t st, bool transposed,
-                  bool overwrite);
+                  bool overwrite, const double* alpha_im = nullptr);
 int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,
              const h2_cg_params* p, h2_cg_result* res);
 int block_gmres(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t m,

@@ -79,8 +79,10 @@ __device__ __forceinline__ void lds_vec(const double* p, double (&v)[N]) {
 // op(A) = A (A is M×K row-major, leading dimension lda) or, with TA, Aᵀ
 // (A stored K×M row-major).  Rows >= M, k >= K and columns >= ncol read as 0.
 // CGB: read B through L2 only (ld.global.cg), for data another CTA of the same
-// launch wrote.
-template <typename T, int RM, int CN, bool TA, bool CGB = false>
+// launch wrote.  IB: B holds interleaved complex columns (real part 2j,
+// imaginary part 2j+1) and i·B is staged instead: column 2j gets -B[:, 2j+1]
+// and column 2j+1 gets B[:, 2j] (ncol even).
+template <typename T, int RM, int CN, bool TA, bool CGB = false, bool IB = false>
 __device__ __forceinline__ void mac(Acc<T, RM, CN>& acc, Smem<T, RM, CN>& sm, const T* __restrict__ A,
                                     int64_t lda, int M, int K, int row0, const T* B,
                                     int64_t ldb, int ncol, int col0) {
@@ -105,7 +107,10 @@ __device__ __forceinline__ void mac(Acc<T, RM, CN>& acc, Smem<T, RM, CN>& sm, co
         for (int e = tid; e < NT * kKC; e += kThreads) {
             const int c = e % NT, kk = e / NT;
             const int gc = col0 + c;
-            if (CGB) sm.b[kk][c] = (gc < ncol && kk < kc) ? __ldcg(B + (int64_t)(k0 + kk) * ldb + gc) : T(0);
+            if (IB) {
+                const T v = (gc < ncol && kk < kc) ? B[(int64_t)(k0 + kk) * ldb + (gc ^ 1)] : T(0);
+                sm.b[kk][c] = (gc & 1) ? v : -v;
+            } else if (CGB) sm.b[kk][c] = (gc < ncol && kk < kc) ? __ldcg(B + (int64_t)(k0 + kk) * ldb + gc) : T(0);
             else sm.b[kk][c] = (gc < ncol && kk < kc) ? B[(int64_t)(k0 + kk) * ldb + gc] : T(0);
         }
         __syncthreads();
@@ -399,6 +404,82 @@ __global__ void __launch_bounds__(kThreads) k_leaf_bwd_near(
             if (gc >= m) continue;
             const double z = (double)acc.v[r][c] + sigma * (double)xrow[gc];
             if (overwrite) yrow[gc] = alpha * z; else yrow[gc] += alpha * z;
+        }
+    }
+}
+
+// ---- the complex product (K = C, Sec. 2): real bases, complex S_b and G_b ----
+// Coefficient blocks and X are interleaved complex columns (2m real columns), so
+// the transfer passes are the real kernels above; only the phases that apply
+// S_b and G_b differ.  With S = S_re + i·S_im (two planes im_off elements apart),
+// S·x̂ = S_re·x̂ + S_im·(i·x̂), two real products into one accumulator.
+template <typename T, int RM, int CN>
+__global__ void __launch_bounds__(kThreads) k_coupling_c(const int32_t* __restrict__ rowptr,
+                                                         const int32_t* __restrict__ other,
+                                                         const T* __restrict__ S, int64_t im_off,
+                                                         const T* __restrict__ xhat, T* __restrict__ yhat, int k,
+                                                         int m2) {
+    __shared__ Smem<T, RM, CN> sm;
+    const int t = blockIdx.x;
+    const int col0 = blockIdx.y * 16 * CN, row0 = blockIdx.z * 16 * RM;
+    Acc<T, RM, CN> acc;
+    acc.zero();
+    const int64_t kk = (int64_t)k * k, km = (int64_t)k * m2;
+    for (int e = rowptr[t]; e < rowptr[t + 1]; ++e) {
+        const T* xs = xhat + (int64_t)other[e] * km;
+        mac<T, RM, CN, false>(acc, sm, S + e * kk, k, k, k, row0, xs, m2, m2, col0);
+        mac<T, RM, CN, false, false, true>(acc, sm, S + im_off + e * kk, k, k, k, row0, xs, m2, m2, col0);
+    }
+    store_tile<T, RM, CN, false>(acc, yhat + (int64_t)t * km, m2, k, m2, row0, col0);
+}
+
+// Y[perm[off_t + i], :] (+)= α (V_t ŷ_t + Σ_b G_b Xp|_ŝ + σ Xp|_t̂)[i, :] over C:
+// G_b = G_re + i·G_im (planes im_off elements apart), α = alpha_re + i·alpha_im.
+// CN is even, so a thread holds both parts of each complex column.
+template <typename T, int RM, int CN>
+__global__ void __launch_bounds__(kThreads) k_leaf_bwd_near_c(
+    const int32_t* __restrict__ leaves, const int32_t* __restrict__ cl_off, const int32_t* __restrict__ cl_size,
+    const int32_t* __restrict__ perm, const T* __restrict__ V, const T* __restrict__ yhat,
+    const int32_t* __restrict__ nptr, const int32_t* __restrict__ nother, const int64_t* __restrict__ near_off,
+    const T* __restrict__ G, int64_t im_off, const T* __restrict__ Xp, double* __restrict__ Y, int64_t ldy,
+    double alpha_re, double alpha_im, double sigma, int k, int m2, int overwrite) {
+    static_assert(CN % 2 == 0, "complex columns are pairs within a thread");
+    __shared__ Smem<T, RM, CN> sm;
+    const int lp = blockIdx.x;
+    const int t = leaves[lp];
+    const int col0 = blockIdx.y * 16 * CN, row0 = blockIdx.z * 16 * RM;
+    const int off = cl_off[t], nt = cl_size[t];
+    Acc<T, RM, CN> acc;
+    acc.zero();
+    mac<T, RM, CN, false>(acc, sm, V + (int64_t)off * k, k, nt, k, row0, yhat + (int64_t)t * k * m2, m2, m2, col0);
+    for (int e = nptr[lp]; e < nptr[lp + 1]; ++e) {
+        const int s = nother[e];
+        const int os = cl_off[s], ns = cl_size[s];
+        const T* xs = Xp + (int64_t)os * m2;
+        mac<T, RM, CN, false>(acc, sm, G + near_off[e], ns, nt, ns, row0, xs, m2, m2, col0);
+        mac<T, RM, CN, false, false, true>(acc, sm, G + im_off + near_off[e], ns, nt, ns, row0, xs, m2, m2, col0);
+    }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+        const int i = row0 + RM * ty + r;
+        if (i >= nt) continue;
+        double* yrow = Y + (int64_t)perm[off + i] * ldy;
+        const T* xrow = Xp + (int64_t)(off + i) * m2;
+#pragma unroll
+        for (int c = 0; c < CN; c += 2) {
+            const int gc = col0 + CN * tx + c;  // even: the real part of a complex column
+            if (gc >= m2) continue;
+            const double zr = (double)acc.v[r][c] + sigma * (double)xrow[gc];
+            const double zi = (double)acc.v[r][c + 1] + sigma * (double)xrow[gc + 1];
+            const double vr = alpha_re * zr - alpha_im * zi, vi = alpha_re * zi + alpha_im * zr;
+            if (overwrite) {
+                yrow[gc] = vr;
+                yrow[gc + 1] = vi;
+            } else {
+                yrow[gc] += vr;
+                yrow[gc + 1] += vi;
+            }
         }
     }
 }
@@ -993,9 +1074,12 @@ int backward_pass(h2_matrix* A, const T* E, T* yhat, int m, unsigned gy, unsigne
     return 0;
 }
 
+// alpha_im: the complex product (m counts the 2·m_c real columns of the interleaved
+// complex blocks; CN is even); the transfer passes are the real ones.
 template <typename T, int RM, int CN>
 int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
-              int m, cudaStream_t st, bool transposed, bool overwrite, T* Xp, T* xhat, T* yhat, const SyncBufs& sb) {
+              int m, cudaStream_t st, bool transposed, bool overwrite, T* Xp, T* xhat, T* yhat, const SyncBufs& sb,
+              const double* alpha_im = nullptr) {
     constexpr int MT = 16 * RM, NT = 16 * CN;
     const int k = A->k;
     const unsigned gy = (unsigned)((m + NT - 1) / NT);
@@ -1018,7 +1102,15 @@ int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int
     const unsigned NL = (unsigned)A->leaves.size();
     if ((rc = forward_pass<T, RM, CN>(A, V, E, Xp, xhat, m, gy, gzk, st, sb, marks))) return rc;
     marks.kernel_begin();
-    if (transposed)
+    if (alpha_im) {
+        if constexpr (CN % 2 == 0) {
+            k_coupling_c<T, RM, CN><<<dim3((unsigned)A->nc, gy, gzk), kThreads, 0, st>>>(
+                A->d_adm_rowptr, A->d_adm_col, S, A->n_adm * (int64_t)k * k, xhat, yhat, k, m);
+        } else {
+            set_error("complex product: column tiles must hold whole complex columns");
+            return H2_E_UNSUPPORTED;
+        }
+    } else if (transposed)
         k_coupling<T, RM, CN, true><<<dim3((unsigned)A->nc, gy, gzk), kThreads, 0, st>>>(
             A->d_admT_rowptr, A->d_admT_row, A->d_admT_blk, S, xhat, yhat, k, m);
     else
@@ -1030,7 +1122,16 @@ int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int
     if ((rc = backward_pass<T, RM, CN>(A, E, yhat, m, gy, gzk, st, sb))) return rc;
     marks.mark();
     if ((rc = wait_y_staged(A->ws, st))) return rc;
-    if (transposed)
+    if (alpha_im) {
+        if constexpr (CN % 2 == 0) {
+            k_leaf_bwd_near_c<T, RM, CN><<<dim3(NL, gy, gzl), kThreads, 0, st>>>(
+                A->d_leaves, A->d_cl_off, A->d_cl_size, A->d_perm, V, yhat, A->d_near_ptr, A->d_near_col,
+                A->d_near_off, G, A->nnz_near, Xp, Y, ldy, alpha, *alpha_im, A->sigma, k, m, overwrite ? 1 : 0);
+        } else {
+            set_error("complex product: column tiles must hold whole complex columns");
+            return H2_E_UNSUPPORTED;
+        }
+    } else if (transposed)
         k_leaf_bwd_near<T, RM, CN, true><<<dim3(NL, gy, gzl), kThreads, 0, st>>>(
             A->d_leaves, A->d_cl_off, A->d_cl_size, A->d_perm, V, yhat, A->d_nearT_ptr, A->d_nearT_row,
             A->d_nearT_blk, A->d_near_off, G, Xp, Y, ldy, alpha, A->sigma, k, m, overwrite ? 1 : 0);
@@ -1354,7 +1455,14 @@ int dispatch_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t l
 template <typename T>
 int dispatch_cn(h2_matrix* A, const MatData& D, double alpha, const double* X, int64_t ldx, double* Y,
                 int64_t ldy, int m, cudaStream_t st, bool transposed, bool overwrite, T* Xp, T* xhat, T* yhat,
-                const SyncBufs& sb) {
+                const SyncBufs& sb, const double* alpha_im = nullptr) {
+    if (alpha_im) {  // complex: column tiles of an even width (2 or 4 per thread)
+        if (m <= 32)
+            return run_chain<T, 4, 2>(A, D, alpha, X, ldx, Y, ldy, m, st, false, overwrite, Xp, xhat, yhat, sb,
+                                      alpha_im);
+        return run_chain<T, 4, 4>(A, D, alpha, X, ldx, Y, ldy, m, st, false, overwrite, Xp, xhat, yhat, sb,
+                                  alpha_im);
+    }
     if (m <= 16) return run_chain<T, 4, 1>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat, sb);
     if (m <= 32) return run_chain<T, 4, 2>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat, sb);
     return run_chain<T, 4, 4>(A, D, alpha, X, ldx, Y, ldy, m, st, transposed, overwrite, Xp, xhat, yhat, sb);
@@ -1400,8 +1508,26 @@ int check_device_error(h2_matrix* A) {
 
 }  // namespace
 
+int refuse_complex(const h2_matrix* A, const char* what) {
+    if (A && A->cplx) {
+        set_error(std::string(what) + ": the matrix has a complex kernel; use h2_matmul_complex");
+        return H2_E_UNSUPPORTED;
+    }
+    return 0;
+}
+
 int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
-                  int32_t dtype, cudaStream_t st, bool transposed, bool overwrite) {
+                  int32_t dtype, cudaStream_t st, bool transposed, bool overwrite, const double* alpha_im) {
+    if (!alpha_im) {
+        const int rc = refuse_complex(A, "real product");
+        if (rc) return rc;
+    } else {
+        if (!A->cplx) { set_error("h2_matmul_complex: the matrix has a real kernel"); return H2_E_UNSUPPORTED; }
+        if (transposed || (dtype != H2_F64 && dtype != H2_F32) || (m & 1)) {
+            set_error("complex product: A·X in H2_F64 or H2_F32 only");
+            return H2_E_UNSUPPORTED;
+        }
+    }
     if (m == 0) return 0;
     const size_t elt = dtype == H2_F64 ? sizeof(double) : sizeof(float);
     const size_t bXp = align_up((size_t)A->n * m * elt);
@@ -1416,10 +1542,13 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
     if (dtype == H2_F64) {
         if (!A->f64.built) { set_error("FP64 data not built"); return H2_E_UNSUPPORTED; }
         return dispatch_cn<double>(A, A->f64, alpha, X, ldx, Y, ldy, (int)m, st, transposed, overwrite,
-                                   (double*)base, (double*)(base + bXp), (double*)(base + bXp + bC), sb);
+                                   (double*)base, (double*)(base + bXp), (double*)(base + bXp + bC), sb, alpha_im);
     }
     if (dtype == H2_F32) {
         if (!A->f32.built) { set_error("FP32 copy not built (add 1<<H2_F32 to params->precisions)"); return H2_E_UNSUPPORTED; }
+        if (alpha_im)
+            return dispatch_cn<float>(A, A->f32, alpha, X, ldx, Y, ldy, (int)m, st, false, overwrite, (float*)base,
+                                      (float*)(base + bXp), (float*)(base + bXp + bC), sb, alpha_im);
         const Tune& tn = A->tune[0][column_class((int)std::min<int64_t>(m, 64))];
         if (A->tc.has_tf32 && !A->force_simt && tn.path != kPathSimt)
             return dispatch_tc(A, 1, alpha, X, ldx, Y, ldy, m, st, overwrite, sb, transposed);
@@ -1580,16 +1709,23 @@ int matmul_in_scratch(h2_matrix* A, double alpha, const double* X, int64_t ldx, 
 }
 
 int matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
-           int32_t dtype, cudaStream_t st, bool transposed) {
+           int32_t dtype, cudaStream_t st, bool transposed, const double* alpha_im) {
     if (!A || (!X && m > 0) || (!Y && m > 0)) { set_error("null argument"); return H2_E_BADARG; }
     if (m < 0 || ldx < m || ldy < m || m > (int64_t)1 << 20) { set_error("bad m / leading dimension"); return H2_E_BADARG; }
     if (dtype != H2_F64 && dtype != H2_F32 && dtype != H2_BF16 && dtype != H2_F32_MF) {
         set_error("bad dtype");
         return H2_E_BADARG;
     }
+    if (!alpha_im) {
+        const int rc = refuse_complex(A, transposed ? "h2_matmul_transposed" : "h2_matmul");
+        if (rc) return rc;
+    } else if (!A->cplx) {
+        set_error("h2_matmul_complex: the matrix has a real kernel");
+        return H2_E_UNSUPPORTED;
+    }
     if (m == 0) return 0;
     const bool dx = is_device_pointer(X), dy = is_device_pointer(Y);
-    if (dx && dy) return matmul_device(A, alpha, X, ldx, Y, ldy, m, dtype, st, transposed, false);
+    if (dx && dy) return matmul_device(A, alpha, X, ldx, Y, ldy, m, dtype, st, transposed, false, alpha_im);
     // Host blocks go through device staging buffers by the copy engines: X in on the
     // call's stream before the product, Y in on a side stream while the product
     // computes (its final pass waits for that copy), Y back out after it.  The call
@@ -1636,7 +1772,7 @@ int matmul(h2_matrix* A, double alpha, const double* X, int64_t ldx, double* Y, 
         Yd = W.stage_y;
         ldyd = m;
     }
-    rc = matmul_device(A, alpha, Xd, ldxd, Yd, ldyd, m, dtype, st, transposed, false);
+    rc = matmul_device(A, alpha, Xd, ldxd, Yd, ldyd, m, dtype, st, transposed, false, alpha_im);
     if (!rc) rc = wait_y_staged(W, st);  // a path that never reached its final pass
     if (rc) {
         W.y_wait = false;

@@ -98,6 +98,7 @@ extern "C" int h2_matmul_noalloc(h2_matrix* A, double alpha, const double* X, in
         h2::set_error("h2_matmul_noalloc: dtype must be H2_F64 or H2_F32");
         return H2_E_UNSUPPORTED;
     }
+    if (int rc = h2::refuse_complex(A, "h2_matmul_noalloc")) return rc;
     if (m == 0) return 0;
     if ((dtype == H2_F64 && !A->f64.built) || (dtype == H2_F32 && !A->f32.built)) {
         h2::set_error("h2_matmul_noalloc: this precision was not built for the matrix");

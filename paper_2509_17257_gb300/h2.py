@@ -49,9 +49,14 @@ class H2Error(RuntimeError):
         self.code = code
 
 
+H2_KERNEL_EXP, H2_KERNEL_HELMHOLTZ = 0, 1
+KERNELS = {"exp": H2_KERNEL_EXP, "helmholtz": H2_KERNEL_HELMHOLTZ}
+
+
 class BuildParams(C.Structure):
     _fields_ = [("q", C.c_int32), ("leaf_size", C.c_int32), ("eta", C.c_double), ("length", C.c_double),
-                ("sigma", C.c_double), ("precisions", C.c_uint32), ("stream", C.c_void_p)]
+                ("sigma", C.c_double), ("precisions", C.c_uint32), ("stream", C.c_void_p),
+                ("kernel", C.c_int32), ("kappa", C.c_double), ("delta", C.c_double)]
 
 
 class Info(C.Structure):
@@ -103,7 +108,8 @@ class TreeView(C.Structure):
 
 
 #: every symbol include/h2.h declares
-EXPORTS = ["h2_build", "h2_free", "h2_info", "h2_matmul", "h2_matmul_transposed", "h2_matmul_noalloc", "h2_block_cg", "h2_block_gmres",
+EXPORTS = ["h2_build", "h2_free", "h2_info", "h2_matmul", "h2_matmul_transposed", "h2_matmul_noalloc",
+           "h2_matmul_complex", "h2_block_cg", "h2_block_gmres",
            "h2_timing_enable", "h2_timing_query", "h2_coupling_get", "h2_coupling_set", "h2_shift_set",
            "h2_adjoint_grads", "h2_batch_create", "h2_batch_free", "h2_batch_matmul", "h2_batch_block_cg",
            "h2_autotune", "h2_autotune_ex",
@@ -129,6 +135,7 @@ def lib() -> C.CDLL:
     L.h2_info.argtypes = [vp, C.POINTER(Info)]
     for f in (L.h2_matmul, L.h2_matmul_transposed, L.h2_matmul_noalloc):
         f.argtypes = [vp, dbl, vp, i64, vp, i64, i64, i32, vp]
+    L.h2_matmul_complex.argtypes = [vp, dbl, dbl, vp, i64, vp, i64, i64, i32, vp]
     L.h2_block_cg.argtypes = [vp, vp, i64, vp, i64, i64, C.POINTER(CGParams), C.POINTER(CGResult)]
     L.h2_block_gmres.argtypes = [vp, vp, i64, vp, i64, i64, C.POINTER(GMRESParams), C.POINTER(CGResult)]
     L.h2_coupling_get.argtypes = [vp, vp, vp]
@@ -216,15 +223,18 @@ def _ptr_ld(a, name: str, want_rows: int | None = None, writable=False):
 # ---------------------------------------------------------------------------
 # C-named entry points
 # ---------------------------------------------------------------------------
-def h2_build(points, q=3, leaf_size=64, eta=2.0, length=0.5, sigma=1e-2, precisions=("f32",), stream=None):
-    """Build the H² matrix of a point cloud; returns an opaque handle (int)."""
+def h2_build(points, q=3, leaf_size=64, eta=2.0, length=0.5, sigma=1e-2, precisions=("f32",), stream=None,
+             kernel="exp", kappa=1.0, delta=0.05):
+    """Build the H² matrix of a point cloud; returns an opaque handle (int).
+    kernel "exp": exp(-r/length); "helmholtz": exp(i·kappa·r)/(4π·sqrt(r² + delta²))
+    (complex; multiply with h2_matmul_complex)."""
     pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64))
     if pts.ndim != 2 or pts.shape[1] != 3:
         raise ValueError("points must be n×3")
     mask = 0
     for p in precisions:
         mask |= 1 << DTYPES[p]
-    bp = BuildParams(q, leaf_size, eta, length, sigma, mask, _stream_ptr(stream))
+    bp = BuildParams(q, leaf_size, eta, length, sigma, mask, _stream_ptr(stream), KERNELS[kernel], kappa, delta)
     h = C.c_void_p()
     _check(lib().h2_build(C.byref(bp), pts.ctypes.data, pts.shape[0], C.byref(h)), "h2_build")
     return h.value
@@ -254,6 +264,53 @@ def _mm(fn, where, handle, alpha, X, Y, dtype, stream):
 def h2_matmul(handle, alpha, X, Y, dtype="f64", stream=None):
     """Y += alpha·A·X (Y is updated in place and returned)."""
     return _mm(lib().h2_matmul, "h2_matmul", handle, alpha, X, Y, dtype, stream)
+
+
+def _ptr_ld_complex(a, name: str, want_rows: int, writable=False):
+    """(pointer, leading dimension in complex elements, m, keepalive) of a complex128 n×m block."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        if a.dtype != torch.complex128:
+            raise TypeError(f"{name} must be complex128")
+        if a.dim() == 1:
+            a = a.view(-1, 1)
+        if a.dim() != 2 or (a.shape[1] > 1 and a.stride(1) != 1):
+            raise ValueError(f"{name} must be 2-D with unit column stride")
+        if a.shape[0] != want_rows:
+            raise ValueError(f"{name} must have {want_rows} rows")
+        ld = a.stride(0) if a.shape[0] > 1 else a.shape[1]
+        return a.data_ptr(), int(ld), int(a.shape[1]), a
+    arr = np.asarray(a)
+    if arr.dtype != np.complex128:
+        raise TypeError(f"{name} must be complex128")
+    if arr.ndim == 1:
+        arr = arr.reshape(-1, 1)
+    if writable and not arr.flags.writeable:
+        raise ValueError(f"{name} must be writable")
+    if arr.strides[1] != 16 and arr.shape[1] > 1:
+        raise ValueError(f"{name} must have unit column stride")
+    if arr.shape[0] != want_rows:
+        raise ValueError(f"{name} must have {want_rows} rows")
+    ld = arr.strides[0] // 16 if arr.shape[0] > 1 else arr.shape[1]
+    return arr.ctypes.data, int(ld), int(arr.shape[1]), arr
+
+
+def h2_matmul_complex(handle, alpha, X, Y, dtype="f64", stream=None):
+    """Y += alpha·A·X over C for a matrix built with kernel="helmholtz"; X, Y complex128
+    (torch tensors on the device or host, or numpy arrays), alpha complex."""
+    n = h2_info(handle)["n"]
+    xp, ldx, m, kx = _ptr_ld_complex(X, "X", n)
+    yp, ldy, my, ky = _ptr_ld_complex(Y, "Y", n, writable=True)
+    if my != m:
+        raise ValueError("X and Y must have the same number of columns")
+    a = complex(alpha)
+    dt = PRODUCT_DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    _check(lib().h2_matmul_complex(handle, a.real, a.imag, xp, ldx, yp, ldy, m, dt, _stream_ptr(stream)),
+           "h2_matmul_complex")
+    return Y
 
 
 def h2_matmul_transposed(handle, alpha, X, Y, dtype="f64", stream=None):
@@ -539,8 +596,9 @@ class H2Matrix:
     """Owning wrapper around an h2_matrix handle."""
 
     def __init__(self, points, q=3, leaf_size=64, eta=2.0, length=0.5, sigma=1e-2, precisions=("f32",),
-                 stream=None):
-        self.handle = h2_build(points, q, leaf_size, eta, length, sigma, precisions, stream)
+                 stream=None, kernel="exp", kappa=1.0, delta=0.05):
+        self.handle = h2_build(points, q, leaf_size, eta, length, sigma, precisions, stream, kernel, kappa, delta)
+        self.kernel = kernel
         self.info = h2_info(self.handle)
         self.n = self.info["n"]
 
@@ -549,6 +607,9 @@ class H2Matrix:
 
     def matmul_transposed(self, X, Y, alpha=1.0, dtype="f64", stream=None):
         return h2_matmul_transposed(self.handle, alpha, X, Y, dtype, stream)
+
+    def matmul_complex(self, X, Y, alpha=1.0, dtype="f64", stream=None):
+        return h2_matmul_complex(self.handle, alpha, X, Y, dtype, stream)
 
     def block_cg(self, B, X, **kw) -> SolveResult:
         return h2_block_cg(self.handle, B, X, **kw)

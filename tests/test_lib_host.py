@@ -156,13 +156,19 @@ def test_matrix_entry_points_reject_bad_arguments_before_any_device_work(h2lib):
     gp = H.GMRESParams(1e-8, 100, 30, h2lib.H2_F64, h2lib.H2_PRECOND_NONE, 0, None)
     assert L.h2_block_gmres(None, x.ctypes.data, 2, x.ctypes.data, 2, 2, C.byref(gp), C.byref(res)) == BAD
     assert "null" in L.h2_last_error_string().decode()
+    assert L.h2_matmul_complex(None, 1.0, 0.0, x.ctypes.data, 1, x.ctypes.data, 1, 1, h2lib.H2_F64, None) == BAD
     pts = np.ascontiguousarray(sphere_points(50, 1))
     h = C.c_void_p()
     for params, code in ((H.BuildParams(3, 64, 0.0, 0.5, 0.0, 1, None), BAD),       # eta
                          (H.BuildParams(3, 64, 2.0, -1.0, 0.0, 1, None), BAD),      # length
                          (H.BuildParams(3, 64, 2.0, 0.5, np.nan, 1, None), BAD),    # sigma
                          (H.BuildParams(6, 64, 2.0, 0.5, 0.0, 1, None), UNSUP),     # q
-                         (H.BuildParams(3, 65, 2.0, 0.5, 0.0, 1, None), UNSUP)):    # leaf size
+                         (H.BuildParams(3, 65, 2.0, 0.5, 0.0, 1, None), UNSUP),     # leaf size
+                         (H.BuildParams(3, 64, 2.0, 0.5, 0.0, 1, None, 2, 1.0, 0.05), BAD),        # kernel
+                         (H.BuildParams(3, 64, 2.0, 0.5, 0.0, 1, None, 1, np.inf, 0.05), BAD),     # kappa
+                         (H.BuildParams(3, 64, 2.0, 0.5, 0.0, 1, None, 1, 1.0, 0.0), BAD),         # delta
+                         (H.BuildParams(3, 64, 2.0, 0.5, 0.0, 1 << h2lib.H2_BF16, None, 1, 1.0, 0.05),
+                          UNSUP)):                                                   # BF16 of a complex kernel
         assert L.h2_build(C.byref(params), pts.ctypes.data, 50, C.byref(h)) == code
         assert not h.value
     ok = H.BuildParams(3, 64, 2.0, 0.5, 0.0, 1, None)

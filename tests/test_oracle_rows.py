@@ -4,6 +4,7 @@ expansion and brute force; and of its coupling gradients against
 adjoint_grads."""
 import numpy as np
 
+from _helpers import rel_fro
 from oracle import h2_oracle as O
 from workloads import gaussian_rhs, sphere_points
 
@@ -42,3 +43,17 @@ def test_coupling_grads_equal_adjoint_grads():
     got = R.coupling_grads(L, X, pairs)
     for p in pairs:
         assert np.allclose(got[p], dS[p], rtol=1e-12, atol=1e-12 * np.abs(dS[p]).max())
+
+
+def test_rows_match_the_full_complex_product():
+    """K = C (the regularised Helmholtz kernel): complex rows, complex α."""
+    pts = sphere_points(1500, 4)
+    g = O.helmholtz_kernel(1.0, 0.05)
+    H = O.H2Matrix(pts, q=3, leaf_size=32, eta=2.0, kernel=g, sigma=1e-2)
+    R = O.H2Rows(pts, q=3, leaf_size=32, eta=2.0, sigma=1e-2, kernel=g)
+    X = gaussian_rhs(1500, 3, 8) + 1j * gaussian_rhs(1500, 3, 9)
+    rows = [0, 17, 640, 999, 1499]
+    full = O.h2mm(H, 0.3 - 0.2j, X)
+    got = R.rows(0.3 - 0.2j, X, rows)
+    assert np.iscomplexobj(got)
+    assert rel_fro(got, full[rows]) <= 1e-13
