@@ -423,6 +423,13 @@ def run_ours(args):
               "kernel_evaluations_per_step": int(info["n_adm"] * info["k"] * info["k"]),
               "s_bytes_not_read": int(info["n_adm"] * info["k"] * info["k"] * 4)}
 
+    # the complex product (K = C): the same points and tree with the Helmholtz kernel
+    # exp(i kappa r) / (4 pi sqrt(r^2 + delta^2)), m complex columns, FP64 and FP32 on
+    # the CUDA cores; the coupling kernel against the ALU peak of its precision
+    cx = None
+    if not args.no_complex and workload == WORKLOAD:
+        cx = complex_products(P, torch, dev, pts, cfg, rank, dist, clk, peaks)
+
     # roofline of the dominant kernel: the coupling phase (one launch per product)
     elt = 8 if dtype == "f64" else 4
     n_adm, nc = info["n_adm"], info["n_clusters"]
@@ -596,6 +603,7 @@ def run_ours(args):
                       "coupling_GBps": round(n_adm * info["k"] * info["k"] * 2 / (phasesbf["coupling"] * 1e-3) / 1e9, 1),
                       "phases_ms": {kk: round(v, 4) for kk, v in phasesbf.items()}},
         "h2mm_f32_matrix_free": mf,
+        "h2mm_complex": cx,
         "batch": batch,
         "roofline": roof,
         "roofline_product": roof_product,
@@ -612,6 +620,51 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+KAPPA, DELTA = 1.0, 0.05  # the Helmholtz kernel's wave number (the paper's) and regularisation length
+
+
+def complex_products(P, torch, dev, pts, cfg, rank, dist, clk, peaks) -> dict:
+    n, m = cfg["n"], cfg["m"]
+    G = P.H2Matrix(pts, q=cfg["q"], leaf_size=cfg["leaf"], eta=cfg["eta"], sigma=cfg["sigma"],
+                   precisions=("f32",), kernel="helmholtz", kappa=KAPPA, delta=DELTA)
+    info = G.info
+    X = torch.from_numpy(rank_rhs(n, m, cfg["rhs_seed"], rank) + 1j * rank_rhs(n, m, cfg["rhs_seed"] + 1, rank)).to(dev)
+    Y = torch.zeros_like(X)
+    flops = G.flops(m)
+    coup_flops = 8.0 * info["n_adm"] * info["k"] ** 2 * m
+    clock_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    out = {"kernel": f"exp(i*{KAPPA}*r)/(4*pi*sqrt(r^2+{DELTA}^2)), sigma={cfg['sigma']}", "m_complex": m,
+           "gflop_per_step": round(flops / 1e9, 4)}
+    stream = torch.cuda.current_stream()
+    for dt, steps in (("f64", 5), ("f32", 10)):
+        for _ in range(3):
+            G.matmul_complex(X, Y, dtype=dt)
+        P.h2_timing_query(G.handle, reset=True)
+        P.h2_timing_enable(G.handle, True)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            G.matmul_complex(X, Y, dtype=dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev)
+        P.h2_timing_enable(G.handle, False)
+        ph, calls = P.h2_timing_query(G.handle, reset=True)
+        cms = ph["coupling_kernel"] / max(calls, 1)
+        peak = FP64_NOMINAL_TFLOPS if dt == "f64" else SM_COUNT * FP32_FMA_PER_CLK_SM * 2 * clock_mhz * 1e6 / 1e12
+        ach = coup_flops / (cms * 1e-3) / 1e12
+        out[dt] = {"value": round(flops / (ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s", "ms_per_step": round(ms, 4),
+                   "steps": steps,
+                   "coupling_kernel": {"ms": round(cms, 4), "bound": "alu", "achieved_TFLOPs": round(ach, 3),
+                                       "peak_TFLOPs": round(peak, 2), "frac": round(ach / peak, 4),
+                                       "kernel": "k_coupling_c"}}
+    G.close()
+    return out
 
 
 def batch_products(P, torch, dev, steps: int, dist=None) -> dict:
@@ -765,6 +818,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-system batched product in the bench line")
+    ap.add_argument("--no-complex", action="store_true", help="skip the complex (Helmholtz kernel) product")
     ap.add_argument("--solve-max-iter", type=int, default=8000)
     ap.add_argument("--workload", choices=sorted(CONFIGS), default=WORKLOAD,
                     help="workload of the bench line (default: the precision workload, n = 65536)")

@@ -379,10 +379,13 @@ int h2_batch_block_cg(h2_batch* batch, const double* const* B, const int64_t* ld
  *      (path 1), tensor cores with the tensor-core transfer passes (Alg.
  *      "forward/backward" as work lists in dependency order: one launch per
  *      phase, path 2, or sharing the coupling's and the leaf phase's launches,
- *      path 3; FP32 only), CUDA cores only (path 4; FP32 only);
+ *      path 3; FP32 only), CUDA cores only (path 4; FP32 only), and tensor
+ *      cores with the CUDA-core subtree passes stopping at the upward cut,
+ *      whose clusters above the cut become transfer items of the coupling
+ *      launch (path 5; FP32 only);
  *   2. on the best path, the pipeline stage count of the tensor-core kernels
  *      (4 and 5 against as many as fit);
- *   3. on path 1, the cut targets of the CUDA-core subtree passes (the task
+ *   3. on paths 1 and 5, the cut targets of the CUDA-core subtree passes (the task
  *      counts that the upward and the downward schedules aim at: half and
  *      twice the default, upward first).
  * The fastest variant is kept for later products of this precision whose
@@ -392,7 +395,7 @@ int h2_batch_block_cg(h2_batch* batch, const double* const* B, const int64_t* ld
  * (H2_E_BADARG).  out (optional) receives the candidates and the choice. */
 typedef struct h2_tune_result {
     int32_t dtype, m;
-    int32_t path;          /* chosen path (1..4, as above)                          */
+    int32_t path;          /* chosen path (1..5, as above)                          */
     int32_t stages;        /* chosen stage count (0: as many as fit)                */
     int32_t up_target;     /* chosen cut targets of the CUDA-core transfer passes   */
     int32_t down_target;

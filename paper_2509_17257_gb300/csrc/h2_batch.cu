@@ -370,9 +370,10 @@ int h2_autotune_ex(h2_matrix* A, int64_t m, int32_t dtype, void* stream, h2_tune
     const int cls = column_class(mc);
     const int di = dtype == H2_BF16 ? 1 : 0;
     const Tune keep = A->tune[di][cls];
-    const int keep_flow = A->use_flow;
+    const int keep_flow = A->use_flow, keep_hybrid = A->use_hybrid;
     const int keep_up = A->up_target, keep_down = A->down_target;
     A->use_flow = -1;  // the candidates set the path themselves
+    A->use_hybrid = -1;
     double* buf = nullptr;
     H2_CUDA_TRY(cudaMallocAsync((void**)&buf, 2 * (size_t)A->n * m * sizeof(double), st));
     H2_CUDA_TRY(cudaMemsetAsync(buf, 0, 2 * (size_t)A->n * m * sizeof(double), st));
@@ -409,13 +410,14 @@ int h2_autotune_ex(h2_matrix* A, int64_t m, int32_t dtype, void* stream, h2_tune
         trial(Tune{kPathTcFlow, 0}, keep_up, keep_down);
         trial(Tune{kPathTcFused, 0}, keep_up, keep_down);
     }
+    if (dtype == H2_F32 && A->tc.hybrid) trial(Tune{kPathTcHybrid, 0}, keep_up, keep_down);
     if (dtype == H2_F32) trial(Tune{kPathSimt, 0}, keep_up, keep_down);
     // 2. the stage count of the tensor-core kernels on the best path
     if (!rc && best_t.path != kPathSimt)
         for (int sc : {4, 5}) trial(Tune{best_t.path, (int8_t)sc}, best_up, best_down);
     // 3. the cut of the CUDA-core subtree passes, upward then downward
     const bool subtree = A->f32.Et && A->k % 8 == 0 && A->k <= 64 && mc % 4 == 0 && A->T.leaf_size <= 64;
-    if (!rc && best_t.path == kPathTcOwn && subtree) {
+    if (!rc && (best_t.path == kPathTcOwn || best_t.path == kPathTcHybrid) && subtree) {
         const int up0 = best_up;
         for (int u : {kUpTasks / 2, kUpTasks * 2}) trial(best_t, u, best_down);
         (void)up0;
@@ -426,6 +428,7 @@ int h2_autotune_ex(h2_matrix* A, int64_t m, int32_t dtype, void* stream, h2_tune
     cudaFreeAsync(buf, st);
     cudaStreamSynchronize(st);
     A->use_flow = keep_flow;
+    A->use_hybrid = keep_hybrid;
     if (rc) {
         A->tune[di][cls] = keep;
         set_transfer_targets(A, keep_up, keep_down, st);

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -338,12 +339,13 @@ void down_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, st
 // level with at least `target` tasks whose step lists fit kUpMaxSteps and
 // whose stacks fit kUpMaxEntries.
 void up_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std::vector<UpStep>& steps,
-                 int32_t& ntasks, int32_t& entries) {
+                 int32_t& ntasks, int32_t& entries, int32_t* cut_level) {
     const int64_t nc = T.n_clusters();
     task_ptr.assign(1, 0);
     steps.clear();
     ntasks = 0;
     entries = 3;
+    if (cut_level) *cut_level = 0;
     if (nc < 1) return;
     std::vector<int64_t> nsub(nc, 1);
     for (int64_t c = nc - 1; c >= 1; --c) nsub[T.parent[c]] += nsub[c];
@@ -409,6 +411,7 @@ void up_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std:
             }
         if ((count >= target || l == T.depth) && size <= kUpMaxSteps && ent <= kUpMaxEntries) { Lu = l; break; }
     }
+    if (cut_level) *cut_level = Lu;
     std::vector<std::vector<UpStep>> task_steps;
     for (int64_t c = 0; c < nc; ++c)
         if (T.level[c] == Lu || (T.level[c] < Lu && T.is_leaf((int32_t)c))) {
@@ -554,7 +557,7 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
         UP(A->d_dn_task_ptr, task_ptr);
         UP(A->d_dn_steps, dsteps);
         std::vector<UpStep> usteps;
-        up_schedule(T, A->up_target, task_ptr, usteps, A->up_ntasks, A->up_entries);
+        up_schedule(T, A->up_target, task_ptr, usteps, A->up_ntasks, A->up_entries, &A->up_cut);
         UP(A->d_up_task_ptr, task_ptr);
         UP(A->d_up_steps, usteps);
     }
@@ -848,6 +851,117 @@ int flow_lists(h2_matrix* A, const FlowTiles& ft, const std::vector<int64_t>& s_
     return 0;
 }
 
+// The coupling launch of the hybrid upward pass (k_tc_gemm<4, 1>).  The CUDA-core
+// subtree pass (k_up_own without its climb) computes every cluster at or below
+// the cut level up_cut (and the leaves above it); the clusters above the cut,
+// x̂_t = E_s0ᵀ x̂_s0 + E_s1ᵀ x̂_s1 (Alg. "forward/backward"), become transfer items
+// of the coupling launch, each writing its split tile and ready flag.  A term
+// whose source is above the cut waits for that flag: a transfer item for its
+// sons, a coupling item for its source cluster.  Keys order the list so that
+// every wait points to a strictly smaller key (each CTA takes its items in list
+// order, so the item with the smallest unfinished key can always proceed):
+//   transfer item at height h above the cut (h = 1 for fathers of task roots): 2h - 1;
+//   coupling item reading only clusters at or below the cut: key 2r for the
+//     rounds r < H between two heights, the smallest items first and about
+//     kHybridRoundTerms terms per CTA per round (the time a transfer item takes
+//     to become readable), the rest key 2H;
+//   coupling item reading a cluster above the cut: key 2H too if its highest
+//     source is at height H - 3 or below, else 2H + 1.
+// Each of the last two groups is dealt largest first.  The transfer items thus
+// run early, a few microseconds apart, and the coupling items that read them
+// come with the bulk of the coupling work, those reading the top of the tree
+// last.
+constexpr int kHybridRoundTerms = 16;  // H2_HYBRID_ROUND_TERMS overrides it (1..64)
+// The product takes the hybrid upward pass by default when the coupling work
+// that reads no cluster above the cut gives every CTA at least this many terms
+// per height above the cut: then the chain of transfer items (a few
+// microseconds per height) runs under that work instead of after it.
+constexpr int kHybridTermsPerHeight = 12;
+
+int hybrid_lists(h2_matrix* A, cudaStream_t st) {
+    TcData& D = A->tc;
+    const Tree& T = A->T;
+    const int KP = D.KP, NP = D.NP;
+    const int64_t nc = A->nc;
+    D.hybrid = false;
+    D.h_default = false;
+    if (!D.flow || D.s_off_host.size() != (size_t)A->n_adm || D.et_off_host.size() != (size_t)nc) return 0;
+    // height above the cut: 0 for clusters at or below it and for leaves above it
+    std::vector<int32_t> h(nc, 0);
+    int32_t H = 0;
+    for (int64_t c = nc - 1; c >= 0; --c)  // pre-order: sons follow their father
+        if (!T.is_leaf((int32_t)c) && T.level[c] < A->up_cut) {
+            h[c] = 1 + std::max(h[T.son0[c]], h[T.son1[c]]);
+            H = std::max(H, h[c]);
+        }
+    const int16_t kWait = (int16_t)(0 | kTermWait);
+    auto np_role = [](int np, int32_t role) { return (int32_t)(np | (role << 16)); };
+    std::vector<TcTerm> terms;
+    std::vector<KeyedItem> keyed;
+    for (int64_t c = 0; c < nc; ++c) {
+        if (h[c] == 0) continue;
+        const int32_t e0 = (int32_t)terms.size();
+        for (int32_t s : {T.son0[c], T.son1[c]})
+            terms.push_back(TcTerm{D.et_off_host[s], (int32_t)((int64_t)s * KP), (int16_t)KP,
+                                   h[s] > 0 ? kWait : (int16_t)0});
+        keyed.push_back(KeyedItem{2 * h[c] - 1, TcItem{(int32_t)c, e0, (int32_t)terms.size(), np_role(NP, kRoleTransfer)}});
+    }
+    struct Free {
+        int64_t cost;
+        TcItem it;
+        int32_t hs;  // largest height above the cut among the sources
+    };
+    std::vector<Free> free_items, late;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int64_t j0 = T.adm_rowptr[c], j1 = T.adm_rowptr[c + 1];
+        if (j1 == j0) continue;
+        const int32_t e0 = (int32_t)terms.size();
+        int32_t hs = 0;
+        for (int64_t j = j0; j < j1; ++j) {
+            const int32_t sc = T.adm_col[j];
+            hs = std::max(hs, h[sc]);
+            terms.push_back(TcTerm{D.s_off_host[j], (int32_t)((int64_t)sc * KP), (int16_t)KP,
+                                   h[sc] > 0 ? kWait : (int16_t)0});
+        }
+        const TcItem it{(int32_t)c, e0, (int32_t)terms.size(), np_role(NP, 0)};
+        if (hs > 0) late.push_back(Free{j1 - j0, it, hs});
+        else free_items.push_back(Free{j1 - j0, it, 0});
+    }
+    // smallest first into the rounds, each round up to kHybridRoundTerms terms per CTA
+    std::stable_sort(free_items.begin(), free_items.end(), [](const Free& a, const Free& b) { return a.cost < b.cost; });
+    int round_terms = kHybridRoundTerms;
+    if (const char* e = getenv("H2_HYBRID_ROUND_TERMS")) round_terms = std::min(64, std::max(1, atoi(e)));
+    const int64_t budget = (int64_t)round_terms * kTcGrid;
+    size_t i = 0;
+    for (int32_t r = 0; r < H; ++r) {
+        int64_t used = 0;
+        while (i < free_items.size() && used + free_items[i].cost <= budget) {
+            used += free_items[i].cost;
+            keyed.push_back(KeyedItem{2 * r, free_items[i++].it});
+        }
+    }
+    // the rest, and the coupling items that read clusters above the cut: largest
+    // first (snake-dealt within the key)
+    std::vector<Free> rest(free_items.begin() + (long)i, free_items.end());
+    rest.insert(rest.end(), late.begin(), late.end());
+    std::stable_sort(rest.begin(), rest.end(), [](const Free& a, const Free& b) { return a.cost > b.cost; });
+    for (const Free& f : rest) keyed.push_back(KeyedItem{f.hs > H - 3 ? 2 * H + 1 : 2 * H, f.it});
+    std::vector<TcItem> items;
+    order_by_key(keyed, items);
+    release_allocation(A, D.h_items);
+    release_allocation(A, D.h_terms);
+    D.h_items = nullptr;
+    D.h_terms = nullptr;
+    int rc = 0;
+    if ((rc = upload(A, &D.h_items, items, st)) || (rc = upload(A, &D.h_terms, terms, st))) return rc;
+    D.h_nitems = (int)items.size();
+    D.hybrid = true;
+    int64_t free_terms = 0;
+    for (const Free& f : free_items) free_terms += f.cost;
+    D.h_default = free_terms >= (int64_t)kHybridTermsPerHeight * H * kTcGrid;
+    return 0;
+}
+
 // Core-matrix copies of S, V and G for the tensor cores (BF16 and/or FP32 for
 // the split-TF32 product), and the schedules of the two tcgen05 kernels
 // (coupling over row clusters, leaf phase over row leaves).
@@ -986,7 +1100,12 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     std::stable_sort(l_items.begin(), l_items.end(),
                      [&](const TcItem& a, const TcItem& b) { return l_cost[a.id] > l_cost[b.id]; });
     snake_order(l_items, kTcGrid);
-    if (flow && (rc = flow_lists(A, ft, s_off, v_off, g_off, xkoff, st))) return rc;
+    if (flow) {
+        if ((rc = flow_lists(A, ft, s_off, v_off, g_off, xkoff, st))) return rc;
+        D.s_off_host = s_off;
+        D.et_off_host = ft.et_off;
+        if ((rc = hybrid_lists(A, st))) return rc;
+    }
     D.xk_total = xkoff[NL];
     D.c_nitems = (int)c_items.size();
     D.c_nzero = (int)c_zero.size();
@@ -1144,7 +1263,8 @@ int set_transfer_targets(h2_matrix* A, int up_target, int down_target, cudaStrea
     std::vector<UpStep> usteps;
     int32_t dn_ntasks = 0, dn_entries = 0, up_ntasks = 0, up_entries = 0;
     down_schedule(A->T, down_target, dptr, dsteps, dn_ntasks, dn_entries);
-    up_schedule(A->T, up_target, uptr, usteps, up_ntasks, up_entries);
+    int32_t up_cut = 0;
+    up_schedule(A->T, up_target, uptr, usteps, up_ntasks, up_entries, &up_cut);
     if (up_entries > kUpMaxEntries || dn_entries > 8) {
         set_error("transfer-pass schedule needs more stack entries than the kernels hold");
         return H2_E_UNSUPPORTED;
@@ -1171,6 +1291,9 @@ int set_transfer_targets(h2_matrix* A, int up_target, int down_target, cudaStrea
     A->up_entries = up_entries;
     A->up_target = up_target;
     A->down_target = down_target;
+    const bool cut_moved = up_cut != A->up_cut;
+    A->up_cut = up_cut;
+    if (cut_moved && A->tc.flow) return hybrid_lists(A, st);
     return 0;
 }
 

@@ -213,6 +213,15 @@ struct TcData {
     // launches that serve several matrices (h2_batch_matmul)
     std::vector<int32_t> f1_keys, f2_keys;
     std::vector<TcItem> f1_host, f2_host;
+    // the coupling launch that also computes the clusters above the CUDA-core
+    // upward pass's cut (k_tc_gemm<4, 1>; rebuilt with the cut): transfer items
+    // for those clusters interleaved with the coupling items (hybrid_lists)
+    bool hybrid = false;
+    bool h_default = false;  // the built-in rule takes it (enough coupling work to hide the chain)
+    TcItem* h_items = nullptr;
+    TcTerm* h_terms = nullptr;
+    int h_nitems = 0;
+    std::vector<int64_t> s_off_host, et_off_host;  // tile offsets of S_j and of Eᵀ_c in mat32 (elements)
 };
 
 // Inter-CTA bookkeeping of the one-launch transfer passes: arrival counters of
@@ -252,7 +261,8 @@ struct Tree;
 void down_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std::vector<DownStep>& steps,
                    int32_t& ntasks, int32_t& entries);
 void up_schedule(const Tree& T, int target, std::vector<int32_t>& task_ptr, std::vector<UpStep>& steps,
-                 int32_t& ntasks, int32_t& entries);
+                 int32_t& ntasks, int32_t& entries,
+                 int32_t* cut_level = nullptr);
 
 // Product variants the autotuner chooses among (h2_autotune).
 enum ProductPath : int8_t {
@@ -261,7 +271,9 @@ enum ProductPath : int8_t {
     kPathTcOwn = 1,    // tensor cores, CUDA-core transfer passes
     kPathTcFlow = 2,   // tensor cores, tensor-core transfer passes, one launch per phase
     kPathTcFused = 3,  // tensor cores, transfer passes sharing launches with coupling and leaf phases
-    kPathSimt = 4      // CUDA cores only (FP32)
+    kPathSimt = 4,     // CUDA cores only (FP32)
+    kPathTcHybrid = 5  // tensor cores, CUDA-core subtree passes below the cut, the clusters above
+                       // the upward cut as transfer items of the coupling launch
 };
 struct Tune {
     int8_t path = kPathDefault;
@@ -372,6 +384,9 @@ struct h2_matrix {
     // (columns per 64-column chunk: <= 8, <= 16, <= 32, <= 64)
     h2::Tune tune[2][4];
     int32_t up_target = h2::kUpTasks, down_target = h2::kDownTasks;  // transfer-pass cut targets
+    int32_t up_cut = 0;  // level of the upward pass's task roots (leaves above it are tasks too)
+    // H2_TC_HYBRID at build: 1 / 0 force the hybrid upward pass on / off (unset: tuning or default)
+    int use_hybrid = -1;
     bool s_replaced = false;  // h2_coupling_set was called: S_b are no longer g's values  // H2_FORCE_SIMT=1 at build: FP32 product on the CUDA cores only
     // block-Jacobi preconditioner (h2_precond.cu): (G_(t,t) + σI)⁻¹ per leaf, built on first use
     double* bj_inv = nullptr;     // concatenated n_t×n_t inverses, leaf order
@@ -532,6 +547,8 @@ int product_prepare(h2_matrix* A, int64_t m, int32_t dtype, cudaStream_t st);
 int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st, int stages = 0);
 // Rebuild the subtree schedules of the CUDA-core transfer passes for other cut targets.
 int set_transfer_targets(h2_matrix* A, int up_target, int down_target, cudaStream_t st);
+// Work list of the coupling launch with the clusters above the upward cut (TcData::h_*).
+int hybrid_lists(h2_matrix* A, cudaStream_t st);
 int launch_pack_tiles(const TcPackTile* tiles, int64_t count, const double* src, uint8_t* dst, int es,
                       cudaStream_t st);
 int launch_pack_act(const float* src, int64_t ld, int ids, const int32_t* idmap, const int32_t* base,

@@ -589,8 +589,10 @@ __device__ __forceinline__ void pack_points(const PackOut& pk, uint8_t* tile, in
 // reset by the last arriver), adding the two brothers' contributions E_sᵀ x̂_s,
 // which each brother computes and publishes before the atomic.  One IEEE
 // addition of two contributions does not depend on their order, so the result
-// does not depend on which brother arrives last.  64·CN threads, thread
-// (tx, ty) owns rows 4ty.. and columns 4tx.. of the k×m result.
+// does not depend on which brother arrives last.  With climb = 0 a CTA stops
+// at its task's root: the clusters above the cut are then items of the
+// coupling launch (k_tc_gemm<4, 1>).  64·CN threads, thread (tx, ty) owns rows
+// 4ty.. and columns 4tx.. of the k×m result.
 template <int CN>
 __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ task_ptr, int ntasks,
                                                     const UpStep* __restrict__ steps,
@@ -602,7 +604,7 @@ __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ 
                                                     const float* __restrict__ E, const float* __restrict__ Xp,
                                                     float* xhat, float* part, unsigned* __restrict__ cnt,
                                                     unsigned* __restrict__ claim, int* __restrict__ err, int nent, int k,
-                                                    int m, PackOut pk) {
+                                                    int m, PackOut pk, int climb) {
     constexpr int NT = 16 * CN;
     extern __shared__ __align__(16) float fsm[];
     float* sbuf = fsm;                 // [2 slots][2][64·64]  V_c and X|_ĉ, or E_s0 and E_s1
@@ -703,6 +705,7 @@ __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ 
             __syncthreads();
         }
         if (failed || cur < 0) break;
+        if (!climb) continue;
         // ---- climb above the cut ----
         // Every CTA publishes its cluster's contribution P_c = E_cᵀ x̂_c to the father
         // (in `part`, the ŷ buffer, unused until the coupling phase) before the
@@ -1199,10 +1202,17 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         const int stg = tn.stages;
         const bool fast = A->f32.Et && k % 8 == 0 && k <= 64 && mc % 4 == 0 && A->T.leaf_size <= 64;
         bool want_flow = !fast;
-        if (tn.path == kPathTcOwn) want_flow = false;
+        if (tn.path == kPathTcOwn || tn.path == kPathTcHybrid) want_flow = false;
         if (tn.path == kPathTcFlow || tn.path == kPathTcFused) want_flow = true;
         if (A->use_flow >= 0) want_flow = A->use_flow == 1;
-        const bool flow = kind == 1 && D.flow && want_flow && !stream_capture_active(st);
+        const bool capturing = stream_capture_active(st);
+        const bool flow = kind == 1 && D.flow && want_flow && !capturing;
+        // hybrid: the subtree passes stop at the upward cut, and the clusters above it
+        // are transfer items of the coupling launch (k_tc_gemm<4, 1>), which waits for
+        // them only where a coupling reads them
+        bool want_hybrid = tn.path == kPathTcHybrid || (tn.path == kPathDefault && D.h_default);
+        if (A->use_hybrid >= 0) want_hybrid = A->use_hybrid == 1;
+        const bool hybrid = kind == 1 && fast && !flow && !trans && !mf && D.hybrid && want_hybrid && !capturing;
         int rc = ensure_workspace(A, bXp + 2 * bC + bXcm + 3 * bAct, st);
         if (rc) return rc;
         char* base = (char*)A->ws.base;
@@ -1350,9 +1360,10 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
             const unsigned g = (unsigned)std::min(A->up_ntasks, 152 * std::max(1, (227 * 1024) / (usm + 2048)));
             H2_CUDA_TRY(cudaMemsetAsync(sbc.cnt, 0, (size_t)nc * sizeof(unsigned), st));
             H2_CUDA_TRY(cudaMemsetAsync(sbc.claim, 0, sizeof(unsigned), st));
-            if (fcn == 1) k_up_own<1><<<g, 64, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, yhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk);
-            else if (fcn == 2) k_up_own<2><<<g, 128, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, yhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk);
-            else k_up_own<4><<<g, 256, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, yhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk);
+            const int climb = hybrid ? 0 : 1;
+            if (fcn == 1) k_up_own<1><<<g, 64, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, yhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk, climb);
+            else if (fcn == 2) k_up_own<2><<<g, 128, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, yhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk, climb);
+            else k_up_own<4><<<g, 256, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, yhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk, climb);
             H2_LAUNCH_CHECK();
             marks.mark();
             marks.mark();
@@ -1384,8 +1395,18 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         cp.nodes = D.nodes4;
         cp.inv_len = (float)(1.0 / A->length);
         cp.KP = KP;
+        if (hybrid) {
+            cp.n_items = D.h_nitems;
+            cp.items = D.h_items;
+            cp.terms = D.h_terms;
+            cp.out_act = xcm;  // the transfer items' split tiles
+            cp.flag = sbc.fflag;
+            cp.epoch = 1;
+            H2_CUDA_TRY(cudaMemsetAsync(sbc.fflag, 0, (size_t)nc * sizeof(int), st));
+        }
         marks.kernel_begin();
-        if (cp.n_items > 0 && (rc = launch_tc_gemm(mf ? 2 : 0, kind, cp, std::min(cp.n_items, grid_cap), st, stg)))
+        if (cp.n_items > 0 &&
+            (rc = launch_tc_gemm(hybrid ? 4 : (mf ? 2 : 0), kind, cp, std::min(cp.n_items, grid_cap), st, stg)))
             return rc;
         marks.kernel_end();
         marks.mark();

@@ -287,11 +287,15 @@ __global__ void k_pack_act(const float* __restrict__ src, int64_t ld, int ids, c
 // one per cluster) put their result, split, into the cluster's activation tile
 // and release it with a ready flag; coupling items write split tiles; leaf items
 // write rows of Z.  A term marked kTermWait waits (bounded) for the ready flag
-// of the tile it reads before its copy.
+// of the tile it reads before its copy.  MODE 4 (KIND 1 only): such a list for
+// one system, whose role-0 items write rows of ŷ like MODE 0: the coupling
+// launch that also computes the clusters above the upward pass's cut (their
+// transfer items wait for their sons and release their own tiles).
 template <int MODE, int KIND>
 __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmParams p) {
     constexpr bool MF = MODE == 2;
     constexpr bool FLOW = MODE == 3;
+    constexpr bool LIST = MODE == 3 || MODE == 4;  // items carry roles, terms may wait for ready flags
     // the coupling writes its result as split tiles when the downward pass runs on
     // the tensor cores (p.out_act set)
     const bool COUP_SPLIT = (MODE == 0 || MODE == 2) && p.out_act != nullptr;
@@ -394,12 +398,12 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 // for all), and lane 0 issues a term's copies once its bit is set.
                 uint32_t ready_mask = 0xffffffffu;
                 const int* my_flag = nullptr;
-                if (FLOW) {
+                if (LIST) {
                     if (lane < cnt && (t.asrc & kTermWait)) my_flag = PSYS(cur, flag) + t.akoff / PSYS(cur, KP);
                     ready_mask = __ballot_sync(0xffffffffu, !my_flag || flag_acquire(my_flag) == p.epoch);
                     __syncwarp();
                 }
-                const uint64_t t_batch = FLOW ? global_ns() : 0;
+                const uint64_t t_batch = LIST ? global_ns() : 0;
                 for (int j = 0; j < cnt; ++j) {
                     const int kpj = __shfl_sync(0xffffffffu, (int)t.kp, j);
                     const int asj = __shfl_sync(0xffffffffu, (int)t.asrc, j);
@@ -407,7 +411,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                     const int akj = __shfl_sync(0xffffffffu, t.akoff, j);
                     const int64_t aj = (int64_t)akj * Ri * ES;
                     bool ready = true;
-                    if (FLOW && !((ready_mask >> j) & 1u)) {
+                    if (LIST && !((ready_mask >> j) & 1u)) {
                         // poll again (bounded: gives up after about one second)
                         while (true) {
                             __nanosleep(32);
@@ -423,7 +427,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                     int bad = 0;
                     if (lane == 0) {
                         // the flags acquired by the warp order the tiles' writes before this copy
-                        if (FLOW && (asj & kTermWait)) fence_proxy_async_global();
+                        if (LIST && (asj & kTermWait)) fence_proxy_async_global();
                         if (!ready || !mbar_wait(&empty_bar[stage], phase ^ 1)) {
                             bad = 1;
                         } else {
@@ -617,7 +621,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
         float* xch = reinterpret_cast<float*>(smem + nst * stage_bytes);  // [2][64 i][64 n]
         int it = 0, par = 0;
         // rows of Z: the leaf phase, and the leaf items of a transfer-pass launch
-        auto leaf_rows = [&](const TcItem& t) { return MODE == 1 || (FLOW && item_role(t) == kRoleLeaf); };
+        auto leaf_rows = [&](const TcItem& t) { return MODE == 1 || (LIST && item_role(t) == kRoleLeaf); };
         TcItem cur = blockIdx.x < p.n_items ? p.items[blockIdx.x] : TcItem{-1, 0, 0, 0};
         // an item's system: its sizes and buffers (SYSF reads a field of the system
         // table of a multi-system launch, else of the launch's own arguments)
@@ -641,8 +645,9 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                       ldci = SYSF(cur, ldc);
             const bool wide = Ri > 64;
             const bool vec4 = (mci & 3) == 0 && (ldci & 3) == 0;
-            const int role = FLOW ? item_role(cur) : 0;
-            const bool split_out = COUP_SPLIT || (FLOW && role != kRoleLeaf);
+            const int role = LIST ? item_role(cur) : 0;
+            // role 0 (MODE 4's coupling items): rows of ŷ, as in MODE 0
+            const bool split_out = COUP_SPLIT || (LIST && role != kRoleLeaf && role != 0);
             float sum[kAccCols];
 #pragma unroll
             for (int j = 0; j < kAccCols; ++j) sum[j] = 0.f;
@@ -742,7 +747,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                     }
                 }
                 // the tile is in global memory: release it to the CTAs that wait for it
-                if (FLOW && role == kRoleTransfer && q == 0 && lane == 0) {
+                if (LIST && role == kRoleTransfer && q == 0 && lane == 0) {
                     fence_proxy_async_global();
                     flag_release(SYSF(cur, flag) + id, p.epoch);
                 }
@@ -1030,6 +1035,7 @@ int tc_prepare() {
     H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     g_tc_attr_device = dev;
     return 0;
 }
@@ -1058,6 +1064,10 @@ int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st
         // its CTAs wait on each other's ready flags: one CTA per SM, at most one per SM
         // of the device, so that every CTA is resident (the waits are bounded in any case)
         return launch_one<3, 1>(p, grid, smem, st);
+    }
+    if (mode == 4) {
+        if (kind != 1) { set_error("the coupling launch with transfer items runs on the TF32 path only"); return H2_E_UNSUPPORTED; }
+        return launch_one<4, 1>(p, grid, smem, st);  // waits on flags too: one CTA per SM, every CTA resident
     }
     if (mode == 0 && kind == 0) return launch_one<0, 0>(p, grid, smem, st);
     if (mode == 1 && kind == 0) return launch_one<1, 0>(p, grid, smem, st);

@@ -93,7 +93,8 @@ class TuneResult(C.Structure):
 
 #: product paths of h2_autotune_ex
 TUNE_PATHS = {1: "tensor cores, CUDA-core transfer passes", 2: "tensor cores, tensor-core transfer passes",
-              3: "tensor cores, transfer passes fused with coupling and leaf phases", 4: "CUDA cores"}
+              3: "tensor cores, transfer passes fused with coupling and leaf phases", 4: "CUDA cores",
+              5: "tensor cores, CUDA-core subtree passes, clusters above the upward cut in the coupling launch"}
 
 
 class TreeView(C.Structure):
