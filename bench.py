@@ -42,17 +42,20 @@ FALLBACK_HBM_GBS = 6800.0
 SM_COUNT = 152
 FP32_FMA_PER_CLK_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_tc_gemm<0,1> launch (the FP32
-# coupling kernel) on precision_n65536, with the SHA-256 (first 16 hex digits) of the kernel's
-# sources when the counters were taken.  The line reports the bytes only while the sources
-# still hash to that value; after a change to the kernel they are stale and `traffic` is null.
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP32 coupling kernel
+# on precision_n65536 (k_tc_gemm<4,1>: the coupling with the transfer items above the upward
+# cut), with the SHA-256 (first 16 hex digits) of the kernel's sources and of the work-list
+# builder when the counters were taken.  The line reports the bytes only while the sources
+# still hash to that value; after a change they are stale and `traffic` is null.
 TC_F32_COUPLING_DRAM = {
-    "bytes": 754010112,  # 733.855 MB read + 20.155 MB written
+    "kernel": "k_tc_gemm<4,1>",
+    "bytes": 770685696,  # 738.204 MB read + 32.482 MB written
     "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-               "--clock-control none --kernel-name-base demangled -k regex:k_tc_gemm<(int)0, (int)1> -c 1 "
-               "python bench.py --steps 2 --warmup 1 --no-solve --no-cpu-baseline --no-batch",
-    "sources": ("paper_2509_17257_gb300/csrc/h2_tc.cu", "paper_2509_17257_gb300/csrc/h2_async.cuh"),
-    "source_sha16": "3e70e236f81751ca",
+               "--clock-control none --kernel-name-base demangled -k regex:k_tc_gemm<(int)4, (int)1> -c 1 "
+               "python bench.py --steps 2 --warmup 1 --no-solve --no-cpu-baseline --no-batch --no-complex",
+    "sources": ("paper_2509_17257_gb300/csrc/h2_tc.cu", "paper_2509_17257_gb300/csrc/h2_async.cuh",
+                "paper_2509_17257_gb300/csrc/h2_build.cu"),
+    "source_sha16": "dac5d48c3df4ca45",
 }
 
 
@@ -108,14 +111,16 @@ def product_bytes(n, k, m, nc, n_adm, nnz_near, elt, elt_x=8, elt_acc=4):
             + 4 * nc * k * m * elt_acc)
 
 
-def phase_bytes(n, k, m, nc, n_leaves, n_adm, nnz_near, elt):
+def phase_bytes(n, k, m, nc, n_leaves, n_adm, nnz_near, elt, n_above=0):
     """Algorithmic bytes of each phase of the tensor-core FP32/BF16 product, as timed by
-    h2_timing (coefficients, gathered X and leaf results in FP32; the caller's X, Y in FP64)."""
+    h2_timing (coefficients, gathered X and leaf results in FP32; the caller's X, Y in FP64).
+    n_above: clusters above the upward cut computed in the coupling launch (hybrid)."""
     a = 4  # coefficient / gathered-block element size
     return {
         "gather": 8 * n * m + a * n * m,
-        "leaf_fwd": elt * (n * k + (nc - 1) * k * k) + a * n * m + a * nc * k * m,  # upward pass fused in
-        "coupling": elt * n_adm * k * k + 2 * a * nc * k * m,
+        "leaf_fwd": (elt * (n * k + (nc - 1 - 2 * n_above) * k * k) + a * n * m
+                     + a * (nc - n_above) * k * m),  # upward pass fused in
+        "coupling": elt * (n_adm + 2 * n_above) * k * k + 2 * a * nc * k * m + a * n_above * k * m,
         "down": elt * (nc - 1) * k * k + 2 * a * nc * k * m,
         "leaf_bwd_near": (elt * (n * k + nnz_near) + a * n_leaves * k * m + 2 * a * n * m
                           + a * n * m + 8 * n * m + 2 * 8 * n * m),  # leaf kernel, then the scatter into Y
@@ -435,6 +440,12 @@ def run_ours(args):
     n_adm, nc = info["n_adm"], info["n_clusters"]
     coup_bytes = elt * (n_adm * k * k + 2 * nc * k * m)
     coup_flops = 2.0 * n_adm * k * k * m
+    # the FP32 tensor-core product's coupling launch also computes the clusters above the
+    # upward cut (hybrid): two Eᵀ per cluster read, its x̂ written, 2·2k²m flops
+    hybrid = dtype == "f32" and info["launches_tc"] > 0 and info["hybrid"] == 1
+    n_above = int(info["n_above_cut"]) if hybrid else 0
+    coup_bytes += elt * (2 * n_above * k * k + n_above * k * m)
+    coup_flops += 4.0 * n_above * k * k * m
     # the coupling kernel's own launch (events around it alone; the phase also packs x̂)
     coup_ms = phases.get("coupling_kernel") or phases["coupling"]
     clock_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
@@ -463,11 +474,13 @@ def run_ours(args):
         cap = TC_F32_COUPLING_DRAM
         sha_now = _sources_sha16(cap["sources"])
         fresh = sha_now == cap["source_sha16"]
-        applies = tensor_path and dtype == "f32" and args.workload == WORKLOAD
+        kname = "k_tc_gemm<4,1>" if hybrid else ("k_tc_gemm<0,1>" if tensor_path else "k_coupling")
+        applies = tensor_path and dtype == "f32" and args.workload == WORKLOAD and cap["kernel"] == kname
         measured = cap["bytes"] if (applies and fresh) else None
+        what = (f" (coupling + {n_above} transfer items above the upward cut, split TF32)" if hybrid
+                else (" (coupling, split TF32)" if tensor_path else ""))
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "traffic": measured,
-                "kernel": "k_tc_gemm<0,1> (coupling, split TF32)" if tensor_path else "k_coupling",
+                "frac": round(achieved / hbm_peak, 4), "traffic": measured, "kernel": kname + what,
                 "peak_source": f"{peak_kind} hbm_gbs"}
         if applies:
             roof["traffic_source"] = {"capture": cap["capture"], "bytes": cap["bytes"],
@@ -488,7 +501,7 @@ def run_ours(args):
     per_phase = None
     if tensor_path:
         per_phase = {}
-        for ph, b in phase_bytes(n, k, m, nc, n_leaves, n_adm, info["nnz_near"], elt).items():
+        for ph, b in phase_bytes(n, k, m, nc, n_leaves, n_adm, info["nnz_near"], elt, n_above).items():
             t = phases.get(ph)
             if t and t > 0:
                 per_phase[ph] = {"ms": round(t, 4), "algorithmic_bytes": int(b),

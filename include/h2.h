@@ -120,6 +120,11 @@ typedef struct h2_info_t {
                              most 64 columns, a multiple of 4 of them; with k % 4 == 0 and
                              k <= 64 the transfer passes pack the tensor-core operands
                              themselves, otherwise three packing launches are counted  */
+    int32_t kernel;       /* h2_kernel of the build                                     */
+    int32_t hybrid;       /* 1: the FP32 tensor-core product takes, by default, the hybrid
+                             upward pass (the CUDA-core subtree pass stops at its cut, the
+                             clusters above it are transfer items of the coupling launch) */
+    int64_t n_above_cut;  /* clusters above that cut (transfer items of that launch)      */
 } h2_info_t;
 
 /* Build A from n points (pts: n×3 row-major doubles, host or device).  On

@@ -320,6 +320,9 @@ int h2_info(const h2_matrix* A, h2_info_t* info) {
     info->launches_tc = A->tc.built ? (own_passes ? 5 : 8) + (A->down_ptr.back() > 0 ? 1 : 0) +
                                           (A->tc.c_nzero > 0 ? 1 : 0)
                                     : 0;
+    info->kernel = A->kernel;
+    info->hybrid = A->tc.hybrid && A->tc.h_default ? 1 : 0;
+    info->n_above_cut = A->tc.h_nabove;
     return 0;
 }
 

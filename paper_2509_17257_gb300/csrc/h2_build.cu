@@ -956,6 +956,8 @@ int hybrid_lists(h2_matrix* A, cudaStream_t st) {
     if ((rc = upload(A, &D.h_items, items, st)) || (rc = upload(A, &D.h_terms, terms, st))) return rc;
     D.h_nitems = (int)items.size();
     D.hybrid = true;
+    D.h_nabove = 0;
+    for (int64_t c = 0; c < nc; ++c) D.h_nabove += h[c] > 0;
     int64_t free_terms = 0;
     for (const Free& f : free_items) free_terms += f.cost;
     D.h_default = free_terms >= (int64_t)kHybridTermsPerHeight * H * kTcGrid;

@@ -218,6 +218,7 @@ struct TcData {
     // for those clusters interleaved with the coupling items (hybrid_lists)
     bool hybrid = false;
     bool h_default = false;  // the built-in rule takes it (enough coupling work to hide the chain)
+    int64_t h_nabove = 0;    // clusters above the cut (its transfer items)
     TcItem* h_items = nullptr;
     TcTerm* h_terms = nullptr;
     int h_nitems = 0;

@@ -63,7 +63,8 @@ class Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("k", C.c_int64), ("n_clusters", C.c_int64), ("n_leaves", C.c_int64),
                 ("n_adm", C.c_int64), ("n_near", C.c_int64), ("nnz_near", C.c_int64), ("depth", C.c_int32),
                 ("q", C.c_int32), ("bytes_f64", C.c_int64), ("bytes_f32", C.c_int64), ("bytes_bf16", C.c_int64),
-                ("flops_per_col", C.c_double), ("launches", C.c_int32), ("launches_tc", C.c_int32)]
+                ("flops_per_col", C.c_double), ("launches", C.c_int32), ("launches_tc", C.c_int32),
+                ("kernel", C.c_int32), ("hybrid", C.c_int32), ("n_above_cut", C.c_int64)]
 
 
 class CGParams(C.Structure):
