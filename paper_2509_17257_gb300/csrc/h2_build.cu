@@ -635,8 +635,9 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
         H2_CUDA_TRY(cudaHostGetDevicePointer((void**)&A->err_dev, A->err_host, 0));
     }
     const bool want_bf16 = (precisions & (1u << H2_BF16)) != 0;
-    // the complex product runs on the CUDA cores only: no tensor-core tiles
-    const bool want_tf32 = (precisions & (1u << H2_F32)) != 0 && k <= 64 && !A->cplx;
+    // the complex product takes the TF32 tiles of both planes of S and G (no BF16, no
+    // transfer-pass or matrix-free tiles)
+    const bool want_tf32 = (precisions & (1u << H2_F32)) != 0 && k <= 64;
     if (want_bf16 && A->cplx) {
         set_error("a complex kernel has no BF16 product");
         return H2_E_UNSUPPORTED;
@@ -989,7 +990,12 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
         return off - b;
     };
     std::vector<int64_t> s_off(A->n_adm), v_off(NL), g_off(A->n_near);
+    // a complex matrix: the imaginary planes' tiles follow the real ones (S at
+    // n_adm·k², G at nnz_near elements further on in the FP64 arrays)
+    std::vector<int64_t> si_off(A->cplx ? A->n_adm : 0), gi_off(A->cplx ? A->n_near : 0);
     for (int64_t j = 0; j < A->n_adm; ++j) s_off[j] = add(j * k * k, k, k, k, NP, KP);
+    if (A->cplx)
+        for (int64_t j = 0; j < A->n_adm; ++j) si_off[j] = add((A->n_adm + j) * k * k, k, k, k, NP, KP);
     const int64_t nS = (int64_t)tiles.size();
     for (int64_t lp = 0; lp < NL; ++lp) {
         const int32_t t = A->leaves[lp];
@@ -1013,12 +1019,22 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
                 acc += (int64_t)nt * ns;
             }
         }
+        if (A->cplx) {
+            int64_t jj = 0;
+            for (int64_t lp = 0; lp < NL; ++lp) {
+                const int nt = (int)T.size[A->leaves[lp]];
+                for (int64_t e = T.near_rowptr[A->leaves[lp]]; e < T.near_rowptr[A->leaves[lp] + 1]; ++e, ++jj) {
+                    const int ns = (int)T.size[T.near_col[e]];
+                    gi_off[jj] = add(near_src[jj] + A->nnz_near, nt, ns, ns, round16(nt), round16(ns));
+                }
+            }
+        }
     }
     const int64_t nG = (int64_t)tiles.size() - nS - nV;
     D.bytes = off;  // BF16 bytes; the FP32 copy is twice that
     // the transfer passes' tiles follow in the FP32 copy only
     FlowTiles ft;
-    const bool flow = tf32 && k <= 64 && T.leaf_size <= 64;
+    const bool flow = tf32 && k <= 64 && T.leaf_size <= 64 && !A->cplx;
     if (flow) flow_tiles(A, tiles, off, ft);
     const int64_t off32 = off;
     int rc = 0;
@@ -1049,7 +1065,7 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     }
     D.has_bf16 = bf16;
     D.has_tf32 = tf32;
-    if (tf32) {
+    if (tf32 && !A->cplx) {
         if ((rc = device_alloc(A, (void**)&D.nodes4, (size_t)nc * KP * sizeof(float4)))) return rc;
         const unsigned g = (unsigned)std::min<int64_t>((nc * KP + 255) / 256, 152 * 16);
         k_nodes4<<<g, 256, 0, st>>>(A->d_nodes, nc, A->q, KP, D.nodes4);
@@ -1059,12 +1075,17 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     // ---- coupling schedule: outputs = clusters with at least one admissible block ----
     std::vector<int32_t> c_zero;
     std::vector<TcItem> c_items;
-    std::vector<TcTerm> c_terms(A->n_adm);
-    for (int64_t j = 0; j < A->n_adm; ++j)
-        c_terms[j] = TcTerm{s_off[j], (int32_t)((int64_t)T.adm_col[j] * KP), (int16_t)KP, (int16_t)0};
+    // a complex matrix: two terms per block, S_re·x̂_s and S_im·(i·x̂_s)
+    const int tpb = A->cplx ? 2 : 1;
+    std::vector<TcTerm> c_terms(tpb * A->n_adm);
+    for (int64_t j = 0; j < A->n_adm; ++j) {
+        const int32_t ak = (int32_t)((int64_t)T.adm_col[j] * KP);
+        c_terms[tpb * j] = TcTerm{s_off[j], ak, (int16_t)KP, (int16_t)0};
+        if (A->cplx) c_terms[2 * j + 1] = TcTerm{si_off[j], ak, (int16_t)KP, kTermImag};
+    }
     for (int64_t c = 0; c < nc; ++c) {
         const int32_t e0 = (int32_t)T.adm_rowptr[c], e1 = (int32_t)T.adm_rowptr[c + 1];
-        if (e1 > e0) c_items.push_back(TcItem{(int32_t)c, e0, e1, NP});
+        if (e1 > e0) c_items.push_back(TcItem{(int32_t)c, tpb * e0, tpb * e1, NP});
         else c_zero.push_back((int32_t)c);
     }
     // longest lists first, dealt to the CTAs in snake order
@@ -1095,6 +1116,10 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
                 const int kps = round16((int)T.size[sc]);
                 l_terms.push_back(TcTerm{g_off[j], (int32_t)xkoff[leaf_pos[sc]], (int16_t)kps, (int16_t)0});
                 l_cost[lp] += (int64_t)l_np[lp] * kps;
+                if (A->cplx) {  // G_im·(i·X|_ŝ)
+                    l_terms.push_back(TcTerm{gi_off[j], (int32_t)xkoff[leaf_pos[sc]], (int16_t)kps, kTermImag});
+                    l_cost[lp] += (int64_t)l_np[lp] * kps;
+                }
             }
             l_items[lp] = TcItem{(int32_t)lp, e0, (int32_t)l_terms.size(), l_np[lp]};
         }

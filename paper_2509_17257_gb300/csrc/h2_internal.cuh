@@ -93,6 +93,11 @@ struct TcTerm {
     int16_t kp, asrc;
 };
 constexpr int16_t kTermWait = 4;
+// The complex product (TcGemmParams::cplx): the term multiplies i·act instead of
+// act, i.e. its activation columns come in (real, imaginary) pairs and column 2j
+// takes -(column 2j + 1), column 2j + 1 takes column 2j (the epilogue applies
+// the swap and the sign to the term's result).
+constexpr int16_t kTermImag = 8;
 
 // The per-system arguments of a multi-system launch of the tcgen05 segmented
 // GEMM (one launch serving several H² matrices, h2_batch_matmul): an item's
@@ -149,6 +154,8 @@ struct TcGemmParams {
     const float4* nodes;
     float inv_len;
     int KP;
+    // modes 0 and 1 of the complex product: terms marked kTermImag apply i·act
+    int cplx;
 };
 
 // BF16 tensor-core copy of the matrix data and the schedules of its kernels.

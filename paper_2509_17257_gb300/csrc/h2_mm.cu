@@ -187,6 +187,34 @@ __global__ void k_scatter_y(const float* __restrict__ Z, int ldz, const int32_t*
     }
 }
 
+// ---- the same over C: interleaved (real, imaginary) columns, m2 = 2·m_c, and
+// Y[perm[i], :] (+)= α (Z[i, :] + σ X[perm[i], :]) with α = alpha_re + i·alpha_im ----
+__global__ void k_scatter_yc(const float* __restrict__ Z, int ldz, const int32_t* __restrict__ perm, int64_t n,
+                             int m2, const double* __restrict__ X, int64_t ldx, double* __restrict__ Y, int64_t ldy,
+                             double alpha_re, double alpha_im, double sigma, int overwrite) {
+    const int mc = m2 >> 1;
+    const int P = row_lanes(mc), R = 32 / P;
+    const int lane = threadIdx.x & 31, sub = lane / P, cl = lane % P;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * R + sub; i < n; i += nw * R) {
+        const int64_t g = perm[i];
+        const float* z = Z + i * ldz;
+        const double* x = X + g * ldx;
+        double* y = Y + g * ldy;
+        for (int c = cl; c < mc; c += P) {
+            const double zr = (double)z[2 * c] + sigma * x[2 * c], zi = (double)z[2 * c + 1] + sigma * x[2 * c + 1];
+            const double vr = alpha_re * zr - alpha_im * zi, vi = alpha_re * zi + alpha_im * zr;
+            if (overwrite) {
+                y[2 * c] = vr;
+                y[2 * c + 1] = vi;
+            } else {
+                y[2 * c] += vr;
+                y[2 * c + 1] += vi;
+            }
+        }
+    }
+}
+
 // ---- forward transformation at the leaves: x̂_t = V_tᵀ Xp|_t̂ ----
 template <typename T, int RM, int CN>
 __global__ void __launch_bounds__(kThreads) k_leaf_fwd(const int32_t* __restrict__ leaves,
@@ -1173,7 +1201,10 @@ int ensure_workspace(h2_matrix* A, size_t bytes, cudaStream_t st) {
 // high and low parts of each column).
 template <int CN>
 int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy, int m,
-                 cudaStream_t st, bool overwrite, const SyncBufs& sb, bool trans) {
+                 cudaStream_t st, bool overwrite, const SyncBufs& sb, bool trans, const double* alpha_im) {
+    // alpha_im: the complex product (m counts the 2·m_c interleaved real columns; the
+    // term lists carry the S_im and G_im terms, the transfer passes are the real ones)
+    const bool cx = alpha_im != nullptr;
     // kind 2: the TF32 product with the matrix-free coupling (tensor-core kernel mode 2)
     const bool mf = kind == 2;
     if (mf) kind = 1;
@@ -1206,13 +1237,13 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         if (tn.path == kPathTcFlow || tn.path == kPathTcFused) want_flow = true;
         if (A->use_flow >= 0) want_flow = A->use_flow == 1;
         const bool capturing = stream_capture_active(st);
-        const bool flow = kind == 1 && D.flow && want_flow && !capturing;
+        const bool flow = kind == 1 && D.flow && want_flow && !capturing && !cx;
         // hybrid: the subtree passes stop at the upward cut, and the clusters above it
         // are transfer items of the coupling launch (k_tc_gemm<4, 1>), which waits for
         // them only where a coupling reads them
         bool want_hybrid = tn.path == kPathTcHybrid || (tn.path == kPathDefault && D.h_default);
         if (A->use_hybrid >= 0) want_hybrid = A->use_hybrid == 1;
-        const bool hybrid = kind == 1 && fast && !flow && !trans && !mf && D.hybrid && want_hybrid && !capturing;
+        const bool hybrid = kind == 1 && fast && !flow && !trans && !mf && !cx && D.hybrid && want_hybrid && !capturing;
         int rc = ensure_workspace(A, bXp + 2 * bC + bXcm + 3 * bAct, st);
         if (rc) return rc;
         char* base = (char*)A->ws.base;
@@ -1395,6 +1426,7 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         cp.nodes = D.nodes4;
         cp.inv_len = (float)(1.0 / A->length);
         cp.KP = KP;
+        cp.cplx = cx ? 1 : 0;
         if (hybrid) {
             cp.n_items = D.h_nitems;
             cp.items = D.h_items;
@@ -1447,13 +1479,18 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         lp.err = A->err_dev;
         lp.zp = Xp;  // the gathered FP32 X is no longer read after the forward pass and its packing
         lp.ldc = mc;
+        lp.cplx = cx ? 1 : 0;
         if ((rc = launch_tc_gemm(1, kind, lp, std::min(lp.n_items, grid_cap), st, stg))) return rc;
         {
             const int64_t total = n * mc;
             const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
             if ((rc = wait_y_staged(A->ws, st))) return rc;
-            k_scatter_y<<<g, 256, 0, st>>>(Xp, mc, A->d_perm, n, mc, X + c0, ldx, Y + c0, ldy, alpha, A->sigma,
-                                           overwrite ? 1 : 0);
+            if (cx)
+                k_scatter_yc<<<g, 256, 0, st>>>(Xp, mc, A->d_perm, n, mc, X + c0, ldx, Y + c0, ldy, alpha, *alpha_im,
+                                                A->sigma, overwrite ? 1 : 0);
+            else
+                k_scatter_y<<<g, 256, 0, st>>>(Xp, mc, A->d_perm, n, mc, X + c0, ldx, Y + c0, ldy, alpha, A->sigma,
+                                               overwrite ? 1 : 0);
             H2_LAUNCH_CHECK();
         }
         marks.mark();
@@ -1463,14 +1500,15 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
 }
 
 int dispatch_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
-                int64_t m, cudaStream_t st, bool overwrite, const SyncBufs& sb, bool trans = false) {
+                int64_t m, cudaStream_t st, bool overwrite, const SyncBufs& sb, bool trans = false,
+                const double* alpha_im = nullptr) {
     if (trans) {
         int rc = build_tc_transposed(A, st);
         if (rc) return rc;
     }
-    if (m <= 16) return run_chain_tc<1>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb, trans);
-    if (m <= 32) return run_chain_tc<2>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb, trans);
-    return run_chain_tc<4>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb, trans);
+    if (m <= 16) return run_chain_tc<1>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb, trans, alpha_im);
+    if (m <= 32) return run_chain_tc<2>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb, trans, alpha_im);
+    return run_chain_tc<4>(A, kind, alpha, X, ldx, Y, ldy, (int)m, st, overwrite, sb, trans, alpha_im);
 }
 
 template <typename T>
@@ -1567,9 +1605,13 @@ int matmul_device(h2_matrix* A, double alpha, const double* X, int64_t ldx, doub
     }
     if (dtype == H2_F32) {
         if (!A->f32.built) { set_error("FP32 copy not built (add 1<<H2_F32 to params->precisions)"); return H2_E_UNSUPPORTED; }
-        if (alpha_im)
+        if (alpha_im) {
+            // the complex product: split-TF32 tensor cores where their tiles were built
+            if (A->tc.has_tf32 && !A->force_simt)
+                return dispatch_tc(A, 1, alpha, X, ldx, Y, ldy, m, st, overwrite, sb, false, alpha_im);
             return dispatch_cn<float>(A, A->f32, alpha, X, ldx, Y, ldy, (int)m, st, false, overwrite, (float*)base,
                                       (float*)(base + bXp), (float*)(base + bXp + bC), sb, alpha_im);
+        }
         const Tune& tn = A->tune[0][column_class((int)std::min<int64_t>(m, 64))];
         if (A->tc.has_tf32 && !A->force_simt && tn.path != kPathSimt)
             return dispatch_tc(A, 1, alpha, X, ldx, Y, ldy, m, st, overwrite, sb, transposed);

@@ -652,7 +652,13 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
 #pragma unroll
             for (int j = 0; j < kAccCols; ++j) sum[j] = 0.f;
             bool failed = false;
+            uint32_t imask = 0;  // complex product: bit t of the batch of 32 terms applies i·act
             for (int term = 0; term < nterms; ++term, ++it) {
+                if (!FLOW && p.cplx && (term & 31) == 0) {
+                    const int tt = term + lane;
+                    imask = __ballot_sync(0xffffffffu, tt < nterms && (p.terms[cur.e0 + tt].asrc & kTermImag));
+                }
+                const bool imag = (imask >> (term & 31)) & 1u;
                 const int acc = it % nacc;
                 if (!__any_sync(0xffffffffu, mbar_wait(&accf_bar[acc], (it / nacc) & 1))) {
                     failed = true;
@@ -682,10 +688,25 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                         tmem_ld32_async(ta + 64 * h, r0);
                         tmem_ld32_async(ta + 64 * h + 32, r1);
                         tmem_wait_ld();
+                        if (!imag) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            sum[32 * h + j] += __uint_as_float(r0[2 * j]) + __uint_as_float(r0[2 * j + 1]);
-                            sum[32 * h + 16 + j] += __uint_as_float(r1[2 * j]) + __uint_as_float(r1[2 * j + 1]);
+                            for (int j = 0; j < 16; ++j) {
+                                sum[32 * h + j] += __uint_as_float(r0[2 * j]) + __uint_as_float(r0[2 * j + 1]);
+                                sum[32 * h + 16 + j] += __uint_as_float(r1[2 * j]) + __uint_as_float(r1[2 * j + 1]);
+                            }
+                        } else {
+                            // i·act: column 2j takes -(column 2j + 1), column 2j + 1 takes column 2j
+#pragma unroll
+                            for (int j = 0; j < 16; j += 2) {
+                                const float a0 = __uint_as_float(r0[2 * j]) + __uint_as_float(r0[2 * j + 1]);
+                                const float a1 = __uint_as_float(r0[2 * j + 2]) + __uint_as_float(r0[2 * j + 3]);
+                                const float b0 = __uint_as_float(r1[2 * j]) + __uint_as_float(r1[2 * j + 1]);
+                                const float b1 = __uint_as_float(r1[2 * j + 2]) + __uint_as_float(r1[2 * j + 3]);
+                                sum[32 * h + j] -= a1;
+                                sum[32 * h + j + 1] += a0;
+                                sum[32 * h + 16 + j] -= b1;
+                                sum[32 * h + 16 + j + 1] += b0;
+                            }
                         }
                     }
                 }

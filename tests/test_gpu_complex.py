@@ -7,6 +7,8 @@ element by element, through h2_matmul_complex:
 * column counts that fill no tile exactly (1, 5, 17, 33, 70), q = 2, 3, 4,
   a ragged leaf size and an odd n;
 * the precision workload's size (n = 65536, q = 4, m = 32) on sampled rows;
+* the FP32 product on the split-TF32 tensor cores (S_im and G_im terms whose
+  activation columns the epilogue swaps and negates) and on the CUDA cores;
 * the entry points that compute over R refuse a complex matrix, and the
   complex product refuses a real one, BF16 and a transposed request."""
 import numpy as np
@@ -135,3 +137,28 @@ def test_complex_product_repeats_bit_for_bit(P):
         G.matmul_complex(Xd, Yd, alpha=1.0, dtype="f32")
         outs.append(Yd.cpu())
     assert torch.equal(outs[0], outs[1])
+
+
+def test_complex_product_on_the_cuda_cores_too(P, monkeypatch):
+    """The FP32 complex product takes split-TF32 tensor cores where their tiles
+    were built; with H2_FORCE_SIMT=1 at build it runs on the CUDA cores.  Both
+    against the oracle, and against each other."""
+    torch = require_cuda()
+    _, H = _case(P, 4096, 3, 64)
+    pts = sphere_points(4096, 3)
+    monkeypatch.setenv("H2_FORCE_SIMT", "1")
+    Gs = P.H2Matrix(pts, q=3, leaf_size=64, eta=2.0, sigma=SIGMA, precisions=("f32",), kernel="helmholtz",
+                    kappa=KAPPA, delta=DELTA)
+    monkeypatch.delenv("H2_FORCE_SIMT")
+    Gt, _ = _case(P, 4096, 3, 64)
+    X, Y0 = _cx(4096, 20, 61), _cx(4096, 20, 62)
+    ref = O.h2mm(H, 0.3 + 0.9j, X, Y0)
+    outs = []
+    for G in (Gs, Gt):
+        Yd = torch.from_numpy(Y0.copy()).cuda()
+        G.matmul_complex(torch.from_numpy(X).cuda(), Yd, alpha=0.3 + 0.9j, dtype="f32")
+        torch.cuda.synchronize()
+        outs.append(Yd.cpu().numpy())
+        assert rel_fro(outs[-1], ref) <= TOL["f32"]
+    assert rel_fro(outs[0], outs[1]) <= 5e-6
+    Gs.close()
