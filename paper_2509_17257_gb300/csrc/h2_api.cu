@@ -277,6 +277,8 @@ int h2_build(const h2_build_params* params, const double* pts, int64_t n, h2_mat
     A->use_flow = ft && ft[0] == '1' ? 1 : (ft && ft[0] == '0' ? 0 : -1);
     const char* fh = getenv("H2_TC_HYBRID");
     A->use_hybrid = fh && fh[0] == '1' ? 1 : (fh && fh[0] == '0' ? 0 : -1);
+    const char* fk = getenv("H2_KRON");
+    A->use_kron = fk && fk[0] == '0' ? 0 : 1;
     rc = h2::build_device(A, hp, params->precisions, st);
     if (rc) {
         free_matrix(A);

@@ -44,6 +44,7 @@ struct MatData {
     void* V = nullptr;
     void* E = nullptr;
     void* Et = nullptr;  // FP32 only, k % 8 == 0, k <= 64: E_{t'}ᵀ per cluster, rows of kEtLd floats
+    void* kron = nullptr;  // FP32 only, q = 4: the 4×4 factors F_x, F_y, F_z of E_{t'} = F_z ⊗ F_y ⊗ F_x
     void* S = nullptr;
     void* Near = nullptr;
     int64_t bytes = 0;
@@ -395,6 +396,8 @@ struct h2_matrix {
     int32_t up_cut = 0;  // level of the upward pass's task roots (leaves above it are tasks too)
     // H2_TC_HYBRID at build: 1 / 0 force the hybrid upward pass on / off (unset: tuning or default)
     int use_hybrid = -1;
+    // H2_KRON at build: 0 keeps the q = 4 transfer passes on the dense transfer matrices
+    int use_kron = 1;
     bool s_replaced = false;  // h2_coupling_set was called: S_b are no longer g's values  // H2_FORCE_SIMT=1 at build: FP32 product on the CUDA cores only
     // block-Jacobi preconditioner (h2_precond.cu): (G_(t,t) + σI)⁻¹ per leaf, built on first use
     double* bj_inv = nullptr;     // concatenated n_t×n_t inverses, leaf order

@@ -984,10 +984,194 @@ __global__ void __launch_bounds__(128) k_down_own(const int32_t* __restrict__ ta
     }
 }
 
+// ---- transfer matrices as Kronecker products (q = 4) ----
+// With tensor Chebyshev interpolation E_c[μ, ν] = L_{ν_x}(ξ_{μ_x}) L_{ν_y}(ξ_{μ_y})
+// L_{ν_z}(ξ_{μ_z}) (1-D Lagrange polynomials of the father's nodes at the son's
+// nodes, per axis), so E_c = F_z ⊗ F_y ⊗ F_x with 4×4 factors (ν = ν_x + 4ν_y +
+// 16ν_z): E_c y costs three 4×4 mode products (48 multiply-adds per column and
+// slab) instead of a 64×64 product, and E_c is 48 numbers.  kron[c] holds F_x,
+// F_y, F_z row-major (F_a[μ][ν]).
+//
+// The thread layout of kron_step: lane quad (4 consecutive lanes) g = 0..3 holds
+// the z-slab ν_z = g of one column; the x and y mode products stay in the
+// thread, the z mode product sums the quad's four slabs through shuffles.
+//   f:   F_x and F_y (32 values); fz: the thread's row g of F_z (TR: its column g)
+//   in:  x[ν_y][ν_x] = block rows 16g + 4ν_y + ν_x, one column
+//   out: y[μ_y][μ_x] = rows 16g + 4μ_y + μ_x of (F_z ⊗ F_y ⊗ F_x) x (TR: of the
+//        transposed product, (F_z ⊗ F_y ⊗ F_x)ᵀ = F_zᵀ ⊗ F_yᵀ ⊗ F_xᵀ)
+template <bool TR>
+__device__ __forceinline__ void kron_step(const float (&f)[32], const float (&fz)[4], const float (&x)[16],
+                                          float (&y)[16]) {
+    auto F = [&](int a, int mu, int nu) { return TR ? f[16 * a + 4 * nu + mu] : f[16 * a + 4 * mu + nu]; };
+    float t[16];
+#pragma unroll
+    for (int vy = 0; vy < 4; ++vy)
+#pragma unroll
+        for (int mx = 0; mx < 4; ++mx) {
+            float a = 0.f;
+#pragma unroll
+            for (int vx = 0; vx < 4; ++vx) a = fmaf(F(0, mx, vx), x[4 * vy + vx], a);
+            t[4 * vy + mx] = a;
+        }
+    float u[16];
+#pragma unroll
+    for (int my = 0; my < 4; ++my)
+#pragma unroll
+        for (int mx = 0; mx < 4; ++mx) {
+            float a = 0.f;
+#pragma unroll
+            for (int vy = 0; vy < 4; ++vy) a = fmaf(F(1, my, vy), t[4 * vy + mx], a);
+            u[4 * my + mx] = a;
+        }
+    const int base = (threadIdx.x & 31) & ~3;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        float a = 0.f;
+#pragma unroll
+        for (int vz = 0; vz < 4; ++vz) a = fmaf(fz[vz], __shfl_sync(0xffffffffu, u[e], base | vz), a);
+        y[e] = a;
+    }
+}
+
+// Downward pass with subtree ownership for q = 4 (the schedule of k_down_own):
+// each step ŷ_c = ŷ_c + E_c ŷ_father as the Kronecker product above, on the
+// CUDA cores.  The father's ŷ comes from a shared-memory stack entry written by
+// an earlier step of the same task; the factors of the next step and its
+// coupling result load into registers while the current step computes.  The
+// first step of a task copies the root's ŷ into its entry (bulk copies); a
+// leaf's ŷ goes to global memory and into its split tile, as in k_down_own.
+// 128 threads: quad (column c, slab g), c = threadIdx.x / 4 + 32j for j < NT/32.
+template <int CN>
+__global__ void __launch_bounds__(128) k_down_kron(const int32_t* __restrict__ task_ptr, int ntasks,
+                                                   const DownStep* __restrict__ steps,
+                                                   const float* __restrict__ kron, float* yhat,
+                                                   unsigned* __restrict__ claim, int* __restrict__ err, int m,
+                                                   PackOut pk) {
+    constexpr int NT = 16 * CN, LDY = NT + 8, NJ = NT >= 32 ? NT / 32 : 1;
+    constexpr int k = 64;
+    extern __shared__ __align__(16) float fsm[];
+    float* stk = fsm;  // [entries][64][LDY]   final ŷ along the current path
+    __shared__ int s_task;
+    __shared__ DownStep s_steps[kDownMaxSteps];
+    __shared__ __align__(8) uint64_t bar;
+    const int g = threadIdx.x & 3, cq = threadIdx.x >> 2;
+    const int64_t km = (int64_t)k * m;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    bool failed = false;
+    // factors (F_x, F_y and row g of F_z) and coupling rows of one step (this
+    // thread's slab, columns c_j)
+    auto load_step = [&](int c, float (&f)[32], float (&fz)[4], float (&cp)[NJ][16]) {
+        if (c < 0) return;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) f[i] = __ldg(kron + (int64_t)c * 48 + i);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) fz[i] = __ldg(kron + (int64_t)c * 48 + 32 + 4 * g + i);
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int col = cq + 32 * j;
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+                cp[j][e] = (col < m) ? __ldcg(yhat + (int64_t)c * km + (int64_t)(16 * g + e) * m + col) : 0.f;
+        }
+    };
+    while (!failed) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_task = (int)atomicAdd(claim, 1u);
+        __syncthreads();
+        const int task = s_task;
+        if (task >= ntasks) break;
+        const int s0 = task_ptr[task], s1 = min(task_ptr[task + 1], s0 + kDownMaxSteps);
+        for (int i = threadIdx.x; i < s1 - s0; i += blockDim.x) s_steps[i] = steps[s0 + i];
+        __syncthreads();
+        float fcur[32], fnext[32], zcur[4], znext[4], ccur[NJ][16], cnext[NJ][16];
+        {
+            int f0 = -1;
+            for (int t = s0; t < s1; ++t)
+                if (!(s_steps[t - s0].flags & kDownLoad)) { f0 = t; break; }
+            if (f0 >= 0) load_step(s_steps[f0 - s0].c, fcur, zcur, ccur);
+        }
+        for (int s = s0; s < s1; ++s) {
+            const DownStep d = s_steps[s - s0];
+            if (d.flags & kDownLoad) {
+                // the root's ŷ (its coupling result) into entry wr, one bulk copy per row
+                const uint32_t rowb = (uint32_t)m * 4;
+                if (threadIdx.x < 32) {
+                    if (threadIdx.x == 0) mbar_expect_tx(&bar, rowb * (uint32_t)k);
+                    __syncwarp();
+                    for (int r = threadIdx.x; r < k; r += 32)
+                        bulk_g2s(stk + (d.wr * 64 + r) * LDY, yhat + (int64_t)d.c * km + (int64_t)r * m, rowb, &bar);
+                }
+                const bool ok = mbar_wait(&bar, phase);
+                phase ^= 1u;
+                if (__syncthreads_or(!ok)) {
+                    if (threadIdx.x == 0) {
+                        atomicExch(err, 9);
+                        mbar_wait(&bar, phase);  // the copies land before the CTA leaves (bounded)
+                    }
+                    failed = true;
+                    break;
+                }
+                continue;
+            }
+            // the next step's factors and coupling rows load while this one computes
+            int nx = -1;
+            for (int t = s + 1; t < s1; ++t)
+                if (!(s_steps[t - s0].flags & kDownLoad)) { nx = t; break; }
+            load_step(nx >= 0 ? s_steps[nx - s0].c : -1, fnext, znext, cnext);
+            const float* in = stk + d.rd * 64 * LDY;
+            float* out = stk + d.wr * 64 * LDY;
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                const int col = cq + 32 * j;
+                if (cq < NT) {  // whole quads: the shuffles stay within active lanes
+                    float x[16], y[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) x[e] = in[(16 * g + e) * LDY + col];
+                    kron_step<false>(fcur, zcur, x, y);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) out[(16 * g + e) * LDY + col] = y[e] + ccur[j][e];
+                }
+            }
+            __syncthreads();  // entry wr complete
+            if (d.flags & kDownStore) {
+                // a leaf: ŷ_c to global memory and into its split tile, read back in 4×4 blocks
+                float* gout = yhat + (int64_t)d.c * km;
+                uint8_t* tile = pk.act + (int64_t)d.c * pk.KP * pk.R * pk.es;
+                for (int blk = threadIdx.x; blk < 16 * (NT / 4); blk += blockDim.x) {
+                    const int ty = blk / (NT / 4), tx = blk % (NT / 4);
+                    float acc[4][4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const float4 v = *(const float4*)(out + (4 * ty + r) * LDY + 4 * tx);
+                        acc[r][0] = v.x; acc[r][1] = v.y; acc[r][2] = v.z; acc[r][3] = v.w;
+                        if (4 * tx < m) *(float4*)(gout + (4 * ty + r) * m + 4 * tx) = v;
+                    }
+                    pack_rows(pk, tile, acc, tx, ty, k, m);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) fcur[i] = fnext[i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) zcur[i] = znext[i];
+#pragma unroll
+            for (int j = 0; j < NJ; ++j)
+#pragma unroll
+                for (int e = 0; e < 16; ++e) ccur[j][e] = cnext[j][e];
+        }
+    }
+}
+
 // k_up_own: two slots of two 64×64 blocks plus the stack
 int up_own_smem_bytes(int cn, int entries) { return (4 * 64 * 64 + entries * 64 * 16 * cn) * (int)sizeof(float); }
 // k_down_own: two Eᵀ buffers (rows of 72) plus the stack (rows of 16·cn + 8, at most 8 entries)
 int down_own_smem_bytes(int cn, int entries) { return (2 * 64 * 72 + entries * 64 * (16 * cn + 8)) * (int)sizeof(float); }
+// k_down_kron: the stack only (rows of 16·cn + 8)
+int down_kron_smem_bytes(int cn, int entries) { return entries * 64 * (16 * cn + 8) * (int)sizeof(float); }
 
 int g_fast_attr_device = -1;
 
@@ -1001,6 +1185,9 @@ int fast_prepare() {
     H2_CUDA_TRY(cudaFuncSetAttribute(k_down_own<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_own_smem_bytes(1, 8)));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_down_own<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_own_smem_bytes(2, 8)));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_down_own<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_own_smem_bytes(4, 8)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_down_kron<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_kron_smem_bytes(1, 8)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_down_kron<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_kron_smem_bytes(2, 8)));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_down_kron<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_kron_smem_bytes(4, 8)));
     g_fast_attr_device = dev;
     return 0;
 }
@@ -1452,7 +1639,17 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
                 const float* Et = (const float*)A->f32.Et;
                 const int smem = down_own_smem_bytes(fcn, A->dn_entries);
                 const unsigned g = (unsigned)std::min(A->dn_ntasks, 152 * std::max(1, (227 * 1024) / (smem + 4096)));
-                if (fcn == 1) k_down_own<1><<<g, 128, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
+                const float* kron = (const float*)A->f32.kron;
+                if (kron && k == 64 && A->use_kron && fcn >= 2) {
+                    // q = 4: each step as three 4×4 mode products (E_c = F_z ⊗ F_y ⊗ F_x); with
+                    // 16 columns or fewer half its threads would idle, and the dense pass is faster
+                    const int ksm = down_kron_smem_bytes(fcn, A->dn_entries);
+                    const unsigned gk =
+                        (unsigned)std::min(A->dn_ntasks, 152 * std::max(1, (227 * 1024) / (ksm + 4096)));
+                    if (fcn == 1) k_down_kron<1><<<gk, 128, ksm, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, kron, yhat, sbc.claim, sbc.err, mc, pk);
+                    else if (fcn == 2) k_down_kron<2><<<gk, 128, ksm, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, kron, yhat, sbc.claim, sbc.err, mc, pk);
+                    else k_down_kron<4><<<gk, 128, ksm, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, kron, yhat, sbc.claim, sbc.err, mc, pk);
+                } else if (fcn == 1) k_down_own<1><<<g, 128, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
                 else if (fcn == 2) k_down_own<2><<<g, 128, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
                 else k_down_own<4><<<g, 128, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
                 H2_LAUNCH_CHECK();
