@@ -128,15 +128,16 @@ __global__ void k_transfer(const int32_t* __restrict__ parent, const double* __r
 // polynomials of the father's nodes on axis a at the son's nodes on that axis, so
 // E_c[μ, ν] = F_x[μ_x][ν_x] F_y[μ_y][ν_y] F_z[μ_z][ν_z] (k_transfer's entries are
 // these products); in FP32, 48 per cluster (zero for the root).
+template <typename T>
 __global__ void k_kron_factors(const int32_t* __restrict__ parent, const double* __restrict__ nodes, int64_t nc,
-                               float* __restrict__ F) {
+                               T* __restrict__ F) {
     const int q = 4;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc * 48; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = e / 48;
         const int r = (int)(e % 48), a = r / 16, mu = (r % 16) / 4, nu = r % 4;
         const int p = parent[c];
-        F[e] = p < 0 ? 0.f
-                     : (float)lagrange(nodes + ((size_t)p * 3 + a) * q, q, nu, nodes[((size_t)c * 3 + a) * q + mu]);
+        F[e] = p < 0 ? T(0)
+                     : (T)lagrange(nodes + ((size_t)p * 3 + a) * q, q, nu, nodes[((size_t)c * 3 + a) * q + mu]);
     }
 }
 
@@ -634,6 +635,16 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
         H2_LAUNCH_CHECK();
     }
     A->f64.built = true;
+    // q = 4: the Kronecker factors of the transfer matrices, E_c = F_z ⊗ F_y ⊗ F_x
+    const unsigned gkf = (unsigned)std::min<int64_t>((nc * 48 + 255) / 256, 152 * 8);
+    if (q == 4) {
+        if ((rc = device_alloc(A, &A->f64.kron, (size_t)nc * 48 * sizeof(double)))) return rc;
+        k_kron_factors<double><<<gkf, 256, 0, st>>>(A->d_parent, A->d_nodes, nc, (double*)A->f64.kron);
+        H2_LAUNCH_CHECK();
+        if ((rc = device_alloc(A, &A->f32.kron, (size_t)nc * 48 * sizeof(float)))) return rc;
+        k_kron_factors<float><<<gkf, 256, 0, st>>>(A->d_parent, A->d_nodes, nc, (float*)A->f32.kron);
+        H2_LAUNCH_CHECK();
+    }
 
     if (precisions & (1u << H2_F32)) {
         if ((rc = cast_copy(A, (const double*)A->f64.V, &A->f32.V, (int64_t)n * k, st))) return rc;
@@ -674,13 +685,7 @@ int build_device(h2_matrix* A, const double* pts_host, uint32_t precisions, cuda
             k_transpose_f32<<<1216, 256, 0, st>>>((const double*)A->f64.E, (float*)A->f32.Et, nc, k);
             H2_LAUNCH_CHECK();
         }
-        if (q == 4) {
-            // the Kronecker factors of the transfer matrices (the q = 4 downward pass)
-            if ((rc = device_alloc(A, &A->f32.kron, (size_t)nc * 48 * sizeof(float)))) return rc;
-            k_kron_factors<<<(unsigned)std::min<int64_t>((nc * 48 + 255) / 256, 152 * 8), 256, 0, st>>>(
-                A->d_parent, A->d_nodes, nc, (float*)A->f32.kron);
-            H2_LAUNCH_CHECK();
-        }
+
         if ((rc = build_tc(A, want_bf16, want_tf32, st))) return rc;
     }
     H2_CUDA_TRY(cudaStreamSynchronize(st));

@@ -44,7 +44,7 @@ struct MatData {
     void* V = nullptr;
     void* E = nullptr;
     void* Et = nullptr;  // FP32 only, k % 8 == 0, k <= 64: E_{t'}ᵀ per cluster, rows of kEtLd floats
-    void* kron = nullptr;  // FP32 only, q = 4: the 4×4 factors F_x, F_y, F_z of E_{t'} = F_z ⊗ F_y ⊗ F_x
+    void* kron = nullptr;  // q = 4: the 4×4 factors F_x, F_y, F_z of E_{t'} = F_z ⊗ F_y ⊗ F_x [n_c][48]
     void* S = nullptr;
     void* Near = nullptr;
     int64_t bytes = 0;

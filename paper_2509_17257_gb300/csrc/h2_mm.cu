@@ -145,6 +145,79 @@ __device__ __forceinline__ void store_tile(const Acc<T, RM, CN>& acc, T* __restr
     }
 }
 
+// acc += E·B (TR: Eᵀ·B) for q = 4, with E = F_z ⊗ F_y ⊗ F_x (4×4 factors at f,
+// F_a[μ][ν] row-major: F_x, F_y, F_z; ν = ν_x + 4ν_y + 16ν_z) and B the 64 rows ×
+// columns col0.. of a block (leading dimension ldb; columns >= ncol read as 0,
+// read through L2 as in mac<CGB>): three 4×4 mode products in place in the
+// CTA's shared memory (the Smem struct as one flat buffer), instead of a 64×64
+// product.  Thread (tx, ty) owns rows 4ty.. (an x-fiber: μ_y = ty & 3, μ_z =
+// ty >> 2) and columns CN·tx.., as in mac with RM = 4.
+template <typename T, int CN, bool TR>
+__device__ __forceinline__ void kron_tile(Acc<T, 4, CN>& acc, Smem<T, 4, CN>& sm, const T* __restrict__ f,
+                                          const T* B, int64_t ldb, int ncol, int col0) {
+    constexpr int NT = 16 * CN;
+    static_assert(sizeof(Smem<T, 4, CN>) >= sizeof(T) * (64 * NT + 48), "kron_tile needs 64 rows and the factors");
+    T* X = reinterpret_cast<T*>(&sm);  // [64][NT]
+    T* Fs = X + 64 * NT;               // [48]
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    __syncthreads();  // earlier readers of the shared memory are done
+    for (int e = tid; e < 64 * NT; e += kThreads) {
+        const int r = e / NT, c = e % NT, gc = col0 + c;
+        X[e] = gc < ncol ? __ldcg(B + (int64_t)r * ldb + gc) : T(0);
+    }
+    if (tid < 48) Fs[tid] = f[tid];
+    __syncthreads();
+    auto F = [&](int a, int mu, int nu) { return TR ? Fs[16 * a + 4 * nu + mu] : Fs[16 * a + 4 * mu + nu]; };
+    const int my = ty & 3, mz = ty >> 2;
+    T t[4][CN];
+    // x: the thread's own fiber
+#pragma unroll
+    for (int j = 0; j < CN; ++j) {
+        T x[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) x[v] = X[(4 * ty + v) * NT + CN * tx + j];
+#pragma unroll
+        for (int mx = 0; mx < 4; ++mx) {
+            T a = T(0);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) a = fma(F(0, mx, v), x[v], a);
+            t[mx][j] = a;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int mx = 0; mx < 4; ++mx)
+#pragma unroll
+        for (int j = 0; j < CN; ++j) X[(4 * ty + mx) * NT + CN * tx + j] = t[mx][j];
+    __syncthreads();
+    // y: rows μ_x + 4ν_y + 16μ_z
+#pragma unroll
+    for (int mx = 0; mx < 4; ++mx)
+#pragma unroll
+        for (int j = 0; j < CN; ++j) {
+            T a = T(0);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) a = fma(F(1, my, v), X[(mx + 4 * v + 16 * mz) * NT + CN * tx + j], a);
+            t[mx][j] = a;
+        }
+    __syncthreads();
+#pragma unroll
+    for (int mx = 0; mx < 4; ++mx)
+#pragma unroll
+        for (int j = 0; j < CN; ++j) X[(4 * ty + mx) * NT + CN * tx + j] = t[mx][j];
+    __syncthreads();
+    // z: rows μ_x + 4μ_y + 16ν_z
+#pragma unroll
+    for (int mx = 0; mx < 4; ++mx)
+#pragma unroll
+        for (int j = 0; j < CN; ++j) {
+            T a = T(0);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) a = fma(F(2, mz, v), X[(mx + 4 * my + 16 * v) * NT + CN * tx + j], a);
+            acc.v[mx][j] += a;
+        }
+}
+
 // Lanes per row for m columns: the power of two ≥ m, at most 32, so a warp
 // covers 32 / P rows per step, each with one perm lookup and contiguous columns
 // (no per-element division).
@@ -263,7 +336,8 @@ __global__ void __launch_bounds__(kThreads) k_up_fused(const int32_t* __restrict
                                                        const int32_t* __restrict__ son0,
                                                        const int32_t* __restrict__ son1, const T* __restrict__ V,
                                                        const T* __restrict__ E, const T* __restrict__ Xp, T* xhat,
-                                                       unsigned* __restrict__ cnt, int k, int m) {
+                                                       unsigned* __restrict__ cnt, int k, int m,
+                                                       const T* __restrict__ kron) {
     __shared__ Smem<T, RM, CN> sm;
     __shared__ int s_go;
     const int tile = blockIdx.y, gy = gridDim.y;
@@ -291,6 +365,14 @@ __global__ void __launch_bounds__(kThreads) k_up_fused(const int32_t* __restrict
         c = par;
         const int s0 = son0[c], s1 = son1[c];
         acc.zero();
+        if constexpr (RM == 4) {
+            if (kron) {  // q = 4: E_sᵀ as Kronecker products
+                kron_tile<T, CN, true>(acc, sm, kron + (int64_t)s0 * 48, xhat + s0 * km, m, m, col0);
+                kron_tile<T, CN, true>(acc, sm, kron + (int64_t)s1 * 48, xhat + s1 * km, m, m, col0);
+                store_tile<T, RM, CN, false>(acc, xhat + (int64_t)c * km, m, k, m, 0, col0);
+                continue;
+            }
+        }
         mac<T, RM, CN, true, true>(acc, sm, E + s0 * kk, k, k, k, 0, xhat + s0 * km, m, m, col0);
         mac<T, RM, CN, true, true>(acc, sm, E + s1 * kk, k, k, k, 0, xhat + s1 * km, m, m, col0);
         store_tile<T, RM, CN, false>(acc, xhat + (int64_t)c * km, m, k, m, 0, col0);
@@ -316,7 +398,8 @@ template <typename T, int RM, int CN>
 __global__ void __launch_bounds__(kThreads) k_down_fused(const int32_t* __restrict__ order, int n_items,
                                                          const int32_t* __restrict__ parent, const T* __restrict__ E,
                                                          T* yhat, unsigned* __restrict__ claim, int* flag, int epoch,
-                                                         int* __restrict__ err, int k, int m, long long spin_limit) {
+                                                         int* __restrict__ err, int k, int m, long long spin_limit,
+                                                         const T* __restrict__ kron) {
     __shared__ Smem<T, RM, CN> sm;
     __shared__ int s_item, s_ok;
     const int tile = blockIdx.y, gy = gridDim.y;
@@ -349,7 +432,15 @@ __global__ void __launch_bounds__(kThreads) k_down_fused(const int32_t* __restri
         if (!s_ok) break;
         Acc<T, RM, CN> acc;
         acc.zero();
-        mac<T, RM, CN, false, true>(acc, sm, E + (int64_t)c * kk, k, k, k, 0, yhat + (int64_t)par * km, m, m, col0);
+        bool done = false;
+        if constexpr (RM == 4) {
+            if (kron) {  // q = 4: E_c as a Kronecker product
+                kron_tile<T, CN, false>(acc, sm, kron + (int64_t)c * 48, yhat + (int64_t)par * km, m, m, col0);
+                done = true;
+            }
+        }
+        if (!done)
+            mac<T, RM, CN, false, true>(acc, sm, E + (int64_t)c * kk, k, k, k, 0, yhat + (int64_t)par * km, m, m, col0);
         store_tile<T, RM, CN, true>(acc, yhat + (int64_t)c * km, m, k, m, 0, col0);
         __threadfence();
         __syncthreads();
@@ -1237,13 +1328,13 @@ struct PhaseMarks {
 // level otherwise).  Records the leaf-forward and upward phase marks.
 template <typename T, int RM, int CN>
 int forward_pass(h2_matrix* A, const T* V, const T* E, const T* Xp, T* xhat, int m, unsigned gy, unsigned gzk,
-                 cudaStream_t st, const SyncBufs& sb, PhaseMarks& marks) {
+                 cudaStream_t st, const SyncBufs& sb, PhaseMarks& marks, const T* kron = nullptr) {
     const int k = A->k;
     const unsigned NL = (unsigned)A->leaves.size();
     if (gzk == 1) {
         k_up_fused<T, RM, CN><<<dim3(NL, gy), kThreads, 0, st>>>(A->d_leaves, A->d_cl_off, A->d_cl_size,
                                                                 A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat,
-                                                                sb.cnt, k, m);
+                                                                sb.cnt, k, m, kron);
         H2_LAUNCH_CHECK();
         marks.mark();
         marks.mark();
@@ -1267,7 +1358,7 @@ int forward_pass(h2_matrix* A, const T* V, const T* E, const T* Xp, T* xhat, int
 // Backward transfer pass ŷ_{t'} += E_{t'} ŷ_t (one launch when k <= 64).
 template <typename T, int RM, int CN>
 int backward_pass(h2_matrix* A, const T* E, T* yhat, int m, unsigned gy, unsigned gzk, cudaStream_t st,
-                  const SyncBufs& sb) {
+                  const SyncBufs& sb, const T* kron = nullptr) {
     const int k = A->k;
     const int n_items = (int)A->down_ptr[A->depth + 1];
     if (n_items == 0) return 0;
@@ -1278,7 +1369,7 @@ int backward_pass(h2_matrix* A, const T* E, T* yhat, int m, unsigned gy, unsigne
         const unsigned g = (unsigned)std::min(n_items, 152 * 6);
         k_down_fused<T, RM, CN><<<dim3(g, gy), kThreads, 0, st>>>(A->d_down_list, n_items, A->d_parent, E, yhat,
                                                                  sb.claim, sb.flag, sb.epoch, sb.err, k, m,
-                                                                 wait_limit());
+                                                                 wait_limit(), kron);
         H2_LAUNCH_CHECK();
         return 0;
     }
@@ -1307,6 +1398,8 @@ int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int
     const T* E = (const T*)D.E;
     const T* S = (const T*)D.S;
     const T* G = (const T*)D.Near;
+    // q = 4: the transfer passes apply E_c as a Kronecker product of its 1-D factors
+    const T* kron = (k == 64 && RM == 4 && A->use_kron) ? (const T*)D.kron : nullptr;
     PhaseMarks marks(A, st);
     int rc = 0;
     marks.mark();
@@ -1318,7 +1411,7 @@ int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int
     }
     marks.mark();
     const unsigned NL = (unsigned)A->leaves.size();
-    if ((rc = forward_pass<T, RM, CN>(A, V, E, Xp, xhat, m, gy, gzk, st, sb, marks))) return rc;
+    if ((rc = forward_pass<T, RM, CN>(A, V, E, Xp, xhat, m, gy, gzk, st, sb, marks, kron))) return rc;
     marks.kernel_begin();
     if (alpha_im) {
         if constexpr (CN % 2 == 0) {
@@ -1337,7 +1430,7 @@ int run_chain(h2_matrix* A, const MatData& D, double alpha, const double* X, int
     H2_LAUNCH_CHECK();
     marks.kernel_end();
     marks.mark();
-    if ((rc = backward_pass<T, RM, CN>(A, E, yhat, m, gy, gzk, st, sb))) return rc;
+    if ((rc = backward_pass<T, RM, CN>(A, E, yhat, m, gy, gzk, st, sb, kron))) return rc;
     marks.mark();
     if ((rc = wait_y_staged(A->ws, st))) return rc;
     if (alpha_im) {

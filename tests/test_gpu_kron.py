@@ -77,3 +77,18 @@ def test_kron_down_repeats_bit_for_bit(pair):
     a = _apply(G, X, np.zeros_like(X), 1.0)
     b = _apply(G, X, np.zeros_like(X), 1.0)
     assert np.array_equal(a, b), name
+
+
+@pytest.mark.parametrize("m", [3, 16, 40])
+def test_kron_fp64_passes(P, pair, m):
+    """The FP64 product's one-launch transfer passes take the Kronecker factors
+    too (against H2_KRON=0 and the oracle)."""
+    torch = require_cuda()
+    name, n, H, G, G0 = pair
+    X, Y0 = gaussian_rhs(n, m, 80 + m), gaussian_rhs(n, m, 90 + m)
+    ref = O.h2mm(H, -0.5, X, Y0)
+    for Gx in (G, G0):
+        Yd = torch.from_numpy(Y0).cuda()
+        Gx.matmul(torch.from_numpy(X).cuda(), Yd, alpha=-0.5, dtype="f64")
+        torch.cuda.synchronize()
+        assert rel_fro(Yd.cpu().numpy(), ref) <= 1e-12, (name, m)
