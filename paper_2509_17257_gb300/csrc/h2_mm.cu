@@ -698,6 +698,70 @@ __device__ __forceinline__ void pack_points(const PackOut& pk, uint8_t* tile, in
     }
 }
 
+// acc (rows 4ty.., columns 4tx.. of a 64-row block) += E_cᵀ x for q = 4, E_c =
+// F_z ⊗ F_y ⊗ F_x with the factors at f (global memory, F_a[μ][ν] row-major) and x
+// in shared memory (row stride ldx): the x mode product in the thread (its rows
+// are one x-fiber), the y and z mode products through `scratch` (64 rows of ld
+// floats, ld >= 4·(tx + 1), of shared memory free for the call).  Columns past
+// the block's read neighbouring data and give outputs nobody stores.  Every
+// thread of the CTA calls it.
+__device__ __forceinline__ void kron_own_t(float (&acc)[4][4], const float* x, int ldx, float* scratch, int ld,
+                                           const float* __restrict__ f, int tx, int ty) {
+    float F[48];
+#pragma unroll
+    for (int i = 0; i < 48; ++i) F[i] = __ldg(f + i);
+    // transposed factors: Fᵀ_a[μ][ν] = F_a[ν][μ]
+    auto Ft = [&](int a, int mu, int nu) { return F[16 * a + 4 * nu + mu]; };
+    const int my = ty & 3, mz = ty >> 2;
+    float t[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = x[(4 * ty + r) * ldx + 4 * tx + j];
+#pragma unroll
+        for (int mx = 0; mx < 4; ++mx) {
+            float a = 0.f;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a = fmaf(Ft(0, mx, r), v[r], a);
+            t[mx][j] = a;
+        }
+    }
+    __syncthreads();  // earlier users of the scratch are done
+#pragma unroll
+    for (int mx = 0; mx < 4; ++mx)
+        *(float4*)(scratch + (4 * ty + mx) * ld + 4 * tx) = make_float4(t[mx][0], t[mx][1], t[mx][2], t[mx][3]);
+    __syncthreads();
+#pragma unroll
+    for (int mx = 0; mx < 4; ++mx) {
+        float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float4 w = *(const float4*)(scratch + (mx + 4 * v + 16 * mz) * ld + 4 * tx);
+            const float c = Ft(1, my, v);
+            a[0] = fmaf(c, w.x, a[0]); a[1] = fmaf(c, w.y, a[1]); a[2] = fmaf(c, w.z, a[2]); a[3] = fmaf(c, w.w, a[3]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) t[mx][j] = a[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int mx = 0; mx < 4; ++mx)
+        *(float4*)(scratch + (4 * ty + mx) * ld + 4 * tx) = make_float4(t[mx][0], t[mx][1], t[mx][2], t[mx][3]);
+    __syncthreads();
+#pragma unroll
+    for (int mx = 0; mx < 4; ++mx)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float4 w = *(const float4*)(scratch + (mx + 4 * my + 16 * v) * ld + 4 * tx);
+            const float c = Ft(2, mz, v);
+            acc[mx][0] = fmaf(c, w.x, acc[mx][0]);
+            acc[mx][1] = fmaf(c, w.y, acc[mx][1]);
+            acc[mx][2] = fmaf(c, w.z, acc[mx][2]);
+            acc[mx][3] = fmaf(c, w.w, acc[mx][3]);
+        }
+}
+
 // Upward pass with subtree ownership (schedule: up_schedule, h2_build.cu), the
 // forward transformation of Alg. "fast_addeval" (Sec. 3): x̂_t = V_tᵀ X|_t̂ at
 // the leaves and x̂_t = E_s0ᵀ x̂_s0 + E_s1ᵀ x̂_s1 above.  A CTA claims a task and
@@ -723,7 +787,7 @@ __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ 
                                                     const float* __restrict__ E, const float* __restrict__ Xp,
                                                     float* xhat, float* part, unsigned* __restrict__ cnt,
                                                     unsigned* __restrict__ claim, int* __restrict__ err, int nent, int k,
-                                                    int m, PackOut pk, int climb) {
+                                                    int m, PackOut pk, int climb, const float* __restrict__ kron) {
     constexpr int NT = 16 * CN;
     extern __shared__ __align__(16) float fsm[];
     float* sbuf = fsm;                 // [2 slots][2][64·64]  V_c and X|_ĉ, or E_s0 and E_s1
@@ -785,6 +849,8 @@ __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ 
                 mbar_expect_tx(&bar[b], vb + xb);
                 bulk_g2s(slot(b, 0), V + (int64_t)off * k, vb, &bar[b]);
                 bulk_g2s(slot(b, 1), Xp + (int64_t)off * m, xb, &bar[b]);
+            } else if (kron) {
+                mbar_arrive(&bar[b]);  // Kronecker factors: nothing to copy, the phase completes now
             } else {
                 mbar_expect_tx(&bar[b], (uint32_t)(2 * kk * 4));
                 bulk_g2s(slot(b, 0), E + (int64_t)son0[u.c] * kk, (uint32_t)(kk * 4), &bar[b]);
@@ -814,6 +880,11 @@ __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ 
                 // X|_ĉ (in shared memory) as the leaf's split tile for the nearfield phase
                 const int64_t x0 = pk.xkoff[u.rd1];
                 pack_points(pk, pk.leafX + x0 * pk.R * pk.es, (int)(pk.xkoff[u.rd1 + 1] - x0), slot(b, 1), nt, m);
+            } else if (kron) {
+                // q = 4: E_sᵀ as Kronecker products, slot b (no E copied) as scratch
+                kron_own_t(acc, ent(u.rd0), m, slot(b, 0), NT, kron + (int64_t)son0[u.c] * 48, tx, ty);
+                kron_own_t(acc, ent(u.rd1), m, slot(b, 0), NT, kron + (int64_t)son1[u.c] * 48, tx, ty);
+                __syncthreads();  // x̂ of the father goes into its first son's entry
             } else {
                 contract44(acc, slot(b, 0), k, ent(u.rd0), m, k, tx, ty);
                 contract44(acc, slot(b, 1), k, ent(u.rd1), m, k, tx, ty);
@@ -835,8 +906,12 @@ __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ 
         // after the task's last step)
         auto fetch_e = [&](int cl) {
             if (threadIdx.x == 0) {
-                mbar_expect_tx(&bar[0], (uint32_t)(kk * 4));
-                bulk_g2s(slot(0, 0), E + (int64_t)cl * kk, (uint32_t)(kk * 4), &bar[0]);
+                if (kron) {
+                    mbar_arrive(&bar[0]);  // nothing to copy
+                } else {
+                    mbar_expect_tx(&bar[0], (uint32_t)(kk * 4));
+                    bulk_g2s(slot(0, 0), E + (int64_t)cl * kk, (uint32_t)(kk * 4), &bar[0]);
+                }
             }
         };
         if (parent[c] >= 0) fetch_e(c);
@@ -850,7 +925,8 @@ __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ 
                 break;
             }
             float pc[4][4] = {};
-            contract44(pc, slot(0, 0), k, ent(cur), m, k, tx, ty);
+            if (kron) kron_own_t(pc, ent(cur), m, slot(0, 1), NT, kron + (int64_t)c * 48, tx, ty);
+            else contract44(pc, slot(0, 0), k, ent(cur), m, k, tx, ty);
             if (colv) {
                 float* g = part + (int64_t)c * km;
 #pragma unroll
@@ -1672,9 +1748,11 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
             H2_CUDA_TRY(cudaMemsetAsync(sbc.cnt, 0, (size_t)nc * sizeof(unsigned), st));
             H2_CUDA_TRY(cudaMemsetAsync(sbc.claim, 0, sizeof(unsigned), st));
             const int climb = hybrid ? 0 : 1;
-            if (fcn == 1) k_up_own<1><<<g, 64, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, yhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk, climb);
-            else if (fcn == 2) k_up_own<2><<<g, 128, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, yhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk, climb);
-            else k_up_own<4><<<g, 256, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, yhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk, climb);
+            // q = 4: the inner steps and the climb apply E_sᵀ as Kronecker products
+            const float* ukron = (k == 64 && A->use_kron) ? (const float*)A->f32.kron : nullptr;
+            if (fcn == 1) k_up_own<1><<<g, 64, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, yhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk, climb, ukron);
+            else if (fcn == 2) k_up_own<2><<<g, 128, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, yhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk, climb, ukron);
+            else k_up_own<4><<<g, 256, usm, st>>>(A->d_up_task_ptr, A->up_ntasks, A->d_up_steps, A->d_cl_off, A->d_cl_size, A->d_parent, A->d_son0, A->d_son1, V, E, Xp, xhat, yhat, sbc.cnt, sbc.claim, sbc.err, A->up_entries, k, mc, pk, climb, ukron);
             H2_LAUNCH_CHECK();
             marks.mark();
             marks.mark();

@@ -1,11 +1,12 @@
-"""The q = 4 subtree downward pass with the transfer matrices as Kronecker
-products (E_c = F_z ⊗ F_y ⊗ F_x of 4×4 factors, the 1-D Lagrange polynomials
-of the father's nodes at the son's nodes: three 4×4 mode products per step
-instead of a 64×64 product, taken for more than 16 columns per chunk) against
-the FP64 oracle and against the dense pass (H2_KRON=0), for 4 to 96 columns
-(one and two chunks), leaves on several levels, and repeated products (bit
-for bit).  The oracle uses the dense E_c, so this also checks that tensor
-Chebyshev interpolation makes E_c exactly that product."""
+"""The q = 4 transfer passes with the transfer matrices as Kronecker products
+(E_c = F_z ⊗ F_y ⊗ F_x of 4×4 factors, the 1-D Lagrange polynomials of the
+father's nodes at the son's nodes: three 4×4 mode products instead of a
+64×64 product) against the FP64 oracle and against the dense passes
+(H2_KRON=0): the FP32 subtree passes (downward above 16 columns per chunk;
+upward inner steps and climb), the FP64 one-launch passes, for 3 to 96
+columns (one and two chunks), leaves on several levels, and repeated
+products (bit for bit).  The oracle uses the dense E_c, so this also checks
+that tensor Chebyshev interpolation makes E_c exactly that product."""
 import numpy as np
 import pytest
 
