@@ -809,17 +809,14 @@ __global__ void __launch_bounds__(64 * CN) k_up_own(const int32_t* __restrict__ 
     auto slot = [&](int b, int h) { return sbuf + (2 * b + h) * 64 * 64; };
     auto ent = [&](int e) { return stk + e * 64 * NT; };
     // acc → stack entry e, x̂_c in global memory and its split tile for the coupling phase
+    // (the tensor-core phases read only the split tiles, so x̂ is not stored in FP32)
     auto put = [&](const float (&acc)[4][4], int e, int c) {
         pack_rows(pk, pk.act + (int64_t)c * pk.KP * pk.R * pk.es, acc, tx, ty, k, m);
         if (!colv) return;
         float* out = ent(e);
-        float* g = xhat + (int64_t)c * km;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float4 v = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-            *(float4*)(out + (4 * ty + r) * m + 4 * tx) = v;
-            if (4 * ty + r < k) *(float4*)(g + (4 * ty + r) * m + 4 * tx) = v;
-        }
+        for (int r = 0; r < 4; ++r)
+            *(float4*)(out + (4 * ty + r) * m + 4 * tx) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
     };
     auto wait_slot = [&](int b) {
         const bool ok = mbar_wait(&bar[b], (phase >> b) & 1u);
@@ -1122,10 +1119,9 @@ __global__ void __launch_bounds__(128) k_down_own(const int32_t* __restrict__ ta
                         *(float2*)(out + (m0 + g + 8 * h) * LDY + 8 * nt + 2 * t) =
                             make_float2(ccur[nt][2 * h], ccur[nt][2 * h + 1]);
                 if (d.flags & kDownStore) {
-                    // a leaf: ŷ_c to global memory and into its split tile, read back
+                    // a leaf: ŷ_c into its split tile (what the leaf phase reads), read back
                     // from the stack entry in 4×4 blocks
                     __syncthreads();
-                    float* gout = yhat + (int64_t)d.c * km;
                     uint8_t* tile = pk.act + (int64_t)d.c * pk.KP * pk.R * pk.es;
                     for (int blk = threadIdx.x; blk < 16 * (NT / 4); blk += blockDim.x) {
                         const int ty = blk / (NT / 4), tx = blk % (NT / 4);
@@ -1134,7 +1130,6 @@ __global__ void __launch_bounds__(128) k_down_own(const int32_t* __restrict__ ta
                         for (int r = 0; r < 4; ++r) {
                             const float4 v = *(const float4*)(out + (4 * ty + r) * LDY + 4 * tx);
                             acc[r][0] = v.x; acc[r][1] = v.y; acc[r][2] = v.z; acc[r][3] = v.w;
-                            if (4 * ty + r < k && 4 * tx < m) *(float4*)(gout + (4 * ty + r) * m + 4 * tx) = v;
                         }
                         pack_rows(pk, tile, acc, tx, ty, k, m);
                     }
@@ -1306,8 +1301,7 @@ __global__ void __launch_bounds__(128) k_down_kron(const int32_t* __restrict__ t
             }
             __syncthreads();  // entry wr complete
             if (d.flags & kDownStore) {
-                // a leaf: ŷ_c to global memory and into its split tile, read back in 4×4 blocks
-                float* gout = yhat + (int64_t)d.c * km;
+                // a leaf: ŷ_c into its split tile (what the leaf phase reads), read back in 4×4 blocks
                 uint8_t* tile = pk.act + (int64_t)d.c * pk.KP * pk.R * pk.es;
                 for (int blk = threadIdx.x; blk < 16 * (NT / 4); blk += blockDim.x) {
                     const int ty = blk / (NT / 4), tx = blk % (NT / 4);
@@ -1316,7 +1310,6 @@ __global__ void __launch_bounds__(128) k_down_kron(const int32_t* __restrict__ t
                     for (int r = 0; r < 4; ++r) {
                         const float4 v = *(const float4*)(out + (4 * ty + r) * LDY + 4 * tx);
                         acc[r][0] = v.x; acc[r][1] = v.y; acc[r][2] = v.z; acc[r][3] = v.w;
-                        if (4 * tx < m) *(float4*)(gout + (4 * ty + r) * m + 4 * tx) = v;
                     }
                     pack_rows(pk, tile, acc, tx, ty, k, m);
                 }
