@@ -127,6 +127,20 @@ typedef struct h2_info_t {
     int64_t n_above_cut;  /* clusters above that cut (transfer items of that launch)      */
 } h2_info_t;
 
+/* Environment variables read by the library (none is needed; each forces one
+ * choice of the built-in rules or of h2_autotune_ex, for comparisons and tests):
+ *   read by h2_build for that matrix:
+ *     H2_FORCE_SIMT=1        FP32 products on the CUDA cores only
+ *     H2_TC_TRANSFER=0|1     FP32 transfer passes on the CUDA cores / the tensor cores
+ *     H2_TC_HYBRID=0|1       the hybrid upward pass off / on
+ *     H2_KRON=0              q = 4 transfer passes on the dense transfer matrices
+ *     H2_HYBRID_ROUND_TERMS  coupling terms per CTA between two heights of the hybrid
+ *                            pass's transfer items (1..64, default 16)
+ *   read by h2_batch_create for that batch:
+ *     H2_BATCH_MULTI=0       batched FP32 products as per-system graph branches
+ *   read by each solve:
+ *     H2_CG_TRACE=k          block CG prints its largest residual every k checks */
+
 /* Build A from n points (pts: n×3 row-major doubles, host or device).  On
  * success *out owns all device memory of the matrix.  The call synchronises
  * params->stream before returning.  Errors: H2_E_BADARG (n < 1, bad params,
