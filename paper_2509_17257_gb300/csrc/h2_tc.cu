@@ -374,6 +374,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
         uint32_t phase = 0;
         uint32_t pend_mask = 0, pend_par = 0;
         bool aborted = false;
+        const uint64_t pol_keep = l2_policy_evict_last(), pol_stream = l2_policy_evict_first();
         // an item's system: its terms, buffers and sizes (PSYS reads a field of the
         // system table of a multi-system launch, else of the launch's own arguments)
 #define PSYS(it_, f_) ((FLOW && p.sys) ? p.sys[item_sys(it_)].f_ : p.f_)
@@ -449,8 +450,9 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                                 mbar_expect_tx(&full_bar[stage], ab + bb);
                                 const uint8_t* asrc = (asj & 3) == 0 ? PSYS(cur, act0)
                                                                      : ((asj & 3) == 1 ? PSYS(cur, act1) : PSYS(cur, act2));
-                                bulk_g2s(sA, asrc + aj, ab, &full_bar[stage]);
-                                bulk_g2s(sB, PSYS(cur, bmat) + bj * (ES / 2), bb, &full_bar[stage]);
+                                // the activation tiles are read by many terms, the matrix tiles once
+                                bulk_g2s_hint(sA, asrc + aj, ab, &full_bar[stage], pol_keep);
+                                bulk_g2s_hint(sB, PSYS(cur, bmat) + bj * (ES / 2), bb, &full_bar[stage], pol_stream);
                             }
                             pend_mask |= 1u << stage;
                             pend_par = (pend_par & ~(1u << stage)) | (phase << stage);
