@@ -932,16 +932,20 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 if (ok && !end) {
                     const bool rv = n < p.k;
                     const float4 xt = p.nodes[(int64_t)stage_t[stage] * p.KP + (rv ? n : 0)];
-                    const float4* xs = p.nodes + (int64_t)stage_s[stage] * p.KP;
                     const int mu0 = lo_part ? 32 : 0;
+                    // the warp's 32 source nodes: one coalesced load (lane l holds node
+                    // mu0 + l), handed to every lane by shuffles
+                    const float4 ys = mu0 + lane < p.KP ? p.nodes[(int64_t)stage_s[stage] * p.KP + mu0 + lane]
+                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
                     const float sc = -p.inv_len * 1.4426950408889634f;
 #pragma unroll 8
                     for (int j = 0; j < 32; ++j) {
                         const int mu = mu0 + j;
+                        const float y0 = __shfl_sync(0xffffffffu, ys.x, j), y1 = __shfl_sync(0xffffffffu, ys.y, j),
+                                    y2 = __shfl_sync(0xffffffffu, ys.z, j);
                         float g = 0.f;
                         if (rv && mu < p.k) {
-                            const float4 y = xs[mu];
-                            const float d0 = xt.x - y.x, d1 = xt.y - y.y, d2 = xt.z - y.z;
+                            const float d0 = xt.x - y0, d1 = xt.y - y1, d2 = xt.z - y2;
                             const float r2 = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
                             const float e = r2 * rsqrtf(r2) * sc;
                             asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(e));
