@@ -257,6 +257,47 @@ void snake_order(std::vector<TcItem>& v, int G) {
     v.swap(out);
 }
 
+// A term's fixed cost in the balance of the tensor-core work lists, in units of
+// tile elements (a full 64×64 tile adds a third of it): a term's copies and
+// hand-offs take nearly as long whatever its tile's size.
+constexpr int64_t kTermFixedCost = 3 * 64 * 64;
+
+// Lays the items out for a launch of G CTAs, where position r·G + c runs on
+// CTA c: the items, largest first, are dealt round by round, each round's
+// largest to the CTA with the least work so far; the CTAs that receive an item
+// in the last, partial round are numbered first.
+template <class Cost>
+void balance_order(std::vector<TcItem>& v, Cost cost, int G) {
+    const size_t n = v.size();
+    if (G < 2 || n <= (size_t)G) return;
+    std::stable_sort(v.begin(), v.end(), [&](const TcItem& a, const TcItem& b) { return cost(a) > cost(b); });
+    const size_t rounds = (n + G - 1) / G;
+    std::vector<int64_t> load(G, 0);
+    std::vector<std::vector<TcItem>> per(G);
+    std::vector<int> idx(G);
+    for (size_t r = 0; r < rounds; ++r) {
+        for (int c = 0; c < G; ++c) idx[c] = c;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return load[a] < load[b]; });
+        const size_t i0 = r * G, i1 = std::min(n, i0 + G);
+        for (size_t i = i0; i < i1; ++i) {
+            const int c = idx[i - i0];
+            per[c].push_back(v[i]);
+            load[c] += cost(v[i]);
+        }
+    }
+    std::vector<int> order;
+    for (int c = 0; c < G; ++c)
+        if (per[c].size() == rounds) order.push_back(c);
+    for (int c = 0; c < G; ++c)
+        if (per[c].size() < rounds) order.push_back(c);
+    std::vector<TcItem> out;
+    out.reserve(n);
+    for (size_t r = 0; r < rounds; ++r)
+        for (int c = 0; c < G; ++c)
+            if (per[order[c]].size() > r) out.push_back(per[order[c]][r]);
+    v.swap(out);
+}
+
 int cast_copy(h2_matrix* A, const double* src, void** dst, int64_t count, cudaStream_t st) {
     int rc = device_alloc(A, dst, (size_t)(count > 0 ? count : 1) * sizeof(float));
     if (rc) return rc;
@@ -1116,10 +1157,8 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
         if (e1 > e0) c_items.push_back(TcItem{(int32_t)c, tpb * e0, tpb * e1, NP});
         else c_zero.push_back((int32_t)c);
     }
-    // longest lists first, dealt to the CTAs in snake order
-    std::stable_sort(c_items.begin(), c_items.end(),
-                     [](const TcItem& a, const TcItem& b) { return a.e1 - a.e0 > b.e1 - b.e0; });
-    snake_order(c_items, kTcGrid);
+    // longest lists first, each to the CTA with the least work so far
+    balance_order(c_items, [](const TcItem& a) { return (int64_t)(a.e1 - a.e0); }, kTcGrid);
     // ---- leaf schedule: outputs = leaf positions; terms = V_t ŷ_t, then G_b X|_ŝ ----
     std::vector<int64_t> xkoff(NL + 1, 0);
     std::vector<int32_t> leaf_base(NL), leaf_kdim(NL);
@@ -1138,23 +1177,21 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
             const int32_t t = A->leaves[lp];
             const int32_t e0 = (int32_t)l_terms.size();
             l_terms.push_back(TcTerm{v_off[lp], (int32_t)((int64_t)t * KP), (int16_t)KP, (int16_t)1});
-            l_cost[lp] += (int64_t)l_np[lp] * KP;
+            l_cost[lp] += kTermFixedCost + (int64_t)l_np[lp] * KP;
             for (int64_t e = T.near_rowptr[t]; e < T.near_rowptr[t + 1]; ++e, ++j) {
                 const int32_t sc = T.near_col[e];
                 const int kps = round16((int)T.size[sc]);
                 l_terms.push_back(TcTerm{g_off[j], (int32_t)xkoff[leaf_pos[sc]], (int16_t)kps, (int16_t)0});
-                l_cost[lp] += (int64_t)l_np[lp] * kps;
+                l_cost[lp] += kTermFixedCost + (int64_t)l_np[lp] * kps;
                 if (A->cplx) {  // G_im·(i·X|_ŝ)
                     l_terms.push_back(TcTerm{gi_off[j], (int32_t)xkoff[leaf_pos[sc]], (int16_t)kps, kTermImag});
-                    l_cost[lp] += (int64_t)l_np[lp] * kps;
+                    l_cost[lp] += kTermFixedCost + (int64_t)l_np[lp] * kps;
                 }
             }
             l_items[lp] = TcItem{(int32_t)lp, e0, (int32_t)l_terms.size(), l_np[lp]};
         }
     }
-    std::stable_sort(l_items.begin(), l_items.end(),
-                     [&](const TcItem& a, const TcItem& b) { return l_cost[a.id] > l_cost[b.id]; });
-    snake_order(l_items, kTcGrid);
+    balance_order(l_items, [&](const TcItem& a) { return l_cost[a.id]; }, kTcGrid);
     if (flow) {
         if ((rc = flow_lists(A, ft, s_off, v_off, g_off, xkoff, st))) return rc;
         D.s_off_host = s_off;
@@ -1265,9 +1302,7 @@ int build_tc_transposed(h2_matrix* A, cudaStream_t st) {
             else c_zero.push_back((int32_t)sc);
         }
     }
-    std::stable_sort(c_items.begin(), c_items.end(),
-                     [](const TcItem& a, const TcItem& b) { return a.e1 - a.e0 > b.e1 - b.e0; });
-    snake_order(c_items, kTcGrid);
+    balance_order(c_items, [](const TcItem& a) { return (int64_t)(a.e1 - a.e0); }, kTcGrid);
     // ---- leaf list over column leaves: item s, terms V_s ŷ_s, then G_bᵀ x|_t̂ ----
     std::vector<int64_t> xkoff(NL + 1, 0);
     for (int64_t lp = 0; lp < NL; ++lp) xkoff[lp + 1] = xkoff[lp] + round16((int)T.size[A->leaves[lp]]);
@@ -1281,18 +1316,16 @@ int build_tc_transposed(h2_matrix* A, cudaStream_t st) {
         const int np = round16((int)T.size[sc]);
         const int32_t e0 = (int32_t)l_terms.size();
         l_terms.push_back(TcTerm{v_off[lp], (int32_t)((int64_t)sc * KP), (int16_t)KP, (int16_t)1});
-        l_cost[lp] += (int64_t)np * KP;
+        l_cost[lp] += kTermFixedCost + (int64_t)np * KP;
         for (int64_t j : near_by_col[lp]) {
             const int32_t t = near_t[j];
             const int kpt = round16((int)T.size[t]);
             l_terms.push_back(TcTerm{g_off[j], (int32_t)xkoff[leaf_pos[t]], (int16_t)kpt, (int16_t)0});
-            l_cost[lp] += (int64_t)np * kpt;
+            l_cost[lp] += kTermFixedCost + (int64_t)np * kpt;
         }
         l_items[lp] = TcItem{(int32_t)lp, e0, (int32_t)l_terms.size(), np};
     }
-    std::stable_sort(l_items.begin(), l_items.end(),
-                     [&](const TcItem& a, const TcItem& b) { return l_cost[a.id] > l_cost[b.id]; });
-    snake_order(l_items, kTcGrid);
+    balance_order(l_items, [&](const TcItem& a) { return l_cost[a.id]; }, kTcGrid);
     D.ct_nitems = (int)c_items.size();
     D.ct_nzero = (int)c_zero.size();
     D.lt_nitems = (int)NL;
