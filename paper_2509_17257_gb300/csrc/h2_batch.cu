@@ -410,7 +410,7 @@ int h2_autotune_ex(h2_matrix* A, int64_t m, int32_t dtype, void* stream, h2_tune
         trial(Tune{kPathTcFlow, 0}, keep_up, keep_down);
         trial(Tune{kPathTcFused, 0}, keep_up, keep_down);
     }
-    if (dtype == H2_F32 && A->tc.hybrid) trial(Tune{kPathTcHybrid, 0}, keep_up, keep_down);
+    if (dtype == H2_F32 ? A->tc.hybrid : A->tc.hybrid_bf16) trial(Tune{kPathTcHybrid, 0}, keep_up, keep_down);
     if (dtype == H2_F32) trial(Tune{kPathSimt, 0}, keep_up, keep_down);
     // 2. the stage count of the tensor-core kernels on the best path
     if (!rc && best_t.path != kPathSimt)

@@ -921,7 +921,7 @@ int flow_lists(h2_matrix* A, const FlowTiles& ft, const std::vector<int64_t>& s_
     return 0;
 }
 
-// The coupling launch of the hybrid upward pass (k_tc_gemm<4, 1>).  The CUDA-core
+// The coupling launch of the hybrid upward pass (k_tc_gemm<4, KIND>).  The CUDA-core
 // subtree pass (k_up_own without its climb) computes every cluster at or below
 // the cut level up_cut (and the leaves above it); the clusters above the cut,
 // x̂_t = E_s0ᵀ x̂_s0 + E_s1ᵀ x̂_s1 (Alg. "forward/backward"), become transfer items
@@ -954,8 +954,13 @@ int hybrid_lists(h2_matrix* A, cudaStream_t st) {
     const int KP = D.KP, NP = D.NP;
     const int64_t nc = A->nc;
     D.hybrid = false;
+    D.hybrid_bf16 = false;
     D.h_default = false;
-    if (!D.flow || D.s_off_host.size() != (size_t)A->n_adm || D.et_off_host.size() != (size_t)nc) return 0;
+    // FP32 lists: the Eᵀ tiles of the tensor-core transfer passes; BF16 lists: the
+    // split BF16 Eᵀ tiles
+    const bool f32 = D.flow && D.et_off_host.size() == (size_t)nc;
+    const bool b16 = D.ebh_off_host.size() == (size_t)nc && D.ebl_off_host.size() == (size_t)nc;
+    if ((!f32 && !b16) || D.s_off_host.size() != (size_t)A->n_adm) return 0;
     // height above the cut: 0 for clusters at or below it and for leaves above it
     std::vector<int32_t> h(nc, 0);
     int32_t H = 0;
@@ -966,70 +971,89 @@ int hybrid_lists(h2_matrix* A, cudaStream_t st) {
         }
     const int16_t kWait = (int16_t)(0 | kTermWait);
     auto np_role = [](int np, int32_t role) { return (int32_t)(np | (role << 16)); };
-    std::vector<TcTerm> terms;
-    std::vector<KeyedItem> keyed;
-    for (int64_t c = 0; c < nc; ++c) {
-        if (h[c] == 0) continue;
-        const int32_t e0 = (int32_t)terms.size();
-        for (int32_t s : {T.son0[c], T.son1[c]})
-            terms.push_back(TcTerm{D.et_off_host[s], (int32_t)((int64_t)s * KP), (int16_t)KP,
-                                   h[s] > 0 ? kWait : (int16_t)0});
-        keyed.push_back(KeyedItem{2 * h[c] - 1, TcItem{(int32_t)c, e0, (int32_t)terms.size(), np_role(NP, kRoleTransfer)}});
-    }
-    struct Free {
-        int64_t cost;
-        TcItem it;
-        int32_t hs;  // largest height above the cut among the sources
-    };
-    std::vector<Free> free_items, late;
-    for (int64_t c = 0; c < nc; ++c) {
-        const int64_t j0 = T.adm_rowptr[c], j1 = T.adm_rowptr[c + 1];
-        if (j1 == j0) continue;
-        const int32_t e0 = (int32_t)terms.size();
-        int32_t hs = 0;
-        for (int64_t j = j0; j < j1; ++j) {
-            const int32_t sc = T.adm_col[j];
-            hs = std::max(hs, h[sc]);
-            terms.push_back(TcTerm{D.s_off_host[j], (int32_t)((int64_t)sc * KP), (int16_t)KP,
-                                   h[sc] > 0 ? kWait : (int16_t)0});
-        }
-        const TcItem it{(int32_t)c, e0, (int32_t)terms.size(), np_role(NP, 0)};
-        if (hs > 0) late.push_back(Free{j1 - j0, it, hs});
-        else free_items.push_back(Free{j1 - j0, it, 0});
-    }
-    // smallest first into the rounds, each round up to kHybridRoundTerms terms per CTA
-    std::stable_sort(free_items.begin(), free_items.end(), [](const Free& a, const Free& b) { return a.cost < b.cost; });
     int round_terms = kHybridRoundTerms;
     if (const char* e = getenv("H2_HYBRID_ROUND_TERMS")) round_terms = std::min(64, std::max(1, atoi(e)));
-    const int64_t budget = (int64_t)round_terms * kTcGrid;
-    size_t i = 0;
-    for (int32_t r = 0; r < H; ++r) {
-        int64_t used = 0;
-        while (i < free_items.size() && used + free_items[i].cost <= budget) {
-            used += free_items[i].cost;
-            keyed.push_back(KeyedItem{2 * r, free_items[i++].it});
+    int64_t free_terms = 0;
+    // The list of one kind: transfer terms E_sᵀ x̂_s from the tiles et (and, BF16, the
+    // remainder tiles etl as a second term per son).
+    auto build = [&](const std::vector<int64_t>& et, const std::vector<int64_t>* etl, TcItem** d_items,
+                     TcTerm** d_terms, int* n_items) -> int {
+        std::vector<TcTerm> terms;
+        std::vector<KeyedItem> keyed;
+        for (int64_t c = 0; c < nc; ++c) {
+            if (h[c] == 0) continue;
+            const int32_t e0 = (int32_t)terms.size();
+            for (int32_t s : {T.son0[c], T.son1[c]}) {
+                const int16_t w = h[s] > 0 ? kWait : (int16_t)0;
+                terms.push_back(TcTerm{et[s], (int32_t)((int64_t)s * KP), (int16_t)KP, w});
+                if (etl) terms.push_back(TcTerm{(*etl)[s], (int32_t)((int64_t)s * KP), (int16_t)KP, w});
+            }
+            keyed.push_back(
+                KeyedItem{2 * h[c] - 1, TcItem{(int32_t)c, e0, (int32_t)terms.size(), np_role(NP, kRoleTransfer)}});
         }
-    }
-    // the rest, and the coupling items that read clusters above the cut: largest
-    // first (snake-dealt within the key)
-    std::vector<Free> rest(free_items.begin() + (long)i, free_items.end());
-    rest.insert(rest.end(), late.begin(), late.end());
-    std::stable_sort(rest.begin(), rest.end(), [](const Free& a, const Free& b) { return a.cost > b.cost; });
-    for (const Free& f : rest) keyed.push_back(KeyedItem{f.hs > H - 3 ? 2 * H + 1 : 2 * H, f.it});
-    std::vector<TcItem> items;
-    order_by_key(keyed, items);
-    release_allocation(A, D.h_items);
-    release_allocation(A, D.h_terms);
-    D.h_items = nullptr;
-    D.h_terms = nullptr;
+        struct Free {
+            int64_t cost;
+            TcItem it;
+            int32_t hs;  // largest height above the cut among the sources
+        };
+        std::vector<Free> free_items, late;
+        for (int64_t c = 0; c < nc; ++c) {
+            const int64_t j0 = T.adm_rowptr[c], j1 = T.adm_rowptr[c + 1];
+            if (j1 == j0) continue;
+            const int32_t e0 = (int32_t)terms.size();
+            int32_t hs = 0;
+            for (int64_t j = j0; j < j1; ++j) {
+                const int32_t sc = T.adm_col[j];
+                hs = std::max(hs, h[sc]);
+                terms.push_back(TcTerm{D.s_off_host[j], (int32_t)((int64_t)sc * KP), (int16_t)KP,
+                                       h[sc] > 0 ? kWait : (int16_t)0});
+            }
+            const TcItem it{(int32_t)c, e0, (int32_t)terms.size(), np_role(NP, 0)};
+            if (hs > 0) late.push_back(Free{j1 - j0, it, hs});
+            else free_items.push_back(Free{j1 - j0, it, 0});
+        }
+        // smallest first into the rounds, each round up to kHybridRoundTerms terms per CTA
+        std::stable_sort(free_items.begin(), free_items.end(),
+                         [](const Free& a, const Free& b) { return a.cost < b.cost; });
+        const int64_t budget = (int64_t)round_terms * kTcGrid;
+        size_t i = 0;
+        for (int32_t r = 0; r < H; ++r) {
+            int64_t used = 0;
+            while (i < free_items.size() && used + free_items[i].cost <= budget) {
+                used += free_items[i].cost;
+                keyed.push_back(KeyedItem{2 * r, free_items[i++].it});
+            }
+        }
+        // the rest, and the coupling items that read clusters above the cut: largest
+        // first (snake-dealt within the key)
+        std::vector<Free> rest(free_items.begin() + (long)i, free_items.end());
+        rest.insert(rest.end(), late.begin(), late.end());
+        std::stable_sort(rest.begin(), rest.end(), [](const Free& a, const Free& b) { return a.cost > b.cost; });
+        for (const Free& f : rest) keyed.push_back(KeyedItem{f.hs > H - 3 ? 2 * H + 1 : 2 * H, f.it});
+        std::vector<TcItem> items;
+        order_by_key(keyed, items);
+        release_allocation(A, *d_items);
+        release_allocation(A, *d_terms);
+        *d_items = nullptr;
+        *d_terms = nullptr;
+        int rc = 0;
+        if ((rc = upload(A, d_items, items, st)) || (rc = upload(A, d_terms, terms, st))) return rc;
+        *n_items = (int)items.size();
+        free_terms = 0;
+        for (const Free& f : free_items) free_terms += f.cost;
+        return 0;
+    };
     int rc = 0;
-    if ((rc = upload(A, &D.h_items, items, st)) || (rc = upload(A, &D.h_terms, terms, st))) return rc;
-    D.h_nitems = (int)items.size();
-    D.hybrid = true;
+    if (f32) {
+        if ((rc = build(D.et_off_host, nullptr, &D.h_items, &D.h_terms, &D.h_nitems))) return rc;
+        D.hybrid = true;
+    }
+    if (b16) {
+        if ((rc = build(D.ebh_off_host, &D.ebl_off_host, &D.hb_items, &D.hb_terms, &D.hb_nitems))) return rc;
+        D.hybrid_bf16 = true;
+    }
     D.h_nabove = 0;
     for (int64_t c = 0; c < nc; ++c) D.h_nabove += h[c] > 0;
-    int64_t free_terms = 0;
-    for (const Free& f : free_items) free_terms += f.cost;
     D.h_default = free_terms >= (int64_t)kHybridTermsPerHeight * H * kTcGrid;
     return 0;
 }
@@ -1106,6 +1130,22 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     const bool flow = tf32 && k <= 64 && T.leaf_size <= 64 && !A->cplx;
     if (flow) flow_tiles(A, tiles, off, ft);
     const int64_t off32 = off;
+    // the BF16 hybrid lists' Eᵀ_c tiles (high part, then remainder) after the BF16
+    // tiles of S, V and G, in the BF16 copy only
+    std::vector<TcPackTile> tilesE;
+    int64_t off16 = D.bytes;
+    D.ebh_off_host.clear();
+    D.ebl_off_host.clear();
+    if (bf16 && k <= 64 && T.leaf_size <= 64 && !A->cplx && nc > 1) {
+        D.ebh_off_host.assign(nc, -1);
+        D.ebl_off_host.assign(nc, -1);
+        for (int64_t c = 1; c < nc; ++c)
+            for (int lo = 0; lo < 2; ++lo) {
+                (lo ? D.ebl_off_host : D.ebh_off_host)[c] = off16;
+                tilesE.push_back(TcPackTile{c * k * k, off16, k, k, k, NP, KP, 1 | (lo << 1)});  // row ν, column μ
+                off16 += (int64_t)NP * KP * 2;
+            }
+    }
     int rc = 0;
     TcPackTile* d_tiles = nullptr;
     if ((rc = upload(A, &d_tiles, tiles, st))) return rc;
@@ -1114,7 +1154,7 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
     for (int es = 2; es <= 4; es += 2) {
         if ((es == 2 && !bf16) || (es == 4 && !tf32)) continue;
         void* pm = nullptr;
-        const int64_t total = es == 4 ? off32 : D.bytes;
+        const int64_t total = es == 4 ? off32 : off16;
         if ((rc = device_alloc(A, &pm, (size_t)std::max<int64_t>(total * (es / 2), 128)))) return rc;
         uint8_t* dst = (uint8_t*)pm;
         if ((rc = launch_pack_tiles(d_tiles, nS, (const double*)A->f64.S, dst, es, st))) return rc;
@@ -1129,6 +1169,12 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
                 return rc;
             H2_CUDA_TRY(cudaMemcpyAsync(dst + ft.id_off * 2, ft.ident.data(), ft.ident.size() * sizeof(float),
                                         cudaMemcpyHostToDevice, st));
+        }
+        if (es == 2 && !tilesE.empty()) {
+            TcPackTile* d_tilesE = nullptr;
+            if ((rc = upload(A, &d_tilesE, tilesE, st))) return rc;
+            if ((rc = launch_pack_tiles(d_tilesE, (int64_t)tilesE.size(), (const double*)A->f64.E, dst, es, st)))
+                return rc;
         }
         if (es == 2) D.mat = dst; else D.mat32 = dst;
     }
@@ -1192,12 +1238,13 @@ int build_tc(h2_matrix* A, bool bf16, bool tf32, cudaStream_t st) {
         }
     }
     balance_order(l_items, [&](const TcItem& a) { return l_cost[a.id]; }, kTcGrid);
+    D.s_off_host = s_off;
+    D.et_off_host.clear();
     if (flow) {
         if ((rc = flow_lists(A, ft, s_off, v_off, g_off, xkoff, st))) return rc;
-        D.s_off_host = s_off;
         D.et_off_host = ft.et_off;
-        if ((rc = hybrid_lists(A, st))) return rc;
     }
+    if ((rc = hybrid_lists(A, st))) return rc;
     D.xk_total = xkoff[NL];
     D.c_nitems = (int)c_items.size();
     D.c_nzero = (int)c_zero.size();
@@ -1381,7 +1428,7 @@ int set_transfer_targets(h2_matrix* A, int up_target, int down_target, cudaStrea
     A->down_target = down_target;
     const bool cut_moved = up_cut != A->up_cut;
     A->up_cut = up_cut;
-    if (cut_moved && A->tc.flow) return hybrid_lists(A, st);
+    if (cut_moved && A->tc.built) return hybrid_lists(A, st);
     return 0;
 }
 

@@ -70,7 +70,8 @@ struct Timing {
 struct TcPackTile {
     int64_t src, dst;
     int32_t n, k, ld, np, kp;
-    int32_t tr;  // 1: the tile holds the transpose, row r column c = src[c·ld + r]
+    int32_t tr;  // bit 0: the tile holds the transpose, row r column c = src[c·ld + r];
+                 // bit 1 (BF16): the remainder v - bf16(v) instead of v
 };
 
 // One output tile of the tcgen05 segmented GEMM: output id, its terms
@@ -231,6 +232,14 @@ struct TcData {
     TcTerm* h_terms = nullptr;
     int h_nitems = 0;
     std::vector<int64_t> s_off_host, et_off_host;  // tile offsets of S_j and of Eᵀ_c in mat32 (elements)
+    // The BF16 product's hybrid lists (k_tc_gemm<4, 0>): Eᵀ_c as two BF16 tiles, its
+    // high part and the remainder (after the BF16 tiles of S, V and G in mat), so
+    // the transfer items lose no accuracy to the rounding of E; two terms per son.
+    bool hybrid_bf16 = false;
+    TcItem* hb_items = nullptr;
+    TcTerm* hb_terms = nullptr;
+    int hb_nitems = 0;
+    std::vector<int64_t> ebh_off_host, ebl_off_host;  // Eᵀ_c high and low tiles in mat (bytes)
 };
 
 // Inter-CTA bookkeeping of the one-launch transfer passes: arrival counters of

@@ -1588,11 +1588,12 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         const bool capturing = stream_capture_active(st);
         const bool flow = kind == 1 && D.flow && want_flow && !capturing && !cx;
         // hybrid: the subtree passes stop at the upward cut, and the clusters above it
-        // are transfer items of the coupling launch (k_tc_gemm<4, 1>), which waits for
-        // them only where a coupling reads them
+        // are transfer items of the coupling launch (k_tc_gemm<4, KIND>), which waits
+        // for them only where a coupling reads them
         bool want_hybrid = tn.path == kPathTcHybrid || (tn.path == kPathDefault && D.h_default);
         if (A->use_hybrid >= 0) want_hybrid = A->use_hybrid == 1;
-        const bool hybrid = kind == 1 && fast && !flow && !trans && !mf && !cx && D.hybrid && want_hybrid && !capturing;
+        const bool lists = kind == 1 ? D.hybrid : D.hybrid_bf16;
+        const bool hybrid = fast && !flow && !trans && !mf && !cx && lists && want_hybrid && !capturing;
         int rc = ensure_workspace(A, bXp + 2 * bC + bXcm + 3 * bAct, st);
         if (rc) return rc;
         char* base = (char*)A->ws.base;
@@ -1779,9 +1780,9 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         cp.KP = KP;
         cp.cplx = cx ? 1 : 0;
         if (hybrid) {
-            cp.n_items = D.h_nitems;
-            cp.items = D.h_items;
-            cp.terms = D.h_terms;
+            cp.n_items = kind == 1 ? D.h_nitems : D.hb_nitems;
+            cp.items = kind == 1 ? D.h_items : D.hb_items;
+            cp.terms = kind == 1 ? D.h_terms : D.hb_terms;
             cp.out_act = xcm;  // the transfer items' split tiles
             cp.flag = sbc.fflag;
             cp.epoch = 1;

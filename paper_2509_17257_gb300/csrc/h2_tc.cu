@@ -207,11 +207,16 @@ __global__ void k_pack_tiles(const TcPackTile* __restrict__ tiles, int64_t count
         uint8_t* base = dst + d.dst * (es / 2);
         for (int e = threadIdx.x; e < d.np * d.kp; e += blockDim.x) {
             const int r = e / d.kp, c = e % d.kp;
-            const double v = (r < d.n && c < d.k)
-                                 ? src[d.src + (d.tr ? (int64_t)c * d.ld + r : (int64_t)r * d.ld + c)]
-                                 : 0.0;
-            if (es == 2) *(__nv_bfloat16*)(base + cm_off(r, c, d.kp, 2)) = __double2bfloat16(v);
-            else *(float*)(base + cm_off(r, c, d.kp, 4)) = (float)v;
+            double v = (r < d.n && c < d.k)
+                           ? src[d.src + ((d.tr & 1) ? (int64_t)c * d.ld + r : (int64_t)r * d.ld + c)]
+                           : 0.0;
+            if (es == 2) {
+                __nv_bfloat16 b = __double2bfloat16(v);
+                if (d.tr & 2) b = __double2bfloat16(v - (double)__bfloat162float(b));
+                *(__nv_bfloat16*)(base + cm_off(r, c, d.kp, 2)) = b;
+            } else {
+                *(float*)(base + cm_off(r, c, d.kp, 4)) = (float)v;
+            }
         }
     }
 }
@@ -872,12 +877,50 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acce_bar[acc]);
             }
-            if (failed) {
+            if (LIST && item_role(cur) == kRoleTransfer) {
+                // A transfer item of the hybrid upward pass: x̂ of the cluster as a
+                // split BF16 tile (row 2i: bf16(v), row 2i + 1: bf16(v - bf16(v)); rows
+                // of columns i >= mc get zero sums, as their activation rows are zero),
+                // stored by the even-row threads, ordered for the bulk copies of other
+                // CTAs by a proxy fence, and released by the ready flag once all four
+                // warps have stored.  Every epilogue warp meets the barrier once per
+                // transfer item, failed or not, and all of them learn of a failure.
+                if (bar_red_or(1, 128, failed)) {
+                    if (lane == 0) atomicExch(p.err, 6);
+                    abort_flag = 1;
+                    break;
+                }
+                if (row >= 0 && !(row & 1) && i < R / 2) {
+                    uint8_t* gt = p.out_act + (int64_t)id * p.KP * R * 2;
+#pragma unroll
+                    for (int u = 0; u < kAccCols / 8; ++u) {
+                        if (8 * u >= p.KP) break;
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float v0 = 8 * u + 2 * e < p.k ? sum[8 * u + 2 * e] : 0.f;
+                            const float v1 = 8 * u + 2 * e + 1 < p.k ? sum[8 * u + 2 * e + 1] : 0.f;
+                            const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+                            const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+                            const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+                            hw[e] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                            lw[e] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                        }
+                        *(uint4*)(gt + cm_off(2 * i, 8 * u, p.KP, 2)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *(uint4*)(gt + cm_off(2 * i + 1, 8 * u, p.KP, 2)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                    fence_proxy_async_global();
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (warp == 2 && lane == 0) {
+                    __threadfence();
+                    flag_release(p.flag + id, p.epoch);
+                }
+            } else if (failed) {
                 if (lane == 0) atomicExch(p.err, 6);
                 abort_flag = 1;
                 break;
-            }
-            if (writer) {
+            } else if (writer) {
                 if (MODE != 1) {
                     float* out = p.yhat + (int64_t)id * p.k * p.ldc;
 #pragma unroll
@@ -1063,6 +1106,7 @@ int tc_prepare() {
     H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     g_tc_attr_device = dev;
     return 0;
 }
@@ -1092,10 +1136,8 @@ int launch_tc_gemm(int mode, int kind, TcGemmParams p, int grid, cudaStream_t st
         // of the device, so that every CTA is resident (the waits are bounded in any case)
         return launch_one<3, 1>(p, grid, smem, st);
     }
-    if (mode == 4) {
-        if (kind != 1) { set_error("the coupling launch with transfer items runs on the TF32 path only"); return H2_E_UNSUPPORTED; }
-        return launch_one<4, 1>(p, grid, smem, st);  // waits on flags too: one CTA per SM, every CTA resident
-    }
+    // waits on flags too: one CTA per SM, every CTA resident
+    if (mode == 4) return kind == 1 ? launch_one<4, 1>(p, grid, smem, st) : launch_one<4, 0>(p, grid, smem, st);
     if (mode == 0 && kind == 0) return launch_one<0, 0>(p, grid, smem, st);
     if (mode == 1 && kind == 0) return launch_one<1, 0>(p, grid, smem, st);
     if (mode == 0 && kind == 1) return launch_one<0, 1>(p, grid, smem, st);
