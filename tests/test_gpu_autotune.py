@@ -40,7 +40,8 @@ def test_tuned_products_stay_correct(case, dtype, m):
     assert (chosen["path"], chosen["stages"], chosen["up_target"], chosen["down_target"]) == \
         (r["path"], r["stages"], r["up_target"], r["down_target"])
     if dtype == "bf16":
-        assert {c["path"] for c in r["candidates"]} == {1}
+        # the BF16 product: the subtree passes, with or without the hybrid upward pass
+        assert 1 in {c["path"] for c in r["candidates"]} <= {1, 5}
     else:
         assert {1, 4} <= {c["path"] for c in r["candidates"]}
     X = gaussian_rhs(12000, m, 7 + m)
