@@ -370,6 +370,7 @@ struct Solver {
     bool gram = false;   // variant H2_CG_GRAM (m <= 64)
     bool pcg = false;    // block-Jacobi preconditioned block CG (Alg. "pcg block")
     double* Z = nullptr; // [n×m] M⁻¹ R when pcg
+    bool pc_low = false; // M⁻¹ in FP32 (the low-precision iterations of a mixed solve)
     CgDev d{};
     GramDev g{};
     double *R = nullptr, *P = nullptr, *AP = nullptr;
@@ -621,7 +622,7 @@ struct Solver {
         H2_LAUNCH_CHECK();
         if (pcg) {
             // restarted columns take the preconditioned residual as direction
-            if ((rc = bj_apply(A, R, Z, n, m, nullptr, d, st))) return rc;
+            if ((rc = bj_apply(A, R, Z, n, m, nullptr, d, st, pc_low))) return rc;
             k_cg_restart_from<<<grid, blk, 0, st>>>(Z, P, m, n, m, d);
             H2_LAUNCH_CHECK();
         }
@@ -642,7 +643,7 @@ struct Solver {
         if (rc) return rc;
         const double* src = R;
         if (pcg) {
-            if ((rc = bj_apply(A, R, Z, n, m, nullptr, d, st))) return rc;
+            if ((rc = bj_apply(A, R, Z, n, m, nullptr, d, st, pc_low))) return rc;
             src = Z;
         }
         if (gram) return gram_start(P, src, n, m, g, d, st);
@@ -662,7 +663,7 @@ struct Solver {
         H2_CUDA_TRY(cudaMemsetAsync(d.summary, 0, 4 * sizeof(int), st));
         k_cg_init<<<grid2d(), dim3(kColsPerCta, 8), 0, st>>>(B, ldb, R, m, n, m, tol, d);
         H2_LAUNCH_CHECK();
-        int rc = bj_apply(A, R, Z, n, m, nullptr, d, st);
+        int rc = bj_apply(A, R, Z, n, m, nullptr, d, st, pc_low);
         if (rc) return rc;
         k_copy2d<<<copy_grid(), 256, 0, st>>>(Z, m, P, m, n, m);
         H2_LAUNCH_CHECK();
@@ -682,7 +683,7 @@ struct Solver {
                 H2_LAUNCH_CHECK();
                 k_cg_update<<<grid, blk, 0, st>>>(X, ldx, P, AP, R, m, n, m, tol, it, d);
                 H2_LAUNCH_CHECK();
-                if ((rc = bj_apply(A, R, Z, n, m, AP, d, st))) return rc;
+                if ((rc = bj_apply(A, R, Z, n, m, AP, d, st, pc_low))) return rc;
                 k_cg_dir<<<grid, blk, 0, st>>>(P, Z, m, n, m, d);
                 H2_LAUNCH_CHECK();
                 if (it % check_every != 0 && it != max_iter) continue;
@@ -737,7 +738,7 @@ struct Solver {
         k_cg_init<<<grid2d(), dim3(kColsPerCta, 8), 0, st>>>(B, ldb, R, m, n, m, tol, d);
         H2_LAUNCH_CHECK();
         int rc = 0;
-        if (pcg && (rc = bj_apply(A, R, Z, n, m, nullptr, d, st))) return rc;
+        if (pcg && (rc = bj_apply(A, R, Z, n, m, nullptr, d, st, pc_low))) return rc;
         if ((rc = gram_start(P, pcg ? Z : R, n, m, g, d, st))) return rc;
         if (Rt) H2_CUDA_TRY(cudaMemcpyAsync(rupd, d.rnorm, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
         H2_CUDA_TRY(cudaMemcpyAsync(h_summary, d.summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -754,7 +755,7 @@ struct Solver {
                 if ((rc = gram_alpha(P, AP, R, n, m, g, d, st))) return rc;
                 if (pcg) {
                     if ((rc = gram_update(X, ldx, P, AP, R, n, m, g, st))) return rc;
-                    if ((rc = bj_apply(A, R, Z, n, m, nullptr, d, st))) return rc;
+                    if ((rc = bj_apply(A, R, Z, n, m, nullptr, d, st, pc_low))) return rc;
                     if ((rc = gram_gamma_dir_from(P, AP, Z, n, m, tol, g, d, st))) return rc;
                 } else if ((rc = gram_update_dir(X, ldx, P, AP, R, n, m, tol, g, d, st))) {
                     return rc;
@@ -1108,6 +1109,7 @@ int block_cg(h2_matrix* A, const double* B, int64_t ldb, double* X, int64_t ldx,
         S.trans = p->transposed != 0;
         S.gram = p->variant == H2_CG_GRAM;
         S.pcg = p->precond == H2_PRECOND_BLOCK_JACOBI;
+        S.pc_low = p->dtype != H2_F64;
         int rc = S.init();
         if (rc) return rc;
         int total_iters = 0;

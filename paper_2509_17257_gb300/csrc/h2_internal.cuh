@@ -410,6 +410,8 @@ struct h2_matrix {
     bool s_replaced = false;  // h2_coupling_set was called: S_b are no longer g's values  // H2_FORCE_SIMT=1 at build: FP32 product on the CUDA cores only
     // block-Jacobi preconditioner (h2_precond.cu): (G_(t,t) + σI)⁻¹ per leaf, built on first use
     double* bj_inv = nullptr;     // concatenated n_t×n_t inverses, leaf order
+    float* bj_inv32 = nullptr;    // the same rounded to FP32 (the low-precision iterations of mixed solves)
+    int64_t bj_count = 0;         // entries of bj_inv
     int64_t* bj_off = nullptr;    // [n_leaves] element offset of leaf t's inverse
     double bj_sigma = 0.0;        // σ the inverses were formed with
     bool bj_valid = false;
@@ -450,9 +452,9 @@ struct GramDev {
 int bj_prepare(h2_matrix* A, cudaStream_t st);
 // Z = M⁻¹ R (n×m, ld m, caller's point order).  With AP != nullptr also
 // d.gamma[i] = <AP_i, Z_i> / d.beta[i] for the active columns (fixed-order
-// reduction).
+// reduction).  `low`: FP32 arithmetic with the FP32-rounded inverses.
 int bj_apply(h2_matrix* A, const double* R, double* Z, int64_t n, int m, const double* AP, const CgDev& d,
-             cudaStream_t st);
+             cudaStream_t st, bool low = false);
 
 constexpr int kGramMaxCols = 64;
 size_t gram_scratch_bytes(int m);

@@ -9,7 +9,11 @@
 // Apply (k_bj_apply, every iteration): Z|_t̂ = D_t⁻¹ R|_t̂ per leaf, rows
 // gathered from and scattered to the caller's point order, 2 n_t² m flops per
 // leaf; optionally the per-column dots <AP_i, Z_i> for γ_i of the paper's
-// recurrence, reduced in fixed order by the last CTA.
+// recurrence, reduced in fixed order by the last CTA.  In FP64, or, inside the
+// low-precision iterations of a mixed solve, in FP32 with the inverses rounded
+// to FP32 (R and Z stay FP64 in memory, the dots accumulate in FP64): the
+// apply is then as cheap next to the FP32 product as the FP64 apply is next
+// to the FP64 one, and its rounding stays below the FP32 product's.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -113,17 +117,19 @@ __global__ void __launch_bounds__(256) k_bj_invert(const int32_t* __restrict__ l
 // CTA forms γ_c = <AP_c, Z_c> / β_c on active columns.  Thread t owns column
 // t mod cw of the chunk (cw = chunk width rounded up to 32 or 64) and every
 // (256/cw)-th row of the leaf.  Three CTAs fit on an SM (66.5 KB of tiles each).
+template <typename T>
 __global__ void __launch_bounds__(256) k_bj_apply(const double* __restrict__ R, double* __restrict__ Z, int m,
                                                   const int32_t* __restrict__ perm,
                                                   const int32_t* __restrict__ leaves, int NL,
                                                   const int32_t* __restrict__ cl_off,
                                                   const int32_t* __restrict__ cl_size,
                                                   const int64_t* __restrict__ bj_off,
-                                                  const double* __restrict__ inv, const double* __restrict__ AP,
+                                                  const T* __restrict__ inv, const double* __restrict__ AP,
                                                   CgDev d) {
-    extern __shared__ double sm[];
-    double(*sD)[kLd] = (double(*)[kLd])sm;
-    double(*sR)[kLd] = (double(*)[kLd])(sm + 64 * kLd);
+    extern __shared__ double sm_raw[];
+    T* sm = reinterpret_cast<T*>(sm_raw);
+    T(*sD)[kLd] = (T(*)[kLd])sm;
+    T(*sR)[kLd] = (T(*)[kLd])(sm + 64 * kLd);
     __shared__ double red[8][64];
     __shared__ int srow[64];
     const int t = threadIdx.x;
@@ -135,23 +141,23 @@ __global__ void __launch_bounds__(256) k_bj_apply(const double* __restrict__ R, 
         for (int lp = blockIdx.x; lp < NL; lp += gridDim.x) {
             const int cl = leaves[lp];
             const int off = cl_off[cl], l = cl_size[cl];
-            const double* Dt = inv + bj_off[lp];
+            const T* Dt = inv + bj_off[lp];
             __syncthreads();  // previous leaf's tiles are consumed
             for (int a = t; a < l; a += blockDim.x) srow[a] = perm[off + a];
             for (int x = t; x < l * l; x += blockDim.x) sD[x / l][x % l] = Dt[x];
             __syncthreads();
             for (int x = t; x < l * mc; x += blockDim.x) {
                 const int a = x / mc, c = x % mc;
-                sR[a][c] = R[(int64_t)srow[a] * m + c0 + c];
+                sR[a][c] = (T)R[(int64_t)srow[a] * m + c0 + c];
             }
             __syncthreads();
             if (tc < mc)
                 for (int a = tr; a < l; a += nr) {
-                    double z = 0.0;
+                    T z = 0;
                     for (int b = 0; b < l; ++b) z = fma(sD[a][b], sR[b][tc], z);
                     const int64_t e = (int64_t)srow[a] * m + c0 + tc;
-                    Z[e] = z;
-                    if (AP) aq = fma(AP[e], z, aq);
+                    Z[e] = (double)z;
+                    if (AP) aq = fma(AP[e], (double)z, aq);
                 }
         }
         if (AP) {
@@ -181,6 +187,11 @@ __global__ void __launch_bounds__(256) k_bj_apply(const double* __restrict__ R, 
     if (t == 0) d.ticket[0] = 0;
 }
 
+__global__ void k_bj_round_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
 int g_bj_attr_device = -1;
 
 int bj_attr() {
@@ -188,7 +199,8 @@ int bj_attr() {
     H2_CUDA_TRY(cudaGetDevice(&dev));
     if (dev == g_bj_attr_device) return 0;
     H2_CUDA_TRY(cudaFuncSetAttribute(k_bj_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, kBjSmem));
-    H2_CUDA_TRY(cudaFuncSetAttribute(k_bj_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, kBjSmem));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_bj_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBjSmem));
+    H2_CUDA_TRY(cudaFuncSetAttribute(k_bj_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBjSmem));
     g_bj_attr_device = dev;
     return 0;
 }
@@ -211,6 +223,8 @@ int bj_prepare(h2_matrix* A, cudaStream_t st) {
         }
         if ((rc = device_alloc(A, (void**)&A->bj_off, NL * sizeof(int64_t)))) return rc;
         if ((rc = device_alloc(A, (void**)&A->bj_inv, std::max<int64_t>(acc, 1) * sizeof(double)))) return rc;
+        if ((rc = device_alloc(A, (void**)&A->bj_inv32, std::max<int64_t>(acc, 1) * sizeof(float)))) return rc;
+        A->bj_count = acc;
         H2_CUDA_TRY(cudaMemcpyAsync(A->bj_off, off.data(), NL * sizeof(int64_t), cudaMemcpyHostToDevice, st));
         H2_CUDA_TRY(cudaStreamSynchronize(st));  // `off` is pageable host memory
     }
@@ -229,18 +243,27 @@ int bj_prepare(h2_matrix* A, cudaStream_t st) {
         set_error("block-Jacobi preconditioner: a diagonal block G_(t,t) + σI is not positive definite");
         return H2_E_BREAKDOWN;
     }
+    if (A->bj_count > 0) {
+        k_bj_round_f32<<<(unsigned)std::min<int64_t>((A->bj_count + 255) / 256, 152 * 8), 256, 0, st>>>(
+            A->bj_inv, A->bj_inv32, A->bj_count);
+        H2_LAUNCH_CHECK();
+    }
     A->bj_valid = true;
     A->bj_sigma = A->sigma;
     return 0;
 }
 
 int bj_apply(h2_matrix* A, const double* R, double* Z, int64_t n, int m, const double* AP, const CgDev& d,
-             cudaStream_t st) {
+             cudaStream_t st, bool low) {
     (void)n;
     const int NL = (int)A->leaves.size();
     const unsigned g = (unsigned)std::min(NL, kBjCtas);
-    k_bj_apply<<<g, 256, kBjSmem, st>>>(R, Z, m, A->d_perm, A->d_leaves, NL, A->d_cl_off, A->d_cl_size, A->bj_off,
-                                        A->bj_inv, AP, d);
+    if (low)
+        k_bj_apply<float><<<g, 256, kBjSmem, st>>>(R, Z, m, A->d_perm, A->d_leaves, NL, A->d_cl_off, A->d_cl_size,
+                                                   A->bj_off, A->bj_inv32, AP, d);
+    else
+        k_bj_apply<double><<<g, 256, kBjSmem, st>>>(R, Z, m, A->d_perm, A->d_leaves, NL, A->d_cl_off, A->d_cl_size,
+                                                    A->bj_off, A->bj_inv, AP, d);
     H2_LAUNCH_CHECK();
     return 0;
 }

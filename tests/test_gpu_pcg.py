@@ -77,6 +77,14 @@ def test_pcg_mixed_precision(case4096, refine):
     assert _true_rel(A, B, X).max() <= 1.5e-8  # dense recomputation in another rounding order
     assert res.rel_residual.max() <= 1e-8  # the solver confirms convergence on this FP64 residual
     assert rel_fro(X, sla.cho_solve(cf, B)) <= 1e-6
+    if refine == 2:
+        # the low-precision iterations apply M⁻¹ in FP32: no more iterations than
+        # the FP64 solve with the FP64 apply, within a margin
+        X64 = torch.zeros_like(Xd)
+        r64 = G.block_cg(torch.from_numpy(B).cuda(), X64, tol=1e-8, max_iter=5000, dtype="f64",
+                         precond="block_jacobi", check_every=2)
+        assert r64.status == 0
+        assert res.iterations <= 1.2 * r64.iterations + 10, (res.iterations, r64.iterations)
 
 
 def test_pcg_shift_change_refactors(case4096, P):
