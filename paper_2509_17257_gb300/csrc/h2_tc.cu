@@ -879,9 +879,8 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
             }
             if (LIST && item_role(cur) == kRoleTransfer) {
                 // A transfer item of the hybrid upward pass: x̂ of the cluster as a
-                // split BF16 tile (row 2i: bf16(v), row 2i + 1: bf16(v - bf16(v)); rows
-                // of columns i >= mc get zero sums, as their activation rows are zero),
-                // stored by the even-row threads, ordered for the bulk copies of other
+                // split BF16 tile (row 2i: bf16(v), row 2i + 1: bf16(v - bf16(v)); zero
+                // for columns i >= mc and past row k), stored by the even-row threads, ordered for the bulk copies of other
                 // CTAs by a proxy fence, and released by the ready flag once all four
                 // warps have stored.  Every epilogue warp meets the barrier once per
                 // transfer item, failed or not, and all of them learn of a failure.
@@ -892,14 +891,15 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1) k_tc_gemm(const TcGemmP
                 }
                 if (row >= 0 && !(row & 1) && i < R / 2) {
                     uint8_t* gt = p.out_act + (int64_t)id * p.KP * R * 2;
+                    const bool live = i < p.mc;
 #pragma unroll
                     for (int u = 0; u < kAccCols / 8; ++u) {
                         if (8 * u >= p.KP) break;
                         uint32_t hw[4], lw[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            const float v0 = 8 * u + 2 * e < p.k ? sum[8 * u + 2 * e] : 0.f;
-                            const float v1 = 8 * u + 2 * e + 1 < p.k ? sum[8 * u + 2 * e + 1] : 0.f;
+                            const float v0 = live && 8 * u + 2 * e < p.k ? sum[8 * u + 2 * e] : 0.f;
+                            const float v1 = live && 8 * u + 2 * e + 1 < p.k ? sum[8 * u + 2 * e + 1] : 0.f;
                             const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
                             const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
                             const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
