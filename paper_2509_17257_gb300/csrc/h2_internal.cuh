@@ -306,6 +306,7 @@ struct SyncBufs {
     int epoch = 0;
     int* err = nullptr;
     int* fflag = nullptr;  // [2 × n_clusters] ready flags of the tensor-core upward and downward passes
+    unsigned* claim2 = nullptr;  // the tensor-core chain's downward-pass task counter (claim is the upward one)
 };
 
 struct Workspace {

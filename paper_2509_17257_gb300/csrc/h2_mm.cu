@@ -229,8 +229,17 @@ __device__ __forceinline__ int row_lanes(int m) {
 
 // ---- gather: Xp[i, :] = X[perm[i], :] in the compute type ----
 template <typename T>
+// With z1/z2/z3 it also zeroes the counters and flags the passes after it use
+// (in place of separate memsets on the stream).
 __global__ void k_gather(const double* __restrict__ X, int64_t ldx, const int32_t* __restrict__ perm, int64_t n,
-                         int m, T* __restrict__ Xp) {
+                         int m, T* __restrict__ Xp, unsigned* __restrict__ z1 = nullptr, int n1 = 0,
+                         unsigned* __restrict__ z2 = nullptr, int n2 = 0, int* __restrict__ z3 = nullptr, int n3 = 0) {
+    {
+        const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t i = t; i < n1; i += nt) z1[i] = 0u;
+        for (int64_t i = t; i < n2; i += nt) z2[i] = 0u;
+        for (int64_t i = t; i < n3; i += nt) z3[i] = 0;
+    }
     const int P = row_lanes(m), R = 32 / P;
     const int lane = threadIdx.x & 31, sub = lane / P, cl = lane % P;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1607,10 +1616,19 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         const unsigned gy = (unsigned)((mc + NT - 1) / NT), gzk = (unsigned)((k + MT - 1) / MT);
         PhaseMarks marks(A, st);
         marks.mark();
+        // the subtree passes' arrival counters and task counters, and the hybrid
+        // launch's ready flags, are zeroed by the gather
+        const bool reset_in_gather = fast && !flow && sbc.claim2;
         {
             const int64_t total = n * mc;
             const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
-            k_gather<float><<<g, 256, 0, st>>>(X + c0, ldx, A->d_perm, n, mc, Xp);
+            // claim2 follows the claim counters in the same allocation: zero them all
+            if (reset_in_gather)
+                k_gather<float><<<g, 256, 0, st>>>(X + c0, ldx, A->d_perm, n, mc, Xp, sbc.cnt, (int)nc, sbc.claim,
+                                                   (int)(sbc.claim2 - sbc.claim) + 1, hybrid ? sbc.fflag : nullptr,
+                                                   hybrid ? (int)nc : 0);
+            else
+                k_gather<float><<<g, 256, 0, st>>>(X + c0, ldx, A->d_perm, n, mc, Xp);
             H2_LAUNCH_CHECK();
         }
         // (fast: the subtree-owning CUDA-core transfer passes apply, rows of 16-byte
@@ -1739,8 +1757,10 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
             const PackOut pk{xcm, Xcm, D.xkoff, KP, R, es};
             const int usm = up_own_smem_bytes(fcn, A->up_entries);
             const unsigned g = (unsigned)std::min(A->up_ntasks, 152 * std::max(1, (227 * 1024) / (usm + 2048)));
-            H2_CUDA_TRY(cudaMemsetAsync(sbc.cnt, 0, (size_t)nc * sizeof(unsigned), st));
-            H2_CUDA_TRY(cudaMemsetAsync(sbc.claim, 0, sizeof(unsigned), st));
+            if (!reset_in_gather) {
+                H2_CUDA_TRY(cudaMemsetAsync(sbc.cnt, 0, (size_t)nc * sizeof(unsigned), st));
+                H2_CUDA_TRY(cudaMemsetAsync(sbc.claim, 0, sizeof(unsigned), st));
+            }
             const int climb = hybrid ? 0 : 1;
             // q = 4: the inner steps and the climb apply E_sᵀ as Kronecker products
             const float* ukron = (k == 64 && A->use_kron) ? (const float*)A->f32.kron : nullptr;
@@ -1786,7 +1806,7 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
             cp.out_act = xcm;  // the transfer items' split tiles
             cp.flag = sbc.fflag;
             cp.epoch = 1;
-            H2_CUDA_TRY(cudaMemsetAsync(sbc.fflag, 0, (size_t)nc * sizeof(int), st));
+            if (!reset_in_gather) H2_CUDA_TRY(cudaMemsetAsync(sbc.fflag, 0, (size_t)nc * sizeof(int), st));
         }
         marks.kernel_begin();
         if (cp.n_items > 0 &&
@@ -1800,7 +1820,9 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
             if (n_items > 0) {
                 const PackOut pk{ycm, nullptr, nullptr, KP, R, es};
                 leaf_y_packed = true;
-                H2_CUDA_TRY(cudaMemsetAsync(sbc.claim, 0, sizeof(unsigned), st));
+                // the task counter of this pass: claim2, zeroed by the gather (else claim again)
+                unsigned* dclaim = reset_in_gather ? sbc.claim2 : sbc.claim;
+                if (!reset_in_gather) H2_CUDA_TRY(cudaMemsetAsync(sbc.claim, 0, sizeof(unsigned), st));
                 const float* Et = (const float*)A->f32.Et;
                 const int smem = down_own_smem_bytes(fcn, A->dn_entries);
                 const unsigned g = (unsigned)std::min(A->dn_ntasks, 152 * std::max(1, (227 * 1024) / (smem + 4096)));
@@ -1811,12 +1833,12 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
                     const int ksm = down_kron_smem_bytes(fcn, A->dn_entries);
                     const unsigned gk =
                         (unsigned)std::min(A->dn_ntasks, 152 * std::max(1, (227 * 1024) / (ksm + 4096)));
-                    if (fcn == 1) k_down_kron<1><<<gk, 128, ksm, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, kron, yhat, sbc.claim, sbc.err, mc, pk);
-                    else if (fcn == 2) k_down_kron<2><<<gk, 128, ksm, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, kron, yhat, sbc.claim, sbc.err, mc, pk);
-                    else k_down_kron<4><<<gk, 128, ksm, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, kron, yhat, sbc.claim, sbc.err, mc, pk);
-                } else if (fcn == 1) k_down_own<1><<<g, 128, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
-                else if (fcn == 2) k_down_own<2><<<g, 128, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
-                else k_down_own<4><<<g, 128, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, sbc.claim, sbc.err, k, mc, pk);
+                    if (fcn == 1) k_down_kron<1><<<gk, 128, ksm, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, kron, yhat, dclaim, sbc.err, mc, pk);
+                    else if (fcn == 2) k_down_kron<2><<<gk, 128, ksm, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, kron, yhat, dclaim, sbc.err, mc, pk);
+                    else k_down_kron<4><<<gk, 128, ksm, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, kron, yhat, dclaim, sbc.err, mc, pk);
+                } else if (fcn == 1) k_down_own<1><<<g, 128, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, dclaim, sbc.err, k, mc, pk);
+                else if (fcn == 2) k_down_own<2><<<g, 128, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, dclaim, sbc.err, k, mc, pk);
+                else k_down_own<4><<<g, 128, smem, st>>>(A->d_dn_task_ptr, A->dn_ntasks, A->d_dn_steps, Et, yhat, dclaim, sbc.err, k, mc, pk);
                 H2_LAUNCH_CHECK();
             }
         } else if ((rc = backward_pass<float, RM, CN>(A, E, yhat, mc, gy, gzk, st, sbc))) {
@@ -1900,18 +1922,20 @@ int ensure_sync(h2_matrix* A, int64_t tiles, cudaStream_t st, SyncBufs* sb) {
         A->sync_cnt = nullptr;
         A->sync_tiles = 0;
         const size_t per = (size_t)A->nc * tiles;
-        const size_t bytes = per * (sizeof(unsigned) + sizeof(int)) + tiles * sizeof(unsigned) +
+        // claim: `tiles` counters and one more (the tensor-core chain's downward pass)
+        const size_t bytes = per * (sizeof(unsigned) + sizeof(int)) + (tiles + 1) * sizeof(unsigned) +
                              2 * (size_t)A->nc * sizeof(int);
         H2_CUDA_TRY(cudaMalloc(&A->sync_cnt, bytes));
         H2_CUDA_TRY(cudaMemsetAsync(A->sync_cnt, 0, bytes, st));
         A->sync_flag = (int*)(A->sync_cnt + per);
         A->sync_claim = (unsigned*)(A->sync_flag + per);
-        A->sync_fflag = (int*)(A->sync_claim + tiles);
+        A->sync_fflag = (int*)(A->sync_claim + tiles + 1);
         A->sync_tiles = tiles;
     }
     sb->cnt = A->sync_cnt;
     sb->flag = A->sync_flag;
     sb->claim = A->sync_claim;
+    sb->claim2 = A->sync_claim + A->sync_tiles;
     sb->fflag = A->sync_fflag;
     sb->epoch = 1;  // flags are cleared before every downward pass
     sb->err = A->err_dev;
