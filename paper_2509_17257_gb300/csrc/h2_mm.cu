@@ -229,16 +229,24 @@ __device__ __forceinline__ int row_lanes(int m) {
 
 // ---- gather: Xp[i, :] = X[perm[i], :] in the compute type ----
 template <typename T>
-// With z1/z2/z3 it also zeroes the counters and flags the passes after it use
-// (in place of separate memsets on the stream).
+// With z1/z2/z3 it also zeroes the counters and flags the passes after it use,
+// and with zid the k×zmc blocks of ŷ (rows of zld) of the clusters zid[0..nzc)
+// (in place of separate memsets and launches on the stream).
 __global__ void k_gather(const double* __restrict__ X, int64_t ldx, const int32_t* __restrict__ perm, int64_t n,
                          int m, T* __restrict__ Xp, unsigned* __restrict__ z1 = nullptr, int n1 = 0,
-                         unsigned* __restrict__ z2 = nullptr, int n2 = 0, int* __restrict__ z3 = nullptr, int n3 = 0) {
+                         unsigned* __restrict__ z2 = nullptr, int n2 = 0, int* __restrict__ z3 = nullptr, int n3 = 0,
+                         const int32_t* __restrict__ zid = nullptr, int nzc = 0, float* __restrict__ zy = nullptr,
+                         int zk = 0, int zld = 0, int zmc = 0) {
     {
         const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
         for (int64_t i = t; i < n1; i += nt) z1[i] = 0u;
         for (int64_t i = t; i < n2; i += nt) z2[i] = 0u;
         for (int64_t i = t; i < n3; i += nt) z3[i] = 0;
+        const int64_t blk = (int64_t)zk * zmc;
+        for (int64_t e = t; e < nzc * blk; e += nt) {
+            const int64_t c = e / blk, r = e % blk;
+            zy[((int64_t)zid[c] * zk + r / zmc) * zld + r % zmc] = 0.f;
+        }
     }
     const int P = row_lanes(m), R = 32 / P;
     const int lane = threadIdx.x & 31, sub = lane / P, cl = lane % P;
@@ -1623,10 +1631,13 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
             const int64_t total = n * mc;
             const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
             // claim2 follows the claim counters in the same allocation: zero them all
+            // with the hybrid pass (no climb, so nothing writes ŷ before the coupling
+            // launch) also ŷ of the clusters without couplings
             if (reset_in_gather)
                 k_gather<float><<<g, 256, 0, st>>>(X + c0, ldx, A->d_perm, n, mc, Xp, sbc.cnt, (int)nc, sbc.claim,
                                                    (int)(sbc.claim2 - sbc.claim) + 1, hybrid ? sbc.fflag : nullptr,
-                                                   hybrid ? (int)nc : 0);
+                                                   hybrid ? (int)nc : 0, hybrid ? D.c_zero : nullptr,
+                                                   hybrid ? D.c_nzero : 0, yhat, k, mc, mc);
             else
                 k_gather<float><<<g, 256, 0, st>>>(X + c0, ldx, A->d_perm, n, mc, Xp);
             H2_LAUNCH_CHECK();
@@ -1779,7 +1790,8 @@ int run_chain_tc(h2_matrix* A, int kind, double alpha, const double* X, int64_t 
         // Aᵀ: the coupling runs over column clusters with S_bᵀ, the leaf phase over
         // column leaves with G_bᵀ (tiles and lists of build_tc_transposed)
         const uint8_t* bmat = trans ? (kind == 0 ? D.matT : D.matT32) : (kind == 0 ? D.mat : D.mat32);
-        if ((rc = launch_zero_clusters(trans ? D.ct_zero : D.c_zero, trans ? D.ct_nzero : D.c_nzero, yhat, k, mc, mc,
+        if (!(reset_in_gather && hybrid) &&
+            (rc = launch_zero_clusters(trans ? D.ct_zero : D.c_zero, trans ? D.ct_nzero : D.c_nzero, yhat, k, mc, mc,
                                        st)))
             return rc;
         TcGemmParams cp{};
