@@ -142,13 +142,35 @@ __global__ void __launch_bounds__(256) k_bj_apply(const double* __restrict__ R, 
             const int cl = leaves[lp];
             const int off = cl_off[cl], l = cl_size[cl];
             const T* Dt = inv + bj_off[lp];
+            // The leaf's loads are issued together, each thread's into registers
+            // (l² ≤ 4096 and l·mc ≤ 4096 entries: at most 16 per thread), so a leaf
+            // waits for two rounds of global latency (D_t⁻¹ and the point indices,
+            // then the rows of R) instead of one per loop trip.
+            constexpr int kPer = 64 * 64 / 256;
+            T dv[kPer];
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                const int x = t + 256 * i;
+                dv[i] = x < l * l ? Dt[x] : (T)0;
+            }
             __syncthreads();  // previous leaf's tiles are consumed
-            for (int a = t; a < l; a += blockDim.x) srow[a] = perm[off + a];
-            for (int x = t; x < l * l; x += blockDim.x) sD[x / l][x % l] = Dt[x];
+            if (t < l) srow[t] = perm[off + t];
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                const int x = t + 256 * i;
+                if (x < l * l) sD[x / l][x % l] = dv[i];
+            }
             __syncthreads();
-            for (int x = t; x < l * mc; x += blockDim.x) {
-                const int a = x / mc, c = x % mc;
-                sR[a][c] = (T)R[(int64_t)srow[a] * m + c0 + c];
+            double rv[kPer];
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                const int x = t + 256 * i;
+                rv[i] = x < l * mc ? R[(int64_t)srow[x / mc] * m + c0 + x % mc] : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                const int x = t + 256 * i;
+                if (x < l * mc) sR[x / mc][x % mc] = (T)rv[i];
             }
             __syncthreads();
             if (tc < mc)
