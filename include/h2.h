@@ -121,9 +121,10 @@ typedef struct h2_info_t {
                              k <= 64 the transfer passes pack the tensor-core operands
                              themselves, otherwise three packing launches are counted  */
     int32_t kernel;       /* h2_kernel of the build                                     */
-    int32_t hybrid;       /* 1: the FP32 tensor-core product takes, by default, the hybrid
-                             upward pass (the CUDA-core subtree pass stops at its cut, the
-                             clusters above it are transfer items of the coupling launch) */
+    int32_t hybrid;       /* 1: the FP32 and BF16 tensor-core products take, by default,
+                             the hybrid upward pass (the CUDA-core subtree pass stops at its
+                             cut, the clusters above it are transfer items of the coupling
+                             launch)                                                      */
     int64_t n_above_cut;  /* clusters above that cut (transfer items of that launch)      */
 } h2_info_t;
 
@@ -401,7 +402,7 @@ int h2_batch_block_cg(h2_batch* batch, const double* const* B, const int64_t* ld
  *      path 3; FP32 only), CUDA cores only (path 4; FP32 only), and tensor
  *      cores with the CUDA-core subtree passes stopping at the upward cut,
  *      whose clusters above the cut become transfer items of the coupling
- *      launch (path 5; FP32 only);
+ *      launch (path 5; FP32 and BF16);
  *   2. on the best path, the pipeline stage count of the tensor-core kernels
  *      (4 and 5 against as many as fit);
  *   3. on paths 1 and 5, the cut targets of the CUDA-core subtree passes (the task

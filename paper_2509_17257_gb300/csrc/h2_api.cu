@@ -319,12 +319,12 @@ int h2_info(const h2_matrix* A, h2_info_t* info) {
     // clusters without couplings (done by the gather with the hybrid upward pass); where the subtree-owning
     // transfer passes do not apply (k % 4 != 0 or k > 64) also the packing of X, x̂ and ŷ
     const bool own_passes = A->f32.Et && A->k % 8 == 0 && A->k <= 64;
-    const bool hybrid_default = own_passes && A->tc.hybrid && A->tc.h_default;
+    const bool hybrid_default = own_passes && (A->tc.hybrid || A->tc.hybrid_bf16) && A->tc.h_default;
     info->launches_tc = A->tc.built ? (own_passes ? 5 : 8) + (A->down_ptr.back() > 0 ? 1 : 0) +
                                           (A->tc.c_nzero > 0 && !hybrid_default ? 1 : 0)
                                     : 0;
     info->kernel = A->kernel;
-    info->hybrid = A->tc.hybrid && A->tc.h_default ? 1 : 0;
+    info->hybrid = (A->tc.hybrid || A->tc.hybrid_bf16) && A->tc.h_default ? 1 : 0;
     info->n_above_cut = A->tc.h_nabove;
     return 0;
 }
